@@ -1,0 +1,231 @@
+"""ctypes front end of the CPU oracle.
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by the smoke check and by
+the benchmark's CPU-baseline leg.  The product package never imports it.
+
+The problem argument is any object with the attributes of a pooled problem
+description (grid_off, energy, sigma_t, f_abs, awr, mat_off, nuc_id, density,
+edges, precision, geoms[]); no module of the product is imported here.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import build as _build
+
+STATUS_ALIVE, STATUS_ABSORBED, STATUS_LEAKED, STATUS_CUTOFF, STATUS_LIMIT, STATUS_LEAKED_FAR = range(6)
+S_COLLISION, S_ABSORPTION, S_LEAK, S_CUTOFF, S_LIMIT, S_LEAK_FAR, S_FLIGHT, S_HISTORY = range(8)
+NSCAL = 8
+MAX_FLIGHTS = 100000
+
+_P = C.POINTER
+
+
+class _Problem(C.Structure):
+    _fields_ = [
+        ("n_nuc", C.c_int32), ("grid_off", _P(C.c_int64)), ("energy", _P(C.c_double)),
+        ("sigma_t", _P(C.c_double)), ("f_abs", _P(C.c_double)), ("awr", _P(C.c_double)),
+        ("n_mat", C.c_int32), ("mat_off", _P(C.c_int32)), ("nuc_id", _P(C.c_int32)),
+        ("density", _P(C.c_double)), ("n_bins", C.c_int32), ("edges", _P(C.c_double)),
+        ("precision", C.c_int32),
+        ("kind", C.c_int32), ("source", C.c_int32), ("E0", C.c_double), ("E_cut", C.c_double),
+        ("mat", C.c_int32), ("n", C.c_int32), ("pitch", C.c_double), ("radius", C.c_double),
+        ("height", C.c_double), ("mat_pin", C.c_int32), ("mat_mod", C.c_int32),
+        ("bc_side", C.c_int32), ("bc_z", C.c_int32), ("n_layers", C.c_int32),
+        ("layer_dx", C.c_double), ("n_first", C.c_int32), ("mat_a", C.c_int32),
+        ("mat_b", C.c_int32),
+    ]
+
+
+class _Result(C.Structure):
+    _fields_ = [
+        ("n_coll", _P(C.c_int32)), ("status", _P(C.c_int8)), ("n_flights", _P(C.c_int32)),
+        ("n_draws", _P(C.c_uint32)), ("E", _P(C.c_double)), ("x", _P(C.c_double)),
+        ("y", _P(C.c_double)), ("z", _P(C.c_double)), ("flux", _P(C.c_double)),
+        ("counts", _P(C.c_int64)), ("weights", _P(C.c_double)),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build()
+        L = C.CDLL(path)
+        L.or_philox4x64_10.argtypes = [_P(C.c_uint64), _P(C.c_uint64), _P(C.c_uint64)]
+        L.or_u01.argtypes = [C.c_uint64]
+        L.or_u01.restype = C.c_double
+        L.or_log.argtypes = [C.c_double]
+        L.or_log.restype = C.c_double
+        L.or_search.argtypes = [_P(C.c_double), C.c_int64, C.c_double]
+        L.or_search.restype = C.c_int64
+        L.or_micro.argtypes = [_P(_Problem), C.c_int32, C.c_double]
+        L.or_micro.restype = C.c_double
+        L.or_macro.argtypes = [_P(_Problem), C.c_int32, _P(C.c_double), C.c_int64,
+                               _P(C.c_double), _P(C.c_double)]
+        L.or_macro.restype = C.c_int
+        L.or_dist_cylinder.argtypes = [C.c_double] * 5 + [C.c_int]
+        L.or_dist_cylinder.restype = C.c_double
+        L.or_elastic.argtypes = [C.c_double, C.c_double, C.c_double, _P(C.c_double), _P(C.c_double)]
+        L.or_rotate.argtypes = [_P(C.c_double)] * 3 + [C.c_double] * 3
+        L.or_run.argtypes = [_P(_Problem), C.c_uint64, C.c_uint64, C.c_int64, C.c_int64,
+                             C.c_int, _P(_Result)]
+        L.or_run.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(_P(ctype))
+
+
+def philox(ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint64)
+    k = np.ascontiguousarray(key, dtype=np.uint64)
+    out = np.zeros(4, dtype=np.uint64)
+    lib().or_philox4x64_10(_ptr(c, C.c_uint64), _ptr(k, C.c_uint64), _ptr(out, C.c_uint64))
+    return out
+
+
+def u01(x: int) -> float:
+    return lib().or_u01(int(x))
+
+
+def log(x: float) -> float:
+    return lib().or_log(float(x))
+
+
+def search(g, E: float) -> int:
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    return int(lib().or_search(_ptr(g, C.c_double), len(g), float(E)))
+
+
+def dist_cylinder(dx, dy, u, v, r, inside) -> float:
+    return lib().or_dist_cylinder(dx, dy, u, v, r, int(inside))
+
+
+def elastic(E, A, mu):
+    e = C.c_double()
+    m = C.c_double()
+    lib().or_elastic(E, A, mu, C.byref(e), C.byref(m))
+    return e.value, m.value
+
+
+def rotate(u, v, w, mu, cphi, sphi):
+    a, b, c = C.c_double(u), C.c_double(v), C.c_double(w)
+    lib().or_rotate(C.byref(a), C.byref(b), C.byref(c), mu, cphi, sphi)
+    return a.value, b.value, c.value
+
+
+class _Bound:
+    """Keeps the numpy arrays alive while the C structure points at them."""
+
+    def __init__(self, prob, geom_index: int = 0, precision=None):
+        g = prob.geoms[geom_index]
+        self.arrs = dict(
+            grid_off=np.ascontiguousarray(prob.grid_off, dtype=np.int64),
+            energy=np.ascontiguousarray(prob.energy, dtype=np.float64),
+            sigma_t=np.ascontiguousarray(prob.sigma_t, dtype=np.float64),
+            f_abs=np.ascontiguousarray(prob.f_abs, dtype=np.float64),
+            awr=np.ascontiguousarray(prob.awr, dtype=np.float64),
+            mat_off=np.ascontiguousarray(prob.mat_off, dtype=np.int32),
+            nuc_id=np.ascontiguousarray(prob.nuc_id, dtype=np.int32),
+            density=np.ascontiguousarray(prob.density, dtype=np.float64),
+            edges=np.ascontiguousarray(prob.edges, dtype=np.float64),
+        )
+        a = self.arrs
+        p = _Problem()
+        p.n_nuc = len(a["grid_off"]) - 1
+        p.grid_off = _ptr(a["grid_off"], C.c_int64)
+        p.energy = _ptr(a["energy"], C.c_double)
+        p.sigma_t = _ptr(a["sigma_t"], C.c_double)
+        p.f_abs = _ptr(a["f_abs"], C.c_double)
+        p.awr = _ptr(a["awr"], C.c_double)
+        p.n_mat = len(a["mat_off"]) - 1
+        p.mat_off = _ptr(a["mat_off"], C.c_int32)
+        p.nuc_id = _ptr(a["nuc_id"], C.c_int32)
+        p.density = _ptr(a["density"], C.c_double)
+        p.n_bins = len(a["edges"]) - 1
+        p.edges = _ptr(a["edges"], C.c_double)
+        p.precision = int(prob.precision if precision is None else precision)
+        for name in ("kind", "source", "mat", "n", "mat_pin", "mat_mod", "bc_side", "bc_z",
+                     "n_layers", "n_first", "mat_a", "mat_b"):
+            setattr(p, name, int(getattr(g, name)))
+        for name in ("E0", "E_cut", "pitch", "radius", "height", "layer_dx"):
+            setattr(p, name, float(getattr(g, name)))
+        self.p = p
+        self.n_cells = g.n_cells()
+        self.n_bins = p.n_bins
+
+
+def micro(prob, nuc: int, E: float) -> float:
+    b = _Bound(prob, precision=0)
+    return lib().or_micro(C.byref(b.p), int(nuc), float(E))
+
+
+def macro(prob, mat: int, E, precision=None):
+    b = _Bound(prob, precision=precision)
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    st = np.zeros_like(E)
+    sa = np.zeros_like(E)
+    rc = lib().or_macro(C.byref(b.p), int(mat), _ptr(E, C.c_double), len(E),
+                        _ptr(st, C.c_double), _ptr(sa, C.c_double))
+    if rc != 0:
+        raise MemoryError("oracle lookup failed")
+    return st, sa
+
+
+def key_hi(problem_index: int, batch: int) -> int:
+    """Second Philox key word: problem index in the high 32 bits, batch low."""
+    return ((int(problem_index) & 0xFFFFFFFF) << 32) | (int(batch) & 0xFFFFFFFF)
+
+
+def run(prob, seed: int, batch: int = 0, first_id: int = 0, n=None, geom_index: int = 0,
+        problem_index: int = 0, threads=None, precision=None):
+    """Histories [first_id, first_id + n) of one batch; returns a dict with
+    per-particle outcomes, the flux tally [n_cells, n_bins] and the scalars."""
+    b = _Bound(prob, geom_index, precision)
+    if n is None:
+        n = prob.n_particles[geom_index]
+    n = int(n)
+    if threads is None:
+        threads = len(os.sched_getaffinity(0))
+    out = dict(
+        n_coll=np.zeros(n, np.int32), status=np.zeros(n, np.int8),
+        n_flights=np.zeros(n, np.int32), n_draws=np.zeros(n, np.uint32),
+        E=np.zeros(n), x=np.zeros(n), y=np.zeros(n), z=np.zeros(n),
+        flux=np.zeros((b.n_cells, b.n_bins)), counts=np.zeros(NSCAL, np.int64),
+        weights=np.zeros(NSCAL),
+    )
+    r = _Result()
+    r.n_coll = _ptr(out["n_coll"], C.c_int32)
+    r.status = _ptr(out["status"], C.c_int8)
+    r.n_flights = _ptr(out["n_flights"], C.c_int32)
+    r.n_draws = _ptr(out["n_draws"], C.c_uint32)
+    for k in ("E", "x", "y", "z", "flux", "weights"):
+        setattr(r, k, _ptr(out[k], C.c_double))
+    r.counts = _ptr(out["counts"], C.c_int64)
+    rc = lib().or_run(C.byref(b.p), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                      key_hi(problem_index, batch), int(first_id), n, int(threads), C.byref(r))
+    if rc != 0:
+        raise MemoryError("oracle run failed")
+    return out
+
+
+def birth_state(prob, seed: int, id_: int, batch: int = 0, problem_index: int = 0,
+                geom_index: int = 0):
+    """(x, y, z, u, v, w, E), (i, j, inside, material) of a particle at birth."""
+    b = _Bound(prob, geom_index)
+    st = np.zeros(7)
+    cell = np.zeros(4, np.int32)
+    L = lib()
+    L.or_birth_state.argtypes = [_P(_Problem), C.c_uint64, C.c_uint64, C.c_int64,
+                                 _P(C.c_double), _P(C.c_int32)]
+    L.or_birth_state(C.byref(b.p), int(seed), key_hi(problem_index, batch), int(id_),
+                     _ptr(st, C.c_double), _ptr(cell, C.c_int32))
+    return st, cell
