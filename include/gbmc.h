@@ -1,0 +1,266 @@
+/*
+ * gbmc -- GB300-native event-based continuous-energy Monte Carlo transport
+ * hot path.  C ABI (C99, extern "C"): plain pointers and sizes only.
+ *
+ * The operations follow the method studied in Tramm et al., "Performance
+ * Portable Monte Carlo Particle Transport on Intel, NVIDIA, and AMD GPUs":
+ *   - event-based parallelism, one narrow kernel per event type over every
+ *     queued particle (Sec. 2, "Event-Based Parallelism");
+ *   - particles sorted by material and energy before the cross-section
+ *     lookup, the dominant kernel (Sec. 2, "Sorting");
+ *   - tallies scored during active batches (Sec. 2, "Tallying");
+ *   - a cap on particles in flight, refilled from the batch's remaining
+ *     source particles (Sec. 2, "In-Flight Particles");
+ *   - surface (ray) tracking, delta tracking disabled (Sec. 3);
+ *   - results reproducible between a serial history-based CPU run and the
+ *     event-based GPU run up to floating-point summation order (Sec. 4.3).
+ *
+ * Conventions for every entry point:
+ *   - return value: GBMC_OK (0) or a negative GBMC_ERR_* code; no exception
+ *     or exit crosses the ABI; gbmc_last_error() returns a context-owned
+ *     message describing the last failure;
+ *   - host pointers are read (or written) during the call only and never
+ *     retained; device memory is allocated and owned by the context unless
+ *     an entry point says it takes device pointers from the caller;
+ *   - units: energies in eV, lengths in cm, microscopic cross sections in
+ *     barns, densities in atoms/(barn cm);
+ *   - one context drives one device; calls on one context must not overlap.
+ */
+#ifndef GBMC_H
+#define GBMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define GBMC_OK 0
+#define GBMC_ERR_INVALID_ARG (-1)     /* argument failed validation */
+#define GBMC_ERR_NOT_INITIALIZED (-2) /* tables / materials / tally not loaded */
+#define GBMC_ERR_OOM (-3)             /* device allocation failed */
+#define GBMC_ERR_CUDA (-4)            /* a CUDA runtime call failed */
+#define GBMC_ERR_TIMEOUT (-5)         /* the device event loop hit its iteration bound */
+#define GBMC_ERR_DEVICE_FLAG (-6)     /* a kernel flagged an inconsistency */
+#define GBMC_ERR_UNSUPPORTED (-7)     /* feature not available on this device */
+
+/* ---- table precision --------------------------------------------------- */
+#define GBMC_FP64 0 /* binary64 tables, interpolation and sums */
+#define GBMC_FP32 1 /* binary32 tables, interpolation and sums; binary64
+                       positions, directions, distances and tallies */
+
+/* ---- geometry kinds, boundary conditions, sources ---------------------- */
+#define GBMC_GEOM_INFINITE 0 /* one homogeneous material, no surfaces */
+#define GBMC_GEOM_LATTICE 1  /* n x n pin cells of pitch p: a cylinder of radius
+                                r on each cell axis, height H along z */
+#define GBMC_GEOM_SLAB 2     /* n_layers layers of thickness dx along x */
+#define GBMC_BC_VACUUM 0
+#define GBMC_BC_REFLECT 1
+#define GBMC_SRC_ORIGIN 0    /* point at the origin, isotropic */
+#define GBMC_SRC_BOX 1       /* uniform in the lattice box, isotropic */
+#define GBMC_SRC_SLAB_FACE 2 /* point on x = 0, isotropic over the inward hemisphere */
+
+/* ---- per-particle outcome status -------------------------------------- */
+#define GBMC_STATUS_ABSORBED 1
+#define GBMC_STATUS_LEAKED 2
+#define GBMC_STATUS_CUTOFF 3     /* energy fell below E_cut */
+#define GBMC_STATUS_LIMIT 4      /* GBMC_MAX_FLIGHTS flights reached */
+#define GBMC_STATUS_LEAKED_FAR 5 /* slab: left through x = n_layers dx */
+#define GBMC_MAX_FLIGHTS 100000
+
+/* ---- scalar tally slots (counts are int64, weights binary64) ----------- */
+#define GBMC_S_COLLISION 0
+#define GBMC_S_ABSORPTION 1
+#define GBMC_S_LEAK 2
+#define GBMC_S_CUTOFF 3
+#define GBMC_S_LIMIT 4
+#define GBMC_S_LEAK_FAR 5
+#define GBMC_S_FLIGHT 6
+#define GBMC_S_HISTORY 7
+#define GBMC_NSCAL 8
+
+typedef struct gbmc_ctx gbmc_ctx;
+
+/* Launch and scheduling options.  Any field left 0 takes its default. */
+typedef struct {
+    int32_t precision;       /* GBMC_FP64 or GBMC_FP32 (tables must be loaded in it) */
+    int64_t max_in_flight;   /* cap on particles in flight (Sec. 2, "In-Flight
+                                Particles"); 0: min(particles of the run, 8M) */
+    int32_t sort;            /* 1 (default): sort the lookup queue by material
+                                and energy (Sec. 2, "Sorting"); -1: do not sort */
+    int32_t block_lookup;    /* threads per block of the lookup kernel (default 256) */
+    int32_t block_event;     /* threads per block of the other event kernels (256) */
+    int32_t blocks_per_sm;   /* event-kernel grid = SMs x blocks_per_sm (default 8) */
+    int32_t max_iterations;  /* bound on event-loop iterations of one run
+                                (default 4 * GBMC_MAX_FLIGHTS); reaching it
+                                returns GBMC_ERR_TIMEOUT from the next read */
+    int32_t reserved[8];
+} gbmc_options;
+
+/* One geometry (and its source).  Fields of other kinds are ignored. */
+typedef struct {
+    int32_t kind;     /* GBMC_GEOM_* */
+    int32_t source;   /* GBMC_SRC_* */
+    double E0;        /* source energy (eV) */
+    double E_cut;     /* energy cutoff (eV): a scatter below it ends the history */
+    int32_t mat;      /* INFINITE: material index */
+    int32_t n;        /* LATTICE: cells per side */
+    double pitch;     /* LATTICE: cell pitch p */
+    double radius;    /* LATTICE: pin radius r, 0 < r < p/2 */
+    double height;    /* LATTICE: height H (z in [0, H]) */
+    int32_t mat_pin;  /* LATTICE: material inside the pins */
+    int32_t mat_mod;  /* LATTICE: material outside the pins */
+    int32_t bc_side;  /* LATTICE: x/y outer faces, GBMC_BC_* */
+    int32_t bc_z;     /* LATTICE: z = 0 and z = H faces, GBMC_BC_* */
+    int32_t n_layers; /* SLAB: number of layers (x in [0, n_layers dx]); both faces vacuum */
+    double layer_dx;  /* SLAB: layer thickness */
+    int32_t n_first;  /* SLAB: layers [0, n_first) hold mat_a, the rest mat_b */
+    int32_t mat_a, mat_b;
+} gbmc_geometry;
+
+/* One independent fixed-source problem of a run. */
+typedef struct {
+    gbmc_geometry geom;
+    uint64_t seed;           /* Philox key word 0 */
+    uint32_t problem_index;  /* Philox key word 1 = problem_index << 32 | batch */
+    uint32_t batch;
+    int64_t first_id;        /* histories first_id .. first_id + n_particles - 1 */
+    int64_t n_particles;
+} gbmc_problem;
+
+/* Counters of the last run (for throughput figures). */
+typedef struct {
+    int64_t iterations;       /* event-loop iterations */
+    int64_t lookups;          /* macroscopic lookups (lookup-event particles) */
+    int64_t micro_lookups;    /* nuclide lookups in the lookup event */
+    int64_t flights;          /* advance events */
+    int64_t crossings;        /* surface events */
+    int64_t collisions;       /* collision events */
+    int64_t histories;        /* particles born */
+    int32_t device_error;     /* 0, or the first GBMC_ERR_* a kernel flagged */
+    int32_t reserved;
+} gbmc_stats;
+
+/* Per-kernel device time of one profiled run (gbmc_profile_problems). */
+#define GBMC_NKERNELS 9
+typedef struct {
+    /* kernels: 0 plan, 1 source, 2 sort keys, 3 sort scan, 4 sort scatter,
+       5 lookup, 6 advance, 7 surface, 8 collision */
+    double ms[GBMC_NKERNELS];        /* summed device time (CUDA events) */
+    int64_t launches[GBMC_NKERNELS]; /* launches of each kernel */
+} gbmc_kernel_times;
+
+/* Fill *opt with the defaults. */
+int gbmc_default_options(gbmc_options *opt);
+
+/* Create a context on CUDA device `device` (opt may be NULL: defaults).
+ * On success *out owns its device memory until gbmc_destroy. */
+int gbmc_create(gbmc_ctx **out, int device, const gbmc_options *opt);
+
+/* Release every device allocation of the context.  NULL is accepted. */
+int gbmc_destroy(gbmc_ctx *ctx);
+
+/* Message of the last failure on ctx ("" if none).  Owned by the context;
+ * valid until the next call on it.  With ctx == NULL: the last gbmc_create
+ * failure of this thread. */
+const char *gbmc_last_error(const gbmc_ctx *ctx);
+
+/* Replace the options.  Takes effect at the next run. */
+int gbmc_set_options(gbmc_ctx *ctx, const gbmc_options *opt);
+
+/* Load the pointwise nuclide tables (Sec. 2, "Sorting": the lookup reads
+ * each nuclide's energy grid and cross sections).
+ *   n_nuc     number of nuclides (>= 1)
+ *   grid_off  [n_nuc+1] int64, grid_off[0] = 0, at least 2 points per nuclide
+ *   energy    [grid_off[n_nuc]] eV, strictly increasing within each nuclide, > 0
+ *   sigma_t   [grid_off[n_nuc]] barns, > 0, finite
+ *   f_abs     [n_nuc] absorption fraction sigma_a / sigma_t in [0, 1]
+ *   awr       [n_nuc] atomic-weight ratio A >= 1 (elastic kinematics)
+ *   precision GBMC_FP64 or GBMC_FP32: which device copy to build; the
+ *             binary32 copy is the round-to-nearest cast of each value and is
+ *             rejected (GBMC_ERR_INVALID_ARG) if a grid stops being strictly
+ *             increasing after the cast.  Loading one precision keeps the
+ *             other's copy if it was loaded from the same tables before.
+ * Host arrays are copied.  Replaces earlier tables of that precision. */
+int gbmc_load_xs_tables(gbmc_ctx *ctx, int32_t n_nuc, const int64_t *grid_off,
+                        const double *energy, const double *sigma_t,
+                        const double *f_abs, const double *awr, int32_t precision);
+
+/* Define the materials: material m holds nuclides nuc_id[mat_off[m] ..
+ * mat_off[m+1]-1] with densities density[...] (atoms/(b cm), > 0).  The
+ * listed order is the summation order of the macroscopic cross section.
+ *   mat_off [n_mat+1] int32, nuc_id and density [mat_off[n_mat]].
+ * Requires the tables (nuclide ids are range-checked).  Host arrays copied. */
+int gbmc_init_materials(gbmc_ctx *ctx, int32_t n_mat, const int32_t *mat_off,
+                        const int32_t *nuc_id, const double *density);
+
+/* Energy bins of the track-length flux tally: edges [n_bins+1], strictly
+ * increasing.  The bin of energy E is the largest b <= n_bins-1 with
+ * edges[b] <= E (b = 0 below edges[0]).  Zeroes all tallies. */
+int gbmc_set_tally(gbmc_ctx *ctx, int32_t n_bins, const double *edges);
+
+/* Zero the tallies of every problem slot (stream-ordered on `stream`). */
+int gbmc_reset_tallies(gbmc_ctx *ctx, void *stream);
+
+/* Run one batch of one problem: histories prob->first_id .. + n_particles-1
+ * of batch prob->batch, event by event on the GPU (Sec. 2).  Asynchronous on
+ * `stream` (a cudaStream_t; NULL = legacy default stream).  Tallies
+ * accumulate into problem slot 0 (reset when the slot layout changes);
+ * per-particle outcomes of this run replace the previous ones.
+ * Equivalent to gbmc_run_problems(ctx, 1, prob, stream). */
+int gbmc_run_batch(gbmc_ctx *ctx, const gbmc_problem *prob, void *stream);
+
+/* Run n_prob independent problems (each with its own geometry, source,
+ * Philox key and particle count) in one device-driven event loop: their
+ * particles share the in-flight bank, queues and kernels; tallies go to
+ * problem slots 0 .. n_prob-1.  Asynchronous on `stream`. */
+int gbmc_run_problems(gbmc_ctx *ctx, int32_t n_prob, const gbmc_problem *probs,
+                      void *stream);
+
+/* Synchronize the last run's stream and copy the tallies of problem slot
+ * `slot`: flux [n_cells * n_bins] (cell-major; n_flux must equal it; NULL
+ * skips), counts [GBMC_NSCAL] and weights [GBMC_NSCAL] (NULL skips).
+ * Returns GBMC_ERR_TIMEOUT / GBMC_ERR_DEVICE_FLAG if the run reported one. */
+int gbmc_read_tallies(gbmc_ctx *ctx, int32_t slot, double *flux, int64_t n_flux,
+                      int64_t *counts, double *weights);
+
+/* Synchronize and copy per-particle outcomes of the last run for particles
+ * first .. first+n-1 of problem slot `slot` (index within that problem's
+ * batch).  Any output pointer may be NULL.  Final E and position are the
+ * state at death. */
+int gbmc_read_outcomes(gbmc_ctx *ctx, int32_t slot, int64_t first, int64_t n,
+                       int32_t *n_coll, int8_t *status, int32_t *n_flights,
+                       uint32_t *n_draws, double *E, double *x, double *y, double *z);
+
+/* Synchronize and return the counters of the last run. */
+int gbmc_read_stats(gbmc_ctx *ctx, gbmc_stats *out);
+
+/* Macroscopic lookup only (the lookup event of Sec. 2 "Sorting", outside
+ * the transport loop), on DEVICE pointers owned by the caller:
+ *   d_E [n] binary64 energies within the tables' grids, d_mat [n] int32
+ *   material ids, outputs d_sigma_t and d_sigma_a [n] binary64.
+ * precision selects the loaded table copy.  sort = 1 sorts the queries by
+ * (material, energy) into context-owned scratch first (results are written
+ * back in query order).  Asynchronous on `stream`. */
+int gbmc_lookup_macro(gbmc_ctx *ctx, int32_t precision, const double *d_E,
+                      const int32_t *d_mat, int64_t n, double *d_sigma_t,
+                      double *d_sigma_a, int32_t sort, void *stream);
+
+/* Run like gbmc_run_problems, but launch each iteration's kernels eagerly
+ * (no graph) with a CUDA event around every kernel on `stream`, and add the
+ * per-kernel device times to *out (zero it first).  Synchronizes once per
+ * iteration, so the run is slower end to end; outcomes and tallies are the
+ * same as gbmc_run_problems'. */
+int gbmc_profile_problems(gbmc_ctx *ctx, int32_t n_prob, const gbmc_problem *probs,
+                          void *stream, gbmc_kernel_times *out);
+
+/* Device timing of the last run's event loop (ms, CUDA events on the run's
+ * stream around the graph launch); synchronizes. */
+int gbmc_last_run_ms(gbmc_ctx *ctx, double *ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBMC_H */

@@ -258,7 +258,8 @@ int or_macro(const or_problem *P, int32_t m, const double *E, int64_t n,
 
 /* Collision nuclide: first i (listed order) whose running sum of N_i sigma_i
  * exceeds target = xi * Sigma_t; the running sums are formed exactly as in
- * macro_xs.  If rounding leaves none, the last nuclide with a positive term. */
+ * macro_xs.  If rounding leaves none, the last nuclide with a positive term
+ * (the first listed nuclide if no term is positive). */
 static int32_t pick_nuclide(const tables_t *T, int32_t m, double E, double target)
 {
     const or_problem *P = T->P;
@@ -282,7 +283,7 @@ static int32_t pick_nuclide(const tables_t *T, int32_t m, double E, double targe
             if (target < (double)cum) return i;
         }
     }
-    return last;
+    return last >= 0 ? last : P->nuc_id[P->mat_off[m]];
 }
 
 /* ------------------------------------------------------------------------ */

@@ -1,0 +1,999 @@
+// C ABI of the transport hot path (include/gbmc.h): context, validation of
+// every input before any launch, device uploads, the graph that runs the
+// device-driven event loop, and the read-back calls.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include "device.cuh"
+#include "launch.h"
+
+using namespace gbmc;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// Free a device buffer; work still queued on any stream may use it, so the
+// device is drained first (reallocation is rare: buffers only grow).
+template <class T>
+void dfree(T*& p) {
+    if (p) {
+        cudaDeviceSynchronize();
+        cudaFree((void*)p);
+    }
+    p = nullptr;
+}
+
+}  // namespace
+
+struct gbmc_ctx {
+    int device = 0;
+    int sms = 0;
+    gbmc_options opt{};
+    std::string err;
+
+    // tables
+    int32_t n_nuc = 0;
+    bool has64 = false, has32 = false;
+    std::vector<int64_t> h_grid_off;
+    std::vector<double> h_gmin, h_gmax;   // per nuclide grid range
+    double emin_all = 0, emax_all = 0;
+    int64_t* d_grid_off = nullptr;
+    double *d_e64 = nullptr, *d_s64 = nullptr, *d_fabs = nullptr, *d_awr = nullptr;
+    float *d_e32 = nullptr, *d_s32 = nullptr, *d_fabs32 = nullptr;
+    uint64_t table_hash = 0;   // identifies the tables both copies were built from
+
+    // materials
+    int32_t n_mat = 0;
+    std::vector<int32_t> h_mat_off, h_nuc_id;
+    int32_t *d_mat_off = nullptr, *d_nuc_id = nullptr;
+    double* d_density = nullptr;
+    float* d_density32 = nullptr;
+
+    // tally definition
+    int32_t n_bins = 0;
+    double* d_edges = nullptr;
+
+    // particle bank and queues
+    int32_t capacity = 0;
+    Bank B{};
+    Queues Q{};
+
+    // outcomes
+    int64_t out_cap = 0;
+    Outcomes O{};
+
+    // tallies: slot layout
+    std::vector<int32_t> slot_cells;
+    std::vector<int64_t> slot_flux_off;
+    int64_t flux_cap = 0;
+    int32_t slots_cap = 0;
+    Tallies Y{};
+
+    // run descriptors
+    DevProblem* d_probs = nullptr;
+    int32_t probs_cap = 0;
+    DevProblem* h_probs = nullptr;   // pinned staging
+    int32_t h_probs_cap = 0;
+    Ctl* d_ctl = nullptr;
+    Ctl* h_ctl = nullptr;            // pinned staging / read-back
+    cudaEvent_t staged = nullptr;
+
+    // graph of the event loop
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    Params graph_params{};
+    LaunchCfg graph_launch{};
+    bool graph_valid = false;
+
+    // last run
+    bool ran = false;
+    cudaStream_t last_stream = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::vector<int64_t> run_start, run_n;
+
+    // standalone-lookup scratch
+    int64_t q_cap = 0;
+    int32_t* q_perm = nullptr;
+    uint32_t* q_keys = nullptr;
+    uint32_t *q_hist = nullptr, *q_cursor = nullptr;
+};
+
+namespace {
+
+int fail(gbmc_ctx* c, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+    return code;
+}
+
+#define CK(call)                                                                      \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess) {                                                      \
+            if (e_ == cudaErrorMemoryAllocation)                                      \
+                return fail(c, GBMC_ERR_OOM, "%s: %s", #call, cudaGetErrorString(e_)); \
+            return fail(c, GBMC_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));   \
+        }                                                                             \
+    } while (0)
+
+template <class T>
+int dalloc(gbmc_ctx* c, T** p, size_t n) {
+    dfree(*p);
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(c, GBMC_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", n * sizeof(T),
+                    cudaGetErrorString(e));
+    }
+    return GBMC_OK;
+}
+
+template <class T>
+int upload(gbmc_ctx* c, T** dst, const T* src, size_t n) {
+    int rc = dalloc(c, dst, n);
+    if (rc) return rc;
+    CK(cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice));
+    return GBMC_OK;
+}
+
+void fill_defaults(gbmc_options* o) {
+    if (o->precision != GBMC_FP32) o->precision = GBMC_FP64;
+    if (o->sort == 0) o->sort = 1;
+    if (o->block_lookup <= 0) o->block_lookup = 256;
+    if (o->block_event <= 0) o->block_event = 256;
+    if (o->blocks_per_sm <= 0) o->blocks_per_sm = 8;
+    if (o->max_iterations <= 0) o->max_iterations = 4 * GBMC_MAX_FLIGHTS;
+}
+
+int check_options(gbmc_ctx* c, const gbmc_options* o) {
+    if (o->precision != GBMC_FP64 && o->precision != GBMC_FP32)
+        return fail(c, GBMC_ERR_INVALID_ARG, "precision must be GBMC_FP64 or GBMC_FP32");
+    if (o->block_lookup != 256 || o->block_event != 256)
+        return fail(c, GBMC_ERR_UNSUPPORTED, "block sizes other than 256 are not built");
+    if (o->blocks_per_sm > 32)
+        return fail(c, GBMC_ERR_INVALID_ARG, "blocks_per_sm must be in [1, 32]");
+    if (o->max_in_flight < 0 || o->max_in_flight > (int64_t)(1 << 30))
+        return fail(c, GBMC_ERR_INVALID_ARG, "max_in_flight must be in [0, 2^30]");
+    return GBMC_OK;
+}
+
+int set_device(gbmc_ctx* c) {
+    CK(cudaSetDevice(c->device));
+    return GBMC_OK;
+}
+
+uint64_t fnv1a(const void* p, size_t n, uint64_t h) {
+    const unsigned char* b = (const unsigned char*)p;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= b[i];
+        h *= 0x100000001b3ull;
+    }
+    return h;
+}
+
+void free_bank(gbmc_ctx* c) {
+    Bank& B = c->B;
+    dfree(B.x); dfree(B.y); dfree(B.z); dfree(B.u); dfree(B.v); dfree(B.w);
+    dfree(B.E); dfree(B.wgt); dfree(B.st); dfree(B.sa);
+    dfree(B.ci); dfree(B.cj); dfree(B.mat); dfree(B.ncoll); dfree(B.nflt); dfree(B.prob);
+    dfree(B.rj); dfree(B.gidx); dfree(B.inside); dfree(B.surf);
+    Queues& Q = c->Q;
+    dfree(Q.lq[0]); dfree(Q.lq[1]); dfree(Q.aq[0]); dfree(Q.aq[1]);
+    dfree(Q.sq); dfree(Q.cq); dfree(Q.fq); dfree(Q.lqs); dfree(Q.keys);
+    dfree(Q.hist); dfree(Q.cursor);
+    c->capacity = 0;
+}
+
+int ensure_bank(gbmc_ctx* c, int32_t M) {
+    if (M <= c->capacity) return GBMC_OK;
+    free_bank(c);
+    c->graph_valid = false;
+    size_t n = (size_t)M;
+    Bank& B = c->B;
+    int rc = 0;
+    rc |= dalloc(c, &B.x, n); rc |= dalloc(c, &B.y, n); rc |= dalloc(c, &B.z, n);
+    rc |= dalloc(c, &B.u, n); rc |= dalloc(c, &B.v, n); rc |= dalloc(c, &B.w, n);
+    rc |= dalloc(c, &B.E, n); rc |= dalloc(c, &B.wgt, n); rc |= dalloc(c, &B.st, n);
+    rc |= dalloc(c, &B.sa, n); rc |= dalloc(c, &B.ci, n); rc |= dalloc(c, &B.cj, n);
+    rc |= dalloc(c, &B.mat, n); rc |= dalloc(c, &B.ncoll, n); rc |= dalloc(c, &B.nflt, n);
+    rc |= dalloc(c, &B.prob, n); rc |= dalloc(c, &B.rj, n); rc |= dalloc(c, &B.gidx, n);
+    rc |= dalloc(c, &B.inside, n); rc |= dalloc(c, &B.surf, n);
+    Queues& Q = c->Q;
+    rc |= dalloc(c, &Q.lq[0], n); rc |= dalloc(c, &Q.lq[1], n);
+    rc |= dalloc(c, &Q.aq[0], n); rc |= dalloc(c, &Q.aq[1], n);
+    rc |= dalloc(c, &Q.sq, n); rc |= dalloc(c, &Q.cq, n); rc |= dalloc(c, &Q.fq, n);
+    rc |= dalloc(c, &Q.lqs, n); rc |= dalloc(c, &Q.keys, n);
+    rc |= dalloc(c, &Q.hist, kSortBuckets); rc |= dalloc(c, &Q.cursor, kSortBuckets);
+    if (rc) {
+        free_bank(c);
+        return GBMC_ERR_OOM;
+    }
+    CK(cudaMemset(Q.hist, 0, sizeof(uint32_t) * kSortBuckets));
+    c->capacity = M;
+    return GBMC_OK;
+}
+
+int ensure_outcomes(gbmc_ctx* c, int64_t n) {
+    if (n <= c->out_cap) return GBMC_OK;
+    Outcomes& O = c->O;
+    int rc = 0;
+    rc |= dalloc(c, &O.ncoll, n); rc |= dalloc(c, &O.status, n); rc |= dalloc(c, &O.nflt, n);
+    rc |= dalloc(c, &O.ndraw, n); rc |= dalloc(c, &O.E, n); rc |= dalloc(c, &O.x, n);
+    rc |= dalloc(c, &O.y, n); rc |= dalloc(c, &O.z, n);
+    if (rc) {
+        c->out_cap = 0;
+        return GBMC_ERR_OOM;
+    }
+    c->out_cap = n;
+    c->graph_valid = false;
+    return GBMC_OK;
+}
+
+// Tally slots follow the problem list of the run; a different layout (slot
+// count or cells per slot) re-zeroes every tally.
+int ensure_tallies(gbmc_ctx* c, const std::vector<int32_t>& cells, cudaStream_t s) {
+    if (cells == c->slot_cells && c->Y.flux) return GBMC_OK;
+    std::vector<int64_t> off(cells.size());
+    int64_t tot = 0;
+    for (size_t p = 0; p < cells.size(); ++p) {
+        off[p] = tot;
+        tot += (int64_t)cells[p] * c->n_bins;
+    }
+    if (tot > c->flux_cap || !c->Y.flux) {
+        int rc = dalloc(c, &c->Y.flux, (size_t)tot);
+        if (rc) return rc;
+        c->flux_cap = tot;
+        c->graph_valid = false;
+    }
+    int32_t ns = (int32_t)cells.size();
+    if (ns > c->slots_cap || !c->Y.counts) {
+        int rc = dalloc(c, &c->Y.counts, (size_t)ns * GBMC_NSCAL);
+        rc |= dalloc(c, &c->Y.weights, (size_t)ns * GBMC_NSCAL);
+        if (rc) return GBMC_ERR_OOM;
+        c->slots_cap = ns;
+        c->graph_valid = false;
+    }
+    CK(cudaMemsetAsync(c->Y.flux, 0, sizeof(double) * (size_t)(tot ? tot : 1), s));
+    CK(cudaMemsetAsync(c->Y.counts, 0, sizeof(unsigned long long) * c->slots_cap * GBMC_NSCAL, s));
+    CK(cudaMemsetAsync(c->Y.weights, 0, sizeof(double) * c->slots_cap * GBMC_NSCAL, s));
+    c->slot_cells = cells;
+    c->slot_flux_off = off;
+    return GBMC_OK;
+}
+
+Tables make_tables(const gbmc_ctx* c) {
+    Tables T{};
+    T.grid_off = c->d_grid_off;
+    T.e64 = c->d_e64; T.s64 = c->d_s64; T.e32 = c->d_e32; T.s32 = c->d_s32;
+    T.f_abs = c->d_fabs; T.f_abs32 = c->d_fabs32; T.awr = c->d_awr;
+    T.mat_off = c->d_mat_off; T.nuc_id = c->d_nuc_id;
+    T.density = c->d_density; T.density32 = c->d_density32;
+    T.edges = c->d_edges;
+    T.n_nuc = c->n_nuc; T.n_mat = c->n_mat; T.n_bins = c->n_bins;
+    return T;
+}
+
+int ceil_log2(uint64_t v) {
+    int k = 0;
+    while ((1ull << k) < v) ++k;
+    return k;
+}
+
+void sort_params(const gbmc_ctx* c, Params& P) {
+    int mb = ceil_log2((uint64_t)(c->n_mat > 1 ? c->n_mat : 1));
+    int bpm = 16 - mb;
+    if (bpm < 0) bpm = 0;
+    uint64_t lo, hi;
+    memcpy(&lo, &c->emin_all, 8);
+    memcpy(&hi, &c->emax_all, 8);
+    uint64_t range = hi - lo + 1;
+    uint32_t shift = 0;
+    while ((range >> shift) > (1ull << bpm)) ++shift;
+    P.sort_ebase = lo;
+    P.sort_shift = shift;
+    P.bpm_log2 = (uint32_t)bpm;
+}
+
+Params make_params(gbmc_ctx* c) {
+    Params P{};
+    P.T = make_tables(c);
+    P.B = c->B;
+    P.Q = c->Q;
+    P.O = c->O;
+    P.Y = c->Y;
+    P.ctl = c->d_ctl;
+    P.probs = c->d_probs;
+    P.capacity = c->capacity;
+    P.precision = c->opt.precision;
+    P.sort = c->opt.sort > 0 ? 1 : 0;
+    P.sort_min = 4096;
+    P.max_iter = c->opt.max_iterations;
+    sort_params(c, P);
+    return P;
+}
+
+LaunchCfg make_launch(const gbmc_ctx* c) {
+    LaunchCfg L;
+    L.grid = c->sms * c->opt.blocks_per_sm;
+    L.grid_lookup = c->sms * c->opt.blocks_per_sm;
+    return L;
+}
+
+void destroy_graph(gbmc_ctx* c) {
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->exec = nullptr;
+    c->graph = nullptr;
+    c->graph_valid = false;
+}
+
+// Graph: [free-list init] -> while (cond) { one event-loop iteration }.  The
+// plan kernel at the head of the body clears the condition once the bank is
+// empty and the batch exhausted (or the iteration bound is hit).
+int build_graph(gbmc_ctx* c, Params P, const LaunchCfg& L) {
+    destroy_graph(c);
+    if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    cudaGraph_t g;
+    CK(cudaGraphCreate(&g, 0));
+    c->graph = g;
+    CK(cudaStreamBeginCaptureToGraph(c->cap_stream, g, nullptr, nullptr, 0,
+                                     cudaStreamCaptureModeThreadLocal));
+    cudaError_t le = launch_init_run(P, L, c->cap_stream);
+    cudaGraph_t g2 = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &g2);
+    if (le != cudaSuccess) return fail(c, GBMC_ERR_CUDA, "init capture: %s", cudaGetErrorString(le));
+    if (ee != cudaSuccess) return fail(c, GBMC_ERR_CUDA, "init capture end: %s", cudaGetErrorString(ee));
+    size_t nn = 0;
+    CK(cudaGraphGetNodes(g, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    CK(cudaGraphGetNodes(g, nodes.data(), &nn));
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cn;
+    CK(cudaGraphAddNode(&cn, g, nodes.data(), nullptr, nn, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    P.cond = h;
+    P.use_cond = 1;
+    CK(cudaStreamBeginCaptureToGraph(c->cap_stream, body, nullptr, nullptr, 0,
+                                     cudaStreamCaptureModeThreadLocal));
+    le = launch_iteration(P, L, c->cap_stream);
+    cudaGraph_t b2 = nullptr;
+    ee = cudaStreamEndCapture(c->cap_stream, &b2);
+    if (le != cudaSuccess) return fail(c, GBMC_ERR_CUDA, "body capture: %s", cudaGetErrorString(le));
+    if (ee != cudaSuccess) return fail(c, GBMC_ERR_CUDA, "body capture end: %s", cudaGetErrorString(ee));
+    cudaError_t ie = cudaGraphInstantiate(&c->exec, g, 0);
+    if (ie != cudaSuccess) {
+        c->exec = nullptr;
+        return fail(c, GBMC_ERR_UNSUPPORTED, "graph with a device while-node: %s",
+                    cudaGetErrorString(ie));
+    }
+    c->graph_params = P;
+    c->graph_launch = L;
+    c->graph_valid = true;
+    return GBMC_OK;
+}
+
+bool same_params(const Params& a, const Params& b) {
+    Params x = a, y = b;
+    x.cond = y.cond = cudaGraphConditionalHandle{};
+    x.use_cond = y.use_cond = 0;
+    return memcmp(&x, &y, sizeof(Params)) == 0;
+}
+
+int check_geometry(gbmc_ctx* c, const gbmc_geometry& g, int idx) {
+    auto bad_mat = [&](int32_t m) { return m < 0 || m >= c->n_mat; };
+    if (!(g.E0 > 0 && std::isfinite(g.E0)) || !(g.E_cut > 0 && std::isfinite(g.E_cut)) ||
+        g.E_cut > g.E0)
+        return fail(c, GBMC_ERR_INVALID_ARG, "problem %d: need 0 < E_cut <= E0", idx);
+    std::vector<int32_t> mats;
+    if (g.kind == GBMC_GEOM_INFINITE) {
+        if (g.source != GBMC_SRC_ORIGIN)
+            return fail(c, GBMC_ERR_INVALID_ARG, "problem %d: infinite medium takes the origin source", idx);
+        if (bad_mat(g.mat)) return fail(c, GBMC_ERR_INVALID_ARG, "problem %d: material out of range", idx);
+        mats = {g.mat};
+    } else if (g.kind == GBMC_GEOM_LATTICE) {
+        if (g.source != GBMC_SRC_BOX)
+            return fail(c, GBMC_ERR_INVALID_ARG, "problem %d: lattice takes the box source", idx);
+        if (g.n < 1 || g.n > 1 << 14 || !(g.pitch > 0) || !std::isfinite(g.pitch) ||
+            !(g.radius > 0) || !(g.radius < 0.5 * g.pitch) || !(g.height > 0) ||
+            !std::isfinite(g.height))
+            return fail(c, GBMC_ERR_INVALID_ARG,
+                        "problem %d: lattice needs n >= 1, p > 0, 0 < r < p/2, H > 0", idx);
+        if ((g.bc_side != 0 && g.bc_side != 1) || (g.bc_z != 0 && g.bc_z != 1))
+            return fail(c, GBMC_ERR_INVALID_ARG, "problem %d: boundary condition must be 0 or 1", idx);
+        if (bad_mat(g.mat_pin) || bad_mat(g.mat_mod))
+            return fail(c, GBMC_ERR_INVALID_ARG, "problem %d: material out of range", idx);
+        mats = {g.mat_pin, g.mat_mod};
+    } else if (g.kind == GBMC_GEOM_SLAB) {
+        if (g.source != GBMC_SRC_SLAB_FACE)
+            return fail(c, GBMC_ERR_INVALID_ARG, "problem %d: slab takes the face source", idx);
+        if (g.n_layers < 1 || !(g.layer_dx > 0) || !std::isfinite(g.layer_dx) || g.n_first < 0 ||
+            g.n_first > g.n_layers)
+            return fail(c, GBMC_ERR_INVALID_ARG,
+                        "problem %d: slab needs n_layers >= 1, dx > 0, 0 <= n_first <= n_layers", idx);
+        if (bad_mat(g.mat_a) || bad_mat(g.mat_b))
+            return fail(c, GBMC_ERR_INVALID_ARG, "problem %d: material out of range", idx);
+        mats = {g.mat_a, g.mat_b};
+    } else {
+        return fail(c, GBMC_ERR_INVALID_ARG, "problem %d: unknown geometry kind %d", idx, g.kind);
+    }
+    // every energy the walk can reach, [E_cut, E0], must lie inside every
+    // grid the lookup may search (scattering never raises the energy)
+    for (int32_t m : mats)
+        for (int32_t q = c->h_mat_off[m]; q < c->h_mat_off[m + 1]; ++q) {
+            int32_t i = c->h_nuc_id[q];
+            if (c->h_gmin[i] > g.E_cut || c->h_gmax[i] < g.E0)
+                return fail(c, GBMC_ERR_INVALID_ARG,
+                            "problem %d: nuclide %d grid [%g, %g] does not cover [E_cut, E0]",
+                            idx, i, c->h_gmin[i], c->h_gmax[i]);
+        }
+    return GBMC_OK;
+}
+
+int n_cells_of(const gbmc_geometry& g) {
+    if (g.kind == GBMC_GEOM_LATTICE) return g.n * g.n;
+    if (g.kind == GBMC_GEOM_SLAB) return g.n_layers;
+    return 1;
+}
+
+int read_ctl(gbmc_ctx* c) {
+    if (!c->ran) return fail(c, GBMC_ERR_NOT_INITIALIZED, "no run has been launched");
+    CK(cudaStreamSynchronize(c->last_stream));
+    CK(cudaMemcpy(c->h_ctl, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+    if (c->h_ctl->err == GBMC_ERR_TIMEOUT)
+        return fail(c, GBMC_ERR_TIMEOUT, "event loop stopped at its iteration bound (%d)",
+                    c->opt.max_iterations);
+    if (c->h_ctl->err)
+        return fail(c, GBMC_ERR_DEVICE_FLAG, "device flagged error %d", c->h_ctl->err);
+    return GBMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gbmc_default_options(gbmc_options* opt) {
+    if (!opt) return GBMC_ERR_INVALID_ARG;
+    memset(opt, 0, sizeof(*opt));
+    fill_defaults(opt);
+    return GBMC_OK;
+}
+
+int gbmc_create(gbmc_ctx** out, int device, const gbmc_options* opt) {
+    if (!out) {
+        g_create_error = "out is NULL";
+        return GBMC_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+        g_create_error = std::string("no CUDA device: ") + cudaGetErrorString(e);
+        return GBMC_ERR_CUDA;
+    }
+    if (device < 0 || device >= ndev) {
+        g_create_error = "device index out of range";
+        return GBMC_ERR_INVALID_ARG;
+    }
+    gbmc_ctx* c = new gbmc_ctx();
+    c->device = device;
+    gbmc_options o{};
+    if (opt) o = *opt;
+    fill_defaults(&o);
+    int rc = check_options(c, &o);
+    if (rc) {
+        g_create_error = c->err;
+        delete c;
+        return rc;
+    }
+    c->opt = o;
+    auto bail = [&](const char* what, cudaError_t err) {
+        g_create_error = std::string(what) + ": " + cudaGetErrorString(err);
+        delete c;
+        return err == cudaErrorMemoryAllocation ? GBMC_ERR_OOM : GBMC_ERR_CUDA;
+    };
+    if ((e = cudaSetDevice(device)) != cudaSuccess) return bail("cudaSetDevice", e);
+    cudaDeviceProp prop;
+    if ((e = cudaGetDeviceProperties(&prop, device)) != cudaSuccess) return bail("properties", e);
+    if (prop.major < 10) {
+        g_create_error = "needs a Blackwell-class GPU (sm_100 or newer)";
+        delete c;
+        return GBMC_ERR_UNSUPPORTED;
+    }
+    c->sms = prop.multiProcessorCount;
+    if ((e = cudaMalloc((void**)&c->d_ctl, sizeof(Ctl))) != cudaSuccess) return bail("ctl", e);
+    if ((e = cudaMallocHost((void**)&c->h_ctl, sizeof(Ctl))) != cudaSuccess) return bail("ctl host", e);
+    if ((e = cudaEventCreate(&c->staged)) != cudaSuccess) return bail("event", e);
+    if ((e = cudaEventCreate(&c->ev0)) != cudaSuccess) return bail("event", e);
+    if ((e = cudaEventCreate(&c->ev1)) != cudaSuccess) return bail("event", e);
+    *out = c;
+    return GBMC_OK;
+}
+
+int gbmc_destroy(gbmc_ctx* c) {
+    if (!c) return GBMC_OK;
+    cudaSetDevice(c->device);
+    if (c->ran && c->last_stream) cudaStreamSynchronize(c->last_stream);
+    destroy_graph(c);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    free_bank(c);
+    Outcomes& O = c->O;
+    dfree(O.ncoll); dfree(O.status); dfree(O.nflt); dfree(O.ndraw);
+    dfree(O.E); dfree(O.x); dfree(O.y); dfree(O.z);
+    dfree(c->Y.flux); dfree(c->Y.counts); dfree(c->Y.weights);
+    dfree(c->d_grid_off); dfree(c->d_e64); dfree(c->d_s64); dfree(c->d_e32); dfree(c->d_s32);
+    dfree(c->d_fabs); dfree(c->d_fabs32); dfree(c->d_awr);
+    dfree(c->d_mat_off); dfree(c->d_nuc_id); dfree(c->d_density); dfree(c->d_density32);
+    dfree(c->d_edges); dfree(c->d_probs); dfree(c->d_ctl);
+    dfree(c->q_perm); dfree(c->q_keys); dfree(c->q_hist); dfree(c->q_cursor);
+    if (c->h_probs) cudaFreeHost(c->h_probs);
+    if (c->h_ctl) cudaFreeHost(c->h_ctl);
+    if (c->staged) cudaEventDestroy(c->staged);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    delete c;
+    return GBMC_OK;
+}
+
+const char* gbmc_last_error(const gbmc_ctx* c) {
+    if (!c) return g_create_error.c_str();
+    return c->err.c_str();
+}
+
+int gbmc_set_options(gbmc_ctx* c, const gbmc_options* opt) {
+    if (!c || !opt) return GBMC_ERR_INVALID_ARG;
+    gbmc_options o = *opt;
+    fill_defaults(&o);
+    int rc = check_options(c, &o);
+    if (rc) return rc;
+    if (memcmp(&o, &c->opt, sizeof o) != 0) c->graph_valid = false;
+    c->opt = o;
+    return GBMC_OK;
+}
+
+int gbmc_load_xs_tables(gbmc_ctx* c, int32_t n_nuc, const int64_t* grid_off, const double* energy,
+                        const double* sigma_t, const double* f_abs, const double* awr,
+                        int32_t precision) {
+    if (!c) return GBMC_ERR_INVALID_ARG;
+    if (n_nuc < 1 || !grid_off || !energy || !sigma_t || !f_abs || !awr)
+        return fail(c, GBMC_ERR_INVALID_ARG, "n_nuc >= 1 and non-NULL arrays required");
+    if (precision != GBMC_FP64 && precision != GBMC_FP32)
+        return fail(c, GBMC_ERR_INVALID_ARG, "precision must be GBMC_FP64 or GBMC_FP32");
+    if (grid_off[0] != 0) return fail(c, GBMC_ERR_INVALID_ARG, "grid_off[0] must be 0");
+    std::vector<double> gmin(n_nuc), gmax(n_nuc);
+    for (int32_t i = 0; i < n_nuc; ++i) {
+        int64_t a = grid_off[i], b = grid_off[i + 1];
+        if (b - a < 2) return fail(c, GBMC_ERR_INVALID_ARG, "nuclide %d has fewer than 2 grid points", i);
+        for (int64_t k = a; k < b; ++k) {
+            if (!(energy[k] > 0) || !std::isfinite(energy[k]))
+                return fail(c, GBMC_ERR_INVALID_ARG, "nuclide %d: energy %lld not positive finite", i, (long long)(k - a));
+            if (k > a && !(energy[k] > energy[k - 1]))
+                return fail(c, GBMC_ERR_INVALID_ARG, "nuclide %d: grid not strictly increasing at %lld", i, (long long)(k - a));
+            if (!(sigma_t[k] > 0) || !std::isfinite(sigma_t[k]))
+                return fail(c, GBMC_ERR_INVALID_ARG, "nuclide %d: sigma_t %lld not positive finite", i, (long long)(k - a));
+            if (precision == GBMC_FP32 && k > a && !((float)energy[k] > (float)energy[k - 1]))
+                return fail(c, GBMC_ERR_INVALID_ARG,
+                            "nuclide %d: grid points %lld and %lld coincide in binary32", i,
+                            (long long)(k - a - 1), (long long)(k - a));
+        }
+        if (!(f_abs[i] >= 0 && f_abs[i] <= 1))
+            return fail(c, GBMC_ERR_INVALID_ARG, "nuclide %d: f_abs outside [0, 1]", i);
+        if (!(awr[i] > 0) || !std::isfinite(awr[i]))
+            return fail(c, GBMC_ERR_INVALID_ARG, "nuclide %d: awr must be positive", i);
+        gmin[i] = precision == GBMC_FP32 ? (double)(float)energy[a] : energy[a];
+        gmax[i] = precision == GBMC_FP32 ? (double)(float)energy[b - 1] : energy[b - 1];
+    }
+    int rc = set_device(c);
+    if (rc) return rc;
+    int64_t tot = grid_off[n_nuc];
+    uint64_t h = fnv1a(grid_off, sizeof(int64_t) * (n_nuc + 1), 1469598103934665603ull);
+    h = fnv1a(energy, sizeof(double) * tot, h);
+    h = fnv1a(sigma_t, sizeof(double) * tot, h);
+    h = fnv1a(f_abs, sizeof(double) * n_nuc, h);
+    h = fnv1a(awr, sizeof(double) * n_nuc, h);
+    bool same = (h == c->table_hash && n_nuc == c->n_nuc);
+    if (!same) {
+        // new tables: drop the copy of the other precision
+        dfree(c->d_e64); dfree(c->d_s64); dfree(c->d_e32); dfree(c->d_s32);
+        c->has64 = c->has32 = false;
+        // materials refer to nuclide ids of the old tables
+        if (c->n_mat) {
+            dfree(c->d_mat_off); dfree(c->d_nuc_id); dfree(c->d_density); dfree(c->d_density32);
+            c->n_mat = 0;
+            c->h_mat_off.clear();
+            c->h_nuc_id.clear();
+        }
+    }
+    if ((rc = upload(c, &c->d_grid_off, grid_off, (size_t)n_nuc + 1))) return rc;
+    if ((rc = upload(c, &c->d_fabs, f_abs, (size_t)n_nuc))) return rc;
+    if ((rc = upload(c, &c->d_awr, awr, (size_t)n_nuc))) return rc;
+    std::vector<float> f32(n_nuc);
+    for (int32_t i = 0; i < n_nuc; ++i) f32[i] = (float)f_abs[i];
+    if ((rc = upload(c, &c->d_fabs32, f32.data(), (size_t)n_nuc))) return rc;
+    if (precision == GBMC_FP64) {
+        if ((rc = upload(c, &c->d_e64, energy, (size_t)tot))) return rc;
+        if ((rc = upload(c, &c->d_s64, sigma_t, (size_t)tot))) return rc;
+        c->has64 = true;
+    } else {
+        std::vector<float> e(tot), s(tot);
+        for (int64_t k = 0; k < tot; ++k) {
+            e[k] = (float)energy[k];
+            s[k] = (float)sigma_t[k];
+        }
+        if ((rc = upload(c, &c->d_e32, e.data(), (size_t)tot))) return rc;
+        if ((rc = upload(c, &c->d_s32, s.data(), (size_t)tot))) return rc;
+        c->has32 = true;
+    }
+    c->n_nuc = n_nuc;
+    c->table_hash = h;
+    c->h_grid_off.assign(grid_off, grid_off + n_nuc + 1);
+    // the grid range check uses the tighter of the two copies
+    if (!same) {
+        c->h_gmin = gmin;
+        c->h_gmax = gmax;
+    } else {
+        for (int32_t i = 0; i < n_nuc; ++i) {
+            c->h_gmin[i] = std::max(c->h_gmin[i], gmin[i]);
+            c->h_gmax[i] = std::min(c->h_gmax[i], gmax[i]);
+        }
+    }
+    c->emin_all = *std::min_element(c->h_gmin.begin(), c->h_gmin.end());
+    c->emax_all = *std::max_element(c->h_gmax.begin(), c->h_gmax.end());
+    c->graph_valid = false;
+    return GBMC_OK;
+}
+
+int gbmc_init_materials(gbmc_ctx* c, int32_t n_mat, const int32_t* mat_off, const int32_t* nuc_id,
+                        const double* density) {
+    if (!c) return GBMC_ERR_INVALID_ARG;
+    if (!c->n_nuc) return fail(c, GBMC_ERR_NOT_INITIALIZED, "load the tables first");
+    if (n_mat < 1 || !mat_off || !nuc_id || !density)
+        return fail(c, GBMC_ERR_INVALID_ARG, "n_mat >= 1 and non-NULL arrays required");
+    if (mat_off[0] != 0) return fail(c, GBMC_ERR_INVALID_ARG, "mat_off[0] must be 0");
+    for (int32_t m = 0; m < n_mat; ++m) {
+        if (mat_off[m + 1] <= mat_off[m])
+            return fail(c, GBMC_ERR_INVALID_ARG, "material %d has no nuclide", m);
+        for (int32_t q = mat_off[m]; q < mat_off[m + 1]; ++q) {
+            if (nuc_id[q] < 0 || nuc_id[q] >= c->n_nuc)
+                return fail(c, GBMC_ERR_INVALID_ARG, "material %d: nuclide id %d out of range", m, nuc_id[q]);
+            if (!(density[q] > 0) || !std::isfinite(density[q]))
+                return fail(c, GBMC_ERR_INVALID_ARG, "material %d: density must be positive", m);
+        }
+    }
+    int rc = set_device(c);
+    if (rc) return rc;
+    int32_t tot = mat_off[n_mat];
+    if ((rc = upload(c, &c->d_mat_off, mat_off, (size_t)n_mat + 1))) return rc;
+    if ((rc = upload(c, &c->d_nuc_id, nuc_id, (size_t)tot))) return rc;
+    if ((rc = upload(c, &c->d_density, density, (size_t)tot))) return rc;
+    std::vector<float> d32(tot);
+    for (int32_t q = 0; q < tot; ++q) d32[q] = (float)density[q];
+    if ((rc = upload(c, &c->d_density32, d32.data(), (size_t)tot))) return rc;
+    c->n_mat = n_mat;
+    c->h_mat_off.assign(mat_off, mat_off + n_mat + 1);
+    c->h_nuc_id.assign(nuc_id, nuc_id + tot);
+    c->graph_valid = false;
+    return GBMC_OK;
+}
+
+int gbmc_set_tally(gbmc_ctx* c, int32_t n_bins, const double* edges) {
+    if (!c) return GBMC_ERR_INVALID_ARG;
+    if (n_bins < 1 || !edges) return fail(c, GBMC_ERR_INVALID_ARG, "n_bins >= 1 and edges required");
+    for (int32_t b = 0; b <= n_bins; ++b) {
+        if (!(edges[b] > 0) || !std::isfinite(edges[b]))
+            return fail(c, GBMC_ERR_INVALID_ARG, "tally edges must be positive and finite");
+        if (b && !(edges[b] > edges[b - 1]))
+            return fail(c, GBMC_ERR_INVALID_ARG, "tally edges must be strictly increasing");
+    }
+    int rc = set_device(c);
+    if (rc) return rc;
+    if ((rc = upload(c, &c->d_edges, edges, (size_t)n_bins + 1))) return rc;
+    c->n_bins = n_bins;
+    c->slot_cells.clear();   // forces re-zeroing at the next run
+    c->graph_valid = false;
+    return GBMC_OK;
+}
+
+int gbmc_reset_tallies(gbmc_ctx* c, void* stream) {
+    if (!c) return GBMC_ERR_INVALID_ARG;
+    int rc = set_device(c);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (c->Y.flux) CK(cudaMemsetAsync(c->Y.flux, 0, sizeof(double) * c->flux_cap, s));
+    if (c->Y.counts) {
+        CK(cudaMemsetAsync(c->Y.counts, 0, sizeof(unsigned long long) * c->slots_cap * GBMC_NSCAL, s));
+        CK(cudaMemsetAsync(c->Y.weights, 0, sizeof(double) * c->slots_cap * GBMC_NSCAL, s));
+    }
+    return GBMC_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Validate a run, size the buffers, stage descriptors and the control block
+// (stream-ordered copies on s).  Fills the launch parameters.
+int prepare_run(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, cudaStream_t s,
+                Params* Pout, LaunchCfg* Lout) {
+    if (n_prob < 1 || !probs) return fail(c, GBMC_ERR_INVALID_ARG, "n_prob >= 1 and probs required");
+    if (!c->n_nuc || !c->n_mat || !c->n_bins)
+        return fail(c, GBMC_ERR_NOT_INITIALIZED, "tables, materials and tally must be set first");
+    if ((c->opt.precision == GBMC_FP64 && !c->has64) || (c->opt.precision == GBMC_FP32 && !c->has32))
+        return fail(c, GBMC_ERR_NOT_INITIALIZED, "tables not loaded in the selected precision");
+    std::vector<int32_t> cells(n_prob);
+    std::vector<int64_t> start(n_prob), nn(n_prob);
+    int64_t total = 0;
+    for (int32_t p = 0; p < n_prob; ++p) {
+        int rc = check_geometry(c, probs[p].geom, p);
+        if (rc) return rc;
+        if (probs[p].n_particles < 0 || probs[p].first_id < 0 ||
+            probs[p].first_id > std::numeric_limits<int64_t>::max() - probs[p].n_particles)
+            return fail(c, GBMC_ERR_INVALID_ARG, "problem %d: bad particle range", p);
+        cells[p] = n_cells_of(probs[p].geom);
+        start[p] = total;
+        nn[p] = probs[p].n_particles;
+        total += probs[p].n_particles;
+        if (total > ((int64_t)1 << 40))
+            return fail(c, GBMC_ERR_INVALID_ARG, "more than 2^40 particles in one run");
+    }
+    int rc = set_device(c);
+    if (rc) return rc;
+    int64_t M64 = c->opt.max_in_flight > 0 ? c->opt.max_in_flight : ((int64_t)8 << 20);
+    if (M64 > total) M64 = total;
+    if (M64 < 1) M64 = 1;
+    int32_t M = (int32_t)M64;
+    if ((rc = ensure_bank(c, M))) return rc;
+    if ((rc = ensure_outcomes(c, total > 0 ? total : 1))) return rc;
+    if ((rc = ensure_tallies(c, cells, s))) return rc;
+    if (n_prob > c->probs_cap) {
+        if ((rc = dalloc(c, &c->d_probs, (size_t)n_prob))) return rc;
+        c->probs_cap = n_prob;
+        c->graph_valid = false;
+    }
+    if (n_prob > c->h_probs_cap) {
+        CK(cudaEventSynchronize(c->staged));
+        if (c->h_probs) cudaFreeHost(c->h_probs);
+        c->h_probs = nullptr;
+        CK(cudaMallocHost((void**)&c->h_probs, sizeof(DevProblem) * n_prob));
+        c->h_probs_cap = n_prob;
+    }
+    *Pout = make_params(c);
+    *Lout = make_launch(c);
+    // stage the descriptors (pinned) once the previous staging copy is done
+    CK(cudaEventSynchronize(c->staged));
+    for (int32_t p = 0; p < n_prob; ++p) {
+        DevProblem& d = c->h_probs[p];
+        memset(&d, 0, sizeof d);
+        d.g = probs[p].geom;
+        d.seed = probs[p].seed;
+        d.key_hi = ((uint64_t)probs[p].problem_index << 32) | (uint64_t)probs[p].batch;
+        d.first_id = probs[p].first_id;
+        d.n = probs[p].n_particles;
+        d.start = start[p];
+        d.flux_off = c->slot_flux_off[p];
+        d.n_cells = cells[p];
+    }
+    Ctl& k = *c->h_ctl;
+    memset(&k, 0, sizeof k);
+    k.n_free = M;
+    k.cur = 1;
+    k.total = total;
+    k.M = M;
+    k.n_prob = n_prob;
+    CK(cudaMemcpyAsync(c->d_probs, c->h_probs, sizeof(DevProblem) * n_prob, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->d_ctl, c->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    CK(cudaEventRecord(c->staged, s));
+    c->run_start = start;
+    c->run_n = nn;
+    return GBMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gbmc_run_problems(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, void* stream) {
+    if (!c) return GBMC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (c->ran) {
+        int rc0 = set_device(c);
+        if (rc0) return rc0;
+    }
+    Params P;
+    LaunchCfg L;
+    int rc = prepare_run(c, n_prob, probs, s, &P, &L);
+    if (rc) return rc;
+    if (!c->graph_valid || !same_params(P, c->graph_params) ||
+        memcmp(&L, &c->graph_launch, sizeof L) != 0) {
+        CK(cudaStreamSynchronize(s));
+        if (c->ran) CK(cudaStreamSynchronize(c->last_stream));
+        if ((rc = build_graph(c, P, L))) return rc;
+    }
+    CK(cudaEventRecord(c->ev0, s));
+    CK(cudaGraphLaunch(c->exec, s));
+    CK(cudaEventRecord(c->ev1, s));
+    c->ran = true;
+    c->last_stream = s;
+    return GBMC_OK;
+}
+
+int gbmc_profile_problems(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, void* stream,
+                          gbmc_kernel_times* out) {
+    if (!c || !out) return GBMC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Params P;
+    LaunchCfg L;
+    int rc = prepare_run(c, n_prob, probs, s, &P, &L);
+    if (rc) return rc;
+    P.use_cond = 0;
+    cudaEvent_t ev[kTimedKernels + 1];
+    for (int k = 0; k <= kTimedKernels; ++k) CK(cudaEventCreate(&ev[k]));
+    cudaError_t e = launch_init_run(P, L, s);
+    int it = 0;
+    while (e == cudaSuccess) {
+        e = launch_iteration_timed(P, L, s, ev);
+        if (e != cudaSuccess) break;
+        e = cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) break;
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) break;
+        for (int k = 0; k < kTimedKernels; ++k) {
+            float ms = 0;
+            e = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+            if (e != cudaSuccess) break;
+            bool launched = (k < 2 || k > 4 || P.sort);
+            out->ms[k] += ms;
+            out->launches[k] += launched ? 1 : 0;
+        }
+        if (c->h_ctl->done || ++it > c->opt.max_iterations + 1) break;
+    }
+    for (int k = 0; k <= kTimedKernels; ++k) cudaEventDestroy(ev[k]);
+    if (e != cudaSuccess) return fail(c, GBMC_ERR_CUDA, "profiled run: %s", cudaGetErrorString(e));
+    c->ran = true;
+    c->last_stream = s;
+    CK(cudaEventRecord(c->ev0, s));
+    CK(cudaEventRecord(c->ev1, s));
+    return GBMC_OK;
+}
+
+int gbmc_run_batch(gbmc_ctx* c, const gbmc_problem* prob, void* stream) {
+    return gbmc_run_problems(c, 1, prob, stream);
+}
+
+int gbmc_read_tallies(gbmc_ctx* c, int32_t slot, double* flux, int64_t n_flux, int64_t* counts,
+                      double* weights) {
+    if (!c) return GBMC_ERR_INVALID_ARG;
+    int rc = set_device(c);
+    if (rc) return rc;
+    if ((rc = read_ctl(c))) return rc;
+    if (slot < 0 || slot >= (int32_t)c->slot_cells.size())
+        return fail(c, GBMC_ERR_INVALID_ARG, "tally slot %d out of range", slot);
+    int64_t nf = (int64_t)c->slot_cells[slot] * c->n_bins;
+    if (flux) {
+        if (n_flux != nf)
+            return fail(c, GBMC_ERR_INVALID_ARG, "n_flux must be %lld", (long long)nf);
+        CK(cudaMemcpy(flux, c->Y.flux + c->slot_flux_off[slot], sizeof(double) * nf,
+                      cudaMemcpyDeviceToHost));
+    }
+    if (counts) {
+        static_assert(sizeof(unsigned long long) == sizeof(int64_t), "count width");
+        CK(cudaMemcpy(counts, c->Y.counts + (size_t)slot * GBMC_NSCAL,
+                      sizeof(int64_t) * GBMC_NSCAL, cudaMemcpyDeviceToHost));
+    }
+    if (weights)
+        CK(cudaMemcpy(weights, c->Y.weights + (size_t)slot * GBMC_NSCAL,
+                      sizeof(double) * GBMC_NSCAL, cudaMemcpyDeviceToHost));
+    return GBMC_OK;
+}
+
+int gbmc_read_outcomes(gbmc_ctx* c, int32_t slot, int64_t first, int64_t n, int32_t* n_coll,
+                       int8_t* status, int32_t* n_flights, uint32_t* n_draws, double* E, double* x,
+                       double* y, double* z) {
+    if (!c) return GBMC_ERR_INVALID_ARG;
+    int rc = set_device(c);
+    if (rc) return rc;
+    if ((rc = read_ctl(c))) return rc;
+    if (slot < 0 || slot >= (int32_t)c->run_start.size())
+        return fail(c, GBMC_ERR_INVALID_ARG, "problem slot %d out of range", slot);
+    if (first < 0 || n < 0 || first + n > c->run_n[slot])
+        return fail(c, GBMC_ERR_INVALID_ARG, "particle range outside the problem's batch");
+    int64_t o = c->run_start[slot] + first;
+    if (n == 0) return GBMC_OK;
+    if (n_coll) CK(cudaMemcpy(n_coll, c->O.ncoll + o, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+    if (status) CK(cudaMemcpy(status, c->O.status + o, sizeof(int8_t) * n, cudaMemcpyDeviceToHost));
+    if (n_flights) CK(cudaMemcpy(n_flights, c->O.nflt + o, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+    if (n_draws) CK(cudaMemcpy(n_draws, c->O.ndraw + o, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
+    if (E) CK(cudaMemcpy(E, c->O.E + o, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    if (x) CK(cudaMemcpy(x, c->O.x + o, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    if (y) CK(cudaMemcpy(y, c->O.y + o, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    if (z) CK(cudaMemcpy(z, c->O.z + o, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    return GBMC_OK;
+}
+
+int gbmc_read_stats(gbmc_ctx* c, gbmc_stats* out) {
+    if (!c || !out) return GBMC_ERR_INVALID_ARG;
+    int rc = set_device(c);
+    if (rc) return rc;
+    memset(out, 0, sizeof *out);
+    rc = read_ctl(c);
+    if (rc && rc != GBMC_ERR_TIMEOUT && rc != GBMC_ERR_DEVICE_FLAG) return rc;
+    const Ctl& k = *c->h_ctl;
+    out->iterations = k.iter;
+    out->lookups = (int64_t)k.st_lookups;
+    out->micro_lookups = (int64_t)k.st_micro;
+    out->flights = (int64_t)k.st_flights;
+    out->crossings = (int64_t)k.st_cross;
+    out->collisions = (int64_t)k.st_coll;
+    out->histories = (int64_t)k.st_hist;
+    out->device_error = k.err;
+    return rc;
+}
+
+int gbmc_last_run_ms(gbmc_ctx* c, double* ms) {
+    if (!c || !ms) return GBMC_ERR_INVALID_ARG;
+    if (!c->ran) return fail(c, GBMC_ERR_NOT_INITIALIZED, "no run has been launched");
+    int rc = set_device(c);
+    if (rc) return rc;
+    CK(cudaEventSynchronize(c->ev1));
+    float f = 0;
+    CK(cudaEventElapsedTime(&f, c->ev0, c->ev1));
+    *ms = f;
+    return GBMC_OK;
+}
+
+int gbmc_lookup_macro(gbmc_ctx* c, int32_t precision, const double* d_E, const int32_t* d_mat,
+                      int64_t n, double* d_sigma_t, double* d_sigma_a, int32_t sort, void* stream) {
+    if (!c) return GBMC_ERR_INVALID_ARG;
+    if (n < 0 || (n > 0 && (!d_E || !d_mat || !d_sigma_t || !d_sigma_a)))
+        return fail(c, GBMC_ERR_INVALID_ARG, "n >= 0 and device arrays required");
+    if (n > ((int64_t)1 << 31) - 1) return fail(c, GBMC_ERR_INVALID_ARG, "n must be < 2^31");
+    if (precision != GBMC_FP64 && precision != GBMC_FP32)
+        return fail(c, GBMC_ERR_INVALID_ARG, "precision must be GBMC_FP64 or GBMC_FP32");
+    if (!c->n_nuc || !c->n_mat) return fail(c, GBMC_ERR_NOT_INITIALIZED, "tables and materials required");
+    if ((precision == GBMC_FP64 && !c->has64) || (precision == GBMC_FP32 && !c->has32))
+        return fail(c, GBMC_ERR_NOT_INITIALIZED, "tables not loaded in that precision");
+    if (n == 0) return GBMC_OK;
+    int rc = set_device(c);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (sort > 0 && n > c->q_cap) {
+        if (c->ran) CK(cudaStreamSynchronize(c->last_stream));
+        CK(cudaDeviceSynchronize());
+        if ((rc = dalloc(c, &c->q_perm, (size_t)n))) return rc;
+        if ((rc = dalloc(c, &c->q_keys, (size_t)n))) return rc;
+        c->q_cap = n;
+    }
+    if (sort > 0 && !c->q_hist) {
+        if ((rc = dalloc(c, &c->q_hist, kSortBuckets))) return rc;
+        if ((rc = dalloc(c, &c->q_cursor, kSortBuckets))) return rc;
+        CK(cudaMemset(c->q_hist, 0, sizeof(uint32_t) * kSortBuckets));
+    }
+    Params P = make_params(c);
+    P.precision = precision;
+    LaunchCfg L = make_launch(c);
+    cudaError_t e = launch_query_lookup(P, L, d_E, d_mat, n, d_sigma_t, d_sigma_a,
+                                        sort > 0 ? c->q_perm : nullptr, c->q_keys, c->q_hist,
+                                        c->q_cursor, s);
+    if (e != cudaSuccess) return fail(c, GBMC_ERR_CUDA, "lookup launch: %s", cudaGetErrorString(e));
+    return GBMC_OK;
+}
+
+}  // extern "C"

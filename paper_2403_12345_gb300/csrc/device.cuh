@@ -1,0 +1,414 @@
+// Device-side building blocks of the transport hot path: the per-particle
+// counter-based random stream, a reproducible logarithm, the cross-section
+// lookup, surface distances and elastic-scatter kinematics.
+//
+// Every binary64/binary32 expression here is compiled without FMA
+// contraction (-fmad=false) and evaluated exactly in the written order, so a
+// particle's random walk is a pure function of its inputs and matches a
+// serial history-based evaluation of the same definitions bit for bit
+// (reproducibility between CPU and GPU up to summation order: Sec. 4.3).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "../../include/gbmc.h"
+
+namespace gbmc {
+
+// ---------------------------------------------------------------- layouts
+
+struct Tables {
+    const int64_t* grid_off;   // [n_nuc+1]
+    const double* e64;         // binary64 grid (eV)
+    const double* s64;         // binary64 sigma_t (b)
+    const float* e32;          // binary32 grid
+    const float* s32;          // binary32 sigma_t
+    const double* f_abs;       // [n_nuc]
+    const float* f_abs32;      // [n_nuc]
+    const double* awr;         // [n_nuc]
+    const int32_t* mat_off;    // [n_mat+1]
+    const int32_t* nuc_id;     // [mat_off[n_mat]]
+    const double* density;     // [mat_off[n_mat]]
+    const float* density32;    // [mat_off[n_mat]]
+    const double* edges;       // [n_bins+1] tally energy edges
+    int32_t n_nuc, n_mat, n_bins, pad;
+};
+
+// One problem of a run, as the kernels see it.
+struct DevProblem {
+    gbmc_geometry g;
+    uint64_t seed, key_hi;
+    int64_t first_id, n, start;   // start: index of its first particle in the run
+    int64_t flux_off;             // offset of its flux tally
+    int32_t n_cells, pad;
+};
+
+// Particle bank, structure of arrays, capacity M slots.
+struct Bank {
+    double *x, *y, *z, *u, *v, *w, *E, *wgt, *st, *sa;
+    int32_t *ci, *cj, *mat, *ncoll, *nflt, *prob;
+    uint32_t* rj;       // draws consumed from the particle's stream
+    int64_t* gidx;      // index of the particle in the run
+    uint8_t* inside;    // inside the pin cylinder (lattice)
+    uint8_t* surf;      // surface reached by the last flight
+};
+
+// Event queues (slot indices) and sort scratch.
+struct Queues {
+    int32_t* lq[2];     // lookup queue (double buffered)
+    int32_t* aq[2];     // advance queue (double buffered)
+    int32_t* sq;        // surface queue
+    int32_t* cq;        // collision queue
+    int32_t* fq;        // free slots
+    int32_t* lqs;       // lookup queue in (material, energy) order
+    uint32_t* keys;     // sort keys of lq
+    uint32_t* hist;     // [kSortBuckets] bucket counts
+    uint32_t* cursor;   // [kSortBuckets] bucket write positions
+};
+
+struct Outcomes {
+    int32_t* ncoll;
+    int8_t* status;
+    int32_t* nflt;
+    uint32_t* ndraw;
+    double *E, *x, *y, *z;
+};
+
+struct Tallies {
+    double* flux;
+    unsigned long long* counts;   // [slot * GBMC_NSCAL + s]
+    double* weights;
+};
+
+// Device-resident event-loop state.
+struct Ctl {
+    int32_t n_lq[2], n_aq[2], n_sq, n_cq, n_free;
+    int32_t cur;                 // queues[cur] are consumed this iteration
+    int32_t lookup_n, aq_base;   // lookups of this iteration, where they append in aq[cur]
+    int32_t n_birth, free_base, lq_base, sorted;
+    int64_t next_base;           // run index of the first particle born this iteration
+    int64_t next, total;         // next unborn run index, particles in the run
+    int32_t M;                   // in-flight cap of this run (<= capacity)
+    int32_t n_prob;
+    int32_t done, err, iter, pad;
+    unsigned long long st_lookups, st_micro, st_flights, st_cross, st_coll, st_hist;
+};
+
+constexpr int kSortBuckets = 1 << 16;
+constexpr int kMaxSharedProblems = 64;
+
+struct Params {
+    Tables T;
+    Bank B;
+    Queues Q;
+    Outcomes O;
+    Tallies Y;
+    Ctl* ctl;
+    const DevProblem* probs;
+    int32_t capacity;        // bank slots allocated
+    int32_t precision;       // GBMC_FP64 / GBMC_FP32
+    int32_t sort;            // sort the lookup queue
+    int32_t sort_min;        // sort only when at least this many lookups
+    int32_t max_iter;
+    uint32_t sort_shift;     // energy-bits >> shift = bucket within a material
+    uint32_t bpm_log2;       // log2 buckets per material
+    int32_t use_cond;        // 1 inside the graph while-body, 0 for eager launches
+    uint64_t sort_ebase;     // bits of the smallest grid energy
+    cudaGraphConditionalHandle cond;
+};
+
+// ---------------------------------------------------------------- Philox4x64-10
+// Salmon et al., SC'11: ten rounds; each multiplies counter words 0 and 2 by
+// the round constants (full 128-bit products), swaps and xors the high halves
+// with words 1 and 3 and the key, which is bumped between rounds by the
+// golden-ratio and sqrt(3)-1 Weyl increments.
+
+struct Philox {
+    uint64_t c0, c1, c2, c3;
+};
+
+__device__ __forceinline__ Philox philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2,
+                                                 uint64_t c3, uint64_t k0, uint64_t k1) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += W0;
+            k1 += W1;
+        }
+        uint64_t lo0 = M0 * c0, hi0 = __umul64hi(M0, c0);
+        uint64_t lo1 = M1 * c2, hi1 = __umul64hi(M1, c2);
+        uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    return {c0, c1, c2, c3};
+}
+
+// The particle's stream: key (seed, problem << 32 | batch), counter
+// (history id, block, 0, 0); draw j is word j % 4 of block j / 4, mapped to
+// (0, 1] as ((x >> 11) + 1) 2^-53.
+struct Stream {
+    uint64_t k0, k1, id;
+    uint32_t j, blk;
+    bool have;
+    Philox b;
+
+    __device__ __forceinline__ void init(uint64_t seed, uint64_t key_hi, uint64_t hid, uint32_t j0) {
+        k0 = seed;
+        k1 = key_hi;
+        id = hid;
+        j = j0;
+        have = false;
+        blk = 0;
+    }
+    __device__ __forceinline__ double next() {
+        uint32_t bk = j >> 2;
+        if (!have || bk != blk) {
+            b = philox4x64_10(id, bk, 0, 0, k0, k1);
+            blk = bk;
+            have = true;
+        }
+        uint32_t w = j & 3u;
+        uint64_t x = w == 0 ? b.c0 : (w == 1 ? b.c1 : (w == 2 ? b.c2 : b.c3));
+        j += 1;
+        return (double)((x >> 11) + 1ull) * 0x1.0p-53;
+    }
+};
+
+// ---------------------------------------------------------------- logarithm
+// ln x for positive normal x: x = 2^e m with m in (sqrt(2)/2, sqrt(2)];
+// ln m = 2 atanh(s), s = (m - 1)/(m + 1), as the series
+// 2s (1 + s^2/3 + ... + s^20/21) (Abramowitz & Stegun 4.1.28), evaluated by
+// Horner's rule from the 1/21 term; e ln 2 with ln 2 split in a high part
+// carrying 21 trailing zero bits (so e * high is exact) and a low part.
+__device__ __forceinline__ double ln_series(double x) {
+    long long b = __double_as_longlong(x);
+    int e = (int)((b >> 52) & 0x7ff) - 1023;
+    double m = __longlong_as_double((b & 0x000FFFFFFFFFFFFFll) | 0x3FF0000000000000ll);
+    if (m > 0x1.6a09e667f3bcdp+0) {
+        m = m * 0.5;
+        e = e + 1;
+    }
+    double s = (m - 1.0) / (m + 1.0);
+    double z = s * s;
+    double q = 0x1.8618618618618p-5;
+    q = 0x1.af286bca1af28p-5 + z * q;
+    q = 0x1.e1e1e1e1e1e1ep-5 + z * q;
+    q = 0x1.1111111111111p-4 + z * q;
+    q = 0x1.3b13b13b13b14p-4 + z * q;
+    q = 0x1.745d1745d1746p-4 + z * q;
+    q = 0x1.c71c71c71c71cp-4 + z * q;
+    q = 0x1.2492492492492p-3 + z * q;
+    q = 0x1.999999999999ap-3 + z * q;
+    q = 0x1.5555555555555p-2 + z * q;
+    q = z * q;
+    double t = 2.0 * s;
+    double lm = t + t * q;
+    double de = (double)e;
+    return de * 0x1.62e42fee00000p-1 + (lm + de * 0x1.a39ef35793c76p-33);
+}
+
+// ---------------------------------------------------------------- lookup
+// Bracket search: largest j in [0, n-2] with grid[j] <= E.  Positive IEEE
+// values order like their bit patterns, so the comparisons run on the
+// integer pipe (binary64 compares would use the scarce FP64 units).
+__device__ __forceinline__ int64_t bracket64(const long long* __restrict__ g, int64_t n,
+                                             long long eb) {
+    int64_t lo = 0, hi = n - 1;
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) >> 1;
+        if (__ldg(g + mid) <= eb)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int64_t bracket32(const int* __restrict__ g, int64_t n, int eb) {
+    int64_t lo = 0, hi = n - 1;
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) >> 1;
+        if (__ldg(g + mid) <= eb)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Micro cross section of nuclide i at E: lin-lin interpolation between the
+// bracketing grid points, f = (E - E_j) / (E_j+1 - E_j), s_j + f (s_j+1 - s_j).
+__device__ __forceinline__ double micro64(const Tables& T, int32_t i, double E) {
+    int64_t lo = __ldg(T.grid_off + i);
+    int64_t n = __ldg(T.grid_off + i + 1) - lo;
+    const long long* g = reinterpret_cast<const long long*>(T.e64 + lo);
+    int64_t j = bracket64(g, n, __double_as_longlong(E));
+    double e0 = __ldg(T.e64 + lo + j), e1 = __ldg(T.e64 + lo + j + 1);
+    double s0 = __ldg(T.s64 + lo + j), s1 = __ldg(T.s64 + lo + j + 1);
+    double f = (E - e0) / (e1 - e0);
+    return s0 + f * (s1 - s0);
+}
+
+// binary32 tables: the bracket satisfies (double)E_j <= E, found by
+// comparing against E rounded toward -inf (exact for binary32 grid values);
+// the interpolation runs in binary32 on E rounded to nearest.
+__device__ __forceinline__ float micro32(const Tables& T, int32_t i, double E) {
+    int64_t lo = __ldg(T.grid_off + i);
+    int64_t n = __ldg(T.grid_off + i + 1) - lo;
+    const int* g = reinterpret_cast<const int*>(T.e32 + lo);
+    int64_t j = bracket32(g, n, __float_as_int(__double2float_rd(E)));
+    float e0 = __ldg(T.e32 + lo + j), e1 = __ldg(T.e32 + lo + j + 1);
+    float s0 = __ldg(T.s32 + lo + j), s1 = __ldg(T.s32 + lo + j + 1);
+    float Ef = __double2float_rn(E);
+    float f = (Ef - e0) / (e1 - e0);
+    return s0 + f * (s1 - s0);
+}
+
+// Macroscopic sigma_t, sigma_a of material m: sum over its nuclides in the
+// listed order of N_i sigma_i, and of (N_i sigma_i) f_abs,i.
+__device__ __forceinline__ void macro64(const Tables& T, int32_t m, double E, double& st,
+                                        double& sa) {
+    double at = 0.0, aa = 0.0;
+    int32_t q0 = __ldg(T.mat_off + m), q1 = __ldg(T.mat_off + m + 1);
+    for (int32_t q = q0; q < q1; ++q) {
+        int32_t i = __ldg(T.nuc_id + q);
+        double t = __ldg(T.density + q) * micro64(T, i, E);
+        at = at + t;
+        aa = aa + t * __ldg(T.f_abs + i);
+    }
+    st = at;
+    sa = aa;
+}
+
+__device__ __forceinline__ void macro32(const Tables& T, int32_t m, double E, double& st,
+                                        double& sa) {
+    float at = 0.0f, aa = 0.0f;
+    int32_t q0 = __ldg(T.mat_off + m), q1 = __ldg(T.mat_off + m + 1);
+    for (int32_t q = q0; q < q1; ++q) {
+        int32_t i = __ldg(T.nuc_id + q);
+        float t = __ldg(T.density32 + q) * micro32(T, i, E);
+        at = at + t;
+        aa = aa + t * __ldg(T.f_abs32 + i);
+    }
+    st = (double)at;
+    sa = (double)aa;
+}
+
+// Collision nuclide: first nuclide (listed order) whose running sum of
+// N_i sigma_i exceeds target = xi Sigma_t, with the running sums formed as
+// in the macroscopic lookup; if rounding leaves none, the last nuclide with
+// a positive term (the first listed one if no term is positive).
+__device__ __forceinline__ int32_t pick_nuclide(const Tables& T, int precision, int32_t m,
+                                                double E, double target) {
+    int32_t last = -1;
+    int32_t q0 = __ldg(T.mat_off + m), q1 = __ldg(T.mat_off + m + 1);
+    if (precision == GBMC_FP64) {
+        double cum = 0.0;
+        for (int32_t q = q0; q < q1; ++q) {
+            int32_t i = __ldg(T.nuc_id + q);
+            double t = __ldg(T.density + q) * micro64(T, i, E);
+            cum = cum + t;
+            if (t > 0.0) last = i;
+            if (target < cum) return i;
+        }
+    } else {
+        float cum = 0.0f;
+        for (int32_t q = q0; q < q1; ++q) {
+            int32_t i = __ldg(T.nuc_id + q);
+            float t = __ldg(T.density32 + q) * micro32(T, i, E);
+            cum = cum + t;
+            if (t > 0.0f) last = i;
+            if (target < (double)cum) return i;
+        }
+    }
+    return last >= 0 ? last : __ldg(T.nuc_id + q0);
+}
+
+// Tally energy bin: largest b in [0, n_bins-1] with edges[b] <= E.
+__device__ __forceinline__ int32_t energy_bin(const Tables& T, double E) {
+    return (int32_t)bracket64(reinterpret_cast<const long long*>(T.edges), (int64_t)T.n_bins + 1,
+                              __double_as_longlong(E));
+}
+
+// ---------------------------------------------------------------- geometry
+enum : uint8_t { kSurfNone = 0, kSurfCyl = 1, kSurfX = 2, kSurfY = 3, kSurfZ = 4 };
+
+// Distance along (u, v) from (dx, dy), relative to the pin axis, to the
+// cylinder of radius r: a d^2 + 2 k d + c = 0 with a = u^2 + v^2,
+// k = dx u + dy v, c = dx^2 + dy^2 - r^2, D = k^2 - a c, each root in its
+// cancellation-free form.  Inside: the far root; outside: the near root if
+// the path approaches and meets the cylinder, else no crossing.
+__device__ __forceinline__ double dist_cylinder(double dx, double dy, double u, double v,
+                                                double r, bool inside) {
+    double a = u * u + v * v;
+    double k = dx * u + dy * v;
+    double c = (dx * dx + dy * dy) - r * r;
+    double D = k * k - a * c;
+    if (inside) {
+        if (a == 0.0) return CUDART_INF;
+        if (D < 0.0) D = 0.0;
+        double sD = sqrt(D);
+        if (k <= 0.0) return (sD - k) / a;
+        return (0.0 - c) / (k + sD);
+    }
+    if (a == 0.0 || k >= 0.0 || D < 0.0) return CUDART_INF;
+    double sD = sqrt(D);
+    return c / (sD - k);
+}
+
+__device__ __forceinline__ double dist_planes(double x, double u, double lo, double hi) {
+    if (u > 0.0) return (hi - x) / u;
+    if (u < 0.0) return (lo - x) / u;
+    return CUDART_INF;
+}
+
+// Elastic scatter off a nucleus at rest, isotropic in the centre-of-mass
+// frame: E' = E (A^2 + 2 A mu + 1) / (A + 1)^2,
+// mu_lab = (1 + A mu) / sqrt(A^2 + 2 A mu + 1).
+__device__ __forceinline__ void elastic(double E, double A, double mu, double& E_out,
+                                        double& mu_lab) {
+    double t1 = (A * A + (2.0 * A) * mu) + 1.0;
+    double ap1 = A + 1.0;
+    E_out = (E * t1) / (ap1 * ap1);
+    mu_lab = (1.0 + A * mu) / sqrt(t1);
+}
+
+// Rotate (u, v, w) by polar cosine mu and azimuth (cos phi, sin phi).
+__device__ __forceinline__ void rotate(double& u, double& v, double& w, double mu, double cphi,
+                                       double sphi) {
+    double m2 = 1.0 - mu * mu;
+    if (m2 < 0.0) m2 = 0.0;
+    double st = sqrt(m2);
+    double u0 = u, v0 = v, w0 = w;
+    if (fabs(w0) < 0.9999999999) {
+        double q = sqrt(1.0 - w0 * w0);
+        u = mu * u0 + (st * ((u0 * w0) * cphi - v0 * sphi)) / q;
+        v = mu * v0 + (st * ((v0 * w0) * cphi + u0 * sphi)) / q;
+        w = mu * w0 - (st * q) * cphi;
+    } else {
+        u = st * cphi;
+        v = st * sphi;
+        w = w0 > 0.0 ? mu : -mu;
+    }
+}
+
+// Marsaglia (1972): (a, b) uniform in the unit disk by rejection; returns
+// s = a^2 + b^2 in (0, 1).
+__device__ __forceinline__ double disk_pair(Stream& r, double& a, double& b) {
+    for (;;) {
+        a = 2.0 * r.next() - 1.0;
+        b = 2.0 * r.next() - 1.0;
+        double s = a * a + b * b;
+        if (s > 0.0 && s < 1.0) return s;
+    }
+}
+
+}  // namespace gbmc
+

@@ -1,0 +1,34 @@
+// Host-side launchers of the device kernels (defined in transport.cu).
+#pragma once
+
+#include "device.cuh"
+
+namespace gbmc {
+
+struct LaunchCfg {
+    int grid;          // blocks of the event kernels (multiple of the SM count)
+    int grid_lookup;   // blocks of the lookup kernel
+};
+
+// Fill the free-slot list of a run (the run's control block is written by
+// the host before the launch).
+cudaError_t launch_init_run(const Params& P, const LaunchCfg& L, cudaStream_t s);
+
+// One event-loop iteration: plan, source, sort, lookup, advance, surface,
+// collision.  Captured once into the body of a graph while-node.
+cudaError_t launch_iteration(const Params& P, const LaunchCfg& L, cudaStream_t s);
+
+// The same iteration launched eagerly with an event before and after each
+// kernel (ev[0..9]), for per-kernel device timing.
+constexpr int kTimedKernels = 9;
+cudaError_t launch_iteration_timed(const Params& P, const LaunchCfg& L, cudaStream_t s,
+                                   cudaEvent_t* ev);
+
+// Standalone macroscopic lookup of caller-provided queries; with perm != NULL
+// the queries are first bucket-sorted by (material, energy) into perm.
+cudaError_t launch_query_lookup(const Params& P, const LaunchCfg& L, const double* E,
+                                const int32_t* mat, int64_t n, double* st, double* sa,
+                                int32_t* perm, uint32_t* keys, uint32_t* hist, uint32_t* cursor,
+                                cudaStream_t s);
+
+}  // namespace gbmc

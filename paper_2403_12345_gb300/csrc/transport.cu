@@ -1,0 +1,759 @@
+// Event kernels of the transport loop (Sec. 2, "Event-Based Parallelism"):
+// every kernel processes the whole queue of one event type and routes each
+// particle to the queue of its next event.  Grids are fixed (a multiple of
+// the SM count) and read their queue lengths from device memory, so one
+// iteration is a fixed sequence of launches that a CUDA graph replays under
+// a device-evaluated while-condition: no host round trip per event.
+//
+// Iteration: plan -> source (refill, Sec. 2 "In-Flight Particles") ->
+// sort (Sec. 2 "Sorting") -> lookup -> advance -> surface -> collision.
+#include "device.cuh"
+#include "launch.h"
+
+namespace gbmc {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Append `slot` to queue q (length *count) for every lane with pred set; one
+// atomic per warp.  Called by all 32 lanes of the warp.
+__device__ __forceinline__ void warp_append(int32_t* q, int32_t* count, int32_t slot, bool pred) {
+    unsigned m = __ballot_sync(kFull, pred);
+    if (m == 0) return;
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(count, __popc(m));
+    base = __shfl_sync(kFull, base, leader);
+    if (pred) q[base + __popc(m & lanemask_lt())] = slot;
+}
+
+// ---------------------------------------------------------------- scalar tallies
+// Per-block accumulation of the scalar tallies in shared memory (one entry
+// per problem slot and tally kind), flushed with one global atomic per entry
+// at the end of the kernel; problem slots beyond the shared table go straight
+// to global memory.
+struct BlockScalars {
+    double* w;
+    unsigned long long* c;
+    int nslot;
+
+    __device__ __forceinline__ void init(double* sw, unsigned long long* sc, int n_prob) {
+        w = sw;
+        c = sc;
+        nslot = min(n_prob, kMaxSharedProblems);
+        for (int e = threadIdx.x; e < nslot * GBMC_NSCAL; e += blockDim.x) {
+            w[e] = 0.0;
+            c[e] = 0ull;
+        }
+        __syncthreads();
+    }
+    // all 32 lanes call; lanes with pred score weight wt into (prob, kind)
+    __device__ __forceinline__ void add(const Tallies& Y, bool pred, int prob, int kind, double wt) {
+        unsigned vm = __ballot_sync(kFull, pred);
+        if (vm == 0) return;
+        unsigned peers = __match_any_sync(kFull, pred ? prob : -1);
+        int lane = threadIdx.x & 31;
+        if (vm == kFull && peers == kFull) {
+            double s = wt;
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+            if (lane == 0) put(Y, prob, kind, s, 32ull);
+        } else if (pred) {
+            put(Y, prob, kind, wt, 1ull);
+        }
+    }
+    __device__ __forceinline__ void put(const Tallies& Y, int prob, int kind, double s,
+                                        unsigned long long k) {
+        if (prob < nslot) {
+            atomicAdd(&w[prob * GBMC_NSCAL + kind], s);
+            atomicAdd(&c[prob * GBMC_NSCAL + kind], k);
+        } else {
+            atomicAdd(&Y.weights[prob * GBMC_NSCAL + kind], s);
+            atomicAdd(&Y.counts[prob * GBMC_NSCAL + kind], k);
+        }
+    }
+    __device__ __forceinline__ void flush(const Tallies& Y) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < nslot * GBMC_NSCAL; e += blockDim.x) {
+            if (c[e]) {
+                atomicAdd(&Y.weights[e], w[e]);
+                atomicAdd(&Y.counts[e], c[e]);
+            }
+        }
+    }
+};
+
+#define GBMC_BLOCK_SCALARS(name, n_prob)                                          \
+    __shared__ double name##_w[kMaxSharedProblems * GBMC_NSCAL];                  \
+    __shared__ unsigned long long name##_c[kMaxSharedProblems * GBMC_NSCAL];      \
+    BlockScalars name;                                                            \
+    name.init(name##_w, name##_c, n_prob)
+
+// Warp-uniform grid-stride loop: every lane of a warp runs the same number of
+// iterations (so warp collectives inside are safe); `valid` marks real items.
+#define GBMC_WARP_LOOP(idx, valid, n)                                                   \
+    for (int64_t idx##_0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);      \
+         idx##_0 < (int64_t)(n); idx##_0 += (int64_t)gridDim.x * blockDim.x)            \
+        for (int64_t idx = idx##_0 + (threadIdx.x & 31), idx##_once = 0; idx##_once < 1; \
+             ++idx##_once)                                                              \
+            for (bool valid = idx < (int64_t)(n), valid##_once = true; valid##_once;     \
+                 valid##_once = false)
+
+// ---------------------------------------------------------------- run set-up
+
+__global__ void k_init_run(Params P) {
+    const Ctl* c = P.ctl;
+    int32_t M = c->M;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M;
+         i += (int64_t)gridDim.x * blockDim.x)
+        P.Q.fq[i] = (int32_t)i;
+}
+
+// One thread: close the previous iteration, plan this one.
+__global__ void k_plan(Params P) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    Ctl* c = P.ctl;
+    // events of the previous iteration
+    c->st_cross += (unsigned long long)c->n_sq;
+    c->st_coll += (unsigned long long)c->n_cq;
+    int cur = 1 - c->cur;
+    c->cur = cur;
+    c->n_lq[1 - cur] = 0;
+    c->n_aq[1 - cur] = 0;
+    c->n_sq = 0;
+    c->n_cq = 0;
+    // refill free slots from the batch's unborn particles
+    int64_t remain = c->total - c->next;
+    int32_t k = (int32_t)(remain < (int64_t)c->n_free ? remain : (int64_t)c->n_free);
+    c->n_birth = k;
+    c->free_base = c->n_free - k;
+    c->n_free -= k;
+    c->next_base = c->next;
+    c->next += k;
+    c->lq_base = c->n_lq[cur];
+    c->n_lq[cur] += k;
+    c->st_hist += (unsigned long long)k;
+    int done = (c->n_free == c->M);   // nothing in flight, nothing left to birth
+    c->iter += 1;
+    if (!done && c->iter > P.max_iter) {
+        c->err = GBMC_ERR_TIMEOUT;
+        done = 1;
+    }
+    if (done) {
+        c->n_birth = 0;
+        c->n_lq[cur] = 0;
+        c->n_aq[cur] = 0;
+    }
+    c->lookup_n = c->n_lq[cur];
+    c->aq_base = c->n_aq[cur];
+    c->n_aq[cur] += c->lookup_n;
+    c->sorted = (P.sort && c->lookup_n >= P.sort_min) ? 1 : 0;
+    c->st_lookups += (unsigned long long)c->lookup_n;
+    c->st_flights += (unsigned long long)c->n_aq[cur];
+    c->done = done;
+    if (P.use_cond) cudaGraphSetConditional(P.cond, done ? 0u : 1u);
+}
+
+__device__ __forceinline__ int find_problem(const DevProblem* probs, int n_prob, int64_t gi) {
+    int lo = 0, hi = n_prob;   // largest p with start <= gi
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (probs[mid].start <= gi)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------- source / birth
+
+__global__ void __launch_bounds__(256) k_source(Params P) {
+    const Ctl* c = P.ctl;
+    int32_t n = c->n_birth;
+    if (n == 0) return;
+    GBMC_BLOCK_SCALARS(sc, c->n_prob);
+    int cur = c->cur;
+    int32_t fb = c->free_base, lb = c->lq_base;
+    int64_t nb = c->next_base;
+    GBMC_WARP_LOOP(idx, valid, n) {
+        int prob = 0;
+        if (valid) {
+            int32_t slot = P.Q.fq[fb + idx];
+            int64_t gi = nb + idx;
+            prob = find_problem(P.probs, c->n_prob, gi);
+            const DevProblem& pr = P.probs[prob];
+            Stream r;
+            r.init(pr.seed, pr.key_hi, (uint64_t)(pr.first_id + (gi - pr.start)), 0u);
+            const gbmc_geometry& g = pr.g;
+            double x = 0.0, y = 0.0, z = 0.0;
+            if (g.source == GBMC_SRC_BOX) {
+                double L = (double)g.n * g.pitch;
+                x = r.next() * L;
+                y = r.next() * L;
+                z = r.next() * g.height;
+            }
+            double a, b;
+            double s = disk_pair(r, a, b);
+            double t = 2.0 * sqrt(1.0 - s);
+            double w = 1.0 - 2.0 * s;
+            double u, v;
+            if (g.source == GBMC_SRC_SLAB_FACE) {
+                u = fabs(w);
+                v = a * t;
+                w = b * t;
+            } else {
+                u = a * t;
+                v = b * t;
+            }
+            int32_t ci = 0, cj = 0, mat;
+            uint8_t inside = 0;
+            if (g.kind == GBMC_GEOM_LATTICE) {
+                double p = g.pitch;
+                ci = (int32_t)floor(x / p);
+                cj = (int32_t)floor(y / p);
+                ci = ci < 0 ? 0 : (ci > g.n - 1 ? g.n - 1 : ci);
+                cj = cj < 0 ? 0 : (cj > g.n - 1 ? g.n - 1 : cj);
+                double dx = x - ((double)ci + 0.5) * p;
+                double dy = y - ((double)cj + 0.5) * p;
+                inside = (dx * dx + dy * dy) < (g.radius * g.radius);
+                mat = inside ? g.mat_pin : g.mat_mod;
+            } else if (g.kind == GBMC_GEOM_SLAB) {
+                mat = g.n_first > 0 ? g.mat_a : g.mat_b;
+            } else {
+                mat = g.mat;
+            }
+            Bank& B = const_cast<Bank&>(P.B);
+            B.x[slot] = x; B.y[slot] = y; B.z[slot] = z;
+            B.u[slot] = u; B.v[slot] = v; B.w[slot] = w;
+            B.E[slot] = g.E0; B.wgt[slot] = 1.0;
+            B.ci[slot] = ci; B.cj[slot] = cj; B.inside[slot] = inside; B.mat[slot] = mat;
+            B.ncoll[slot] = 0; B.nflt[slot] = 0; B.rj[slot] = r.j;
+            B.gidx[slot] = gi; B.prob[slot] = prob;
+            P.Q.lq[cur][lb + idx] = slot;
+        }
+        sc.add(P.Y, valid, prob, GBMC_S_HISTORY, 1.0);
+    }
+    sc.flush(P.Y);
+}
+
+// ---------------------------------------------------------------- sort
+// Counting sort of the lookup queue by a 16-bit key: material in the high
+// bits, a monotone function of energy (the binary64 bit pattern above the
+// smallest grid energy, shifted) in the low bits.  Order within a bucket is
+// arbitrary: sorting only buys locality (Sec. 2, "Sorting"); the lookup's
+// results do not depend on the order.
+__device__ __forceinline__ uint32_t sort_key(const Params& P, double E, int32_t m) {
+    unsigned long long eb = (unsigned long long)__double_as_longlong(E);
+    unsigned long long d = eb > P.sort_ebase ? eb - P.sort_ebase : 0ull;
+    unsigned long long b = d >> P.sort_shift;
+    unsigned long long bmax = (1ull << P.bpm_log2) - 1ull;
+    if (b > bmax) b = bmax;
+    return (((uint32_t)m << P.bpm_log2) | (uint32_t)b) & (uint32_t)(kSortBuckets - 1);
+}
+
+__device__ __forceinline__ void warp_count(uint32_t* hist, uint32_t key, bool valid) {
+    unsigned peers = __match_any_sync(kFull, valid ? key : 0xffffffffu);
+    int lane = threadIdx.x & 31;
+    if (valid && lane == __ffs(peers) - 1) atomicAdd(&hist[key], (uint32_t)__popc(peers));
+}
+
+__device__ __forceinline__ void warp_place(uint32_t* cursor, uint32_t key, bool valid,
+                                           int32_t* out, int32_t value) {
+    unsigned peers = __match_any_sync(kFull, valid ? key : 0xffffffffu);
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (valid && lane == leader) base = atomicAdd(&cursor[key], (uint32_t)__popc(peers));
+    base = __shfl_sync(kFull, base, leader);
+    if (valid) out[base + __popc(peers & lanemask_lt())] = value;
+}
+
+__global__ void __launch_bounds__(256) k_sort_keys(Params P) {
+    const Ctl* c = P.ctl;
+    if (!c->sorted) return;
+    int32_t n = c->lookup_n;
+    const int32_t* q = P.Q.lq[c->cur];
+    GBMC_WARP_LOOP(idx, valid, n) {
+        uint32_t key = 0;
+        if (valid) {
+            int32_t slot = q[idx];
+            key = sort_key(P, P.B.E[slot], P.B.mat[slot]);
+            P.Q.keys[idx] = key;
+        }
+        warp_count(P.Q.hist, key, valid);
+    }
+}
+
+// Exclusive scan of the bucket counts into write cursors (one block of 1024
+// threads, 64 buckets each); clears the counts for the next sort.
+__device__ void scan_buckets(uint32_t* hist, uint32_t* cursor) {
+    __shared__ uint32_t warp_sums[32];
+    constexpr int kPer = kSortBuckets / 1024;
+    int t = threadIdx.x;
+    uint32_t local[kPer];
+    uint32_t sum = 0;
+#pragma unroll 8
+    for (int k = 0; k < kPer; ++k) {
+        local[k] = hist[t * kPer + k];
+        sum += local[k];
+    }
+    // inclusive scan of per-thread sums across the block
+    int lane = t & 31, wid = t >> 5;
+    uint32_t v = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) warp_sums[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t s = warp_sums[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(kFull, s, o);
+            if (lane >= o) s += y;
+        }
+        warp_sums[lane] = s;
+    }
+    __syncthreads();
+    uint32_t base = v - sum + (wid ? warp_sums[wid - 1] : 0u);
+#pragma unroll 8
+    for (int k = 0; k < kPer; ++k) {
+        cursor[t * kPer + k] = base;
+        base += local[k];
+        hist[t * kPer + k] = 0u;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_sort_scan(Params P) {
+    if (!P.ctl->sorted) return;
+    scan_buckets(P.Q.hist, P.Q.cursor);
+}
+
+__global__ void __launch_bounds__(256) k_sort_scatter(Params P) {
+    const Ctl* c = P.ctl;
+    if (!c->sorted) return;
+    int32_t n = c->lookup_n;
+    const int32_t* q = P.Q.lq[c->cur];
+    GBMC_WARP_LOOP(idx, valid, n) {
+        uint32_t key = valid ? P.Q.keys[idx] : 0u;
+        int32_t slot = valid ? q[idx] : 0;
+        warp_place(P.Q.cursor, key, valid, P.Q.lqs, slot);
+    }
+}
+
+// ---------------------------------------------------------------- lookup event
+
+template <int PREC>
+__global__ void __launch_bounds__(256) k_lookup(Params P) {
+    const Ctl* c = P.ctl;
+    int32_t n = c->lookup_n;
+    if (n == 0) return;
+    int cur = c->cur;
+    const int32_t* q = c->sorted ? P.Q.lqs : P.Q.lq[cur];
+    int32_t* aq = P.Q.aq[cur] + c->aq_base;
+    unsigned long long micro = 0;
+    GBMC_WARP_LOOP(idx, valid, n) {
+        if (valid) {
+            int32_t slot = q[idx];
+            double E = P.B.E[slot];
+            int32_t m = P.B.mat[slot];
+            double st, sa;
+            if (PREC == GBMC_FP64)
+                macro64(P.T, m, E, st, sa);
+            else
+                macro32(P.T, m, E, st, sa);
+            P.B.st[slot] = st;
+            P.B.sa[slot] = sa;
+            aq[idx] = slot;
+            micro += (unsigned long long)(__ldg(P.T.mat_off + m + 1) - __ldg(P.T.mat_off + m));
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) micro += __shfl_xor_sync(kFull, micro, o);
+    if ((threadIdx.x & 31) == 0 && micro) atomicAdd(&P.ctl->st_micro, micro);
+}
+
+// ---------------------------------------------------------------- death
+
+__device__ __forceinline__ void record_death(const Params& P, int32_t slot, int status, int32_t ncoll,
+                                             int32_t nflt, uint32_t rj, double E, double x,
+                                             double y, double z) {
+    int64_t gi = P.B.gidx[slot];
+    P.O.ncoll[gi] = ncoll;
+    P.O.status[gi] = (int8_t)status;
+    P.O.nflt[gi] = nflt;
+    P.O.ndraw[gi] = rj;
+    P.O.E[gi] = E;
+    P.O.x[gi] = x;
+    P.O.y[gi] = y;
+    P.O.z[gi] = z;
+}
+
+// ---------------------------------------------------------------- advance event
+// Sample the distance to collision, find the distance to the nearest surface
+// of the current cell, move by the smaller one, score the track length in
+// the (cell, energy bin) flux tally, route to collision or surface.
+
+__global__ void __launch_bounds__(256) k_advance(Params P) {
+    Ctl* c = P.ctl;
+    int cur = c->cur;
+    int32_t n = c->n_aq[cur];
+    if (n == 0) return;
+    GBMC_BLOCK_SCALARS(sc, c->n_prob);
+    const int32_t* q = P.Q.aq[cur];
+    GBMC_WARP_LOOP(idx, valid, n) {
+        int32_t slot = 0;
+        int prob = 0;
+        bool collide = false;
+        double wgt = 0.0;
+        if (valid) {
+            slot = q[idx];
+            const Bank& B = P.B;
+            prob = B.prob[slot];
+            const DevProblem& pr = P.probs[prob];
+            const gbmc_geometry& g = pr.g;
+            double x = B.x[slot], y = B.y[slot], z = B.z[slot];
+            double u = B.u[slot], v = B.v[slot], w = B.w[slot];
+            double E = B.E[slot], st = B.st[slot];
+            wgt = B.wgt[slot];
+            int32_t ci = B.ci[slot], cj = B.cj[slot];
+            Stream r;
+            r.init(pr.seed, pr.key_hi, (uint64_t)(pr.first_id + (B.gidx[slot] - pr.start)), B.rj[slot]);
+            double xi = r.next();
+            double dcol = (0.0 - ln_series(xi)) / st;
+            double dbnd = CUDART_INF;
+            uint8_t surf = kSurfNone;
+            int32_t cell = 0;
+            if (g.kind == GBMC_GEOM_LATTICE) {
+                double p = g.pitch;
+                double cx = ((double)ci + 0.5) * p;
+                double cy = ((double)cj + 0.5) * p;
+                double dc = dist_cylinder(x - cx, y - cy, u, v, g.radius, B.inside[slot] != 0);
+                double dx = dist_planes(x, u, (double)ci * p, (double)(ci + 1) * p);
+                double dy = dist_planes(y, v, (double)cj * p, (double)(cj + 1) * p);
+                double dz = dist_planes(z, w, 0.0, g.height);
+                if (dc < 0.0) dc = 0.0;
+                if (dx < 0.0) dx = 0.0;
+                if (dy < 0.0) dy = 0.0;
+                if (dz < 0.0) dz = 0.0;
+                dbnd = dc;
+                surf = kSurfCyl;
+                if (dx < dbnd) { dbnd = dx; surf = kSurfX; }
+                if (dy < dbnd) { dbnd = dy; surf = kSurfY; }
+                if (dz < dbnd) { dbnd = dz; surf = kSurfZ; }
+                cell = cj * g.n + ci;
+            } else if (g.kind == GBMC_GEOM_SLAB) {
+                double h = g.layer_dx;
+                double dx = dist_planes(x, u, (double)ci * h, (double)(ci + 1) * h);
+                if (dx < 0.0) dx = 0.0;
+                dbnd = dx;
+                surf = kSurfX;
+                cell = ci;
+            }
+            collide = dcol < dbnd;
+            double d = collide ? dcol : dbnd;
+            x = x + d * u;
+            y = y + d * v;
+            z = z + d * w;
+            int32_t bin = energy_bin(P.T, E);
+            atomicAdd(&P.Y.flux[pr.flux_off + (int64_t)cell * P.T.n_bins + bin], wgt * d);
+            Bank& Bw = const_cast<Bank&>(P.B);
+            Bw.x[slot] = x; Bw.y[slot] = y; Bw.z[slot] = z;
+            Bw.rj[slot] = r.j;
+            Bw.nflt[slot] = B.nflt[slot] + 1;
+            Bw.surf[slot] = surf;
+        }
+        sc.add(P.Y, valid, prob, GBMC_S_FLIGHT, wgt);
+        warp_append(P.Q.cq, &c->n_cq, slot, valid && collide);
+        warp_append(P.Q.sq, &c->n_sq, slot, valid && !collide);
+    }
+    sc.flush(P.Y);
+}
+
+// ---------------------------------------------------------------- surface event
+
+__global__ void __launch_bounds__(256) k_surface(Params P) {
+    Ctl* c = P.ctl;
+    int32_t n = c->n_sq;
+    if (n == 0) return;
+    GBMC_BLOCK_SCALARS(sc, c->n_prob);
+    int nxt = 1 - c->cur;
+    GBMC_WARP_LOOP(idx, valid, n) {
+        int32_t slot = 0;
+        int prob = 0;
+        int status = 0;
+        bool relook = false;
+        double wgt = 0.0;
+        if (valid) {
+            slot = P.Q.sq[idx];
+            Bank& B = const_cast<Bank&>(P.B);
+            prob = B.prob[slot];
+            const gbmc_geometry& g = P.probs[prob].g;
+            wgt = B.wgt[slot];
+            int32_t ci = B.ci[slot], cj = B.cj[slot], mat = B.mat[slot];
+            double x = B.x[slot], y = B.y[slot], z = B.z[slot];
+            double u = B.u[slot], v = B.v[slot], w = B.w[slot];
+            uint8_t surf = B.surf[slot];
+            if (g.kind == GBMC_GEOM_SLAB) {
+                double h = g.layer_dx;
+                if (u > 0.0) {
+                    x = (double)(ci + 1) * h;
+                    if (ci < g.n_layers - 1) ci += 1;
+                    else status = GBMC_STATUS_LEAKED_FAR;
+                } else {
+                    x = (double)ci * h;
+                    if (ci > 0) ci -= 1;
+                    else status = GBMC_STATUS_LEAKED;
+                }
+                if (!status) {
+                    int32_t m = ci < g.n_first ? g.mat_a : g.mat_b;
+                    relook = m != mat;
+                    mat = m;
+                }
+            } else if (surf == kSurfCyl) {
+                uint8_t in = B.inside[slot] ? 0 : 1;
+                B.inside[slot] = in;
+                int32_t m = in ? g.mat_pin : g.mat_mod;
+                relook = m != mat;
+                mat = m;
+            } else if (surf == kSurfX) {
+                double p = g.pitch;
+                if (u > 0.0) {
+                    x = (double)(ci + 1) * p;
+                    if (ci < g.n - 1) ci += 1;
+                    else if (g.bc_side == GBMC_BC_REFLECT) u = -u;
+                    else status = GBMC_STATUS_LEAKED;
+                } else {
+                    x = (double)ci * p;
+                    if (ci > 0) ci -= 1;
+                    else if (g.bc_side == GBMC_BC_REFLECT) u = -u;
+                    else status = GBMC_STATUS_LEAKED;
+                }
+            } else if (surf == kSurfY) {
+                double p = g.pitch;
+                if (v > 0.0) {
+                    y = (double)(cj + 1) * p;
+                    if (cj < g.n - 1) cj += 1;
+                    else if (g.bc_side == GBMC_BC_REFLECT) v = -v;
+                    else status = GBMC_STATUS_LEAKED;
+                } else {
+                    y = (double)cj * p;
+                    if (cj > 0) cj -= 1;
+                    else if (g.bc_side == GBMC_BC_REFLECT) v = -v;
+                    else status = GBMC_STATUS_LEAKED;
+                }
+            } else {  // z planes
+                z = w > 0.0 ? g.height : 0.0;
+                if (g.bc_z == GBMC_BC_REFLECT) w = -w;
+                else status = GBMC_STATUS_LEAKED;
+            }
+            int32_t nflt = B.nflt[slot];
+            if (!status && nflt >= GBMC_MAX_FLIGHTS) status = GBMC_STATUS_LIMIT;
+            B.x[slot] = x; B.y[slot] = y; B.z[slot] = z;
+            B.u[slot] = u; B.v[slot] = v; B.w[slot] = w;
+            B.ci[slot] = ci; B.cj[slot] = cj; B.mat[slot] = mat;
+            if (status)
+                record_death(P, slot, status, B.ncoll[slot], nflt, B.rj[slot], B.E[slot], x, y, z);
+        }
+        bool dead = valid && status != 0;
+        sc.add(P.Y, dead && (status == GBMC_STATUS_LEAKED || status == GBMC_STATUS_LEAKED_FAR),
+               prob, GBMC_S_LEAK, wgt);
+        sc.add(P.Y, dead && status == GBMC_STATUS_LEAKED_FAR, prob, GBMC_S_LEAK_FAR, wgt);
+        sc.add(P.Y, dead && status == GBMC_STATUS_LIMIT, prob, GBMC_S_LIMIT, wgt);
+        warp_append(P.Q.fq, &c->n_free, slot, dead);
+        warp_append(P.Q.lq[nxt], &c->n_lq[nxt], slot, valid && !dead && relook);
+        warp_append(P.Q.aq[nxt], &c->n_aq[nxt], slot, valid && !dead && !relook);
+    }
+    sc.flush(P.Y);
+}
+
+// ---------------------------------------------------------------- collision event
+// Pick the nuclide, absorb or scatter elastically (isotropic in the CM
+// frame, target at rest), apply the energy cutoff.
+
+template <int PREC>
+__global__ void __launch_bounds__(256) k_collision(Params P) {
+    Ctl* c = P.ctl;
+    int32_t n = c->n_cq;
+    if (n == 0) return;
+    GBMC_BLOCK_SCALARS(sc, c->n_prob);
+    int nxt = 1 - c->cur;
+    GBMC_WARP_LOOP(idx, valid, n) {
+        int32_t slot = 0;
+        int prob = 0;
+        int status = 0;
+        double wgt = 0.0;
+        if (valid) {
+            slot = P.Q.cq[idx];
+            Bank& B = const_cast<Bank&>(P.B);
+            prob = B.prob[slot];
+            const DevProblem& pr = P.probs[prob];
+            wgt = B.wgt[slot];
+            double E = B.E[slot];
+            int32_t mat = B.mat[slot];
+            Stream r;
+            r.init(pr.seed, pr.key_hi, (uint64_t)(pr.first_id + (B.gidx[slot] - pr.start)), B.rj[slot]);
+            double target = r.next() * B.st[slot];
+            int32_t nuc = pick_nuclide(P.T, PREC, mat, E, target);
+            int32_t ncoll = B.ncoll[slot] + 1;
+            double xa = r.next();
+            if (xa < __ldg(P.T.f_abs + nuc)) {
+                status = GBMC_STATUS_ABSORBED;
+            } else {
+                double mu = 2.0 * r.next() - 1.0;
+                double a, b;
+                double s = disk_pair(r, a, b);
+                double cphi = (a * a - b * b) / s;
+                double sphi = ((2.0 * a) * b) / s;
+                double E1, mul;
+                elastic(E, __ldg(P.T.awr + nuc), mu, E1, mul);
+                double u = B.u[slot], v = B.v[slot], w = B.w[slot];
+                rotate(u, v, w, mul, cphi, sphi);
+                B.u[slot] = u; B.v[slot] = v; B.w[slot] = w;
+                E = E1;
+                B.E[slot] = E;
+                if (E < pr.g.E_cut) status = GBMC_STATUS_CUTOFF;
+            }
+            int32_t nflt = B.nflt[slot];
+            if (!status && nflt >= GBMC_MAX_FLIGHTS) status = GBMC_STATUS_LIMIT;
+            B.ncoll[slot] = ncoll;
+            B.rj[slot] = r.j;
+            if (status)
+                record_death(P, slot, status, ncoll, nflt, r.j, E, B.x[slot], B.y[slot], B.z[slot]);
+        }
+        bool dead = valid && status != 0;
+        sc.add(P.Y, valid, prob, GBMC_S_COLLISION, wgt);
+        sc.add(P.Y, dead && status == GBMC_STATUS_ABSORBED, prob, GBMC_S_ABSORPTION, wgt);
+        sc.add(P.Y, dead && status == GBMC_STATUS_CUTOFF, prob, GBMC_S_CUTOFF, wgt);
+        sc.add(P.Y, dead && status == GBMC_STATUS_LIMIT, prob, GBMC_S_LIMIT, wgt);
+        warp_append(P.Q.fq, &c->n_free, slot, dead);
+        warp_append(P.Q.lq[nxt], &c->n_lq[nxt], slot, valid && !dead);
+    }
+    sc.flush(P.Y);
+}
+
+// ---------------------------------------------------------------- standalone lookup
+
+__global__ void __launch_bounds__(256) k_query_keys(Params P, const double* E, const int32_t* mat,
+                                                    int64_t n, uint32_t* keys, uint32_t* hist) {
+    GBMC_WARP_LOOP(idx, valid, n) {
+        uint32_t key = 0;
+        if (valid) {
+            key = sort_key(P, E[idx], mat[idx]);
+            keys[idx] = key;
+        }
+        warp_count(hist, key, valid);
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_query_scan(uint32_t* hist, uint32_t* cursor) {
+    scan_buckets(hist, cursor);
+}
+
+__global__ void __launch_bounds__(256) k_query_scatter(int64_t n, const uint32_t* keys,
+                                                       uint32_t* cursor, int32_t* perm) {
+    GBMC_WARP_LOOP(idx, valid, n) {
+        uint32_t key = valid ? keys[idx] : 0u;
+        warp_place(cursor, key, valid, perm, (int32_t)idx);
+    }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(256) k_query_lookup(Tables T, const double* __restrict__ E,
+                                                      const int32_t* __restrict__ mat, int64_t n,
+                                                      const int32_t* __restrict__ perm,
+                                                      double* __restrict__ st,
+                                                      double* __restrict__ sa) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = perm ? (int64_t)perm[k] : k;
+        double a, b;
+        if (PREC == GBMC_FP64)
+            macro64(T, mat[i], E[i], a, b);
+        else
+            macro32(T, mat[i], E[i], a, b);
+        st[i] = a;
+        sa[i] = b;
+    }
+}
+
+// ---------------------------------------------------------------- host launchers
+
+cudaError_t launch_init_run(const Params& P, const LaunchCfg& L, cudaStream_t s) {
+    k_init_run<<<L.grid, 256, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_iteration(const Params& P, const LaunchCfg& L, cudaStream_t s) {
+    k_plan<<<1, 32, 0, s>>>(P);
+    k_source<<<L.grid, 256, 0, s>>>(P);
+    if (P.sort) {
+        k_sort_keys<<<L.grid, 256, 0, s>>>(P);
+        k_sort_scan<<<1, 1024, 0, s>>>(P);
+        k_sort_scatter<<<L.grid, 256, 0, s>>>(P);
+    }
+    if (P.precision == GBMC_FP64)
+        k_lookup<GBMC_FP64><<<L.grid_lookup, 256, 0, s>>>(P);
+    else
+        k_lookup<GBMC_FP32><<<L.grid_lookup, 256, 0, s>>>(P);
+    k_advance<<<L.grid, 256, 0, s>>>(P);
+    k_surface<<<L.grid, 256, 0, s>>>(P);
+    if (P.precision == GBMC_FP64)
+        k_collision<GBMC_FP64><<<L.grid, 256, 0, s>>>(P);
+    else
+        k_collision<GBMC_FP32><<<L.grid, 256, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_iteration_timed(const Params& P, const LaunchCfg& L, cudaStream_t s,
+                                   cudaEvent_t* ev) {
+    cudaEventRecord(ev[0], s);
+    k_plan<<<1, 32, 0, s>>>(P);
+    cudaEventRecord(ev[1], s);
+    k_source<<<L.grid, 256, 0, s>>>(P);
+    cudaEventRecord(ev[2], s);
+    if (P.sort) k_sort_keys<<<L.grid, 256, 0, s>>>(P);
+    cudaEventRecord(ev[3], s);
+    if (P.sort) k_sort_scan<<<1, 1024, 0, s>>>(P);
+    cudaEventRecord(ev[4], s);
+    if (P.sort) k_sort_scatter<<<L.grid, 256, 0, s>>>(P);
+    cudaEventRecord(ev[5], s);
+    if (P.precision == GBMC_FP64)
+        k_lookup<GBMC_FP64><<<L.grid_lookup, 256, 0, s>>>(P);
+    else
+        k_lookup<GBMC_FP32><<<L.grid_lookup, 256, 0, s>>>(P);
+    cudaEventRecord(ev[6], s);
+    k_advance<<<L.grid, 256, 0, s>>>(P);
+    cudaEventRecord(ev[7], s);
+    k_surface<<<L.grid, 256, 0, s>>>(P);
+    cudaEventRecord(ev[8], s);
+    if (P.precision == GBMC_FP64)
+        k_collision<GBMC_FP64><<<L.grid, 256, 0, s>>>(P);
+    else
+        k_collision<GBMC_FP32><<<L.grid, 256, 0, s>>>(P);
+    cudaEventRecord(ev[9], s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_query_lookup(const Params& P, const LaunchCfg& L, const double* E,
+                                const int32_t* mat, int64_t n, double* st, double* sa,
+                                int32_t* perm, uint32_t* keys, uint32_t* hist, uint32_t* cursor,
+                                cudaStream_t s) {
+    if (perm) {
+        k_query_keys<<<L.grid, 256, 0, s>>>(P, E, mat, n, keys, hist);
+        k_query_scan<<<1, 1024, 0, s>>>(hist, cursor);
+        k_query_scatter<<<L.grid, 256, 0, s>>>(n, keys, cursor, perm);
+    }
+    if (P.precision == GBMC_FP64)
+        k_query_lookup<GBMC_FP64><<<L.grid_lookup, 256, 0, s>>>(P.T, E, mat, n, perm, st, sa);
+    else
+        k_query_lookup<GBMC_FP32><<<L.grid_lookup, 256, 0, s>>>(P.T, E, mat, n, perm, st, sa);
+    return cudaGetLastError();
+}
+
+}  // namespace gbmc

@@ -1,0 +1,310 @@
+"""Python binding of the gbmc C ABI (include/gbmc.h): argument marshalling only.
+
+Every step of the transport hot path runs in the CUDA kernels of
+libgbmc.so; this module converts arrays and structures and checks return
+codes.  PyTorch supplies device memory and streams where an entry point takes
+device pointers.  There is no CPU fallback: if the library cannot be loaded,
+importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgbmc.so")
+
+OK = 0
+ERR_INVALID_ARG, ERR_NOT_INITIALIZED, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_DEVICE_FLAG, \
+    ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6, -7
+FP64, FP32 = 0, 1
+GEOM_INFINITE, GEOM_LATTICE, GEOM_SLAB = 0, 1, 2
+BC_VACUUM, BC_REFLECT = 0, 1
+SRC_ORIGIN, SRC_BOX, SRC_SLAB_FACE = 0, 1, 2
+STATUS_ABSORBED, STATUS_LEAKED, STATUS_CUTOFF, STATUS_LIMIT, STATUS_LEAKED_FAR = 1, 2, 3, 4, 5
+S_COLLISION, S_ABSORPTION, S_LEAK, S_CUTOFF, S_LIMIT, S_LEAK_FAR, S_FLIGHT, S_HISTORY = range(8)
+NSCAL = 8
+MAX_FLIGHTS = 100000
+
+EXPORTS = ["gbmc_default_options", "gbmc_create", "gbmc_destroy", "gbmc_last_error",
+           "gbmc_set_options", "gbmc_load_xs_tables", "gbmc_init_materials", "gbmc_set_tally",
+           "gbmc_reset_tallies", "gbmc_run_batch", "gbmc_run_problems", "gbmc_read_tallies",
+           "gbmc_read_outcomes", "gbmc_read_stats", "gbmc_lookup_macro", "gbmc_last_run_ms",
+           "gbmc_profile_problems"]
+KERNEL_NAMES = ["plan", "source", "sort_keys", "sort_scan", "sort_scatter", "lookup", "advance",
+                "surface", "collision"]
+
+
+class GbmcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"gbmc error {code}: {msg}")
+        self.code = code
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("max_in_flight", C.c_int64), ("sort", C.c_int32),
+                ("block_lookup", C.c_int32), ("block_event", C.c_int32),
+                ("blocks_per_sm", C.c_int32), ("max_iterations", C.c_int32),
+                ("reserved", C.c_int32 * 8)]
+
+
+class Geometry(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("source", C.c_int32), ("E0", C.c_double),
+                ("E_cut", C.c_double), ("mat", C.c_int32), ("n", C.c_int32),
+                ("pitch", C.c_double), ("radius", C.c_double), ("height", C.c_double),
+                ("mat_pin", C.c_int32), ("mat_mod", C.c_int32), ("bc_side", C.c_int32),
+                ("bc_z", C.c_int32), ("n_layers", C.c_int32), ("layer_dx", C.c_double),
+                ("n_first", C.c_int32), ("mat_a", C.c_int32), ("mat_b", C.c_int32)]
+
+
+class Problem(C.Structure):
+    _fields_ = [("geom", Geometry), ("seed", C.c_uint64), ("problem_index", C.c_uint32),
+                ("batch", C.c_uint32), ("first_id", C.c_int64), ("n_particles", C.c_int64)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iterations", C.c_int64), ("lookups", C.c_int64), ("micro_lookups", C.c_int64),
+                ("flights", C.c_int64), ("crossings", C.c_int64), ("collisions", C.c_int64),
+                ("histories", C.c_int64), ("device_error", C.c_int32), ("reserved", C.c_int32)]
+
+
+class KernelTimes(C.Structure):
+    _fields_ = [("ms", C.c_double * 9), ("launches", C.c_int64 * 9)]
+
+
+_P = C.POINTER
+_lib = None
+
+
+def lib():
+    """The loaded libgbmc.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "paper_2403_12345_gb300/build.py (there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        vp = C.c_void_p
+        L.gbmc_default_options.argtypes = [_P(Options)]
+        L.gbmc_create.argtypes = [_P(vp), C.c_int, _P(Options)]
+        L.gbmc_destroy.argtypes = [vp]
+        L.gbmc_last_error.argtypes = [vp]
+        L.gbmc_last_error.restype = C.c_char_p
+        L.gbmc_set_options.argtypes = [vp, _P(Options)]
+        L.gbmc_load_xs_tables.argtypes = [vp, C.c_int32, _P(C.c_int64), _P(C.c_double),
+                                          _P(C.c_double), _P(C.c_double), _P(C.c_double),
+                                          C.c_int32]
+        L.gbmc_init_materials.argtypes = [vp, C.c_int32, _P(C.c_int32), _P(C.c_int32),
+                                          _P(C.c_double)]
+        L.gbmc_set_tally.argtypes = [vp, C.c_int32, _P(C.c_double)]
+        L.gbmc_reset_tallies.argtypes = [vp, vp]
+        L.gbmc_run_batch.argtypes = [vp, _P(Problem), vp]
+        L.gbmc_run_problems.argtypes = [vp, C.c_int32, _P(Problem), vp]
+        L.gbmc_read_tallies.argtypes = [vp, C.c_int32, _P(C.c_double), C.c_int64,
+                                        _P(C.c_int64), _P(C.c_double)]
+        L.gbmc_read_outcomes.argtypes = [vp, C.c_int32, C.c_int64, C.c_int64, _P(C.c_int32),
+                                         _P(C.c_int8), _P(C.c_int32), _P(C.c_uint32),
+                                         _P(C.c_double), _P(C.c_double), _P(C.c_double),
+                                         _P(C.c_double)]
+        L.gbmc_read_stats.argtypes = [vp, _P(Stats)]
+        L.gbmc_lookup_macro.argtypes = [vp, C.c_int32, vp, vp, C.c_int64, vp, vp, C.c_int32, vp]
+        L.gbmc_last_run_ms.argtypes = [vp, _P(C.c_double)]
+        L.gbmc_profile_problems.argtypes = [vp, C.c_int32, _P(Problem), vp, _P(KernelTimes)]
+        for name in EXPORTS:
+            if name != "gbmc_last_error":
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _arr(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(_P(ct))
+
+
+def _stream(stream):
+    """cudaStream_t from None / int / torch.cuda.Stream."""
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def geometry(**kw) -> Geometry:
+    g = Geometry()
+    g.E0, g.E_cut = 1e6, 1e-5
+    g.pitch, g.radius, g.height, g.layer_dx = 1.26, 0.4, 100.0, 1.0
+    g.n = 1
+    for k, v in kw.items():
+        setattr(g, k, v)
+    return g
+
+
+def geometry_from(obj) -> Geometry:
+    """Geometry from any object carrying the same field names."""
+    return geometry(**{name: getattr(obj, name) for name, _ in Geometry._fields_})
+
+
+def problem(geom: Geometry, seed: int, n_particles: int, batch: int = 0,
+            problem_index: int = 0, first_id: int = 0) -> Problem:
+    p = Problem()
+    p.geom = geom
+    p.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    p.problem_index = int(problem_index)
+    p.batch = int(batch)
+    p.first_id = int(first_id)
+    p.n_particles = int(n_particles)
+    return p
+
+
+class Context:
+    """One gbmc context (gbmc_create ... gbmc_destroy) on one CUDA device."""
+
+    def __init__(self, device: int = 0, **options):
+        L = lib()
+        opt = Options()
+        L.gbmc_default_options(C.byref(opt))
+        for k, v in options.items():
+            setattr(opt, k, v)
+        h = C.c_void_p()
+        rc = L.gbmc_create(C.byref(h), int(device), C.byref(opt))
+        if rc != OK:
+            raise GbmcError(rc, L.gbmc_last_error(None).decode())
+        self._h = h
+        self.options = opt
+        self.n_bins = 0
+        self._cells = []
+
+    def _ck(self, rc):
+        if rc != OK:
+            raise GbmcError(rc, lib().gbmc_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().gbmc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- set-up ---------------------------------------------------------------
+    def set_options(self, **kw):
+        for k, v in kw.items():
+            setattr(self.options, k, v)
+        self._ck(lib().gbmc_set_options(self._h, C.byref(self.options)))
+
+    def load_xs_tables(self, grid_off, energy, sigma_t, f_abs, awr, precision=FP64):
+        go = _arr(grid_off, np.int64)
+        e, s = _arr(energy, np.float64), _arr(sigma_t, np.float64)
+        fa, aw = _arr(f_abs, np.float64), _arr(awr, np.float64)
+        self._ck(lib().gbmc_load_xs_tables(self._h, len(go) - 1, _p(go, C.c_int64),
+                                           _p(e, C.c_double), _p(s, C.c_double),
+                                           _p(fa, C.c_double), _p(aw, C.c_double),
+                                           int(precision)))
+
+    def init_materials(self, mat_off, nuc_id, density):
+        mo, ni, de = _arr(mat_off, np.int32), _arr(nuc_id, np.int32), _arr(density, np.float64)
+        self._ck(lib().gbmc_init_materials(self._h, len(mo) - 1, _p(mo, C.c_int32),
+                                           _p(ni, C.c_int32), _p(de, C.c_double)))
+
+    def set_tally(self, edges):
+        ed = _arr(edges, np.float64)
+        self._ck(lib().gbmc_set_tally(self._h, len(ed) - 1, _p(ed, C.c_double)))
+        self.n_bins = len(ed) - 1
+
+    def load(self, prob, precisions=(FP64,)):
+        """Tables, materials and tally edges of a pooled problem description
+        (any object with grid_off, energy, sigma_t, f_abs, awr, mat_off,
+        nuc_id, density and edges)."""
+        for prec in precisions:
+            self.load_xs_tables(prob.grid_off, prob.energy, prob.sigma_t, prob.f_abs,
+                                prob.awr, prec)
+        self.init_materials(prob.mat_off, prob.nuc_id, prob.density)
+        self.set_tally(prob.edges)
+
+    def reset_tallies(self, stream=None):
+        self._ck(lib().gbmc_reset_tallies(self._h, _stream(stream)))
+
+    # -- runs -----------------------------------------------------------------
+    def run_batch(self, prob: Problem, stream=None):
+        self._ck(lib().gbmc_run_batch(self._h, C.byref(prob), _stream(stream)))
+        self._cells = [_n_cells(prob.geom)]
+
+    def run_problems(self, probs, stream=None):
+        arr = (Problem * len(probs))(*probs)
+        self._ck(lib().gbmc_run_problems(self._h, len(probs), arr, _stream(stream)))
+        self._cells = [_n_cells(p.geom) for p in probs]
+
+    def profile_problems(self, probs, stream=None) -> dict:
+        """Run with every kernel launched eagerly between CUDA events; returns
+        {kernel: (total ms, launches)}."""
+        arr = (Problem * len(probs))(*probs)
+        kt = KernelTimes()
+        self._ck(lib().gbmc_profile_problems(self._h, len(probs), arr, _stream(stream),
+                                             C.byref(kt)))
+        self._cells = [_n_cells(p.geom) for p in probs]
+        return {name: (kt.ms[k], kt.launches[k]) for k, name in enumerate(KERNEL_NAMES)}
+
+    # -- read-back ------------------------------------------------------------
+    def read_tallies(self, slot: int = 0):
+        nc = self._cells[slot]
+        flux = np.zeros((nc, self.n_bins))
+        counts = np.zeros(NSCAL, np.int64)
+        weights = np.zeros(NSCAL)
+        self._ck(lib().gbmc_read_tallies(self._h, int(slot), _p(flux, C.c_double), flux.size,
+                                         _p(counts, C.c_int64), _p(weights, C.c_double)))
+        return flux, counts, weights
+
+    def read_outcomes(self, slot: int = 0, first: int = 0, n: int = 0):
+        o = dict(n_coll=np.zeros(n, np.int32), status=np.zeros(n, np.int8),
+                 n_flights=np.zeros(n, np.int32), n_draws=np.zeros(n, np.uint32),
+                 E=np.zeros(n), x=np.zeros(n), y=np.zeros(n), z=np.zeros(n))
+        self._ck(lib().gbmc_read_outcomes(
+            self._h, int(slot), int(first), int(n), _p(o["n_coll"], C.c_int32),
+            _p(o["status"], C.c_int8), _p(o["n_flights"], C.c_int32),
+            _p(o["n_draws"], C.c_uint32), _p(o["E"], C.c_double), _p(o["x"], C.c_double),
+            _p(o["y"], C.c_double), _p(o["z"], C.c_double)))
+        return o
+
+    def read_stats(self) -> dict:
+        s = Stats()
+        self._ck(lib().gbmc_read_stats(self._h, C.byref(s)))
+        return {name: getattr(s, name) for name, _ in Stats._fields_ if name != "reserved"}
+
+    def last_run_ms(self) -> float:
+        ms = C.c_double()
+        self._ck(lib().gbmc_last_run_ms(self._h, C.byref(ms)))
+        return ms.value
+
+    def lookup_macro(self, E, mat, sigma_t, sigma_a, precision=FP64, sort=False, stream=None):
+        """E (float64), mat (int32), sigma_t, sigma_a (float64): CUDA tensors
+        (or raw device addresses) of equal length, written in query order."""
+        def ptr(t):
+            return C.c_void_p(t if isinstance(t, int) else t.data_ptr())
+        n = E.numel() if hasattr(E, "numel") else len(E)
+        self._ck(lib().gbmc_lookup_macro(self._h, int(precision), ptr(E), ptr(mat), int(n),
+                                         ptr(sigma_t), ptr(sigma_a), 1 if sort else 0,
+                                         _stream(stream)))
+
+
+def _n_cells(g: Geometry) -> int:
+    if g.kind == GEOM_LATTICE:
+        return g.n * g.n
+    if g.kind == GEOM_SLAB:
+        return g.n_layers
+    return 1

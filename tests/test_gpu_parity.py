@@ -1,0 +1,201 @@
+"""GPU path vs the CPU oracle, through the C ABI.
+
+Per-particle outcomes (collisions, fate, flights, draws, final energy and
+position) must match bit for bit in the binary64 mode and in the binary32
+table mode against the oracle run in the same precision; tallies must match
+to summation order (1e-12 per bin, counts exactly).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from paper_2403_12345_gb300 import gbmc
+
+from gpu_helpers import (assert_outcomes_equal, assert_tallies_close, gpu_problem, make_ctx,
+                         run_gpu)
+
+pytestmark = pytest.mark.gpu
+
+
+def _parity(prob, n, precision=gbmc.FP64, batch=0, **options):
+    ctx = make_ctx(prob, (precision,), precision=precision, **options)
+    try:
+        gp = gpu_problem(prob, n=n, batch=batch)
+        g = run_gpu(ctx, gp)
+        stats = ctx.read_stats()
+    finally:
+        ctx.close()
+    ref = oracle.run(prob, seed=prob.seed, batch=batch, n=n, precision=precision)
+    assert_outcomes_equal(g, ref)
+    assert_tallies_close(g, ref)
+    return g, ref, stats
+
+
+def test_infinite_medium_parity():
+    p = synth.make_config(1)
+    g, ref, st = _parity(p, 100_000)
+    assert st["histories"] == 100_000
+    assert st["collisions"] == ref["counts"][oracle.S_COLLISION]
+
+
+def test_lattice_parity_with_refill_and_ragged_tail():
+    p = synth.make_config(2, grid_scale=0.05)
+    # in-flight cap far below the batch: many refills; 20011 is not a
+    # multiple of any block or warp size
+    g, ref, st = _parity(p, 20_011, max_in_flight=3_000, batch=4)
+    assert st["iterations"] > 10
+    assert st["flights"] == ref["counts"][oracle.S_FLIGHT]
+
+
+def test_lattice_fp32_tables_parity_and_error_vs_fp64():
+    p = synth.make_config(3, grid_scale=0.05)
+    g, ref32, _ = _parity(p, 20_000, precision=gbmc.FP32)
+    ref64 = oracle.run(p, seed=p.seed, n=20_000, precision=0)
+    rel = np.linalg.norm(g["flux"] - ref64["flux"]) / np.linalg.norm(ref64["flux"])
+    assert rel < 1e-2
+
+
+def test_slab_parity():
+    p = synth.make_tiny_problem(seed=31, n_nuc=4, n_points=(20, 200), kind=synth.GEOM_SLAB,
+                                n_particles=20_000)
+    _parity(p, 20_000)
+
+
+def test_all_reflective_lattice_parity():
+    p = synth.make_tiny_problem(seed=32, n_nuc=4, n_points=(50, 300), kind=synth.GEOM_LATTICE,
+                                lattice_n=4, n_particles=10_000)
+    p.geom.bc_z = synth.BC_REFLECT
+    _parity(p, 10_000)
+
+
+def test_vacuum_sides_lattice_parity():
+    p = synth.make_tiny_problem(seed=33, n_nuc=5, n_points=(50, 300), kind=synth.GEOM_LATTICE,
+                                lattice_n=5, n_particles=10_000)
+    p.geom.bc_side = synth.BC_VACUUM
+    _parity(p, 10_000)
+
+
+def test_sort_does_not_change_outcomes():
+    p = synth.make_config(2, grid_scale=0.05)
+    res = []
+    for sort in (1, -1):
+        ctx = make_ctx(p, sort=sort)
+        try:
+            res.append(run_gpu(ctx, gpu_problem(p, n=30_000)))
+        finally:
+            ctx.close()
+    assert_outcomes_equal(res[0], res[1], label="sort on/off")
+    assert_tallies_close(res[0], res[1])
+
+
+def test_in_flight_cap_one_and_empty_batch():
+    p = synth.make_tiny_problem(seed=34, n_nuc=3, n_points=(10, 50), n_particles=50)
+    ctx = make_ctx(p, max_in_flight=1)
+    try:
+        g = run_gpu(ctx, gpu_problem(p, n=50))
+        ref = oracle.run(p, seed=p.seed, n=50)
+        assert_outcomes_equal(g, ref)
+        assert_tallies_close(g, ref)
+        g0 = run_gpu(ctx, gpu_problem(p, n=0))
+        assert g0["flux"].sum() == 0 and g0["counts"].sum() == 0
+    finally:
+        ctx.close()
+
+
+def test_id_subset_and_batches_accumulate():
+    p = synth.make_config(2, grid_scale=0.02)
+    ctx = make_ctx(p)
+    try:
+        ctx.reset_tallies()
+        for b in range(3):
+            ctx.run_batch(gpu_problem(p, n=4000, first_id=1000, batch=b))
+            out = ctx.read_outcomes(0, 0, 4000)
+            ref = oracle.run(p, seed=p.seed, batch=b, first_id=1000, n=4000)
+            assert_outcomes_equal(out, ref, label=f"batch {b}")
+        flux, counts, _ = ctx.read_tallies(0)
+    finally:
+        ctx.close()
+    tot = sum(oracle.run(p, seed=p.seed, batch=b, first_id=1000, n=4000)["flux"] for b in range(3))
+    nz = tot > 0
+    assert np.all(np.abs(flux[nz] - tot[nz]) <= 1e-12 * tot[nz])
+    assert counts[oracle.S_HISTORY] == 12_000
+
+
+def test_multi_problem_run_matches_single_runs():
+    p = synth.make_config(4, n_problems=5, n_particles=3000, grid_scale=0.02)
+    ctx = make_ctx(p, (gbmc.FP32,), precision=gbmc.FP32, max_in_flight=5000)
+    try:
+        probs = [gpu_problem(p, geom_index=k, n=3000 + 7 * k, problem_index=k, batch=2)
+                 for k in range(5)]
+        ctx.reset_tallies()
+        ctx.run_problems(probs)
+        for k in range(5):
+            ref = oracle.run(p, seed=p.seed, batch=2, n=3000 + 7 * k, geom_index=k,
+                             problem_index=k, precision=1)
+            out = ctx.read_outcomes(k, 0, 3000 + 7 * k)
+            assert_outcomes_equal(out, ref, label=f"problem {k}")
+            flux, counts, weights = ctx.read_tallies(k)
+            assert_tallies_close(dict(flux=flux, counts=counts, weights=weights), ref)
+    finally:
+        ctx.close()
+
+
+@pytest.mark.parametrize("precision", [gbmc.FP64, gbmc.FP32])
+@pytest.mark.parametrize("sort", [False, True])
+def test_lookup_macro_matches_oracle(precision, sort):
+    import torch
+    prob, E, mat = synth.make_stress_lookup(n_queries=20_011, n_nuc=40, n_in_mat=30,
+                                            n_points=3000)
+    mat[::3] = 1
+    ctx = make_ctx(prob, (precision,))
+    try:
+        dE = torch.tensor(E, device="cuda")
+        dm = torch.tensor(mat, device="cuda")
+        st = torch.empty_like(dE)
+        sa = torch.empty_like(dE)
+        ctx.lookup_macro(dE, dm, st, sa, precision=precision, sort=sort)
+        torch.cuda.synchronize()
+        st, sa = st.cpu().numpy(), sa.cpu().numpy()
+    finally:
+        ctx.close()
+    for m in (0, 1):
+        sel = mat == m
+        rt, ra = oracle.macro(prob, m, E[sel], precision=precision)
+        assert np.array_equal(st[sel].view(np.int64), rt.view(np.int64))
+        assert np.array_equal(sa[sel].view(np.int64), ra.view(np.int64))
+
+
+def test_invalid_inputs_rejected_before_launch():
+    p = synth.make_tiny_problem(seed=35, n_nuc=2, n_points=(5, 9))
+    ctx = gbmc.Context(0)
+    try:
+        e = p.energy.copy()
+        e[2] = e[1]
+        with pytest.raises(gbmc.GbmcError) as ex:
+            ctx.load_xs_tables(p.grid_off, e, p.sigma_t, p.f_abs, p.awr)
+        assert ex.value.code == gbmc.ERR_INVALID_ARG
+        s = p.sigma_t.copy()
+        s[0] = -1.0
+        with pytest.raises(gbmc.GbmcError):
+            ctx.load_xs_tables(p.grid_off, p.energy, s, p.f_abs, p.awr)
+        e = p.energy.copy()
+        e[1] = np.nextafter(e[0], np.inf)   # distinct in binary64, equal in binary32
+        with pytest.raises(gbmc.GbmcError):
+            ctx.load_xs_tables(p.grid_off, e, p.sigma_t, p.f_abs, p.awr, gbmc.FP32)
+        with pytest.raises(gbmc.GbmcError) as ex:
+            ctx.run_batch(gpu_problem(p, n=10))
+        assert ex.value.code == gbmc.ERR_NOT_INITIALIZED
+        ctx.load(p)
+        with pytest.raises(gbmc.GbmcError):
+            ctx.init_materials([0, 2], [0, 7], [0.5, 0.5])
+        g = gpu_problem(p, n=10)
+        g.geom.E0 = 3e7   # above every grid
+        with pytest.raises(gbmc.GbmcError):
+            ctx.run_batch(g)
+        with pytest.raises(gbmc.GbmcError) as ex:
+            ctx.set_options(precision=gbmc.FP32)
+            ctx.run_batch(gpu_problem(p, n=10))
+        assert ex.value.code == gbmc.ERR_NOT_INITIALIZED
+    finally:
+        ctx.close()
