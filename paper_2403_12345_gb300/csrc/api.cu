@@ -99,11 +99,16 @@ struct gbmc_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<int64_t> run_start, run_n;
 
+    // running sums of N_i sigma_i per bank slot (collision nuclide choice)
+    void* d_cum = nullptr;
+    size_t cum_bytes = 0;
+    int32_t max_nuc_per_mat = 0;
+
     // standalone-lookup scratch
     int64_t q_cap = 0;
     int32_t* q_perm = nullptr;
     uint32_t* q_keys = nullptr;
-    uint32_t *q_hist = nullptr, *q_cursor = nullptr;
+    uint32_t *q_hist = nullptr, *q_cursor = nullptr, *q_btot = nullptr;
 };
 
 namespace {
@@ -193,7 +198,7 @@ void free_bank(gbmc_ctx* c) {
     Queues& Q = c->Q;
     dfree(Q.lq[0]); dfree(Q.lq[1]); dfree(Q.aq[0]); dfree(Q.aq[1]);
     dfree(Q.sq); dfree(Q.cq); dfree(Q.fq); dfree(Q.lqs); dfree(Q.keys);
-    dfree(Q.hist); dfree(Q.cursor);
+    dfree(Q.hist); dfree(Q.cursor); dfree(Q.btot);
     c->capacity = 0;
 }
 
@@ -217,12 +222,40 @@ int ensure_bank(gbmc_ctx* c, int32_t M) {
     rc |= dalloc(c, &Q.sq, n); rc |= dalloc(c, &Q.cq, n); rc |= dalloc(c, &Q.fq, n);
     rc |= dalloc(c, &Q.lqs, n); rc |= dalloc(c, &Q.keys, n);
     rc |= dalloc(c, &Q.hist, kSortBuckets); rc |= dalloc(c, &Q.cursor, kSortBuckets);
+    rc |= dalloc(c, &Q.btot, kSortBuckets / 1024);
     if (rc) {
         free_bank(c);
         return GBMC_ERR_OOM;
     }
     CK(cudaMemset(Q.hist, 0, sizeof(uint32_t) * kSortBuckets));
     c->capacity = M;
+    return GBMC_OK;
+}
+
+// Running-sum cache: max nuclides per material x bank slots, in the table
+// precision.  Above kCumBudget bytes the collision recomputes instead.
+constexpr size_t kCumBudget = (size_t)16 << 30;
+
+int ensure_cum(gbmc_ctx* c) {
+    size_t el = c->opt.precision == GBMC_FP64 ? sizeof(double) : sizeof(float);
+    size_t need = (size_t)c->max_nuc_per_mat * (size_t)c->capacity * el;
+    if (need > kCumBudget) need = 0;
+    if (need <= c->cum_bytes && (need == 0) == (c->d_cum == nullptr)) return GBMC_OK;
+    if (c->d_cum) {
+        cudaDeviceSynchronize();
+        cudaFree(c->d_cum);
+        c->d_cum = nullptr;
+        c->cum_bytes = 0;
+    }
+    c->graph_valid = false;
+    if (need == 0) return GBMC_OK;
+    cudaError_t e = cudaMalloc(&c->d_cum, need);
+    if (e != cudaSuccess) {
+        c->d_cum = nullptr;   // fall back to recomputation
+        cudaGetLastError();
+        return GBMC_OK;
+    }
+    c->cum_bytes = need;
     return GBMC_OK;
 }
 
@@ -322,6 +355,8 @@ Params make_params(gbmc_ctx* c) {
     P.sort_min = 4096;
     P.max_iter = c->opt.max_iterations;
     sort_params(c, P);
+    P.cum = c->d_cum;
+    P.cum_stride = c->d_cum ? c->capacity : 0;
     return P;
 }
 
@@ -543,7 +578,8 @@ int gbmc_destroy(gbmc_ctx* c) {
     dfree(c->d_fabs); dfree(c->d_fabs32); dfree(c->d_awr);
     dfree(c->d_mat_off); dfree(c->d_nuc_id); dfree(c->d_density); dfree(c->d_density32);
     dfree(c->d_edges); dfree(c->d_probs); dfree(c->d_ctl);
-    dfree(c->q_perm); dfree(c->q_keys); dfree(c->q_hist); dfree(c->q_cursor);
+    if (c->d_cum) { cudaDeviceSynchronize(); cudaFree(c->d_cum); }
+    dfree(c->q_perm); dfree(c->q_keys); dfree(c->q_hist); dfree(c->q_cursor); dfree(c->q_btot);
     if (c->h_probs) cudaFreeHost(c->h_probs);
     if (c->h_ctl) cudaFreeHost(c->h_ctl);
     if (c->staged) cudaEventDestroy(c->staged);
@@ -688,6 +724,9 @@ int gbmc_init_materials(gbmc_ctx* c, int32_t n_mat, const int32_t* mat_off, cons
     for (int32_t q = 0; q < tot; ++q) d32[q] = (float)density[q];
     if ((rc = upload(c, &c->d_density32, d32.data(), (size_t)tot))) return rc;
     c->n_mat = n_mat;
+    c->max_nuc_per_mat = 0;
+    for (int32_t m = 0; m < n_mat; ++m)
+        c->max_nuc_per_mat = std::max(c->max_nuc_per_mat, mat_off[m + 1] - mat_off[m]);
     c->h_mat_off.assign(mat_off, mat_off + n_mat + 1);
     c->h_nuc_id.assign(nuc_id, nuc_id + tot);
     c->graph_valid = false;
@@ -761,6 +800,7 @@ int prepare_run(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, cudaStre
     if (M64 < 1) M64 = 1;
     int32_t M = (int32_t)M64;
     if ((rc = ensure_bank(c, M))) return rc;
+    if ((rc = ensure_cum(c))) return rc;
     if ((rc = ensure_outcomes(c, total > 0 ? total : 1))) return rc;
     if ((rc = ensure_tallies(c, cells, s))) return rc;
     if (n_prob > c->probs_cap) {
@@ -984,6 +1024,7 @@ int gbmc_lookup_macro(gbmc_ctx* c, int32_t precision, const double* d_E, const i
     if (sort > 0 && !c->q_hist) {
         if ((rc = dalloc(c, &c->q_hist, kSortBuckets))) return rc;
         if ((rc = dalloc(c, &c->q_cursor, kSortBuckets))) return rc;
+        if ((rc = dalloc(c, &c->q_btot, kSortBuckets / 1024))) return rc;
         CK(cudaMemset(c->q_hist, 0, sizeof(uint32_t) * kSortBuckets));
     }
     Params P = make_params(c);
@@ -991,7 +1032,7 @@ int gbmc_lookup_macro(gbmc_ctx* c, int32_t precision, const double* d_E, const i
     LaunchCfg L = make_launch(c);
     cudaError_t e = launch_query_lookup(P, L, d_E, d_mat, n, d_sigma_t, d_sigma_a,
                                         sort > 0 ? c->q_perm : nullptr, c->q_keys, c->q_hist,
-                                        c->q_cursor, s);
+                                        c->q_cursor, c->q_btot, s);
     if (e != cudaSuccess) return fail(c, GBMC_ERR_CUDA, "lookup launch: %s", cudaGetErrorString(e));
     return GBMC_OK;
 }

@@ -65,7 +65,8 @@ struct Queues {
     int32_t* lqs;       // lookup queue in (material, energy) order
     uint32_t* keys;     // sort keys of lq
     uint32_t* hist;     // [kSortBuckets] bucket counts
-    uint32_t* cursor;   // [kSortBuckets] bucket write positions
+    uint32_t* cursor;   // [kSortBuckets] bucket write positions (block-local)
+    uint32_t* btot;     // [kSortBuckets / 1024] bucket-block totals
 };
 
 struct Outcomes {
@@ -98,6 +99,7 @@ struct Ctl {
 
 constexpr int kSortBuckets = 1 << 16;
 constexpr int kMaxSharedProblems = 64;
+static_assert(kSortBuckets == 64 * 1024, "the bucket scan runs 64 blocks of 1024");
 
 struct Params {
     Tables T;
@@ -115,7 +117,9 @@ struct Params {
     uint32_t sort_shift;     // energy-bits >> shift = bucket within a material
     uint32_t bpm_log2;       // log2 buckets per material
     int32_t use_cond;        // 1 inside the graph while-body, 0 for eager launches
-    uint64_t sort_ebase;     // bits of the smallest grid energy
+    uint64_t sort_ebase;
+    void* cum;               // running sums of N_i sigma_i per slot (NULL: recompute)
+    int64_t cum_stride;      // elements between nuclide k and k+1 of one slot     // bits of the smallest grid energy
     cudaGraphConditionalHandle cond;
 };
 
@@ -272,30 +276,102 @@ __device__ __forceinline__ float micro32(const Tables& T, int32_t i, double E) {
 }
 
 // Macroscopic sigma_t, sigma_a of material m: sum over its nuclides in the
-// listed order of N_i sigma_i, and of (N_i sigma_i) f_abs,i.
+// listed order of N_i sigma_i, and of (N_i sigma_i) f_abs,i.  With cum !=
+// NULL the running sum of N_i sigma_i after nuclide k is also stored at
+// cum[k * stride] (the collision picks its nuclide from these sums).
+//
+// The brackets of kIlp consecutive nuclides are searched in lock step (kIlp
+// independent chains of dependent loads in flight per thread); the terms are
+// then formed and added strictly in the listed order.
+constexpr int kIlp = 4;
+
+template <class G>
+__device__ __forceinline__ void brackets(const Tables& T, int32_t q, int32_t q1, G eb,
+                                         const G* g, int64_t* lo, int64_t* off) {
+    int64_t hi[kIlp];
+#pragma unroll
+    for (int u = 0; u < kIlp; ++u) {
+        lo[u] = 0;
+        hi[u] = 1;
+        off[u] = 0;
+        if (q + u < q1) {
+            int32_t i = __ldg(T.nuc_id + q + u);
+            off[u] = __ldg(T.grid_off + i);
+            hi[u] = __ldg(T.grid_off + i + 1) - off[u] - 1;
+        }
+    }
+    bool more = true;
+    while (more) {
+        more = false;
+#pragma unroll
+        for (int u = 0; u < kIlp; ++u) {
+            if (hi[u] - lo[u] > 1) {
+                int64_t mid = (lo[u] + hi[u]) >> 1;
+                if (__ldg(g + off[u] + mid) <= eb)
+                    lo[u] = mid;
+                else
+                    hi[u] = mid;
+                more = true;
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ void macro64(const Tables& T, int32_t m, double E, double& st,
-                                        double& sa) {
+                                        double& sa, double* cum = nullptr,
+                                        int64_t stride = 0) {
     double at = 0.0, aa = 0.0;
     int32_t q0 = __ldg(T.mat_off + m), q1 = __ldg(T.mat_off + m + 1);
-    for (int32_t q = q0; q < q1; ++q) {
-        int32_t i = __ldg(T.nuc_id + q);
-        double t = __ldg(T.density + q) * micro64(T, i, E);
-        at = at + t;
-        aa = aa + t * __ldg(T.f_abs + i);
+    const long long* g = reinterpret_cast<const long long*>(T.e64);
+    long long eb = __double_as_longlong(E);
+    for (int32_t q = q0; q < q1; q += kIlp) {
+        int64_t lo[kIlp], off[kIlp];
+        brackets<long long>(T, q, q1, eb, g, lo, off);
+#pragma unroll
+        for (int u = 0; u < kIlp; ++u) {
+            if (q + u < q1) {
+                int64_t k = off[u] + lo[u];
+                double e0 = __ldg(T.e64 + k), e1 = __ldg(T.e64 + k + 1);
+                double s0 = __ldg(T.s64 + k), s1 = __ldg(T.s64 + k + 1);
+                double f = (E - e0) / (e1 - e0);
+                double sig = s0 + f * (s1 - s0);
+                int32_t i = __ldg(T.nuc_id + q + u);
+                double t = __ldg(T.density + q + u) * sig;
+                at = at + t;
+                aa = aa + t * __ldg(T.f_abs + i);
+                if (cum) cum[(int64_t)(q + u - q0) * stride] = at;
+            }
+        }
     }
     st = at;
     sa = aa;
 }
 
 __device__ __forceinline__ void macro32(const Tables& T, int32_t m, double E, double& st,
-                                        double& sa) {
+                                        double& sa, float* cum = nullptr, int64_t stride = 0) {
     float at = 0.0f, aa = 0.0f;
     int32_t q0 = __ldg(T.mat_off + m), q1 = __ldg(T.mat_off + m + 1);
-    for (int32_t q = q0; q < q1; ++q) {
-        int32_t i = __ldg(T.nuc_id + q);
-        float t = __ldg(T.density32 + q) * micro32(T, i, E);
-        at = at + t;
-        aa = aa + t * __ldg(T.f_abs32 + i);
+    const int* g = reinterpret_cast<const int*>(T.e32);
+    int eb = __float_as_int(__double2float_rd(E));
+    float Ef = __double2float_rn(E);
+    for (int32_t q = q0; q < q1; q += kIlp) {
+        int64_t lo[kIlp], off[kIlp];
+        brackets<int>(T, q, q1, eb, g, lo, off);
+#pragma unroll
+        for (int u = 0; u < kIlp; ++u) {
+            if (q + u < q1) {
+                int64_t k = off[u] + lo[u];
+                float e0 = __ldg(T.e32 + k), e1 = __ldg(T.e32 + k + 1);
+                float s0 = __ldg(T.s32 + k), s1 = __ldg(T.s32 + k + 1);
+                float f = (Ef - e0) / (e1 - e0);
+                float sig = s0 + f * (s1 - s0);
+                int32_t i = __ldg(T.nuc_id + q + u);
+                float t = __ldg(T.density32 + q + u) * sig;
+                at = at + t;
+                aa = aa + t * __ldg(T.f_abs32 + i);
+                if (cum) cum[(int64_t)(q + u - q0) * stride] = at;
+            }
+        }
     }
     st = (double)at;
     sa = (double)aa;
@@ -329,6 +405,24 @@ __device__ __forceinline__ int32_t pick_nuclide(const Tables& T, int precision, 
         }
     }
     return last >= 0 ? last : __ldg(T.nuc_id + q0);
+}
+
+// The same choice from the running sums the lookup stored (cum[k * stride],
+// non-decreasing in k): binary search for the first k with target < cum_k.
+// Returns -1 when no sum exceeds the target (then pick_nuclide decides).
+template <class F>
+__device__ __forceinline__ int32_t pick_from_sums(const Tables& T, int32_t m, const F* cum,
+                                                  int64_t stride, double target) {
+    int32_t q0 = __ldg(T.mat_off + m), nq = __ldg(T.mat_off + m + 1) - q0;
+    int32_t lo = 0, hi = nq;
+    while (lo < hi) {
+        int32_t mid = (lo + hi) >> 1;
+        if (target < (double)cum[(int64_t)mid * stride])
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo < nq ? __ldg(T.nuc_id + q0 + lo) : -1;
 }
 
 // Tally energy bin: largest b in [0, n_bins-1] with edges[b] <= E.

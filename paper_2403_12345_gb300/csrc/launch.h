@@ -29,6 +29,6 @@ cudaError_t launch_iteration_timed(const Params& P, const LaunchCfg& L, cudaStre
 cudaError_t launch_query_lookup(const Params& P, const LaunchCfg& L, const double* E,
                                 const int32_t* mat, int64_t n, double* st, double* sa,
                                 int32_t* perm, uint32_t* keys, uint32_t* hist, uint32_t* cursor,
-                                cudaStream_t s);
+                                uint32_t* btot, cudaStream_t s);
 
 }  // namespace gbmc

@@ -263,17 +263,6 @@ __device__ __forceinline__ void warp_count(uint32_t* hist, uint32_t key, bool va
     if (valid && lane == __ffs(peers) - 1) atomicAdd(&hist[key], (uint32_t)__popc(peers));
 }
 
-__device__ __forceinline__ void warp_place(uint32_t* cursor, uint32_t key, bool valid,
-                                           int32_t* out, int32_t value) {
-    unsigned peers = __match_any_sync(kFull, valid ? key : 0xffffffffu);
-    int lane = threadIdx.x & 31;
-    int leader = __ffs(peers) - 1;
-    uint32_t base = 0;
-    if (valid && lane == leader) base = atomicAdd(&cursor[key], (uint32_t)__popc(peers));
-    base = __shfl_sync(kFull, base, leader);
-    if (valid) out[base + __popc(peers & lanemask_lt())] = value;
-}
-
 __global__ void __launch_bounds__(256) k_sort_keys(Params P) {
     const Ctl* c = P.ctl;
     if (!c->sorted) return;
@@ -290,22 +279,19 @@ __global__ void __launch_bounds__(256) k_sort_keys(Params P) {
     }
 }
 
-// Exclusive scan of the bucket counts into write cursors (one block of 1024
-// threads, 64 buckets each); clears the counts for the next sort.
-__device__ void scan_buckets(uint32_t* hist, uint32_t* cursor) {
+// Exclusive scan of the bucket counts, in kScanBlocks blocks of 1024
+// buckets: each block writes block-local offsets into cursor and its total
+// into btot, and clears its counts for the next sort; the scatter adds the
+// prefix of the block totals.
+constexpr int kScanBlocks = kSortBuckets / 1024;
+
+__device__ void scan_bucket_block(uint32_t* hist, uint32_t* cursor, uint32_t* btot) {
     __shared__ uint32_t warp_sums[32];
-    constexpr int kPer = kSortBuckets / 1024;
     int t = threadIdx.x;
-    uint32_t local[kPer];
-    uint32_t sum = 0;
-#pragma unroll 8
-    for (int k = 0; k < kPer; ++k) {
-        local[k] = hist[t * kPer + k];
-        sum += local[k];
-    }
-    // inclusive scan of per-thread sums across the block
+    int64_t e = (int64_t)blockIdx.x * 1024 + t;
+    uint32_t x = hist[e];
     int lane = t & 31, wid = t >> 5;
-    uint32_t v = sum;
+    uint32_t v = x;
     for (int o = 1; o < 32; o <<= 1) {
         uint32_t y = __shfl_up_sync(kFull, v, o);
         if (lane >= o) v += y;
@@ -313,37 +299,64 @@ __device__ void scan_buckets(uint32_t* hist, uint32_t* cursor) {
     if (lane == 31) warp_sums[wid] = v;
     __syncthreads();
     if (wid == 0) {
-        uint32_t s = warp_sums[lane];
+        uint32_t s2 = warp_sums[lane];
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(kFull, s, o);
-            if (lane >= o) s += y;
+            uint32_t y = __shfl_up_sync(kFull, s2, o);
+            if (lane >= o) s2 += y;
         }
-        warp_sums[lane] = s;
+        warp_sums[lane] = s2;
     }
     __syncthreads();
-    uint32_t base = v - sum + (wid ? warp_sums[wid - 1] : 0u);
-#pragma unroll 8
-    for (int k = 0; k < kPer; ++k) {
-        cursor[t * kPer + k] = base;
-        base += local[k];
-        hist[t * kPer + k] = 0u;
+    cursor[e] = v - x + (wid ? warp_sums[wid - 1] : 0u);
+    hist[e] = 0u;
+    if (t == 1023) btot[blockIdx.x] = warp_sums[31];
+}
+
+// Exclusive prefix of the kScanBlocks block totals, into shared memory.
+__device__ __forceinline__ void block_offsets(const uint32_t* btot, uint32_t* boff) {
+    if (threadIdx.x < 32) {
+        int lane = threadIdx.x;
+        uint32_t a = btot[2 * lane], b = btot[2 * lane + 1];
+        uint32_t v = a + b;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(kFull, v, o);
+            if (lane >= o) v += y;
+        }
+        uint32_t ex = v - a - b;
+        boff[2 * lane] = ex;
+        boff[2 * lane + 1] = ex + a;
     }
+    __syncthreads();
 }
 
 __global__ void __launch_bounds__(1024) k_sort_scan(Params P) {
     if (!P.ctl->sorted) return;
-    scan_buckets(P.Q.hist, P.Q.cursor);
+    scan_bucket_block(P.Q.hist, P.Q.cursor, P.Q.btot);
+}
+
+__device__ __forceinline__ void warp_place_off(uint32_t* cursor, const uint32_t* boff, uint32_t key,
+                                               bool valid, int32_t* out, int32_t value) {
+    unsigned peers = __match_any_sync(kFull, valid ? key : 0xffffffffu);
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (valid && lane == leader)
+        base = atomicAdd(&cursor[key], (uint32_t)__popc(peers)) + boff[key >> 10];
+    base = __shfl_sync(kFull, base, leader);
+    if (valid) out[base + __popc(peers & lanemask_lt())] = value;
 }
 
 __global__ void __launch_bounds__(256) k_sort_scatter(Params P) {
     const Ctl* c = P.ctl;
     if (!c->sorted) return;
+    __shared__ uint32_t boff[kScanBlocks];
+    block_offsets(P.Q.btot, boff);
     int32_t n = c->lookup_n;
     const int32_t* q = P.Q.lq[c->cur];
     GBMC_WARP_LOOP(idx, valid, n) {
         uint32_t key = valid ? P.Q.keys[idx] : 0u;
         int32_t slot = valid ? q[idx] : 0;
-        warp_place(P.Q.cursor, key, valid, P.Q.lqs, slot);
+        warp_place_off(P.Q.cursor, boff, key, valid, P.Q.lqs, slot);
     }
 }
 
@@ -365,9 +378,9 @@ __global__ void __launch_bounds__(256) k_lookup(Params P) {
             int32_t m = P.B.mat[slot];
             double st, sa;
             if (PREC == GBMC_FP64)
-                macro64(P.T, m, E, st, sa);
+                macro64(P.T, m, E, st, sa, P.cum ? (double*)P.cum + slot : nullptr, P.cum_stride);
             else
-                macro32(P.T, m, E, st, sa);
+                macro32(P.T, m, E, st, sa, P.cum ? (float*)P.cum + slot : nullptr, P.cum_stride);
             P.B.st[slot] = st;
             P.B.sa[slot] = sa;
             aq[idx] = slot;
@@ -599,7 +612,14 @@ __global__ void __launch_bounds__(256) k_collision(Params P) {
             Stream r;
             r.init(pr.seed, pr.key_hi, (uint64_t)(pr.first_id + (B.gidx[slot] - pr.start)), B.rj[slot]);
             double target = r.next() * B.st[slot];
-            int32_t nuc = pick_nuclide(P.T, PREC, mat, E, target);
+            int32_t nuc = -1;
+            if (P.cum) {
+                if (PREC == GBMC_FP64)
+                    nuc = pick_from_sums(P.T, mat, (const double*)P.cum + slot, P.cum_stride, target);
+                else
+                    nuc = pick_from_sums(P.T, mat, (const float*)P.cum + slot, P.cum_stride, target);
+            }
+            if (nuc < 0) nuc = pick_nuclide(P.T, PREC, mat, E, target);
             int32_t ncoll = B.ncoll[slot] + 1;
             double xa = r.next();
             if (xa < __ldg(P.T.f_abs + nuc)) {
@@ -651,15 +671,19 @@ __global__ void __launch_bounds__(256) k_query_keys(Params P, const double* E, c
     }
 }
 
-__global__ void __launch_bounds__(1024) k_query_scan(uint32_t* hist, uint32_t* cursor) {
-    scan_buckets(hist, cursor);
+__global__ void __launch_bounds__(1024) k_query_scan(uint32_t* hist, uint32_t* cursor,
+                                                     uint32_t* btot) {
+    scan_bucket_block(hist, cursor, btot);
 }
 
 __global__ void __launch_bounds__(256) k_query_scatter(int64_t n, const uint32_t* keys,
-                                                       uint32_t* cursor, int32_t* perm) {
+                                                       uint32_t* cursor, const uint32_t* btot,
+                                                       int32_t* perm) {
+    __shared__ uint32_t boff[kScanBlocks];
+    block_offsets(btot, boff);
     GBMC_WARP_LOOP(idx, valid, n) {
         uint32_t key = valid ? keys[idx] : 0u;
-        warp_place(cursor, key, valid, perm, (int32_t)idx);
+        warp_place_off(cursor, boff, key, valid, perm, (int32_t)idx);
     }
 }
 
@@ -694,7 +718,7 @@ cudaError_t launch_iteration(const Params& P, const LaunchCfg& L, cudaStream_t s
     k_source<<<L.grid, 256, 0, s>>>(P);
     if (P.sort) {
         k_sort_keys<<<L.grid, 256, 0, s>>>(P);
-        k_sort_scan<<<1, 1024, 0, s>>>(P);
+        k_sort_scan<<<kScanBlocks, 1024, 0, s>>>(P);
         k_sort_scatter<<<L.grid, 256, 0, s>>>(P);
     }
     if (P.precision == GBMC_FP64)
@@ -719,7 +743,7 @@ cudaError_t launch_iteration_timed(const Params& P, const LaunchCfg& L, cudaStre
     cudaEventRecord(ev[2], s);
     if (P.sort) k_sort_keys<<<L.grid, 256, 0, s>>>(P);
     cudaEventRecord(ev[3], s);
-    if (P.sort) k_sort_scan<<<1, 1024, 0, s>>>(P);
+    if (P.sort) k_sort_scan<<<kScanBlocks, 1024, 0, s>>>(P);
     cudaEventRecord(ev[4], s);
     if (P.sort) k_sort_scatter<<<L.grid, 256, 0, s>>>(P);
     cudaEventRecord(ev[5], s);
@@ -743,11 +767,11 @@ cudaError_t launch_iteration_timed(const Params& P, const LaunchCfg& L, cudaStre
 cudaError_t launch_query_lookup(const Params& P, const LaunchCfg& L, const double* E,
                                 const int32_t* mat, int64_t n, double* st, double* sa,
                                 int32_t* perm, uint32_t* keys, uint32_t* hist, uint32_t* cursor,
-                                cudaStream_t s) {
+                                uint32_t* btot, cudaStream_t s) {
     if (perm) {
         k_query_keys<<<L.grid, 256, 0, s>>>(P, E, mat, n, keys, hist);
-        k_query_scan<<<1, 1024, 0, s>>>(hist, cursor);
-        k_query_scatter<<<L.grid, 256, 0, s>>>(n, keys, cursor, perm);
+        k_query_scan<<<kScanBlocks, 1024, 0, s>>>(hist, cursor, btot);
+        k_query_scatter<<<L.grid, 256, 0, s>>>(n, keys, cursor, btot, perm);
     }
     if (P.precision == GBMC_FP64)
         k_query_lookup<GBMC_FP64><<<L.grid_lookup, 256, 0, s>>>(P.T, E, mat, n, perm, st, sa);
