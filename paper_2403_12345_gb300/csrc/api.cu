@@ -47,6 +47,8 @@ struct gbmc_ctx {
     int64_t* d_grid_off = nullptr;
     double *d_e64 = nullptr, *d_s64 = nullptr, *d_fabs = nullptr, *d_awr = nullptr;
     float *d_e32 = nullptr, *d_s32 = nullptr, *d_fabs32 = nullptr;
+    NucIndex *d_nx64 = nullptr, *d_nx32 = nullptr;   // coarse search indexes
+    uint32_t *d_idx64 = nullptr, *d_idx32 = nullptr;
     uint64_t table_hash = 0;   // identifies the tables both copies were built from
 
     // materials
@@ -310,6 +312,7 @@ int ensure_tallies(gbmc_ctx* c, const std::vector<int32_t>& cells, cudaStream_t 
 Tables make_tables(const gbmc_ctx* c) {
     Tables T{};
     T.grid_off = c->d_grid_off;
+    T.nx64 = c->d_nx64; T.idx64 = c->d_idx64; T.nx32 = c->d_nx32; T.idx32 = c->d_idx32;
     T.e64 = c->d_e64; T.s64 = c->d_s64; T.e32 = c->d_e32; T.s32 = c->d_s32;
     T.f_abs = c->d_fabs; T.f_abs32 = c->d_fabs32; T.awr = c->d_awr;
     T.mat_off = c->d_mat_off; T.nuc_id = c->d_nuc_id;
@@ -489,6 +492,50 @@ int n_cells_of(const gbmc_geometry& g) {
     return 1;
 }
 
+// Coarse search index of every nuclide grid (binary64 or binary32 bit
+// patterns): buckets (bits - bits(E_0)) >> shift, about 8 grid points per
+// bucket, idx[b] = number of grid points whose bucket is below b.
+int build_index(gbmc_ctx* c, int32_t n_nuc, const int64_t* grid_off, const double* energy,
+                int32_t precision, NucIndex** d_nx, uint32_t** d_idx) {
+    auto bits = [&](int64_t k) -> uint64_t {
+        if (precision == GBMC_FP64) {
+            uint64_t b;
+            memcpy(&b, &energy[k], 8);
+            return b;
+        }
+        float f = (float)energy[k];
+        uint32_t b;
+        memcpy(&b, &f, 4);
+        return b;
+    };
+    std::vector<NucIndex> nx(n_nuc);
+    std::vector<uint32_t> idx;
+    for (int32_t i = 0; i < n_nuc; ++i) {
+        int64_t off = grid_off[i], n = grid_off[i + 1] - off;
+        uint64_t base = bits(off), range = bits(off + n - 1) - base;
+        int32_t nb = 16;
+        while ((int64_t)nb * 8 < n && nb < (1 << 16)) nb <<= 1;
+        int32_t shift = 0;
+        while ((range >> shift) >= (uint64_t)nb) ++shift;
+        NucIndex d{};
+        d.off = off;
+        d.idx_off = (int64_t)idx.size();
+        d.base = base;
+        d.n = (int32_t)n;
+        d.shift = shift;
+        d.nb = nb;
+        nx[i] = d;
+        int64_t j = 0;
+        for (int64_t b = 0; b <= nb; ++b) {
+            while (j < n && ((bits(off + j) - base) >> shift) < (uint64_t)b) ++j;
+            idx.push_back((uint32_t)j);
+        }
+    }
+    int rc = upload(c, d_nx, nx.data(), nx.size());
+    if (rc) return rc;
+    return upload(c, d_idx, idx.data(), idx.size());
+}
+
 int read_ctl(gbmc_ctx* c) {
     if (!c->ran) return fail(c, GBMC_ERR_NOT_INITIALIZED, "no run has been launched");
     CK(cudaStreamSynchronize(c->last_stream));
@@ -576,6 +623,7 @@ int gbmc_destroy(gbmc_ctx* c) {
     dfree(c->Y.flux); dfree(c->Y.counts); dfree(c->Y.weights);
     dfree(c->d_grid_off); dfree(c->d_e64); dfree(c->d_s64); dfree(c->d_e32); dfree(c->d_s32);
     dfree(c->d_fabs); dfree(c->d_fabs32); dfree(c->d_awr);
+    dfree(c->d_nx64); dfree(c->d_nx32); dfree(c->d_idx64); dfree(c->d_idx32);
     dfree(c->d_mat_off); dfree(c->d_nuc_id); dfree(c->d_density); dfree(c->d_density32);
     dfree(c->d_edges); dfree(c->d_probs); dfree(c->d_ctl);
     if (c->d_cum) { cudaDeviceSynchronize(); cudaFree(c->d_cum); }
@@ -649,6 +697,7 @@ int gbmc_load_xs_tables(gbmc_ctx* c, int32_t n_nuc, const int64_t* grid_off, con
     if (!same) {
         // new tables: drop the copy of the other precision
         dfree(c->d_e64); dfree(c->d_s64); dfree(c->d_e32); dfree(c->d_s32);
+        dfree(c->d_nx64); dfree(c->d_nx32); dfree(c->d_idx64); dfree(c->d_idx32);
         c->has64 = c->has32 = false;
         // materials refer to nuclide ids of the old tables
         if (c->n_mat) {
@@ -667,6 +716,8 @@ int gbmc_load_xs_tables(gbmc_ctx* c, int32_t n_nuc, const int64_t* grid_off, con
     if (precision == GBMC_FP64) {
         if ((rc = upload(c, &c->d_e64, energy, (size_t)tot))) return rc;
         if ((rc = upload(c, &c->d_s64, sigma_t, (size_t)tot))) return rc;
+        if ((rc = build_index(c, n_nuc, grid_off, energy, GBMC_FP64, &c->d_nx64, &c->d_idx64)))
+            return rc;
         c->has64 = true;
     } else {
         std::vector<float> e(tot), s(tot);
@@ -676,6 +727,8 @@ int gbmc_load_xs_tables(gbmc_ctx* c, int32_t n_nuc, const int64_t* grid_off, con
         }
         if ((rc = upload(c, &c->d_e32, e.data(), (size_t)tot))) return rc;
         if ((rc = upload(c, &c->d_s32, s.data(), (size_t)tot))) return rc;
+        if ((rc = build_index(c, n_nuc, grid_off, energy, GBMC_FP32, &c->d_nx32, &c->d_idx32)))
+            return rc;
         c->has32 = true;
     }
     c->n_nuc = n_nuc;

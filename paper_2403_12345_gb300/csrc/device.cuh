@@ -12,6 +12,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 #include <math_constants.h>
+#include <cstring>
 
 #include "../../include/gbmc.h"
 
@@ -19,8 +20,24 @@ namespace gbmc {
 
 // ---------------------------------------------------------------- layouts
 
+// Per-nuclide search descriptor (48 bytes, three 16-byte loads).
+struct NucIndex {
+    int64_t off;        // first grid point of the nuclide in the pooled grid
+    int64_t idx_off;    // first entry of its coarse index
+    uint64_t base;      // bit pattern of its first grid energy
+    int32_t n;          // grid points
+    int32_t shift;      // bucket of E = (bits(E) - base) >> shift
+    int32_t nb;         // buckets; index entries idx[idx_off .. idx_off + nb]
+    int32_t pad[3];
+};
+static_assert(sizeof(NucIndex) == 48, "NucIndex is read as three int4");
+
 struct Tables {
     const int64_t* grid_off;   // [n_nuc+1]
+    const NucIndex* nx64;      // [n_nuc] descriptors over the binary64 grid
+    const uint32_t* idx64;     // coarse index of the binary64 grids
+    const NucIndex* nx32;      // [n_nuc] descriptors over the binary32 grid
+    const uint32_t* idx32;
     const double* e64;         // binary64 grid (eV)
     const double* s64;         // binary64 sigma_t (b)
     const float* e32;          // binary32 grid
@@ -219,12 +236,31 @@ __device__ __forceinline__ double ln_series(double x) {
 }
 
 // ---------------------------------------------------------------- lookup
-// Bracket search: largest j in [0, n-2] with grid[j] <= E.  Positive IEEE
-// values order like their bit patterns, so the comparisons run on the
-// integer pipe (binary64 compares would use the scarce FP64 units).
-__device__ __forceinline__ int64_t bracket64(const long long* __restrict__ g, int64_t n,
-                                             long long eb) {
-    int64_t lo = 0, hi = n - 1;
+// Bracket search: the largest j in [0, n-2] with grid[j] <= E.  Positive IEEE
+// values order like their bit patterns, so every comparison runs on the
+// integer pipe (binary64 compares would occupy the scarce FP64 units).
+//
+// Each nuclide carries a coarse index over its grid's bit patterns
+// (key(E) = (bits(E) - bits(E_0)) >> shift, i.e. piecewise-logarithmic
+// buckets; idx[b] = number of grid points whose key is below b).  A query in
+// bucket b has its bracket in [idx[b] - 1, idx[b+1] - 1]: one index load
+// replaces the top levels of the binary search, whose result is unchanged
+// because the bracket is unique (the "double indexing" of the CPU codes the
+// paper compares against, Sec. 3).
+
+template <class U>
+__device__ __forceinline__ void coarse_range(const NucIndex& d, const uint32_t* __restrict__ idx,
+                                             U eb, int64_t& lo, int64_t& hi) {
+    uint64_t b = (uint64_t)eb >= d.base ? ((uint64_t)eb - d.base) >> d.shift : 0ull;
+    if (b > (uint64_t)(d.nb - 1)) b = (uint64_t)(d.nb - 1);
+    int64_t s0 = __ldg(idx + d.idx_off + b), s1 = __ldg(idx + d.idx_off + b + 1);
+    lo = s0 > 0 ? s0 - 1 : 0;
+    if (lo > d.n - 2) lo = d.n - 2;
+    hi = s1 < d.n - 1 ? s1 : d.n - 1;
+}
+
+template <class U>
+__device__ __forceinline__ int64_t bracket_in(const U* __restrict__ g, int64_t lo, int64_t hi, U eb) {
     while (hi - lo > 1) {
         int64_t mid = (lo + hi) >> 1;
         if (__ldg(g + mid) <= eb)
@@ -235,27 +271,27 @@ __device__ __forceinline__ int64_t bracket64(const long long* __restrict__ g, in
     return lo;
 }
 
-__device__ __forceinline__ int64_t bracket32(const int* __restrict__ g, int64_t n, int eb) {
-    int64_t lo = 0, hi = n - 1;
-    while (hi - lo > 1) {
-        int64_t mid = (lo + hi) >> 1;
-        if (__ldg(g + mid) <= eb)
-            lo = mid;
-        else
-            hi = mid;
-    }
-    return lo;
+__device__ __forceinline__ NucIndex load_index(const NucIndex* p) {
+    NucIndex d;
+    const int4* q = reinterpret_cast<const int4*>(p);
+    int4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
+    memcpy(&d, &a, 16);
+    memcpy(reinterpret_cast<char*>(&d) + 16, &b, 16);
+    memcpy(reinterpret_cast<char*>(&d) + 32, &c, 16);
+    return d;
 }
 
 // Micro cross section of nuclide i at E: lin-lin interpolation between the
 // bracketing grid points, f = (E - E_j) / (E_j+1 - E_j), s_j + f (s_j+1 - s_j).
 __device__ __forceinline__ double micro64(const Tables& T, int32_t i, double E) {
-    int64_t lo = __ldg(T.grid_off + i);
-    int64_t n = __ldg(T.grid_off + i + 1) - lo;
-    const long long* g = reinterpret_cast<const long long*>(T.e64 + lo);
-    int64_t j = bracket64(g, n, __double_as_longlong(E));
-    double e0 = __ldg(T.e64 + lo + j), e1 = __ldg(T.e64 + lo + j + 1);
-    double s0 = __ldg(T.s64 + lo + j), s1 = __ldg(T.s64 + lo + j + 1);
+    NucIndex d = load_index(T.nx64 + i);
+    unsigned long long eb = (unsigned long long)__double_as_longlong(E);
+    int64_t lo, hi;
+    coarse_range(d, T.idx64, eb, lo, hi);
+    const unsigned long long* g = reinterpret_cast<const unsigned long long*>(T.e64 + d.off);
+    int64_t k = d.off + bracket_in(g, lo, hi, eb);
+    double e0 = __ldg(T.e64 + k), e1 = __ldg(T.e64 + k + 1);
+    double s0 = __ldg(T.s64 + k), s1 = __ldg(T.s64 + k + 1);
     double f = (E - e0) / (e1 - e0);
     return s0 + f * (s1 - s0);
 }
@@ -264,12 +300,14 @@ __device__ __forceinline__ double micro64(const Tables& T, int32_t i, double E) 
 // comparing against E rounded toward -inf (exact for binary32 grid values);
 // the interpolation runs in binary32 on E rounded to nearest.
 __device__ __forceinline__ float micro32(const Tables& T, int32_t i, double E) {
-    int64_t lo = __ldg(T.grid_off + i);
-    int64_t n = __ldg(T.grid_off + i + 1) - lo;
-    const int* g = reinterpret_cast<const int*>(T.e32 + lo);
-    int64_t j = bracket32(g, n, __float_as_int(__double2float_rd(E)));
-    float e0 = __ldg(T.e32 + lo + j), e1 = __ldg(T.e32 + lo + j + 1);
-    float s0 = __ldg(T.s32 + lo + j), s1 = __ldg(T.s32 + lo + j + 1);
+    NucIndex d = load_index(T.nx32 + i);
+    uint32_t eb = (uint32_t)__float_as_int(__double2float_rd(E));
+    int64_t lo, hi;
+    coarse_range(d, T.idx32, eb, lo, hi);
+    const uint32_t* g = reinterpret_cast<const uint32_t*>(T.e32 + d.off);
+    int64_t k = d.off + bracket_in(g, lo, hi, eb);
+    float e0 = __ldg(T.e32 + k), e1 = __ldg(T.e32 + k + 1);
+    float s0 = __ldg(T.s32 + k), s1 = __ldg(T.s32 + k + 1);
     float Ef = __double2float_rn(E);
     float f = (Ef - e0) / (e1 - e0);
     return s0 + f * (s1 - s0);
@@ -285,19 +323,20 @@ __device__ __forceinline__ float micro32(const Tables& T, int32_t i, double E) {
 // then formed and added strictly in the listed order.
 constexpr int kIlp = 4;
 
-template <class G>
-__device__ __forceinline__ void brackets(const Tables& T, int32_t q, int32_t q1, G eb,
-                                         const G* g, int64_t* lo, int64_t* off) {
-    int64_t hi[kIlp];
+template <class U>
+__device__ __forceinline__ void brackets(const Tables& T, const NucIndex* nx,
+                                         const uint32_t* idx, const U* g, int32_t q, int32_t q1,
+                                         U eb, int64_t* pos) {
+    int64_t lo[kIlp], hi[kIlp], off[kIlp];
 #pragma unroll
     for (int u = 0; u < kIlp; ++u) {
         lo[u] = 0;
         hi[u] = 1;
         off[u] = 0;
         if (q + u < q1) {
-            int32_t i = __ldg(T.nuc_id + q + u);
-            off[u] = __ldg(T.grid_off + i);
-            hi[u] = __ldg(T.grid_off + i + 1) - off[u] - 1;
+            NucIndex d = load_index(nx + __ldg(T.nuc_id + q + u));
+            off[u] = d.off;
+            coarse_range(d, idx, eb, lo[u], hi[u]);
         }
     }
     bool more = true;
@@ -315,6 +354,8 @@ __device__ __forceinline__ void brackets(const Tables& T, int32_t q, int32_t q1,
             }
         }
     }
+#pragma unroll
+    for (int u = 0; u < kIlp; ++u) pos[u] = off[u] + lo[u];
 }
 
 __device__ __forceinline__ void macro64(const Tables& T, int32_t m, double E, double& st,
@@ -322,15 +363,15 @@ __device__ __forceinline__ void macro64(const Tables& T, int32_t m, double E, do
                                         int64_t stride = 0) {
     double at = 0.0, aa = 0.0;
     int32_t q0 = __ldg(T.mat_off + m), q1 = __ldg(T.mat_off + m + 1);
-    const long long* g = reinterpret_cast<const long long*>(T.e64);
-    long long eb = __double_as_longlong(E);
+    const unsigned long long* g = reinterpret_cast<const unsigned long long*>(T.e64);
+    unsigned long long eb = (unsigned long long)__double_as_longlong(E);
     for (int32_t q = q0; q < q1; q += kIlp) {
-        int64_t lo[kIlp], off[kIlp];
-        brackets<long long>(T, q, q1, eb, g, lo, off);
+        int64_t pos[kIlp];
+        brackets(T, T.nx64, T.idx64, g, q, q1, eb, pos);
 #pragma unroll
         for (int u = 0; u < kIlp; ++u) {
             if (q + u < q1) {
-                int64_t k = off[u] + lo[u];
+                int64_t k = pos[u];
                 double e0 = __ldg(T.e64 + k), e1 = __ldg(T.e64 + k + 1);
                 double s0 = __ldg(T.s64 + k), s1 = __ldg(T.s64 + k + 1);
                 double f = (E - e0) / (e1 - e0);
@@ -351,16 +392,16 @@ __device__ __forceinline__ void macro32(const Tables& T, int32_t m, double E, do
                                         double& sa, float* cum = nullptr, int64_t stride = 0) {
     float at = 0.0f, aa = 0.0f;
     int32_t q0 = __ldg(T.mat_off + m), q1 = __ldg(T.mat_off + m + 1);
-    const int* g = reinterpret_cast<const int*>(T.e32);
-    int eb = __float_as_int(__double2float_rd(E));
+    const uint32_t* g = reinterpret_cast<const uint32_t*>(T.e32);
+    uint32_t eb = (uint32_t)__float_as_int(__double2float_rd(E));
     float Ef = __double2float_rn(E);
     for (int32_t q = q0; q < q1; q += kIlp) {
-        int64_t lo[kIlp], off[kIlp];
-        brackets<int>(T, q, q1, eb, g, lo, off);
+        int64_t pos[kIlp];
+        brackets(T, T.nx32, T.idx32, g, q, q1, eb, pos);
 #pragma unroll
         for (int u = 0; u < kIlp; ++u) {
             if (q + u < q1) {
-                int64_t k = off[u] + lo[u];
+                int64_t k = pos[u];
                 float e0 = __ldg(T.e32 + k), e1 = __ldg(T.e32 + k + 1);
                 float s0 = __ldg(T.s32 + k), s1 = __ldg(T.s32 + k + 1);
                 float f = (Ef - e0) / (e1 - e0);
@@ -427,8 +468,8 @@ __device__ __forceinline__ int32_t pick_from_sums(const Tables& T, int32_t m, co
 
 // Tally energy bin: largest b in [0, n_bins-1] with edges[b] <= E.
 __device__ __forceinline__ int32_t energy_bin(const Tables& T, double E) {
-    return (int32_t)bracket64(reinterpret_cast<const long long*>(T.edges), (int64_t)T.n_bins + 1,
-                              __double_as_longlong(E));
+    return (int32_t)bracket_in(reinterpret_cast<const unsigned long long*>(T.edges), (int64_t)0,
+                               (int64_t)T.n_bins, (unsigned long long)__double_as_longlong(E));
 }
 
 // ---------------------------------------------------------------- geometry
