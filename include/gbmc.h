@@ -96,7 +96,11 @@ typedef struct {
     int32_t max_iterations;  /* bound on event-loop iterations of one run
                                 (default 4 * GBMC_MAX_FLIGHTS); reaching it
                                 returns GBMC_ERR_TIMEOUT from the next read */
-    int32_t reserved[8];
+    int32_t sort_min;        /* sort only iterations with at least this many
+                                lookups (default 4096) */
+    int32_t warp_lookup_max; /* iterations with fewer lookups run one warp per
+                                particle instead of one thread (default 32768) */
+    int32_t reserved[6];
 } gbmc_options;
 
 /* One geometry (and its source).  Fields of other kinds are ignored. */
@@ -252,9 +256,15 @@ int gbmc_lookup_macro(gbmc_ctx *ctx, int32_t precision, const double *d_E,
  * (no graph) with a CUDA event around every kernel on `stream`, and add the
  * per-kernel device times to *out (zero it first).  Synchronizes once per
  * iteration, so the run is slower end to end; outcomes and tallies are the
- * same as gbmc_run_problems'. */
+ * same as gbmc_run_problems'.
+ * Optional per-iteration trace (trace_cap = 0 or NULL pointers skip it):
+ *   trace_ms     [trace_cap * GBMC_NKERNELS] device ms of each kernel,
+ *   trace_queues [trace_cap * 4] lookups, advances, surface and collision
+ *                events of each iteration,
+ *   *trace_len   iterations recorded (at most trace_cap). */
 int gbmc_profile_problems(gbmc_ctx *ctx, int32_t n_prob, const gbmc_problem *probs,
-                          void *stream, gbmc_kernel_times *out);
+                          void *stream, gbmc_kernel_times *out, int32_t trace_cap,
+                          double *trace_ms, int32_t *trace_queues, int32_t *trace_len);
 
 /* Device timing of the last run's event loop (ms, CUDA events on the run's
  * stream around the graph launch); synchronizes. */

@@ -15,6 +15,10 @@
 
 using namespace gbmc;
 
+static_assert(sizeof(gbmc_options) == 72, "gbmc_options layout is part of the ABI");
+static_assert(sizeof(gbmc_geometry) == 104, "gbmc_geometry layout is part of the ABI");
+static_assert(sizeof(gbmc_problem) == 136, "gbmc_problem layout is part of the ABI");
+
 namespace {
 
 thread_local std::string g_create_error;
@@ -163,6 +167,9 @@ void fill_defaults(gbmc_options* o) {
     if (o->block_event <= 0) o->block_event = 256;
     if (o->blocks_per_sm <= 0) o->blocks_per_sm = 8;
     if (o->max_iterations <= 0) o->max_iterations = 4 * GBMC_MAX_FLIGHTS;
+    if (o->sort_min <= 0) o->sort_min = 4096;
+    if (o->warp_lookup_max == 0) o->warp_lookup_max = 32768;
+    if (o->warp_lookup_max < 0) o->warp_lookup_max = 0;   // never
 }
 
 int check_options(gbmc_ctx* c, const gbmc_options* o) {
@@ -192,11 +199,7 @@ uint64_t fnv1a(const void* p, size_t n, uint64_t h) {
 }
 
 void free_bank(gbmc_ctx* c) {
-    Bank& B = c->B;
-    dfree(B.x); dfree(B.y); dfree(B.z); dfree(B.u); dfree(B.v); dfree(B.w);
-    dfree(B.E); dfree(B.wgt); dfree(B.st); dfree(B.sa);
-    dfree(B.ci); dfree(B.cj); dfree(B.mat); dfree(B.ncoll); dfree(B.nflt); dfree(B.prob);
-    dfree(B.rj); dfree(B.gidx); dfree(B.inside); dfree(B.surf);
+    dfree(c->B.p);
     Queues& Q = c->Q;
     dfree(Q.lq[0]); dfree(Q.lq[1]); dfree(Q.aq[0]); dfree(Q.aq[1]);
     dfree(Q.sq); dfree(Q.cq); dfree(Q.fq); dfree(Q.lqs); dfree(Q.keys);
@@ -209,15 +212,7 @@ int ensure_bank(gbmc_ctx* c, int32_t M) {
     free_bank(c);
     c->graph_valid = false;
     size_t n = (size_t)M;
-    Bank& B = c->B;
-    int rc = 0;
-    rc |= dalloc(c, &B.x, n); rc |= dalloc(c, &B.y, n); rc |= dalloc(c, &B.z, n);
-    rc |= dalloc(c, &B.u, n); rc |= dalloc(c, &B.v, n); rc |= dalloc(c, &B.w, n);
-    rc |= dalloc(c, &B.E, n); rc |= dalloc(c, &B.wgt, n); rc |= dalloc(c, &B.st, n);
-    rc |= dalloc(c, &B.sa, n); rc |= dalloc(c, &B.ci, n); rc |= dalloc(c, &B.cj, n);
-    rc |= dalloc(c, &B.mat, n); rc |= dalloc(c, &B.ncoll, n); rc |= dalloc(c, &B.nflt, n);
-    rc |= dalloc(c, &B.prob, n); rc |= dalloc(c, &B.rj, n); rc |= dalloc(c, &B.gidx, n);
-    rc |= dalloc(c, &B.inside, n); rc |= dalloc(c, &B.surf, n);
+    int rc = dalloc(c, &c->B.p, n);
     Queues& Q = c->Q;
     rc |= dalloc(c, &Q.lq[0], n); rc |= dalloc(c, &Q.lq[1], n);
     rc |= dalloc(c, &Q.aq[0], n); rc |= dalloc(c, &Q.aq[1], n);
@@ -355,11 +350,12 @@ Params make_params(gbmc_ctx* c) {
     P.capacity = c->capacity;
     P.precision = c->opt.precision;
     P.sort = c->opt.sort > 0 ? 1 : 0;
-    P.sort_min = 4096;
+    P.sort_min = c->opt.sort_min;
+    P.warp_lookup_max = c->opt.warp_lookup_max;
     P.max_iter = c->opt.max_iterations;
     sort_params(c, P);
     P.cum = c->d_cum;
-    P.cum_stride = c->d_cum ? c->capacity : 0;
+    P.cum_stride = c->d_cum ? c->max_nuc_per_mat : 0;
     return P;
 }
 
@@ -929,8 +925,11 @@ int gbmc_run_problems(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, vo
 }
 
 int gbmc_profile_problems(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, void* stream,
-                          gbmc_kernel_times* out) {
+                          gbmc_kernel_times* out, int32_t trace_cap, double* trace_ms,
+                          int32_t* trace_queues, int32_t* trace_len) {
     if (!c || !out) return GBMC_ERR_INVALID_ARG;
+    if (trace_cap < 0) return fail(c, GBMC_ERR_INVALID_ARG, "trace_cap must be >= 0");
+    if (trace_len) *trace_len = 0;
     cudaStream_t s = (cudaStream_t)stream;
     Params P;
     LaunchCfg L;
@@ -955,7 +954,17 @@ int gbmc_profile_problems(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs
             bool launched = (k < 2 || k > 4 || P.sort);
             out->ms[k] += ms;
             out->launches[k] += launched ? 1 : 0;
+            if (trace_ms && it < trace_cap) trace_ms[(int64_t)it * kTimedKernels + k] = ms;
         }
+        if (trace_queues && it < trace_cap) {
+            const Ctl& k = *c->h_ctl;
+            int32_t* tq = trace_queues + (int64_t)it * 4;
+            tq[0] = k.lookup_n;
+            tq[1] = k.n_aq[k.cur];
+            tq[2] = k.n_sq;
+            tq[3] = k.n_cq;
+        }
+        if (trace_len && it < trace_cap) *trace_len = it + 1;
         if (c->h_ctl->done || ++it > c->opt.max_iterations + 1) break;
     }
     for (int k = 0; k <= kTimedKernels; ++k) cudaEventDestroy(ev[k]);

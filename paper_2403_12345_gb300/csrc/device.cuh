@@ -62,14 +62,34 @@ struct DevProblem {
     int32_t n_cells, pad;
 };
 
-// Particle bank, structure of arrays, capacity M slots.
+// One slot of the particle bank: a 128-byte, 128-byte-aligned record (array
+// of structures).  Queues visit slots in data-dependent order, so each
+// particle costs whole cache lines either way; one record per line, with the
+// fields grouped by 32-byte sector after the events that read them, keeps
+// each event to the sectors it needs (the lookup touches sector 0 only).
+struct alignas(128) Particle {
+    // sector 0: lookup reads E, mat; writes st, sa
+    double st, sa;       // macroscopic sigma_t, sigma_a at (E, mat)
+    double E;
+    int32_t mat, prob;   // material, problem slot
+    // sector 1
+    double x, y, z, wgt;
+    // sector 2
+    double u, v, w;
+    int64_t gidx;        // index of the particle in the run
+    // sector 3
+    int32_t ci, cj;      // lattice cell (slab: layer in ci)
+    int32_t ncoll, nflt; // collisions, flights so far
+    uint32_t rj;         // draws consumed from the particle's stream
+    uint8_t inside;      // inside the pin cylinder (lattice)
+    uint8_t surf;        // surface reached by the last flight
+    uint8_t pad8[2];
+    int32_t pad[2];
+};
+static_assert(sizeof(Particle) == 128, "one particle per 128-byte line");
+
 struct Bank {
-    double *x, *y, *z, *u, *v, *w, *E, *wgt, *st, *sa;
-    int32_t *ci, *cj, *mat, *ncoll, *nflt, *prob;
-    uint32_t* rj;       // draws consumed from the particle's stream
-    int64_t* gidx;      // index of the particle in the run
-    uint8_t* inside;    // inside the pin cylinder (lattice)
-    uint8_t* surf;      // surface reached by the last flight
+    Particle* p;         // [capacity]
 };
 
 // Event queues (slot indices) and sort scratch.
@@ -106,6 +126,7 @@ struct Ctl {
     int32_t cur;                 // queues[cur] are consumed this iteration
     int32_t lookup_n, aq_base;   // lookups of this iteration, where they append in aq[cur]
     int32_t n_birth, free_base, lq_base, sorted;
+    int32_t warp_lookup, pad1;   // this iteration's lookups run one warp per particle
     int64_t next_base;           // run index of the first particle born this iteration
     int64_t next, total;         // next unborn run index, particles in the run
     int32_t M;                   // in-flight cap of this run (<= capacity)
@@ -130,13 +151,14 @@ struct Params {
     int32_t precision;       // GBMC_FP64 / GBMC_FP32
     int32_t sort;            // sort the lookup queue
     int32_t sort_min;        // sort only when at least this many lookups
+    int32_t warp_lookup_max; // below this many lookups: one warp per particle
     int32_t max_iter;
     uint32_t sort_shift;     // energy-bits >> shift = bucket within a material
     uint32_t bpm_log2;       // log2 buckets per material
     int32_t use_cond;        // 1 inside the graph while-body, 0 for eager launches
     uint64_t sort_ebase;
-    void* cum;               // running sums of N_i sigma_i per slot (NULL: recompute)
-    int64_t cum_stride;      // elements between nuclide k and k+1 of one slot     // bits of the smallest grid energy
+    void* cum;               // running sums of N_i sigma_i, slot-major (NULL: recompute)
+    int64_t cum_stride;      // elements per slot (the most nuclides of any material)     // bits of the smallest grid energy
     cudaGraphConditionalHandle cond;
 };
 
@@ -416,6 +438,58 @@ __device__ __forceinline__ void macro32(const Tables& T, int32_t m, double E, do
     }
     st = (double)at;
     sa = (double)aa;
+}
+
+// The same macroscopic sums for ONE particle computed by a whole warp (all
+// 32 lanes call with the same m and E): lane l forms the terms of nuclides
+// l, l+32, ... in parallel, then every lane folds the terms in the listed
+// order with shuffles, so the sums are bit-identical to macro64/macro32.
+// Used when the lookup queue is too short to keep the GPU busy with one
+// particle per thread (the per-particle nuclide loop is then a long serial
+// latency chain).
+template <int PREC>
+__device__ __forceinline__ void macro_warp(const Tables& T, int32_t m, double E, double& st,
+                                           double& sa, void* cum, int64_t stride) {
+    const unsigned full = 0xffffffffu;
+    int lane = threadIdx.x & 31;
+    int32_t q0 = __ldg(T.mat_off + m), q1 = __ldg(T.mat_off + m + 1);
+    if (PREC == GBMC_FP64) {
+        double at = 0.0, aa = 0.0;
+        for (int32_t c = q0; c < q1; c += 32) {
+            double t = 0.0, p = 0.0;
+            if (c + lane < q1) {
+                int32_t i = __ldg(T.nuc_id + c + lane);
+                t = __ldg(T.density + c + lane) * micro64(T, i, E);
+                p = t * __ldg(T.f_abs + i);
+            }
+            int32_t kmax = q1 - c < 32 ? q1 - c : 32;
+            for (int k = 0; k < kmax; ++k) {
+                at = at + __shfl_sync(full, t, k);
+                aa = aa + __shfl_sync(full, p, k);
+                if (cum && lane == k) ((double*)cum)[(int64_t)(c + k - q0) * stride] = at;
+            }
+        }
+        st = at;
+        sa = aa;
+    } else {
+        float at = 0.0f, aa = 0.0f;
+        for (int32_t c = q0; c < q1; c += 32) {
+            float t = 0.0f, p = 0.0f;
+            if (c + lane < q1) {
+                int32_t i = __ldg(T.nuc_id + c + lane);
+                t = __ldg(T.density32 + c + lane) * micro32(T, i, E);
+                p = t * __ldg(T.f_abs32 + i);
+            }
+            int32_t kmax = q1 - c < 32 ? q1 - c : 32;
+            for (int k = 0; k < kmax; ++k) {
+                at = at + __shfl_sync(full, t, k);
+                aa = aa + __shfl_sync(full, p, k);
+                if (cum && lane == k) ((float*)cum)[(int64_t)(c + k - q0) * stride] = at;
+            }
+        }
+        st = (double)at;
+        sa = (double)aa;
+    }
 }
 
 // Collision nuclide: first nuclide (listed order) whose running sum of

@@ -153,6 +153,7 @@ __global__ void k_plan(Params P) {
     c->aq_base = c->n_aq[cur];
     c->n_aq[cur] += c->lookup_n;
     c->sorted = (P.sort && c->lookup_n >= P.sort_min) ? 1 : 0;
+    c->warp_lookup = c->lookup_n < P.warp_lookup_max ? 1 : 0;
     c->st_lookups += (unsigned long long)c->lookup_n;
     c->st_flights += (unsigned long long)c->n_aq[cur];
     c->done = done;
@@ -228,13 +229,18 @@ __global__ void __launch_bounds__(256) k_source(Params P) {
             } else {
                 mat = g.mat;
             }
-            Bank& B = const_cast<Bank&>(P.B);
-            B.x[slot] = x; B.y[slot] = y; B.z[slot] = z;
-            B.u[slot] = u; B.v[slot] = v; B.w[slot] = w;
-            B.E[slot] = g.E0; B.wgt[slot] = 1.0;
-            B.ci[slot] = ci; B.cj[slot] = cj; B.inside[slot] = inside; B.mat[slot] = mat;
-            B.ncoll[slot] = 0; B.nflt[slot] = 0; B.rj[slot] = r.j;
-            B.gidx[slot] = gi; B.prob[slot] = prob;
+            Particle rec;
+            memset(&rec, 0, sizeof rec);
+            rec.E = g.E0;
+            rec.mat = mat;
+            rec.prob = prob;
+            rec.x = x; rec.y = y; rec.z = z; rec.wgt = 1.0;
+            rec.u = u; rec.v = v; rec.w = w;
+            rec.gidx = gi;
+            rec.ci = ci; rec.cj = cj;
+            rec.rj = r.j;
+            rec.inside = inside;
+            P.B.p[slot] = rec;
             P.Q.lq[cur][lb + idx] = slot;
         }
         sc.add(P.Y, valid, prob, GBMC_S_HISTORY, 1.0);
@@ -272,7 +278,7 @@ __global__ void __launch_bounds__(256) k_sort_keys(Params P) {
         uint32_t key = 0;
         if (valid) {
             int32_t slot = q[idx];
-            key = sort_key(P, P.B.E[slot], P.B.mat[slot]);
+            key = sort_key(P, P.B.p[slot].E, P.B.p[slot].mat);
             P.Q.keys[idx] = key;
         }
         warp_count(P.Q.hist, key, valid);
@@ -371,20 +377,45 @@ __global__ void __launch_bounds__(256) k_lookup(Params P) {
     const int32_t* q = c->sorted ? P.Q.lqs : P.Q.lq[cur];
     int32_t* aq = P.Q.aq[cur] + c->aq_base;
     unsigned long long micro = 0;
-    GBMC_WARP_LOOP(idx, valid, n) {
-        if (valid) {
+    if (c->warp_lookup) {
+        // one particle per warp
+        int lane = threadIdx.x & 31;
+        int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+        for (int64_t idx = w0; idx < n; idx += nw) {
             int32_t slot = q[idx];
-            double E = P.B.E[slot];
-            int32_t m = P.B.mat[slot];
+            double E = P.B.p[slot].E;
+            int32_t m = P.B.p[slot].mat;
             double st, sa;
-            if (PREC == GBMC_FP64)
-                macro64(P.T, m, E, st, sa, P.cum ? (double*)P.cum + slot : nullptr, P.cum_stride);
-            else
-                macro32(P.T, m, E, st, sa, P.cum ? (float*)P.cum + slot : nullptr, P.cum_stride);
-            P.B.st[slot] = st;
-            P.B.sa[slot] = sa;
-            aq[idx] = slot;
-            micro += (unsigned long long)(__ldg(P.T.mat_off + m + 1) - __ldg(P.T.mat_off + m));
+            void* cum = P.cum ? (PREC == GBMC_FP64 ? (void*)((double*)P.cum + slot * P.cum_stride)
+                                                   : (void*)((float*)P.cum + slot * P.cum_stride))
+                              : nullptr;
+            macro_warp<PREC>(P.T, m, E, st, sa, cum, 1);
+            if (lane == 0) {
+                P.B.p[slot].st = st;
+                P.B.p[slot].sa = sa;
+                aq[idx] = slot;
+                micro += (unsigned long long)(__ldg(P.T.mat_off + m + 1) - __ldg(P.T.mat_off + m));
+            }
+        }
+    } else {
+        GBMC_WARP_LOOP(idx, valid, n) {
+            if (valid) {
+                int32_t slot = q[idx];
+                double E = P.B.p[slot].E;
+                int32_t m = P.B.p[slot].mat;
+                double st, sa;
+                if (PREC == GBMC_FP64)
+                    macro64(P.T, m, E, st, sa,
+                            P.cum ? (double*)P.cum + slot * P.cum_stride : nullptr, 1);
+                else
+                    macro32(P.T, m, E, st, sa,
+                            P.cum ? (float*)P.cum + slot * P.cum_stride : nullptr, 1);
+                P.B.p[slot].st = st;
+                P.B.p[slot].sa = sa;
+                aq[idx] = slot;
+                micro += (unsigned long long)(__ldg(P.T.mat_off + m + 1) - __ldg(P.T.mat_off + m));
+            }
         }
     }
     for (int o = 16; o > 0; o >>= 1) micro += __shfl_xor_sync(kFull, micro, o);
@@ -396,7 +427,7 @@ __global__ void __launch_bounds__(256) k_lookup(Params P) {
 __device__ __forceinline__ void record_death(const Params& P, int32_t slot, int status, int32_t ncoll,
                                              int32_t nflt, uint32_t rj, double E, double x,
                                              double y, double z) {
-    int64_t gi = P.B.gidx[slot];
+    int64_t gi = P.B.p[slot].gidx;
     P.O.ncoll[gi] = ncoll;
     P.O.status[gi] = (int8_t)status;
     P.O.nflt[gi] = nflt;
@@ -426,17 +457,17 @@ __global__ void __launch_bounds__(256) k_advance(Params P) {
         double wgt = 0.0;
         if (valid) {
             slot = q[idx];
-            const Bank& B = P.B;
-            prob = B.prob[slot];
+            Particle& pt = P.B.p[slot];
+            prob = pt.prob;
             const DevProblem& pr = P.probs[prob];
             const gbmc_geometry& g = pr.g;
-            double x = B.x[slot], y = B.y[slot], z = B.z[slot];
-            double u = B.u[slot], v = B.v[slot], w = B.w[slot];
-            double E = B.E[slot], st = B.st[slot];
-            wgt = B.wgt[slot];
-            int32_t ci = B.ci[slot], cj = B.cj[slot];
+            double x = pt.x, y = pt.y, z = pt.z;
+            double u = pt.u, v = pt.v, w = pt.w;
+            double E = pt.E, st = pt.st;
+            wgt = pt.wgt;
+            int32_t ci = pt.ci, cj = pt.cj;
             Stream r;
-            r.init(pr.seed, pr.key_hi, (uint64_t)(pr.first_id + (B.gidx[slot] - pr.start)), B.rj[slot]);
+            r.init(pr.seed, pr.key_hi, (uint64_t)(pr.first_id + (pt.gidx - pr.start)), pt.rj);
             double xi = r.next();
             double dcol = (0.0 - ln_series(xi)) / st;
             double dbnd = CUDART_INF;
@@ -446,7 +477,7 @@ __global__ void __launch_bounds__(256) k_advance(Params P) {
                 double p = g.pitch;
                 double cx = ((double)ci + 0.5) * p;
                 double cy = ((double)cj + 0.5) * p;
-                double dc = dist_cylinder(x - cx, y - cy, u, v, g.radius, B.inside[slot] != 0);
+                double dc = dist_cylinder(x - cx, y - cy, u, v, g.radius, pt.inside != 0);
                 double dx = dist_planes(x, u, (double)ci * p, (double)(ci + 1) * p);
                 double dy = dist_planes(y, v, (double)cj * p, (double)(cj + 1) * p);
                 double dz = dist_planes(z, w, 0.0, g.height);
@@ -475,11 +506,10 @@ __global__ void __launch_bounds__(256) k_advance(Params P) {
             z = z + d * w;
             int32_t bin = energy_bin(P.T, E);
             atomicAdd(&P.Y.flux[pr.flux_off + (int64_t)cell * P.T.n_bins + bin], wgt * d);
-            Bank& Bw = const_cast<Bank&>(P.B);
-            Bw.x[slot] = x; Bw.y[slot] = y; Bw.z[slot] = z;
-            Bw.rj[slot] = r.j;
-            Bw.nflt[slot] = B.nflt[slot] + 1;
-            Bw.surf[slot] = surf;
+            pt.x = x; pt.y = y; pt.z = z;
+            pt.rj = r.j;
+            pt.nflt = pt.nflt + 1;
+            pt.surf = surf;
         }
         sc.add(P.Y, valid, prob, GBMC_S_FLIGHT, wgt);
         warp_append(P.Q.cq, &c->n_cq, slot, valid && collide);
@@ -504,14 +534,14 @@ __global__ void __launch_bounds__(256) k_surface(Params P) {
         double wgt = 0.0;
         if (valid) {
             slot = P.Q.sq[idx];
-            Bank& B = const_cast<Bank&>(P.B);
-            prob = B.prob[slot];
+            Particle& pt = P.B.p[slot];
+            prob = pt.prob;
             const gbmc_geometry& g = P.probs[prob].g;
-            wgt = B.wgt[slot];
-            int32_t ci = B.ci[slot], cj = B.cj[slot], mat = B.mat[slot];
-            double x = B.x[slot], y = B.y[slot], z = B.z[slot];
-            double u = B.u[slot], v = B.v[slot], w = B.w[slot];
-            uint8_t surf = B.surf[slot];
+            wgt = pt.wgt;
+            int32_t ci = pt.ci, cj = pt.cj, mat = pt.mat;
+            double x = pt.x, y = pt.y, z = pt.z;
+            double u = pt.u, v = pt.v, w = pt.w;
+            uint8_t surf = pt.surf;
             if (g.kind == GBMC_GEOM_SLAB) {
                 double h = g.layer_dx;
                 if (u > 0.0) {
@@ -529,8 +559,8 @@ __global__ void __launch_bounds__(256) k_surface(Params P) {
                     mat = m;
                 }
             } else if (surf == kSurfCyl) {
-                uint8_t in = B.inside[slot] ? 0 : 1;
-                B.inside[slot] = in;
+                uint8_t in = pt.inside ? 0 : 1;
+                pt.inside = in;
                 int32_t m = in ? g.mat_pin : g.mat_mod;
                 relook = m != mat;
                 mat = m;
@@ -565,13 +595,12 @@ __global__ void __launch_bounds__(256) k_surface(Params P) {
                 if (g.bc_z == GBMC_BC_REFLECT) w = -w;
                 else status = GBMC_STATUS_LEAKED;
             }
-            int32_t nflt = B.nflt[slot];
+            int32_t nflt = pt.nflt;
             if (!status && nflt >= GBMC_MAX_FLIGHTS) status = GBMC_STATUS_LIMIT;
-            B.x[slot] = x; B.y[slot] = y; B.z[slot] = z;
-            B.u[slot] = u; B.v[slot] = v; B.w[slot] = w;
-            B.ci[slot] = ci; B.cj[slot] = cj; B.mat[slot] = mat;
-            if (status)
-                record_death(P, slot, status, B.ncoll[slot], nflt, B.rj[slot], B.E[slot], x, y, z);
+            pt.x = x; pt.y = y; pt.z = z;
+            pt.u = u; pt.v = v; pt.w = w;
+            pt.ci = ci; pt.cj = cj; pt.mat = mat;
+            if (status) record_death(P, slot, status, pt.ncoll, nflt, pt.rj, pt.E, x, y, z);
         }
         bool dead = valid && status != 0;
         sc.add(P.Y, dead && (status == GBMC_STATUS_LEAKED || status == GBMC_STATUS_LEAKED_FAR),
@@ -590,7 +619,7 @@ __global__ void __launch_bounds__(256) k_surface(Params P) {
 // frame, target at rest), apply the energy cutoff.
 
 template <int PREC>
-__global__ void __launch_bounds__(256) k_collision(Params P) {
+__global__ void __launch_bounds__(256, 3) k_collision(Params P) {
     Ctl* c = P.ctl;
     int32_t n = c->n_cq;
     if (n == 0) return;
@@ -603,24 +632,26 @@ __global__ void __launch_bounds__(256) k_collision(Params P) {
         double wgt = 0.0;
         if (valid) {
             slot = P.Q.cq[idx];
-            Bank& B = const_cast<Bank&>(P.B);
-            prob = B.prob[slot];
+            Particle& pt = P.B.p[slot];
+            prob = pt.prob;
             const DevProblem& pr = P.probs[prob];
-            wgt = B.wgt[slot];
-            double E = B.E[slot];
-            int32_t mat = B.mat[slot];
+            wgt = pt.wgt;
+            double E = pt.E;
+            int32_t mat = pt.mat;
             Stream r;
-            r.init(pr.seed, pr.key_hi, (uint64_t)(pr.first_id + (B.gidx[slot] - pr.start)), B.rj[slot]);
-            double target = r.next() * B.st[slot];
+            r.init(pr.seed, pr.key_hi, (uint64_t)(pr.first_id + (pt.gidx - pr.start)), pt.rj);
+            double target = r.next() * pt.st;
             int32_t nuc = -1;
             if (P.cum) {
                 if (PREC == GBMC_FP64)
-                    nuc = pick_from_sums(P.T, mat, (const double*)P.cum + slot, P.cum_stride, target);
+                    nuc = pick_from_sums(P.T, mat, (const double*)P.cum + slot * P.cum_stride, 1,
+                                         target);
                 else
-                    nuc = pick_from_sums(P.T, mat, (const float*)P.cum + slot, P.cum_stride, target);
+                    nuc = pick_from_sums(P.T, mat, (const float*)P.cum + slot * P.cum_stride, 1,
+                                         target);
             }
             if (nuc < 0) nuc = pick_nuclide(P.T, PREC, mat, E, target);
-            int32_t ncoll = B.ncoll[slot] + 1;
+            int32_t ncoll = pt.ncoll + 1;
             double xa = r.next();
             if (xa < __ldg(P.T.f_abs + nuc)) {
                 status = GBMC_STATUS_ABSORBED;
@@ -632,19 +663,19 @@ __global__ void __launch_bounds__(256) k_collision(Params P) {
                 double sphi = ((2.0 * a) * b) / s;
                 double E1, mul;
                 elastic(E, __ldg(P.T.awr + nuc), mu, E1, mul);
-                double u = B.u[slot], v = B.v[slot], w = B.w[slot];
+                double u = pt.u, v = pt.v, w = pt.w;
                 rotate(u, v, w, mul, cphi, sphi);
-                B.u[slot] = u; B.v[slot] = v; B.w[slot] = w;
+                pt.u = u; pt.v = v; pt.w = w;
                 E = E1;
-                B.E[slot] = E;
+                pt.E = E;
                 if (E < pr.g.E_cut) status = GBMC_STATUS_CUTOFF;
             }
-            int32_t nflt = B.nflt[slot];
+            int32_t nflt = pt.nflt;
             if (!status && nflt >= GBMC_MAX_FLIGHTS) status = GBMC_STATUS_LIMIT;
-            B.ncoll[slot] = ncoll;
-            B.rj[slot] = r.j;
+            pt.ncoll = ncoll;
+            pt.rj = r.j;
             if (status)
-                record_death(P, slot, status, ncoll, nflt, r.j, E, B.x[slot], B.y[slot], B.z[slot]);
+                record_death(P, slot, status, ncoll, nflt, r.j, E, pt.x, pt.y, pt.z);
         }
         bool dead = valid && status != 0;
         sc.add(P.Y, valid, prob, GBMC_S_COLLISION, wgt);

@@ -47,7 +47,8 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_in_flight", C.c_int64), ("sort", C.c_int32),
                 ("block_lookup", C.c_int32), ("block_event", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("max_iterations", C.c_int32),
-                ("reserved", C.c_int32 * 8)]
+                ("sort_min", C.c_int32), ("warp_lookup_max", C.c_int32),
+                ("reserved", C.c_int32 * 6)]
 
 
 class Geometry(C.Structure):
@@ -111,7 +112,9 @@ def lib():
         L.gbmc_read_stats.argtypes = [vp, _P(Stats)]
         L.gbmc_lookup_macro.argtypes = [vp, C.c_int32, vp, vp, C.c_int64, vp, vp, C.c_int32, vp]
         L.gbmc_last_run_ms.argtypes = [vp, _P(C.c_double)]
-        L.gbmc_profile_problems.argtypes = [vp, C.c_int32, _P(Problem), vp, _P(KernelTimes)]
+        L.gbmc_profile_problems.argtypes = [vp, C.c_int32, _P(Problem), vp, _P(KernelTimes),
+                                            C.c_int32, _P(C.c_double), _P(C.c_int32),
+                                            _P(C.c_int32)]
         for name in EXPORTS:
             if name != "gbmc_last_error":
                 getattr(L, name).restype = C.c_int
@@ -250,15 +253,23 @@ class Context:
         self._ck(lib().gbmc_run_problems(self._h, len(probs), arr, _stream(stream)))
         self._cells = [_n_cells(p.geom) for p in probs]
 
-    def profile_problems(self, probs, stream=None) -> dict:
+    def profile_problems(self, probs, stream=None, trace_cap: int = 0):
         """Run with every kernel launched eagerly between CUDA events; returns
-        {kernel: (total ms, launches)}."""
+        {kernel: (total ms, launches)}, and with trace_cap > 0 also a
+        per-iteration trace (ms [iters, 9], queue lengths [iters, 4])."""
         arr = (Problem * len(probs))(*probs)
         kt = KernelTimes()
+        tms = np.zeros((max(trace_cap, 1), 9))
+        tq = np.zeros((max(trace_cap, 1), 4), np.int32)
+        tl = C.c_int32(0)
         self._ck(lib().gbmc_profile_problems(self._h, len(probs), arr, _stream(stream),
-                                             C.byref(kt)))
+                                             C.byref(kt), int(trace_cap), _p(tms, C.c_double),
+                                             _p(tq, C.c_int32), C.byref(tl)))
         self._cells = [_n_cells(p.geom) for p in probs]
-        return {name: (kt.ms[k], kt.launches[k]) for k, name in enumerate(KERNEL_NAMES)}
+        totals = {name: (kt.ms[k], kt.launches[k]) for k, name in enumerate(KERNEL_NAMES)}
+        if trace_cap > 0:
+            return totals, tms[:tl.value], tq[:tl.value]
+        return totals
 
     # -- read-back ------------------------------------------------------------
     def read_tallies(self, slot: int = 0):

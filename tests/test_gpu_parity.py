@@ -76,6 +76,20 @@ def test_vacuum_sides_lattice_parity():
     _parity(p, 10_000)
 
 
+@pytest.mark.parametrize("precision", [gbmc.FP64, gbmc.FP32])
+def test_thread_and_warp_lookup_modes_agree_with_oracle(precision):
+    p = synth.make_config(2, grid_scale=0.05)
+    ref = oracle.run(p, seed=p.seed, n=30_000, precision=precision)
+    for wmax in (-1, 1 << 30):   # never / always one warp per particle
+        ctx = make_ctx(p, (precision,), precision=precision, warp_lookup_max=wmax)
+        try:
+            g = run_gpu(ctx, gpu_problem(p, n=30_000))
+        finally:
+            ctx.close()
+        assert_outcomes_equal(g, ref, label=f"warp_lookup_max={wmax}")
+        assert_tallies_close(g, ref)
+
+
 def test_sort_does_not_change_outcomes():
     p = synth.make_config(2, grid_scale=0.05)
     res = []
