@@ -229,13 +229,17 @@ int ensure_bank(gbmc_ctx* c, int32_t M) {
     return GBMC_OK;
 }
 
-// Running-sum cache: max nuclides per material x bank slots, in the table
-// precision.  Above kCumBudget bytes the collision recomputes instead.
+// Running-sum cache: one row per bank slot of the most nuclides of any
+// material rounded up to 8 (rows start on 32-byte boundaries and the lookup
+// stores 4 sums at a time), in the table precision.  Above kCumBudget bytes
+// the collision recomputes instead.
+int64_t cum_row(const gbmc_ctx* c) { return ((int64_t)c->max_nuc_per_mat + 7) / 8 * 8; }
+
 constexpr size_t kCumBudget = (size_t)16 << 30;
 
 int ensure_cum(gbmc_ctx* c) {
     size_t el = c->opt.precision == GBMC_FP64 ? sizeof(double) : sizeof(float);
-    size_t need = (size_t)c->max_nuc_per_mat * (size_t)c->capacity * el;
+    size_t need = (size_t)cum_row(c) * (size_t)c->capacity * el;
     if (need > kCumBudget) need = 0;
     if (need <= c->cum_bytes && (need == 0) == (c->d_cum == nullptr)) return GBMC_OK;
     if (c->d_cum) {
@@ -355,7 +359,7 @@ Params make_params(gbmc_ctx* c) {
     P.max_iter = c->opt.max_iterations;
     sort_params(c, P);
     P.cum = c->d_cum;
-    P.cum_stride = c->d_cum ? c->max_nuc_per_mat : 0;
+    P.cum_stride = c->d_cum ? cum_row(c) : 0;
     return P;
 }
 

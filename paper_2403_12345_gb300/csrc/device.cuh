@@ -338,7 +338,8 @@ __device__ __forceinline__ float micro32(const Tables& T, int32_t i, double E) {
 // Macroscopic sigma_t, sigma_a of material m: sum over its nuclides in the
 // listed order of N_i sigma_i, and of (N_i sigma_i) f_abs,i.  With cum !=
 // NULL the running sum of N_i sigma_i after nuclide k is also stored at
-// cum[k * stride] (the collision picks its nuclide from these sums).
+// cum[k] (the collision picks its nuclide from these sums); cum must be
+// aligned to 32 bytes and hold the material's count rounded up to kIlp.
 //
 // The brackets of kIlp consecutive nuclides are searched in lock step (kIlp
 // independent chains of dependent loads in flight per thread); the terms are
@@ -381,14 +382,14 @@ __device__ __forceinline__ void brackets(const Tables& T, const NucIndex* nx,
 }
 
 __device__ __forceinline__ void macro64(const Tables& T, int32_t m, double E, double& st,
-                                        double& sa, double* cum = nullptr,
-                                        int64_t stride = 0) {
+                                        double& sa, double* cum = nullptr) {
     double at = 0.0, aa = 0.0;
     int32_t q0 = __ldg(T.mat_off + m), q1 = __ldg(T.mat_off + m + 1);
     const unsigned long long* g = reinterpret_cast<const unsigned long long*>(T.e64);
     unsigned long long eb = (unsigned long long)__double_as_longlong(E);
     for (int32_t q = q0; q < q1; q += kIlp) {
         int64_t pos[kIlp];
+        double run[kIlp];
         brackets(T, T.nx64, T.idx64, g, q, q1, eb, pos);
 #pragma unroll
         for (int u = 0; u < kIlp; ++u) {
@@ -402,8 +403,15 @@ __device__ __forceinline__ void macro64(const Tables& T, int32_t m, double E, do
                 double t = __ldg(T.density + q + u) * sig;
                 at = at + t;
                 aa = aa + t * __ldg(T.f_abs + i);
-                if (cum) cum[(int64_t)(q + u - q0) * stride] = at;
             }
+            run[u] = at;
+        }
+        // one 32-byte sector per group (the slot's row is padded to a
+        // multiple of 8 entries; entries past the material's end are unread)
+        if (cum) {
+            double2* d = reinterpret_cast<double2*>(cum + (q - q0));
+            d[0] = make_double2(run[0], run[1]);
+            d[1] = make_double2(run[2], run[3]);
         }
     }
     st = at;
@@ -411,7 +419,7 @@ __device__ __forceinline__ void macro64(const Tables& T, int32_t m, double E, do
 }
 
 __device__ __forceinline__ void macro32(const Tables& T, int32_t m, double E, double& st,
-                                        double& sa, float* cum = nullptr, int64_t stride = 0) {
+                                        double& sa, float* cum = nullptr) {
     float at = 0.0f, aa = 0.0f;
     int32_t q0 = __ldg(T.mat_off + m), q1 = __ldg(T.mat_off + m + 1);
     const uint32_t* g = reinterpret_cast<const uint32_t*>(T.e32);
@@ -419,6 +427,7 @@ __device__ __forceinline__ void macro32(const Tables& T, int32_t m, double E, do
     float Ef = __double2float_rn(E);
     for (int32_t q = q0; q < q1; q += kIlp) {
         int64_t pos[kIlp];
+        float run[kIlp];
         brackets(T, T.nx32, T.idx32, g, q, q1, eb, pos);
 #pragma unroll
         for (int u = 0; u < kIlp; ++u) {
@@ -432,9 +441,11 @@ __device__ __forceinline__ void macro32(const Tables& T, int32_t m, double E, do
                 float t = __ldg(T.density32 + q + u) * sig;
                 at = at + t;
                 aa = aa + t * __ldg(T.f_abs32 + i);
-                if (cum) cum[(int64_t)(q + u - q0) * stride] = at;
             }
+            run[u] = at;
         }
+        if (cum)
+            *reinterpret_cast<float4*>(cum + (q - q0)) = make_float4(run[0], run[1], run[2], run[3]);
     }
     st = (double)at;
     sa = (double)aa;

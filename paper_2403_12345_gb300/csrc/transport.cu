@@ -407,10 +407,10 @@ __global__ void __launch_bounds__(256) k_lookup(Params P) {
                 double st, sa;
                 if (PREC == GBMC_FP64)
                     macro64(P.T, m, E, st, sa,
-                            P.cum ? (double*)P.cum + slot * P.cum_stride : nullptr, 1);
+                            P.cum ? (double*)P.cum + slot * P.cum_stride : nullptr);
                 else
                     macro32(P.T, m, E, st, sa,
-                            P.cum ? (float*)P.cum + slot * P.cum_stride : nullptr, 1);
+                            P.cum ? (float*)P.cum + slot * P.cum_stride : nullptr);
                 P.B.p[slot].st = st;
                 P.B.p[slot].sa = sa;
                 aq[idx] = slot;
