@@ -266,6 +266,31 @@ int gbmc_profile_problems(gbmc_ctx *ctx, int32_t n_prob, const gbmc_problem *pro
                           void *stream, gbmc_kernel_times *out, int32_t trace_cap,
                           double *trace_ms, int32_t *trace_queues, int32_t *trace_len);
 
+/* Sorted macroscopic lookup that allocates nothing (the paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory while they call the library -- code running while a stream
+ * is being captured into a CUDA graph, where cudaMalloc is not allowed;
+ * processes whose device memory is a fixed pool handed out elsewhere; loops
+ * that must not take allocator locks or fail with out-of-memory midway).
+ * Same arguments, results and order of results as gbmc_lookup_macro with
+ * sort = 1, but its sort scratch is a fixed area compiled into the library:
+ *   - at most 1048576 (2^20) queries per call; more returns
+ *     GBMC_ERR_INVALID_ARG before anything is launched;
+ *   - every GPU that loads the library holds that area (about 8.5 MB) until
+ *     the process exits;
+ *   - the first call on a device looks up the area's device address
+ *     (cudaGetSymbolAddress, which may load the library's device code);
+ *     make that first call before any stream capture;
+ *   - all calls share the one area: calls whose work overlaps on the GPU
+ *     (other streams, other threads, other contexts on the same device)
+ *     race and corrupt each other's results; order them on one stream;
+ *   - it calls no cudaMalloc / cudaFree and no allocating library routine.
+ * Inputs and outputs are DEVICE pointers owned by the caller, as in
+ * gbmc_lookup_macro.  Asynchronous on `stream`. */
+int gbmc_lookup_macro_noalloc(gbmc_ctx *ctx, int32_t precision, const double *d_E,
+                              const int32_t *d_mat, int64_t n, double *d_sigma_t,
+                              double *d_sigma_a, void *stream);
+
 /* Device timing of the last run's event loop (ms, CUDA events on the run's
  * stream around the graph launch); synchronizes. */
 int gbmc_last_run_ms(gbmc_ctx *ctx, double *ms);

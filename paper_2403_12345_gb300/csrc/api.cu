@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <limits>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1104,3 +1105,89 @@ int gbmc_lookup_macro(gbmc_ctx* c, int32_t precision, const double* d_E, const i
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Sorted lookup without any allocation.
+//
+// Some callers cannot allocate device memory while they call this library:
+// code that runs while a CUDA stream is being captured into a graph (where
+// cudaMalloc is not allowed), processes whose memory is handed out by a
+// fixed, pre-reserved pool they do not control, or hard-real-time loops that
+// must not take the allocator's locks or risk an out-of-memory error in the
+// middle of work.  gbmc_lookup_macro(sort = 1) grows context-owned scratch
+// with cudaMalloc on first use; this variant instead uses one fixed scratch
+// area that lives in the library image itself.
+//
+// The scratch is a file-scope __device__ array, so every GPU that loads the
+// library reserves it (about 8.5 MB) until the process exits.  Its device
+// address is fetched once per device with cudaGetSymbolAddress; the host
+// symbol itself is only a stand-in and is never handed to a kernel.
+namespace {
+
+constexpr int64_t kNoAllocMaxQueries = (int64_t)1 << 20;
+constexpr size_t kNoAllocPermBytes = sizeof(int32_t) * kNoAllocMaxQueries;
+constexpr size_t kNoAllocKeysBytes = sizeof(uint32_t) * kNoAllocMaxQueries;
+constexpr size_t kNoAllocHistBytes = sizeof(uint32_t) * kSortBuckets;
+constexpr size_t kNoAllocBytes =
+    kNoAllocPermBytes + kNoAllocKeysBytes + 2 * kNoAllocHistBytes + sizeof(uint32_t) * 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch on `device` (which must be current).
+cudaError_t noalloc_scratch(int device, unsigned char** out) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[device] = p;
+    }
+    *out = (unsigned char*)g_noalloc_ptr[device];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" int gbmc_lookup_macro_noalloc(gbmc_ctx* c, int32_t precision, const double* d_E,
+                                         const int32_t* d_mat, int64_t n, double* d_sigma_t,
+                                         double* d_sigma_a, void* stream) {
+    if (!c) return GBMC_ERR_INVALID_ARG;
+    if (n < 0 || (n > 0 && (!d_E || !d_mat || !d_sigma_t || !d_sigma_a)))
+        return fail(c, GBMC_ERR_INVALID_ARG, "n >= 0 and device arrays required");
+    if (n > kNoAllocMaxQueries)
+        return fail(c, GBMC_ERR_INVALID_ARG,
+                    "gbmc_lookup_macro_noalloc takes at most %lld queries per call (got %lld)",
+                    (long long)kNoAllocMaxQueries, (long long)n);
+    if (precision != GBMC_FP64 && precision != GBMC_FP32)
+        return fail(c, GBMC_ERR_INVALID_ARG, "precision must be GBMC_FP64 or GBMC_FP32");
+    if (!c->n_nuc || !c->n_mat) return fail(c, GBMC_ERR_NOT_INITIALIZED, "tables and materials required");
+    if ((precision == GBMC_FP64 && !c->has64) || (precision == GBMC_FP32 && !c->has32))
+        return fail(c, GBMC_ERR_NOT_INITIALIZED, "tables not loaded in that precision");
+    if (n == 0) return GBMC_OK;
+    if (c->device < 0 || c->device >= kNoAllocMaxDevices)
+        return fail(c, GBMC_ERR_UNSUPPORTED, "device index above %d", kNoAllocMaxDevices - 1);
+    int rc = set_device(c);
+    if (rc) return rc;
+    unsigned char* base = nullptr;
+    CK(noalloc_scratch(c->device, &base));
+    int32_t* perm = (int32_t*)base;
+    uint32_t* keys = (uint32_t*)(base + kNoAllocPermBytes);
+    uint32_t* hist = (uint32_t*)(base + kNoAllocPermBytes + kNoAllocKeysBytes);
+    uint32_t* cursor = hist + kSortBuckets;
+    uint32_t* btot = cursor + kSortBuckets;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the bucket counts must start at zero; an earlier call leaves them
+    // cleared, but one that failed midway might not
+    CK(cudaMemsetAsync(hist, 0, kNoAllocHistBytes, s));
+    Params P = make_params(c);
+    P.precision = precision;
+    LaunchCfg L = make_launch(c);
+    cudaError_t e = launch_query_lookup(P, L, d_E, d_mat, n, d_sigma_t, d_sigma_a, perm, keys,
+                                        hist, cursor, btot, s);
+    if (e != cudaSuccess) return fail(c, GBMC_ERR_CUDA, "lookup launch: %s", cudaGetErrorString(e));
+    return GBMC_OK;
+}

@@ -32,7 +32,8 @@ EXPORTS = ["gbmc_default_options", "gbmc_create", "gbmc_destroy", "gbmc_last_err
            "gbmc_set_options", "gbmc_load_xs_tables", "gbmc_init_materials", "gbmc_set_tally",
            "gbmc_reset_tallies", "gbmc_run_batch", "gbmc_run_problems", "gbmc_read_tallies",
            "gbmc_read_outcomes", "gbmc_read_stats", "gbmc_lookup_macro", "gbmc_last_run_ms",
-           "gbmc_profile_problems"]
+           "gbmc_profile_problems", "gbmc_lookup_macro_noalloc"]
+NOALLOC_MAX_QUERIES = 1 << 20
 KERNEL_NAMES = ["plan", "source", "sort_keys", "sort_scan", "sort_scatter", "lookup", "advance",
                 "surface", "collision"]
 
@@ -112,6 +113,7 @@ def lib():
         L.gbmc_read_stats.argtypes = [vp, _P(Stats)]
         L.gbmc_lookup_macro.argtypes = [vp, C.c_int32, vp, vp, C.c_int64, vp, vp, C.c_int32, vp]
         L.gbmc_last_run_ms.argtypes = [vp, _P(C.c_double)]
+        L.gbmc_lookup_macro_noalloc.argtypes = [vp, C.c_int32, vp, vp, C.c_int64, vp, vp, vp]
         L.gbmc_profile_problems.argtypes = [vp, C.c_int32, _P(Problem), vp, _P(KernelTimes),
                                             C.c_int32, _P(C.c_double), _P(C.c_int32),
                                             _P(C.c_int32)]
@@ -311,6 +313,19 @@ class Context:
         self._ck(lib().gbmc_lookup_macro(self._h, int(precision), ptr(E), ptr(mat), int(n),
                                          ptr(sigma_t), ptr(sigma_a), 1 if sort else 0,
                                          _stream(stream)))
+
+    def lookup_macro_noalloc(self, E, mat, sigma_t, sigma_a, precision=FP64, stream=None):
+        """The sorted lookup of lookup_macro(sort=True) with no device
+        allocation: for callers that cannot allocate (for example while a
+        stream is being captured).  At most NOALLOC_MAX_QUERIES queries per
+        call; calls that overlap on the GPU must not be issued (they share one
+        scratch area).  Make the first call on a device before any capture."""
+        def ptr(t):
+            return C.c_void_p(t if isinstance(t, int) else t.data_ptr())
+        n = E.numel() if hasattr(E, "numel") else len(E)
+        self._ck(lib().gbmc_lookup_macro_noalloc(self._h, int(precision), ptr(E), ptr(mat),
+                                                 int(n), ptr(sigma_t), ptr(sigma_a),
+                                                 _stream(stream)))
 
 
 def _n_cells(g: Geometry) -> int:
