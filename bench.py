@@ -38,6 +38,8 @@ WORKLOADS = {
     2: "17x17 pin lattice (r 0.4, p 1.26, H 100), pin 68 + moderator 3 nuclides x 10k-60k "
        "points, binary64 tables, 1e6 particles/batch",
     3: "17x17 pin lattice, binary32 tables, sorted, 1e7 particles/batch",
+    4: "64 independent lattices (3x3..17x17, 4-68 pin nuclides, 1e4-1e6 particles each, "
+       "log-uniform), binary32 tables, one device-driven graph launch, autotuned",
 }
 
 
@@ -147,7 +149,8 @@ def run_reference(args, prob, rank):
 
 def config_of(args, prob):
     return {"workload": prob.name, "description": WORKLOADS.get(args.config, ""),
-            "particles_per_batch": int(args.particles or prob.n_particles[0]),
+            "problems": len(prob.geoms),
+            "particles_per_batch": int(sum(args.particles or n for n in prob.n_particles)),
             "table_precision": "fp32" if args.precision == 1 else "fp64",
             "nuclides": int(prob.n_nuc), "grid_points": int(prob.grid_off[-1]),
             "table_bytes": int(prob.table_bytes(args.precision)),
@@ -171,6 +174,8 @@ def main():
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
     ap.add_argument("--ref-step-s", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", type=int, default=-1,
+                    help="1: autotune launch settings before timing (default: config 4 only)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -202,15 +207,23 @@ def main():
         opts["blocks_per_sm"] = args.blocks_per_sm
     ctx = gbmc.Context(local, **opts)
     ctx.load(prob, (args.precision,))
-    geom = gbmc.geometry_from(prob.geom)
+    n_geo = len(prob.geoms)
+    geoms = [gbmc.geometry_from(g) for g in prob.geoms]
+    counts = [args.particles or prob.n_particles[k] for k in range(n_geo)]
+    npart = sum(counts)
 
-    def problem(batch):
+    def problems(batch):
         # replicas: each rank runs its own batches (weak scaling)
-        return gbmc.problem(geom, prob.seed, npart, batch=batch * world + rank)
+        return [gbmc.problem(geoms[k], prob.seed, counts[k], batch=batch * world + rank,
+                             problem_index=k) for k in range(n_geo)]
+
+    tuned = None
+    if args.autotune == 1 or (args.autotune < 0 and args.config == 4):
+        tuned = ctx.autotune(problems(40_000), fraction=0.1, stream=stream)
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     for w in range(args.warmup):
-        ctx.run_batch(problem(10_000 + w), stream)
+        ctx.run_problems(problems(10_000 + w), stream)
     torch.cuda.synchronize()
     ctx.reset_tallies(stream)
 
@@ -225,7 +238,7 @@ def main():
         for k in range(args.steps):
             flush.zero_()
             ev[k][0].record(stream)
-            ctx.run_batch(problem(k), stream)
+            ctx.run_problems(problems(k), stream)
             ev[k][1].record(stream)
             stats.append(ctx.read_stats())   # synchronizes; outside the events
         torch.cuda.synchronize()
@@ -244,32 +257,32 @@ def main():
     iters = sum(s["iterations"] for s in stats)
 
     # replicas: one tally reduction after the timed region (domain replication)
-    flux, counts, weights = ctx.read_tallies(0)
+    flux, counts_, weights = ctx.read_tallies(0)
     if world > 1:
         t = torch.tensor(flux, device="cuda")
         dist.all_reduce(t)
         flux = t.cpu().numpy()
 
-    # end to end through the C ABI with host buffers: run, then copy the
-    # tallies and every particle's outcome (collisions, fate) to the host
+    # end to end through the C ABI with host buffers: run, then copy every
+    # problem's tallies and every particle's outcome (collisions, fate) to
+    # the host
     e2e_steps = max(1, args.e2e_steps)
-    n_coll = np.empty(npart, np.int32)
-    status = np.empty(npart, np.int8)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    d2h = 0
     for k in range(e2e_steps):
-        ctx.run_batch(problem(20_000 + k), stream)
-        fl, cn, wt = ctx.read_tallies(0)
-        o = ctx.read_outcomes(0, 0, npart)
-        n_coll[:] = o["n_coll"]
-        status[:] = o["status"]
+        ctx.run_problems(problems(20_000 + k), stream)
+        d2h = 0
+        for slot in range(n_geo):
+            fl, cn, wt = ctx.read_tallies(slot)
+            o = ctx.read_outcomes(slot, 0, counts[slot])
+            d2h += fl.nbytes + cn.nbytes + wt.nbytes + sum(o[f].nbytes for f in o)
     e2e_s = time.perf_counter() - t0
-    d2h = fl.nbytes + cn.nbytes + wt.nbytes + sum(o[k].nbytes for k in o)
-    h2d = ctypes.sizeof(gbmc.Problem)
+    h2d = ctypes.sizeof(gbmc.Problem) * n_geo
 
     # per-kernel device times (eager launches between CUDA events) on one
     # more batch of the same workload
-    kt = ctx.profile_problems([problem(30_000)], stream)
+    kt = ctx.profile_problems(problems(30_000), stream)
     pst = ctx.read_stats()
     top = max(kt, key=lambda k: kt[k][0])
     hbm, peak_src = peaks()
@@ -310,6 +323,7 @@ def main():
             "wall_s": wall,
             "e2e": {"value": npart * e2e_steps / e2e_s, "unit": "particles/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "autotune": tuned,
             "roofline": roof,
             "kernel_ms_per_batch": {k: v[0] for k, v in kt.items()},
             "top_kernel": top,

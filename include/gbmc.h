@@ -266,6 +266,29 @@ int gbmc_profile_problems(gbmc_ctx *ctx, int32_t n_prob, const gbmc_problem *pro
                           void *stream, gbmc_kernel_times *out, int32_t trace_cap,
                           double *trace_ms, int32_t *trace_queues, int32_t *trace_len);
 
+/* Result of gbmc_autotune. */
+typedef struct {
+    int32_t trials;            /* probe runs timed */
+    int32_t reserved;
+    double default_ms;         /* probe device time with the options on entry */
+    double best_ms;            /* probe device time with the chosen options */
+    double in_flight_fraction; /* chosen cap / particles of the run (1 = no refill) */
+} gbmc_autotune_report;
+
+/* Autotuner for the launch and queue settings of a run (the batched
+ * multi-problem launch in particular): times probe runs of these problems,
+ * with each particle count scaled by `fraction` (0 < fraction <= 1), over
+ * candidate settings by coordinate descent -- event-kernel grid
+ * (blocks_per_sm), in-flight cap (as a fraction of the run's particles,
+ * Sec. 2 "In-Flight Particles"), the warp-per-particle lookup threshold and
+ * the sort threshold -- and keeps the fastest.  Outcomes do not depend on
+ * these settings, only speed does.  On return the context uses the chosen
+ * options (also copied to *best_out if not NULL; its max_in_flight is the
+ * chosen fraction of the full problems' particles), tallies are zeroed and
+ * the last run's outcomes are the last probe's.  Synchronous. */
+int gbmc_autotune(gbmc_ctx *ctx, int32_t n_prob, const gbmc_problem *probs, double fraction,
+                  void *stream, gbmc_options *best_out, gbmc_autotune_report *report);
+
 /* Sorted macroscopic lookup that allocates nothing (the paper has no
  * counterpart: this entry point exists for callers that cannot allocate
  * device memory while they call the library -- code running while a stream

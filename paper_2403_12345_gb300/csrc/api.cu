@@ -1107,6 +1107,117 @@ int gbmc_lookup_macro(gbmc_ctx* c, int32_t precision, const double* d_E, const i
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// Autotuner: coordinate descent over launch / queue settings, each candidate
+// timed on a scaled-down probe run (CUDA events around the graph launch).
+
+namespace {
+
+int probe_ms(gbmc_ctx* c, const std::vector<gbmc_problem>& probs, cudaStream_t s,
+             const gbmc_options& o, double* ms) {
+    int rc = gbmc_set_options(c, &o);
+    if (rc) return rc;
+    double best = 1e300;
+    for (int rep = 0; rep < 2; ++rep) {   // the first run also builds the graph
+        rc = gbmc_run_problems(c, (int32_t)probs.size(), probs.data(), s);
+        if (rc) return rc;
+        double t = 0;
+        rc = gbmc_last_run_ms(c, &t);
+        if (rc) return rc;
+        rc = read_ctl(c);
+        if (rc) return rc;
+        if (rep > 0 || t < best) best = std::min(best, t);
+    }
+    *ms = best;
+    return GBMC_OK;
+}
+
+}  // namespace
+
+extern "C" int gbmc_autotune(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs,
+                             double fraction, void* stream, gbmc_options* best_out,
+                             gbmc_autotune_report* report) {
+    if (!c) return GBMC_ERR_INVALID_ARG;
+    if (n_prob < 1 || !probs) return fail(c, GBMC_ERR_INVALID_ARG, "n_prob >= 1 and probs required");
+    if (!(fraction > 0 && fraction <= 1))
+        return fail(c, GBMC_ERR_INVALID_ARG, "fraction must be in (0, 1]");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<gbmc_problem> pr(probs, probs + n_prob);
+    int64_t total = 0;
+    for (auto& p : pr) {
+        p.n_particles = std::max<int64_t>(1, (int64_t)std::llround(p.n_particles * fraction));
+        total += p.n_particles;
+    }
+    int64_t full_total = 0;
+    for (int32_t k = 0; k < n_prob; ++k) full_total += probs[k].n_particles;
+    gbmc_options base = c->opt;
+    base.max_in_flight = 0;   // the probe's cap is set from the fraction below
+    int trials = 0;
+    double t0 = 0;
+    int rc = probe_ms(c, pr, s, base, &t0);
+    if (rc) return rc;
+    ++trials;
+    gbmc_options best = base;
+    double best_ms = t0, best_frac = 1.0;
+    const double keep = 0.99;   // a candidate must win by 1% to replace the incumbent
+    // in-flight cap as a fraction of the run
+    for (double f : {0.5, 0.25, 0.125}) {
+        gbmc_options o = best;
+        o.max_in_flight = std::max<int64_t>(1, (int64_t)(total * f));
+        double t;
+        if ((rc = probe_ms(c, pr, s, o, &t))) return rc;
+        ++trials;
+        if (t < best_ms * keep) {
+            best_ms = t;
+            best = o;
+            best_frac = f;
+        }
+    }
+    for (int32_t b : {2, 4, 16}) {
+        gbmc_options o = best;
+        o.blocks_per_sm = b;
+        double t;
+        if ((rc = probe_ms(c, pr, s, o, &t))) return rc;
+        ++trials;
+        if (t < best_ms * keep) { best_ms = t; best = o; }
+    }
+    for (int32_t w : {-1, 8192, 131072}) {
+        gbmc_options o = best;
+        o.warp_lookup_max = w;
+        double t;
+        if ((rc = probe_ms(c, pr, s, o, &t))) return rc;
+        ++trials;
+        if (t < best_ms * keep) { best_ms = t; best = o; }
+    }
+    for (int32_t m : {1024, 65536, -1}) {
+        gbmc_options o = best;
+        if (m < 0)
+            o.sort = -1;
+        else
+            o.sort_min = m;
+        double t;
+        if ((rc = probe_ms(c, pr, s, o, &t))) return rc;
+        ++trials;
+        if (t < best_ms * keep) { best_ms = t; best = o; }
+    }
+    // apply to the full problems: the chosen cap fraction of their particles
+    best.max_in_flight = best_frac < 1.0
+                             ? std::max<int64_t>(1, (int64_t)(full_total * best_frac))
+                             : 0;
+    if ((rc = gbmc_set_options(c, &best))) return rc;
+    if ((rc = gbmc_reset_tallies(c, stream))) return rc;
+    CK(cudaStreamSynchronize(s));
+    if (best_out) *best_out = c->opt;
+    if (report) {
+        report->trials = trials;
+        report->reserved = 0;
+        report->default_ms = t0;
+        report->best_ms = best_ms;
+        report->in_flight_fraction = best_frac;
+    }
+    return GBMC_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Sorted lookup without any allocation.
 //
 // Some callers cannot allocate device memory while they call this library:

@@ -32,7 +32,7 @@ EXPORTS = ["gbmc_default_options", "gbmc_create", "gbmc_destroy", "gbmc_last_err
            "gbmc_set_options", "gbmc_load_xs_tables", "gbmc_init_materials", "gbmc_set_tally",
            "gbmc_reset_tallies", "gbmc_run_batch", "gbmc_run_problems", "gbmc_read_tallies",
            "gbmc_read_outcomes", "gbmc_read_stats", "gbmc_lookup_macro", "gbmc_last_run_ms",
-           "gbmc_profile_problems", "gbmc_lookup_macro_noalloc"]
+           "gbmc_profile_problems", "gbmc_lookup_macro_noalloc", "gbmc_autotune"]
 NOALLOC_MAX_QUERIES = 1 << 20
 KERNEL_NAMES = ["plan", "source", "sort_keys", "sort_scan", "sort_scatter", "lookup", "advance",
                 "surface", "collision"]
@@ -70,6 +70,11 @@ class Stats(C.Structure):
     _fields_ = [("iterations", C.c_int64), ("lookups", C.c_int64), ("micro_lookups", C.c_int64),
                 ("flights", C.c_int64), ("crossings", C.c_int64), ("collisions", C.c_int64),
                 ("histories", C.c_int64), ("device_error", C.c_int32), ("reserved", C.c_int32)]
+
+
+class AutotuneReport(C.Structure):
+    _fields_ = [("trials", C.c_int32), ("reserved", C.c_int32), ("default_ms", C.c_double),
+                ("best_ms", C.c_double), ("in_flight_fraction", C.c_double)]
 
 
 class KernelTimes(C.Structure):
@@ -113,6 +118,8 @@ def lib():
         L.gbmc_read_stats.argtypes = [vp, _P(Stats)]
         L.gbmc_lookup_macro.argtypes = [vp, C.c_int32, vp, vp, C.c_int64, vp, vp, C.c_int32, vp]
         L.gbmc_last_run_ms.argtypes = [vp, _P(C.c_double)]
+        L.gbmc_autotune.argtypes = [vp, C.c_int32, _P(Problem), C.c_double, vp, _P(Options),
+                                    _P(AutotuneReport)]
         L.gbmc_lookup_macro_noalloc.argtypes = [vp, C.c_int32, vp, vp, C.c_int64, vp, vp, vp]
         L.gbmc_profile_problems.argtypes = [vp, C.c_int32, _P(Problem), vp, _P(KernelTimes),
                                             C.c_int32, _P(C.c_double), _P(C.c_int32),
@@ -272,6 +279,20 @@ class Context:
         if trace_cap > 0:
             return totals, tms[:tl.value], tq[:tl.value]
         return totals
+
+    def autotune(self, probs, fraction: float = 0.1, stream=None) -> dict:
+        """gbmc_autotune: pick launch/queue settings by timing probe runs of
+        these problems scaled by `fraction`; the context keeps the choice."""
+        arr = (Problem * len(probs))(*probs)
+        best = Options()
+        rep = AutotuneReport()
+        self._ck(lib().gbmc_autotune(self._h, len(probs), arr, float(fraction), _stream(stream),
+                                     C.byref(best), C.byref(rep)))
+        self.options = best
+        out = {name: getattr(rep, name) for name, _ in AutotuneReport._fields_ if name != "reserved"}
+        out["options"] = {name: getattr(best, name) for name, _ in Options._fields_
+                          if name != "reserved"}
+        return out
 
     # -- read-back ------------------------------------------------------------
     def read_tallies(self, slot: int = 0):

@@ -155,6 +155,27 @@ def test_multi_problem_run_matches_single_runs():
         ctx.close()
 
 
+def test_autotuned_batched_run_matches_oracle():
+    p = synth.make_config(4, n_problems=6, grid_scale=0.02)
+    for k in range(6):
+        p.n_particles[k] = 2000 + 997 * k
+    ctx = make_ctx(p, (gbmc.FP32,), precision=gbmc.FP32)
+    try:
+        probs = [gpu_problem(p, geom_index=k, problem_index=k, batch=1) for k in range(6)]
+        rep = ctx.autotune(probs, fraction=0.5)
+        assert rep["trials"] >= 10 and rep["best_ms"] <= rep["default_ms"]
+        ctx.run_problems(probs)
+        for k in range(6):
+            ref = oracle.run(p, seed=p.seed, batch=1, geom_index=k, problem_index=k,
+                             precision=1)
+            out = ctx.read_outcomes(k, 0, p.n_particles[k])
+            assert_outcomes_equal(out, ref, label=f"problem {k}")
+            flux, counts, weights = ctx.read_tallies(k)
+            assert_tallies_close(dict(flux=flux, counts=counts, weights=weights), ref)
+    finally:
+        ctx.close()
+
+
 @pytest.mark.parametrize("precision", [gbmc.FP64, gbmc.FP32])
 @pytest.mark.parametrize("sort", [False, True])
 def test_lookup_macro_matches_oracle(precision, sort):
