@@ -272,19 +272,21 @@ __device__ __forceinline__ double ln_series(double x) {
 
 template <class U>
 __device__ __forceinline__ void coarse_range(const NucIndex& d, const uint32_t* __restrict__ idx,
-                                             U eb, int64_t& lo, int64_t& hi) {
-    uint64_t b = (uint64_t)eb >= d.base ? ((uint64_t)eb - d.base) >> d.shift : 0ull;
-    if (b > (uint64_t)(d.nb - 1)) b = (uint64_t)(d.nb - 1);
-    int64_t s0 = __ldg(idx + d.idx_off + b), s1 = __ldg(idx + d.idx_off + b + 1);
+                                             U eb, int32_t& lo, int32_t& hi) {
+    U base = (U)d.base;
+    U b = eb >= base ? (U)((eb - base) >> d.shift) : (U)0;
+    if (b > (U)(d.nb - 1)) b = (U)(d.nb - 1);
+    const uint32_t* ix = idx + d.idx_off + b;
+    int32_t s0 = (int32_t)__ldg(ix), s1 = (int32_t)__ldg(ix + 1);
     lo = s0 > 0 ? s0 - 1 : 0;
     if (lo > d.n - 2) lo = d.n - 2;
     hi = s1 < d.n - 1 ? s1 : d.n - 1;
 }
 
 template <class U>
-__device__ __forceinline__ int64_t bracket_in(const U* __restrict__ g, int64_t lo, int64_t hi, U eb) {
+__device__ __forceinline__ int32_t bracket_in(const U* __restrict__ g, int32_t lo, int32_t hi, U eb) {
     while (hi - lo > 1) {
-        int64_t mid = (lo + hi) >> 1;
+        int32_t mid = (lo + hi) >> 1;
         if (__ldg(g + mid) <= eb)
             lo = mid;
         else
@@ -308,7 +310,7 @@ __device__ __forceinline__ NucIndex load_index(const NucIndex* p) {
 __device__ __forceinline__ double micro64(const Tables& T, int32_t i, double E) {
     NucIndex d = load_index(T.nx64 + i);
     unsigned long long eb = (unsigned long long)__double_as_longlong(E);
-    int64_t lo, hi;
+    int32_t lo, hi;
     coarse_range(d, T.idx64, eb, lo, hi);
     const unsigned long long* g = reinterpret_cast<const unsigned long long*>(T.e64 + d.off);
     int64_t k = d.off + bracket_in(g, lo, hi, eb);
@@ -324,7 +326,7 @@ __device__ __forceinline__ double micro64(const Tables& T, int32_t i, double E) 
 __device__ __forceinline__ float micro32(const Tables& T, int32_t i, double E) {
     NucIndex d = load_index(T.nx32 + i);
     uint32_t eb = (uint32_t)__float_as_int(__double2float_rd(E));
-    int64_t lo, hi;
+    int32_t lo, hi;
     coarse_range(d, T.idx32, eb, lo, hi);
     const uint32_t* g = reinterpret_cast<const uint32_t*>(T.e32 + d.off);
     int64_t k = d.off + bracket_in(g, lo, hi, eb);
@@ -350,15 +352,16 @@ template <class U>
 __device__ __forceinline__ void brackets(const Tables& T, const NucIndex* nx,
                                          const uint32_t* idx, const U* g, int32_t q, int32_t q1,
                                          U eb, int64_t* pos) {
-    int64_t lo[kIlp], hi[kIlp], off[kIlp];
+    int32_t lo[kIlp], hi[kIlp];
+    const U* gp[kIlp];
 #pragma unroll
     for (int u = 0; u < kIlp; ++u) {
         lo[u] = 0;
         hi[u] = 1;
-        off[u] = 0;
+        gp[u] = g;
         if (q + u < q1) {
             NucIndex d = load_index(nx + __ldg(T.nuc_id + q + u));
-            off[u] = d.off;
+            gp[u] = g + d.off;
             coarse_range(d, idx, eb, lo[u], hi[u]);
         }
     }
@@ -368,8 +371,8 @@ __device__ __forceinline__ void brackets(const Tables& T, const NucIndex* nx,
 #pragma unroll
         for (int u = 0; u < kIlp; ++u) {
             if (hi[u] - lo[u] > 1) {
-                int64_t mid = (lo[u] + hi[u]) >> 1;
-                if (__ldg(g + off[u] + mid) <= eb)
+                int32_t mid = (lo[u] + hi[u]) >> 1;
+                if (__ldg(gp[u] + mid) <= eb)
                     lo[u] = mid;
                 else
                     hi[u] = mid;
@@ -378,7 +381,7 @@ __device__ __forceinline__ void brackets(const Tables& T, const NucIndex* nx,
         }
     }
 #pragma unroll
-    for (int u = 0; u < kIlp; ++u) pos[u] = off[u] + lo[u];
+    for (int u = 0; u < kIlp; ++u) pos[u] = (gp[u] - g) + lo[u];
 }
 
 __device__ __forceinline__ void macro64(const Tables& T, int32_t m, double E, double& st,
@@ -553,8 +556,8 @@ __device__ __forceinline__ int32_t pick_from_sums(const Tables& T, int32_t m, co
 
 // Tally energy bin: largest b in [0, n_bins-1] with edges[b] <= E.
 __device__ __forceinline__ int32_t energy_bin(const Tables& T, double E) {
-    return (int32_t)bracket_in(reinterpret_cast<const unsigned long long*>(T.edges), (int64_t)0,
-                               (int64_t)T.n_bins, (unsigned long long)__double_as_longlong(E));
+    return bracket_in(reinterpret_cast<const unsigned long long*>(T.edges), 0, T.n_bins,
+                      (unsigned long long)__double_as_longlong(E));
 }
 
 // ---------------------------------------------------------------- geometry
