@@ -100,7 +100,11 @@ typedef struct {
                                 lookups (default 4096) */
     int32_t warp_lookup_max; /* iterations with fewer lookups run one warp per
                                 particle instead of one thread (default 32768) */
-    int32_t reserved[6];
+    int32_t tail_max;        /* once the source is exhausted and at most this many
+                                particles are in flight, the loop stops and a
+                                tail kernel finishes them, one warp per particle
+                                (default 4096; -1: never) */
+    int32_t reserved[5];
 } gbmc_options;
 
 /* One geometry (and its source).  Fields of other kinds are ignored. */
@@ -151,7 +155,8 @@ typedef struct {
 #define GBMC_NKERNELS 9
 typedef struct {
     /* kernels: 0 plan, 1 source, 2 sort keys, 3 sort scan, 4 sort scatter,
-       5 lookup, 6 advance, 7 surface, 8 collision */
+       5 lookup, 6 ray trace (advance and surface events), 7 collision,
+       8 tail (finishes the last particles in flight) */
     double ms[GBMC_NKERNELS];        /* summed device time (CUDA events) */
     int64_t launches[GBMC_NKERNELS]; /* launches of each kernel */
 } gbmc_kernel_times;
@@ -259,8 +264,8 @@ int gbmc_lookup_macro(gbmc_ctx *ctx, int32_t precision, const double *d_E,
  * same as gbmc_run_problems'.
  * Optional per-iteration trace (trace_cap = 0 or NULL pointers skip it):
  *   trace_ms     [trace_cap * GBMC_NKERNELS] device ms of each kernel,
- *   trace_queues [trace_cap * 4] lookups, advances, surface and collision
- *                events of each iteration,
+ *   trace_queues [trace_cap * 4] lookups, ray-traced particles, and
+ *                collision events of each iteration, and particles in flight,
  *   *trace_len   iterations recorded (at most trace_cap). */
 int gbmc_profile_problems(gbmc_ctx *ctx, int32_t n_prob, const gbmc_problem *probs,
                           void *stream, gbmc_kernel_times *out, int32_t trace_cap,

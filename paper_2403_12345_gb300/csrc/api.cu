@@ -17,6 +17,7 @@
 using namespace gbmc;
 
 static_assert(sizeof(gbmc_options) == 72, "gbmc_options layout is part of the ABI");
+static_assert(kTimedKernels == GBMC_NKERNELS, "profile kernel count is part of the ABI");
 static_assert(sizeof(gbmc_geometry) == 104, "gbmc_geometry layout is part of the ABI");
 static_assert(sizeof(gbmc_problem) == 136, "gbmc_problem layout is part of the ABI");
 
@@ -171,6 +172,8 @@ void fill_defaults(gbmc_options* o) {
     if (o->sort_min <= 0) o->sort_min = 4096;
     if (o->warp_lookup_max == 0) o->warp_lookup_max = 32768;
     if (o->warp_lookup_max < 0) o->warp_lookup_max = 0;   // never
+    if (o->tail_max == 0) o->tail_max = 4096;
+    if (o->tail_max < 0) o->tail_max = 0;                 // never
 }
 
 int check_options(gbmc_ctx* c, const gbmc_options* o) {
@@ -182,6 +185,8 @@ int check_options(gbmc_ctx* c, const gbmc_options* o) {
         return fail(c, GBMC_ERR_INVALID_ARG, "blocks_per_sm must be in [1, 32]");
     if (o->max_in_flight < 0 || o->max_in_flight > (int64_t)(1 << 30))
         return fail(c, GBMC_ERR_INVALID_ARG, "max_in_flight must be in [0, 2^30]");
+    if (o->tail_max > (1 << 24))
+        return fail(c, GBMC_ERR_INVALID_ARG, "tail_max must be at most 2^24");
     return GBMC_OK;
 }
 
@@ -357,6 +362,7 @@ Params make_params(gbmc_ctx* c) {
     P.sort = c->opt.sort > 0 ? 1 : 0;
     P.sort_min = c->opt.sort_min;
     P.warp_lookup_max = c->opt.warp_lookup_max;
+    P.tail_max = c->opt.tail_max;
     P.max_iter = c->opt.max_iterations;
     sort_params(c, P);
     P.cum = c->d_cum;
@@ -368,6 +374,7 @@ LaunchCfg make_launch(const gbmc_ctx* c) {
     LaunchCfg L;
     L.grid = c->sms * c->opt.blocks_per_sm;
     L.grid_lookup = c->sms * c->opt.blocks_per_sm;
+    L.grid_tail = std::max(1, (c->opt.tail_max + 7) / 8);   // 8 warps per block
     return L;
 }
 
@@ -418,6 +425,14 @@ int build_graph(gbmc_ctx* c, Params P, const LaunchCfg& L) {
     ee = cudaStreamEndCapture(c->cap_stream, &b2);
     if (le != cudaSuccess) return fail(c, GBMC_ERR_CUDA, "body capture: %s", cudaGetErrorString(le));
     if (ee != cudaSuccess) return fail(c, GBMC_ERR_CUDA, "body capture end: %s", cudaGetErrorString(ee));
+    // the tail kernel after the loop
+    CK(cudaStreamBeginCaptureToGraph(c->cap_stream, g, &cn, nullptr, 1,
+                                     cudaStreamCaptureModeThreadLocal));
+    le = launch_tail(P, L, c->cap_stream);
+    cudaGraph_t g3 = nullptr;
+    ee = cudaStreamEndCapture(c->cap_stream, &g3);
+    if (le != cudaSuccess) return fail(c, GBMC_ERR_CUDA, "tail capture: %s", cudaGetErrorString(le));
+    if (ee != cudaSuccess) return fail(c, GBMC_ERR_CUDA, "tail capture end: %s", cudaGetErrorString(ee));
     cudaError_t ie = cudaGraphInstantiate(&c->exec, g, 0);
     if (ie != cudaSuccess) {
         c->exec = nullptr;
@@ -952,7 +967,7 @@ int gbmc_profile_problems(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs
         if (e != cudaSuccess) break;
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) break;
-        for (int k = 0; k < kTimedKernels; ++k) {
+        for (int k = 0; k < kIterKernels; ++k) {
             float ms = 0;
             e = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
             if (e != cudaSuccess) break;
@@ -965,12 +980,23 @@ int gbmc_profile_problems(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs
             const Ctl& k = *c->h_ctl;
             int32_t* tq = trace_queues + (int64_t)it * 4;
             tq[0] = k.lookup_n;
-            tq[1] = k.n_aq[k.cur];
-            tq[2] = k.n_sq;
-            tq[3] = k.n_cq;
+            tq[1] = k.adv_n;
+            tq[2] = k.n_cq;
+            tq[3] = k.M - k.n_free;
         }
         if (trace_len && it < trace_cap) *trace_len = it + 1;
         if (c->h_ctl->done || ++it > c->opt.max_iterations + 1) break;
+    }
+    if (e == cudaSuccess) {
+        // the tail kernel (a no-op unless the loop stopped early)
+        cudaEventRecord(ev[0], s);
+        e = launch_tail(P, L, s);
+        cudaEventRecord(ev[1], s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+        float ms = 0;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        out->ms[kTimedKernels - 1] += ms;
+        out->launches[kTimedKernels - 1] += 1;
     }
     for (int k = 0; k <= kTimedKernels; ++k) cudaEventDestroy(ev[k]);
     if (e != cudaSuccess) return fail(c, GBMC_ERR_CUDA, "profiled run: %s", cudaGetErrorString(e));
@@ -1187,6 +1213,14 @@ extern "C" int gbmc_autotune(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* pr
         if ((rc = probe_ms(c, pr, s, o, &t))) return rc;
         ++trials;
         if (t < best_ms * keep) { best_ms = t; best = o; }
+    }
+    for (int32_t t : {-1, 1024, 16384, 65536}) {
+        gbmc_options o = best;
+        o.tail_max = t;
+        double t_ms;
+        if ((rc = probe_ms(c, pr, s, o, &t_ms))) return rc;
+        ++trials;
+        if (t_ms < best_ms * keep) { best_ms = t_ms; best = o; }
     }
     for (int32_t m : {1024, 65536, -1}) {
         gbmc_options o = best;

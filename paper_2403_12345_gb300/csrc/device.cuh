@@ -126,7 +126,9 @@ struct Ctl {
     int32_t cur;                 // queues[cur] are consumed this iteration
     int32_t lookup_n, aq_base;   // lookups of this iteration, where they append in aq[cur]
     int32_t n_birth, free_base, lq_base, sorted;
-    int32_t warp_lookup, pad1;   // this iteration's lookups run one warp per particle
+    int32_t warp_lookup;         // this iteration's lookups run one warp per particle
+    int32_t adv_n;               // particles the ray-trace kernel takes this iteration
+    int32_t tail, pad2;          // the loop stopped early: the tail kernel finishes
     int64_t next_base;           // run index of the first particle born this iteration
     int64_t next, total;         // next unborn run index, particles in the run
     int32_t M;                   // in-flight cap of this run (<= capacity)
@@ -152,6 +154,8 @@ struct Params {
     int32_t sort;            // sort the lookup queue
     int32_t sort_min;        // sort only when at least this many lookups
     int32_t warp_lookup_max; // below this many lookups: one warp per particle
+    int32_t tail_max;        // stop the loop and finish in the tail kernel at or below
+                             // this many particles in flight (source exhausted)
     int32_t max_iter;
     uint32_t sort_shift;     // energy-bits >> shift = bucket within a material
     uint32_t bpm_log2;       // log2 buckets per material

@@ -8,19 +8,25 @@ namespace gbmc {
 struct LaunchCfg {
     int grid;          // blocks of the event kernels (multiple of the SM count)
     int grid_lookup;   // blocks of the lookup kernel
+    int grid_tail;     // blocks of the tail kernel (one warp per particle)
 };
 
 // Fill the free-slot list of a run (the run's control block is written by
 // the host before the launch).
 cudaError_t launch_init_run(const Params& P, const LaunchCfg& L, cudaStream_t s);
 
-// One event-loop iteration: plan, source, sort, lookup, advance, surface,
-// collision.  Captured once into the body of a graph while-node.
+// One event-loop iteration: plan, source, sort, lookup, ray trace (advance +
+// surface), collision.  Captured once into the body of a graph while-node.
 cudaError_t launch_iteration(const Params& P, const LaunchCfg& L, cudaStream_t s);
 
-// The same iteration launched eagerly with an event before and after each
-// kernel (ev[0..9]), for per-kernel device timing.
-constexpr int kTimedKernels = 9;
+// The tail kernel, after the loop: finishes the histories left when the loop
+// stopped early (a no-op otherwise).
+cudaError_t launch_tail(const Params& P, const LaunchCfg& L, cudaStream_t s);
+
+// The iteration launched eagerly with an event before and after each kernel
+// (ev[0..8]), for per-kernel device timing; the tail is timed separately.
+constexpr int kIterKernels = 8;
+constexpr int kTimedKernels = 9;   // + the tail
 cudaError_t launch_iteration_timed(const Params& P, const LaunchCfg& L, cudaStream_t s,
                                    cudaEvent_t* ev);
 

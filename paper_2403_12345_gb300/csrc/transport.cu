@@ -53,18 +53,24 @@ struct BlockScalars {
         }
         __syncthreads();
     }
-    // all 32 lanes call; lanes with pred score weight wt into (prob, kind)
-    __device__ __forceinline__ void add(const Tallies& Y, bool pred, int prob, int kind, double wt) {
+    // all 32 lanes call; lanes with pred score weight wt and count k into
+    // (prob, kind)
+    __device__ __forceinline__ void add(const Tallies& Y, bool pred, int prob, int kind, double wt,
+                                        unsigned long long k) {
         unsigned vm = __ballot_sync(kFull, pred);
         if (vm == 0) return;
         unsigned peers = __match_any_sync(kFull, pred ? prob : -1);
         int lane = threadIdx.x & 31;
         if (vm == kFull && peers == kFull) {
             double s = wt;
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
-            if (lane == 0) put(Y, prob, kind, s, 32ull);
+            unsigned long long ks = k;
+            for (int o = 16; o > 0; o >>= 1) {
+                s += __shfl_xor_sync(kFull, s, o);
+                ks += __shfl_xor_sync(kFull, ks, o);
+            }
+            if (lane == 0) put(Y, prob, kind, s, ks);
         } else if (pred) {
-            put(Y, prob, kind, wt, 1ull);
+            put(Y, prob, kind, wt, k);
         }
     }
     __device__ __forceinline__ void put(const Tallies& Y, int prob, int kind, double s,
@@ -118,8 +124,7 @@ __global__ void k_init_run(Params P) {
 __global__ void k_plan(Params P) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     Ctl* c = P.ctl;
-    // events of the previous iteration
-    c->st_cross += (unsigned long long)c->n_sq;
+    // collisions of the previous iteration
     c->st_coll += (unsigned long long)c->n_cq;
     int cur = 1 - c->cur;
     c->cur = cur;
@@ -138,24 +143,33 @@ __global__ void k_plan(Params P) {
     c->lq_base = c->n_lq[cur];
     c->n_lq[cur] += k;
     c->st_hist += (unsigned long long)k;
-    int done = (c->n_free == c->M);   // nothing in flight, nothing left to birth
+    int alive = c->M - c->n_free;
+    int done = alive == 0;   // nothing in flight, nothing left to birth
     c->iter += 1;
-    if (!done && c->iter > P.max_iter) {
+    c->tail = 0;
+    if (!done && c->next == c->total && alive <= P.tail_max) {
+        // few particles left: the tail kernel after the loop finishes them
+        c->tail = 1;
+        done = 1;
+    } else if (!done && c->iter > P.max_iter) {
         c->err = GBMC_ERR_TIMEOUT;
         done = 1;
-    }
-    if (done) {
-        c->n_birth = 0;
         c->n_lq[cur] = 0;
         c->n_aq[cur] = 0;
     }
-    c->lookup_n = c->n_lq[cur];
-    c->aq_base = c->n_aq[cur];
-    c->n_aq[cur] += c->lookup_n;
+    if (done) {
+        c->n_birth = 0;
+        c->lookup_n = 0;
+        c->adv_n = 0;
+    } else {
+        c->lookup_n = c->n_lq[cur];
+        c->aq_base = c->n_aq[cur];
+        c->adv_n = c->n_aq[cur] + c->lookup_n;
+        c->n_aq[cur] = c->adv_n;
+    }
     c->sorted = (P.sort && c->lookup_n >= P.sort_min) ? 1 : 0;
     c->warp_lookup = c->lookup_n < P.warp_lookup_max ? 1 : 0;
     c->st_lookups += (unsigned long long)c->lookup_n;
-    c->st_flights += (unsigned long long)c->n_aq[cur];
     c->done = done;
     if (P.use_cond) cudaGraphSetConditional(P.cond, done ? 0u : 1u);
 }
@@ -243,7 +257,7 @@ __global__ void __launch_bounds__(256) k_source(Params P) {
             P.B.p[slot] = rec;
             P.Q.lq[cur][lb + idx] = slot;
         }
-        sc.add(P.Y, valid, prob, GBMC_S_HISTORY, 1.0);
+        sc.add(P.Y, valid, prob, GBMC_S_HISTORY, 1.0, 1ull);
     }
     sc.flush(P.Y);
 }
@@ -422,201 +436,262 @@ __global__ void __launch_bounds__(256) k_lookup(Params P) {
     if ((threadIdx.x & 31) == 0 && micro) atomicAdd(&P.ctl->st_micro, micro);
 }
 
-// ---------------------------------------------------------------- death
+// ---------------------------------------------------------------- per-particle steps
+// The steps of one history, shared by the event kernels and the tail kernel
+// so that both perform the identical operations in the identical order.
 
-__device__ __forceinline__ void record_death(const Params& P, int32_t slot, int status, int32_t ncoll,
-                                             int32_t nflt, uint32_t rj, double E, double x,
-                                             double y, double z) {
-    int64_t gi = P.B.p[slot].gidx;
-    P.O.ncoll[gi] = ncoll;
+__device__ __forceinline__ void record_death(const Params& P, const Particle& pt, int status) {
+    int64_t gi = pt.gidx;
+    P.O.ncoll[gi] = pt.ncoll;
     P.O.status[gi] = (int8_t)status;
-    P.O.nflt[gi] = nflt;
-    P.O.ndraw[gi] = rj;
-    P.O.E[gi] = E;
-    P.O.x[gi] = x;
-    P.O.y[gi] = y;
-    P.O.z[gi] = z;
+    P.O.nflt[gi] = pt.nflt;
+    P.O.ndraw[gi] = pt.rj;
+    P.O.E[gi] = pt.E;
+    P.O.x[gi] = pt.x;
+    P.O.y[gi] = pt.y;
+    P.O.z[gi] = pt.z;
 }
 
-// ---------------------------------------------------------------- advance event
-// Sample the distance to collision, find the distance to the nearest surface
-// of the current cell, move by the smaller one, score the track length in
-// the (cell, energy bin) flux tally, route to collision or surface.
+__device__ __forceinline__ void stream_of(const DevProblem& pr, const Particle& pt, Stream& r) {
+    r.init(pr.seed, pr.key_hi, (uint64_t)(pr.first_id + (pt.gidx - pr.start)), pt.rj);
+}
 
-__global__ void __launch_bounds__(256) k_advance(Params P) {
+// One flight (advance event): sample the distance to collision, find the
+// nearest surface of the current cell (ties: cylinder, x, y, z), move by
+// the smaller one and score w d in the (cell, energy bin) flux tally.
+// Returns true for a collision; otherwise pt.surf names the surface reached.
+__device__ __forceinline__ bool fly(const Params& P, const DevProblem& pr, Particle& pt,
+                                    Stream& r) {
+    const gbmc_geometry& g = pr.g;
+    double xi = r.next();
+    double dcol = (0.0 - ln_series(xi)) / pt.st;
+    double dbnd = CUDART_INF;
+    uint8_t surf = kSurfNone;
+    int32_t cell = 0;
+    if (g.kind == GBMC_GEOM_LATTICE) {
+        double p = g.pitch;
+        double cx = ((double)pt.ci + 0.5) * p;
+        double cy = ((double)pt.cj + 0.5) * p;
+        double dc = dist_cylinder(pt.x - cx, pt.y - cy, pt.u, pt.v, g.radius, pt.inside != 0);
+        double dx = dist_planes(pt.x, pt.u, (double)pt.ci * p, (double)(pt.ci + 1) * p);
+        double dy = dist_planes(pt.y, pt.v, (double)pt.cj * p, (double)(pt.cj + 1) * p);
+        double dz = dist_planes(pt.z, pt.w, 0.0, g.height);
+        if (dc < 0.0) dc = 0.0;
+        if (dx < 0.0) dx = 0.0;
+        if (dy < 0.0) dy = 0.0;
+        if (dz < 0.0) dz = 0.0;
+        dbnd = dc;
+        surf = kSurfCyl;
+        if (dx < dbnd) { dbnd = dx; surf = kSurfX; }
+        if (dy < dbnd) { dbnd = dy; surf = kSurfY; }
+        if (dz < dbnd) { dbnd = dz; surf = kSurfZ; }
+        cell = pt.cj * g.n + pt.ci;
+    } else if (g.kind == GBMC_GEOM_SLAB) {
+        double h = g.layer_dx;
+        double dx = dist_planes(pt.x, pt.u, (double)pt.ci * h, (double)(pt.ci + 1) * h);
+        if (dx < 0.0) dx = 0.0;
+        dbnd = dx;
+        surf = kSurfX;
+        cell = pt.ci;
+    }
+    bool collide = dcol < dbnd;
+    double d = collide ? dcol : dbnd;
+    pt.x = pt.x + d * pt.u;
+    pt.y = pt.y + d * pt.v;
+    pt.z = pt.z + d * pt.w;
+    int32_t bin = energy_bin(P.T, pt.E);
+    atomicAdd(&P.Y.flux[pr.flux_off + (int64_t)cell * P.T.n_bins + bin], pt.wgt * d);
+    pt.nflt = pt.nflt + 1;
+    pt.surf = surf;
+    pt.rj = r.j;
+    return collide;
+}
+
+// Surface event: cross pt.surf.  Returns the fate (0: still alive) and sets
+// relook when the material changed (a new lookup is needed).
+__device__ __forceinline__ int cross(const gbmc_geometry& g, Particle& pt, bool& relook) {
+    int status = 0;
+    relook = false;
+    if (g.kind == GBMC_GEOM_SLAB) {
+        double h = g.layer_dx;
+        if (pt.u > 0.0) {
+            pt.x = (double)(pt.ci + 1) * h;
+            if (pt.ci < g.n_layers - 1) pt.ci += 1;
+            else status = GBMC_STATUS_LEAKED_FAR;
+        } else {
+            pt.x = (double)pt.ci * h;
+            if (pt.ci > 0) pt.ci -= 1;
+            else status = GBMC_STATUS_LEAKED;
+        }
+        if (!status) {
+            int32_t m = pt.ci < g.n_first ? g.mat_a : g.mat_b;
+            relook = m != pt.mat;
+            pt.mat = m;
+        }
+    } else if (pt.surf == kSurfCyl) {
+        pt.inside = pt.inside ? 0 : 1;
+        int32_t m = pt.inside ? g.mat_pin : g.mat_mod;
+        relook = m != pt.mat;
+        pt.mat = m;
+    } else if (pt.surf == kSurfX) {
+        double p = g.pitch;
+        if (pt.u > 0.0) {
+            pt.x = (double)(pt.ci + 1) * p;
+            if (pt.ci < g.n - 1) pt.ci += 1;
+            else if (g.bc_side == GBMC_BC_REFLECT) pt.u = -pt.u;
+            else status = GBMC_STATUS_LEAKED;
+        } else {
+            pt.x = (double)pt.ci * p;
+            if (pt.ci > 0) pt.ci -= 1;
+            else if (g.bc_side == GBMC_BC_REFLECT) pt.u = -pt.u;
+            else status = GBMC_STATUS_LEAKED;
+        }
+    } else if (pt.surf == kSurfY) {
+        double p = g.pitch;
+        if (pt.v > 0.0) {
+            pt.y = (double)(pt.cj + 1) * p;
+            if (pt.cj < g.n - 1) pt.cj += 1;
+            else if (g.bc_side == GBMC_BC_REFLECT) pt.v = -pt.v;
+            else status = GBMC_STATUS_LEAKED;
+        } else {
+            pt.y = (double)pt.cj * p;
+            if (pt.cj > 0) pt.cj -= 1;
+            else if (g.bc_side == GBMC_BC_REFLECT) pt.v = -pt.v;
+            else status = GBMC_STATUS_LEAKED;
+        }
+    } else {  // z planes
+        pt.z = pt.w > 0.0 ? g.height : 0.0;
+        if (g.bc_z == GBMC_BC_REFLECT) pt.w = -pt.w;
+        else status = GBMC_STATUS_LEAKED;
+    }
+    if (!status && pt.nflt >= GBMC_MAX_FLIGHTS) status = GBMC_STATUS_LIMIT;
+    return status;
+}
+
+// Collision event: nuclide (from the running sums the lookup stored, else
+// recomputed), absorption, elastic scatter (isotropic in the CM frame,
+// target at rest), energy cutoff.  Returns the fate (0: alive, needs a new
+// lookup).
+template <int PREC>
+__device__ __forceinline__ int collide(const Params& P, const DevProblem& pr, Particle& pt,
+                                       int32_t slot, Stream& r) {
+    double target = r.next() * pt.st;
+    int32_t nuc = -1;
+    if (P.cum) {
+        if (PREC == GBMC_FP64)
+            nuc = pick_from_sums(P.T, pt.mat, (const double*)P.cum + slot * P.cum_stride, 1, target);
+        else
+            nuc = pick_from_sums(P.T, pt.mat, (const float*)P.cum + slot * P.cum_stride, 1, target);
+    }
+    if (nuc < 0) nuc = pick_nuclide(P.T, PREC, pt.mat, pt.E, target);
+    pt.ncoll = pt.ncoll + 1;
+    int status = 0;
+    double xa = r.next();
+    if (xa < __ldg(P.T.f_abs + nuc)) {
+        status = GBMC_STATUS_ABSORBED;
+    } else {
+        double mu = 2.0 * r.next() - 1.0;
+        double a, b;
+        double s = disk_pair(r, a, b);
+        double cphi = (a * a - b * b) / s;
+        double sphi = ((2.0 * a) * b) / s;
+        double E1, mul;
+        elastic(pt.E, __ldg(P.T.awr + nuc), mu, E1, mul);
+        double u = pt.u, v = pt.v, w = pt.w;
+        rotate(u, v, w, mul, cphi, sphi);
+        pt.u = u;
+        pt.v = v;
+        pt.w = w;
+        pt.E = E1;
+        if (pt.E < pr.g.E_cut) status = GBMC_STATUS_CUTOFF;
+    }
+    if (!status && pt.nflt >= GBMC_MAX_FLIGHTS) status = GBMC_STATUS_LIMIT;
+    pt.rj = r.j;
+    return status;
+}
+
+__device__ __forceinline__ int leak_kind(int status) {
+    return status == GBMC_STATUS_LEAKED || status == GBMC_STATUS_LEAKED_FAR;
+}
+
+// ---------------------------------------------------------------- ray-trace event
+// Advance (flight) and surface events of one particle, repeated while the
+// particle crosses surfaces that keep its material (lattice walls,
+// reflections): the paper's "ray trace" kernel.  Ends at a collision (to the
+// collision queue), a material change (to the lookup queue), a leak or the
+// flight limit (death), or after kStreamMax flights (back to the advance
+// queue of the next iteration).
+
+constexpr int kStreamMax = 64;
+
+__global__ void __launch_bounds__(256) k_raytrace(Params P) {
     Ctl* c = P.ctl;
     int cur = c->cur;
-    int32_t n = c->n_aq[cur];
+    int32_t n = c->adv_n;
     if (n == 0) return;
     GBMC_BLOCK_SCALARS(sc, c->n_prob);
     const int32_t* q = P.Q.aq[cur];
+    int nxt = 1 - cur;
+    unsigned long long crossings = 0, nflights = 0;
     GBMC_WARP_LOOP(idx, valid, n) {
         int32_t slot = 0;
-        int prob = 0;
-        bool collide = false;
+        int prob = 0, status = 0, route = 0;   // route 1: collision, 2: lookup, 3: advance
         double wgt = 0.0;
+        int32_t flights = 0;
         if (valid) {
             slot = q[idx];
-            Particle& pt = P.B.p[slot];
+            Particle pt = P.B.p[slot];
             prob = pt.prob;
             const DevProblem& pr = P.probs[prob];
-            const gbmc_geometry& g = pr.g;
-            double x = pt.x, y = pt.y, z = pt.z;
-            double u = pt.u, v = pt.v, w = pt.w;
-            double E = pt.E, st = pt.st;
             wgt = pt.wgt;
-            int32_t ci = pt.ci, cj = pt.cj;
             Stream r;
-            r.init(pr.seed, pr.key_hi, (uint64_t)(pr.first_id + (pt.gidx - pr.start)), pt.rj);
-            double xi = r.next();
-            double dcol = (0.0 - ln_series(xi)) / st;
-            double dbnd = CUDART_INF;
-            uint8_t surf = kSurfNone;
-            int32_t cell = 0;
-            if (g.kind == GBMC_GEOM_LATTICE) {
-                double p = g.pitch;
-                double cx = ((double)ci + 0.5) * p;
-                double cy = ((double)cj + 0.5) * p;
-                double dc = dist_cylinder(x - cx, y - cy, u, v, g.radius, pt.inside != 0);
-                double dx = dist_planes(x, u, (double)ci * p, (double)(ci + 1) * p);
-                double dy = dist_planes(y, v, (double)cj * p, (double)(cj + 1) * p);
-                double dz = dist_planes(z, w, 0.0, g.height);
-                if (dc < 0.0) dc = 0.0;
-                if (dx < 0.0) dx = 0.0;
-                if (dy < 0.0) dy = 0.0;
-                if (dz < 0.0) dz = 0.0;
-                dbnd = dc;
-                surf = kSurfCyl;
-                if (dx < dbnd) { dbnd = dx; surf = kSurfX; }
-                if (dy < dbnd) { dbnd = dy; surf = kSurfY; }
-                if (dz < dbnd) { dbnd = dz; surf = kSurfZ; }
-                cell = cj * g.n + ci;
-            } else if (g.kind == GBMC_GEOM_SLAB) {
-                double h = g.layer_dx;
-                double dx = dist_planes(x, u, (double)ci * h, (double)(ci + 1) * h);
-                if (dx < 0.0) dx = 0.0;
-                dbnd = dx;
-                surf = kSurfX;
-                cell = ci;
+            stream_of(pr, pt, r);
+            for (;;) {
+                bool col = fly(P, pr, pt, r);
+                ++flights;
+                if (col) {
+                    route = 1;
+                    break;
+                }
+                bool relook;
+                status = cross(pr.g, pt, relook);
+                ++crossings;
+                if (status) break;
+                if (relook) {
+                    route = 2;
+                    break;
+                }
+                if (flights >= kStreamMax) {
+                    route = 3;
+                    break;
+                }
             }
-            collide = dcol < dbnd;
-            double d = collide ? dcol : dbnd;
-            x = x + d * u;
-            y = y + d * v;
-            z = z + d * w;
-            int32_t bin = energy_bin(P.T, E);
-            atomicAdd(&P.Y.flux[pr.flux_off + (int64_t)cell * P.T.n_bins + bin], wgt * d);
-            pt.x = x; pt.y = y; pt.z = z;
-            pt.rj = r.j;
-            pt.nflt = pt.nflt + 1;
-            pt.surf = surf;
-        }
-        sc.add(P.Y, valid, prob, GBMC_S_FLIGHT, wgt);
-        warp_append(P.Q.cq, &c->n_cq, slot, valid && collide);
-        warp_append(P.Q.sq, &c->n_sq, slot, valid && !collide);
-    }
-    sc.flush(P.Y);
-}
-
-// ---------------------------------------------------------------- surface event
-
-__global__ void __launch_bounds__(256) k_surface(Params P) {
-    Ctl* c = P.ctl;
-    int32_t n = c->n_sq;
-    if (n == 0) return;
-    GBMC_BLOCK_SCALARS(sc, c->n_prob);
-    int nxt = 1 - c->cur;
-    GBMC_WARP_LOOP(idx, valid, n) {
-        int32_t slot = 0;
-        int prob = 0;
-        int status = 0;
-        bool relook = false;
-        double wgt = 0.0;
-        if (valid) {
-            slot = P.Q.sq[idx];
-            Particle& pt = P.B.p[slot];
-            prob = pt.prob;
-            const gbmc_geometry& g = P.probs[prob].g;
-            wgt = pt.wgt;
-            int32_t ci = pt.ci, cj = pt.cj, mat = pt.mat;
-            double x = pt.x, y = pt.y, z = pt.z;
-            double u = pt.u, v = pt.v, w = pt.w;
-            uint8_t surf = pt.surf;
-            if (g.kind == GBMC_GEOM_SLAB) {
-                double h = g.layer_dx;
-                if (u > 0.0) {
-                    x = (double)(ci + 1) * h;
-                    if (ci < g.n_layers - 1) ci += 1;
-                    else status = GBMC_STATUS_LEAKED_FAR;
-                } else {
-                    x = (double)ci * h;
-                    if (ci > 0) ci -= 1;
-                    else status = GBMC_STATUS_LEAKED;
-                }
-                if (!status) {
-                    int32_t m = ci < g.n_first ? g.mat_a : g.mat_b;
-                    relook = m != mat;
-                    mat = m;
-                }
-            } else if (surf == kSurfCyl) {
-                uint8_t in = pt.inside ? 0 : 1;
-                pt.inside = in;
-                int32_t m = in ? g.mat_pin : g.mat_mod;
-                relook = m != mat;
-                mat = m;
-            } else if (surf == kSurfX) {
-                double p = g.pitch;
-                if (u > 0.0) {
-                    x = (double)(ci + 1) * p;
-                    if (ci < g.n - 1) ci += 1;
-                    else if (g.bc_side == GBMC_BC_REFLECT) u = -u;
-                    else status = GBMC_STATUS_LEAKED;
-                } else {
-                    x = (double)ci * p;
-                    if (ci > 0) ci -= 1;
-                    else if (g.bc_side == GBMC_BC_REFLECT) u = -u;
-                    else status = GBMC_STATUS_LEAKED;
-                }
-            } else if (surf == kSurfY) {
-                double p = g.pitch;
-                if (v > 0.0) {
-                    y = (double)(cj + 1) * p;
-                    if (cj < g.n - 1) cj += 1;
-                    else if (g.bc_side == GBMC_BC_REFLECT) v = -v;
-                    else status = GBMC_STATUS_LEAKED;
-                } else {
-                    y = (double)cj * p;
-                    if (cj > 0) cj -= 1;
-                    else if (g.bc_side == GBMC_BC_REFLECT) v = -v;
-                    else status = GBMC_STATUS_LEAKED;
-                }
-            } else {  // z planes
-                z = w > 0.0 ? g.height : 0.0;
-                if (g.bc_z == GBMC_BC_REFLECT) w = -w;
-                else status = GBMC_STATUS_LEAKED;
-            }
-            int32_t nflt = pt.nflt;
-            if (!status && nflt >= GBMC_MAX_FLIGHTS) status = GBMC_STATUS_LIMIT;
-            pt.x = x; pt.y = y; pt.z = z;
-            pt.u = u; pt.v = v; pt.w = w;
-            pt.ci = ci; pt.cj = cj; pt.mat = mat;
-            if (status) record_death(P, slot, status, pt.ncoll, nflt, pt.rj, pt.E, x, y, z);
+            P.B.p[slot] = pt;
+            if (status) record_death(P, pt, status);
+            nflights += (unsigned long long)flights;
         }
         bool dead = valid && status != 0;
-        sc.add(P.Y, dead && (status == GBMC_STATUS_LEAKED || status == GBMC_STATUS_LEAKED_FAR),
-               prob, GBMC_S_LEAK, wgt);
-        sc.add(P.Y, dead && status == GBMC_STATUS_LEAKED_FAR, prob, GBMC_S_LEAK_FAR, wgt);
-        sc.add(P.Y, dead && status == GBMC_STATUS_LIMIT, prob, GBMC_S_LIMIT, wgt);
+        sc.add(P.Y, valid, prob, GBMC_S_FLIGHT, wgt * flights, (unsigned long long)flights);
+        sc.add(P.Y, dead && leak_kind(status), prob, GBMC_S_LEAK, wgt, 1ull);
+        sc.add(P.Y, dead && status == GBMC_STATUS_LEAKED_FAR, prob, GBMC_S_LEAK_FAR, wgt, 1ull);
+        sc.add(P.Y, dead && status == GBMC_STATUS_LIMIT, prob, GBMC_S_LIMIT, wgt, 1ull);
         warp_append(P.Q.fq, &c->n_free, slot, dead);
-        warp_append(P.Q.lq[nxt], &c->n_lq[nxt], slot, valid && !dead && relook);
-        warp_append(P.Q.aq[nxt], &c->n_aq[nxt], slot, valid && !dead && !relook);
+        warp_append(P.Q.cq, &c->n_cq, slot, valid && route == 1);
+        warp_append(P.Q.lq[nxt], &c->n_lq[nxt], slot, valid && route == 2);
+        warp_append(P.Q.aq[nxt], &c->n_aq[nxt], slot, valid && route == 3);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        crossings += __shfl_xor_sync(kFull, crossings, o);
+        nflights += __shfl_xor_sync(kFull, nflights, o);
+    }
+    if ((threadIdx.x & 31) == 0 && nflights) {
+        atomicAdd(&c->st_cross, crossings);
+        atomicAdd(&c->st_flights, nflights);
     }
     sc.flush(P.Y);
 }
 
 // ---------------------------------------------------------------- collision event
-// Pick the nuclide, absorb or scatter elastically (isotropic in the CM
-// frame, target at rest), apply the energy cutoff.
 
 template <int PREC>
 __global__ void __launch_bounds__(256, 3) k_collision(Params P) {
@@ -632,60 +707,129 @@ __global__ void __launch_bounds__(256, 3) k_collision(Params P) {
         double wgt = 0.0;
         if (valid) {
             slot = P.Q.cq[idx];
-            Particle& pt = P.B.p[slot];
+            Particle pt = P.B.p[slot];
             prob = pt.prob;
             const DevProblem& pr = P.probs[prob];
             wgt = pt.wgt;
-            double E = pt.E;
-            int32_t mat = pt.mat;
             Stream r;
-            r.init(pr.seed, pr.key_hi, (uint64_t)(pr.first_id + (pt.gidx - pr.start)), pt.rj);
-            double target = r.next() * pt.st;
-            int32_t nuc = -1;
-            if (P.cum) {
-                if (PREC == GBMC_FP64)
-                    nuc = pick_from_sums(P.T, mat, (const double*)P.cum + slot * P.cum_stride, 1,
-                                         target);
-                else
-                    nuc = pick_from_sums(P.T, mat, (const float*)P.cum + slot * P.cum_stride, 1,
-                                         target);
-            }
-            if (nuc < 0) nuc = pick_nuclide(P.T, PREC, mat, E, target);
-            int32_t ncoll = pt.ncoll + 1;
-            double xa = r.next();
-            if (xa < __ldg(P.T.f_abs + nuc)) {
-                status = GBMC_STATUS_ABSORBED;
-            } else {
-                double mu = 2.0 * r.next() - 1.0;
-                double a, b;
-                double s = disk_pair(r, a, b);
-                double cphi = (a * a - b * b) / s;
-                double sphi = ((2.0 * a) * b) / s;
-                double E1, mul;
-                elastic(E, __ldg(P.T.awr + nuc), mu, E1, mul);
-                double u = pt.u, v = pt.v, w = pt.w;
-                rotate(u, v, w, mul, cphi, sphi);
-                pt.u = u; pt.v = v; pt.w = w;
-                E = E1;
-                pt.E = E;
-                if (E < pr.g.E_cut) status = GBMC_STATUS_CUTOFF;
-            }
-            int32_t nflt = pt.nflt;
-            if (!status && nflt >= GBMC_MAX_FLIGHTS) status = GBMC_STATUS_LIMIT;
-            pt.ncoll = ncoll;
-            pt.rj = r.j;
-            if (status)
-                record_death(P, slot, status, ncoll, nflt, r.j, E, pt.x, pt.y, pt.z);
+            stream_of(pr, pt, r);
+            status = collide<PREC>(P, pr, pt, slot, r);
+            P.B.p[slot] = pt;
+            if (status) record_death(P, pt, status);
         }
         bool dead = valid && status != 0;
-        sc.add(P.Y, valid, prob, GBMC_S_COLLISION, wgt);
-        sc.add(P.Y, dead && status == GBMC_STATUS_ABSORBED, prob, GBMC_S_ABSORPTION, wgt);
-        sc.add(P.Y, dead && status == GBMC_STATUS_CUTOFF, prob, GBMC_S_CUTOFF, wgt);
-        sc.add(P.Y, dead && status == GBMC_STATUS_LIMIT, prob, GBMC_S_LIMIT, wgt);
+        sc.add(P.Y, valid, prob, GBMC_S_COLLISION, wgt, 1ull);
+        sc.add(P.Y, dead && status == GBMC_STATUS_ABSORBED, prob, GBMC_S_ABSORPTION, wgt, 1ull);
+        sc.add(P.Y, dead && status == GBMC_STATUS_CUTOFF, prob, GBMC_S_CUTOFF, wgt, 1ull);
+        sc.add(P.Y, dead && status == GBMC_STATUS_LIMIT, prob, GBMC_S_LIMIT, wgt, 1ull);
         warp_append(P.Q.fq, &c->n_free, slot, dead);
         warp_append(P.Q.lq[nxt], &c->n_lq[nxt], slot, valid && !dead);
     }
     sc.flush(P.Y);
+}
+
+// ---------------------------------------------------------------- tail
+// Once the batch's source is exhausted and at most tail_max particles are
+// still in flight, an iteration of the event loop costs its launches, not
+// its work.  The loop then stops and this kernel finishes every remaining
+// history: one warp per particle, the lookups warp-cooperative (macro_warp),
+// every other step by lane 0, with the same step functions as the event
+// kernels.
+
+template <int PREC>
+__global__ void __launch_bounds__(256) k_tail(Params P) {
+    Ctl* c = P.ctl;
+    if (!c->tail) return;
+    int cur = c->cur;
+    int32_t nl = c->n_lq[cur], na = c->n_aq[cur];
+    int64_t n = (int64_t)nl + na;
+    int lane = threadIdx.x & 31;
+    int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long lookups = 0, micro = 0, flights = 0, crossings = 0, colls = 0;
+    for (int64_t idx = w0; idx < n; idx += nw) {
+        int32_t slot = idx < nl ? P.Q.lq[cur][idx] : P.Q.aq[cur][idx - nl];
+        bool need = idx < nl;
+        Particle pt = P.B.p[slot];
+        const DevProblem& pr = P.probs[pt.prob];
+        Stream r;
+        stream_of(pr, pt, r);
+        int status = 0;
+        unsigned long long nf = 0, nc = 0;   // this history's flights, collisions
+        double wf = 0.0, wc = 0.0;
+        for (;;) {
+            if (need) {
+                double st, sa;
+                void* cum = P.cum ? (PREC == GBMC_FP64
+                                         ? (void*)((double*)P.cum + slot * P.cum_stride)
+                                         : (void*)((float*)P.cum + slot * P.cum_stride))
+                                  : nullptr;
+                macro_warp<PREC>(P.T, pt.mat, pt.E, st, sa, cum, 1);
+                pt.st = st;
+                pt.sa = sa;
+                if (lane == 0) {
+                    ++lookups;
+                    micro += (unsigned long long)(__ldg(P.T.mat_off + pt.mat + 1) -
+                                                  __ldg(P.T.mat_off + pt.mat));
+                }
+            }
+            int action = 0;   // 0: fly on, 1: new lookup, 2: dead
+            if (lane == 0) {
+                bool col = fly(P, pr, pt, r);
+                ++nf;
+                wf += pt.wgt;
+                if (col) {
+                    ++nc;
+                    wc += pt.wgt;
+                    status = collide<PREC>(P, pr, pt, slot, r);
+                    action = status ? 2 : 1;
+                } else {
+                    bool relook;
+                    status = cross(pr.g, pt, relook);
+                    ++crossings;
+                    action = status ? 2 : (relook ? 1 : 0);
+                }
+            }
+            action = __shfl_sync(kFull, action, 0);
+            if (action == 2) break;
+            need = action == 1;
+            // every lane's lookup reads lane 0's energy and material
+            pt.E = __shfl_sync(kFull, pt.E, 0);
+            pt.mat = __shfl_sync(kFull, pt.mat, 0);
+        }
+        if (lane == 0) {
+            P.B.p[slot] = pt;
+            record_death(P, pt, status);
+            flights += nf;
+            colls += nc;
+            int b = pt.prob * GBMC_NSCAL;
+            atomicAdd(&P.Y.weights[b + GBMC_S_FLIGHT], wf);
+            atomicAdd(&P.Y.counts[b + GBMC_S_FLIGHT], nf);
+            if (nc) {
+                atomicAdd(&P.Y.weights[b + GBMC_S_COLLISION], wc);
+                atomicAdd(&P.Y.counts[b + GBMC_S_COLLISION], nc);
+            }
+            int kind = status == GBMC_STATUS_ABSORBED ? GBMC_S_ABSORPTION
+                     : status == GBMC_STATUS_CUTOFF   ? GBMC_S_CUTOFF
+                     : status == GBMC_STATUS_LIMIT    ? GBMC_S_LIMIT
+                                                      : GBMC_S_LEAK;
+            atomicAdd(&P.Y.weights[b + kind], pt.wgt);
+            atomicAdd(&P.Y.counts[b + kind], 1ull);
+            if (status == GBMC_STATUS_LEAKED_FAR) {
+                atomicAdd(&P.Y.weights[b + GBMC_S_LEAK_FAR], pt.wgt);
+                atomicAdd(&P.Y.counts[b + GBMC_S_LEAK_FAR], 1ull);
+            }
+            int32_t fi = atomicAdd(&c->n_free, 1);
+            P.Q.fq[fi] = slot;
+        }
+    }
+    if (lane == 0 && (lookups | flights)) {
+        atomicAdd(&c->st_lookups, lookups);
+        atomicAdd(&c->st_micro, micro);
+        atomicAdd(&c->st_flights, flights);
+        atomicAdd(&c->st_cross, crossings);
+        atomicAdd(&c->st_coll, colls);
+    }
 }
 
 // ---------------------------------------------------------------- standalone lookup
@@ -756,12 +900,19 @@ cudaError_t launch_iteration(const Params& P, const LaunchCfg& L, cudaStream_t s
         k_lookup<GBMC_FP64><<<L.grid_lookup, 256, 0, s>>>(P);
     else
         k_lookup<GBMC_FP32><<<L.grid_lookup, 256, 0, s>>>(P);
-    k_advance<<<L.grid, 256, 0, s>>>(P);
-    k_surface<<<L.grid, 256, 0, s>>>(P);
+    k_raytrace<<<L.grid, 256, 0, s>>>(P);
     if (P.precision == GBMC_FP64)
         k_collision<GBMC_FP64><<<L.grid, 256, 0, s>>>(P);
     else
         k_collision<GBMC_FP32><<<L.grid, 256, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tail(const Params& P, const LaunchCfg& L, cudaStream_t s) {
+    if (P.precision == GBMC_FP64)
+        k_tail<GBMC_FP64><<<L.grid_tail, 256, 0, s>>>(P);
+    else
+        k_tail<GBMC_FP32><<<L.grid_tail, 256, 0, s>>>(P);
     return cudaGetLastError();
 }
 
@@ -783,15 +934,13 @@ cudaError_t launch_iteration_timed(const Params& P, const LaunchCfg& L, cudaStre
     else
         k_lookup<GBMC_FP32><<<L.grid_lookup, 256, 0, s>>>(P);
     cudaEventRecord(ev[6], s);
-    k_advance<<<L.grid, 256, 0, s>>>(P);
+    k_raytrace<<<L.grid, 256, 0, s>>>(P);
     cudaEventRecord(ev[7], s);
-    k_surface<<<L.grid, 256, 0, s>>>(P);
-    cudaEventRecord(ev[8], s);
     if (P.precision == GBMC_FP64)
         k_collision<GBMC_FP64><<<L.grid, 256, 0, s>>>(P);
     else
         k_collision<GBMC_FP32><<<L.grid, 256, 0, s>>>(P);
-    cudaEventRecord(ev[9], s);
+    cudaEventRecord(ev[8], s);
     return cudaGetLastError();
 }
 

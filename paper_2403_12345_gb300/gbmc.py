@@ -34,8 +34,8 @@ EXPORTS = ["gbmc_default_options", "gbmc_create", "gbmc_destroy", "gbmc_last_err
            "gbmc_read_outcomes", "gbmc_read_stats", "gbmc_lookup_macro", "gbmc_last_run_ms",
            "gbmc_profile_problems", "gbmc_lookup_macro_noalloc", "gbmc_autotune"]
 NOALLOC_MAX_QUERIES = 1 << 20
-KERNEL_NAMES = ["plan", "source", "sort_keys", "sort_scan", "sort_scatter", "lookup", "advance",
-                "surface", "collision"]
+KERNEL_NAMES = ["plan", "source", "sort_keys", "sort_scan", "sort_scatter", "lookup", "raytrace",
+                "collision", "tail"]
 
 
 class GbmcError(RuntimeError):
@@ -49,7 +49,7 @@ class Options(C.Structure):
                 ("block_lookup", C.c_int32), ("block_event", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("max_iterations", C.c_int32),
                 ("sort_min", C.c_int32), ("warp_lookup_max", C.c_int32),
-                ("reserved", C.c_int32 * 6)]
+                ("tail_max", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class Geometry(C.Structure):
@@ -265,7 +265,8 @@ class Context:
     def profile_problems(self, probs, stream=None, trace_cap: int = 0):
         """Run with every kernel launched eagerly between CUDA events; returns
         {kernel: (total ms, launches)}, and with trace_cap > 0 also a
-        per-iteration trace (ms [iters, 9], queue lengths [iters, 4])."""
+        per-iteration trace (ms [iters, 9]; lookups, ray-traced particles,
+        collisions and particles in flight [iters, 4])."""
         arr = (Problem * len(probs))(*probs)
         kt = KernelTimes()
         tms = np.zeros((max(trace_cap, 1), 9))

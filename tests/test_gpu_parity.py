@@ -90,6 +90,17 @@ def test_thread_and_warp_lookup_modes_agree_with_oracle(precision):
         assert_tallies_close(g, ref)
 
 
+@pytest.mark.parametrize("tail_max", [-1, 4096, 1 << 22])
+def test_tail_kernel_threshold_does_not_change_outcomes(tail_max):
+    # -1: the event loop runs to the end; 1 << 22: once the source is
+    # exhausted every particle still in flight is finished by the tail kernel
+    p = synth.make_config(2, grid_scale=0.05)
+    g, ref, st = _parity(p, 40_000, max_in_flight=12_000, tail_max=tail_max, batch=2)
+    assert st["flights"] == ref["counts"][oracle.S_FLIGHT]
+    assert st["collisions"] == ref["counts"][oracle.S_COLLISION]
+    assert st["histories"] == 40_000
+
+
 def test_sort_does_not_change_outcomes():
     p = synth.make_config(2, grid_scale=0.05)
     res = []
