@@ -158,7 +158,9 @@ __global__ void k_plan(Params P) {
         c->n_aq[cur] = 0;
     }
     if (done) {
-        c->n_birth = 0;
+        // a tail-trigger iteration still births its particles (the source
+        // kernel runs before the loop exits); only a timeout drops them
+        if (!c->tail) c->n_birth = 0;
         c->lookup_n = 0;
         c->adv_n = 0;
     } else {
