@@ -128,7 +128,8 @@ struct Ctl {
     int32_t n_birth, free_base, lq_base, sorted;
     int32_t warp_lookup;         // this iteration's lookups run one warp per particle
     int32_t adv_n;               // particles the ray-trace kernel takes this iteration
-    int32_t tail, pad2;          // the loop stopped early: the tail kernel finishes
+    int32_t tail;                // the loop stopped early: the tail kernel finishes
+    int32_t adv_cursor;          // next ray-trace queue entry to hand out
     int64_t next_base;           // run index of the first particle born this iteration
     int64_t next, total;         // next unborn run index, particles in the run
     int32_t M;                   // in-flight cap of this run (<= capacity)

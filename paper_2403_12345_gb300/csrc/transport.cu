@@ -169,6 +169,7 @@ __global__ void k_plan(Params P) {
         c->adv_n = c->n_aq[cur] + c->lookup_n;
         c->n_aq[cur] = c->adv_n;
     }
+    c->adv_cursor = 0;
     c->sorted = (P.sort && c->lookup_n >= P.sort_min) ? 1 : 0;
     c->warp_lookup = c->lookup_n < P.warp_lookup_max ? 1 : 0;
     c->st_lookups += (unsigned long long)c->lookup_n;
@@ -619,14 +620,15 @@ __device__ __forceinline__ int leak_kind(int status) {
 // ---------------------------------------------------------------- ray-trace event
 // Advance (flight) and surface events of one particle, repeated while the
 // particle crosses surfaces that keep its material (lattice walls,
-// reflections): the paper's "ray trace" kernel.  Ends at a collision (to the
-// collision queue), a material change (to the lookup queue), a leak or the
-// flight limit (death), or after kStreamMax flights (back to the advance
-// queue of the next iteration).
+// reflections): the paper's "ray trace" kernel.  A particle leaves at a
+// collision (to the collision queue), a material change (to the lookup
+// queue), or a leak / the flight limit (death).
+//
+// Work-stealing: each lane flies its particle one flight per step; a lane
+// whose particle has left takes the next queue entry (one atomic per warp
+// per refill), so no lane idles behind a long-streaming neighbour.
 
-constexpr int kStreamMax = 64;
-
-__global__ void __launch_bounds__(256) k_raytrace(Params P) {
+__global__ void __launch_bounds__(256, 3) k_raytrace(Params P) {
     Ctl* c = P.ctl;
     int cur = c->cur;
     int32_t n = c->adv_n;
@@ -634,59 +636,80 @@ __global__ void __launch_bounds__(256) k_raytrace(Params P) {
     GBMC_BLOCK_SCALARS(sc, c->n_prob);
     const int32_t* q = P.Q.aq[cur];
     int nxt = 1 - cur;
+    int lane = threadIdx.x & 31;
     unsigned long long crossings = 0, nflights = 0;
-    GBMC_WARP_LOOP(idx, valid, n) {
-        int32_t slot = 0;
-        int prob = 0, status = 0, route = 0;   // route 1: collision, 2: lookup, 3: advance
-        double wgt = 0.0;
-        int32_t flights = 0;
-        if (valid) {
-            slot = q[idx];
-            Particle pt = P.B.p[slot];
-            prob = pt.prob;
-            const DevProblem& pr = P.probs[prob];
-            wgt = pt.wgt;
-            Stream r;
-            stream_of(pr, pt, r);
-            for (;;) {
-                bool col = fly(P, pr, pt, r);
-                ++flights;
-                if (col) {
-                    route = 1;
-                    break;
+    Particle pt;
+    int32_t slot = 0;
+    Stream r;
+    int32_t flights = 0;
+    bool have = false, exhausted = false;
+    for (;;) {
+        bool want = !have && !exhausted;
+        unsigned m = __ballot_sync(kFull, want);
+        if (m) {
+            int leader = __ffs(m) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(&c->adv_cursor, __popc(m));
+            base = __shfl_sync(kFull, base, leader);
+            if (want) {
+                int32_t idx = base + __popc(m & lanemask_lt());
+                if (idx < n) {
+                    slot = q[idx];
+                    pt = P.B.p[slot];
+                    stream_of(P.probs[pt.prob], pt, r);
+                    flights = 0;
+                    have = true;
+                } else {
+                    exhausted = true;
                 }
+            }
+        }
+        if (!__any_sync(kFull, have)) break;
+        int status = 0, route = 0;   // route 1: collision, 2: lookup
+        bool fin = false;
+        if (have) {
+            const DevProblem& pr = P.probs[pt.prob];
+            bool col = fly(P, pr, pt, r);
+            ++flights;
+            if (col) {
+                route = 1;
+                fin = true;
+            } else {
                 bool relook;
                 status = cross(pr.g, pt, relook);
                 ++crossings;
-                if (status) break;
-                if (relook) {
+                if (status) {
+                    fin = true;
+                } else if (relook) {
                     route = 2;
-                    break;
-                }
-                if (flights >= kStreamMax) {
-                    route = 3;
-                    break;
+                    fin = true;
                 }
             }
-            P.B.p[slot] = pt;
-            if (status) record_death(P, pt, status);
-            nflights += (unsigned long long)flights;
+            if (fin) {
+                P.B.p[slot] = pt;
+                if (status) record_death(P, pt, status);
+                nflights += (unsigned long long)flights;
+            }
         }
-        bool dead = valid && status != 0;
-        sc.add(P.Y, valid, prob, GBMC_S_FLIGHT, wgt * flights, (unsigned long long)flights);
-        sc.add(P.Y, dead && leak_kind(status), prob, GBMC_S_LEAK, wgt, 1ull);
-        sc.add(P.Y, dead && status == GBMC_STATUS_LEAKED_FAR, prob, GBMC_S_LEAK_FAR, wgt, 1ull);
-        sc.add(P.Y, dead && status == GBMC_STATUS_LIMIT, prob, GBMC_S_LIMIT, wgt, 1ull);
-        warp_append(P.Q.fq, &c->n_free, slot, dead);
-        warp_append(P.Q.cq, &c->n_cq, slot, valid && route == 1);
-        warp_append(P.Q.lq[nxt], &c->n_lq[nxt], slot, valid && route == 2);
-        warp_append(P.Q.aq[nxt], &c->n_aq[nxt], slot, valid && route == 3);
+        if (__any_sync(kFull, fin)) {
+            bool dead = fin && status != 0;
+            int prob = fin ? pt.prob : 0;
+            double wgt = fin ? pt.wgt : 0.0;
+            sc.add(P.Y, fin, prob, GBMC_S_FLIGHT, wgt * flights, (unsigned long long)flights);
+            sc.add(P.Y, dead && leak_kind(status), prob, GBMC_S_LEAK, wgt, 1ull);
+            sc.add(P.Y, dead && status == GBMC_STATUS_LEAKED_FAR, prob, GBMC_S_LEAK_FAR, wgt, 1ull);
+            sc.add(P.Y, dead && status == GBMC_STATUS_LIMIT, prob, GBMC_S_LIMIT, wgt, 1ull);
+            warp_append(P.Q.fq, &c->n_free, slot, dead);
+            warp_append(P.Q.cq, &c->n_cq, slot, fin && route == 1);
+            warp_append(P.Q.lq[nxt], &c->n_lq[nxt], slot, fin && route == 2);
+            if (fin) have = false;
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         crossings += __shfl_xor_sync(kFull, crossings, o);
         nflights += __shfl_xor_sync(kFull, nflights, o);
     }
-    if ((threadIdx.x & 31) == 0 && nflights) {
+    if (lane == 0 && nflights) {
         atomicAdd(&c->st_cross, crossings);
         atomicAdd(&c->st_flights, nflights);
     }
