@@ -16,9 +16,13 @@ import numpy as np
 
 from .build import build as _build
 
-STATUS_ALIVE, STATUS_ABSORBED, STATUS_LEAKED, STATUS_CUTOFF, STATUS_LIMIT, STATUS_LEAKED_FAR = range(6)
-S_COLLISION, S_ABSORPTION, S_LEAK, S_CUTOFF, S_LIMIT, S_LEAK_FAR, S_FLIGHT, S_HISTORY = range(8)
-NSCAL = 8
+STATUS_ALIVE, STATUS_ABSORBED, STATUS_LEAKED, STATUS_CUTOFF, STATUS_LIMIT, STATUS_LEAKED_FAR, \
+    STATUS_ROULETTE = range(7)
+S_COLLISION, S_ABSORPTION, S_LEAK, S_CUTOFF, S_LIMIT, S_LEAK_FAR, S_FLIGHT, S_HISTORY, S_SPLIT, \
+    S_ROULETTE = range(10)
+NSCAL = 10
+MLP_HIDDEN = 64
+MLP_NPARAM = 64 * 4 + 64 + 64 * 64 + 64 + 64 + 1
 MAX_FLIGHTS = 100000
 
 _P = C.POINTER
@@ -36,7 +40,8 @@ class _Problem(C.Structure):
         ("height", C.c_double), ("mat_pin", C.c_int32), ("mat_mod", C.c_int32),
         ("bc_side", C.c_int32), ("bc_z", C.c_int32), ("n_layers", C.c_int32),
         ("layer_dx", C.c_double), ("n_first", C.c_int32), ("mat_a", C.c_int32),
-        ("mat_b", C.c_int32),
+        ("mat_b", C.c_int32), ("ww_lower", _P(C.c_double)), ("ww_ratio", C.c_double),
+        ("ww_survival", C.c_double), ("ww_max_split", C.c_int32),
     ]
 
 
@@ -76,6 +81,11 @@ def lib():
         L.or_run.argtypes = [_P(_Problem), C.c_uint64, C.c_uint64, C.c_int64, C.c_int64,
                              C.c_int, _P(_Result)]
         L.or_run.restype = C.c_int
+        L.or_mlp_nparam.restype = C.c_int
+        L.or_mlp_forward.argtypes = [_P(C.c_double), _P(C.c_double), C.c_int64, _P(C.c_double)]
+        L.or_mlp_grad.argtypes = [_P(C.c_double), _P(C.c_double), _P(C.c_double),
+                                  _P(C.c_double), C.c_int64, _P(C.c_double)]
+        L.or_mlp_grad.restype = C.c_double
         _lib = L
     return _lib
 
@@ -125,7 +135,7 @@ def rotate(u, v, w, mu, cphi, sphi):
 class _Bound:
     """Keeps the numpy arrays alive while the C structure points at them."""
 
-    def __init__(self, prob, geom_index: int = 0, precision=None):
+    def __init__(self, prob, geom_index: int = 0, precision=None, ww=None):
         g = prob.geoms[geom_index]
         self.arrs = dict(
             grid_off=np.ascontiguousarray(prob.grid_off, dtype=np.int64),
@@ -158,6 +168,13 @@ class _Bound:
             setattr(p, name, int(getattr(g, name)))
         for name in ("E0", "E_cut", "pitch", "radius", "height", "layer_dx"):
             setattr(p, name, float(getattr(g, name)))
+        if ww is not None:
+            lower, ratio, survival, max_split = ww
+            self.ww = np.ascontiguousarray(lower, dtype=np.float64).reshape(-1)
+            if self.ww.size != g.n_cells() * p.n_bins:
+                raise ValueError("weight-window table must be [n_cells, n_bins]")
+            p.ww_lower = _ptr(self.ww, C.c_double)
+            p.ww_ratio, p.ww_survival, p.ww_max_split = float(ratio), float(survival), int(max_split)
         self.p = p
         self.n_cells = g.n_cells()
         self.n_bins = p.n_bins
@@ -186,10 +203,13 @@ def key_hi(problem_index: int, batch: int) -> int:
 
 
 def run(prob, seed: int, batch: int = 0, first_id: int = 0, n=None, geom_index: int = 0,
-        problem_index: int = 0, threads=None, precision=None):
+        problem_index: int = 0, threads=None, precision=None, ww=None):
     """Histories [first_id, first_id + n) of one batch; returns a dict with
-    per-particle outcomes, the flux tally [n_cells, n_bins] and the scalars."""
-    b = _Bound(prob, geom_index, precision)
+    per-particle outcomes, the flux tally [n_cells, n_bins] and the scalars.
+    ww = (lower [n_cells, n_bins], ratio, survival, max_split) turns on
+    weight windows; split copies are transported depth first and scored in
+    the tallies (the outcomes are the primary histories')."""
+    b = _Bound(prob, geom_index, precision, ww)
     if n is None:
         n = prob.n_particles[geom_index]
     n = int(n)
@@ -212,6 +232,8 @@ def run(prob, seed: int, batch: int = 0, first_id: int = 0, n=None, geom_index: 
     r.counts = _ptr(out["counts"], C.c_int64)
     rc = lib().or_run(C.byref(b.p), int(seed) & 0xFFFFFFFFFFFFFFFF,
                       key_hi(problem_index, batch), int(first_id), n, int(threads), C.byref(r))
+    if rc == -2:
+        raise RuntimeError("oracle split stack overflow (more than 2^24 pending copies)")
     if rc != 0:
         raise MemoryError("oracle run failed")
     return out
@@ -229,3 +251,24 @@ def birth_state(prob, seed: int, id_: int, batch: int = 0, problem_index: int = 
     L.or_birth_state(C.byref(b.p), int(seed), key_hi(problem_index, batch), int(id_),
                      _ptr(st, C.c_double), _ptr(cell, C.c_int32))
     return st, cell
+
+
+def mlp_forward(params, x):
+    """Binary64 forward pass of the importance network on features x [n, 4]."""
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 4)
+    out = np.zeros(len(x))
+    lib().or_mlp_forward(_ptr(p, C.c_double), _ptr(x, C.c_double), len(x), _ptr(out, C.c_double))
+    return out
+
+
+def mlp_grad(params, x, y, w):
+    """Weighted MSE loss and its gradient with respect to the parameters."""
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 4)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    g = np.zeros(MLP_NPARAM)
+    loss = lib().or_mlp_grad(_ptr(p, C.c_double), _ptr(x, C.c_double), _ptr(y, C.c_double),
+                             _ptr(w, C.c_double), len(x), _ptr(g, C.c_double))
+    return loss, g

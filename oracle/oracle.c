@@ -581,23 +581,93 @@ static int32_t ebin(const or_problem *P, double E)
     return (int32_t)or_search(P->edges, (int64_t)P->n_bins + 1, E);
 }
 
-static void history(const or_problem *P, const tables_t *T, uint64_t seed, uint64_t key_hi,
-                    int64_t id, acc_t *A, particle_t *out, uint32_t *ndraw)
-{
-    rng_t r;
-    rng_init(&r, seed, key_hi, (uint64_t)id);
+/* A split's copies: same state, weight w/k, a new history with its own
+ * stream.  Copy j of a split at draw position rj of history `hid` has the id
+ * given by word 0 of one Philox block of (hid, rj, j, SPLIT_TAG) under the
+ * batch key, with the top bit set (primary ids stay below 2^63). */
+#define OR_SPLIT_TAG 0x5EED0C41DULL
+
+typedef struct {
     particle_t p;
-    birth(P, &r, &p);
-    A->counts[OR_S_HISTORY] += 1;
-    kadd(&A->ws[OR_S_HISTORY], &A->wc[OR_S_HISTORY], p.wgt);
-    int need_lookup = 1;
+    uint64_t hid;
+} child_t;
+
+typedef struct {
+    child_t *v;
+    int64_t n, cap;
+    int overflow;
+} stack_t_;
+
+static void push_child(stack_t_ *S, const particle_t *p, uint64_t hid)
+{
+    if (S->n == S->cap) {
+        int64_t nc = S->cap ? 2 * S->cap : 64;
+        if (nc > ((int64_t)1 << 24)) {
+            S->overflow = 1;
+            return;
+        }
+        child_t *nv = (child_t *)realloc(S->v, sizeof(child_t) * (size_t)nc);
+        if (!nv) {
+            S->overflow = 1;
+            return;
+        }
+        S->v = nv;
+        S->cap = nc;
+    }
+    S->v[S->n].p = *p;
+    S->v[S->n].hid = hid;
+    S->n += 1;
+}
+
+/* Weight-window check at the particle's (cell, energy bin): split above the
+ * window, Russian roulette below it (survivors take the survival weight). */
+static void ww_check(const or_problem *P, particle_t *p, rng_t *r, stack_t_ *S, acc_t *A)
+{
+    int64_t k = (int64_t)cell_of(P, p) * P->n_bins + ebin(P, p->E);
+    double wl = P->ww_lower[k];
+    if (!(wl > 0.0)) return;
+    double wu = wl * P->ww_ratio;
+    double ws = wl * P->ww_survival;
+    if (p->wgt > wu) {
+        int32_t n = (int32_t)floor(p->wgt / ws);
+        if (n > P->ww_max_split) n = P->ww_max_split;
+        if (n < 2) return;
+        double wc = p->wgt / (double)n;
+        p->wgt = wc;
+        for (int32_t j = 1; j < n; ++j) {
+            uint64_t ctr[4] = {r->id, r->j, (uint64_t)j, OR_SPLIT_TAG};
+            uint64_t out[4];
+            or_philox4x64_10(ctr, r->key, out);
+            particle_t c = *p;
+            c.n_coll = 0;
+            c.n_flights = 0;
+            push_child(S, &c, out[0] | 0x8000000000000000ULL);
+            score(A, OR_S_SPLIT, wc);
+        }
+    } else if (p->wgt < wl) {
+        double xi = rng_next(r);
+        if (xi < p->wgt / ws) {
+            p->wgt = ws;
+        } else {
+            score(A, OR_S_ROULETTE, p->wgt);
+            p->status = OR_STATUS_ROULETTE;
+        }
+    }
+}
+
+/* One history from the given state until death; returns its final state and
+ * the number of draws taken from its stream. */
+static void transport(const or_problem *P, const tables_t *T, rng_t *r, particle_t *pp,
+                      int need_lookup, acc_t *A, stack_t_ *S)
+{
+    particle_t p = *pp;
     const int32_t nb = P->n_bins;
     while (p.status == OR_STATUS_ALIVE) {
         if (need_lookup) {
             macro_xs(T, p.mat, p.E, &p.st, &p.sa);
             need_lookup = 0;
         }
-        double xi = rng_next(&r);
+        double xi = rng_next(r);
         double dcol = (0.0 - or_log(xi)) / p.st;
         double dbnd;
         int surf;
@@ -616,18 +686,18 @@ static void history(const or_problem *P, const tables_t *T, uint64_t seed, uint6
         p.n_flights += 1;
         score(A, OR_S_FLIGHT, p.wgt);
         if (collide) {
-            double target = rng_next(&r) * p.st;
+            double target = rng_next(r) * p.st;
             int32_t nuc = pick_nuclide(T, p.mat, p.E, target);
             p.n_coll += 1;
             score(A, OR_S_COLLISION, p.wgt);
-            double xa = rng_next(&r);
+            double xa = rng_next(r);
             if (xa < P->f_abs[nuc]) {
                 p.status = OR_STATUS_ABSORBED;
                 score(A, OR_S_ABSORPTION, p.wgt);
             } else {
-                double mu = 2.0 * rng_next(&r) - 1.0;
+                double mu = 2.0 * rng_next(r) - 1.0;
                 double a, b;
-                double s = disk_pair(&r, &a, &b);
+                double s = disk_pair(r, &a, &b);
                 double cphi = (a * a - b * b) / s;
                 double sphi = ((2.0 * a) * b) / s;
                 double E1, mul;
@@ -639,23 +709,51 @@ static void history(const or_problem *P, const tables_t *T, uint64_t seed, uint6
                     score(A, OR_S_CUTOFF, p.wgt);
                 } else {
                     need_lookup = 1;
+                    if (P->ww_lower) ww_check(P, &p, r, S, A);
                 }
             }
         } else {
-            need_lookup = cross_surface(P, &p, surf);
+            int changed = cross_surface(P, &p, surf);
             if (p.status == OR_STATUS_LEAKED) score(A, OR_S_LEAK, p.wgt);
             if (p.status == OR_STATUS_LEAKED_FAR) {
                 score(A, OR_S_LEAK, p.wgt);
                 score(A, OR_S_LEAK_FAR, p.wgt);
             }
+            need_lookup = need_lookup || changed;
+            if (p.status == OR_STATUS_ALIVE && P->ww_lower && P->kind == 2)
+                ww_check(P, &p, r, S, A);
         }
         if (p.status == OR_STATUS_ALIVE && p.n_flights >= OR_MAX_FLIGHTS) {
             p.status = OR_STATUS_LIMIT;
             score(A, OR_S_LIMIT, p.wgt);
         }
     }
+    *pp = p;
+}
+
+/* History `id` of the batch and, depth first, every copy its splits made. */
+static int history(const or_problem *P, const tables_t *T, uint64_t seed, uint64_t key_hi,
+                   int64_t id, acc_t *A, particle_t *out, uint32_t *ndraw)
+{
+    rng_t r;
+    rng_init(&r, seed, key_hi, (uint64_t)id);
+    particle_t p;
+    birth(P, &r, &p);
+    A->counts[OR_S_HISTORY] += 1;
+    kadd(&A->ws[OR_S_HISTORY], &A->wc[OR_S_HISTORY], p.wgt);
+    stack_t_ S = {NULL, 0, 0, 0};
+    transport(P, T, &r, &p, 1, A, &S);
     *out = p;
     *ndraw = r.j;
+    while (S.n > 0 && !S.overflow) {
+        child_t ch = S.v[--S.n];
+        rng_t rc;
+        rng_init(&rc, seed, key_hi, ch.hid);
+        transport(P, T, &rc, &ch.p, 1, A, &S);
+    }
+    int bad = S.overflow;
+    free(S.v);
+    return bad;
 }
 
 /* exported for tests: the birth state of particle `id` (x,y,z,u,v,w,E and
@@ -696,6 +794,7 @@ int or_run(const or_problem *P, uint64_t seed, uint64_t key_hi, int64_t first_id
         acc[t].fc = (double *)calloc((size_t)nf, sizeof(double));
         if (!acc[t].fs || !acc[t].fc) return -1;
     }
+    int overflow = 0;
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 16) num_threads(n_threads)
 #endif
@@ -706,7 +805,7 @@ int or_run(const or_problem *P, uint64_t seed, uint64_t key_hi, int64_t first_id
 #endif
         particle_t p;
         uint32_t nd;
-        history(P, &T, seed, key_hi, first_id + k, &acc[t], &p, &nd);
+        if (history(P, &T, seed, key_hi, first_id + k, &acc[t], &p, &nd)) overflow = 1;
         if (R->n_coll) R->n_coll[k] = p.n_coll;
         if (R->status) R->status[k] = (int8_t)p.status;
         if (R->n_flights) R->n_flights[k] = p.n_flights;
@@ -745,5 +844,84 @@ int or_run(const or_problem *P, uint64_t seed, uint64_t key_hi, int64_t first_id
     free(acc);
     free(T.ef);
     free(T.sf);
-    return 0;
+    return overflow ? -2 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Importance network (binary64 reference of the GPU kernels).              */
+/* 4 -> 64 -> 64 -> 1, ReLU after the two hidden layers.  Parameters, in    */
+/* this order: W1[64][4], b1[64], W2[64][64] (row = output unit), b2[64],   */
+/* W3[64], b3.                                                              */
+/* ------------------------------------------------------------------------ */
+#define OR_H 64
+#define OR_NPARAM (OR_H * 4 + OR_H + OR_H * OR_H + OR_H + OR_H + 1)
+
+int or_mlp_nparam(void) { return OR_NPARAM; }
+
+static void mlp_one(const double *P, const double *x, double *z1, double *h1, double *z2,
+                    double *h2, double *out)
+{
+    const double *W1 = P, *b1 = W1 + OR_H * 4, *W2 = b1 + OR_H, *b2 = W2 + OR_H * OR_H,
+                 *W3 = b2 + OR_H, *b3 = W3 + OR_H;
+    for (int o = 0; o < OR_H; ++o) {
+        double s = b1[o];
+        for (int i = 0; i < 4; ++i) s += W1[o * 4 + i] * x[i];
+        z1[o] = s;
+        h1[o] = s > 0.0 ? s : 0.0;
+    }
+    for (int o = 0; o < OR_H; ++o) {
+        double s = b2[o];
+        for (int i = 0; i < OR_H; ++i) s += W2[o * OR_H + i] * h1[i];
+        z2[o] = s;
+        h2[o] = s > 0.0 ? s : 0.0;
+    }
+    double s = b3[0];
+    for (int i = 0; i < OR_H; ++i) s += W3[i] * h2[i];
+    *out = s;
+}
+
+void or_mlp_forward(const double *params, const double *x, int64_t n, double *out)
+{
+    double z1[OR_H], h1[OR_H], z2[OR_H], h2[OR_H];
+    for (int64_t k = 0; k < n; ++k) mlp_one(params, x + 4 * k, z1, h1, z2, h2, &out[k]);
+}
+
+/* Loss L = sum_k w_k (out_k - y_k)^2 / sum_k w_k and its gradient dL/dparams
+ * (same layout as params) by back-propagation. */
+double or_mlp_grad(const double *params, const double *x, const double *y, const double *w,
+                   int64_t n, double *grad)
+{
+    const double *W2 = params + OR_H * 4 + OR_H, *W3 = W2 + OR_H * OR_H + OR_H;
+    double *gW1 = grad, *gb1 = gW1 + OR_H * 4, *gW2 = gb1 + OR_H, *gb2 = gW2 + OR_H * OR_H,
+           *gW3 = gb2 + OR_H, *gb3 = gW3 + OR_H;
+    memset(grad, 0, sizeof(double) * OR_NPARAM);
+    double wsum = 0.0, loss = 0.0;
+    for (int64_t k = 0; k < n; ++k) wsum += w[k];
+    double z1[OR_H], h1[OR_H], z2[OR_H], h2[OR_H], d2[OR_H], d1[OR_H], out;
+    for (int64_t k = 0; k < n; ++k) {
+        const double *xk = x + 4 * k;
+        mlp_one(params, xk, z1, h1, z2, h2, &out);
+        double e = out - y[k];
+        loss += w[k] * e * e;
+        double dout = 2.0 * w[k] * e / wsum;
+        gb3[0] += dout;
+        for (int i = 0; i < OR_H; ++i) {
+            gW3[i] += dout * h2[i];
+            d2[i] = z2[i] > 0.0 ? dout * W3[i] : 0.0;
+        }
+        for (int o = 0; o < OR_H; ++o) {
+            gb2[o] += d2[o];
+            for (int i = 0; i < OR_H; ++i) gW2[o * OR_H + i] += d2[o] * h1[i];
+        }
+        for (int i = 0; i < OR_H; ++i) {
+            double s = 0.0;
+            for (int o = 0; o < OR_H; ++o) s += W2[o * OR_H + i] * d2[o];
+            d1[i] = z1[i] > 0.0 ? s : 0.0;
+        }
+        for (int o = 0; o < OR_H; ++o) {
+            gb1[o] += d1[o];
+            for (int i = 0; i < 4; ++i) gW1[o * 4 + i] += d1[o] * xk[i];
+        }
+    }
+    return loss / wsum;
 }

@@ -23,6 +23,7 @@
 #define OR_STATUS_CUTOFF 3
 #define OR_STATUS_LIMIT 4
 #define OR_STATUS_LEAKED_FAR 5
+#define OR_STATUS_ROULETTE 6
 
 /* scalar tally slots */
 #define OR_S_COLLISION 0
@@ -33,7 +34,9 @@
 #define OR_S_LEAK_FAR 5
 #define OR_S_FLIGHT 6
 #define OR_S_HISTORY 7
-#define OR_NSCAL 8
+#define OR_S_SPLIT 8
+#define OR_S_ROULETTE 9
+#define OR_NSCAL 10
 
 #define OR_MAX_FLIGHTS 100000
 
@@ -62,6 +65,13 @@ typedef struct {
     int32_t n_layers;
     double layer_dx;
     int32_t n_first, mat_a, mat_b;
+    /* weight windows (NULL: analog): lower bound per (cell, energy bin);
+     * upper = ratio * lower, survival = survival * lower; at most max_split
+     * copies per split.  Checked after every scatter and every slab-layer
+     * crossing. */
+    const double *ww_lower;   /* [n_cells * n_bins]; <= 0 means no window */
+    double ww_ratio, ww_survival;
+    int32_t ww_max_split;
 } or_problem;
 
 typedef struct {
