@@ -68,6 +68,7 @@ extern "C" {
 #define GBMC_STATUS_CUTOFF 3     /* energy fell below E_cut */
 #define GBMC_STATUS_LIMIT 4      /* GBMC_MAX_FLIGHTS flights reached */
 #define GBMC_STATUS_LEAKED_FAR 5 /* slab: left through x = n_layers dx */
+#define GBMC_STATUS_ROULETTE 6   /* killed by weight-window roulette */
 #define GBMC_MAX_FLIGHTS 100000
 
 /* ---- scalar tally slots (counts are int64, weights binary64) ----------- */
@@ -79,7 +80,9 @@ extern "C" {
 #define GBMC_S_LEAK_FAR 5
 #define GBMC_S_FLIGHT 6
 #define GBMC_S_HISTORY 7
-#define GBMC_NSCAL 8
+#define GBMC_S_SPLIT 8      /* copies made by weight-window splits (weight they carry) */
+#define GBMC_S_ROULETTE 9   /* histories ended by roulette (weight before) */
+#define GBMC_NSCAL 10
 
 typedef struct gbmc_ctx gbmc_ctx;
 
@@ -270,6 +273,26 @@ int gbmc_lookup_macro(gbmc_ctx *ctx, int32_t precision, const double *d_E,
 int gbmc_profile_problems(gbmc_ctx *ctx, int32_t n_prob, const gbmc_problem *probs,
                           void *stream, gbmc_kernel_times *out, int32_t trace_cap,
                           double *trace_ms, int32_t *trace_queues, int32_t *trace_len);
+
+/* Weight windows for problem slot 0 of the following runs (the variance
+ * reduction the learned importance map drives; the paper has no counterpart
+ * beyond its Monte Carlo method).  lower [n_cells * n_bins], cell-major like
+ * the flux tally, gives the window's lower weight bound per (cell, energy
+ * bin); 0 means no window there.  Upper bound = ratio * lower, survival
+ * weight = survival * lower (need survival >= 1, ratio >= 2 * survival).
+ * Checked after every scatter and, in a slab, after every layer crossing:
+ * above the window a particle splits into min(floor(w / w_s), max_split)
+ * copies of equal weight; below it, Russian roulette keeps it with weight
+ * w_s with probability w / w_s (else status GBMC_STATUS_ROULETTE).  Copies
+ * are new histories with their own streams (ids from the parent's stream
+ * position); they are tallied but have no outcome record.  While windows
+ * are set, half of the bank is kept free for copies and the tail kernel is
+ * not used.  Host array copied. */
+int gbmc_set_weight_windows(gbmc_ctx *ctx, int32_t n_cells, int32_t n_bins, const double *lower,
+                            double ratio, double survival, int32_t max_split);
+
+/* Back to analog transport. */
+int gbmc_clear_weight_windows(gbmc_ctx *ctx);
 
 /* Result of gbmc_autotune. */
 typedef struct {

@@ -112,6 +112,15 @@ struct gbmc_ctx {
     size_t cum_bytes = 0;
     int32_t max_nuc_per_mat = 0;
 
+    // weight windows (problem slot 0) and the split-copy buffer
+    bool ww_on = false;
+    int32_t ww_cells = 0;
+    double ww_ratio = 5.0, ww_survival = 2.5;
+    int32_t ww_max_split = 10;
+    double* d_ww = nullptr;
+    Particle* d_child = nullptr;
+    int32_t child_cap = 0;
+
     // standalone-lookup scratch
     int64_t q_cap = 0;
     int32_t* q_perm = nullptr;
@@ -367,6 +376,14 @@ Params make_params(gbmc_ctx* c) {
     sort_params(c, P);
     P.cum = c->d_cum;
     P.cum_stride = c->d_cum ? cum_row(c) : 0;
+    if (c->ww_on) {
+        P.ww = c->d_ww;
+        P.ww_ratio = c->ww_ratio;
+        P.ww_survival = c->ww_survival;
+        P.ww_max_split = c->ww_max_split;
+        P.child = c->d_child;
+        P.child_cap = c->child_cap;
+    }
     return P;
 }
 
@@ -642,6 +659,7 @@ int gbmc_destroy(gbmc_ctx* c) {
     dfree(c->d_nx64); dfree(c->d_nx32); dfree(c->d_idx64); dfree(c->d_idx32);
     dfree(c->d_mat_off); dfree(c->d_nuc_id); dfree(c->d_density); dfree(c->d_density32);
     dfree(c->d_edges); dfree(c->d_probs); dfree(c->d_ctl);
+    dfree(c->d_ww); dfree(c->d_child);
     if (c->d_cum) { cudaDeviceSynchronize(); cudaFree(c->d_cum); }
     dfree(c->q_perm); dfree(c->q_keys); dfree(c->q_hist); dfree(c->q_cursor); dfree(c->q_btot);
     if (c->h_probs) cudaFreeHost(c->h_probs);
@@ -870,6 +888,16 @@ int prepare_run(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, cudaStre
     int32_t M = (int32_t)M64;
     if ((rc = ensure_bank(c, M))) return rc;
     if ((rc = ensure_cum(c))) return rc;
+    if (c->ww_on) {
+        if (cells[0] != c->ww_cells)
+            return fail(c, GBMC_ERR_INVALID_ARG,
+                        "weight windows cover %d cells, problem slot 0 has %d", c->ww_cells, cells[0]);
+        if (c->child_cap < c->capacity) {
+            if ((rc = dalloc(c, &c->d_child, (size_t)c->capacity))) return rc;
+            c->child_cap = c->capacity;
+            c->graph_valid = false;
+        }
+    }
     if ((rc = ensure_outcomes(c, total > 0 ? total : 1))) return rc;
     if ((rc = ensure_tallies(c, cells, s))) return rc;
     if (n_prob > c->probs_cap) {
@@ -907,6 +935,7 @@ int prepare_run(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, cudaStre
     k.total = total;
     k.M = M;
     k.n_prob = n_prob;
+    k.birth_reserve = c->ww_on ? M / 2 : 0;
     CK(cudaMemcpyAsync(c->d_probs, c->h_probs, sizeof(DevProblem) * n_prob, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c->d_ctl, c->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
     CK(cudaEventRecord(c->staged, s));
@@ -1131,6 +1160,44 @@ int gbmc_lookup_macro(gbmc_ctx* c, int32_t precision, const double* d_E, const i
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Weight windows.
+
+extern "C" int gbmc_set_weight_windows(gbmc_ctx* c, int32_t n_cells, int32_t n_bins,
+                                       const double* lower, double ratio, double survival,
+                                       int32_t max_split) {
+    if (!c) return GBMC_ERR_INVALID_ARG;
+    if (!c->n_bins) return fail(c, GBMC_ERR_NOT_INITIALIZED, "set the tally bins first");
+    if (n_cells < 1 || n_bins != c->n_bins || !lower)
+        return fail(c, GBMC_ERR_INVALID_ARG, "need n_cells >= 1, n_bins = the tally's bins, lower");
+    if (!(survival >= 1.0) || !(ratio >= 2.0 * survival) || !std::isfinite(ratio))
+        return fail(c, GBMC_ERR_INVALID_ARG, "need survival >= 1 and ratio >= 2 * survival");
+    if (max_split < 2 || max_split > 1000)
+        return fail(c, GBMC_ERR_INVALID_ARG, "max_split must be in [2, 1000]");
+    int64_t n = (int64_t)n_cells * n_bins;
+    for (int64_t k = 0; k < n; ++k)
+        if (!(lower[k] >= 0.0) || !std::isfinite(lower[k]))
+            return fail(c, GBMC_ERR_INVALID_ARG, "window bounds must be finite and >= 0");
+    int rc = set_device(c);
+    if (rc) return rc;
+    if (c->ran) CK(cudaStreamSynchronize(c->last_stream));
+    if ((rc = upload(c, &c->d_ww, lower, (size_t)n))) return rc;
+    c->ww_on = true;
+    c->ww_cells = n_cells;
+    c->ww_ratio = ratio;
+    c->ww_survival = survival;
+    c->ww_max_split = max_split;
+    c->graph_valid = false;
+    return GBMC_OK;
+}
+
+extern "C" int gbmc_clear_weight_windows(gbmc_ctx* c) {
+    if (!c) return GBMC_ERR_INVALID_ARG;
+    if (c->ww_on) c->graph_valid = false;
+    c->ww_on = false;
+    return GBMC_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Autotuner: coordinate descent over launch / queue settings, each candidate

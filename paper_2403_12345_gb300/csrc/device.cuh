@@ -76,7 +76,7 @@ struct alignas(128) Particle {
     double x, y, z, wgt;
     // sector 2
     double u, v, w;
-    int64_t gidx;        // index of the particle in the run
+    int64_t gidx;        // index of the particle in the run (-1: a split copy)
     // sector 3
     int32_t ci, cj;      // lattice cell (slab: layer in ci)
     int32_t ncoll, nflt; // collisions, flights so far
@@ -84,7 +84,7 @@ struct alignas(128) Particle {
     uint8_t inside;      // inside the pin cylinder (lattice)
     uint8_t surf;        // surface reached by the last flight
     uint8_t pad8[2];
-    int32_t pad[2];
+    uint64_t hid;        // history id: counter word 0 of the particle's stream
 };
 static_assert(sizeof(Particle) == 128, "one particle per 128-byte line");
 
@@ -130,6 +130,10 @@ struct Ctl {
     int32_t adv_n;               // particles the ray-trace kernel takes this iteration
     int32_t tail;                // the loop stopped early: the tail kernel finishes
     int32_t adv_cursor;          // next ray-trace queue entry to hand out
+    int32_t n_child;             // split copies waiting to be born
+    int32_t n_birth_child;       // copies born this iteration (the first births)
+    int32_t child_base;          // first of them in the copy buffer
+    int32_t birth_reserve;       // free slots the source leaves for split copies
     int64_t next_base;           // run index of the first particle born this iteration
     int64_t next, total;         // next unborn run index, particles in the run
     int32_t M;                   // in-flight cap of this run (<= capacity)
@@ -162,6 +166,11 @@ struct Params {
     uint32_t bpm_log2;       // log2 buckets per material
     int32_t use_cond;        // 1 inside the graph while-body, 0 for eager launches
     uint64_t sort_ebase;
+    const double* ww;        // weight-window lower bounds of problem slot 0 (NULL: analog)
+    double ww_ratio, ww_survival;
+    int32_t ww_max_split;
+    int32_t child_cap;       // capacity of the split-copy buffer
+    Particle* child;         // split copies waiting for a bank slot
     void* cum;               // running sums of N_i sigma_i, slot-major (NULL: recompute)
     int64_t cum_stride;      // elements per slot (the most nuclides of any material)     // bits of the smallest grid energy
     cudaGraphConditionalHandle cond;

@@ -132,22 +132,30 @@ __global__ void k_plan(Params P) {
     c->n_aq[1 - cur] = 0;
     c->n_sq = 0;
     c->n_cq = 0;
-    // refill free slots from the batch's unborn particles
+    // refill free slots: split copies first, then the batch's unborn
+    // particles (with weight windows the source leaves birth_reserve slots
+    // for copies)
+    int32_t nc = c->n_child < c->n_free ? c->n_child : c->n_free;
+    c->n_birth_child = nc;
+    c->child_base = c->n_child - nc;
+    c->n_child -= nc;
+    int32_t avail = c->n_free - nc - (P.ww ? c->birth_reserve : 0);
+    if (avail < 0) avail = 0;
     int64_t remain = c->total - c->next;
-    int32_t k = (int32_t)(remain < (int64_t)c->n_free ? remain : (int64_t)c->n_free);
-    c->n_birth = k;
-    c->free_base = c->n_free - k;
-    c->n_free -= k;
+    int32_t k = (int32_t)(remain < (int64_t)avail ? remain : (int64_t)avail);
+    c->n_birth = nc + k;
+    c->free_base = c->n_free - (nc + k);
+    c->n_free -= nc + k;
     c->next_base = c->next;
     c->next += k;
     c->lq_base = c->n_lq[cur];
-    c->n_lq[cur] += k;
+    c->n_lq[cur] += nc + k;
     c->st_hist += (unsigned long long)k;
     int alive = c->M - c->n_free;
-    int done = alive == 0;   // nothing in flight, nothing left to birth
+    int done = alive == 0;   // nothing in flight, no copy waiting, nothing left to birth
     c->iter += 1;
     c->tail = 0;
-    if (!done && c->next == c->total && alive <= P.tail_max) {
+    if (!done && !P.ww && c->next == c->total && alive <= P.tail_max) {
         // few particles left: the tail kernel after the loop finishes them
         c->tail = 1;
         done = 1;
@@ -198,12 +206,20 @@ __global__ void __launch_bounds__(256) k_source(Params P) {
     GBMC_BLOCK_SCALARS(sc, c->n_prob);
     int cur = c->cur;
     int32_t fb = c->free_base, lb = c->lq_base;
+    int32_t nch = c->n_birth_child, cb = c->child_base;
     int64_t nb = c->next_base;
     GBMC_WARP_LOOP(idx, valid, n) {
         int prob = 0;
-        if (valid) {
+        bool primary = valid && idx >= nch;
+        if (valid && !primary) {
+            // a split copy: its state was made by the split
             int32_t slot = P.Q.fq[fb + idx];
-            int64_t gi = nb + idx;
+            P.B.p[slot] = P.child[cb + idx];
+            P.Q.lq[cur][lb + idx] = slot;
+        }
+        if (primary) {
+            int32_t slot = P.Q.fq[fb + idx];
+            int64_t gi = nb + (idx - nch);
             prob = find_problem(P.probs, c->n_prob, gi);
             const DevProblem& pr = P.probs[prob];
             Stream r;
@@ -257,10 +273,11 @@ __global__ void __launch_bounds__(256) k_source(Params P) {
             rec.ci = ci; rec.cj = cj;
             rec.rj = r.j;
             rec.inside = inside;
+            rec.hid = (uint64_t)(pr.first_id + (gi - pr.start));
             P.B.p[slot] = rec;
             P.Q.lq[cur][lb + idx] = slot;
         }
-        sc.add(P.Y, valid, prob, GBMC_S_HISTORY, 1.0, 1ull);
+        sc.add(P.Y, primary, prob, GBMC_S_HISTORY, 1.0, 1ull);
     }
     sc.flush(P.Y);
 }
@@ -445,6 +462,7 @@ __global__ void __launch_bounds__(256) k_lookup(Params P) {
 
 __device__ __forceinline__ void record_death(const Params& P, const Particle& pt, int status) {
     int64_t gi = pt.gidx;
+    if (gi < 0) return;   // split copies have no outcome record
     P.O.ncoll[gi] = pt.ncoll;
     P.O.status[gi] = (int8_t)status;
     P.O.nflt[gi] = pt.nflt;
@@ -456,7 +474,7 @@ __device__ __forceinline__ void record_death(const Params& P, const Particle& pt
 }
 
 __device__ __forceinline__ void stream_of(const DevProblem& pr, const Particle& pt, Stream& r) {
-    r.init(pr.seed, pr.key_hi, (uint64_t)(pr.first_id + (pt.gidx - pr.start)), pt.rj);
+    r.init(pr.seed, pr.key_hi, pt.hid, pt.rj);
 }
 
 // One flight (advance event): sample the distance to collision, find the
@@ -510,9 +528,71 @@ __device__ __forceinline__ bool fly(const Params& P, const DevProblem& pr, Parti
     return collide;
 }
 
+// Weight-window check at the particle's (cell, energy bin), problem slot 0
+// only: above the window the particle splits into n = min(floor(w / w_s),
+// max_split) copies of weight w / n (the n - 1 new ones wait in the copy
+// buffer for a bank slot); below it, Russian roulette keeps it with weight
+// w_s with probability w / w_s.  Copy j of a split at draw position r.j of
+// history hid has the history id of word 0 of the Philox block of
+// (hid, r.j, j, kSplitTag) under the batch key, top bit set.
+constexpr uint64_t kSplitTag = 0x5EED0C41Dull;
+
+struct WwOut {
+    int32_t copies;     // copies made
+    double copy_w;      // their total weight
+    double roulette_w;  // weight of a history ended by roulette
+};
+
+__device__ __forceinline__ int ww_check(const Params& P, const DevProblem& pr, Particle& pt,
+                                        Stream& r, WwOut& o) {
+    if (!P.ww || pt.prob != 0) return 0;
+    const gbmc_geometry& g = pr.g;
+    int32_t cell = g.kind == GBMC_GEOM_LATTICE ? pt.cj * g.n + pt.ci
+                 : g.kind == GBMC_GEOM_SLAB    ? pt.ci
+                                               : 0;
+    double wl = __ldg(P.ww + (int64_t)cell * P.T.n_bins + energy_bin(P.T, pt.E));
+    if (!(wl > 0.0)) return 0;
+    double wu = wl * P.ww_ratio;
+    double ws = wl * P.ww_survival;
+    if (pt.wgt > wu) {
+        int32_t n = (int32_t)floor(pt.wgt / ws);
+        if (n > P.ww_max_split) n = P.ww_max_split;
+        if (n < 2) return 0;
+        double wc = pt.wgt / (double)n;
+        pt.wgt = wc;
+        for (int32_t j = 1; j < n; ++j) {
+            Philox h = philox4x64_10(pt.hid, (uint64_t)r.j, (uint64_t)j, kSplitTag, r.k0, r.k1);
+            Particle ch = pt;
+            ch.ncoll = 0;
+            ch.nflt = 0;
+            ch.rj = 0;
+            ch.hid = h.c0 | 0x8000000000000000ull;
+            ch.gidx = -1;
+            int32_t k = atomicAdd(&P.ctl->n_child, 1);
+            if (k < P.child_cap)
+                P.child[k] = ch;
+            else
+                atomicCAS(&P.ctl->err, 0, GBMC_ERR_DEVICE_FLAG);
+            o.copies += 1;
+            o.copy_w += wc;
+        }
+    } else if (pt.wgt < wl) {
+        double xi = r.next();
+        if (xi < pt.wgt / ws) {
+            pt.wgt = ws;
+        } else {
+            o.roulette_w += pt.wgt;
+            return GBMC_STATUS_ROULETTE;
+        }
+    }
+    return 0;
+}
+
 // Surface event: cross pt.surf.  Returns the fate (0: still alive) and sets
 // relook when the material changed (a new lookup is needed).
-__device__ __forceinline__ int cross(const gbmc_geometry& g, Particle& pt, bool& relook) {
+__device__ __forceinline__ int cross(const Params& P, const DevProblem& pr, Particle& pt,
+                                     Stream& r, bool& relook, WwOut& wo) {
+    const gbmc_geometry& g = pr.g;
     int status = 0;
     relook = false;
     if (g.kind == GBMC_GEOM_SLAB) {
@@ -567,6 +647,10 @@ __device__ __forceinline__ int cross(const gbmc_geometry& g, Particle& pt, bool&
         if (g.bc_z == GBMC_BC_REFLECT) pt.w = -pt.w;
         else status = GBMC_STATUS_LEAKED;
     }
+    if (!status && g.kind == GBMC_GEOM_SLAB) {
+        status = ww_check(P, pr, pt, r, wo);
+        pt.rj = r.j;
+    }
     if (!status && pt.nflt >= GBMC_MAX_FLIGHTS) status = GBMC_STATUS_LIMIT;
     return status;
 }
@@ -577,7 +661,7 @@ __device__ __forceinline__ int cross(const gbmc_geometry& g, Particle& pt, bool&
 // lookup).
 template <int PREC>
 __device__ __forceinline__ int collide(const Params& P, const DevProblem& pr, Particle& pt,
-                                       int32_t slot, Stream& r) {
+                                       int32_t slot, Stream& r, WwOut& wo) {
     double target = r.next() * pt.st;
     int32_t nuc = -1;
     if (P.cum) {
@@ -606,7 +690,10 @@ __device__ __forceinline__ int collide(const Params& P, const DevProblem& pr, Pa
         pt.v = v;
         pt.w = w;
         pt.E = E1;
-        if (pt.E < pr.g.E_cut) status = GBMC_STATUS_CUTOFF;
+        if (pt.E < pr.g.E_cut)
+            status = GBMC_STATUS_CUTOFF;
+        else
+            status = ww_check(P, pr, pt, r, wo);
     }
     if (!status && pt.nflt >= GBMC_MAX_FLIGHTS) status = GBMC_STATUS_LIMIT;
     pt.rj = r.j;
@@ -667,6 +754,7 @@ __global__ void __launch_bounds__(256, 3) k_raytrace(Params P) {
         if (!__any_sync(kFull, have)) break;
         int status = 0, route = 0;   // route 1: collision, 2: lookup
         bool fin = false;
+        WwOut wo{0, 0.0, 0.0};
         if (have) {
             const DevProblem& pr = P.probs[pt.prob];
             bool col = fly(P, pr, pt, r);
@@ -676,7 +764,7 @@ __global__ void __launch_bounds__(256, 3) k_raytrace(Params P) {
                 fin = true;
             } else {
                 bool relook;
-                status = cross(pr.g, pt, relook);
+                status = cross(P, pr, pt, r, relook, wo);
                 ++crossings;
                 if (status) {
                     fin = true;
@@ -690,6 +778,11 @@ __global__ void __launch_bounds__(256, 3) k_raytrace(Params P) {
                 if (status) record_death(P, pt, status);
                 nflights += (unsigned long long)flights;
             }
+        }
+        if (P.ww && __any_sync(kFull, wo.copies > 0 || wo.roulette_w > 0.0)) {
+            int pw = have ? pt.prob : 0;
+            sc.add(P.Y, wo.copies > 0, pw, GBMC_S_SPLIT, wo.copy_w, (unsigned long long)wo.copies);
+            sc.add(P.Y, wo.roulette_w > 0.0, pw, GBMC_S_ROULETTE, wo.roulette_w, 1ull);
         }
         if (__any_sync(kFull, fin)) {
             bool dead = fin && status != 0;
@@ -730,6 +823,7 @@ __global__ void __launch_bounds__(256, 3) k_collision(Params P) {
         int prob = 0;
         int status = 0;
         double wgt = 0.0;
+        WwOut wo{0, 0.0, 0.0};
         if (valid) {
             slot = P.Q.cq[idx];
             Particle pt = P.B.p[slot];
@@ -738,11 +832,15 @@ __global__ void __launch_bounds__(256, 3) k_collision(Params P) {
             wgt = pt.wgt;
             Stream r;
             stream_of(pr, pt, r);
-            status = collide<PREC>(P, pr, pt, slot, r);
+            status = collide<PREC>(P, pr, pt, slot, r, wo);
             P.B.p[slot] = pt;
             if (status) record_death(P, pt, status);
         }
         bool dead = valid && status != 0;
+        if (P.ww) {
+            sc.add(P.Y, wo.copies > 0, prob, GBMC_S_SPLIT, wo.copy_w, (unsigned long long)wo.copies);
+            sc.add(P.Y, wo.roulette_w > 0.0, prob, GBMC_S_ROULETTE, wo.roulette_w, 1ull);
+        }
         sc.add(P.Y, valid, prob, GBMC_S_COLLISION, wgt, 1ull);
         sc.add(P.Y, dead && status == GBMC_STATUS_ABSORBED, prob, GBMC_S_ABSORPTION, wgt, 1ull);
         sc.add(P.Y, dead && status == GBMC_STATUS_CUTOFF, prob, GBMC_S_CUTOFF, wgt, 1ull);
@@ -806,11 +904,13 @@ __global__ void __launch_bounds__(256) k_tail(Params P) {
                 if (col) {
                     ++nc;
                     wc += pt.wgt;
-                    status = collide<PREC>(P, pr, pt, slot, r);
+                    WwOut wo{0, 0.0, 0.0};
+                    status = collide<PREC>(P, pr, pt, slot, r, wo);
                     action = status ? 2 : 1;
                 } else {
                     bool relook;
-                    status = cross(pr.g, pt, relook);
+                    WwOut wo{0, 0.0, 0.0};
+                    status = cross(P, pr, pt, r, relook, wo);
                     ++crossings;
                     action = status ? 2 : (relook ? 1 : 0);
                 }

@@ -23,16 +23,19 @@ FP64, FP32 = 0, 1
 GEOM_INFINITE, GEOM_LATTICE, GEOM_SLAB = 0, 1, 2
 BC_VACUUM, BC_REFLECT = 0, 1
 SRC_ORIGIN, SRC_BOX, SRC_SLAB_FACE = 0, 1, 2
-STATUS_ABSORBED, STATUS_LEAKED, STATUS_CUTOFF, STATUS_LIMIT, STATUS_LEAKED_FAR = 1, 2, 3, 4, 5
-S_COLLISION, S_ABSORPTION, S_LEAK, S_CUTOFF, S_LIMIT, S_LEAK_FAR, S_FLIGHT, S_HISTORY = range(8)
-NSCAL = 8
+STATUS_ABSORBED, STATUS_LEAKED, STATUS_CUTOFF, STATUS_LIMIT, STATUS_LEAKED_FAR, \
+    STATUS_ROULETTE = 1, 2, 3, 4, 5, 6
+S_COLLISION, S_ABSORPTION, S_LEAK, S_CUTOFF, S_LIMIT, S_LEAK_FAR, S_FLIGHT, S_HISTORY, S_SPLIT, \
+    S_ROULETTE = range(10)
+NSCAL = 10
 MAX_FLIGHTS = 100000
 
 EXPORTS = ["gbmc_default_options", "gbmc_create", "gbmc_destroy", "gbmc_last_error",
            "gbmc_set_options", "gbmc_load_xs_tables", "gbmc_init_materials", "gbmc_set_tally",
            "gbmc_reset_tallies", "gbmc_run_batch", "gbmc_run_problems", "gbmc_read_tallies",
            "gbmc_read_outcomes", "gbmc_read_stats", "gbmc_lookup_macro", "gbmc_last_run_ms",
-           "gbmc_profile_problems", "gbmc_lookup_macro_noalloc", "gbmc_autotune"]
+           "gbmc_profile_problems", "gbmc_lookup_macro_noalloc", "gbmc_autotune",
+           "gbmc_set_weight_windows", "gbmc_clear_weight_windows"]
 NOALLOC_MAX_QUERIES = 1 << 20
 KERNEL_NAMES = ["plan", "source", "sort_keys", "sort_scan", "sort_scatter", "lookup", "raytrace",
                 "collision", "tail"]
@@ -120,6 +123,9 @@ def lib():
         L.gbmc_last_run_ms.argtypes = [vp, _P(C.c_double)]
         L.gbmc_autotune.argtypes = [vp, C.c_int32, _P(Problem), C.c_double, vp, _P(Options),
                                     _P(AutotuneReport)]
+        L.gbmc_set_weight_windows.argtypes = [vp, C.c_int32, C.c_int32, _P(C.c_double),
+                                              C.c_double, C.c_double, C.c_int32]
+        L.gbmc_clear_weight_windows.argtypes = [vp]
         L.gbmc_lookup_macro_noalloc.argtypes = [vp, C.c_int32, vp, vp, C.c_int64, vp, vp, vp]
         L.gbmc_profile_problems.argtypes = [vp, C.c_int32, _P(Problem), vp, _P(KernelTimes),
                                             C.c_int32, _P(C.c_double), _P(C.c_int32),
@@ -248,6 +254,18 @@ class Context:
                                 prob.awr, prec)
         self.init_materials(prob.mat_off, prob.nuc_id, prob.density)
         self.set_tally(prob.edges)
+
+    def set_weight_windows(self, lower, ratio=5.0, survival=2.5, max_split=10):
+        """Windows for problem slot 0: lower [n_cells, n_bins] (0: none)."""
+        lo = np.ascontiguousarray(lower, dtype=np.float64)
+        if lo.ndim != 2:
+            raise ValueError("lower must be [n_cells, n_bins]")
+        self._ck(lib().gbmc_set_weight_windows(self._h, lo.shape[0], lo.shape[1],
+                                               _p(lo, C.c_double), float(ratio), float(survival),
+                                               int(max_split)))
+
+    def clear_weight_windows(self):
+        self._ck(lib().gbmc_clear_weight_windows(self._h))
 
     def reset_tallies(self, stream=None):
         self._ck(lib().gbmc_reset_tallies(self._h, _stream(stream)))
