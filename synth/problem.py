@@ -313,14 +313,17 @@ def make_tiny_problem(seed: int = 7, n_nuc: int = 3, n_points=(2, 9),
              (awr[i] if awr is not None else a)) for i, (e, s, f, a) in enumerate(nucs)]
     off, en, sg, fa, aw = _pool(nucs)
     dens = rng.uniform(0.01, 1.0, n_nuc)
+    half = max(1, n_nuc // 2)
+    if n_nuc > 1:
+        two = [(np.arange(half), dens[:half]), (np.arange(half, n_nuc), dens[half:])]
+    else:
+        two = [(np.arange(1), dens), (np.arange(1), dens)]
     if kind == GEOM_LATTICE:
-        half = max(1, n_nuc // 2)
-        mats = [(np.arange(half), dens[:half]), (np.arange(half, n_nuc), dens[half:])]
+        mats = two
         g = Geometry(kind=GEOM_LATTICE, source=SRC_BOX, n=lattice_n, mat_pin=0,
                      mat_mod=1 if n_nuc > 1 else 0, height=20.0)
     elif kind == GEOM_SLAB:
-        half = max(1, n_nuc // 2)
-        mats = [(np.arange(half), dens[:half]), (np.arange(half, n_nuc), dens[half:])]
+        mats = two
         g = Geometry(kind=GEOM_SLAB, source=SRC_SLAB_FACE, n_layers=8, layer_dx=1.0,
                      n_first=2, mat_a=0, mat_b=1 if n_nuc > 1 else 0)
     else:
