@@ -729,6 +729,7 @@ __global__ void __launch_bounds__(256, 3) k_raytrace(Params P) {
     int32_t slot = 0;
     Stream r;
     int32_t flights = 0;
+    double fw = 0.0;   // weight summed over this particle's flights
     bool have = false, exhausted = false;
     for (;;) {
         bool want = !have && !exhausted;
@@ -745,6 +746,7 @@ __global__ void __launch_bounds__(256, 3) k_raytrace(Params P) {
                     pt = P.B.p[slot];
                     stream_of(P.probs[pt.prob], pt, r);
                     flights = 0;
+                    fw = 0.0;
                     have = true;
                 } else {
                     exhausted = true;
@@ -759,6 +761,7 @@ __global__ void __launch_bounds__(256, 3) k_raytrace(Params P) {
             const DevProblem& pr = P.probs[pt.prob];
             bool col = fly(P, pr, pt, r);
             ++flights;
+            fw += pt.wgt;
             if (col) {
                 route = 1;
                 fin = true;
@@ -788,7 +791,7 @@ __global__ void __launch_bounds__(256, 3) k_raytrace(Params P) {
             bool dead = fin && status != 0;
             int prob = fin ? pt.prob : 0;
             double wgt = fin ? pt.wgt : 0.0;
-            sc.add(P.Y, fin, prob, GBMC_S_FLIGHT, wgt * flights, (unsigned long long)flights);
+            sc.add(P.Y, fin, prob, GBMC_S_FLIGHT, fin ? fw : 0.0, (unsigned long long)flights);
             sc.add(P.Y, dead && leak_kind(status), prob, GBMC_S_LEAK, wgt, 1ull);
             sc.add(P.Y, dead && status == GBMC_STATUS_LEAKED_FAR, prob, GBMC_S_LEAK_FAR, wgt, 1ull);
             sc.add(P.Y, dead && status == GBMC_STATUS_LIMIT, prob, GBMC_S_LIMIT, wgt, 1ull);
