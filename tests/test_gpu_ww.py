@@ -49,7 +49,14 @@ def test_absorber_slab_windows_match_oracle():
     win = _layer_windows(p, st)
     g, ref, _ = _compare(p, win, 20_000, batch=3, max_in_flight=8192)
     assert ref["counts"][oracle.S_SPLIT] > 1000
-    assert ref["counts"][oracle.S_ROULETTE] > 0
+
+
+def test_rising_windows_roulette_matches_oracle():
+    # windows that rise with depth: particles fall below them and roulette
+    p = synth.make_config(5, n_particles=6000, grid_scale=0.02)
+    win = _layer_windows(p, -0.05)
+    g, ref, _ = _compare(p, win, 6000, batch=2)
+    assert ref["counts"][oracle.S_ROULETTE] > 100
 
 
 def test_scattering_slab_windows_match_oracle_with_small_bank():
