@@ -291,8 +291,77 @@ int gbmc_profile_problems(gbmc_ctx *ctx, int32_t n_prob, const gbmc_problem *pro
 int gbmc_set_weight_windows(gbmc_ctx *ctx, int32_t n_cells, int32_t n_bins, const double *lower,
                             double ratio, double survival, int32_t max_split);
 
+/* Copy the current window lower bounds (n = cells * bins) to the host. */
+int gbmc_get_weight_windows(gbmc_ctx *ctx, double *lower, int64_t n);
+
 /* Back to analog transport. */
 int gbmc_clear_weight_windows(gbmc_ctx *ctx);
+
+/* ---- learned importance map (weight windows) ---------------------------
+ * A 4 -> 64 -> 64 -> 1 multilayer perceptron (ReLU after each hidden
+ * layer) maps features of (x, y, z, ln E) to a log-importance; weight
+ * windows are set inversely proportional to the importance.  Weights are
+ * BF16; the 64 x 64 layer runs on the tensor cores (FP32 accumulation) in
+ * inference and training.  The paper has no counterpart (it is the
+ * variance-reduction extension the weight windows serve).
+ * Parameter layout: W1[64][4], b1[64], W2[64][64] (row = output unit),
+ * b2[64], W3[64], b3 -- GBMC_MLP_NPARAM BF16 values.
+ * Features: f_i = (raw_i - offset_i) * scale_i, raw = (x, y, z, ln E). */
+#define GBMC_MLP_HIDDEN 64
+#define GBMC_MLP_NPARAM 4545
+
+/* Set the network (BF16 bit patterns) and its feature map; resets the
+ * optimizer.  Host arrays copied. */
+int gbmc_set_importance_net(gbmc_ctx *ctx, const uint16_t *bf16_params, int32_t n_params,
+                            const double *feat_offset, const double *feat_scale);
+
+/* Copy the current (trained) BF16 parameters to the host; synchronizes. */
+int gbmc_get_importance_net(gbmc_ctx *ctx, uint16_t *bf16_params, int32_t n_params);
+
+/* Network outputs for n feature rows: DEVICE pointers d_feat [n][4]
+ * (float), d_out [n] (float).  Asynchronous on `stream`. */
+int gbmc_mlp_forward(gbmc_ctx *ctx, const float *d_feat, int64_t n, float *d_out, void *stream);
+
+/* Loss L = sum_s w_s (out_s - y_s)^2 / sum_s w_s over n rows (DEVICE
+ * pointers d_feat [n][4], d_target [n], d_weight [n]) and its gradient with
+ * respect to the parameters (host grad [GBMC_MLP_NPARAM], fp32; host loss).
+ * Synchronizes. */
+int gbmc_mlp_gradient(gbmc_ctx *ctx, const float *d_feat, const float *d_target,
+                      const float *d_weight, int64_t n, float *grad, float *loss, void *stream);
+
+/* `steps` full-batch Adam steps (beta 0.9 / 0.999, learning rate lr) on the
+ * same loss, entirely on the device (FP32 master weights, BF16 copies for
+ * the tensor cores).  *loss receives the last step's loss.  Synchronizes. */
+int gbmc_mlp_train(gbmc_ctx *ctx, const float *d_feat, const float *d_target,
+                   const float *d_weight, int64_t n, int32_t steps, float lr, float *loss,
+                   void *stream);
+
+/* Features of the mesh (cells of geometry g x tally energy bins: cell
+ * centre, logarithmic bin centre) into DEVICE d_feat [n][4] with the
+ * network's feature map; *n_out = number of rows (d_feat NULL: count only). */
+int gbmc_mesh_features(gbmc_ctx *ctx, const gbmc_geometry *g, float *d_feat, int64_t n_cap,
+                       int64_t *n_out, void *stream);
+
+/* Weight windows of problem slot 0 from the network: on the mesh of g,
+ * lower = C / exp(out) with C such that the source cell and energy bin has
+ * survival weight 1.  Then as gbmc_set_weight_windows.  Synchronizes. */
+int gbmc_weight_windows_from_net(gbmc_ctx *ctx, const gbmc_geometry *g, double ratio,
+                                 double survival, int32_t max_split, void *stream);
+
+/* Importance estimates from analog runs.  With g != NULL and capacity > 0,
+ * following runs record, for every collision of a problem-slot-0 history,
+ * its mesh cell (cell of g x energy bin before the collision) -- at most
+ * `capacity` per run (NULL / 0: recording off).
+ * gbmc_importance_accumulate, after each such run, scores those samples by
+ * whether their history left through the slab's far face, into per-mesh
+ * counts n and scores s (kept across runs).
+ * gbmc_importance_training_set writes the mesh features, targets
+ * ln((s + 1/2) / (n + 1)) and weights n to DEVICE arrays of n_cap rows. */
+int gbmc_importance_record(gbmc_ctx *ctx, const gbmc_geometry *g, int64_t capacity);
+int gbmc_importance_accumulate(gbmc_ctx *ctx, void *stream);
+int gbmc_importance_training_set(gbmc_ctx *ctx, const gbmc_geometry *g, float *d_feat,
+                                 float *d_target, float *d_weight, int64_t n_cap,
+                                 int64_t *n_out, void *stream);
 
 /* Result of gbmc_autotune. */
 typedef struct {

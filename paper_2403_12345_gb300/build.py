@@ -14,8 +14,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libgbmc.so")
-SOURCES = ["api.cu", "transport.cu"]
-HEADERS = ["device.cuh", "launch.h"]
+SOURCES = ["api.cu", "transport.cu", "mlp.cu"]
+HEADERS = ["device.cuh", "launch.h", "mlp.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ARCH + ["-O3", "-lineinfo", "-fmad=false", "-std=c++17", "-Xcompiler", "-fPIC",

@@ -13,6 +13,7 @@
 
 #include "device.cuh"
 #include "launch.h"
+#include "mlp.h"
 
 using namespace gbmc;
 
@@ -120,6 +121,25 @@ struct gbmc_ctx {
     double* d_ww = nullptr;
     Particle* d_child = nullptr;
     int32_t child_cap = 0;
+
+    // importance network (fp32 master, Adam state, gradient, BF16 copy)
+    bool net_set = false;
+    float *d_net_p = nullptr, *d_net_m = nullptr, *d_net_v = nullptr, *d_net_g = nullptr;
+    float *d_net_scratch = nullptr;   // [0]: 1 / sum of weights, [1]: loss
+    __nv_bfloat16* d_net_w = nullptr;
+    int32_t net_step = 0;
+    double feat_offset[4] = {0, 0, 0, 0}, feat_scale[4] = {1, 1, 1, 1};
+    float *d_mesh_feat = nullptr, *d_mesh_out = nullptr;
+    int64_t mesh_cap = 0;
+    std::vector<double> h_edges;
+
+    // importance samples (analog runs) and their per-mesh-cell estimates
+    int32_t* d_imp_mesh = nullptr;
+    int64_t* d_imp_gidx = nullptr;
+    int32_t imp_cap = 0;
+    bool imp_on = false;
+    double *d_imp_cnt = nullptr, *d_imp_scr = nullptr;
+    int64_t imp_cells = 0;
 
     // standalone-lookup scratch
     int64_t q_cap = 0;
@@ -383,6 +403,11 @@ Params make_params(gbmc_ctx* c) {
         P.ww_max_split = c->ww_max_split;
         P.child = c->d_child;
         P.child_cap = c->child_cap;
+    }
+    if (c->imp_on) {
+        P.imp_mesh = c->d_imp_mesh;
+        P.imp_gidx = c->d_imp_gidx;
+        P.imp_cap = c->imp_cap;
     }
     return P;
 }
@@ -660,6 +685,9 @@ int gbmc_destroy(gbmc_ctx* c) {
     dfree(c->d_mat_off); dfree(c->d_nuc_id); dfree(c->d_density); dfree(c->d_density32);
     dfree(c->d_edges); dfree(c->d_probs); dfree(c->d_ctl);
     dfree(c->d_ww); dfree(c->d_child);
+    dfree(c->d_net_p); dfree(c->d_net_m); dfree(c->d_net_v); dfree(c->d_net_g);
+    dfree(c->d_net_scratch); dfree(c->d_net_w); dfree(c->d_mesh_feat); dfree(c->d_mesh_out);
+    dfree(c->d_imp_mesh); dfree(c->d_imp_gidx); dfree(c->d_imp_cnt); dfree(c->d_imp_scr);
     if (c->d_cum) { cudaDeviceSynchronize(); cudaFree(c->d_cum); }
     dfree(c->q_perm); dfree(c->q_keys); dfree(c->q_hist); dfree(c->q_cursor); dfree(c->q_btot);
     if (c->h_probs) cudaFreeHost(c->h_probs);
@@ -833,6 +861,7 @@ int gbmc_set_tally(gbmc_ctx* c, int32_t n_bins, const double* edges) {
     if (rc) return rc;
     if ((rc = upload(c, &c->d_edges, edges, (size_t)n_bins + 1))) return rc;
     c->n_bins = n_bins;
+    c->h_edges.assign(edges, edges + n_bins + 1);
     c->slot_cells.clear();   // forces re-zeroing at the next run
     c->graph_valid = false;
     return GBMC_OK;
@@ -892,9 +921,11 @@ int prepare_run(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, cudaStre
         if (cells[0] != c->ww_cells)
             return fail(c, GBMC_ERR_INVALID_ARG,
                         "weight windows cover %d cells, problem slot 0 has %d", c->ww_cells, cells[0]);
-        if (c->child_cap < c->capacity) {
-            if ((rc = dalloc(c, &c->d_child, (size_t)c->capacity))) return rc;
-            c->child_cap = c->capacity;
+        // split copies wait here for free slots: room for four bank-fulls
+        int64_t want = std::max<int64_t>((int64_t)c->capacity * 4, (int64_t)1 << 20);
+        if (c->child_cap < want) {
+            if ((rc = dalloc(c, &c->d_child, (size_t)want))) return rc;
+            c->child_cap = (int32_t)want;
             c->graph_valid = false;
         }
     }
@@ -1192,10 +1223,274 @@ extern "C" int gbmc_set_weight_windows(gbmc_ctx* c, int32_t n_cells, int32_t n_b
     return GBMC_OK;
 }
 
+extern "C" int gbmc_get_weight_windows(gbmc_ctx* c, double* lower, int64_t n) {
+    if (!c || !lower) return GBMC_ERR_INVALID_ARG;
+    if (!c->ww_on) return fail(c, GBMC_ERR_NOT_INITIALIZED, "no weight windows set");
+    int64_t need = (int64_t)c->ww_cells * c->n_bins;
+    if (n != need) return fail(c, GBMC_ERR_INVALID_ARG, "n must be %lld", (long long)need);
+    int rc = set_device(c);
+    if (rc) return rc;
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(lower, c->d_ww, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    return GBMC_OK;
+}
+
 extern "C" int gbmc_clear_weight_windows(gbmc_ctx* c) {
     if (!c) return GBMC_ERR_INVALID_ARG;
     if (c->ww_on) c->graph_valid = false;
     c->ww_on = false;
+    return GBMC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Importance network and importance estimates.
+
+namespace {
+
+int need_net(gbmc_ctx* c) {
+    if (!c->net_set) return fail(c, GBMC_ERR_NOT_INITIALIZED, "set the importance network first");
+    return GBMC_OK;
+}
+
+int ensure_mesh(gbmc_ctx* c, int64_t n) {
+    if (n <= c->mesh_cap) return GBMC_OK;
+    int rc = dalloc(c, &c->d_mesh_feat, (size_t)n * 4);
+    if (rc) return rc;
+    if ((rc = dalloc(c, &c->d_mesh_out, (size_t)n))) return rc;
+    c->mesh_cap = n;
+    return GBMC_OK;
+}
+
+MeshSpec mesh_of(const gbmc_ctx* c, const gbmc_geometry& g) {
+    MeshSpec M{};
+    M.g = g;
+    M.n_cells = n_cells_of(g);
+    M.n_bins = c->n_bins;
+    M.edges = c->d_edges;
+    for (int i = 0; i < 4; ++i) {
+        M.offset[i] = c->feat_offset[i];
+        M.scale[i] = c->feat_scale[i];
+    }
+    return M;
+}
+
+}  // namespace
+
+extern "C" int gbmc_set_importance_net(gbmc_ctx* c, const uint16_t* bf16_params, int32_t n_params,
+                                       const double* feat_offset, const double* feat_scale) {
+    if (!c) return GBMC_ERR_INVALID_ARG;
+    if (!bf16_params || n_params != kMlpParams || !feat_offset || !feat_scale)
+        return fail(c, GBMC_ERR_INVALID_ARG, "need %d BF16 parameters and 4 offsets, 4 scales",
+                    kMlpParams);
+    for (int i = 0; i < 4; ++i)
+        if (!std::isfinite(feat_offset[i]) || !std::isfinite(feat_scale[i]))
+            return fail(c, GBMC_ERR_INVALID_ARG, "feature offsets and scales must be finite");
+    int rc = set_device(c);
+    if (rc) return rc;
+    std::vector<float> p(kMlpParams);
+    for (int k = 0; k < kMlpParams; ++k) {
+        uint32_t b = (uint32_t)bf16_params[k] << 16;
+        memcpy(&p[k], &b, 4);
+        if (!std::isfinite(p[k])) return fail(c, GBMC_ERR_INVALID_ARG, "parameter %d not finite", k);
+    }
+    std::vector<float> zero(kMlpParams, 0.f);
+    if ((rc = upload(c, &c->d_net_p, p.data(), p.size()))) return rc;
+    if ((rc = upload(c, &c->d_net_m, zero.data(), zero.size()))) return rc;
+    if ((rc = upload(c, &c->d_net_v, zero.data(), zero.size()))) return rc;
+    if ((rc = upload(c, &c->d_net_g, zero.data(), zero.size()))) return rc;
+    if ((rc = upload(c, &c->d_net_w, reinterpret_cast<const __nv_bfloat16*>(bf16_params),
+                     (size_t)kMlpParams)))
+        return rc;
+    if (!c->d_net_scratch && (rc = dalloc(c, &c->d_net_scratch, 2))) return rc;
+    for (int i = 0; i < 4; ++i) {
+        c->feat_offset[i] = feat_offset[i];
+        c->feat_scale[i] = feat_scale[i];
+    }
+    c->net_step = 0;
+    c->net_set = true;
+    return GBMC_OK;
+}
+
+extern "C" int gbmc_get_importance_net(gbmc_ctx* c, uint16_t* bf16_params, int32_t n_params) {
+    if (!c || !bf16_params || n_params != kMlpParams) return GBMC_ERR_INVALID_ARG;
+    int rc = need_net(c);
+    if (rc) return rc;
+    if ((rc = set_device(c))) return rc;
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(bf16_params, c->d_net_w, sizeof(uint16_t) * kMlpParams, cudaMemcpyDeviceToHost));
+    return GBMC_OK;
+}
+
+extern "C" int gbmc_mlp_forward(gbmc_ctx* c, const float* d_feat, int64_t n, float* d_out,
+                                void* stream) {
+    if (!c || n < 0 || (n > 0 && (!d_feat || !d_out))) return GBMC_ERR_INVALID_ARG;
+    int rc = need_net(c);
+    if (rc) return rc;
+    if ((rc = set_device(c))) return rc;
+    cudaError_t e = mlp_forward(c->d_net_w, d_feat, n, d_out, c->sms, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(c, GBMC_ERR_CUDA, "network forward: %s", cudaGetErrorString(e));
+    return GBMC_OK;
+}
+
+extern "C" int gbmc_mlp_gradient(gbmc_ctx* c, const float* d_feat, const float* d_target,
+                                 const float* d_weight, int64_t n, float* grad_host,
+                                 float* loss_host, void* stream) {
+    if (!c || n < 1 || !d_feat || !d_target || !d_weight) return GBMC_ERR_INVALID_ARG;
+    int rc = need_net(c);
+    if (rc) return rc;
+    if ((rc = set_device(c))) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemsetAsync(c->d_net_g, 0, sizeof(float) * kMlpParams, s));
+    CK(cudaMemsetAsync(c->d_net_scratch, 0, sizeof(float) * 2, s));
+    cudaError_t e = mlp_grad(c->d_net_w, d_feat, d_target, d_weight, n, c->d_net_scratch,
+                             c->d_net_g, c->d_net_scratch + 1, c->sms, s);
+    if (e != cudaSuccess) return fail(c, GBMC_ERR_CUDA, "network gradient: %s", cudaGetErrorString(e));
+    CK(cudaStreamSynchronize(s));
+    if (grad_host)
+        CK(cudaMemcpy(grad_host, c->d_net_g, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost));
+    if (loss_host) CK(cudaMemcpy(loss_host, c->d_net_scratch + 1, sizeof(float), cudaMemcpyDeviceToHost));
+    CK(cudaMemsetAsync(c->d_net_g, 0, sizeof(float) * kMlpParams, s));
+    return GBMC_OK;
+}
+
+extern "C" int gbmc_mlp_train(gbmc_ctx* c, const float* d_feat, const float* d_target,
+                              const float* d_weight, int64_t n, int32_t steps, float lr,
+                              float* loss_host, void* stream) {
+    if (!c || n < 1 || steps < 1 || !(lr > 0) || !d_feat || !d_target || !d_weight)
+        return GBMC_ERR_INVALID_ARG;
+    int rc = need_net(c);
+    if (rc) return rc;
+    if ((rc = set_device(c))) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemsetAsync(c->d_net_g, 0, sizeof(float) * kMlpParams, s));
+    for (int32_t k = 0; k < steps; ++k) {
+        CK(cudaMemsetAsync(c->d_net_scratch, 0, sizeof(float) * 2, s));
+        cudaError_t e = mlp_grad(c->d_net_w, d_feat, d_target, d_weight, n, c->d_net_scratch,
+                                 c->d_net_g, c->d_net_scratch + 1, c->sms, s);
+        if (e == cudaSuccess)
+            e = mlp_adam(c->d_net_p, c->d_net_m, c->d_net_v, c->d_net_g, c->d_net_w, kMlpParams,
+                         lr, ++c->net_step, s);
+        if (e != cudaSuccess) return fail(c, GBMC_ERR_CUDA, "training step: %s", cudaGetErrorString(e));
+    }
+    CK(cudaStreamSynchronize(s));
+    if (loss_host) CK(cudaMemcpy(loss_host, c->d_net_scratch + 1, sizeof(float), cudaMemcpyDeviceToHost));
+    return GBMC_OK;
+}
+
+extern "C" int gbmc_mesh_features(gbmc_ctx* c, const gbmc_geometry* g, float* d_feat, int64_t n_cap,
+                                  int64_t* n_out, void* stream) {
+    if (!c || !g || !n_out) return GBMC_ERR_INVALID_ARG;
+    if (!c->n_bins) return fail(c, GBMC_ERR_NOT_INITIALIZED, "set the tally bins first");
+    int64_t n = (int64_t)n_cells_of(*g) * c->n_bins;
+    *n_out = n;
+    if (!d_feat) return GBMC_OK;
+    if (n_cap < n) return fail(c, GBMC_ERR_INVALID_ARG, "need room for %lld feature rows", (long long)n);
+    int rc = set_device(c);
+    if (rc) return rc;
+    cudaError_t e = mesh_features(mesh_of(c, *g), d_feat, c->sms, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(c, GBMC_ERR_CUDA, "mesh features: %s", cudaGetErrorString(e));
+    return GBMC_OK;
+}
+
+extern "C" int gbmc_weight_windows_from_net(gbmc_ctx* c, const gbmc_geometry* g, double ratio,
+                                            double survival, int32_t max_split, void* stream) {
+    if (!c || !g) return GBMC_ERR_INVALID_ARG;
+    int rc = need_net(c);
+    if (rc) return rc;
+    if (!c->n_bins) return fail(c, GBMC_ERR_NOT_INITIALIZED, "set the tally bins first");
+    if (!(survival >= 1.0) || !(ratio >= 2.0 * survival) || max_split < 2 || max_split > 1000)
+        return fail(c, GBMC_ERR_INVALID_ARG, "need survival >= 1, ratio >= 2 survival, max_split in [2, 1000]");
+    if ((rc = set_device(c))) return rc;
+    MeshSpec M = mesh_of(c, *g);
+    int64_t n = (int64_t)M.n_cells * M.n_bins;
+    if ((rc = ensure_mesh(c, n))) return rc;
+    // source cell (the slab's first layer, the infinite medium's one cell,
+    // the lattice's first cell) and the source energy's bin
+    int64_t b = 0;
+    while (b + 1 < c->n_bins && c->h_edges[b + 1] <= g->E0) ++b;
+    int64_t src = b;
+    if (c->ran) CK(cudaStreamSynchronize(c->last_stream));
+    if (!c->d_ww || c->ww_cells != M.n_cells) {
+        if ((rc = dalloc(c, &c->d_ww, (size_t)n))) return rc;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = mesh_windows(M, c->d_net_w, c->d_mesh_feat, c->d_mesh_out, survival, src,
+                                 c->d_ww, c->sms, s);
+    if (e != cudaSuccess) return fail(c, GBMC_ERR_CUDA, "windows from network: %s", cudaGetErrorString(e));
+    CK(cudaStreamSynchronize(s));
+    c->ww_on = true;
+    c->ww_cells = M.n_cells;
+    c->ww_ratio = ratio;
+    c->ww_survival = survival;
+    c->ww_max_split = max_split;
+    c->graph_valid = false;
+    return GBMC_OK;
+}
+
+extern "C" int gbmc_importance_record(gbmc_ctx* c, const gbmc_geometry* g, int64_t capacity) {
+    if (!c) return GBMC_ERR_INVALID_ARG;
+    if (!g || capacity <= 0) {
+        if (c->imp_on) c->graph_valid = false;
+        c->imp_on = false;
+        return GBMC_OK;
+    }
+    if (!c->n_bins) return fail(c, GBMC_ERR_NOT_INITIALIZED, "set the tally bins first");
+    if (capacity > ((int64_t)1 << 31) - 1) return fail(c, GBMC_ERR_INVALID_ARG, "capacity < 2^31");
+    int rc = set_device(c);
+    if (rc) return rc;
+    if (c->ran) CK(cudaStreamSynchronize(c->last_stream));
+    if (capacity > c->imp_cap) {
+        if ((rc = dalloc(c, &c->d_imp_mesh, (size_t)capacity))) return rc;
+        if ((rc = dalloc(c, &c->d_imp_gidx, (size_t)capacity))) return rc;
+        c->imp_cap = (int32_t)capacity;
+    }
+    int64_t cells = (int64_t)n_cells_of(*g) * c->n_bins;
+    if (cells != c->imp_cells || !c->d_imp_cnt) {
+        if ((rc = dalloc(c, &c->d_imp_cnt, (size_t)cells))) return rc;
+        if ((rc = dalloc(c, &c->d_imp_scr, (size_t)cells))) return rc;
+        CK(cudaMemset(c->d_imp_cnt, 0, sizeof(double) * cells));
+        CK(cudaMemset(c->d_imp_scr, 0, sizeof(double) * cells));
+        c->imp_cells = cells;
+    }
+    c->imp_on = true;
+    c->graph_valid = false;
+    return GBMC_OK;
+}
+
+extern "C" int gbmc_importance_accumulate(gbmc_ctx* c, void* stream) {
+    if (!c) return GBMC_ERR_INVALID_ARG;
+    if (!c->imp_on) return fail(c, GBMC_ERR_NOT_INITIALIZED, "importance recording is off");
+    int rc = set_device(c);
+    if (rc) return rc;
+    if ((rc = read_ctl(c))) return rc;
+    if (c->h_ctl->n_imp > c->imp_cap)
+        return fail(c, GBMC_ERR_DEVICE_FLAG, "importance sample buffer overflowed (%d > %d)",
+                    c->h_ctl->n_imp, c->imp_cap);
+    cudaStream_t s = (cudaStream_t)stream;
+    Params P = make_params(c);
+    cudaError_t e = launch_imp_score(P, c->O.status, c->d_imp_cnt, c->d_imp_scr, c->sms, s);
+    if (e != cudaSuccess) return fail(c, GBMC_ERR_CUDA, "importance scoring: %s", cudaGetErrorString(e));
+    CK(cudaStreamSynchronize(s));
+    return GBMC_OK;
+}
+
+extern "C" int gbmc_importance_training_set(gbmc_ctx* c, const gbmc_geometry* g, float* d_feat,
+                                            float* d_target, float* d_weight, int64_t n_cap,
+                                            int64_t* n_out, void* stream) {
+    if (!c || !g || !n_out) return GBMC_ERR_INVALID_ARG;
+    if (!c->d_imp_cnt) return fail(c, GBMC_ERR_NOT_INITIALIZED, "no importance samples");
+    int64_t n = (int64_t)n_cells_of(*g) * c->n_bins;
+    if (n != c->imp_cells) return fail(c, GBMC_ERR_INVALID_ARG, "geometry differs from the recorded one");
+    *n_out = n;
+    if (!d_feat) return GBMC_OK;
+    if (n_cap < n || !d_target || !d_weight)
+        return fail(c, GBMC_ERR_INVALID_ARG, "need room for %lld rows", (long long)n);
+    int rc = set_device(c);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = mesh_features(mesh_of(c, *g), d_feat, c->sms, s);
+    if (e == cudaSuccess) e = launch_imp_targets(c->d_imp_cnt, c->d_imp_scr, n, d_target, d_weight, c->sms, s);
+    if (e != cudaSuccess) return fail(c, GBMC_ERR_CUDA, "training set: %s", cudaGetErrorString(e));
     return GBMC_OK;
 }
 

@@ -134,6 +134,8 @@ struct Ctl {
     int32_t n_birth_child;       // copies born this iteration (the first births)
     int32_t child_base;          // first of them in the copy buffer
     int32_t birth_reserve;       // free slots the source leaves for split copies
+    int32_t n_imp;               // importance samples recorded
+    int32_t pad6;
     int64_t next_base;           // run index of the first particle born this iteration
     int64_t next, total;         // next unborn run index, particles in the run
     int32_t M;                   // in-flight cap of this run (<= capacity)
@@ -171,6 +173,10 @@ struct Params {
     int32_t ww_max_split;
     int32_t child_cap;       // capacity of the split-copy buffer
     Particle* child;         // split copies waiting for a bank slot
+    int32_t* imp_mesh;       // importance samples: mesh index of a collision (NULL: off)
+    int64_t* imp_gidx;       //   and the history it belongs to
+    int32_t imp_cap;
+    int32_t pad5;
     void* cum;               // running sums of N_i sigma_i, slot-major (NULL: recompute)
     int64_t cum_stride;      // elements per slot (the most nuclides of any material)     // bits of the smallest grid energy
     cudaGraphConditionalHandle cond;

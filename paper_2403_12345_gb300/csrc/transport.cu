@@ -833,6 +833,19 @@ __global__ void __launch_bounds__(256, 3) k_collision(Params P) {
             prob = pt.prob;
             const DevProblem& pr = P.probs[prob];
             wgt = pt.wgt;
+            if (P.imp_mesh && prob == 0 && pt.gidx >= 0) {
+                // importance sample: where this history collided (cell and
+                // energy bin before the collision); its score is its fate
+                const gbmc_geometry& g = pr.g;
+                int32_t cell = g.kind == GBMC_GEOM_LATTICE ? pt.cj * g.n + pt.ci
+                             : g.kind == GBMC_GEOM_SLAB    ? pt.ci
+                                                           : 0;
+                int32_t k = atomicAdd(&c->n_imp, 1);
+                if (k < P.imp_cap) {
+                    P.imp_mesh[k] = cell * P.T.n_bins + energy_bin(P.T, pt.E);
+                    P.imp_gidx[k] = pt.gidx;
+                }
+            }
             Stream r;
             stream_of(pr, pt, r);
             status = collide<PREC>(P, pr, pt, slot, r, wo);
@@ -1085,6 +1098,46 @@ cudaError_t launch_query_lookup(const Params& P, const LaunchCfg& L, const doubl
         k_query_lookup<GBMC_FP64><<<L.grid_lookup, 256, 0, s>>>(P.T, E, mat, n, perm, st, sa);
     else
         k_query_lookup<GBMC_FP32><<<L.grid_lookup, 256, 0, s>>>(P.T, E, mat, n, perm, st, sa);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- importance estimates
+// Scores the collision samples of the last run: per mesh cell, the number of
+// samples and how many of them belong to histories that left through the
+// far face (the analog estimate of the importance there).
+__global__ void k_imp_score(const Ctl* __restrict__ c, int32_t cap, const int32_t* __restrict__ mesh,
+                            const int64_t* __restrict__ gidx, const int8_t* __restrict__ status,
+                            double* __restrict__ cnt, double* __restrict__ scr) {
+    int32_t n = c->n_imp < cap ? c->n_imp : cap;
+    for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        int32_t m = mesh[k];
+        atomicAdd(&cnt[m], 1.0);
+        if (status[gidx[k]] == GBMC_STATUS_LEAKED_FAR) atomicAdd(&scr[m], 1.0);
+    }
+}
+
+// Training targets per mesh cell: ln((s + 1/2) / (n + 1)), weight n.
+__global__ void k_imp_targets(const double* __restrict__ cnt, const double* __restrict__ scr,
+                              int64_t n, float* __restrict__ y, float* __restrict__ w) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        y[k] = (float)log((scr[k] + 0.5) / (cnt[k] + 1.0));
+        w[k] = (float)cnt[k];
+    }
+}
+
+cudaError_t launch_imp_score(const Params& P, const int8_t* status, double* cnt, double* scr,
+                             int sms, cudaStream_t s) {
+    k_imp_score<<<sms * 4, 256, 0, s>>>(P.ctl, P.imp_cap, P.imp_mesh, P.imp_gidx, status, cnt, scr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_imp_targets(const double* cnt, const double* scr, int64_t n, float* y, float* w,
+                               int sms, cudaStream_t s) {
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > sms * 4) blocks = sms * 4;
+    if (blocks < 1) blocks = 1;
+    k_imp_targets<<<blocks, 256, 0, s>>>(cnt, scr, n, y, w);
     return cudaGetLastError();
 }
 

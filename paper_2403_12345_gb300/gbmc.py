@@ -35,7 +35,13 @@ EXPORTS = ["gbmc_default_options", "gbmc_create", "gbmc_destroy", "gbmc_last_err
            "gbmc_reset_tallies", "gbmc_run_batch", "gbmc_run_problems", "gbmc_read_tallies",
            "gbmc_read_outcomes", "gbmc_read_stats", "gbmc_lookup_macro", "gbmc_last_run_ms",
            "gbmc_profile_problems", "gbmc_lookup_macro_noalloc", "gbmc_autotune",
-           "gbmc_set_weight_windows", "gbmc_clear_weight_windows"]
+           "gbmc_set_weight_windows", "gbmc_clear_weight_windows", "gbmc_set_importance_net",
+           "gbmc_get_importance_net", "gbmc_mlp_forward", "gbmc_mlp_gradient", "gbmc_mlp_train",
+           "gbmc_mesh_features", "gbmc_weight_windows_from_net", "gbmc_importance_record",
+           "gbmc_importance_accumulate", "gbmc_importance_training_set",
+           "gbmc_get_weight_windows"]
+MLP_HIDDEN = 64
+MLP_NPARAM = 4545
 NOALLOC_MAX_QUERIES = 1 << 20
 KERNEL_NAMES = ["plan", "source", "sort_keys", "sort_scan", "sort_scatter", "lookup", "raytrace",
                 "collision", "tail"]
@@ -126,6 +132,21 @@ def lib():
         L.gbmc_set_weight_windows.argtypes = [vp, C.c_int32, C.c_int32, _P(C.c_double),
                                               C.c_double, C.c_double, C.c_int32]
         L.gbmc_clear_weight_windows.argtypes = [vp]
+        L.gbmc_get_weight_windows.argtypes = [vp, _P(C.c_double), C.c_int64]
+        L.gbmc_set_importance_net.argtypes = [vp, _P(C.c_uint16), C.c_int32, _P(C.c_double),
+                                              _P(C.c_double)]
+        L.gbmc_get_importance_net.argtypes = [vp, _P(C.c_uint16), C.c_int32]
+        L.gbmc_mlp_forward.argtypes = [vp, vp, C.c_int64, vp, vp]
+        L.gbmc_mlp_gradient.argtypes = [vp, vp, vp, vp, C.c_int64, _P(C.c_float), _P(C.c_float), vp]
+        L.gbmc_mlp_train.argtypes = [vp, vp, vp, vp, C.c_int64, C.c_int32, C.c_float,
+                                     _P(C.c_float), vp]
+        L.gbmc_mesh_features.argtypes = [vp, _P(Geometry), vp, C.c_int64, _P(C.c_int64), vp]
+        L.gbmc_weight_windows_from_net.argtypes = [vp, _P(Geometry), C.c_double, C.c_double,
+                                                   C.c_int32, vp]
+        L.gbmc_importance_record.argtypes = [vp, _P(Geometry), C.c_int64]
+        L.gbmc_importance_accumulate.argtypes = [vp, vp]
+        L.gbmc_importance_training_set.argtypes = [vp, _P(Geometry), vp, vp, vp, C.c_int64,
+                                                   _P(C.c_int64), vp]
         L.gbmc_lookup_macro_noalloc.argtypes = [vp, C.c_int32, vp, vp, C.c_int64, vp, vp, vp]
         L.gbmc_profile_problems.argtypes = [vp, C.c_int32, _P(Problem), vp, _P(KernelTimes),
                                             C.c_int32, _P(C.c_double), _P(C.c_int32),
@@ -264,8 +285,82 @@ class Context:
                                                _p(lo, C.c_double), float(ratio), float(survival),
                                                int(max_split)))
 
+    def get_weight_windows(self, n_cells):
+        lo = np.zeros((n_cells, self.n_bins))
+        self._ck(lib().gbmc_get_weight_windows(self._h, _p(lo, C.c_double), lo.size))
+        return lo
+
     def clear_weight_windows(self):
         self._ck(lib().gbmc_clear_weight_windows(self._h))
+
+    # -- importance network ----------------------------------------------------
+    def set_importance_net(self, bf16_params, feat_offset, feat_scale):
+        """bf16_params: uint16 BF16 bit patterns [MLP_NPARAM]."""
+        p = np.ascontiguousarray(bf16_params, dtype=np.uint16)
+        off = np.ascontiguousarray(feat_offset, dtype=np.float64)
+        sc = np.ascontiguousarray(feat_scale, dtype=np.float64)
+        self._ck(lib().gbmc_set_importance_net(self._h, _p(p, C.c_uint16), len(p),
+                                               _p(off, C.c_double), _p(sc, C.c_double)))
+
+    def get_importance_net(self):
+        p = np.zeros(MLP_NPARAM, np.uint16)
+        self._ck(lib().gbmc_get_importance_net(self._h, _p(p, C.c_uint16), MLP_NPARAM))
+        return p
+
+    @staticmethod
+    def _dptr(t):
+        return C.c_void_p(t if isinstance(t, int) else t.data_ptr())
+
+    def mlp_forward(self, feat, out, stream=None):
+        n = feat.shape[0]
+        self._ck(lib().gbmc_mlp_forward(self._h, self._dptr(feat), int(n), self._dptr(out),
+                                        _stream(stream)))
+
+    def mlp_gradient(self, feat, target, weight, stream=None):
+        g = np.zeros(MLP_NPARAM, np.float32)
+        loss = C.c_float()
+        self._ck(lib().gbmc_mlp_gradient(self._h, self._dptr(feat), self._dptr(target),
+                                         self._dptr(weight), int(feat.shape[0]),
+                                         _p(g, C.c_float), C.byref(loss), _stream(stream)))
+        return loss.value, g
+
+    def mlp_train(self, feat, target, weight, steps, lr, stream=None):
+        loss = C.c_float()
+        self._ck(lib().gbmc_mlp_train(self._h, self._dptr(feat), self._dptr(target),
+                                      self._dptr(weight), int(feat.shape[0]), int(steps),
+                                      float(lr), C.byref(loss), _stream(stream)))
+        return loss.value
+
+    def mesh_rows(self, geom) -> int:
+        n = C.c_int64()
+        self._ck(lib().gbmc_mesh_features(self._h, C.byref(geom), None, 0, C.byref(n), None))
+        return n.value
+
+    def mesh_features(self, geom, feat, stream=None):
+        n = C.c_int64()
+        self._ck(lib().gbmc_mesh_features(self._h, C.byref(geom), self._dptr(feat),
+                                          int(feat.shape[0]), C.byref(n), _stream(stream)))
+        return n.value
+
+    def weight_windows_from_net(self, geom, ratio=5.0, survival=2.5, max_split=10, stream=None):
+        self._ck(lib().gbmc_weight_windows_from_net(self._h, C.byref(geom), float(ratio),
+                                                    float(survival), int(max_split),
+                                                    _stream(stream)))
+
+    def importance_record(self, geom=None, capacity=0):
+        self._ck(lib().gbmc_importance_record(self._h, C.byref(geom) if geom is not None else None,
+                                              int(capacity)))
+
+    def importance_accumulate(self, stream=None):
+        self._ck(lib().gbmc_importance_accumulate(self._h, _stream(stream)))
+
+    def importance_training_set(self, geom, feat, target, weight, stream=None):
+        n = C.c_int64()
+        self._ck(lib().gbmc_importance_training_set(self._h, C.byref(geom), self._dptr(feat),
+                                                    self._dptr(target), self._dptr(weight),
+                                                    int(feat.shape[0]), C.byref(n),
+                                                    _stream(stream)))
+        return n.value
 
     def reset_tallies(self, stream=None):
         self._ck(lib().gbmc_reset_tallies(self._h, _stream(stream)))

@@ -257,9 +257,10 @@ def make_config(k: int, n_particles: Optional[int] = None,
     raise ValueError(f"unknown configuration {k}")
 
 
-# Multiplier on the slab absorber densities (configuration 5), chosen so that
-# the analog far-face leakage probability sits in [1e-6, 1e-4].
-SLAB_ABSORBER_SCALE = 0.05
+# Multiplier on the slab absorber densities (configuration 5), chosen by a
+# pilot analog run of the CPU oracle so that the analog far-face leakage
+# probability sits in [1e-6, 1e-4]: 41 of 4e6 histories (1.0e-5) at 0.1.
+SLAB_ABSORBER_SCALE = 0.1
 
 
 def make_stress_lookup(n_queries: int = 10_000_000, n_nuc: int = 281,
