@@ -96,7 +96,9 @@ def test_windows_from_a_handmade_network():
     finally:
         ctx.close()
     x = (np.arange(g.n_layers) + 0.5) * g.layer_dx
-    out = 2.0 * x / (g.n_layers * g.layer_dx)
+    # the feature in binary32, rounded to BF16 where it enters the tensor cores
+    f0 = (x * sc[0]).astype(np.float32)
+    out = 2.0 * imp.from_bf16(imp.to_bf16(f0)).astype(np.float64)
     expect = np.exp(out[0] - out) / 2.5
     assert np.allclose(lower, expect[:, None], rtol=1e-5, atol=0)
 
