@@ -138,7 +138,7 @@ struct gbmc_ctx {
     int64_t* d_imp_gidx = nullptr;
     int32_t imp_cap = 0;
     bool imp_on = false;
-    double *d_imp_cnt = nullptr, *d_imp_scr = nullptr;
+    double *d_imp_cnt = nullptr, *d_imp_scr = nullptr, *d_imp_cellsum = nullptr;
     int64_t imp_cells = 0;
 
     // standalone-lookup scratch
@@ -688,6 +688,7 @@ int gbmc_destroy(gbmc_ctx* c) {
     dfree(c->d_net_p); dfree(c->d_net_m); dfree(c->d_net_v); dfree(c->d_net_g);
     dfree(c->d_net_scratch); dfree(c->d_net_w); dfree(c->d_mesh_feat); dfree(c->d_mesh_out);
     dfree(c->d_imp_mesh); dfree(c->d_imp_gidx); dfree(c->d_imp_cnt); dfree(c->d_imp_scr);
+    dfree(c->d_imp_cellsum);
     if (c->d_cum) { cudaDeviceSynchronize(); cudaFree(c->d_cum); }
     dfree(c->q_perm); dfree(c->q_keys); dfree(c->q_hist); dfree(c->q_cursor); dfree(c->q_btot);
     if (c->h_probs) cudaFreeHost(c->h_probs);
@@ -1488,8 +1489,12 @@ extern "C" int gbmc_importance_training_set(gbmc_ctx* c, const gbmc_geometry* g,
     int rc = set_device(c);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
+    int32_t cells = n_cells_of(*g);
+    if ((rc = dalloc(c, &c->d_imp_cellsum, 2 * (size_t)cells + 2))) return rc;
     cudaError_t e = mesh_features(mesh_of(c, *g), d_feat, c->sms, s);
-    if (e == cudaSuccess) e = launch_imp_targets(c->d_imp_cnt, c->d_imp_scr, n, d_target, d_weight, c->sms, s);
+    if (e == cudaSuccess)
+        e = launch_imp_targets(c->d_imp_cnt, c->d_imp_scr, cells, c->n_bins, c->d_imp_cellsum,
+                               d_target, d_weight, c->sms, s);
     if (e != cudaSuccess) return fail(c, GBMC_ERR_CUDA, "training set: %s", cudaGetErrorString(e));
     return GBMC_OK;
 }

@@ -40,7 +40,8 @@ cudaError_t launch_query_lookup(const Params& P, const LaunchCfg& L, const doubl
 // Importance estimates from recorded collision samples of the last run.
 cudaError_t launch_imp_score(const Params& P, const int8_t* status, double* cnt, double* scr,
                              int sms, cudaStream_t s);
-cudaError_t launch_imp_targets(const double* cnt, const double* scr, int64_t n, float* y, float* w,
-                               int sms, cudaStream_t s);
+cudaError_t launch_imp_targets(const double* cnt, const double* scr, int32_t n_cells,
+                               int32_t n_bins, double* cell_sums, float* y, float* w, int sms,
+                               cudaStream_t s);
 
 }  // namespace gbmc

@@ -1116,13 +1116,43 @@ __global__ void k_imp_score(const Ctl* __restrict__ c, int32_t cap, const int32_
     }
 }
 
-// Training targets per mesh cell: ln((s + 1/2) / (n + 1)), weight n.
+// Training targets from the scored samples, with shrinkage where data is
+// sparse (deep penetration leaves most cells without a scoring history):
+// a cell's importance pools its energy bins, I_c = (S_c + a p0) / (N_c + a)
+// with p0 the overall score fraction; a bin's, I_b = (s + a I_c) / (n + a).
+// Target ln I_b; weight n / (n + a) + 1/10 in cells with samples, 0 in
+// cells never reached (the network extrapolates there).
+constexpr double kShrink = 5.0;
+
+__global__ void k_imp_cells(const double* __restrict__ cnt, const double* __restrict__ scr,
+                            int32_t n_cells, int32_t n_bins, double* __restrict__ cell_sums) {
+    for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += gridDim.x * blockDim.x) {
+        double N = 0.0, S = 0.0;
+        for (int32_t b = 0; b < n_bins; ++b) {
+            N += cnt[(int64_t)c * n_bins + b];
+            S += scr[(int64_t)c * n_bins + b];
+        }
+        cell_sums[2 * c] = N;
+        cell_sums[2 * c + 1] = S;
+        atomicAdd(&cell_sums[2 * n_cells], N);
+        atomicAdd(&cell_sums[2 * n_cells + 1], S);
+    }
+}
+
 __global__ void k_imp_targets(const double* __restrict__ cnt, const double* __restrict__ scr,
-                              int64_t n, float* __restrict__ y, float* __restrict__ w) {
+                              const double* __restrict__ cell_sums, int32_t n_cells, int32_t n_bins,
+                              float* __restrict__ y, float* __restrict__ w) {
+    int64_t n = (int64_t)n_cells * n_bins;
+    double Nt = cell_sums[2 * n_cells], St = cell_sums[2 * n_cells + 1];
+    double p0 = Nt > 0.0 ? (St + 0.5) / (Nt + 1.0) : 1e-12;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
-        y[k] = (float)log((scr[k] + 0.5) / (cnt[k] + 1.0));
-        w[k] = (float)cnt[k];
+        int32_t c = (int32_t)(k / n_bins);
+        double Nc = cell_sums[2 * c], Sc = cell_sums[2 * c + 1];
+        double Ic = (Sc + kShrink * p0) / (Nc + kShrink);
+        double Ib = (scr[k] + kShrink * Ic) / (cnt[k] + kShrink);
+        y[k] = (float)log(Ib);
+        w[k] = Nc > 0.0 ? (float)(cnt[k] / (cnt[k] + kShrink) + 0.1) : 0.f;
     }
 }
 
@@ -1132,12 +1162,17 @@ cudaError_t launch_imp_score(const Params& P, const int8_t* status, double* cnt,
     return cudaGetLastError();
 }
 
-cudaError_t launch_imp_targets(const double* cnt, const double* scr, int64_t n, float* y, float* w,
-                               int sms, cudaStream_t s) {
+cudaError_t launch_imp_targets(const double* cnt, const double* scr, int32_t n_cells,
+                               int32_t n_bins, double* cell_sums, float* y, float* w, int sms,
+                               cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(cell_sums, 0, sizeof(double) * (2 * (size_t)n_cells + 2), s);
+    if (e != cudaSuccess) return e;
+    k_imp_cells<<<(n_cells + 255) / 256, 256, 0, s>>>(cnt, scr, n_cells, n_bins, cell_sums);
+    int64_t n = (int64_t)n_cells * n_bins;
     int blocks = (int)((n + 255) / 256);
     if (blocks > sms * 4) blocks = sms * 4;
     if (blocks < 1) blocks = 1;
-    k_imp_targets<<<blocks, 256, 0, s>>>(cnt, scr, n, y, w);
+    k_imp_targets<<<blocks, 256, 0, s>>>(cnt, scr, cell_sums, n_cells, n_bins, y, w);
     return cudaGetLastError();
 }
 
