@@ -358,8 +358,8 @@ int gbmc_weight_windows_from_net(gbmc_ctx *ctx, const gbmc_geometry *g, double r
  * gbmc_importance_training_set writes the mesh features, targets and
  * weights to DEVICE arrays of n_cap rows: a cell's importance pools its
  * energy bins, I_c = (S_c + 5 p0) / (N_c + 5) with p0 the overall score
- * fraction, a bin's I_b = (s + 5 I_c) / (n + 5); target ln I_b, weight
- * n / (n + 5) + 0.1 (0 in cells no history reached). */
+ * fraction; every bin of the cell gets target ln I_c and weight
+ * N_c / (N_c + 5) (0 in cells no history reached). */
 int gbmc_importance_record(gbmc_ctx *ctx, const gbmc_geometry *g, int64_t capacity);
 int gbmc_importance_accumulate(gbmc_ctx *ctx, void *stream);
 int gbmc_importance_training_set(gbmc_ctx *ctx, const gbmc_geometry *g, float *d_feat,

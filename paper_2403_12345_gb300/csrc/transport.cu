@@ -1116,12 +1116,12 @@ __global__ void k_imp_score(const Ctl* __restrict__ c, int32_t cap, const int32_
     }
 }
 
-// Training targets from the scored samples, with shrinkage where data is
-// sparse (deep penetration leaves most cells without a scoring history):
-// a cell's importance pools its energy bins, I_c = (S_c + a p0) / (N_c + a)
-// with p0 the overall score fraction; a bin's, I_b = (s + a I_c) / (n + a).
-// Target ln I_b; weight n / (n + a) + 1/10 in cells with samples, 0 in
-// cells never reached (the network extrapolates there).
+// Training targets from the scored samples.  Deep penetration leaves almost
+// every (cell, energy bin) without a scoring history, so a cell's
+// importance pools its energy bins and shrinks toward the overall score
+// fraction p0: I_c = (S_c + a p0) / (N_c + a).  Every bin of the cell gets
+// target ln I_c and weight N_c / (N_c + a); cells never reached get weight 0
+// (the network extrapolates there).
 constexpr double kShrink = 5.0;
 
 __global__ void k_imp_cells(const double* __restrict__ cnt, const double* __restrict__ scr,
@@ -1150,9 +1150,8 @@ __global__ void k_imp_targets(const double* __restrict__ cnt, const double* __re
         int32_t c = (int32_t)(k / n_bins);
         double Nc = cell_sums[2 * c], Sc = cell_sums[2 * c + 1];
         double Ic = (Sc + kShrink * p0) / (Nc + kShrink);
-        double Ib = (scr[k] + kShrink * Ic) / (cnt[k] + kShrink);
-        y[k] = (float)log(Ib);
-        w[k] = Nc > 0.0 ? (float)(cnt[k] / (cnt[k] + kShrink) + 0.1) : 0.f;
+        y[k] = (float)log(Ic);
+        w[k] = (float)(Nc / (Nc + kShrink));
     }
 }
 
