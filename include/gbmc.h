@@ -338,7 +338,8 @@ int gbmc_mlp_train(gbmc_ctx *ctx, const float *d_feat, const float *d_target,
 
 /* Features of the mesh (cells of geometry g x tally energy bins: cell
  * centre, logarithmic bin centre) into DEVICE d_feat [n][4] with the
- * network's feature map; *n_out = number of rows (d_feat NULL: count only). */
+ * network's feature map (the network must be set); *n_out = number of rows
+ * (d_feat NULL: count only). */
 int gbmc_mesh_features(gbmc_ctx *ctx, const gbmc_geometry *g, float *d_feat, int64_t n_cap,
                        int64_t *n_out, void *stream);
 
@@ -355,7 +356,8 @@ int gbmc_weight_windows_from_net(gbmc_ctx *ctx, const gbmc_geometry *g, double r
  * gbmc_importance_accumulate, after each such run, scores those samples by
  * whether their history left through the slab's far face, into per-mesh
  * counts n and scores s (kept across runs).
- * gbmc_importance_training_set writes the mesh features, targets and
+ * gbmc_importance_training_set writes the mesh features (the network's
+ * feature map: set the network first), targets and
  * weights to DEVICE arrays of n_cap rows: a cell's importance pools its
  * energy bins, I_c = (S_c + 5 p0) / (N_c + 5) with p0 the overall score
  * fraction; every bin of the cell gets target ln I_c and weight

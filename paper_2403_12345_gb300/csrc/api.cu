@@ -1386,7 +1386,9 @@ extern "C" int gbmc_mesh_features(gbmc_ctx* c, const gbmc_geometry* g, float* d_
     *n_out = n;
     if (!d_feat) return GBMC_OK;
     if (n_cap < n) return fail(c, GBMC_ERR_INVALID_ARG, "need room for %lld feature rows", (long long)n);
-    int rc = set_device(c);
+    int rc = need_net(c);   // the features use the network's feature map
+    if (rc) return rc;
+    rc = set_device(c);
     if (rc) return rc;
     cudaError_t e = mesh_features(mesh_of(c, *g), d_feat, c->sms, (cudaStream_t)stream);
     if (e != cudaSuccess) return fail(c, GBMC_ERR_CUDA, "mesh features: %s", cudaGetErrorString(e));
@@ -1486,7 +1488,9 @@ extern "C" int gbmc_importance_training_set(gbmc_ctx* c, const gbmc_geometry* g,
     if (!d_feat) return GBMC_OK;
     if (n_cap < n || !d_target || !d_weight)
         return fail(c, GBMC_ERR_INVALID_ARG, "need room for %lld rows", (long long)n);
-    int rc = set_device(c);
+    int rc = need_net(c);   // the features use the network's feature map
+    if (rc) return rc;
+    rc = set_device(c);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     int32_t cells = n_cells_of(*g);

@@ -89,8 +89,9 @@ class LearnedWindows:
         feat = torch.empty((n, 4), dtype=torch.float32, device="cuda")
         y = torch.empty(n, dtype=torch.float32, device="cuda")
         w = torch.empty(n, dtype=torch.float32, device="cuda")
-        self.ctx.importance_training_set(self.geom, feat, y, w, stream)
+        # the network's feature map first: the training set's features use it
         self.ctx.set_importance_net(init_params(self.seed), self.offset, self.scale)
+        self.ctx.importance_training_set(self.geom, feat, y, w, stream)
         self.loss = self.ctx.mlp_train(feat, y, w, steps, lr, stream)
         self.data = (feat, y, w)
         return self.loss
