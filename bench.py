@@ -193,7 +193,7 @@ def main():
 
     import torch
     import torch.distributed as dist
-    from paper_2403_12345_gb300 import gbmc
+    from paper_2403_12345_gb300 import gbmc, replicas
 
     torch.cuda.set_device(local)
     if world > 1:
@@ -259,9 +259,7 @@ def main():
     # replicas: one tally reduction after the timed region (domain replication)
     flux, counts_, weights = ctx.read_tallies(0)
     if world > 1:
-        t = torch.tensor(flux, device="cuda")
-        dist.all_reduce(t)
-        flux = t.cpu().numpy()
+        flux, counts_, weights = replicas.allreduce_tallies(flux, counts_, weights)
 
     # end to end through the C ABI with host buffers: run, then copy every
     # problem's tallies and every particle's outcome (collisions, fate) to
