@@ -90,6 +90,10 @@ struct gbmc_ctx {
     int32_t probs_cap = 0;
     DevProblem* h_probs = nullptr;   // pinned staging
     int32_t h_probs_cap = 0;
+    double* d_planes = nullptr;      // plane tables of the run's problems
+    int64_t planes_cap = 0;
+    double* h_planes = nullptr;      // pinned staging
+    int64_t h_planes_cap = 0;
     Ctl* d_ctl = nullptr;
     Ctl* h_ctl = nullptr;            // pinned staging / read-back
     cudaEvent_t staged = nullptr;
@@ -394,6 +398,7 @@ Params make_params(gbmc_ctx* c) {
     P.tail_max = c->opt.tail_max;
     P.max_iter = c->opt.max_iterations;
     sort_params(c, P);
+    P.planes = c->d_planes;
     P.cum = c->d_cum;
     P.cum_stride = c->d_cum ? cum_row(c) : 0;
     if (c->ww_on) {
@@ -683,7 +688,7 @@ int gbmc_destroy(gbmc_ctx* c) {
     dfree(c->d_fabs); dfree(c->d_fabs32); dfree(c->d_awr);
     dfree(c->d_nx64); dfree(c->d_nx32); dfree(c->d_idx64); dfree(c->d_idx32);
     dfree(c->d_mat_off); dfree(c->d_nuc_id); dfree(c->d_density); dfree(c->d_density32);
-    dfree(c->d_edges); dfree(c->d_probs); dfree(c->d_ctl);
+    dfree(c->d_edges); dfree(c->d_probs); dfree(c->d_planes); dfree(c->d_ctl);
     dfree(c->d_ww); dfree(c->d_child);
     dfree(c->d_net_p); dfree(c->d_net_m); dfree(c->d_net_v); dfree(c->d_net_g);
     dfree(c->d_net_scratch); dfree(c->d_net_w); dfree(c->d_mesh_feat); dfree(c->d_mesh_out);
@@ -692,6 +697,7 @@ int gbmc_destroy(gbmc_ctx* c) {
     if (c->d_cum) { cudaDeviceSynchronize(); cudaFree(c->d_cum); }
     dfree(c->q_perm); dfree(c->q_keys); dfree(c->q_hist); dfree(c->q_cursor); dfree(c->q_btot);
     if (c->h_probs) cudaFreeHost(c->h_probs);
+    if (c->h_planes) cudaFreeHost(c->h_planes);
     if (c->h_ctl) cudaFreeHost(c->h_ctl);
     if (c->staged) cudaEventDestroy(c->staged);
     if (c->ev0) cudaEventDestroy(c->ev0);
@@ -895,8 +901,8 @@ int prepare_run(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, cudaStre
     if ((c->opt.precision == GBMC_FP64 && !c->has64) || (c->opt.precision == GBMC_FP32 && !c->has32))
         return fail(c, GBMC_ERR_NOT_INITIALIZED, "tables not loaded in the selected precision");
     std::vector<int32_t> cells(n_prob);
-    std::vector<int64_t> start(n_prob), nn(n_prob);
-    int64_t total = 0;
+    std::vector<int64_t> start(n_prob), nn(n_prob), plane_off(n_prob);
+    int64_t total = 0, n_planes = 0;
     for (int32_t p = 0; p < n_prob; ++p) {
         int rc = check_geometry(c, probs[p].geom, p);
         if (rc) return rc;
@@ -904,6 +910,11 @@ int prepare_run(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, cudaStre
             probs[p].first_id > std::numeric_limits<int64_t>::max() - probs[p].n_particles)
             return fail(c, GBMC_ERR_INVALID_ARG, "problem %d: bad particle range", p);
         cells[p] = n_cells_of(probs[p].geom);
+        plane_off[p] = n_planes;
+        const gbmc_geometry& g = probs[p].geom;
+        n_planes += g.kind == GBMC_GEOM_LATTICE ? 2 * (int64_t)g.n + 1
+                  : g.kind == GBMC_GEOM_SLAB    ? (int64_t)g.n_layers + 1
+                                                : 0;
         start[p] = total;
         nn[p] = probs[p].n_particles;
         total += probs[p].n_particles;
@@ -937,6 +948,19 @@ int prepare_run(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, cudaStre
         c->probs_cap = n_prob;
         c->graph_valid = false;
     }
+    if (n_planes < 1) n_planes = 1;
+    if (n_planes > c->planes_cap) {
+        if ((rc = dalloc(c, &c->d_planes, (size_t)n_planes))) return rc;
+        c->planes_cap = n_planes;
+        c->graph_valid = false;
+    }
+    if (n_planes > c->h_planes_cap) {
+        CK(cudaEventSynchronize(c->staged));
+        if (c->h_planes) cudaFreeHost(c->h_planes);
+        c->h_planes = nullptr;
+        CK(cudaMallocHost((void**)&c->h_planes, sizeof(double) * n_planes));
+        c->h_planes_cap = n_planes;
+    }
     if (n_prob > c->h_probs_cap) {
         CK(cudaEventSynchronize(c->staged));
         if (c->h_probs) cudaFreeHost(c->h_probs);
@@ -958,7 +982,18 @@ int prepare_run(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, cudaStre
         d.n = probs[p].n_particles;
         d.start = start[p];
         d.flux_off = c->slot_flux_off[p];
+        d.plane_off = plane_off[p];
         d.n_cells = cells[p];
+        // plane positions as the transport forms them: walls i * pitch
+        // (i = 0..n), then lattice cell centres (i + 0.5) * pitch
+        const gbmc_geometry& g = probs[p].geom;
+        double* w = c->h_planes + plane_off[p];
+        if (g.kind == GBMC_GEOM_LATTICE) {
+            for (int32_t i = 0; i <= g.n; ++i) w[i] = (double)i * g.pitch;
+            for (int32_t i = 0; i < g.n; ++i) w[g.n + 1 + i] = ((double)i + 0.5) * g.pitch;
+        } else if (g.kind == GBMC_GEOM_SLAB) {
+            for (int32_t i = 0; i <= g.n_layers; ++i) w[i] = (double)i * g.layer_dx;
+        }
     }
     Ctl& k = *c->h_ctl;
     memset(&k, 0, sizeof k);
@@ -969,6 +1004,7 @@ int prepare_run(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, cudaStre
     k.n_prob = n_prob;
     k.birth_reserve = c->ww_on ? M / 2 : 0;
     CK(cudaMemcpyAsync(c->d_probs, c->h_probs, sizeof(DevProblem) * n_prob, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->d_planes, c->h_planes, sizeof(double) * n_planes, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c->d_ctl, c->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
     CK(cudaEventRecord(c->staged, s));
     c->run_start = start;

@@ -59,6 +59,8 @@ struct DevProblem {
     uint64_t seed, key_hi;
     int64_t first_id, n, start;   // start: index of its first particle in the run
     int64_t flux_off;             // offset of its flux tally
+    int64_t plane_off;            // its plane table: walls (double)i * pitch, i = 0..n, then
+                                  // lattice cell centres ((double)i + 0.5) * pitch, i < n
     int32_t n_cells, pad;
 };
 
@@ -177,6 +179,7 @@ struct Params {
     int64_t* imp_gidx;       //   and the history it belongs to
     int32_t imp_cap;
     int32_t pad5;
+    const double* planes;    // plane tables of the run's problems (DevProblem::plane_off)
     void* cum;               // running sums of N_i sigma_i, slot-major (NULL: recompute)
     int64_t cum_stride;      // elements per slot (the most nuclides of any material)     // bits of the smallest grid energy
     cudaGraphConditionalHandle cond;
@@ -240,7 +243,16 @@ struct Stream {
         uint32_t w = j & 3u;
         uint64_t x = w == 0 ? b.c0 : (w == 1 ? b.c1 : (w == 2 ? b.c2 : b.c3));
         j += 1;
-        return (double)((x >> 11) + 1ull) * 0x1.0p-53;
+        return u01(x);
+    }
+    // ((x >> 11) + 1) 2^-53 in (0, 1], assembled exactly from its bits on the
+    // integer units: the leading one of the 53-bit integer n sets the
+    // exponent, the bits below it the significand.
+    __device__ __forceinline__ static double u01(uint64_t x) {
+        uint64_t n = (x >> 11) + 1ull;
+        int lz = __clzll((long long)n);
+        uint64_t sig = ((n << lz) & 0x7FFFFFFFFFFFFFFFull) >> 11;
+        return __longlong_as_double((long long)(((uint64_t)(1033 - lz) << 52) | sig));
     }
 };
 
@@ -583,33 +595,139 @@ __device__ __forceinline__ int32_t energy_bin(const Tables& T, double E) {
 // ---------------------------------------------------------------- geometry
 enum : uint8_t { kSurfNone = 0, kSurfCyl = 1, kSurfX = 2, kSurfY = 3, kSurfZ = 4 };
 
-// Distance along (u, v) from (dx, dy), relative to the pin axis, to the
-// cylinder of radius r: a d^2 + 2 k d + c = 0 with a = u^2 + v^2,
-// k = dx u + dy v, c = dx^2 + dy^2 - r^2, D = k^2 - a c, each root in its
-// cancellation-free form.  Inside: the far root; outside: the near root if
-// the path approaches and meets the cylinder, else no crossing.
-__device__ __forceinline__ double dist_cylinder(double dx, double dy, double u, double v,
-                                                double r, bool inside) {
-    double a = u * u + v * v;
-    double k = dx * u + dy * v;
-    double c = (dx * dx + dy * dy) - r * r;
-    double D = k * k - a * c;
-    if (inside) {
-        if (a == 0.0) return CUDART_INF;
-        if (D < 0.0) D = 0.0;
-        double sD = sqrt(D);
-        if (k <= 0.0) return (sD - k) / a;
-        return (0.0 - c) / (k + sD);
-    }
-    if (a == 0.0 || k >= 0.0 || D < 0.0) return CUDART_INF;
-    double sD = sqrt(D);
-    return c / (sD - k);
+// ---------------------------------------------------------------- screened distances
+// A flight needs only the smallest of its candidate distances (distance to
+// collision, and the cylinder, x, y and z surfaces of its cell) and that
+// one's value; each candidate is one correctly rounded binary64 expression.
+// Every candidate is first estimated in binary32 from its binary64 operands
+// truncated to 24 significant bits: with no cancellation in the estimate
+// (each sum below adds terms of one sign), it lies within 3 * 2^-23
+// relative of the binary64 value (three truncations or roundings of 2^-23
+// or 2^-24), and its span widens that to 2^-16.  Only a candidate whose span
+// leaves it a possible minimum is evaluated in binary64, so the distance
+// chosen, its value and the tie order are exactly those of evaluating every
+// candidate in binary64, at a fraction of the binary64 divisions, square
+// roots and logarithms (the scarce units of this GPU).
+
+// binary64 -> binary32 by truncating the significand (relative error below
+// 2^-23, sign kept); ok is false outside the normal binary32 range (zero is
+// exact).  Integer instructions only.
+__device__ __forceinline__ float trunc32(double x, bool& ok) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    unsigned hi = (unsigned)(b >> 32);
+    unsigned e = (hi >> 20) & 0x7ffu;
+    bool zero = (b << 1) == 0ull;
+    ok = zero || (e >= 897u && e <= 1150u);
+    unsigned f = (hi & 0x80000000u) | ((e - 896u) << 23) | (unsigned)((b >> 29) & 0x7fffffu);
+    return zero ? 0.0f : __uint_as_float(f);
 }
 
-__device__ __forceinline__ double dist_planes(double x, double u, double lo, double hi) {
-    if (u > 0.0) return (hi - x) / u;
-    if (u < 0.0) return (lo - x) / u;
-    return CUDART_INF;
+// Bounds [lo, hi] of a non-negative distance (a negative value counts as
+// zero) from its binary32 estimate a.
+struct Span {
+    float lo, hi;
+};
+constexpr float kSpanLo = 1.0f - 0x1p-16f, kSpanHi = 1.0f + 0x1p-16f;
+
+__device__ __forceinline__ Span span_of(float a, bool ok) {
+    const float inf = __int_as_float(0x7f800000);
+    if (!ok || !(a == a)) return {0.0f, inf};     // no estimate: anything
+    if (a <= 0.0f) return {0.0f, 1e-37f};          // zero, or below binary32's range
+    if (a == inf) return {1e38f, inf};             // beyond binary32's range
+    return {fmaxf(a * kSpanLo - 1e-37f, 0.0f), a * kSpanHi + 1e-37f};
+}
+
+__device__ __forceinline__ Span span_never() {
+    const float inf = __int_as_float(0x7f800000);
+    return {inf, inf};
+}
+
+// Sign tests on the bit pattern (no binary64 compare).
+__device__ __forceinline__ bool is_neg(double x) {
+    long long b = __double_as_longlong(x);
+    return b < 0 && (b << 1) != 0;
+}
+__device__ __forceinline__ bool is_pos(double x) {
+    long long b = __double_as_longlong(x);
+    return b > 0;
+}
+
+// Cylinder of radius r about the pin axis, from (dx, dy) relative to the
+// axis along (u, v): a d^2 + 2 k d + c = 0 with a = u^2 + v^2,
+// k = dx u + dy v, c = dx^2 + dy^2 - r^2, D = k^2 - a c, each root in its
+// cancellation-free form.  Inside: the far root ((sqrt D - k) / a for
+// k <= 0, -c / (k + sqrt D) otherwise; D < 0 counts as 0); outside: the near
+// root c / (sqrt D - k) if the path approaches (k < 0) and meets the
+// cylinder (D >= 0), else none.
+struct Cyl {
+    double a, k, c, D;
+    int kind;   // 0: no crossing, 1: (sD - k) / a, 2: -c / (k + sD), 3: c / (sD - k)
+};
+
+__device__ __forceinline__ Cyl cylinder_of(double dx, double dy, double u, double v, double r,
+                                           bool inside) {
+    Cyl q;
+    q.a = u * u + v * v;
+    q.k = dx * u + dy * v;
+    q.c = (dx * dx + dy * dy) - r * r;
+    q.D = q.k * q.k - q.a * q.c;
+    bool a0 = (__double_as_longlong(q.a) << 1) == 0;
+    if (inside) {
+        if (is_neg(q.D)) q.D = 0.0;
+        q.kind = a0 ? 0 : (is_pos(q.k) ? 2 : 1);
+    } else {
+        q.kind = (a0 || !is_neg(q.k) || is_neg(q.D)) ? 0 : 3;
+    }
+    return q;
+}
+
+__device__ __forceinline__ Span cylinder_span(const Cyl& q) {
+    if (q.kind == 0) return span_never();
+    bool oa, ok, oc, oD;
+    float a = trunc32(q.a, oa), k = trunc32(q.k, ok), c = trunc32(q.c, oc);
+    float sD = sqrtf(trunc32(q.D, oD));
+    float e = q.kind == 1 ? (sD - k) / a : q.kind == 2 ? (0.0f - c) / (k + sD) : c / (sD - k);
+    bool good = ok && oD && (q.kind == 1 ? oa : oc);
+    return span_of(e, good);
+}
+
+__device__ __forceinline__ double cylinder_exact(const Cyl& q) {
+    if (q.kind == 0) return CUDART_INF;
+    double sD = sqrt(q.D);
+    if (q.kind == 1) return (sD - q.k) / q.a;
+    if (q.kind == 2) return (0.0 - q.c) / (q.k + sD);
+    return q.c / (sD - q.k);
+}
+
+// Plane pair [lo, hi] crossed along direction cosine u from x: the
+// numerator (hi - x for u > 0, lo - x for u < 0) and its quotient by u.
+__device__ __forceinline__ Span plane_span(double num, double u) {
+    if ((__double_as_longlong(u) << 1) == 0) return span_never();
+    bool on, ou;
+    float n = trunc32(num, on), d = trunc32(u, ou);
+    return span_of(n / d, on && ou);
+}
+
+__device__ __forceinline__ double plane_exact(double num, double u) {
+    if ((__double_as_longlong(u) << 1) == 0) return CUDART_INF;
+    return num / u;
+}
+
+// Distance to collision -ln(xi) / Sigma_t estimated with the binary32
+// logarithm (within 2^-23 absolute from the truncated xi, plus one ulp):
+// the span takes 2^-20 absolute on the logarithm, then the relative margin.
+__device__ __forceinline__ Span collision_span(double xi, double st) {
+    bool ox, os;
+    float l = 0.0f - logf(trunc32(xi, ox));
+    float s = trunc32(st, os);
+    if (!(ox && os) || !(s > 0.0f)) return span_of(0.0f, false);
+    const float inf = __int_as_float(0x7f800000);
+    float lo = fmaxf(l - 0x1p-20f, 0.0f) / s;
+    float hi = (l + 0x1p-20f) / s;
+    Span sp;
+    sp.lo = lo == inf ? 1e38f : fmaxf(lo * kSpanLo - 1e-37f, 0.0f);
+    sp.hi = hi * kSpanHi + 1e-37f;
+    return sp;
 }
 
 // Elastic scatter off a nucleus at rest, isotropic in the centre-of-mass

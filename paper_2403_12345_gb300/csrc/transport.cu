@@ -477,55 +477,121 @@ __device__ __forceinline__ void stream_of(const DevProblem& pr, const Particle& 
     r.init(pr.seed, pr.key_hi, pt.hid, pt.rj);
 }
 
+__device__ __forceinline__ int32_t cell_of(const gbmc_geometry& g, const Particle& pt) {
+    return g.kind == GBMC_GEOM_LATTICE ? pt.cj * g.n + pt.ci
+         : g.kind == GBMC_GEOM_SLAB    ? pt.ci
+                                       : 0;
+}
+
 // One flight (advance event): sample the distance to collision, find the
-// nearest surface of the current cell (ties: cylinder, x, y, z), move by
-// the smaller one and score w d in the (cell, energy bin) flux tally.
-// Returns true for a collision; otherwise pt.surf names the surface reached.
+// nearest surface of the current cell (ties: cylinder, x, y, z) and compare.
+// Returns true for a collision, leaving the particle where it is: the move
+// by -ln(xi) / Sigma_t and its track-length score are finish_flight's, run
+// by the collision event, where every lane of a warp needs that logarithm.
+// Otherwise the particle moves to pt.surf and scores w d in the (cell,
+// energy bin) flux tally.  The candidates are screened by their binary32
+// spans: a surface decided by its span alone costs one binary64 quotient,
+// taken by all such lanes of a warp together.
 __device__ __forceinline__ bool fly(const Params& P, const DevProblem& pr, Particle& pt,
-                                    Stream& r) {
+                                    Stream& r, double& xi) {
     const gbmc_geometry& g = pr.g;
-    double xi = r.next();
-    double dcol = (0.0 - ln_series(xi)) / pt.st;
+    xi = r.next();
+    pt.nflt = pt.nflt + 1;
+    pt.rj = r.j;
+    pt.surf = kSurfNone;
+    bool lat = g.kind == GBMC_GEOM_LATTICE;
+    if (!lat && g.kind != GBMC_GEOM_SLAB) return true;   // no surfaces
+    const double* wall = P.planes + pr.plane_off;
+    double nx = (is_pos(pt.u) ? __ldg(wall + pt.ci + 1) : __ldg(wall + pt.ci)) - pt.x;
+    double ny = 0.0, nz = 0.0;
+    Cyl cy;
+    cy.kind = 0;
+    Span sp[4];
+    sp[1] = plane_span(nx, pt.u);
+    if (lat) {
+        const double* ctr = wall + g.n + 1;
+        cy = cylinder_of(pt.x - __ldg(ctr + pt.ci), pt.y - __ldg(ctr + pt.cj), pt.u, pt.v,
+                         g.radius, pt.inside != 0);
+        ny = (is_pos(pt.v) ? __ldg(wall + pt.cj + 1) : __ldg(wall + pt.cj)) - pt.y;
+        nz = is_pos(pt.w) ? g.height - pt.z : 0.0 - pt.z;
+        sp[0] = cylinder_span(cy);
+        sp[2] = plane_span(ny, pt.v);
+        sp[3] = plane_span(nz, pt.w);
+    } else {
+        sp[0] = sp[2] = sp[3] = span_never();
+    }
+    float H = fminf(fminf(sp[0].hi, sp[1].hi), fminf(sp[2].hi, sp[3].hi));
+    float L = fminf(fminf(sp[0].lo, sp[1].lo), fminf(sp[2].lo, sp[3].lo));
+    Span sc = collision_span(xi, pt.st);
+    int known = sc.hi < L ? 1 : (sc.lo >= H ? 0 : -1);   // 1: collision, 0: surface
+    unsigned S = 0;   // candidates that can be the nearest surface
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (sp[k].lo <= H && (lat || k == 1)) S |= 1u << k;   // a slab has its x planes only
     double dbnd = CUDART_INF;
     uint8_t surf = kSurfNone;
-    int32_t cell = 0;
-    if (g.kind == GBMC_GEOM_LATTICE) {
-        double p = g.pitch;
-        double cx = ((double)pt.ci + 0.5) * p;
-        double cy = ((double)pt.cj + 0.5) * p;
-        double dc = dist_cylinder(pt.x - cx, pt.y - cy, pt.u, pt.v, g.radius, pt.inside != 0);
-        double dx = dist_planes(pt.x, pt.u, (double)pt.ci * p, (double)(pt.ci + 1) * p);
-        double dy = dist_planes(pt.y, pt.v, (double)pt.cj * p, (double)(pt.cj + 1) * p);
-        double dz = dist_planes(pt.z, pt.w, 0.0, g.height);
-        if (dc < 0.0) dc = 0.0;
-        if (dx < 0.0) dx = 0.0;
-        if (dy < 0.0) dy = 0.0;
-        if (dz < 0.0) dz = 0.0;
-        dbnd = dc;
-        surf = kSurfCyl;
-        if (dx < dbnd) { dbnd = dx; surf = kSurfX; }
-        if (dy < dbnd) { dbnd = dy; surf = kSurfY; }
-        if (dz < dbnd) { dbnd = dz; surf = kSurfZ; }
-        cell = pt.cj * g.n + pt.ci;
-    } else if (g.kind == GBMC_GEOM_SLAB) {
-        double h = g.layer_dx;
-        double dx = dist_planes(pt.x, pt.u, (double)pt.ci * h, (double)(pt.ci + 1) * h);
-        if (dx < 0.0) dx = 0.0;
-        dbnd = dx;
-        surf = kSurfX;
-        cell = pt.ci;
+    bool collide;
+    if (known == 0 && (S & (S - 1)) == 0) {
+        int k = __ffs(S) - 1;
+        double num, den;
+        if (k == 0) {
+            double sD = sqrt(cy.D);
+            num = cy.kind == 1 ? sD - cy.k : (cy.kind == 2 ? 0.0 - cy.c : cy.c);
+            den = cy.kind == 1 ? cy.a : (cy.kind == 2 ? cy.k + sD : sD - cy.k);
+        } else {
+            num = k == 1 ? nx : (k == 2 ? ny : nz);
+            den = k == 1 ? pt.u : (k == 2 ? pt.v : pt.w);
+        }
+        dbnd = num / den;
+        if (is_neg(dbnd)) dbnd = 0.0;
+        surf = (uint8_t)(kSurfCyl + k);
+        collide = false;
+    } else if (known == 1) {
+        collide = true;
+    } else {
+        // not decided by the spans: every possible candidate in binary64
+        double dcol = (0.0 - ln_series(xi)) / pt.st;
+        bool first = true;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (S >> k & 1u) {
+                double e = k == 0 ? cylinder_exact(cy)
+                         : k == 1 ? plane_exact(nx, pt.u)
+                         : k == 2 ? plane_exact(ny, pt.v)
+                                  : plane_exact(nz, pt.w);
+                if (is_neg(e)) e = 0.0;
+                if (first || e < dbnd) {
+                    dbnd = e;
+                    surf = (uint8_t)(kSurfCyl + k);
+                    first = false;
+                }
+            }
+        }
+        collide = dcol < dbnd;
     }
-    bool collide = dcol < dbnd;
-    double d = collide ? dcol : dbnd;
+    if (!collide) {
+        pt.surf = surf;
+        pt.x = pt.x + dbnd * pt.u;
+        pt.y = pt.y + dbnd * pt.v;
+        pt.z = pt.z + dbnd * pt.w;
+        int32_t bin = energy_bin(P.T, pt.E);
+        atomicAdd(&P.Y.flux[pr.flux_off + (int64_t)cell_of(g, pt) * P.T.n_bins + bin],
+                  pt.wgt * dbnd);
+    }
+    return collide;
+}
+
+// The end of a flight that reached its collision site: d = -ln(xi) /
+// Sigma_t, the move and the track-length score.
+__device__ __forceinline__ void finish_flight(const Params& P, const DevProblem& pr, Particle& pt,
+                                              double xi) {
+    double d = (0.0 - ln_series(xi)) / pt.st;
     pt.x = pt.x + d * pt.u;
     pt.y = pt.y + d * pt.v;
     pt.z = pt.z + d * pt.w;
     int32_t bin = energy_bin(P.T, pt.E);
-    atomicAdd(&P.Y.flux[pr.flux_off + (int64_t)cell * P.T.n_bins + bin], pt.wgt * d);
-    pt.nflt = pt.nflt + 1;
-    pt.surf = surf;
-    pt.rj = r.j;
-    return collide;
+    atomicAdd(&P.Y.flux[pr.flux_off + (int64_t)cell_of(pr.g, pt) * P.T.n_bins + bin],
+              pt.wgt * d);
 }
 
 // Weight-window check at the particle's (cell, energy bin), problem slot 0
@@ -595,14 +661,14 @@ __device__ __forceinline__ int cross(const Params& P, const DevProblem& pr, Part
     const gbmc_geometry& g = pr.g;
     int status = 0;
     relook = false;
+    const double* wall = P.planes + pr.plane_off;   // (double)i * pitch (or layer width)
     if (g.kind == GBMC_GEOM_SLAB) {
-        double h = g.layer_dx;
         if (pt.u > 0.0) {
-            pt.x = (double)(pt.ci + 1) * h;
+            pt.x = __ldg(wall + pt.ci + 1);
             if (pt.ci < g.n_layers - 1) pt.ci += 1;
             else status = GBMC_STATUS_LEAKED_FAR;
         } else {
-            pt.x = (double)pt.ci * h;
+            pt.x = __ldg(wall + pt.ci);
             if (pt.ci > 0) pt.ci -= 1;
             else status = GBMC_STATUS_LEAKED;
         }
@@ -617,27 +683,25 @@ __device__ __forceinline__ int cross(const Params& P, const DevProblem& pr, Part
         relook = m != pt.mat;
         pt.mat = m;
     } else if (pt.surf == kSurfX) {
-        double p = g.pitch;
         if (pt.u > 0.0) {
-            pt.x = (double)(pt.ci + 1) * p;
+            pt.x = __ldg(wall + pt.ci + 1);
             if (pt.ci < g.n - 1) pt.ci += 1;
             else if (g.bc_side == GBMC_BC_REFLECT) pt.u = -pt.u;
             else status = GBMC_STATUS_LEAKED;
         } else {
-            pt.x = (double)pt.ci * p;
+            pt.x = __ldg(wall + pt.ci);
             if (pt.ci > 0) pt.ci -= 1;
             else if (g.bc_side == GBMC_BC_REFLECT) pt.u = -pt.u;
             else status = GBMC_STATUS_LEAKED;
         }
     } else if (pt.surf == kSurfY) {
-        double p = g.pitch;
         if (pt.v > 0.0) {
-            pt.y = (double)(pt.cj + 1) * p;
+            pt.y = __ldg(wall + pt.cj + 1);
             if (pt.cj < g.n - 1) pt.cj += 1;
             else if (g.bc_side == GBMC_BC_REFLECT) pt.v = -pt.v;
             else status = GBMC_STATUS_LEAKED;
         } else {
-            pt.y = (double)pt.cj * p;
+            pt.y = __ldg(wall + pt.cj);
             if (pt.cj > 0) pt.cj -= 1;
             else if (g.bc_side == GBMC_BC_REFLECT) pt.v = -pt.v;
             else status = GBMC_STATUS_LEAKED;
@@ -715,7 +779,7 @@ __device__ __forceinline__ int leak_kind(int status) {
 // whose particle has left takes the next queue entry (one atomic per warp
 // per refill), so no lane idles behind a long-streaming neighbour.
 
-__global__ void __launch_bounds__(256, 3) k_raytrace(Params P) {
+__global__ void __launch_bounds__(256, 2) k_raytrace(Params P) {
     Ctl* c = P.ctl;
     int cur = c->cur;
     int32_t n = c->adv_n;
@@ -759,7 +823,8 @@ __global__ void __launch_bounds__(256, 3) k_raytrace(Params P) {
         WwOut wo{0, 0.0, 0.0};
         if (have) {
             const DevProblem& pr = P.probs[pt.prob];
-            bool col = fly(P, pr, pt, r);
+            double xi;
+            bool col = fly(P, pr, pt, r, xi);
             ++flights;
             fw += pt.wgt;
             if (col) {
@@ -815,7 +880,7 @@ __global__ void __launch_bounds__(256, 3) k_raytrace(Params P) {
 // ---------------------------------------------------------------- collision event
 
 template <int PREC>
-__global__ void __launch_bounds__(256, 3) k_collision(Params P) {
+__global__ void __launch_bounds__(256, 2) k_collision(Params P) {
     Ctl* c = P.ctl;
     int32_t n = c->n_cq;
     if (n == 0) return;
@@ -846,8 +911,10 @@ __global__ void __launch_bounds__(256, 3) k_collision(Params P) {
                     P.imp_gidx[k] = pt.gidx;
                 }
             }
+            // the flight's distance draw is the stream's last one
             Stream r;
-            stream_of(pr, pt, r);
+            r.init(pr.seed, pr.key_hi, pt.hid, pt.rj - 1u);
+            finish_flight(P, pr, pt, r.next());
             status = collide<PREC>(P, pr, pt, slot, r, wo);
             P.B.p[slot] = pt;
             if (status) record_death(P, pt, status);
@@ -914,12 +981,14 @@ __global__ void __launch_bounds__(256) k_tail(Params P) {
             }
             int action = 0;   // 0: fly on, 1: new lookup, 2: dead
             if (lane == 0) {
-                bool col = fly(P, pr, pt, r);
+                double xi;
+                bool col = fly(P, pr, pt, r, xi);
                 ++nf;
                 wf += pt.wgt;
                 if (col) {
                     ++nc;
                     wc += pt.wgt;
+                    finish_flight(P, pr, pt, xi);
                     WwOut wo{0, 0.0, 0.0};
                     status = collide<PREC>(P, pr, pt, slot, r, wo);
                     action = status ? 2 : 1;
