@@ -54,21 +54,25 @@ struct BlockScalars {
         __syncthreads();
     }
     // all 32 lanes call; lanes with pred score weight wt and count k into
-    // (prob, kind)
+    // (prob, kind).  When the scoring lanes share one problem (the common
+    // case: queues are grouped by material) the warp sums first and one lane
+    // adds; binary64 adds to one shared word from many lanes would retry
+    // compare-and-swap loops, each retry a binary64 add.
     __device__ __forceinline__ void add(const Tallies& Y, bool pred, int prob, int kind, double wt,
                                         unsigned long long k) {
         unsigned vm = __ballot_sync(kFull, pred);
         if (vm == 0) return;
         unsigned peers = __match_any_sync(kFull, pred ? prob : -1);
         int lane = threadIdx.x & 31;
-        if (vm == kFull && peers == kFull) {
-            double s = wt;
-            unsigned long long ks = k;
+        int leader = __ffs(vm) - 1;
+        if (__shfl_sync(kFull, peers, leader) == vm) {
+            double s = pred ? wt : 0.0;
+            unsigned long long ks = pred ? k : 0ull;
             for (int o = 16; o > 0; o >>= 1) {
                 s += __shfl_xor_sync(kFull, s, o);
                 ks += __shfl_xor_sync(kFull, ks, o);
             }
-            if (lane == 0) put(Y, prob, kind, s, ks);
+            if (lane == leader) put(Y, prob, kind, s, ks);
         } else if (pred) {
             put(Y, prob, kind, wt, k);
         }
@@ -794,6 +798,10 @@ __global__ void __launch_bounds__(256, 2) k_raytrace(Params P) {
     Stream r;
     int32_t flights = 0;
     double fw = 0.0;   // weight summed over this particle's flights
+    // the lane's flight scores, summed over its particles of one problem
+    int acc_prob = -1;
+    double acc_w = 0.0;
+    unsigned long long acc_n = 0;
     bool have = false, exhausted = false;
     for (;;) {
         bool want = !have && !exhausted;
@@ -856,7 +864,17 @@ __global__ void __launch_bounds__(256, 2) k_raytrace(Params P) {
             bool dead = fin && status != 0;
             int prob = fin ? pt.prob : 0;
             double wgt = fin ? pt.wgt : 0.0;
-            sc.add(P.Y, fin, prob, GBMC_S_FLIGHT, fin ? fw : 0.0, (unsigned long long)flights);
+            bool chg = fin && acc_n && prob != acc_prob;
+            if (__any_sync(kFull, chg)) sc.add(P.Y, chg, acc_prob, GBMC_S_FLIGHT, acc_w, acc_n);
+            if (fin) {
+                if (prob != acc_prob) {
+                    acc_prob = prob;
+                    acc_w = 0.0;
+                    acc_n = 0;
+                }
+                acc_w += fw;
+                acc_n += (unsigned long long)flights;
+            }
             sc.add(P.Y, dead && leak_kind(status), prob, GBMC_S_LEAK, wgt, 1ull);
             sc.add(P.Y, dead && status == GBMC_STATUS_LEAKED_FAR, prob, GBMC_S_LEAK_FAR, wgt, 1ull);
             sc.add(P.Y, dead && status == GBMC_STATUS_LIMIT, prob, GBMC_S_LIMIT, wgt, 1ull);
@@ -866,6 +884,7 @@ __global__ void __launch_bounds__(256, 2) k_raytrace(Params P) {
             if (fin) have = false;
         }
     }
+    sc.add(P.Y, acc_n > 0, acc_prob, GBMC_S_FLIGHT, acc_w, acc_n);
     for (int o = 16; o > 0; o >>= 1) {
         crossings += __shfl_xor_sync(kFull, crossings, o);
         nflights += __shfl_xor_sync(kFull, nflights, o);
