@@ -53,7 +53,8 @@ struct gbmc_ctx {
     double emin_all = 0, emax_all = 0;
     int64_t* d_grid_off = nullptr;
     double *d_e64 = nullptr, *d_s64 = nullptr, *d_fabs = nullptr, *d_awr = nullptr;
-    float *d_e32 = nullptr, *d_s32 = nullptr, *d_fabs32 = nullptr;
+    float2* d_es32 = nullptr;       // binary32 (E, sigma_t) pairs, 8 pairs of padding
+    float* d_fabs32 = nullptr;
     NucIndex *d_nx64 = nullptr, *d_nx32 = nullptr;   // coarse search indexes
     uint32_t *d_idx64 = nullptr, *d_idx32 = nullptr;
     uint64_t table_hash = 0;   // identifies the tables both copies were built from
@@ -61,6 +62,9 @@ struct gbmc_ctx {
     // materials
     int32_t n_mat = 0;
     std::vector<int32_t> h_mat_off, h_nuc_id;
+    std::vector<double> h_density, h_fabs;
+    std::vector<NucIndex> h_nx32;     // binary32 search descriptors (offsets into d_es32)
+    Desc32* d_desc32 = nullptr;       // per material entry: search + density + f_abs
     int32_t *d_mat_off = nullptr, *d_nuc_id = nullptr;
     double* d_density = nullptr;
     float* d_density32 = nullptr;
@@ -350,8 +354,8 @@ int ensure_tallies(gbmc_ctx* c, const std::vector<int32_t>& cells, cudaStream_t 
 Tables make_tables(const gbmc_ctx* c) {
     Tables T{};
     T.grid_off = c->d_grid_off;
-    T.nx64 = c->d_nx64; T.idx64 = c->d_idx64; T.nx32 = c->d_nx32; T.idx32 = c->d_idx32;
-    T.e64 = c->d_e64; T.s64 = c->d_s64; T.e32 = c->d_e32; T.s32 = c->d_s32;
+    T.nx64 = c->d_nx64; T.idx64 = c->d_idx64; T.idx32 = c->d_idx32; T.d32 = c->d_desc32;
+    T.e64 = c->d_e64; T.s64 = c->d_s64; T.es32 = c->d_es32;
     T.f_abs = c->d_fabs; T.f_abs32 = c->d_fabs32; T.awr = c->d_awr;
     T.mat_off = c->d_mat_off; T.nuc_id = c->d_nuc_id;
     T.density = c->d_density; T.density32 = c->d_density32;
@@ -559,7 +563,8 @@ int n_cells_of(const gbmc_geometry& g) {
 // patterns): buckets (bits - bits(E_0)) >> shift, about 8 grid points per
 // bucket, idx[b] = number of grid points whose bucket is below b.
 int build_index(gbmc_ctx* c, int32_t n_nuc, const int64_t* grid_off, const double* energy,
-                int32_t precision, NucIndex** d_nx, uint32_t** d_idx) {
+                int32_t precision, NucIndex** d_nx, uint32_t** d_idx,
+                const int64_t* table_off = nullptr, std::vector<NucIndex>* keep = nullptr) {
     auto bits = [&](int64_t k) -> uint64_t {
         if (precision == GBMC_FP64) {
             uint64_t b;
@@ -576,12 +581,16 @@ int build_index(gbmc_ctx* c, int32_t n_nuc, const int64_t* grid_off, const doubl
     for (int32_t i = 0; i < n_nuc; ++i) {
         int64_t off = grid_off[i], n = grid_off[i + 1] - off;
         uint64_t base = bits(off), range = bits(off + n - 1) - base;
+        // binary64: about 4-8 points a bucket (a few bisection steps follow);
+        // binary32: about 1-2, so that one window of kWindow32 pairs holds it
+        int32_t per = precision == GBMC_FP64 ? 8 : 2;
+        int32_t cap = precision == GBMC_FP64 ? (1 << 16) : (1 << 20);
         int32_t nb = 16;
-        while ((int64_t)nb * 8 < n && nb < (1 << 16)) nb <<= 1;
+        while ((int64_t)nb * per < n && nb < cap) nb <<= 1;
         int32_t shift = 0;
         while ((range >> shift) >= (uint64_t)nb) ++shift;
         NucIndex d{};
-        d.off = off;
+        d.off = table_off ? table_off[i] : off;
         d.idx_off = (int64_t)idx.size();
         d.base = base;
         d.n = (int32_t)n;
@@ -594,9 +603,31 @@ int build_index(gbmc_ctx* c, int32_t n_nuc, const int64_t* grid_off, const doubl
             idx.push_back((uint32_t)j);
         }
     }
-    int rc = upload(c, d_nx, nx.data(), nx.size());
+    if (keep) *keep = nx;
+    int rc = d_nx ? upload(c, d_nx, nx.data(), nx.size()) : 0;
     if (rc) return rc;
     return upload(c, d_idx, idx.data(), idx.size());
+}
+
+// Per material entry records of the binary32 lookup (needs the binary32
+// tables and the materials).
+int build_desc32(gbmc_ctx* c) {
+    if (!c->has32 || !c->n_mat) return GBMC_OK;
+    size_t tot = c->h_nuc_id.size();
+    std::vector<Desc32> d(tot);
+    for (size_t q = 0; q < tot; ++q) {
+        const NucIndex& x = c->h_nx32[c->h_nuc_id[q]];
+        Desc32& e = d[q];
+        e.off = x.off;
+        e.idx_off = x.idx_off;
+        e.base = (uint32_t)x.base;
+        e.n = x.n;
+        e.shift = x.shift;
+        e.nb = x.nb;
+        e.density = (float)c->h_density[q];
+        e.f_abs = (float)c->h_fabs[c->h_nuc_id[q]];
+    }
+    return upload(c, &c->d_desc32, d.data(), tot);
 }
 
 int read_ctl(gbmc_ctx* c) {
@@ -684,10 +715,11 @@ int gbmc_destroy(gbmc_ctx* c) {
     dfree(O.ncoll); dfree(O.status); dfree(O.nflt); dfree(O.ndraw);
     dfree(O.E); dfree(O.x); dfree(O.y); dfree(O.z);
     dfree(c->Y.flux); dfree(c->Y.counts); dfree(c->Y.weights);
-    dfree(c->d_grid_off); dfree(c->d_e64); dfree(c->d_s64); dfree(c->d_e32); dfree(c->d_s32);
+    dfree(c->d_grid_off); dfree(c->d_e64); dfree(c->d_s64); dfree(c->d_es32);
     dfree(c->d_fabs); dfree(c->d_fabs32); dfree(c->d_awr);
     dfree(c->d_nx64); dfree(c->d_nx32); dfree(c->d_idx64); dfree(c->d_idx32);
     dfree(c->d_mat_off); dfree(c->d_nuc_id); dfree(c->d_density); dfree(c->d_density32);
+    dfree(c->d_desc32);
     dfree(c->d_edges); dfree(c->d_probs); dfree(c->d_planes); dfree(c->d_ctl);
     dfree(c->d_ww); dfree(c->d_child);
     dfree(c->d_net_p); dfree(c->d_net_m); dfree(c->d_net_v); dfree(c->d_net_g);
@@ -765,7 +797,7 @@ int gbmc_load_xs_tables(gbmc_ctx* c, int32_t n_nuc, const int64_t* grid_off, con
     bool same = (h == c->table_hash && n_nuc == c->n_nuc);
     if (!same) {
         // new tables: drop the copy of the other precision
-        dfree(c->d_e64); dfree(c->d_s64); dfree(c->d_e32); dfree(c->d_s32);
+        dfree(c->d_e64); dfree(c->d_s64); dfree(c->d_es32);
         dfree(c->d_nx64); dfree(c->d_nx32); dfree(c->d_idx64); dfree(c->d_idx32);
         c->has64 = c->has32 = false;
         // materials refer to nuclide ids of the old tables
@@ -789,18 +821,32 @@ int gbmc_load_xs_tables(gbmc_ctx* c, int32_t n_nuc, const int64_t* grid_off, con
             return rc;
         c->has64 = true;
     } else {
-        std::vector<float> e(tot), s(tot);
-        for (int64_t k = 0; k < tot; ++k) {
-            e[k] = (float)energy[k];
-            s[k] = (float)sigma_t[k];
+        // (E, sigma_t) pairs, each nuclide from an even pair and followed by
+        // kWindow32 pairs (E = +inf, sigma 0): a window of kWindow32 pairs
+        // from inside a grid stays inside its nuclide and its sentinels
+        std::vector<int64_t> poff(n_nuc);
+        int64_t ptot = 0;
+        for (int32_t i = 0; i < n_nuc; ++i) {
+            poff[i] = ptot;
+            int64_t n = grid_off[i + 1] - grid_off[i];
+            ptot += (n + kWindow32 + 1) & ~1ll;
         }
-        if ((rc = upload(c, &c->d_e32, e.data(), (size_t)tot))) return rc;
-        if ((rc = upload(c, &c->d_s32, s.data(), (size_t)tot))) return rc;
-        if ((rc = build_index(c, n_nuc, grid_off, energy, GBMC_FP32, &c->d_nx32, &c->d_idx32)))
+        if (ptot > ((int64_t)1 << 31) - 1)
+            return fail(c, GBMC_ERR_INVALID_ARG, "binary32 tables over 2^31 grid points");
+        const float inf = std::numeric_limits<float>::infinity();
+        std::vector<float2> es(ptot, make_float2(inf, 0.0f));
+        for (int32_t i = 0; i < n_nuc; ++i)
+            for (int64_t k = grid_off[i]; k < grid_off[i + 1]; ++k)
+                es[poff[i] + (k - grid_off[i])] = make_float2((float)energy[k], (float)sigma_t[k]);
+        if ((rc = upload(c, &c->d_es32, es.data(), es.size()))) return rc;
+        if ((rc = build_index(c, n_nuc, grid_off, energy, GBMC_FP32, nullptr, &c->d_idx32,
+                              poff.data(), &c->h_nx32)))
             return rc;
         c->has32 = true;
     }
     c->n_nuc = n_nuc;
+    c->h_fabs.assign(f_abs, f_abs + n_nuc);
+    if ((rc = build_desc32(c))) return rc;
     c->table_hash = h;
     c->h_grid_off.assign(grid_off, grid_off + n_nuc + 1);
     // the grid range check uses the tighter of the two copies
@@ -851,6 +897,8 @@ int gbmc_init_materials(gbmc_ctx* c, int32_t n_mat, const int32_t* mat_off, cons
         c->max_nuc_per_mat = std::max(c->max_nuc_per_mat, mat_off[m + 1] - mat_off[m]);
     c->h_mat_off.assign(mat_off, mat_off + n_mat + 1);
     c->h_nuc_id.assign(nuc_id, nuc_id + tot);
+    c->h_density.assign(density, density + tot);
+    if ((rc = build_desc32(c))) return rc;
     c->graph_valid = false;
     return GBMC_OK;
 }

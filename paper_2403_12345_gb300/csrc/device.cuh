@@ -32,16 +32,30 @@ struct NucIndex {
 };
 static_assert(sizeof(NucIndex) == 48, "NucIndex is read as three int4");
 
+// Per material entry q, binary32 tables: what the lookup reads for nuclide
+// nuc_id[q] in one 32-byte record (two 16-byte loads).
+struct alignas(16) Desc32 {
+    int32_t off;       // first (E, sigma) pair of the nuclide in es32 (even)
+    int32_t idx_off;   // its coarse index: idx32[idx_off .. idx_off + nb]
+    uint32_t base;     // bit pattern of its first grid energy
+    int32_t n;         // grid points
+    int32_t shift;     // bucket of E = (bits(E) - base) >> shift
+    int32_t nb;        // buckets
+    float density;     // N of this entry, binary32
+    float f_abs;       // sigma_a / sigma_t of the nuclide, binary32
+};
+static_assert(sizeof(Desc32) == 32, "Desc32 is read as two int4");
+
 struct Tables {
     const int64_t* grid_off;   // [n_nuc+1]
     const NucIndex* nx64;      // [n_nuc] descriptors over the binary64 grid
     const uint32_t* idx64;     // coarse index of the binary64 grids
-    const NucIndex* nx32;      // [n_nuc] descriptors over the binary32 grid
-    const uint32_t* idx32;
+    const uint32_t* idx32;     // coarse index of the binary32 grids
+    const Desc32* d32;         // [mat_off[n_mat]] per material entry (binary32)
     const double* e64;         // binary64 grid (eV)
     const double* s64;         // binary64 sigma_t (b)
-    const float* e32;          // binary32 grid
-    const float* s32;          // binary32 sigma_t
+    const float2* es32;        // binary32 (E, sigma_t) pairs, each nuclide followed by
+                               // kWindow32 pairs (+inf, 0)
     const double* f_abs;       // [n_nuc]
     const float* f_abs32;      // [n_nuc]
     const double* awr;         // [n_nuc]
@@ -355,18 +369,80 @@ __device__ __forceinline__ double micro64(const Tables& T, int32_t i, double E) 
 // binary32 tables: the bracket satisfies (double)E_j <= E, found by
 // comparing against E rounded toward -inf (exact for binary32 grid values);
 // the interpolation runs in binary32 on E rounded to nearest.
-__device__ __forceinline__ float micro32(const Tables& T, int32_t i, double E) {
-    NucIndex d = load_index(T.nx32 + i);
+//
+// The binary32 grid is stored as (E_j, sigma_j) pairs, each nuclide's from an
+// even pair and followed by kWindow32 sentinel pairs (E = +inf), and its
+// coarse index has about two points a bucket.  The bracket then lies in one
+// aligned window of kWindow32 pairs starting at or below the bucket's first
+// candidate, and its position is a count: every window entry at or below E
+// precedes it (the grid is sorted and the sentinels are never counted), so
+// j = window start + count - 1, capped at n - 2.  Four 16-byte loads and
+// eight compares replace the bisection probes; a bucket wider than the
+// window is first halved by bisection.
+constexpr int kWindow32 = 8;
+constexpr int kIlp32 = 4;   // nuclides whose windows are in flight together
+
+__device__ __forceinline__ Desc32 load_desc32(const Desc32* p) {
+    Desc32 d;
+    const int4* q = reinterpret_cast<const int4*>(p);
+    int4 a = __ldg(q), b = __ldg(q + 1);
+    memcpy(&d, &a, 16);
+    memcpy(reinterpret_cast<char*>(&d) + 16, &b, 16);
+    return d;
+}
+
+// First pair (absolute, even) of the window holding the bracket.
+__device__ __forceinline__ int32_t window_of(const Tables& T, const Desc32& d, uint32_t eb) {
+    uint32_t b = eb >= d.base ? (eb - d.base) >> d.shift : 0u;
+    if (b > (uint32_t)(d.nb - 1)) b = (uint32_t)(d.nb - 1);
+    const uint32_t* ix = T.idx32 + d.idx_off + b;
+    int32_t s0 = (int32_t)__ldg(ix), s1 = (int32_t)__ldg(ix + 1);
+    int32_t lo = s0 > 0 ? s0 - 1 : 0;
+    if (lo > d.n - 2) lo = d.n - 2;
+    int32_t hi = s1 < d.n - 1 ? s1 : d.n - 1;
+    while (hi - (lo & ~1) > kWindow32 - 1) {   // rare: a bucket wider than the window
+        int32_t mid = (lo + hi) >> 1;
+        if (__float_as_uint(__ldg(&T.es32[d.off + mid].x)) <= eb)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return d.off + (lo & ~1);
+}
+
+// Bracket pair position from the window's pairs q[0..3] (loaded from pair aw).
+__device__ __forceinline__ int32_t bracket_from_window(const float4* q, int32_t aw,
+                                                       const Desc32& d, uint32_t eb) {
+    int32_t cnt = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        cnt += __float_as_uint(q[k].x) <= eb ? 1 : 0;
+        cnt += __float_as_uint(q[k].z) <= eb ? 1 : 0;
+    }
+    int32_t j = aw + cnt - 1;
+    int32_t jmax = d.off + d.n - 2;
+    j = j < jmax ? j : jmax;
+    return j > d.off ? j : d.off;   // E below the first grid point: j = 0
+}
+
+__device__ __forceinline__ void load_window(const Tables& T, int32_t aw, float4* q) {
+    const float4* p = reinterpret_cast<const float4*>(T.es32 + aw);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) q[k] = __ldg(p + k);
+}
+
+// Micro cross section of material entry q (binary32) at E.
+__device__ __forceinline__ float micro32(const Tables& T, int32_t q, double E) {
+    Desc32 d = load_desc32(T.d32 + q);
     uint32_t eb = (uint32_t)__float_as_int(__double2float_rd(E));
-    int32_t lo, hi;
-    coarse_range(d, T.idx32, eb, lo, hi);
-    const uint32_t* g = reinterpret_cast<const uint32_t*>(T.e32 + d.off);
-    int64_t k = d.off + bracket_in(g, lo, hi, eb);
-    float e0 = __ldg(T.e32 + k), e1 = __ldg(T.e32 + k + 1);
-    float s0 = __ldg(T.s32 + k), s1 = __ldg(T.s32 + k + 1);
+    int32_t aw = window_of(T, d, eb);
+    float4 w[4];
+    load_window(T, aw, w);
+    int32_t j = bracket_from_window(w, aw, d, eb);
+    float2 p0 = __ldg(T.es32 + j), p1 = __ldg(T.es32 + j + 1);
     float Ef = __double2float_rn(E);
-    float f = (Ef - e0) / (e1 - e0);
-    return s0 + f * (s1 - s0);
+    float f = (Ef - p0.x) / (p1.x - p0.x);
+    return p0.y + f * (p1.y - p0.y);
 }
 
 // Macroscopic sigma_t, sigma_a of material m: sum over its nuclides in the
@@ -457,30 +533,45 @@ __device__ __forceinline__ void macro32(const Tables& T, int32_t m, double E, do
                                         double& sa, float* cum = nullptr) {
     float at = 0.0f, aa = 0.0f;
     int32_t q0 = __ldg(T.mat_off + m), q1 = __ldg(T.mat_off + m + 1);
-    const uint32_t* g = reinterpret_cast<const uint32_t*>(T.e32);
     uint32_t eb = (uint32_t)__float_as_int(__double2float_rd(E));
     float Ef = __double2float_rn(E);
-    for (int32_t q = q0; q < q1; q += kIlp) {
-        int64_t pos[kIlp];
-        float run[kIlp];
-        brackets(T, T.nx32, T.idx32, g, q, q1, eb, pos);
+    for (int32_t q = q0; q < q1; q += kIlp32) {
+        Desc32 d[kIlp32];
+        int32_t aw[kIlp32];
 #pragma unroll
-        for (int u = 0; u < kIlp; ++u) {
+        for (int u = 0; u < kIlp32; ++u) {
+            d[u] = load_desc32(T.d32 + (q + u < q1 ? q + u : q));
+            aw[u] = window_of(T, d[u], eb);
+        }
+        float4 w[kIlp32][4];
+#pragma unroll
+        for (int u = 0; u < kIlp32; ++u) load_window(T, aw[u], w[u]);
+        float2 p0[kIlp32], p1[kIlp32];
+#pragma unroll
+        for (int u = 0; u < kIlp32; ++u) {
+            int32_t jj = bracket_from_window(w[u], aw[u], d[u], eb);
+            p0[u] = __ldg(T.es32 + jj);
+            p1[u] = __ldg(T.es32 + jj + 1);
+        }
+        float run[kIlp32];
+#pragma unroll
+        for (int u = 0; u < kIlp32; ++u) {
             if (q + u < q1) {
-                int64_t k = pos[u];
-                float e0 = __ldg(T.e32 + k), e1 = __ldg(T.e32 + k + 1);
-                float s0 = __ldg(T.s32 + k), s1 = __ldg(T.s32 + k + 1);
-                float f = (Ef - e0) / (e1 - e0);
-                float sig = s0 + f * (s1 - s0);
-                int32_t i = __ldg(T.nuc_id + q + u);
-                float t = __ldg(T.density32 + q + u) * sig;
+                float f = (Ef - p0[u].x) / (p1[u].x - p0[u].x);
+                float sig = p0[u].y + f * (p1[u].y - p0[u].y);
+                float t = d[u].density * sig;
                 at = at + t;
-                aa = aa + t * __ldg(T.f_abs32 + i);
+                aa = aa + t * d[u].f_abs;
             }
             run[u] = at;
         }
-        if (cum)
-            *reinterpret_cast<float4*>(cum + (q - q0)) = make_float4(run[0], run[1], run[2], run[3]);
+        if (cum) {
+            if (kIlp32 == 4)
+                *reinterpret_cast<float4*>(cum + (q - q0)) =
+                    make_float4(run[0], run[1], run[2 % kIlp32], run[3 % kIlp32]);
+            else
+                *reinterpret_cast<float2*>(cum + (q - q0)) = make_float2(run[0], run[1 % kIlp32]);
+        }
     }
     st = (double)at;
     sa = (double)aa;
@@ -522,9 +613,9 @@ __device__ __forceinline__ void macro_warp(const Tables& T, int32_t m, double E,
         for (int32_t c = q0; c < q1; c += 32) {
             float t = 0.0f, p = 0.0f;
             if (c + lane < q1) {
-                int32_t i = __ldg(T.nuc_id + c + lane);
-                t = __ldg(T.density32 + c + lane) * micro32(T, i, E);
-                p = t * __ldg(T.f_abs32 + i);
+                const Desc32* dq = T.d32 + c + lane;
+                t = __ldg(&dq->density) * micro32(T, c + lane, E);
+                p = t * __ldg(&dq->f_abs);
             }
             int32_t kmax = q1 - c < 32 ? q1 - c : 32;
             for (int k = 0; k < kmax; ++k) {
@@ -559,7 +650,7 @@ __device__ __forceinline__ int32_t pick_nuclide(const Tables& T, int precision, 
         float cum = 0.0f;
         for (int32_t q = q0; q < q1; ++q) {
             int32_t i = __ldg(T.nuc_id + q);
-            float t = __ldg(T.density32 + q) * micro32(T, i, E);
+            float t = __ldg(&T.d32[q].density) * micro32(T, q, E);
             cum = cum + t;
             if (t > 0.0f) last = i;
             if (target < (double)cum) return i;
