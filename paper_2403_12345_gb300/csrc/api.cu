@@ -65,6 +65,8 @@ struct gbmc_ctx {
     std::vector<double> h_density, h_fabs;
     std::vector<NucIndex> h_nx32;     // binary32 search descriptors (offsets into d_es32)
     Desc32* d_desc32 = nullptr;       // per material entry: search + density + f_abs
+    float4* d_bw32 = nullptr;         // binary32 bucket windows (4 float4 each)
+    std::vector<int64_t> h_bw_off;    // first window of each nuclide
     int32_t *d_mat_off = nullptr, *d_nuc_id = nullptr;
     double* d_density = nullptr;
     float* d_density32 = nullptr;
@@ -354,7 +356,7 @@ int ensure_tallies(gbmc_ctx* c, const std::vector<int32_t>& cells, cudaStream_t 
 Tables make_tables(const gbmc_ctx* c) {
     Tables T{};
     T.grid_off = c->d_grid_off;
-    T.nx64 = c->d_nx64; T.idx64 = c->d_idx64; T.idx32 = c->d_idx32; T.d32 = c->d_desc32;
+    T.nx64 = c->d_nx64; T.idx64 = c->d_idx64; T.bw32 = c->d_bw32; T.d32 = c->d_desc32;
     T.e64 = c->d_e64; T.s64 = c->d_s64; T.es32 = c->d_es32;
     T.f_abs = c->d_fabs; T.f_abs32 = c->d_fabs32; T.awr = c->d_awr;
     T.mat_off = c->d_mat_off; T.nuc_id = c->d_nuc_id;
@@ -564,7 +566,8 @@ int n_cells_of(const gbmc_geometry& g) {
 // bucket, idx[b] = number of grid points whose bucket is below b.
 int build_index(gbmc_ctx* c, int32_t n_nuc, const int64_t* grid_off, const double* energy,
                 int32_t precision, NucIndex** d_nx, uint32_t** d_idx,
-                const int64_t* table_off = nullptr, std::vector<NucIndex>* keep = nullptr) {
+                const int64_t* table_off = nullptr, std::vector<NucIndex>* keep = nullptr,
+                std::vector<uint32_t>* keep_idx = nullptr) {
     auto bits = [&](int64_t k) -> uint64_t {
         if (precision == GBMC_FP64) {
             uint64_t b;
@@ -582,7 +585,7 @@ int build_index(gbmc_ctx* c, int32_t n_nuc, const int64_t* grid_off, const doubl
         int64_t off = grid_off[i], n = grid_off[i + 1] - off;
         uint64_t base = bits(off), range = bits(off + n - 1) - base;
         // binary64: about 4-8 points a bucket (a few bisection steps follow);
-        // binary32: about 1-2, so that one window of kWindow32 pairs holds it
+        // binary32: about 1-2, so that a bucket window (seven pairs) holds it
         int32_t per = precision == GBMC_FP64 ? 8 : 2;
         int32_t cap = precision == GBMC_FP64 ? (1 << 16) : (1 << 20);
         int32_t nb = 16;
@@ -604,9 +607,10 @@ int build_index(gbmc_ctx* c, int32_t n_nuc, const int64_t* grid_off, const doubl
         }
     }
     if (keep) *keep = nx;
+    if (keep_idx) *keep_idx = idx;
     int rc = d_nx ? upload(c, d_nx, nx.data(), nx.size()) : 0;
     if (rc) return rc;
-    return upload(c, d_idx, idx.data(), idx.size());
+    return d_idx ? upload(c, d_idx, idx.data(), idx.size()) : 0;
 }
 
 // Per material entry records of the binary32 lookup (needs the binary32
@@ -619,7 +623,7 @@ int build_desc32(gbmc_ctx* c) {
         const NucIndex& x = c->h_nx32[c->h_nuc_id[q]];
         Desc32& e = d[q];
         e.off = x.off;
-        e.idx_off = x.idx_off;
+        e.bw_off = (int32_t)c->h_bw_off[c->h_nuc_id[q]];
         e.base = (uint32_t)x.base;
         e.n = x.n;
         e.shift = x.shift;
@@ -717,7 +721,7 @@ int gbmc_destroy(gbmc_ctx* c) {
     dfree(c->Y.flux); dfree(c->Y.counts); dfree(c->Y.weights);
     dfree(c->d_grid_off); dfree(c->d_e64); dfree(c->d_s64); dfree(c->d_es32);
     dfree(c->d_fabs); dfree(c->d_fabs32); dfree(c->d_awr);
-    dfree(c->d_nx64); dfree(c->d_nx32); dfree(c->d_idx64); dfree(c->d_idx32);
+    dfree(c->d_nx64); dfree(c->d_nx32); dfree(c->d_idx64); dfree(c->d_idx32); dfree(c->d_bw32);
     dfree(c->d_mat_off); dfree(c->d_nuc_id); dfree(c->d_density); dfree(c->d_density32);
     dfree(c->d_desc32);
     dfree(c->d_edges); dfree(c->d_probs); dfree(c->d_planes); dfree(c->d_ctl);
@@ -798,7 +802,7 @@ int gbmc_load_xs_tables(gbmc_ctx* c, int32_t n_nuc, const int64_t* grid_off, con
     if (!same) {
         // new tables: drop the copy of the other precision
         dfree(c->d_e64); dfree(c->d_s64); dfree(c->d_es32);
-        dfree(c->d_nx64); dfree(c->d_nx32); dfree(c->d_idx64); dfree(c->d_idx32);
+        dfree(c->d_nx64); dfree(c->d_nx32); dfree(c->d_idx64); dfree(c->d_idx32); dfree(c->d_bw32);
         c->has64 = c->has32 = false;
         // materials refer to nuclide ids of the old tables
         if (c->n_mat) {
@@ -822,14 +826,13 @@ int gbmc_load_xs_tables(gbmc_ctx* c, int32_t n_nuc, const int64_t* grid_off, con
         c->has64 = true;
     } else {
         // (E, sigma_t) pairs, each nuclide from an even pair and followed by
-        // kWindow32 pairs (E = +inf, sigma 0): a window of kWindow32 pairs
-        // from inside a grid stays inside its nuclide and its sentinels
+        // kPad32 pairs (E = +inf, sigma 0) that a window may reach
         std::vector<int64_t> poff(n_nuc);
         int64_t ptot = 0;
         for (int32_t i = 0; i < n_nuc; ++i) {
             poff[i] = ptot;
             int64_t n = grid_off[i + 1] - grid_off[i];
-            ptot += (n + kWindow32 + 1) & ~1ll;
+            ptot += (n + kPad32 + 1) & ~1ll;
         }
         if (ptot > ((int64_t)1 << 31) - 1)
             return fail(c, GBMC_ERR_INVALID_ARG, "binary32 tables over 2^31 grid points");
@@ -839,9 +842,40 @@ int gbmc_load_xs_tables(gbmc_ctx* c, int32_t n_nuc, const int64_t* grid_off, con
             for (int64_t k = grid_off[i]; k < grid_off[i + 1]; ++k)
                 es[poff[i] + (k - grid_off[i])] = make_float2((float)energy[k], (float)sigma_t[k]);
         if ((rc = upload(c, &c->d_es32, es.data(), es.size()))) return rc;
-        if ((rc = build_index(c, n_nuc, grid_off, energy, GBMC_FP32, nullptr, &c->d_idx32,
-                              poff.data(), &c->h_nx32)))
+        std::vector<uint32_t> idx;
+        if ((rc = build_index(c, n_nuc, grid_off, energy, GBMC_FP32, nullptr, nullptr,
+                              poff.data(), &c->h_nx32, &idx)))
             return rc;
+        // bucket windows: bucket b of a nuclide holds the pairs lo .. lo + 6
+        // of its bracket range [lo, hi] (lo = first point of the bucket - 1,
+        // hi = first point of the next bucket, both clamped to the grid) and
+        // (lo, hi) itself; a bucket with hi - lo > 6 is searched by bisection
+        c->h_bw_off.assign(n_nuc, 0);
+        int64_t nw = 0;
+        for (int32_t i = 0; i < n_nuc; ++i) {
+            c->h_bw_off[i] = nw;
+            nw += c->h_nx32[i].nb;
+        }
+        if (nw > ((int64_t)1 << 31) - 1)
+            return fail(c, GBMC_ERR_INVALID_ARG, "binary32 tables over 2^31 index buckets");
+        std::vector<float4> bw((size_t)nw * 4);
+        for (int32_t i = 0; i < n_nuc; ++i) {
+            const NucIndex& x = c->h_nx32[i];
+            const float2* g = es.data() + x.off;
+            for (int32_t b = 0; b < x.nb; ++b) {
+                int32_t s0 = (int32_t)idx[x.idx_off + b], s1 = (int32_t)idx[x.idx_off + b + 1];
+                int32_t lo = std::min(s0 > 0 ? s0 - 1 : 0, x.n - 2);
+                int32_t hi = std::min(s1, x.n - 1);
+                float4* w = bw.data() + (size_t)(c->h_bw_off[i] + b) * 4;
+                float2 pr[8];
+                for (int p = 0; p < 7; ++p) pr[p] = g[lo + p];   // sentinels past the grid
+                int32_t meta[2] = {lo, hi};
+                memcpy(&pr[7], meta, 8);
+                for (int k = 0; k < 4; ++k)
+                    w[k] = make_float4(pr[2 * k].x, pr[2 * k].y, pr[2 * k + 1].x, pr[2 * k + 1].y);
+            }
+        }
+        if ((rc = upload(c, &c->d_bw32, bw.data(), bw.size()))) return rc;
         c->has32 = true;
     }
     c->n_nuc = n_nuc;

@@ -36,7 +36,7 @@ static_assert(sizeof(NucIndex) == 48, "NucIndex is read as three int4");
 // nuc_id[q] in one 32-byte record (two 16-byte loads).
 struct alignas(16) Desc32 {
     int32_t off;       // first (E, sigma) pair of the nuclide in es32 (even)
-    int32_t idx_off;   // its coarse index: idx32[idx_off .. idx_off + nb]
+    int32_t bw_off;    // its first bucket window in bw32
     uint32_t base;     // bit pattern of its first grid energy
     int32_t n;         // grid points
     int32_t shift;     // bucket of E = (bits(E) - base) >> shift
@@ -50,12 +50,12 @@ struct Tables {
     const int64_t* grid_off;   // [n_nuc+1]
     const NucIndex* nx64;      // [n_nuc] descriptors over the binary64 grid
     const uint32_t* idx64;     // coarse index of the binary64 grids
-    const uint32_t* idx32;     // coarse index of the binary32 grids
+    const float4* bw32;        // binary32 bucket windows (four float4 each)
     const Desc32* d32;         // [mat_off[n_mat]] per material entry (binary32)
     const double* e64;         // binary64 grid (eV)
     const double* s64;         // binary64 sigma_t (b)
     const float2* es32;        // binary32 (E, sigma_t) pairs, each nuclide followed by
-                               // kWindow32 pairs (+inf, 0)
+                               // kPad32 pairs (+inf, 0)
     const double* f_abs;       // [n_nuc]
     const float* f_abs32;      // [n_nuc]
     const double* awr;         // [n_nuc]
@@ -370,17 +370,17 @@ __device__ __forceinline__ double micro64(const Tables& T, int32_t i, double E) 
 // comparing against E rounded toward -inf (exact for binary32 grid values);
 // the interpolation runs in binary32 on E rounded to nearest.
 //
-// The binary32 grid is stored as (E_j, sigma_j) pairs, each nuclide's from an
-// even pair and followed by kWindow32 sentinel pairs (E = +inf), and its
-// coarse index has about two points a bucket.  The bracket then lies in one
-// aligned window of kWindow32 pairs starting at or below the bucket's first
-// candidate, and its position is a count: every window entry at or below E
-// precedes it (the grid is sorted and the sentinels are never counted), so
-// j = window start + count - 1, capped at n - 2.  Four 16-byte loads and
-// eight compares replace the bisection probes; a bucket wider than the
-// window is first halved by bisection.
-constexpr int kWindow32 = 8;
+// The binary32 grid is stored as (E_j, sigma_j) pairs, each nuclide followed
+// by sentinel pairs (E = +inf), with a coarse index of about one to two
+// points a bucket.  Each bucket carries its own 64-byte window: the pairs
+// lo .. lo + 6 of its bracket range [lo, hi] and (lo, hi) itself.  The
+// bracket's position is then a count: every window entry at or below E
+// precedes it (the grid is sorted, the sentinels and the points past hi are
+// above E), so j = lo + count - 1, capped to [0, n - 2].  One 64-byte load
+// per nuclide replaces the index load, the bisection probes and the bracket
+// loads; a bucket with hi - lo > 6 is searched by bisection instead.
 constexpr int kIlp32 = 4;   // nuclides whose windows are in flight together
+constexpr int kPad32 = 8;   // sentinel pairs after each nuclide's grid
 
 __device__ __forceinline__ Desc32 load_desc32(const Desc32* p) {
     Desc32 d;
@@ -391,55 +391,60 @@ __device__ __forceinline__ Desc32 load_desc32(const Desc32* p) {
     return d;
 }
 
-// First pair (absolute, even) of the window holding the bracket.
-__device__ __forceinline__ int32_t window_of(const Tables& T, const Desc32& d, uint32_t eb) {
+// The bucket window of E.
+__device__ __forceinline__ const float4* window_of(const Tables& T, const Desc32& d, uint32_t eb) {
     uint32_t b = eb >= d.base ? (eb - d.base) >> d.shift : 0u;
     if (b > (uint32_t)(d.nb - 1)) b = (uint32_t)(d.nb - 1);
-    const uint32_t* ix = T.idx32 + d.idx_off + b;
-    int32_t s0 = (int32_t)__ldg(ix), s1 = (int32_t)__ldg(ix + 1);
-    int32_t lo = s0 > 0 ? s0 - 1 : 0;
-    if (lo > d.n - 2) lo = d.n - 2;
-    int32_t hi = s1 < d.n - 1 ? s1 : d.n - 1;
-    while (hi - (lo & ~1) > kWindow32 - 1) {   // rare: a bucket wider than the window
+    return T.bw32 + ((int64_t)d.bw_off + b) * 4;
+}
+
+__device__ __forceinline__ void load_window(const float4* p, float4* q) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) q[k] = __ldg(p + k);
+}
+
+// The bracket's end points (its pair and the next) from the window w loaded
+// from p.
+__device__ __forceinline__ void bracket32(const Tables& T, const Desc32& d, const float4* p,
+                                          const float4* w, uint32_t eb, float2& p0, float2& p1) {
+    int32_t lo = __float_as_int(w[3].z), hi = __float_as_int(w[3].w);
+    if (hi - lo <= 6) {
+        uint32_t e[7] = {__float_as_uint(w[0].x), __float_as_uint(w[0].z),
+                         __float_as_uint(w[1].x), __float_as_uint(w[1].z),
+                         __float_as_uint(w[2].x), __float_as_uint(w[2].z),
+                         __float_as_uint(w[3].x)};
+        int32_t cnt = 0;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) cnt += e[k] <= eb ? 1 : 0;
+        int32_t r = cnt - 1;                        // window position of the bracket
+        if (r > d.n - 2 - lo) r = d.n - 2 - lo;
+        if (r < 0) r = 0;                           // E below the first grid point
+        const float2* pp = reinterpret_cast<const float2*>(p) + r;
+        p0 = __ldg(pp);                             // the window's own line: an L1 hit
+        p1 = __ldg(pp + 1);
+        return;
+    }
+    const float2* g = T.es32 + d.off;
+    while (hi - lo > 1) {
         int32_t mid = (lo + hi) >> 1;
-        if (__float_as_uint(__ldg(&T.es32[d.off + mid].x)) <= eb)
+        if (__float_as_uint(__ldg(&g[mid].x)) <= eb)
             lo = mid;
         else
             hi = mid;
     }
-    return d.off + (lo & ~1);
-}
-
-// Bracket pair position from the window's pairs q[0..3] (loaded from pair aw).
-__device__ __forceinline__ int32_t bracket_from_window(const float4* q, int32_t aw,
-                                                       const Desc32& d, uint32_t eb) {
-    int32_t cnt = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        cnt += __float_as_uint(q[k].x) <= eb ? 1 : 0;
-        cnt += __float_as_uint(q[k].z) <= eb ? 1 : 0;
-    }
-    int32_t j = aw + cnt - 1;
-    int32_t jmax = d.off + d.n - 2;
-    j = j < jmax ? j : jmax;
-    return j > d.off ? j : d.off;   // E below the first grid point: j = 0
-}
-
-__device__ __forceinline__ void load_window(const Tables& T, int32_t aw, float4* q) {
-    const float4* p = reinterpret_cast<const float4*>(T.es32 + aw);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) q[k] = __ldg(p + k);
+    p0 = __ldg(g + lo);
+    p1 = __ldg(g + lo + 1);
 }
 
 // Micro cross section of material entry q (binary32) at E.
 __device__ __forceinline__ float micro32(const Tables& T, int32_t q, double E) {
     Desc32 d = load_desc32(T.d32 + q);
     uint32_t eb = (uint32_t)__float_as_int(__double2float_rd(E));
-    int32_t aw = window_of(T, d, eb);
+    const float4* p = window_of(T, d, eb);
     float4 w[4];
-    load_window(T, aw, w);
-    int32_t j = bracket_from_window(w, aw, d, eb);
-    float2 p0 = __ldg(T.es32 + j), p1 = __ldg(T.es32 + j + 1);
+    load_window(p, w);
+    float2 p0, p1;
+    bracket32(T, d, p, w, eb, p0, p1);
     float Ef = __double2float_rn(E);
     float f = (Ef - p0.x) / (p1.x - p0.x);
     return p0.y + f * (p1.y - p0.y);
@@ -537,22 +542,18 @@ __device__ __forceinline__ void macro32(const Tables& T, int32_t m, double E, do
     float Ef = __double2float_rn(E);
     for (int32_t q = q0; q < q1; q += kIlp32) {
         Desc32 d[kIlp32];
-        int32_t aw[kIlp32];
+        const float4* pw[kIlp32];
 #pragma unroll
         for (int u = 0; u < kIlp32; ++u) {
             d[u] = load_desc32(T.d32 + (q + u < q1 ? q + u : q));
-            aw[u] = window_of(T, d[u], eb);
+            pw[u] = window_of(T, d[u], eb);
         }
         float4 w[kIlp32][4];
 #pragma unroll
-        for (int u = 0; u < kIlp32; ++u) load_window(T, aw[u], w[u]);
+        for (int u = 0; u < kIlp32; ++u) load_window(pw[u], w[u]);
         float2 p0[kIlp32], p1[kIlp32];
 #pragma unroll
-        for (int u = 0; u < kIlp32; ++u) {
-            int32_t jj = bracket_from_window(w[u], aw[u], d[u], eb);
-            p0[u] = __ldg(T.es32 + jj);
-            p1[u] = __ldg(T.es32 + jj + 1);
-        }
+        for (int u = 0; u < kIlp32; ++u) bracket32(T, d[u], pw[u], w[u], eb, p0[u], p1[u]);
         float run[kIlp32];
 #pragma unroll
         for (int u = 0; u < kIlp32; ++u) {
