@@ -6,7 +6,10 @@
 // a device-evaluated while-condition: no host round trip per event.
 //
 // Iteration: plan -> source (refill, Sec. 2 "In-Flight Particles") ->
-// sort (Sec. 2 "Sorting") -> lookup -> advance -> surface -> collision.
+// sort (Sec. 2 "Sorting") -> lookup -> ray trace (flights and the surface
+// crossings that keep the material) -> collision (which first finishes the
+// flight that reached it).  Once the source is exhausted and few particles
+// remain, a tail kernel finishes them one warp per particle.
 #include "device.cuh"
 #include "launch.h"
 

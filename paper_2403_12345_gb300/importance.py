@@ -6,8 +6,9 @@ Orchestration only; every step runs in libgbmc's kernels:
    energy bin); after each run the sites are scored by whether their
    history left through the slab's far face (gbmc_importance_record /
    _accumulate) -- the analog estimate of the importance there;
-2. the mesh's features, targets ln((s + 1/2) / (n + 1)) and weights n form
-   the training set (gbmc_importance_training_set);
+2. the mesh's features with per-cell targets form the training set
+   (gbmc_importance_training_set): a cell pools its energy bins and shrinks
+   toward the overall score fraction, target ln I_c, weight N_c / (N_c + 5);
 3. the 4 -> 64 -> 64 -> 1 network is trained by full-batch Adam on the GPU
    (gbmc_mlp_train: BF16 tensor-core forward and backward);
 4. the windows are set from the network on the mesh
