@@ -278,7 +278,10 @@ int ensure_bank(gbmc_ctx* c, int32_t M) {
 // material rounded up to 8 (rows start on 32-byte boundaries and the lookup
 // stores 4 sums at a time), in the table precision.  Above kCumBudget bytes
 // the collision recomputes instead.
-int64_t cum_row(const gbmc_ctx* c) { return ((int64_t)c->max_nuc_per_mat + 7) / 8 * 8; }
+// checkpoints per slot: one per kCumGroup entries of the largest material
+int64_t cum_row(const gbmc_ctx* c) {
+    return ((int64_t)c->max_nuc_per_mat + kCumGroup - 1) / kCumGroup;
+}
 
 constexpr size_t kCumBudget = (size_t)16 << 30;
 

@@ -304,6 +304,9 @@ __device__ __forceinline__ double ln_series(double x) {
 }
 
 // ---------------------------------------------------------------- lookup
+// The lookup stores the running sum after every kCumGroup entries of the
+// material (checkpoints); the collision recomputes at most kCumGroup terms.
+constexpr int kCumGroup = 4;
 // Bracket search: the largest j in [0, n-2] with grid[j] <= E.  Positive IEEE
 // values order like their bit patterns, so every comparison runs on the
 // integer pipe (binary64 compares would occupy the scarce FP64 units).
@@ -380,6 +383,7 @@ __device__ __forceinline__ double micro64(const Tables& T, int32_t i, double E) 
 // per nuclide replaces the index load, the bisection probes and the bracket
 // loads; a bucket with hi - lo > 6 is searched by bisection instead.
 constexpr int kIlp32 = 4;   // nuclides whose windows are in flight together
+static_assert(kIlp32 == kCumGroup, "one checkpoint per lock-step group");
 constexpr int kPad32 = 8;   // sentinel pairs after each nuclide's grid
 
 __device__ __forceinline__ Desc32 load_desc32(const Desc32* p) {
@@ -452,14 +456,15 @@ __device__ __forceinline__ float micro32(const Tables& T, int32_t q, double E) {
 
 // Macroscopic sigma_t, sigma_a of material m: sum over its nuclides in the
 // listed order of N_i sigma_i, and of (N_i sigma_i) f_abs,i.  With cum !=
-// NULL the running sum of N_i sigma_i after nuclide k is also stored at
-// cum[k] (the collision picks its nuclide from these sums); cum must be
-// aligned to 32 bytes and hold the material's count rounded up to kIlp.
+// NULL the running sum of N_i sigma_i after every kCumGroup nuclides (and
+// after the last) is stored at cum[g] (the collision picks its nuclide from
+// these checkpoints).
 //
 // The brackets of kIlp consecutive nuclides are searched in lock step (kIlp
 // independent chains of dependent loads in flight per thread); the terms are
 // then formed and added strictly in the listed order.
 constexpr int kIlp = 4;
+static_assert(kIlp == kCumGroup, "one checkpoint per lock-step group");
 
 template <class U>
 __device__ __forceinline__ void brackets(const Tables& T, const NucIndex* nx,
@@ -522,13 +527,8 @@ __device__ __forceinline__ void macro64(const Tables& T, int32_t m, double E, do
             }
             run[u] = at;
         }
-        // one 32-byte sector per group (the slot's row is padded to a
-        // multiple of 8 entries; entries past the material's end are unread)
-        if (cum) {
-            double2* d = reinterpret_cast<double2*>(cum + (q - q0));
-            d[0] = make_double2(run[0], run[1]);
-            d[1] = make_double2(run[2], run[3]);
-        }
+        // the running sum after each group of kCumGroup entries
+        if (cum) cum[(q - q0) / kCumGroup] = run[kIlp - 1];
     }
     st = at;
     sa = aa;
@@ -566,13 +566,7 @@ __device__ __forceinline__ void macro32(const Tables& T, int32_t m, double E, do
             }
             run[u] = at;
         }
-        if (cum) {
-            if (kIlp32 == 4)
-                *reinterpret_cast<float4*>(cum + (q - q0)) =
-                    make_float4(run[0], run[1], run[2 % kIlp32], run[3 % kIlp32]);
-            else
-                *reinterpret_cast<float2*>(cum + (q - q0)) = make_float2(run[0], run[1 % kIlp32]);
-        }
+        if (cum) cum[(q - q0) / kCumGroup] = run[kIlp32 - 1];
     }
     st = (double)at;
     sa = (double)aa;
@@ -604,7 +598,8 @@ __device__ __forceinline__ void macro_warp(const Tables& T, int32_t m, double E,
             for (int k = 0; k < kmax; ++k) {
                 at = at + __shfl_sync(full, t, k);
                 aa = aa + __shfl_sync(full, p, k);
-                if (cum && lane == k) ((double*)cum)[(int64_t)(c + k - q0) * stride] = at;
+                if (cum && lane == k && ((c + k - q0) % kCumGroup == kCumGroup - 1 || c + k == q1 - 1))
+                    ((double*)cum)[(int64_t)((c + k - q0) / kCumGroup) * stride] = at;
             }
         }
         st = at;
@@ -622,7 +617,8 @@ __device__ __forceinline__ void macro_warp(const Tables& T, int32_t m, double E,
             for (int k = 0; k < kmax; ++k) {
                 at = at + __shfl_sync(full, t, k);
                 aa = aa + __shfl_sync(full, p, k);
-                if (cum && lane == k) ((float*)cum)[(int64_t)(c + k - q0) * stride] = at;
+                if (cum && lane == k && ((c + k - q0) % kCumGroup == kCumGroup - 1 || c + k == q1 - 1))
+                    ((float*)cum)[(int64_t)((c + k - q0) / kCumGroup) * stride] = at;
             }
         }
         st = (double)at;
@@ -660,22 +656,47 @@ __device__ __forceinline__ int32_t pick_nuclide(const Tables& T, int precision, 
     return last >= 0 ? last : __ldg(T.nuc_id + q0);
 }
 
-// The same choice from the running sums the lookup stored (cum[k * stride],
-// non-decreasing in k): binary search for the first k with target < cum_k.
-// Returns -1 when no sum exceeds the target (then pick_nuclide decides).
-template <class F>
-__device__ __forceinline__ int32_t pick_from_sums(const Tables& T, int32_t m, const F* cum,
-                                                  int64_t stride, double target) {
+// The same choice from the lookup's checkpoints (cum[g * stride]: the
+// running sum after entry kCumGroup g + kCumGroup - 1, non-decreasing in g):
+// the first group whose checkpoint exceeds the target holds the nuclide; its
+// terms are recomputed exactly as the lookup formed them and added to the
+// previous checkpoint in the listed order, so every running sum, and hence
+// the choice, is the one the full sums give.  Returns -1 when no sum exceeds
+// the target (then pick_nuclide decides).
+template <int PREC>
+__device__ __forceinline__ int32_t pick_from_sums(const Tables& T, int32_t m, const void* cum,
+                                                  int64_t stride, double E, double target) {
     int32_t q0 = __ldg(T.mat_off + m), nq = __ldg(T.mat_off + m + 1) - q0;
-    int32_t lo = 0, hi = nq;
+    int32_t ng = (nq + kCumGroup - 1) / kCumGroup;
+    const double* c64 = (const double*)cum;
+    const float* c32 = (const float*)cum;
+    int32_t lo = 0, hi = ng;
     while (lo < hi) {
         int32_t mid = (lo + hi) >> 1;
-        if (target < (double)cum[(int64_t)mid * stride])
+        double v = PREC == GBMC_FP64 ? c64[(int64_t)mid * stride] : (double)c32[(int64_t)mid * stride];
+        if (target < v)
             hi = mid;
         else
             lo = mid + 1;
     }
-    return lo < nq ? __ldg(T.nuc_id + q0 + lo) : -1;
+    if (lo >= ng) return -1;
+    int32_t k0 = lo * kCumGroup, k1 = min(k0 + kCumGroup, nq);
+    if (PREC == GBMC_FP64) {
+        double at = lo > 0 ? c64[(int64_t)(lo - 1) * stride] : 0.0;
+        for (int32_t k = k0; k < k1; ++k) {
+            int32_t i = __ldg(T.nuc_id + q0 + k);
+            at = at + __ldg(T.density + q0 + k) * micro64(T, i, E);
+            if (target < at) return i;
+        }
+    } else {
+        float at = lo > 0 ? c32[(int64_t)(lo - 1) * stride] : 0.0f;
+        for (int32_t k = k0; k < k1; ++k) {
+            float t = __ldg(&T.d32[q0 + k].density) * micro32(T, q0 + k, E);
+            at = at + t;
+            if (target < (double)at) return __ldg(T.nuc_id + q0 + k);
+        }
+    }
+    return -1;   // not reached: the group's checkpoint exceeds the target
 }
 
 // Tally energy bin: largest b in [0, n_bins-1] with edges[b] <= E.

@@ -736,10 +736,9 @@ __device__ __forceinline__ int collide(const Params& P, const DevProblem& pr, Pa
     double target = r.next() * pt.st;
     int32_t nuc = -1;
     if (P.cum) {
-        if (PREC == GBMC_FP64)
-            nuc = pick_from_sums(P.T, pt.mat, (const double*)P.cum + slot * P.cum_stride, 1, target);
-        else
-            nuc = pick_from_sums(P.T, pt.mat, (const float*)P.cum + slot * P.cum_stride, 1, target);
+        const void* row = PREC == GBMC_FP64 ? (const void*)((const double*)P.cum + slot * P.cum_stride)
+                                            : (const void*)((const float*)P.cum + slot * P.cum_stride);
+        nuc = pick_from_sums<PREC>(P.T, pt.mat, row, 1, pt.E, target);
     }
     if (nuc < 0) nuc = pick_nuclide(P.T, PREC, pt.mat, pt.E, target);
     pt.ncoll = pt.ncoll + 1;
@@ -1002,6 +1001,7 @@ __global__ void __launch_bounds__(256) k_tail(Params P) {
                 }
             }
             int action = 0;   // 0: fly on, 1: new lookup, 2: dead
+            __syncwarp();     // the lanes' running-sum checkpoints, visible to lane 0
             if (lane == 0) {
                 double xi;
                 bool col = fly(P, pr, pt, r, xi);
