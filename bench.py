@@ -1,12 +1,14 @@
 """Throughput of the event-based transport hot path on one GB300.
 
 One step = one batch of the workload through the whole hot path (source,
-sort, lookup, advance, surface, collision, tallies) in one device-driven
-run of libgbmc.  Default workload: the 17x17 pin lattice with 68 + 3
-synthetic nuclides of 10k-60k grid points, binary64 tables, 1e6 particles
-per batch.
+sort, lookup, ray trace, collision, tallies) in one device-driven run of
+libgbmc.  Default workload: the 17x17 pin lattice with 68 + 3 synthetic
+nuclides of 10k-60k grid points, binary64 tables, 1e6 particles per batch.
+--config 3 / 4: binary32 lattice, 64 lattices in one launch; --config 5:
+learned weight windows against analog (figure of merit); --config 6: the
+lookup-only stress set.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbmc|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbmc|reference] [--config C]
 """
 import argparse
 import ctypes
@@ -31,7 +33,8 @@ FP64_NOMINAL_TFLOPS = 1.25       # GB300 dense FP64 (recipe table)
 # DFMA/s on this GPU)
 FP64_SLOTS_PER_MICRO = 9 + 9.2
 BRACKET_BYTES = {0: 32, 1: 16}    # E_j, E_j+1, s_j, s_j+1
-LOOKUP_IO_BYTES = 36              # queue index 4, E 8, material 4, sigma_t/a 16, advance-queue 4
+LOOKUP_IO_BYTES = 28              # per macro lookup: E 8, material 4, sigma_t and sigma_a 16
+ITER_KERNELS = 8                  # plan, source, 3 sort, lookup, ray trace, collision
 
 WORKLOADS = {
     1: "infinite medium, 4 nuclides x 2000 log-spaced points, 1e5 particles/batch",
@@ -40,6 +43,10 @@ WORKLOADS = {
     3: "17x17 pin lattice, binary32 tables, sorted, 1e7 particles/batch",
     4: "64 independent lattices (3x3..17x17, 4-68 pin nuclides, 1e4-1e6 particles each, "
        "log-uniform), binary32 tables, one device-driven graph launch, autotuned",
+    5: "deep-penetration slab (10 cm scatterer + 100 cm absorber), far-face leakage; learned "
+       "weight windows (4-64-64-1 BF16 MLP trained on analog estimates) against analog",
+    6: "lookup-only stress set: 281 nuclides x 60k points, one 244-nuclide material, 1e7 "
+       "energies log-uniform on [1e-5, 2e7] eV (unsorted; the library sorts)",
 }
 
 
@@ -158,6 +165,240 @@ def config_of(args, prob):
             "parallelism": f"replicas{args.gpus}"}
 
 
+def _timed(ctx_call, steps, flush, stream, clk_index):
+    """CUDA-event times (ms) of `steps` calls of ctx_call(k), with an L2 flush
+    before each, and the clocks sampled meanwhile."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    torch.cuda.synchronize()
+    with Clocks(clk_index) as clk:
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            ctx_call(k)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev], clk.summary()
+
+
+def _max_over_ranks(x, world):
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([x], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    return x
+
+
+def run_stress(args, rank, world, local):
+    """Lookup-only stress set: one step = the macroscopic lookup of every query
+    (sorted by the library, then looked up) through gbmc_lookup_macro."""
+    import torch
+    from paper_2403_12345_gb300 import gbmc
+    prec = 1 if args.precision < 0 else args.precision
+    nq = args.particles or 10_000_000
+    prob, E, mat = synth.make_stress_lookup(n_queries=nq, seed_offset=rank)
+    micro_per = int(prob.mat_off[1] - prob.mat_off[0])
+    bracket = BRACKET_BYTES[prec]
+    cfg = {"workload": prob.name, "description": WORKLOADS[6], "queries_per_step": nq,
+           "table_precision": "fp32" if prec == 1 else "fp64", "nuclides": int(prob.n_nuc),
+           "grid_points": int(prob.grid_off[-1]), "nuclides_in_material": micro_per,
+           "table_bytes": int(prob.table_bytes(prec)),
+           "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas{args.gpus}"}
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import oracle
+        n = 2000
+        t = time.perf_counter()
+        oracle.macro(prob, 0, E[:n], precision=prec)
+        dt = time.perf_counter() - t
+        n = int(min(nq, max(2000, args.ref_step_s / max(dt, 1e-6) * n)))
+        times = []
+        for k in range(args.steps):
+            t = time.perf_counter()
+            oracle.macro(prob, 0, E[k * 7919 % max(1, nq - n):][:n], precision=prec)
+            times.append(time.perf_counter() - t)
+        value = n * args.steps / sum(times)
+        print(json.dumps({
+            "impl": "reference", "metric": "XS lookups/s", "value": value, "unit": "lookups/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == 1 else "f64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": "lookups/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{n} queries per step"},
+            "e2e": {"value": value, "unit": "lookups/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}), flush=True)
+        return
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    stream = torch.cuda.current_stream()
+    ctx = gbmc.Context(local, precision=prec)
+    ctx.load(prob, (prec,))
+    dE = torch.from_numpy(E).cuda()
+    dm = torch.from_numpy(mat).cuda()
+    st = torch.empty_like(dE)
+    sa = torch.empty_like(dE)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        ctx.lookup_macro(dE, dm, st, sa, precision=prec, sort=True, stream=stream)
+    if world > 1:
+        dist.barrier()
+    ms, clocks = _timed(lambda k: ctx.lookup_macro(dE, dm, st, sa, precision=prec, sort=True,
+                                                   stream=stream),
+                        args.steps, flush, stream, local)
+    tot_ms = _max_over_ranks(sum(ms), world)
+    value = nq * args.steps * world / (tot_ms * 1e-3)
+    # the lookup kernel alone: queries in sorted order, no library sort
+    order = np.argsort(E, kind="stable")
+    dEs = torch.from_numpy(E[order]).cuda()
+    for _ in range(2):
+        ctx.lookup_macro(dEs, dm, st, sa, precision=prec, sort=False, stream=stream)
+    kms, _ = _timed(lambda k: ctx.lookup_macro(dEs, dm, st, sa, precision=prec, sort=False,
+                                               stream=stream), args.steps, flush, stream, local)
+    lk_ms = statistics.median(kms)
+    alg = nq * (micro_per * bracket + LOOKUP_IO_BYTES)
+    hbm, peak_src = peaks()
+    gbs = alg / (lk_ms * 1e-3) / 1e9
+    # end to end: queries from pinned host memory, results back to the host
+    hE = torch.from_numpy(E).pin_memory()
+    hst = torch.empty(nq, dtype=torch.float64).pin_memory()
+    hsa = torch.empty(nq, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        dE.copy_(hE, non_blocking=True)
+        ctx.lookup_macro(dE, dm, st, sa, precision=prec, sort=True, stream=stream)
+        hst.copy_(st, non_blocking=True)
+        hsa.copy_(sa, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e = nq * args.e2e_steps / (time.perf_counter() - t0)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        n = 2000
+        t = time.perf_counter()
+        oracle.macro(prob, 0, E[:n], precision=prec)
+        n = int(min(nq, max(2000, args.cpu_budget_s / max(time.perf_counter() - t, 1e-6) * n)))
+        t = time.perf_counter()
+        oracle.macro(prob, 0, E[:n], precision=prec)
+        dt = time.perf_counter() - t
+        cpu = {"value": n / dt, "unit": "lookups/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {n} queries ({dt:.1f} s, one thread)"}
+    roof = {"kernel": "lookup (sorted queries, no library sort)", "bound": "hbm",
+            "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": None,
+            "peak_source": peak_src, "launches": 1, "avg_launch_ms": lk_ms,
+            "algorithmic_bytes_per_launch": alg}
+    if prec == 0:
+        slots = nq * micro_per * FP64_SLOTS_PER_MICRO / (lk_ms * 1e-3)
+        alu_peak = FP64_NOMINAL_TFLOPS * 1e12 / 2
+        if slots / alu_peak > roof["frac"]:
+            roof.update({"bound": "alu", "achieved": slots / 1e9, "peak": alu_peak / 1e9,
+                         "unit": "G FP64-slot/s", "frac": slots / alu_peak,
+                         "peak_source": "nominal 1.25 TFLOP/s FP64 = 625 G DFMA slots/s",
+                         "hbm_equiv_gbs": gbs})
+    if rank == 0:
+        print(json.dumps({
+            "metric": "XS lookups/s", "value": value, "unit": "lookups/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if prec == 1 else "f64", "data": "synthetic", "config": cfg,
+            "micro_lookups_per_s": value * micro_per,
+            "e2e": {"value": e2e, "unit": "lookups/s", "h2d_bytes_per_step": nq * 8,
+                    "d2h_bytes_per_step": nq * 16},
+            "roofline": roof,
+            "cpu_baseline": cpu, "clocks": clocks,
+            "gpu_launches": 4 * args.steps}), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_windows(args, prob, rank, world, local):
+    """Deep-penetration slab: learned weight windows against analog.  One step
+    = one batch with the learned windows; the figure of merit FOM = 1/(R^2 T)
+    of the far-face leakage is reported for both methods."""
+    import torch
+    import torch.distributed as dist
+    from paper_2403_12345_gb300 import gbmc
+    from paper_2403_12345_gb300 import importance as imp
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    stream = torch.cuda.current_stream()
+    g = gbmc.geometry_from(prob.geom)
+    ctx = gbmc.Context(local)
+    ctx.load(prob)
+    n_an = 4_000_000
+    n_ww = args.particles or 400_000
+    off = 100_000 * rank
+    analog = lambda b: gbmc.problem(g, prob.seed, n_an, batch=off + b)
+    learned = lambda b: gbmc.problem(g, prob.seed, n_ww, batch=off + b)
+    t0 = time.perf_counter()
+    lw = imp.LearnedWindows(ctx, g, prob.edges, seed=5)
+    lw.collect(analog, range(50_000, 50_004), capacity=16_000_000, stream=stream)
+    loss = lw.train(steps=1500, lr=3e-3, stream=stream)
+    lw.apply(stream=stream)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for w in range(args.warmup):
+        ctx.run_batch(learned(60_000 + w), stream)
+    if world > 1:
+        dist.barrier()
+    ms, clocks = _timed(lambda k: ctx.run_batch(learned(k), stream), args.steps, flush, stream,
+                        local)
+    tot_ms = _max_over_ranks(sum(ms), world)
+    value = n_ww * args.steps * world / (tot_ms * 1e-3)
+    fw = imp.figure_of_merit(ctx, learned, range(1000, 1020), n_ww, stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, args.e2e_steps)
+    for k in range(e2e_steps):
+        ctx.run_batch(learned(2000 + k), stream)
+        flux, _, _ = ctx.read_tallies(0)
+    e2e = n_ww * e2e_steps / (time.perf_counter() - t0)
+    ctx.clear_weight_windows()
+    fa = imp.figure_of_merit(ctx, analog, range(3000, 3020), n_an, stream)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        threads = len(os.sched_getaffinity(0))
+        rate, n, dt = oracle_rate(prob, args.cpu_budget_s, threads)
+        cpu = {"value": rate, "unit": "particles/s", "cores": threads, "kind": "oracle",
+               "sample": f"first {n} analog histories of batch 0 ({dt:.1f} s)"}
+    if rank == 0:
+        se = float(np.hypot(fa["mean"] * fa["rel_err"], fw["mean"] * fw["rel_err"]))
+        print(json.dumps({
+            "metric": "particles/s", "value": value, "unit": "particles/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": prob.name, "description": WORKLOADS[5],
+                       "particles_per_batch": n_ww, "analog_particles_per_batch": n_an,
+                       "table_precision": "fp64", "nuclides": int(prob.n_nuc),
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "parallelism": f"replicas{args.gpus}"},
+            "fom": {"analog": fa["fom"], "learned": fw["fom"], "ratio": fw["fom"] / fa["fom"],
+                    "analog_leak_far": [fa["mean"], fa["mean"] * fa["rel_err"]],
+                    "learned_leak_far": [fw["mean"], fw["mean"] * fw["rel_err"]],
+                    "z": (fw["mean"] - fa["mean"]) / se if se > 0 else None,
+                    "batches": 20, "train_loss": loss, "setup_s": setup_s},
+            "e2e": {"value": e2e, "unit": "particles/s",
+                    "h2d_bytes_per_step": ctypes.sizeof(gbmc.Problem),
+                    "d2h_bytes_per_step": int(flux.nbytes + 16 * gbmc.NSCAL)},
+            "roofline": None,
+            "cpu_baseline": cpu, "clocks": clocks,
+            "gpu_launches": None}), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -182,6 +423,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
+    if args.config == 6:
+        run_stress(args, rank, world, local)
+        return
     prob = synth.make_config(args.config, n_particles=args.particles or None)
     if args.precision < 0:
         args.precision = prob.precision
@@ -189,6 +433,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, prob, rank)
+        return
+    if args.config == 5:
+        run_windows(args, prob, rank, world, local)
         return
 
     import torch
@@ -307,7 +554,7 @@ def main():
         cpu = {"value": rate, "unit": "particles/s", "cores": threads, "kind": "oracle",
                "sample": f"first {n} histories of batch 0 ({dt:.1f} s)"}
 
-    launches = sum(1 + 9 * s["iterations"] for s in stats)
+    launches = sum(2 + ITER_KERNELS * s["iterations"] for s in stats)   # + init, tail
     if rank == 0:
         line = {
             "metric": "particles/s", "value": value, "unit": "particles/s", "n_gpus": world,
