@@ -383,7 +383,7 @@ __device__ __forceinline__ double micro64(const Tables& T, int32_t i, double E) 
 // per nuclide replaces the index load, the bisection probes and the bracket
 // loads; a bucket with hi - lo > 6 is searched by bisection instead.
 constexpr int kIlp32 = 4;   // nuclides whose windows are in flight together
-static_assert(kIlp32 == kCumGroup, "one checkpoint per lock-step group");
+static_assert(kIlp32 % kCumGroup == 0, "whole checkpoint groups per lock-step group");
 constexpr int kPad32 = 8;   // sentinel pairs after each nuclide's grid
 
 __device__ __forceinline__ Desc32 load_desc32(const Desc32* p) {
@@ -566,7 +566,11 @@ __device__ __forceinline__ void macro32(const Tables& T, int32_t m, double E, do
             }
             run[u] = at;
         }
-        if (cum) cum[(q - q0) / kCumGroup] = run[kIlp32 - 1];
+        if (cum) {
+#pragma unroll
+            for (int u = kCumGroup - 1; u < kIlp32; u += kCumGroup)
+                if (q + u - (kCumGroup - 1) < q1) cum[(q - q0 + u) / kCumGroup] = run[u];
+        }
     }
     st = (double)at;
     sa = (double)aa;

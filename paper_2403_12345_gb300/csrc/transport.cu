@@ -410,57 +410,65 @@ __global__ void __launch_bounds__(256) k_sort_scatter(Params P) {
 // ---------------------------------------------------------------- lookup event
 
 template <int PREC>
-__global__ void __launch_bounds__(256) k_lookup(Params P) {
+// Thread mode (long queues): one particle per thread.
+__global__ void __launch_bounds__(256, 3) k_lookup(Params P) {
     const Ctl* c = P.ctl;
     int32_t n = c->lookup_n;
-    if (n == 0) return;
+    if (n == 0 || c->warp_lookup) return;
     int cur = c->cur;
     const int32_t* q = c->sorted ? P.Q.lqs : P.Q.lq[cur];
     int32_t* aq = P.Q.aq[cur] + c->aq_base;
     unsigned long long micro = 0;
-    if (c->warp_lookup) {
-        // one particle per warp
-        int lane = threadIdx.x & 31;
-        int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-        int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-        for (int64_t idx = w0; idx < n; idx += nw) {
+    GBMC_WARP_LOOP(idx, valid, n) {
+        if (valid) {
             int32_t slot = q[idx];
             double E = P.B.p[slot].E;
             int32_t m = P.B.p[slot].mat;
             double st, sa;
-            void* cum = P.cum ? (PREC == GBMC_FP64 ? (void*)((double*)P.cum + slot * P.cum_stride)
-                                                   : (void*)((float*)P.cum + slot * P.cum_stride))
-                              : nullptr;
-            macro_warp<PREC>(P.T, m, E, st, sa, cum, 1);
-            if (lane == 0) {
-                P.B.p[slot].st = st;
-                P.B.p[slot].sa = sa;
-                aq[idx] = slot;
-                micro += (unsigned long long)(__ldg(P.T.mat_off + m + 1) - __ldg(P.T.mat_off + m));
-            }
-        }
-    } else {
-        GBMC_WARP_LOOP(idx, valid, n) {
-            if (valid) {
-                int32_t slot = q[idx];
-                double E = P.B.p[slot].E;
-                int32_t m = P.B.p[slot].mat;
-                double st, sa;
-                if (PREC == GBMC_FP64)
-                    macro64(P.T, m, E, st, sa,
-                            P.cum ? (double*)P.cum + slot * P.cum_stride : nullptr);
-                else
-                    macro32(P.T, m, E, st, sa,
-                            P.cum ? (float*)P.cum + slot * P.cum_stride : nullptr);
-                P.B.p[slot].st = st;
-                P.B.p[slot].sa = sa;
-                aq[idx] = slot;
-                micro += (unsigned long long)(__ldg(P.T.mat_off + m + 1) - __ldg(P.T.mat_off + m));
-            }
+            if (PREC == GBMC_FP64)
+                macro64(P.T, m, E, st, sa, P.cum ? (double*)P.cum + slot * P.cum_stride : nullptr);
+            else
+                macro32(P.T, m, E, st, sa, P.cum ? (float*)P.cum + slot * P.cum_stride : nullptr);
+            P.B.p[slot].st = st;
+            P.B.p[slot].sa = sa;
+            aq[idx] = slot;
+            micro += (unsigned long long)(__ldg(P.T.mat_off + m + 1) - __ldg(P.T.mat_off + m));
         }
     }
     for (int o = 16; o > 0; o >>= 1) micro += __shfl_xor_sync(kFull, micro, o);
     if ((threadIdx.x & 31) == 0 && micro) atomicAdd(&P.ctl->st_micro, micro);
+}
+
+// Warp mode (short queues): one particle per warp.
+template <int PREC>
+__global__ void __launch_bounds__(256) k_lookup_warp(Params P) {
+    const Ctl* c = P.ctl;
+    int32_t n = c->lookup_n;
+    if (n == 0 || !c->warp_lookup) return;
+    int cur = c->cur;
+    const int32_t* q = c->sorted ? P.Q.lqs : P.Q.lq[cur];
+    int32_t* aq = P.Q.aq[cur] + c->aq_base;
+    unsigned long long micro = 0;
+    int lane = threadIdx.x & 31;
+    int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t idx = w0; idx < n; idx += nw) {
+        int32_t slot = q[idx];
+        double E = P.B.p[slot].E;
+        int32_t m = P.B.p[slot].mat;
+        double st, sa;
+        void* cum = P.cum ? (PREC == GBMC_FP64 ? (void*)((double*)P.cum + slot * P.cum_stride)
+                                               : (void*)((float*)P.cum + slot * P.cum_stride))
+                          : nullptr;
+        macro_warp<PREC>(P.T, m, E, st, sa, cum, 1);
+        if (lane == 0) {
+            P.B.p[slot].st = st;
+            P.B.p[slot].sa = sa;
+            aq[idx] = slot;
+            micro += (unsigned long long)(__ldg(P.T.mat_off + m + 1) - __ldg(P.T.mat_off + m));
+        }
+    }
+    if (lane == 0 && micro) atomicAdd(&P.ctl->st_micro, micro);
 }
 
 // ---------------------------------------------------------------- per-particle steps
@@ -1095,7 +1103,7 @@ __global__ void __launch_bounds__(256) k_query_scatter(int64_t n, const uint32_t
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(256) k_query_lookup(Tables T, const double* __restrict__ E,
+__global__ void __launch_bounds__(256, 4) k_query_lookup(Tables T, const double* __restrict__ E,
                                                       const int32_t* __restrict__ mat, int64_t n,
                                                       const int32_t* __restrict__ perm,
                                                       double* __restrict__ st,
@@ -1128,10 +1136,13 @@ cudaError_t launch_iteration(const Params& P, const LaunchCfg& L, cudaStream_t s
         k_sort_scan<<<kScanBlocks, 1024, 0, s>>>(P);
         k_sort_scatter<<<L.grid, 256, 0, s>>>(P);
     }
-    if (P.precision == GBMC_FP64)
+    if (P.precision == GBMC_FP64) {
+        k_lookup_warp<GBMC_FP64><<<L.grid_lookup, 256, 0, s>>>(P);
         k_lookup<GBMC_FP64><<<L.grid_lookup, 256, 0, s>>>(P);
-    else
+    } else {
+        k_lookup_warp<GBMC_FP32><<<L.grid_lookup, 256, 0, s>>>(P);
         k_lookup<GBMC_FP32><<<L.grid_lookup, 256, 0, s>>>(P);
+    }
     k_raytrace<<<L.grid, 256, 0, s>>>(P);
     if (P.precision == GBMC_FP64)
         k_collision<GBMC_FP64><<<L.grid, 256, 0, s>>>(P);
@@ -1161,10 +1172,13 @@ cudaError_t launch_iteration_timed(const Params& P, const LaunchCfg& L, cudaStre
     cudaEventRecord(ev[4], s);
     if (P.sort) k_sort_scatter<<<L.grid, 256, 0, s>>>(P);
     cudaEventRecord(ev[5], s);
-    if (P.precision == GBMC_FP64)
+    if (P.precision == GBMC_FP64) {
+        k_lookup_warp<GBMC_FP64><<<L.grid_lookup, 256, 0, s>>>(P);
         k_lookup<GBMC_FP64><<<L.grid_lookup, 256, 0, s>>>(P);
-    else
+    } else {
+        k_lookup_warp<GBMC_FP32><<<L.grid_lookup, 256, 0, s>>>(P);
         k_lookup<GBMC_FP32><<<L.grid_lookup, 256, 0, s>>>(P);
+    }
     cudaEventRecord(ev[6], s);
     k_raytrace<<<L.grid, 256, 0, s>>>(P);
     cudaEventRecord(ev[7], s);
