@@ -238,6 +238,23 @@ int gbmc_run_problems(gbmc_ctx *ctx, int32_t n_prob, const gbmc_problem *probs,
 int gbmc_read_tallies(gbmc_ctx *ctx, int32_t slot, double *flux, int64_t n_flux,
                       int64_t *counts, double *weights);
 
+/* Track-length absorption-rate tally (reaction-rate tally; the next step
+ * after the lookup and tally of Sec. 2 "Tallying", which says tallies are
+ * scored in active batches): for every flight segment of length d,
+ * w d Sigma_a(E) is added to the segment's (cell, energy bin), Sigma_a being
+ * the macroscopic absorption cross section the lookup formed for the
+ * segment's energy and material.  Laid out as the flux tally.  Off by
+ * default; gbmc_set_reaction_tally(ctx, 1) turns it on for the following
+ * runs, starting it at zero (gbmc_reset_tallies zeroes it with the others),
+ * 0 turns it off and frees it.  Errors: INVALID_ARG for on not 0/1. */
+int gbmc_set_reaction_tally(gbmc_ctx *ctx, int32_t on);
+
+/* Copy problem slot `slot`'s absorption-rate tally [n_cells x n_bins]
+ * (row = cell) to HOST absrate[n]; n must equal the slot's cells x bins.
+ * Synchronizes with the last run.  Errors: NOT_INITIALIZED while the tally
+ * is off or before a run, INVALID_ARG for a bad slot or size. */
+int gbmc_read_reaction_tally(gbmc_ctx *ctx, int32_t slot, double *absrate, int64_t n);
+
 /* Synchronize and copy per-particle outcomes of the last run for particles
  * first .. first+n-1 of problem slot `slot` (index within that problem's
  * batch).  Any output pointer may be NULL.  Final E and position are the

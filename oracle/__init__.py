@@ -50,7 +50,7 @@ class _Result(C.Structure):
         ("n_coll", _P(C.c_int32)), ("status", _P(C.c_int8)), ("n_flights", _P(C.c_int32)),
         ("n_draws", _P(C.c_uint32)), ("E", _P(C.c_double)), ("x", _P(C.c_double)),
         ("y", _P(C.c_double)), ("z", _P(C.c_double)), ("flux", _P(C.c_double)),
-        ("counts", _P(C.c_int64)), ("weights", _P(C.c_double)),
+        ("absrate", _P(C.c_double)), ("counts", _P(C.c_int64)), ("weights", _P(C.c_double)),
     ]
 
 
@@ -205,7 +205,8 @@ def key_hi(problem_index: int, batch: int) -> int:
 def run(prob, seed: int, batch: int = 0, first_id: int = 0, n=None, geom_index: int = 0,
         problem_index: int = 0, threads=None, precision=None, ww=None):
     """Histories [first_id, first_id + n) of one batch; returns a dict with
-    per-particle outcomes, the flux tally [n_cells, n_bins] and the scalars.
+    per-particle outcomes, the flux tally [n_cells, n_bins], the track-length
+    absorption-rate tally sum w d Sigma_a [n_cells, n_bins] and the scalars.
     ww = (lower [n_cells, n_bins], ratio, survival, max_split) turns on
     weight windows; split copies are transported depth first and scored in
     the tallies (the outcomes are the primary histories')."""
@@ -219,7 +220,8 @@ def run(prob, seed: int, batch: int = 0, first_id: int = 0, n=None, geom_index: 
         n_coll=np.zeros(n, np.int32), status=np.zeros(n, np.int8),
         n_flights=np.zeros(n, np.int32), n_draws=np.zeros(n, np.uint32),
         E=np.zeros(n), x=np.zeros(n), y=np.zeros(n), z=np.zeros(n),
-        flux=np.zeros((b.n_cells, b.n_bins)), counts=np.zeros(NSCAL, np.int64),
+        flux=np.zeros((b.n_cells, b.n_bins)), absrate=np.zeros((b.n_cells, b.n_bins)),
+        counts=np.zeros(NSCAL, np.int64),
         weights=np.zeros(NSCAL),
     )
     r = _Result()
@@ -227,7 +229,7 @@ def run(prob, seed: int, batch: int = 0, first_id: int = 0, n=None, geom_index: 
     r.status = _ptr(out["status"], C.c_int8)
     r.n_flights = _ptr(out["n_flights"], C.c_int32)
     r.n_draws = _ptr(out["n_draws"], C.c_uint32)
-    for k in ("E", "x", "y", "z", "flux", "weights"):
+    for k in ("E", "x", "y", "z", "flux", "absrate", "weights"):
         setattr(r, k, _ptr(out[k], C.c_double))
     r.counts = _ptr(out["counts"], C.c_int64)
     rc = lib().or_run(C.byref(b.p), int(seed) & 0xFFFFFFFFFFFFFFFF,

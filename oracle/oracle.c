@@ -492,6 +492,7 @@ static double disk_pair(rng_t *r, double *a, double *b)
 /* ------------------------------------------------------------------------ */
 typedef struct {
     double *fs, *fc;   /* flux sum / compensation */
+    double *as, *ac;   /* absorption-rate sum / compensation (NULL: off) */
     int64_t counts[OR_NSCAL];
     double ws[OR_NSCAL], wc[OR_NSCAL];
 } acc_t;
@@ -680,8 +681,12 @@ static void transport(const or_problem *P, const tables_t *T, rng_t *r, particle
         p.y = p.y + d * p.v;
         p.z = p.z + d * p.w;
         {
+            /* track-length estimators: flux w d and absorption rate
+             * (w d) Sigma_a of the segment's (cell, energy bin) */
             int64_t k = (int64_t)cell * nb + ebin(P, p.E);
-            kadd(&A->fs[k], &A->fc[k], p.wgt * d);
+            double wd = p.wgt * d;
+            kadd(&A->fs[k], &A->fc[k], wd);
+            if (A->as) kadd(&A->as[k], &A->ac[k], wd * p.sa);
         }
         p.n_flights += 1;
         score(A, OR_S_FLIGHT, p.wgt);
@@ -793,6 +798,11 @@ int or_run(const or_problem *P, uint64_t seed, uint64_t key_hi, int64_t first_id
         acc[t].fs = (double *)calloc((size_t)nf, sizeof(double));
         acc[t].fc = (double *)calloc((size_t)nf, sizeof(double));
         if (!acc[t].fs || !acc[t].fc) return -1;
+        if (R->absrate) {
+            acc[t].as = (double *)calloc((size_t)nf, sizeof(double));
+            acc[t].ac = (double *)calloc((size_t)nf, sizeof(double));
+            if (!acc[t].as || !acc[t].ac) return -1;
+        }
     }
     int overflow = 0;
 #ifdef _OPENMP
@@ -826,6 +836,16 @@ int or_run(const or_problem *P, uint64_t seed, uint64_t key_hi, int64_t first_id
             R->flux[b] = s + c;
         }
     }
+    if (R->absrate) {
+        for (int64_t b = 0; b < nf; ++b) {
+            double s = 0.0, c = 0.0;
+            for (int t = 0; t < n_threads; ++t) {
+                kadd(&s, &c, acc[t].as[b]);
+                kadd(&s, &c, acc[t].ac[b]);
+            }
+            R->absrate[b] = s + c;
+        }
+    }
     for (int q = 0; q < OR_NSCAL; ++q) {
         int64_t cnt = 0;
         double s = 0.0, c = 0.0;
@@ -840,6 +860,8 @@ int or_run(const or_problem *P, uint64_t seed, uint64_t key_hi, int64_t first_id
     for (int t = 0; t < n_threads; ++t) {
         free(acc[t].fs);
         free(acc[t].fc);
+        free(acc[t].as);
+        free(acc[t].ac);
     }
     free(acc);
     free(T.ef);

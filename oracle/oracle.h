@@ -81,6 +81,8 @@ typedef struct {
     uint32_t *n_draws;    /* [n] */
     double *E, *x, *y, *z;/* [n] final state */
     double *flux;         /* [n_cells*n_bins], overwritten */
+    double *absrate;      /* [n_cells*n_bins] track-length absorption rate sum w d Sigma_a
+                           * (NULL: not scored), overwritten */
     int64_t *counts;      /* [OR_NSCAL], overwritten */
     double *weights;      /* [OR_NSCAL], overwritten */
 } or_result;

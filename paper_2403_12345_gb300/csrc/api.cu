@@ -90,6 +90,7 @@ struct gbmc_ctx {
     int64_t flux_cap = 0;
     int32_t slots_cap = 0;
     Tallies Y{};
+    bool rr_on = false;              // absorption-rate tally on
 
     // run descriptors
     DevProblem* d_probs = nullptr;
@@ -339,6 +340,15 @@ int ensure_tallies(gbmc_ctx* c, const std::vector<int32_t>& cells, cudaStream_t 
         if (rc) return rc;
         c->flux_cap = tot;
         c->graph_valid = false;
+        if (c->Y.absrate) {
+            dfree(c->Y.absrate);
+            c->Y.absrate = nullptr;
+        }
+    }
+    if (c->rr_on && !c->Y.absrate) {
+        int rc = dalloc(c, &c->Y.absrate, (size_t)c->flux_cap);
+        if (rc) return rc;
+        c->graph_valid = false;
     }
     int32_t ns = (int32_t)cells.size();
     if (ns > c->slots_cap || !c->Y.counts) {
@@ -349,6 +359,7 @@ int ensure_tallies(gbmc_ctx* c, const std::vector<int32_t>& cells, cudaStream_t 
         c->graph_valid = false;
     }
     CK(cudaMemsetAsync(c->Y.flux, 0, sizeof(double) * (size_t)(tot ? tot : 1), s));
+    if (c->Y.absrate) CK(cudaMemsetAsync(c->Y.absrate, 0, sizeof(double) * (size_t)c->flux_cap, s));
     CK(cudaMemsetAsync(c->Y.counts, 0, sizeof(unsigned long long) * c->slots_cap * GBMC_NSCAL, s));
     CK(cudaMemsetAsync(c->Y.weights, 0, sizeof(double) * c->slots_cap * GBMC_NSCAL, s));
     c->slot_cells = cells;
@@ -721,7 +732,7 @@ int gbmc_destroy(gbmc_ctx* c) {
     Outcomes& O = c->O;
     dfree(O.ncoll); dfree(O.status); dfree(O.nflt); dfree(O.ndraw);
     dfree(O.E); dfree(O.x); dfree(O.y); dfree(O.z);
-    dfree(c->Y.flux); dfree(c->Y.counts); dfree(c->Y.weights);
+    dfree(c->Y.flux); dfree(c->Y.counts); dfree(c->Y.weights); dfree(c->Y.absrate);
     dfree(c->d_grid_off); dfree(c->d_e64); dfree(c->d_s64); dfree(c->d_es32);
     dfree(c->d_fabs); dfree(c->d_fabs32); dfree(c->d_awr);
     dfree(c->d_nx64); dfree(c->d_nx32); dfree(c->d_idx64); dfree(c->d_idx32); dfree(c->d_bw32);
@@ -965,6 +976,7 @@ int gbmc_reset_tallies(gbmc_ctx* c, void* stream) {
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     if (c->Y.flux) CK(cudaMemsetAsync(c->Y.flux, 0, sizeof(double) * c->flux_cap, s));
+    if (c->Y.absrate) CK(cudaMemsetAsync(c->Y.absrate, 0, sizeof(double) * c->flux_cap, s));
     if (c->Y.counts) {
         CK(cudaMemsetAsync(c->Y.counts, 0, sizeof(unsigned long long) * c->slots_cap * GBMC_NSCAL, s));
         CK(cudaMemsetAsync(c->Y.weights, 0, sizeof(double) * c->slots_cap * GBMC_NSCAL, s));
@@ -1216,6 +1228,40 @@ int gbmc_read_tallies(gbmc_ctx* c, int32_t slot, double* flux, int64_t n_flux, i
     if (weights)
         CK(cudaMemcpy(weights, c->Y.weights + (size_t)slot * GBMC_NSCAL,
                       sizeof(double) * GBMC_NSCAL, cudaMemcpyDeviceToHost));
+    return GBMC_OK;
+}
+
+int gbmc_set_reaction_tally(gbmc_ctx* c, int32_t on) {
+    if (!c) return GBMC_ERR_INVALID_ARG;
+    if (on != 0 && on != 1) return fail(c, GBMC_ERR_INVALID_ARG, "on must be 0 or 1");
+    int rc = set_device(c);
+    if (rc) return rc;
+    if ((bool)on == c->rr_on) return GBMC_OK;
+    c->rr_on = on != 0;
+    c->graph_valid = false;
+    if (!c->rr_on) {
+        dfree(c->Y.absrate);
+        c->Y.absrate = nullptr;
+    } else if (c->Y.flux) {
+        if ((rc = dalloc(c, &c->Y.absrate, (size_t)c->flux_cap))) return rc;
+        CK(cudaMemset(c->Y.absrate, 0, sizeof(double) * (size_t)c->flux_cap));
+    }
+    return GBMC_OK;
+}
+
+int gbmc_read_reaction_tally(gbmc_ctx* c, int32_t slot, double* absrate, int64_t n) {
+    if (!c || !absrate) return GBMC_ERR_INVALID_ARG;
+    int rc = set_device(c);
+    if (rc) return rc;
+    if (!c->rr_on || !c->Y.absrate)
+        return fail(c, GBMC_ERR_NOT_INITIALIZED, "the absorption-rate tally is off or has not run");
+    if ((rc = read_ctl(c))) return rc;
+    if (slot < 0 || slot >= (int32_t)c->slot_cells.size())
+        return fail(c, GBMC_ERR_INVALID_ARG, "tally slot %d out of range", slot);
+    int64_t nf = (int64_t)c->slot_cells[slot] * c->n_bins;
+    if (n != nf) return fail(c, GBMC_ERR_INVALID_ARG, "n must be %lld", (long long)nf);
+    CK(cudaMemcpy(absrate, c->Y.absrate + c->slot_flux_off[slot], sizeof(double) * nf,
+                  cudaMemcpyDeviceToHost));
     return GBMC_OK;
 }
 

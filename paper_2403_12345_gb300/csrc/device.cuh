@@ -134,6 +134,7 @@ struct Tallies {
     double* flux;
     unsigned long long* counts;   // [slot * GBMC_NSCAL + s]
     double* weights;
+    double* absrate;              // track-length absorption rate, laid out as flux (NULL: off)
 };
 
 // Device-resident event-loop state.

@@ -498,6 +498,16 @@ __device__ __forceinline__ int32_t cell_of(const gbmc_geometry& g, const Particl
                                        : 0;
 }
 
+// Track-length scores of a segment of length d in the particle's (cell,
+// energy bin): flux w d and, when on, the absorption rate (w d) Sigma_a.
+__device__ __forceinline__ void score_segment(const Params& P, const DevProblem& pr,
+                                              const Particle& pt, double d) {
+    int64_t k = pr.flux_off + (int64_t)cell_of(pr.g, pt) * P.T.n_bins + energy_bin(P.T, pt.E);
+    double wd = pt.wgt * d;
+    atomicAdd(&P.Y.flux[k], wd);
+    if (P.Y.absrate) atomicAdd(&P.Y.absrate[k], wd * pt.sa);
+}
+
 // One flight (advance event): sample the distance to collision, find the
 // nearest surface of the current cell (ties: cylinder, x, y, z) and compare.
 // Returns true for a collision, leaving the particle where it is: the move
@@ -589,9 +599,7 @@ __device__ __forceinline__ bool fly(const Params& P, const DevProblem& pr, Parti
         pt.x = pt.x + dbnd * pt.u;
         pt.y = pt.y + dbnd * pt.v;
         pt.z = pt.z + dbnd * pt.w;
-        int32_t bin = energy_bin(P.T, pt.E);
-        atomicAdd(&P.Y.flux[pr.flux_off + (int64_t)cell_of(g, pt) * P.T.n_bins + bin],
-                  pt.wgt * dbnd);
+        score_segment(P, pr, pt, dbnd);
     }
     return collide;
 }
@@ -604,9 +612,7 @@ __device__ __forceinline__ void finish_flight(const Params& P, const DevProblem&
     pt.x = pt.x + d * pt.u;
     pt.y = pt.y + d * pt.v;
     pt.z = pt.z + d * pt.w;
-    int32_t bin = energy_bin(P.T, pt.E);
-    atomicAdd(&P.Y.flux[pr.flux_off + (int64_t)cell_of(pr.g, pt) * P.T.n_bins + bin],
-              pt.wgt * d);
+    score_segment(P, pr, pt, d);
 }
 
 // Weight-window check at the particle's (cell, energy bin), problem slot 0

@@ -39,7 +39,7 @@ EXPORTS = ["gbmc_default_options", "gbmc_create", "gbmc_destroy", "gbmc_last_err
            "gbmc_get_importance_net", "gbmc_mlp_forward", "gbmc_mlp_gradient", "gbmc_mlp_train",
            "gbmc_mesh_features", "gbmc_weight_windows_from_net", "gbmc_importance_record",
            "gbmc_importance_accumulate", "gbmc_importance_training_set",
-           "gbmc_get_weight_windows"]
+           "gbmc_get_weight_windows", "gbmc_set_reaction_tally", "gbmc_read_reaction_tally"]
 MLP_HIDDEN = 64
 MLP_NPARAM = 4545
 NOALLOC_MAX_QUERIES = 1 << 20
@@ -120,6 +120,8 @@ def lib():
         L.gbmc_run_problems.argtypes = [vp, C.c_int32, _P(Problem), vp]
         L.gbmc_read_tallies.argtypes = [vp, C.c_int32, _P(C.c_double), C.c_int64,
                                         _P(C.c_int64), _P(C.c_double)]
+        L.gbmc_set_reaction_tally.argtypes = [vp, C.c_int32]
+        L.gbmc_read_reaction_tally.argtypes = [vp, C.c_int32, _P(C.c_double), C.c_int64]
         L.gbmc_read_outcomes.argtypes = [vp, C.c_int32, C.c_int64, C.c_int64, _P(C.c_int32),
                                          _P(C.c_int8), _P(C.c_int32), _P(C.c_uint32),
                                          _P(C.c_double), _P(C.c_double), _P(C.c_double),
@@ -417,6 +419,15 @@ class Context:
         self._ck(lib().gbmc_read_tallies(self._h, int(slot), _p(flux, C.c_double), flux.size,
                                          _p(counts, C.c_int64), _p(weights, C.c_double)))
         return flux, counts, weights
+
+    def set_reaction_tally(self, on: bool = True):
+        self._ck(lib().gbmc_set_reaction_tally(self._h, 1 if on else 0))
+
+    def read_reaction_tally(self, slot: int = 0):
+        """Track-length absorption rate sum w d Sigma_a [cells, bins] of a slot."""
+        out = np.zeros((self._cells[slot], self.n_bins))
+        self._ck(lib().gbmc_read_reaction_tally(self._h, int(slot), _p(out, C.c_double), out.size))
+        return out
 
     def read_outcomes(self, slot: int = 0, first: int = 0, n: int = 0):
         o = dict(n_coll=np.zeros(n, np.int32), status=np.zeros(n, np.int8),
