@@ -336,7 +336,9 @@ int gbmc_set_importance_net(gbmc_ctx *ctx, const uint16_t *bf16_params, int32_t 
 int gbmc_get_importance_net(gbmc_ctx *ctx, uint16_t *bf16_params, int32_t n_params);
 
 /* Network outputs for n feature rows: DEVICE pointers d_feat [n][4]
- * (float), d_out [n] (float).  Asynchronous on `stream`. */
+ * (float), d_out [n] (float).  The 64 x 64 layer runs on the tensor cores
+ * (tcgen05, TMEM accumulator).  Synchronizes with `stream`; TIMEOUT if a
+ * bounded wait for the tensor cores gave up (d_out then incomplete). */
 int gbmc_mlp_forward(gbmc_ctx *ctx, const float *d_feat, int64_t n, float *d_out, void *stream);
 
 /* Loss L = sum_s w_s (out_s - y_s)^2 / sum_s w_s over n rows (DEVICE

@@ -138,6 +138,7 @@ struct gbmc_ctx {
     float *d_net_p = nullptr, *d_net_m = nullptr, *d_net_v = nullptr, *d_net_g = nullptr;
     float *d_net_scratch = nullptr;   // [0]: 1 / sum of weights, [1]: loss
     __nv_bfloat16* d_net_w = nullptr;
+    int* d_mlp_err = nullptr;        // set by the tensor-core forward if a wait gave up
     int32_t net_step = 0;
     double feat_offset[4] = {0, 0, 0, 0}, feat_scale[4] = {1, 1, 1, 1};
     float *d_mesh_feat = nullptr, *d_mesh_out = nullptr;
@@ -742,6 +743,7 @@ int gbmc_destroy(gbmc_ctx* c) {
     dfree(c->d_ww); dfree(c->d_child);
     dfree(c->d_net_p); dfree(c->d_net_m); dfree(c->d_net_v); dfree(c->d_net_g);
     dfree(c->d_net_scratch); dfree(c->d_net_w); dfree(c->d_mesh_feat); dfree(c->d_mesh_out);
+    dfree(c->d_mlp_err);
     dfree(c->d_imp_mesh); dfree(c->d_imp_gidx); dfree(c->d_imp_cnt); dfree(c->d_imp_scr);
     dfree(c->d_imp_cellsum);
     if (c->d_cum) { cudaDeviceSynchronize(); cudaFree(c->d_cum); }
@@ -1420,6 +1422,19 @@ int need_net(gbmc_ctx* c) {
     return GBMC_OK;
 }
 
+// Waits for stream s and reports (and clears) a tensor-core wait that gave
+// up in the network forward.
+int mlp_status(gbmc_ctx* c, cudaStream_t s) {
+    CK(cudaStreamSynchronize(s));
+    int flag = 0;
+    CK(cudaMemcpy(&flag, c->d_mlp_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        CK(cudaMemset(c->d_mlp_err, 0, sizeof(int)));
+        return fail(c, GBMC_ERR_TIMEOUT, "network forward: tensor-core wait gave up");
+    }
+    return GBMC_OK;
+}
+
 int ensure_mesh(gbmc_ctx* c, int64_t n) {
     if (n <= c->mesh_cap) return GBMC_OK;
     int rc = dalloc(c, &c->d_mesh_feat, (size_t)n * 4);
@@ -1470,6 +1485,10 @@ extern "C" int gbmc_set_importance_net(gbmc_ctx* c, const uint16_t* bf16_params,
                      (size_t)kMlpParams)))
         return rc;
     if (!c->d_net_scratch && (rc = dalloc(c, &c->d_net_scratch, 2))) return rc;
+    if (!c->d_mlp_err) {
+        if ((rc = dalloc(c, &c->d_mlp_err, 1))) return rc;
+        CK(cudaMemset(c->d_mlp_err, 0, sizeof(int)));
+    }
     for (int i = 0; i < 4; ++i) {
         c->feat_offset[i] = feat_offset[i];
         c->feat_scale[i] = feat_scale[i];
@@ -1495,9 +1514,10 @@ extern "C" int gbmc_mlp_forward(gbmc_ctx* c, const float* d_feat, int64_t n, flo
     int rc = need_net(c);
     if (rc) return rc;
     if ((rc = set_device(c))) return rc;
-    cudaError_t e = mlp_forward(c->d_net_w, d_feat, n, d_out, c->sms, (cudaStream_t)stream);
+    cudaError_t e = mlp_forward(c->d_net_w, d_feat, n, d_out, c->d_mlp_err, c->sms,
+                                (cudaStream_t)stream);
     if (e != cudaSuccess) return fail(c, GBMC_ERR_CUDA, "network forward: %s", cudaGetErrorString(e));
-    return GBMC_OK;
+    return mlp_status(c, (cudaStream_t)stream);
 }
 
 extern "C" int gbmc_mlp_gradient(gbmc_ctx* c, const float* d_feat, const float* d_target,
@@ -1585,9 +1605,9 @@ extern "C" int gbmc_weight_windows_from_net(gbmc_ctx* c, const gbmc_geometry* g,
     }
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = mesh_windows(M, c->d_net_w, c->d_mesh_feat, c->d_mesh_out, survival, src,
-                                 c->d_ww, c->sms, s);
+                                 c->d_ww, c->d_mlp_err, c->sms, s);
     if (e != cudaSuccess) return fail(c, GBMC_ERR_CUDA, "windows from network: %s", cudaGetErrorString(e));
-    CK(cudaStreamSynchronize(s));
+    if ((rc = mlp_status(c, s))) return rc;
     c->ww_on = true;
     c->ww_cells = M.n_cells;
     c->ww_ratio = ratio;

@@ -1,11 +1,17 @@
 // Importance network for weight windows: a 4 -> 64 -> 64 -> 1 MLP (ReLU)
 // with BF16 weights and FP32 accumulation, evaluated and trained by these
-// kernels.  The 64 x 64 layer runs on the tensor cores (mma.sync m16n8k16,
-// bf16 in, f32 accumulate): each warp carries 16 samples through the whole
-// network in registers -- the accumulator tiles of one layer are, element
-// for element, the A operand of the next, so activations never leave the
-// registers.  The 4-input and 1-output layers are too narrow for the tensor
-// cores and run on the FP32 pipe.
+// kernels.  The 4-input and 1-output layers are too narrow for the tensor
+// cores and run on the FP32 pipe; the 64 x 64 layer runs on the tensor cores:
+//
+// - inference (k_mlp_forward_tc): fifth-generation tensor cores.  A CTA of
+//   four warps takes 128 samples at a time: layer 1 writes relu(z1) as BF16
+//   into shared memory in the canonical K-major layout, one thread issues
+//   four tcgen05.mma (M 128, N 64, K 16 each) into a TMEM accumulator and
+//   commits them to an mbarrier, and each warp reads its 32 TMEM lanes
+//   (rows) back for bias, ReLU and layer 3;
+// - training (k_mlp_grad): mma.sync m16n8k16, each warp carrying 16 samples
+//   through forward and backward in registers (the accumulator fragments of
+//   one layer are the A fragments of the next).
 //
 // Parameter layout (also the C ABI's): W1[64][4], b1[64], W2[64][64]
 // (row = output unit), b2[64], W3[64], b3.
@@ -155,25 +161,179 @@ __device__ __forceinline__ void load_features(const float* __restrict__ feat, in
     }
 }
 
-__global__ void __launch_bounds__(256) k_mlp_forward(const __nv_bfloat16* __restrict__ w,
-                                                     const float* __restrict__ feat, int64_t n,
-                                                     float* __restrict__ out) {
-    __shared__ SmemNet S;
-    load_net(S, w);
-    int lane = threadIdx.x & 31;
-    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t base = warp * 16; base < n; base += nw * 16) {
-        Tile16 T;
-        load_features(feat, n, base, T);
-        forward16(S, T);
-        if ((lane & 3) == 0) {
-            int g = lane >> 2;
-            if (base + g < n) out[base + g] = T.out[0];
-            if (base + g + 8 < n) out[base + g + 8] = T.out[1];
-        }
-    }
+// ---------------------------------------------------------------- tcgen05 forward
+// Shared-memory matrix descriptor (tcgen05): start address, leading byte
+// offset (between core matrices along K), stride byte offset (between
+// 8-row groups along M or N), all in 16-byte units; descriptor version 1;
+// no swizzle.  A core matrix is 8 rows x 16 bytes, rows 16 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) |
+           ((uint64_t)(sbo >> 4) << 32) | (1ull << 46);
 }
+
+// Instruction descriptor, kind::f16: D f32, A and B bf16, both K-major,
+// N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t kTcM = 128, kTcN = 64;
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((kTcN >> 3) << 17) |
+                              ((kTcM >> 4) << 24);
+constexpr uint32_t kTcCols = 64;           // TMEM columns: the 128 x 64 f32 accumulator
+constexpr uint32_t kTileBytes = 128 * 64 * 2;   // A: 128 rows x 64 bf16
+constexpr uint32_t kWBytes = 64 * 64 * 2;       // B: W2, 64 rows (out) x 64 bf16 (in)
+constexpr uint32_t kTcSpin = 1u << 22;     // mbarrier polls before giving up
+
+struct TcNet {
+    float W1[H * 4], b1[H], b2[H], W3[H], b3;
+};
+constexpr size_t kBarOff = (kTileBytes + kWBytes + sizeof(TcNet) + 7) & ~(size_t)7;
+
+// Byte offset of element (row, k) of a 64-wide K-major bf16 operand in the
+// canonical no-swizzle layout with K core matrices 128 bytes apart and row
+// groups 1024 bytes apart.
+__device__ __forceinline__ uint32_t kmajor_off(uint32_t row, uint32_t k) {
+    return (row >> 3) * 1024u + (k >> 3) * 128u + (row & 7u) * 16u + (k & 7u) * 2u;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Polls the mbarrier for the completion of `phase`, at most kTcSpin times.
+__device__ __forceinline__ bool wait_phase(uint64_t* mbar, uint32_t phase) {
+    uint32_t done = 0;
+    for (uint32_t spin = 0; spin < kTcSpin && !done; ++spin)
+        asm volatile(
+            "{\n.reg .pred P;\nmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, P;\n}\n"
+            : "=r"(done) : "r"(smem_u32(mbar)), "r"(phase) : "memory");
+    return done != 0;
+}
+
+__global__ void __launch_bounds__(128) k_mlp_forward_tc(const __nv_bfloat16* __restrict__ w,
+                                                        const float* __restrict__ feat, int64_t n,
+                                                        float* __restrict__ out,
+                                                        int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char* A = sm;                       // 16 KB
+    unsigned char* B = sm + kTileBytes;          // 8 KB
+    TcNet& S = *reinterpret_cast<TcNet*>(sm + kTileBytes + kWBytes);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + kBarOff);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // parameters: W2 into the B operand layout, the narrow layers as fp32
+    const __nv_bfloat16* W1 = w;
+    const __nv_bfloat16* b1 = W1 + H * 4;
+    const __nv_bfloat16* W2 = b1 + H;
+    const __nv_bfloat16* b2 = W2 + H * H;
+    const __nv_bfloat16* W3 = b2 + H;
+    for (int k = tid; k < H * H; k += blockDim.x)
+        *reinterpret_cast<__nv_bfloat16*>(B + kmajor_off(k / H, k % H)) = W2[k];
+    for (int k = tid; k < H * 4; k += blockDim.x) S.W1[k] = __bfloat162float(W1[k]);
+    for (int k = tid; k < H; k += blockDim.x) {
+        S.b1[k] = __bfloat162float(b1[k]);
+        S.b2[k] = __bfloat162float(b2[k]);
+        S.W3[k] = __bfloat162float(W3[k]);
+    }
+    if (tid == 0) {
+        S.b3 = __bfloat162float(W3[H]);
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
+                     ::"r"(smem_u32(tslot)), "r"(kTcCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = *tslot;
+    const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
+    uint32_t phase = 0;
+    bool ok = true;
+
+    for (int64_t base = (int64_t)blockIdx.x * 128; base < n && ok; base += (int64_t)gridDim.x * 128) {
+        // layer 1 (fp32) for row tid; relu(z1) as bf16 into the A tile
+        int64_t row = base + tid;
+        float x[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) x[i] = row < n ? feat[row * 4 + i] : 0.f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            uint32_t pk[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                float z[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    int u = 8 * j + 2 * e + h;
+                    float s = S.b1[u];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) s += S.W1[u * 4 + i] * x[i];
+                    z[h] = fmaxf(s, 0.f);
+                }
+                pk[e] = pack2(z[0], z[1]);
+            }
+            *reinterpret_cast<uint4*>(A + kmajor_off(tid, 8 * j)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll
+            for (uint32_t s = 0; s < 4; ++s) {
+                uint64_t ad = smem_desc(a0 + 256u * s, 128u, 1024u);
+                uint64_t bd = smem_desc(b0 + 256u * s, 128u, 1024u);
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                    ::"r"(tmem), "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(s));
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                ::"r"(smem_u32(mbar)) : "memory");
+        }
+        // wait for the products (bounded; the whole CTA gives up together)
+        if (__syncthreads_or(!wait_phase(mbar, phase))) {
+            if (tid == 0) atomicExch(err, 1);
+            ok = false;
+            wait_phase(mbar, phase);   // once more (bounded) for the products in flight
+            break;
+        }
+        phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        // this warp's 32 accumulator rows: lane = row, 64 columns
+        float acc[64];
+        uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            uint32_t* r = reinterpret_cast<uint32_t*>(acc + 16 * c);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,"
+                "%12,%13,%14,%15}, [%16];\n"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                  "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                  "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                : "r"(taddr + 16u * c));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        // bias, relu, layer 3 (fp32)
+        float o = S.b3;
+#pragma unroll
+        for (int u = 0; u < 64; ++u) o += S.W3[u] * fmaxf(acc[u] + S.b2[u], 0.f);
+        int64_t r = base + 32 * warp + lane;
+        if (r < n) out[r] = o;
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        __syncthreads();   // the A tile and the accumulator are free again
+    }
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                     "r"(kTcCols));
+}
+
+constexpr size_t kTcSmem = kBarOff + 16;   // + the mbarrier and the TMEM address slot
 
 // Gradient of L = sum_s w_s (out_s - y_s)^2 / sum_s w_s, accumulated into
 // grad (fp32, parameter layout) and the loss into *loss.  inv_wsum = 1 /
@@ -420,11 +580,20 @@ __global__ void k_windows(const float* __restrict__ out, int64_t n, int64_t src,
 }  // namespace
 
 cudaError_t mlp_forward(const __nv_bfloat16* w, const float* feat, int64_t n, float* out,
-                        int sms, cudaStream_t s) {
+                        int* err, int sms, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    int64_t warps = (n + 15) / 16;
-    int blocks = (int)std::min<int64_t>((warps + kWarps - 1) / kWarps, (int64_t)sms * 8);
-    k_mlp_forward<<<blocks, 32 * kWarps, 0, s>>>(w, feat, n, out);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_mlp_forward_tc,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kTcSmem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    // at most 4 CTAs (4 x 64 TMEM columns) per SM
+    int64_t tiles = (n + 127) / 128;
+    int blocks = (int)std::min<int64_t>(tiles, (int64_t)sms * 4);
+    k_mlp_forward_tc<<<blocks, 128, kTcSmem, s>>>(w, feat, n, out, err);
     return cudaGetLastError();
 }
 
@@ -465,11 +634,12 @@ cudaError_t mesh_features(const MeshSpec& M, float* feat, int sms, cudaStream_t 
 }
 
 cudaError_t mesh_windows(const MeshSpec& M, const __nv_bfloat16* w, float* feat, float* out,
-                         double survival, int64_t src, double* lower, int sms, cudaStream_t s) {
+                         double survival, int64_t src, double* lower, int* err, int sms,
+                         cudaStream_t s) {
     int64_t n = (int64_t)M.n_cells * M.n_bins;
     int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 4);
     k_mesh_features<<<blocks, 256, 0, s>>>(M, feat);
-    cudaError_t e = mlp_forward(w, feat, n, out, sms, s);
+    cudaError_t e = mlp_forward(w, feat, n, out, err, sms, s);
     if (e != cudaSuccess) return e;
     k_windows<<<blocks, 256, 0, s>>>(out, n, src, survival, lower);
     return cudaGetLastError();

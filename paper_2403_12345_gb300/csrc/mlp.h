@@ -20,9 +20,11 @@ struct MeshSpec {
     double offset[4], scale[4];
 };
 
-// Network output for n feature rows (feat [n][4]) with BF16 weights w.
+// Network output for n feature rows (feat [n][4]) with BF16 weights w, on
+// the tensor cores; *err (device) is set to 1 if a wait for the tensor cores
+// gave up.
 cudaError_t mlp_forward(const __nv_bfloat16* w, const float* feat, int64_t n, float* out,
-                        int sms, cudaStream_t s);
+                        int* err, int sms, cudaStream_t s);
 
 // Adds the gradient of the weighted mean squared error to grad and the loss
 // to *loss (both device, fp32); scratch_inv receives 1 / sum of weights.
@@ -37,7 +39,8 @@ cudaError_t mlp_adam(float* p, float* m, float* v, float* grad, __nv_bfloat16* w
 // Window lower bounds on the mesh from the network (features and outputs go
 // through feat [n][4] and out [n]); src is the source's mesh index.
 cudaError_t mesh_windows(const MeshSpec& M, const __nv_bfloat16* w, float* feat, float* out,
-                         double survival, int64_t src, double* lower, int sms, cudaStream_t s);
+                         double survival, int64_t src, double* lower, int* err, int sms,
+                         cudaStream_t s);
 
 // Mesh features only.
 cudaError_t mesh_features(const MeshSpec& M, float* feat, int sms, cudaStream_t s);

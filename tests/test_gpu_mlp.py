@@ -61,6 +61,43 @@ def test_forward_and_gradient_match_oracle():
         ctx.close()
 
 
+def _emulate(pb, x):
+    """The forward as the kernels form it: layer 1 in binary32 (no fused
+    multiply-add), relu(z1) rounded to BF16 for the tensor cores, layers 2
+    and 3 then exact (binary64) -- the tensor cores' binary32 accumulation
+    of 64 products differs from it by a few ulp."""
+    H = gbmc.MLP_HIDDEN
+    p = imp.from_bf16(pb)
+    W1, b1 = p[:4 * H].reshape(H, 4), p[4 * H:5 * H]
+    W2, b2 = p[5 * H:5 * H + H * H].reshape(H, H), p[5 * H + H * H:6 * H + H * H]
+    W3, b3 = p[6 * H + H * H:7 * H + H * H], p[7 * H + H * H]
+    z1 = np.repeat(b1[None, :], len(x), 0).astype(np.float32)
+    for i in range(4):
+        z1 = (z1 + (W1[:, i][None, :] * x[:, i:i + 1]).astype(np.float32)).astype(np.float32)
+    h1 = imp.from_bf16(imp.to_bf16(np.maximum(z1, 0))).astype(np.float64)
+    z2 = h1 @ W2.astype(np.float64).T + b2
+    return np.maximum(z2, 0) @ W3.astype(np.float64) + float(b3)
+
+
+def test_forward_matches_bf16_emulation():
+    # a tight check of the tensor-core layer (operand layouts, every row of
+    # the 128-row tiles and a ragged last tile)
+    import torch
+    rng = np.random.default_rng(17)
+    pb = imp.to_bf16(rng.normal(0, 0.3, gbmc.MLP_NPARAM))
+    n = 128 * 37 + 19
+    x = rng.uniform(-1, 1, (n, 4)).astype(np.float32)
+    ctx, _ = _ctx(pb)
+    try:
+        out = torch.empty(n, dtype=torch.float32, device="cuda")
+        ctx.mlp_forward(torch.tensor(x, device="cuda"), out)
+        o = out.cpu().numpy().astype(np.float64)
+    finally:
+        ctx.close()
+    ref = _emulate(pb, x)
+    assert np.abs(o - ref).max() <= 1e-4 * (np.abs(ref).max() + 1.0), np.abs(o - ref).max()
+
+
 def test_training_fits_and_gradients_stay_exact():
     import torch
     rng = np.random.default_rng(4)
