@@ -319,6 +319,78 @@ def run_stress(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def run_streams(args, prob, rank, world, local):
+    """K independent event loops on K concurrent CUDA streams (the paper's
+    several ranks per GPU, Sec. 2 "GPU Streams"): each context runs a share
+    of the step's work -- whole problems balanced by size, or for a single
+    problem an id range -- and a step ends when all K have finished."""
+    import torch
+    import torch.distributed as dist
+    from paper_2403_12345_gb300 import gbmc, replicas
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    K = args.streams
+    opts = dict(precision=args.precision, sort=args.sort)
+    if args.max_in_flight:
+        opts["max_in_flight"] = args.max_in_flight
+    if args.blocks_per_sm:
+        opts["blocks_per_sm"] = args.blocks_per_sm
+    ctxs = [gbmc.Context(local, **opts) for _ in range(K)]
+    for c in ctxs:
+        c.load(prob, (args.precision,))
+    geoms = [gbmc.geometry_from(g) for g in prob.geoms]
+    counts = [args.particles or n for n in prob.n_particles]
+    by = "ids" if len(geoms) == 1 else "problems"
+
+    def shares(batch):
+        probs = [gbmc.problem(geoms[k], prob.seed, counts[k], batch=batch * world + rank,
+                              problem_index=k) for k in range(len(geoms))]
+        return [replicas.shard_problems(probs, r, K, by=by)[0] for r in range(K)]
+
+    streams = [torch.cuda.Stream() for _ in range(K)]
+    main = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step(batch):
+        go = torch.cuda.Event()
+        go.record(main)
+        done = []
+        for c, st, sh in zip(ctxs, streams, shares(batch)):
+            st.wait_event(go)
+            if sh:
+                c.run_problems(sh, st)
+            e = torch.cuda.Event()
+            e.record(st)
+            done.append(e)
+        for e in done:
+            main.wait_event(e)
+
+    for w in range(args.warmup):
+        step(10_000 + w)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms, clocks = _timed(step, args.steps, flush, main, local)
+    tot_ms = _max_over_ranks(sum(ms), world)
+    npart = sum(counts)
+    value = npart * args.steps * world / (tot_ms * 1e-3)
+    if rank == 0:
+        cfg = config_of(args, prob)
+        cfg["parallelism"] = f"replicas{args.gpus} x {K} concurrent event loops ({by} split)"
+        print(json.dumps({
+            "metric": "particles/s", "value": value, "unit": "particles/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == 1 else "f64", "data": "synthetic", "config": cfg,
+            "streams": K, "e2e": None, "roofline": None, "cpu_baseline": None, "clocks": clocks,
+            "gpu_launches": None}), flush=True)
+    for c in ctxs:
+        c.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def run_windows(args, prob, rank, world, local):
     """Deep-penetration slab: learned weight windows against analog.  One step
     = one batch with the learned windows; the figure of merit FOM = 1/(R^2 T)
@@ -415,6 +487,9 @@ def main():
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
     ap.add_argument("--ref-step-s", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--streams", type=int, default=1,
+                    help="K > 1: K independent event loops (contexts) on K concurrent streams, "
+                         "the work split between them, instead of one batched launch")
     ap.add_argument("--autotune", type=int, default=-1,
                     help="1: autotune launch settings before timing (default: config 4 only)")
     args = ap.parse_args()
@@ -436,6 +511,9 @@ def main():
         return
     if args.config == 5:
         run_windows(args, prob, rank, world, local)
+        return
+    if args.streams > 1:
+        run_streams(args, prob, rank, world, local)
         return
 
     import torch
