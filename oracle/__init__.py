@@ -42,6 +42,9 @@ class _Problem(C.Structure):
         ("layer_dx", C.c_double), ("n_first", C.c_int32), ("mat_a", C.c_int32),
         ("mat_b", C.c_int32), ("ww_lower", _P(C.c_double)), ("ww_ratio", C.c_double),
         ("ww_survival", C.c_double), ("ww_max_split", C.c_int32),
+        ("nu", _P(C.c_double)), ("f_fis", _P(C.c_double)), ("k_norm", C.c_double),
+        ("max_sites", C.c_int32), ("bank", _P(C.c_double)), ("bank_n", C.c_int64),
+        ("bank_total", C.c_int64),
     ]
 
 
@@ -51,6 +54,7 @@ class _Result(C.Structure):
         ("n_draws", _P(C.c_uint32)), ("E", _P(C.c_double)), ("x", _P(C.c_double)),
         ("y", _P(C.c_double)), ("z", _P(C.c_double)), ("flux", _P(C.c_double)),
         ("absrate", _P(C.c_double)), ("counts", _P(C.c_int64)), ("weights", _P(C.c_double)),
+        ("sites", _P(C.c_double)), ("n_sites", _P(C.c_int32)),
     ]
 
 
@@ -135,7 +139,7 @@ def rotate(u, v, w, mu, cphi, sphi):
 class _Bound:
     """Keeps the numpy arrays alive while the C structure points at them."""
 
-    def __init__(self, prob, geom_index: int = 0, precision=None, ww=None):
+    def __init__(self, prob, geom_index: int = 0, precision=None, ww=None, eigen=None):
         g = prob.geoms[geom_index]
         self.arrs = dict(
             grid_off=np.ascontiguousarray(prob.grid_off, dtype=np.int64),
@@ -175,6 +179,22 @@ class _Bound:
                 raise ValueError("weight-window table must be [n_cells, n_bins]")
             p.ww_lower = _ptr(self.ww, C.c_double)
             p.ww_ratio, p.ww_survival, p.ww_max_split = float(ratio), float(survival), int(max_split)
+        if eigen is not None:
+            self.nu = np.ascontiguousarray(eigen["nu"], dtype=np.float64)
+            self.ffis = np.ascontiguousarray(eigen["f_fis"], dtype=np.float64)
+            p.nu = _ptr(self.nu, C.c_double)
+            p.f_fis = _ptr(self.ffis, C.c_double)
+            p.k_norm = float(eigen.get("k_norm", 1.0))
+            p.max_sites = int(eigen.get("max_sites", 32))
+            bank = eigen.get("bank")
+            if bank is not None:
+                xyz, total = bank
+                self.bank = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+                if len(self.bank) < 1 or int(total) < 1:
+                    raise ValueError("empty source bank")
+                p.bank = _ptr(self.bank, C.c_double)
+                p.bank_n, p.bank_total = len(self.bank), int(total)
+                p.source = 3
         self.p = p
         self.n_cells = g.n_cells()
         self.n_bins = p.n_bins
@@ -203,14 +223,18 @@ def key_hi(problem_index: int, batch: int) -> int:
 
 
 def run(prob, seed: int, batch: int = 0, first_id: int = 0, n=None, geom_index: int = 0,
-        problem_index: int = 0, threads=None, precision=None, ww=None):
+        problem_index: int = 0, threads=None, precision=None, ww=None, eigen=None):
     """Histories [first_id, first_id + n) of one batch; returns a dict with
     per-particle outcomes, the flux tally [n_cells, n_bins], the track-length
     absorption-rate tally sum w d Sigma_a [n_cells, n_bins] and the scalars.
     ww = (lower [n_cells, n_bins], ratio, survival, max_split) turns on
     weight windows; split copies are transported depth first and scored in
-    the tallies (the outcomes are the primary histories')."""
-    b = _Bound(prob, geom_index, precision, ww)
+    the tallies (the outcomes are the primary histories').
+    eigen = dict(nu, f_fis, k_norm, max_sites[, bank=(xyz [m, 3], n_total)])
+    banks fission sites (k-eigenvalue mode; with `bank` the histories start
+    from it); the result then holds n_sites per history and `sites`, the
+    bank in history order."""
+    b = _Bound(prob, geom_index, precision, ww, eigen)
     if n is None:
         n = prob.n_particles[geom_index]
     n = int(n)
@@ -232,19 +256,30 @@ def run(prob, seed: int, batch: int = 0, first_id: int = 0, n=None, geom_index: 
     for k in ("E", "x", "y", "z", "flux", "absrate", "weights"):
         setattr(r, k, _ptr(out[k], C.c_double))
     r.counts = _ptr(out["counts"], C.c_int64)
+    if eigen is not None:
+        ms = int(b.p.max_sites)
+        raw = np.zeros((n, ms, 3))
+        out["n_sites"] = np.zeros(n, np.int32)
+        r.sites = _ptr(raw, C.c_double)
+        r.n_sites = _ptr(out["n_sites"], C.c_int32)
     rc = lib().or_run(C.byref(b.p), int(seed) & 0xFFFFFFFFFFFFFFFF,
                       key_hi(problem_index, batch), int(first_id), n, int(threads), C.byref(r))
     if rc == -2:
         raise RuntimeError("oracle split stack overflow (more than 2^24 pending copies)")
+    if rc == -3:
+        raise RuntimeError("a history banked more than max_sites fission sites")
+    if eigen is not None:
+        ns = out["n_sites"]
+        out["sites"] = np.concatenate([raw[k, :ns[k]] for k in range(n)]) if n else np.zeros((0, 3))
     if rc != 0:
         raise MemoryError("oracle run failed")
     return out
 
 
 def birth_state(prob, seed: int, id_: int, batch: int = 0, problem_index: int = 0,
-                geom_index: int = 0):
+                geom_index: int = 0, eigen=None):
     """(x, y, z, u, v, w, E), (i, j, inside, material) of a particle at birth."""
-    b = _Bound(prob, geom_index)
+    b = _Bound(prob, geom_index, eigen=eigen)
     st = np.zeros(7)
     cell = np.zeros(4, np.int32)
     L = lib()

@@ -530,10 +530,15 @@ static int32_t cell_of(const or_problem *P, const particle_t *p)
 /* ------------------------------------------------------------------------ */
 /* One history, birth to death.                                             */
 /* ------------------------------------------------------------------------ */
-static void birth(const or_problem *P, rng_t *r, particle_t *p)
+static void birth(const or_problem *P, rng_t *r, particle_t *p, int64_t id)
 {
     memset(p, 0, sizeof(*p));
-    if (P->source == 1) {
+    if (P->source == OR_SRC_BANK) {
+        int64_t s = id * P->bank_n / P->bank_total;
+        p->x = P->bank[3 * s];
+        p->y = P->bank[3 * s + 1];
+        p->z = P->bank[3 * s + 2];
+    } else if (P->source == 1) {
         double L = (double)P->n * P->pitch;
         p->x = rng_next(r) * L;
         p->y = rng_next(r) * L;
@@ -658,8 +663,15 @@ static void ww_check(const or_problem *P, particle_t *p, rng_t *r, stack_t_ *S, 
 
 /* One history from the given state until death; returns its final state and
  * the number of draws taken from its stream. */
+/* Fission sites of one history (k-eigenvalue mode). */
+typedef struct {
+    double *xyz;      /* [cap][3] */
+    int32_t n, cap;
+    int overflow;
+} sites_t;
+
 static void transport(const or_problem *P, const tables_t *T, rng_t *r, particle_t *pp,
-                      int need_lookup, acc_t *A, stack_t_ *S)
+                      int need_lookup, acc_t *A, stack_t_ *S, sites_t *B)
 {
     particle_t p = *pp;
     const int32_t nb = P->n_bins;
@@ -695,6 +707,22 @@ static void transport(const or_problem *P, const tables_t *T, rng_t *r, particle
             int32_t nuc = pick_nuclide(T, p.mat, p.E, target);
             p.n_coll += 1;
             score(A, OR_S_COLLISION, p.wgt);
+            if (P->nu) {
+                /* fission sites: expected w nu sigma_f / sigma_t / k_norm */
+                double xf = rng_next(r);
+                double y = (p.wgt * P->nu[nuc]) * P->f_fis[nuc] / P->k_norm + xf;
+                int32_t nb = (int32_t)floor(y);
+                for (int32_t q = 0; q < nb; ++q) {
+                    if (B->n >= B->cap) {
+                        B->overflow = 1;
+                        break;
+                    }
+                    B->xyz[3 * B->n] = p.x;
+                    B->xyz[3 * B->n + 1] = p.y;
+                    B->xyz[3 * B->n + 2] = p.z;
+                    B->n += 1;
+                }
+            }
             double xa = rng_next(r);
             if (xa < P->f_abs[nuc]) {
                 p.status = OR_STATUS_ABSORBED;
@@ -738,25 +766,25 @@ static void transport(const or_problem *P, const tables_t *T, rng_t *r, particle
 
 /* History `id` of the batch and, depth first, every copy its splits made. */
 static int history(const or_problem *P, const tables_t *T, uint64_t seed, uint64_t key_hi,
-                   int64_t id, acc_t *A, particle_t *out, uint32_t *ndraw)
+                   int64_t id, acc_t *A, particle_t *out, uint32_t *ndraw, sites_t *B)
 {
     rng_t r;
     rng_init(&r, seed, key_hi, (uint64_t)id);
     particle_t p;
-    birth(P, &r, &p);
+    birth(P, &r, &p, id);
     A->counts[OR_S_HISTORY] += 1;
     kadd(&A->ws[OR_S_HISTORY], &A->wc[OR_S_HISTORY], p.wgt);
     stack_t_ S = {NULL, 0, 0, 0};
-    transport(P, T, &r, &p, 1, A, &S);
+    transport(P, T, &r, &p, 1, A, &S, B);
     *out = p;
     *ndraw = r.j;
     while (S.n > 0 && !S.overflow) {
         child_t ch = S.v[--S.n];
         rng_t rc;
         rng_init(&rc, seed, key_hi, ch.hid);
-        transport(P, T, &rc, &ch.p, 1, A, &S);
+        transport(P, T, &rc, &ch.p, 1, A, &S, B);
     }
-    int bad = S.overflow;
+    int bad = S.overflow ? 1 : (B->overflow ? 3 : 0);
     free(S.v);
     return bad;
 }
@@ -769,7 +797,7 @@ void or_birth_state(const or_problem *P, uint64_t seed, uint64_t key_hi, int64_t
     rng_t r;
     rng_init(&r, seed, key_hi, (uint64_t)id);
     particle_t p;
-    birth(P, &r, &p);
+    birth(P, &r, &p, id);
     st[0] = p.x; st[1] = p.y; st[2] = p.z;
     st[3] = p.u; st[4] = p.v; st[5] = p.w; st[6] = p.E;
     cell[0] = p.i; cell[1] = p.j; cell[2] = p.inside; cell[3] = p.mat;
@@ -815,7 +843,14 @@ int or_run(const or_problem *P, uint64_t seed, uint64_t key_hi, int64_t first_id
 #endif
         particle_t p;
         uint32_t nd;
-        if (history(P, &T, seed, key_hi, first_id + k, &acc[t], &p, &nd)) overflow = 1;
+        sites_t B = {NULL, 0, 0, 0};
+        if (P->nu && R->sites) {
+            B.xyz = R->sites + (size_t)k * (size_t)P->max_sites * 3;
+            B.cap = P->max_sites;
+        }
+        int bad = history(P, &T, seed, key_hi, first_id + k, &acc[t], &p, &nd, &B);
+        if (bad) overflow = bad;
+        if (R->n_sites) R->n_sites[k] = B.n;
         if (R->n_coll) R->n_coll[k] = p.n_coll;
         if (R->status) R->status[k] = (int8_t)p.status;
         if (R->n_flights) R->n_flights[k] = p.n_flights;
@@ -866,7 +901,7 @@ int or_run(const or_problem *P, uint64_t seed, uint64_t key_hi, int64_t first_id
     free(acc);
     free(T.ef);
     free(T.sf);
-    return overflow ? -2 : 0;
+    return overflow == 3 ? -3 : (overflow ? -2 : 0);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -72,7 +72,20 @@ typedef struct {
     const double *ww_lower;   /* [n_cells * n_bins]; <= 0 means no window */
     double ww_ratio, ww_survival;
     int32_t ww_max_split;
+    /* k-eigenvalue (nu NULL: off).  At every collision in nuclide i the
+     * history banks floor(w nu_i f_fis_i / k_norm + xi) fission sites at the
+     * collision point (xi one draw, taken right after the nuclide choice), at
+     * most max_sites per history.  source 3 starts history id at site
+     * floor(id bank_n / bank_total) of the bank, energy E0, isotropic. */
+    const double *nu;         /* [n_nuc] mean neutrons per fission */
+    const double *f_fis;      /* [n_nuc] sigma_f / sigma_t */
+    double k_norm;
+    int32_t max_sites;
+    const double *bank;       /* [bank_n][3] */
+    int64_t bank_n, bank_total;
 } or_problem;
+
+#define OR_SRC_BANK 3
 
 typedef struct {
     int32_t *n_coll;      /* [n] */
@@ -85,6 +98,8 @@ typedef struct {
                            * (NULL: not scored), overwritten */
     int64_t *counts;      /* [OR_NSCAL], overwritten */
     double *weights;      /* [OR_NSCAL], overwritten */
+    double *sites;        /* [n][max_sites][3] fission sites in banking order (k-eigenvalue) */
+    int32_t *n_sites;     /* [n] sites banked by each history */
 } or_result;
 
 #endif

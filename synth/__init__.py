@@ -12,11 +12,11 @@ material, pointwise continuous-energy tables of 1e4-6e4 points, and a
 cylinder-in-box lattice.
 """
 from .problem import (Problem, Geometry, make_config, make_stress_lookup,
-                      make_tiny_problem, GEOM_INFINITE, GEOM_LATTICE, GEOM_SLAB,
+                      make_tiny_problem, make_eigen_lattice, GEOM_INFINITE, GEOM_LATTICE, GEOM_SLAB,
                       BC_VACUUM, BC_REFLECT, SRC_BOX, SRC_ORIGIN, SRC_SLAB_FACE,
                       BASE_SEED)
 
 __all__ = ["Problem", "Geometry", "make_config", "make_stress_lookup",
-           "make_tiny_problem", "GEOM_INFINITE", "GEOM_LATTICE", "GEOM_SLAB",
+           "make_tiny_problem", "make_eigen_lattice", "GEOM_INFINITE", "GEOM_LATTICE", "GEOM_SLAB",
            "BC_VACUUM", "BC_REFLECT", "SRC_BOX", "SRC_ORIGIN", "SRC_SLAB_FACE",
            "BASE_SEED"]

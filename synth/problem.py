@@ -94,6 +94,8 @@ class Problem:
     seed: int = BASE_SEED
     precision: int = 0            # 0 = binary64 tables, 1 = binary32 tables
     extra: dict = field(default_factory=dict)
+    nu: Optional[np.ndarray] = None     # float64 [n_nuc] mean neutrons per fission
+    f_fis: Optional[np.ndarray] = None  # float64 [n_nuc] sigma_f / sigma_t (<= f_abs)
 
     @property
     def n_nuc(self) -> int:
@@ -261,6 +263,25 @@ def make_config(k: int, n_particles: Optional[int] = None,
 # pilot analog run of the CPU oracle so that the analog far-face leakage
 # probability sits in [1e-6, 1e-4]: 41 of 4e6 histories (1.0e-5) at 0.1.
 SLAB_ABSORBER_SCALE = 0.1
+
+
+def make_eigen_lattice(n_particles: int = 1_000_000, grid_scale: float = 1.0,
+                       n_fissile: int = 40) -> Problem:
+    """k-eigenvalue workload: the 17x17 lattice of configuration 2 (same
+    tables and seeds) with the first n_fissile pin nuclides made fissile:
+    sigma_f = g f_abs sigma_t with g uniform on [0.7, 0.95] (fission is part
+    of absorption) and nu uniform on [2.4, 2.9]; with 40 of the 68 pin
+    nuclides the lattice is near critical (k about 1.00).  The source of the first
+    generation is the box source; later generations start from the bank."""
+    p = make_config(2, n_particles=n_particles, grid_scale=grid_scale)
+    rng = np.random.default_rng(BASE_SEED + 7)
+    nu = np.zeros(p.n_nuc)
+    ff = np.zeros(p.n_nuc)
+    nu[:n_fissile] = rng.uniform(2.4, 2.9, n_fissile)
+    ff[:n_fissile] = p.f_abs[:n_fissile] * rng.uniform(0.7, 0.95, n_fissile)
+    p.name = "lattice17-eigenvalue-fp64"
+    p.nu, p.f_fis = nu, ff
+    return p
 
 
 def make_stress_lookup(n_queries: int = 10_000_000, n_nuc: int = 281,
