@@ -61,6 +61,8 @@ extern "C" {
 #define GBMC_SRC_ORIGIN 0    /* point at the origin, isotropic */
 #define GBMC_SRC_BOX 1       /* uniform in the lattice box, isotropic */
 #define GBMC_SRC_SLAB_FACE 2 /* point on x = 0, isotropic over the inward hemisphere */
+#define GBMC_SRC_BANK 3      /* the fission bank set by gbmc_set_source_bank, isotropic
+                              * (lattice or infinite medium; k-eigenvalue mode) */
 
 /* ---- per-particle outcome status -------------------------------------- */
 #define GBMC_STATUS_ABSORBED 1
@@ -237,6 +239,39 @@ int gbmc_run_problems(gbmc_ctx *ctx, int32_t n_prob, const gbmc_problem *probs,
  * Returns GBMC_ERR_TIMEOUT / GBMC_ERR_DEVICE_FLAG if the run reported one. */
 int gbmc_read_tallies(gbmc_ctx *ctx, int32_t slot, double *flux, int64_t n_flux,
                       int64_t *counts, double *weights);
+
+/* k-eigenvalue mode (power iteration; the paper's production setting runs
+ * inactive then active generations, Sec. 2 "Tallying").  Fission data per
+ * nuclide: nu = mean neutrons per fission (>= 0) and f_fis = sigma_f /
+ * sigma_t (0 <= f_fis <= f_abs: fission is part of absorption).  HOST
+ * arrays of n_nuc (the loaded tables' count), copied.  Errors: INVALID_ARG,
+ * NOT_INITIALIZED before the tables. */
+int gbmc_load_fission(gbmc_ctx *ctx, int32_t n_nuc, const double *nu, const double *f_fis);
+
+/* Fission banking for the following runs (k_norm > 0; k_norm <= 0 turns it
+ * off): at every collision in nuclide i a history banks floor(w nu_i
+ * f_fis_i / k_norm + xi) sites at the collision point, xi being one more
+ * draw taken right after the nuclide choice; at most max_sites (1..255)
+ * per history (DEVICE_FLAG beyond).  After a run the sites form the bank in
+ * history order (run index, then banking order), whatever the order of the
+ * events.  Runs then take one problem and no weight windows (UNSUPPORTED).
+ * k_norm is normally the previous generation's k estimate, so the bank
+ * stays near the generation size; generation g's estimate is then
+ * k_g = (bank size / N) k_norm. */
+int gbmc_set_eigen(gbmc_ctx *ctx, double k_norm, int32_t max_sites);
+
+/* The last k-eigenvalue run's bank: *n_out = its size; if xyz != NULL the
+ * sites into HOST xyz[n_cap][3] (n_cap >= size, else INVALID_ARG).
+ * Synchronizes.  NOT_INITIALIZED before a k-eigenvalue run. */
+int gbmc_read_bank(gbmc_ctx *ctx, double *xyz, int64_t n_cap, int64_t *n_out);
+
+/* Source bank of the runs whose geometry has source GBMC_SRC_BANK: HOST
+ * xyz[n][3] (copied), or xyz == NULL for the last run's own bank (kept on the
+ * device; n is then ignored).  n_total = the generation's size N: history id
+ * i (0 <= i < N; the problem's ids must lie in [0, N)) starts at site
+ * floor(i n / N) -- systematic sampling, so replicas that split the ids and
+ * share one bank start exactly the histories of one run.  Synchronizes. */
+int gbmc_set_source_bank(gbmc_ctx *ctx, const double *xyz, int64_t n, int64_t n_total);
 
 /* Track-length absorption-rate tally (reaction-rate tally; the next step
  * after the lookup and tally of Sec. 2 "Tallying", which says tallies are

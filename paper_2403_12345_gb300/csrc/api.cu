@@ -92,6 +92,22 @@ struct gbmc_ctx {
     Tallies Y{};
     bool rr_on = false;              // absorption-rate tally on
 
+    // k-eigenvalue mode
+    double *d_nu = nullptr, *d_ffis = nullptr;
+    bool fis_loaded = false;
+    bool eig_on = false;
+    double k_norm = 1.0;
+    int32_t max_sites = 32;
+    double* d_sites = nullptr;       // [sites_cap][max_sites][3] per-history slots
+    int32_t* d_site_n = nullptr;     // [sites_cap]
+    int64_t* d_site_off = nullptr;   // [sites_cap]
+    double* d_bank_out = nullptr;    // [sites_cap * max_sites][3] the last run's bank
+    int64_t* d_bank_size = nullptr;
+    int64_t sites_cap = 0;
+    int32_t sites_ms = 0;            // max_sites the slots were sized for
+    double* d_bank_src = nullptr;    // source bank of GBMC_SRC_BANK runs
+    int64_t src_cap = 0, src_n = 0, src_total = 0;
+
     // run descriptors
     DevProblem* d_probs = nullptr;
     int32_t probs_cap = 0;
@@ -377,6 +393,7 @@ Tables make_tables(const gbmc_ctx* c) {
     T.mat_off = c->d_mat_off; T.nuc_id = c->d_nuc_id;
     T.density = c->d_density; T.density32 = c->d_density32;
     T.edges = c->d_edges;
+    T.nu = c->d_nu; T.f_fis = c->d_ffis;
     T.n_nuc = c->n_nuc; T.n_mat = c->n_mat; T.n_bins = c->n_bins;
     return T;
 }
@@ -420,6 +437,15 @@ Params make_params(gbmc_ctx* c) {
     P.max_iter = c->opt.max_iterations;
     sort_params(c, P);
     P.planes = c->d_planes;
+    P.bank = c->d_bank_src;
+    if (c->eig_on) {
+        P.sites = c->d_sites;
+        P.site_n = c->d_site_n;
+        P.site_off = c->d_site_off;
+        P.bank_size = c->d_bank_size;
+        P.bank_out = c->d_bank_out;
+        P.max_sites = c->max_sites;
+    }
     P.cum = c->d_cum;
     P.cum_stride = c->d_cum ? cum_row(c) : 0;
     if (c->ww_on) {
@@ -497,6 +523,7 @@ int build_graph(gbmc_ctx* c, Params P, const LaunchCfg& L) {
     CK(cudaStreamBeginCaptureToGraph(c->cap_stream, g, &cn, nullptr, 1,
                                      cudaStreamCaptureModeThreadLocal));
     le = launch_tail(P, L, c->cap_stream);
+    if (le == cudaSuccess && P.sites) le = launch_bank(P, L, c->cap_stream);
     cudaGraph_t g3 = nullptr;
     ee = cudaStreamEndCapture(c->cap_stream, &g3);
     if (le != cudaSuccess) return fail(c, GBMC_ERR_CUDA, "tail capture: %s", cudaGetErrorString(le));
@@ -527,13 +554,15 @@ int check_geometry(gbmc_ctx* c, const gbmc_geometry& g, int idx) {
         return fail(c, GBMC_ERR_INVALID_ARG, "problem %d: need 0 < E_cut <= E0", idx);
     std::vector<int32_t> mats;
     if (g.kind == GBMC_GEOM_INFINITE) {
-        if (g.source != GBMC_SRC_ORIGIN)
-            return fail(c, GBMC_ERR_INVALID_ARG, "problem %d: infinite medium takes the origin source", idx);
+        if (g.source != GBMC_SRC_ORIGIN && g.source != GBMC_SRC_BANK)
+            return fail(c, GBMC_ERR_INVALID_ARG,
+                        "problem %d: infinite medium takes the origin or bank source", idx);
         if (bad_mat(g.mat)) return fail(c, GBMC_ERR_INVALID_ARG, "problem %d: material out of range", idx);
         mats = {g.mat};
     } else if (g.kind == GBMC_GEOM_LATTICE) {
-        if (g.source != GBMC_SRC_BOX)
-            return fail(c, GBMC_ERR_INVALID_ARG, "problem %d: lattice takes the box source", idx);
+        if (g.source != GBMC_SRC_BOX && g.source != GBMC_SRC_BANK)
+            return fail(c, GBMC_ERR_INVALID_ARG, "problem %d: lattice takes the box or bank source",
+                        idx);
         if (g.n < 1 || g.n > 1 << 14 || !(g.pitch > 0) || !std::isfinite(g.pitch) ||
             !(g.radius > 0) || !(g.radius < 0.5 * g.pitch) || !(g.height > 0) ||
             !std::isfinite(g.height))
@@ -734,6 +763,8 @@ int gbmc_destroy(gbmc_ctx* c) {
     dfree(O.ncoll); dfree(O.status); dfree(O.nflt); dfree(O.ndraw);
     dfree(O.E); dfree(O.x); dfree(O.y); dfree(O.z);
     dfree(c->Y.flux); dfree(c->Y.counts); dfree(c->Y.weights); dfree(c->Y.absrate);
+    dfree(c->d_nu); dfree(c->d_ffis); dfree(c->d_sites); dfree(c->d_site_n); dfree(c->d_site_off);
+    dfree(c->d_bank_out); dfree(c->d_bank_size); dfree(c->d_bank_src);
     dfree(c->d_grid_off); dfree(c->d_e64); dfree(c->d_s64); dfree(c->d_es32);
     dfree(c->d_fabs); dfree(c->d_fabs32); dfree(c->d_awr);
     dfree(c->d_nx64); dfree(c->d_nx32); dfree(c->d_idx64); dfree(c->d_idx32); dfree(c->d_bw32);
@@ -1040,6 +1071,33 @@ int prepare_run(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, cudaStre
             c->graph_valid = false;
         }
     }
+    for (int32_t p = 0; p < n_prob; ++p) {
+        if (probs[p].geom.source != GBMC_SRC_BANK) continue;
+        if (c->src_n < 1)
+            return fail(c, GBMC_ERR_NOT_INITIALIZED, "problem %d takes the bank source: set it first", p);
+        if (probs[p].first_id + probs[p].n_particles > c->src_total)
+            return fail(c, GBMC_ERR_INVALID_ARG,
+                        "problem %d: ids beyond the source bank's generation size %lld", p,
+                        (long long)c->src_total);
+    }
+    if (c->eig_on) {
+        if (n_prob != 1 || c->ww_on)
+            return fail(c, GBMC_ERR_UNSUPPORTED,
+                        "k-eigenvalue runs take one problem and no weight windows");
+        if (total > c->sites_cap || c->max_sites != c->sites_ms) {
+            int64_t cap = std::max<int64_t>(total, 1);
+            size_t ns = (size_t)cap * (size_t)c->max_sites * 3;
+            if ((rc = dalloc(c, &c->d_sites, ns))) return rc;
+            if ((rc = dalloc(c, &c->d_bank_out, ns))) return rc;
+            if ((rc = dalloc(c, &c->d_site_n, (size_t)cap))) return rc;
+            if ((rc = dalloc(c, &c->d_site_off, (size_t)cap))) return rc;
+            if (!c->d_bank_size && (rc = dalloc(c, &c->d_bank_size, 1))) return rc;
+            c->sites_cap = cap;
+            c->sites_ms = c->max_sites;
+            c->graph_valid = false;
+        }
+        CK(cudaMemsetAsync(c->d_site_n, 0, sizeof(int32_t) * (size_t)std::max<int64_t>(total, 1), s));
+    }
     if ((rc = ensure_outcomes(c, total > 0 ? total : 1))) return rc;
     if ((rc = ensure_tallies(c, cells, s))) return rc;
     if (n_prob > c->probs_cap) {
@@ -1102,6 +1160,9 @@ int prepare_run(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, cudaStre
     k.M = M;
     k.n_prob = n_prob;
     k.birth_reserve = c->ww_on ? M / 2 : 0;
+    k.k_norm = c->k_norm;
+    k.bank_n = c->src_n;
+    k.bank_total = c->src_total;
     CK(cudaMemcpyAsync(c->d_probs, c->h_probs, sizeof(DevProblem) * n_prob, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c->d_planes, c->h_planes, sizeof(double) * n_planes, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c->d_ctl, c->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
@@ -1187,6 +1248,7 @@ int gbmc_profile_problems(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs
         // the tail kernel (a no-op unless the loop stopped early)
         cudaEventRecord(ev[0], s);
         e = launch_tail(P, L, s);
+        if (e == cudaSuccess && P.sites) e = launch_bank(P, L, s);
         cudaEventRecord(ev[1], s);
         if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
         float ms = 0;
@@ -1264,6 +1326,90 @@ int gbmc_read_reaction_tally(gbmc_ctx* c, int32_t slot, double* absrate, int64_t
     if (n != nf) return fail(c, GBMC_ERR_INVALID_ARG, "n must be %lld", (long long)nf);
     CK(cudaMemcpy(absrate, c->Y.absrate + c->slot_flux_off[slot], sizeof(double) * nf,
                   cudaMemcpyDeviceToHost));
+    return GBMC_OK;
+}
+
+int gbmc_load_fission(gbmc_ctx* c, int32_t n_nuc, const double* nu, const double* f_fis) {
+    if (!c) return GBMC_ERR_INVALID_ARG;
+    if (!c->n_nuc) return fail(c, GBMC_ERR_NOT_INITIALIZED, "load the tables first");
+    if (n_nuc != c->n_nuc || !nu || !f_fis)
+        return fail(c, GBMC_ERR_INVALID_ARG, "need nu and f_fis for the %d loaded nuclides", c->n_nuc);
+    for (int32_t i = 0; i < n_nuc; ++i) {
+        if (!(nu[i] >= 0) || !std::isfinite(nu[i]))
+            return fail(c, GBMC_ERR_INVALID_ARG, "nuclide %d: nu must be finite and >= 0", i);
+        if (!(f_fis[i] >= 0) || !(f_fis[i] <= c->h_fabs[i]))
+            return fail(c, GBMC_ERR_INVALID_ARG, "nuclide %d: need 0 <= f_fis <= f_abs", i);
+    }
+    int rc = set_device(c);
+    if (rc) return rc;
+    if ((rc = upload(c, &c->d_nu, nu, (size_t)n_nuc))) return rc;
+    if ((rc = upload(c, &c->d_ffis, f_fis, (size_t)n_nuc))) return rc;
+    c->fis_loaded = true;
+    c->graph_valid = false;
+    return GBMC_OK;
+}
+
+int gbmc_set_eigen(gbmc_ctx* c, double k_norm, int32_t max_sites) {
+    if (!c) return GBMC_ERR_INVALID_ARG;
+    if (!(k_norm > 0) || !std::isfinite(k_norm)) {
+        if (c->eig_on) c->graph_valid = false;
+        c->eig_on = false;
+        return GBMC_OK;
+    }
+    if (!c->fis_loaded) return fail(c, GBMC_ERR_NOT_INITIALIZED, "load the fission data first");
+    if (max_sites < 1 || max_sites > 255)
+        return fail(c, GBMC_ERR_INVALID_ARG, "max_sites must be in [1, 255]");
+    if (!c->eig_on || max_sites != c->max_sites) c->graph_valid = false;
+    c->eig_on = true;
+    c->k_norm = k_norm;
+    c->max_sites = max_sites;
+    return GBMC_OK;
+}
+
+int gbmc_read_bank(gbmc_ctx* c, double* xyz, int64_t n_cap, int64_t* n_out) {
+    if (!c || !n_out) return GBMC_ERR_INVALID_ARG;
+    int rc = set_device(c);
+    if (rc) return rc;
+    if (!c->d_bank_size) return fail(c, GBMC_ERR_NOT_INITIALIZED, "no k-eigenvalue run yet");
+    if ((rc = read_ctl(c))) return rc;
+    int64_t n = 0;
+    CK(cudaMemcpy(&n, c->d_bank_size, sizeof n, cudaMemcpyDeviceToHost));
+    *n_out = n;
+    if (xyz) {
+        if (n_cap < n) return fail(c, GBMC_ERR_INVALID_ARG, "need room for %lld sites", (long long)n);
+        CK(cudaMemcpy(xyz, c->d_bank_out, sizeof(double) * 3 * (size_t)n, cudaMemcpyDeviceToHost));
+    }
+    return GBMC_OK;
+}
+
+int gbmc_set_source_bank(gbmc_ctx* c, const double* xyz, int64_t n, int64_t n_total) {
+    if (!c) return GBMC_ERR_INVALID_ARG;
+    int rc = set_device(c);
+    if (rc) return rc;
+    if (n_total < 1 || n_total > ((int64_t)1 << 31) - 1)
+        return fail(c, GBMC_ERR_INVALID_ARG, "n_total must be in [1, 2^31)");
+    if (!xyz) {
+        if (!c->d_bank_size) return fail(c, GBMC_ERR_NOT_INITIALIZED, "no k-eigenvalue run yet");
+        if ((rc = read_ctl(c))) return rc;
+        CK(cudaMemcpy(&n, c->d_bank_size, sizeof n, cudaMemcpyDeviceToHost));
+    } else {
+        for (int64_t i = 0; i < 3 * n; ++i)
+            if (!std::isfinite(xyz[i])) return fail(c, GBMC_ERR_INVALID_ARG, "bank coordinate not finite");
+    }
+    if (n < 1 || n > ((int64_t)1 << 31) - 1)
+        return fail(c, GBMC_ERR_INVALID_ARG, "the bank must hold 1 to 2^31 - 1 sites");
+    if (n > c->src_cap) {
+        if ((rc = dalloc(c, &c->d_bank_src, (size_t)n * 3))) return rc;
+        c->src_cap = n;
+        c->graph_valid = false;
+    }
+    if (xyz)
+        CK(cudaMemcpy(c->d_bank_src, xyz, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice));
+    else
+        CK(cudaMemcpy(c->d_bank_src, c->d_bank_out, sizeof(double) * 3 * (size_t)n,
+                      cudaMemcpyDeviceToDevice));
+    c->src_n = n;
+    c->src_total = n_total;
     return GBMC_OK;
 }
 

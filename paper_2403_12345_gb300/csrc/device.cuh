@@ -64,6 +64,8 @@ struct Tables {
     const double* density;     // [mat_off[n_mat]]
     const float* density32;    // [mat_off[n_mat]]
     const double* edges;       // [n_bins+1] tally energy edges
+    const double* nu;          // [n_nuc] mean neutrons per fission (k-eigenvalue)
+    const double* f_fis;       // [n_nuc] sigma_f / sigma_t
     int32_t n_nuc, n_mat, n_bins, pad;
 };
 
@@ -99,7 +101,8 @@ struct alignas(128) Particle {
     uint32_t rj;         // draws consumed from the particle's stream
     uint8_t inside;      // inside the pin cylinder (lattice)
     uint8_t surf;        // surface reached by the last flight
-    uint8_t pad8[2];
+    uint8_t nsite;       // fission sites banked by the history so far (k-eigenvalue)
+    uint8_t pad8;
     uint64_t hid;        // history id: counter word 0 of the particle's stream
 };
 static_assert(sizeof(Particle) == 128, "one particle per 128-byte line");
@@ -159,6 +162,8 @@ struct Ctl {
     int32_t n_prob;
     int32_t done, err, iter, pad;
     unsigned long long st_lookups, st_micro, st_flights, st_cross, st_coll, st_hist;
+    double k_norm;               // k-eigenvalue: fission yield normalisation of this run
+    int64_t bank_n, bank_total;  // source bank size, generation size (GBMC_SRC_BANK)
 };
 
 constexpr int kSortBuckets = 1 << 16;
@@ -195,6 +200,17 @@ struct Params {
     int32_t imp_cap;
     int32_t pad5;
     const double* planes;    // plane tables of the run's problems (DevProblem::plane_off)
+    // k-eigenvalue (sites NULL: off): history g of the run banks its fission
+    // sites at sites[(g max_sites + k) * 3], its count at site_n[g]; after
+    // the run they are compacted into bank_out (size *bank_size)
+    double* sites;
+    int32_t* site_n;
+    int64_t* site_off;
+    int64_t* bank_size;
+    double* bank_out;
+    const double* bank;      // source bank [Ctl::bank_n][3] of GBMC_SRC_BANK runs
+    int32_t max_sites;
+    int32_t pad6;
     void* cum;               // running sums of N_i sigma_i, slot-major (NULL: recompute)
     int64_t cum_stride;      // elements per slot (the most nuclides of any material)     // bits of the smallest grid energy
     cudaGraphConditionalHandle cond;

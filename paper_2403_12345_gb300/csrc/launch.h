@@ -23,6 +23,10 @@ cudaError_t launch_iteration(const Params& P, const LaunchCfg& L, cudaStream_t s
 // stopped early (a no-op otherwise).
 cudaError_t launch_tail(const Params& P, const LaunchCfg& L, cudaStream_t s);
 
+// k-eigenvalue: compacts the run's per-history fission-site slots into
+// P.bank_out (history order), the size into *P.bank_size.
+cudaError_t launch_bank(const Params& P, const LaunchCfg& L, cudaStream_t s);
+
 // The iteration launched eagerly with an event before and after each kernel
 // (ev[0..8]; the lookup's two mode kernels share one interval), for
 // per-kernel device timing; the tail is timed separately.

@@ -233,7 +233,15 @@ __global__ void __launch_bounds__(256) k_source(Params P) {
             r.init(pr.seed, pr.key_hi, (uint64_t)(pr.first_id + (gi - pr.start)), 0u);
             const gbmc_geometry& g = pr.g;
             double x = 0.0, y = 0.0, z = 0.0;
-            if (g.source == GBMC_SRC_BOX) {
+            if (g.source == GBMC_SRC_BANK) {
+                // systematic sampling of the bank: history id i starts at
+                // site floor(i bank_n / bank_total)
+                int64_t id = pr.first_id + (gi - pr.start);
+                int64_t sidx = id * c->bank_n / c->bank_total;
+                x = P.bank[3 * sidx];
+                y = P.bank[3 * sidx + 1];
+                z = P.bank[3 * sidx + 2];
+            } else if (g.source == GBMC_SRC_BOX) {
                 double L = (double)g.n * g.pitch;
                 x = r.next() * L;
                 y = r.next() * L;
@@ -740,6 +748,31 @@ __device__ __forceinline__ int cross(const Params& P, const DevProblem& pr, Part
     return status;
 }
 
+// k-eigenvalue banking at a collision in nuclide nuc: floor(w nu f_fis /
+// k_norm + xi) fission sites at the collision point (xi one draw, right
+// after the nuclide choice), in the history's own slots (so the bank's order
+// is the histories' order, whatever the order of the events).  More than
+// max_sites sites for one history flags the run.
+__device__ __forceinline__ void bank_sites(const Params& P, Particle& pt, int32_t nuc, Stream& r) {
+    double xf = r.next();
+    double y = (pt.wgt * __ldg(P.T.nu + nuc)) * __ldg(P.T.f_fis + nuc) / P.ctl->k_norm + xf;
+    int32_t nb = (int32_t)floor(y);
+    if (nb <= 0 || pt.gidx < 0) return;
+    int32_t k = pt.nsite;
+    if (k + nb > P.max_sites) {
+        atomicCAS(&P.ctl->err, 0, GBMC_ERR_DEVICE_FLAG);
+        nb = P.max_sites - k;
+    }
+    double* s = P.sites + ((size_t)pt.gidx * (size_t)P.max_sites + (size_t)k) * 3;
+    for (int32_t q = 0; q < nb; ++q) {
+        s[3 * q] = pt.x;
+        s[3 * q + 1] = pt.y;
+        s[3 * q + 2] = pt.z;
+    }
+    pt.nsite = (uint8_t)(k + nb);
+    P.site_n[pt.gidx] = k + nb;
+}
+
 // Collision event: nuclide (from the running sums the lookup stored, else
 // recomputed), absorption, elastic scatter (isotropic in the CM frame,
 // target at rest), energy cutoff.  Returns the fate (0: alive, needs a new
@@ -756,6 +789,7 @@ __device__ __forceinline__ int collide(const Params& P, const DevProblem& pr, Pa
     }
     if (nuc < 0) nuc = pick_nuclide(P.T, PREC, pt.mat, pt.E, target);
     pt.ncoll = pt.ncoll + 1;
+    if (P.sites) bank_sites(P, pt, nuc, r);
     int status = 0;
     double xa = r.next();
     if (xa < __ldg(P.T.f_abs + nuc)) {
@@ -1125,6 +1159,54 @@ __global__ void __launch_bounds__(256, 4) k_query_lookup(Tables T, const double*
         st[i] = a;
         sa[i] = b;
     }
+}
+
+// ---------------------------------------------------------------- fission bank
+// Compaction of the run's per-history site slots into the bank, in history
+// order: one block scans the counts (each thread a contiguous range), then a
+// grid copies the sites; *bank_size receives the bank size.
+__global__ void __launch_bounds__(1024) k_bank_scan(Params P) {
+    __shared__ int64_t part[1024];
+    const int64_t n = P.ctl->total;
+    int64_t per = (n + blockDim.x - 1) / blockDim.x;
+    int64_t a = (int64_t)threadIdx.x * per;
+    int64_t b = a + per < n ? a + per : n;
+    int64_t s = 0;
+    for (int64_t i = a; i < b; ++i) s += P.site_n[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t run = 0;
+        for (int k = 0; k < (int)blockDim.x; ++k) {
+            int64_t v = part[k];
+            part[k] = run;
+            run += v;
+        }
+        *P.bank_size = run;
+    }
+    __syncthreads();
+    s = part[threadIdx.x];
+    for (int64_t i = a; i < b; ++i) {
+        P.site_off[i] = s;
+        s += P.site_n[i];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_bank_compact(Params P) {
+    const int64_t n = P.ctl->total;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        int32_t m = P.site_n[g];
+        const double* src = P.sites + (size_t)g * (size_t)P.max_sites * 3;
+        double* dst = P.bank_out + (size_t)P.site_off[g] * 3;
+        for (int32_t k = 0; k < 3 * m; ++k) dst[k] = src[k];
+    }
+}
+
+cudaError_t launch_bank(const Params& P, const LaunchCfg& L, cudaStream_t s) {
+    k_bank_scan<<<1, 1024, 0, s>>>(P);
+    k_bank_compact<<<L.grid, 256, 0, s>>>(P);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- host launchers

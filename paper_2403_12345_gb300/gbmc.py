@@ -22,7 +22,7 @@ ERR_INVALID_ARG, ERR_NOT_INITIALIZED, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_DEVICE
 FP64, FP32 = 0, 1
 GEOM_INFINITE, GEOM_LATTICE, GEOM_SLAB = 0, 1, 2
 BC_VACUUM, BC_REFLECT = 0, 1
-SRC_ORIGIN, SRC_BOX, SRC_SLAB_FACE = 0, 1, 2
+SRC_ORIGIN, SRC_BOX, SRC_SLAB_FACE, SRC_BANK = 0, 1, 2, 3
 STATUS_ABSORBED, STATUS_LEAKED, STATUS_CUTOFF, STATUS_LIMIT, STATUS_LEAKED_FAR, \
     STATUS_ROULETTE = 1, 2, 3, 4, 5, 6
 S_COLLISION, S_ABSORPTION, S_LEAK, S_CUTOFF, S_LIMIT, S_LEAK_FAR, S_FLIGHT, S_HISTORY, S_SPLIT, \
@@ -39,7 +39,8 @@ EXPORTS = ["gbmc_default_options", "gbmc_create", "gbmc_destroy", "gbmc_last_err
            "gbmc_get_importance_net", "gbmc_mlp_forward", "gbmc_mlp_gradient", "gbmc_mlp_train",
            "gbmc_mesh_features", "gbmc_weight_windows_from_net", "gbmc_importance_record",
            "gbmc_importance_accumulate", "gbmc_importance_training_set",
-           "gbmc_get_weight_windows", "gbmc_set_reaction_tally", "gbmc_read_reaction_tally"]
+           "gbmc_get_weight_windows", "gbmc_set_reaction_tally", "gbmc_read_reaction_tally",
+           "gbmc_load_fission", "gbmc_set_eigen", "gbmc_read_bank", "gbmc_set_source_bank"]
 MLP_HIDDEN = 64
 MLP_NPARAM = 4545
 NOALLOC_MAX_QUERIES = 1 << 20
@@ -121,6 +122,10 @@ def lib():
         L.gbmc_read_tallies.argtypes = [vp, C.c_int32, _P(C.c_double), C.c_int64,
                                         _P(C.c_int64), _P(C.c_double)]
         L.gbmc_set_reaction_tally.argtypes = [vp, C.c_int32]
+        L.gbmc_load_fission.argtypes = [vp, C.c_int32, _P(C.c_double), _P(C.c_double)]
+        L.gbmc_set_eigen.argtypes = [vp, C.c_double, C.c_int32]
+        L.gbmc_read_bank.argtypes = [vp, _P(C.c_double), C.c_int64, _P(C.c_int64)]
+        L.gbmc_set_source_bank.argtypes = [vp, _P(C.c_double), C.c_int64, C.c_int64]
         L.gbmc_read_reaction_tally.argtypes = [vp, C.c_int32, _P(C.c_double), C.c_int64]
         L.gbmc_read_outcomes.argtypes = [vp, C.c_int32, C.c_int64, C.c_int64, _P(C.c_int32),
                                          _P(C.c_int8), _P(C.c_int32), _P(C.c_uint32),
@@ -419,6 +424,33 @@ class Context:
         self._ck(lib().gbmc_read_tallies(self._h, int(slot), _p(flux, C.c_double), flux.size,
                                          _p(counts, C.c_int64), _p(weights, C.c_double)))
         return flux, counts, weights
+
+    # -- k-eigenvalue -------------------------------------------------------------
+    def load_fission(self, nu, f_fis):
+        a, b = _arr(nu, np.float64), _arr(f_fis, np.float64)
+        self._ck(lib().gbmc_load_fission(self._h, len(a), _p(a, C.c_double), _p(b, C.c_double)))
+
+    def set_eigen(self, k_norm: float, max_sites: int = 32):
+        self._ck(lib().gbmc_set_eigen(self._h, float(k_norm), int(max_sites)))
+
+    def read_bank(self, sites: bool = True):
+        """The last run's fission bank [n, 3] in history order (or its size)."""
+        n = C.c_int64()
+        self._ck(lib().gbmc_read_bank(self._h, None, 0, C.byref(n)))
+        if not sites:
+            return n.value
+        out = np.zeros((n.value, 3))
+        self._ck(lib().gbmc_read_bank(self._h, _p(out, C.c_double), n.value, C.byref(n)))
+        return out
+
+    def set_source_bank(self, xyz=None, n_total: int = 0):
+        """Source bank for GBMC_SRC_BANK runs: host sites [n, 3], or None for
+        the last run's own bank."""
+        if xyz is None:
+            self._ck(lib().gbmc_set_source_bank(self._h, None, 0, int(n_total)))
+        else:
+            a = _arr(xyz, np.float64).reshape(-1, 3)
+            self._ck(lib().gbmc_set_source_bank(self._h, _p(a, C.c_double), len(a), int(n_total)))
 
     def set_reaction_tally(self, on: bool = True):
         self._ck(lib().gbmc_set_reaction_tally(self._h, 1 if on else 0))

@@ -103,3 +103,15 @@ def gather_outcomes(outcomes: dict, group=None, dst: int = 0):
     if rank != dst:
         return None
     return {k: np.concatenate([p[k] for p in parts]) for k in parts[0]}
+
+
+def gather_bank(xyz, group=None):
+    """The fission banks of the ranks' id shares, concatenated in rank order
+    (the one-run bank, when the shares are `id_range` shares): every rank
+    gets the whole bank for the next generation."""
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    parts = [None] * world
+    dist.all_gather_object(parts, np.ascontiguousarray(xyz, np.float64).reshape(-1, 3),
+                           group=group)
+    return np.concatenate(parts)

@@ -163,3 +163,47 @@ def test_shard_problems_copies():
     assert probs[0].first_id == 0 and probs[0].n_particles == 260   # inputs untouched
     with pytest.raises(ValueError):
         replicas.shard_problems(probs, 0, 2, by="cells")
+
+
+# ---------------------------------------------------------------- k-eigenvalue
+
+def _eigen_worker(rank, world, port, outdir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        p = synth.make_eigen_lattice(n_particles=3000, grid_scale=0.02)
+        N = 3000
+        first, n = replicas.id_range(0, N, rank, world)
+        k, bank, ks = 1.0, None, []
+        for gen in range(3):
+            eig = dict(nu=p.nu, f_fis=p.f_fis, k_norm=k, max_sites=64)
+            if bank is not None:
+                eig["bank"] = (bank, N)
+            r = oracle.run(p, seed=p.seed, batch=gen, first_id=first, n=n, eigen=eig, threads=1)
+            bank = replicas.gather_bank(r["sites"])        # the source-bank exchange
+            k = len(bank) / N * k
+            ks.append(k)
+        if rank == 0:
+            with open(os.path.join(outdir, "eigen.pkl"), "wb") as f:
+                pickle.dump(dict(ks=ks, bank=bank), f)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_eigen_bank_exchange_equals_one_process(tmp_path):
+    mp.spawn(_eigen_worker, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
+    with open(tmp_path / "eigen.pkl", "rb") as f:
+        res = pickle.load(f)
+    p = synth.make_eigen_lattice(n_particles=3000, grid_scale=0.02)
+    k, bank, ks = 1.0, None, []
+    for gen in range(3):
+        eig = dict(nu=p.nu, f_fis=p.f_fis, k_norm=k, max_sites=64)
+        if bank is not None:
+            eig["bank"] = (bank, 3000)
+        r = oracle.run(p, seed=p.seed, batch=gen, n=3000, eigen=eig)
+        bank = r["sites"]
+        k = len(bank) / 3000 * k
+        ks.append(k)
+    assert res["ks"] == ks
+    assert np.array_equal(res["bank"], bank)
