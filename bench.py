@@ -47,6 +47,8 @@ WORKLOADS = {
        "weight windows (4-64-64-1 BF16 MLP trained on analog estimates) against analog",
     6: "lookup-only stress set: 281 nuclides x 60k points, one 244-nuclide material, 1e7 "
        "energies log-uniform on [1e-5, 2e7] eV (unsorted; the library sorts)",
+    7: "k-eigenvalue power iteration on the 17x17 lattice (40 fissile pin nuclides), binary64 "
+       "tables, 1e6 particles per generation; steps are active generations after the inactive ones",
 }
 
 
@@ -109,16 +111,24 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _eigen_of(prob):
+    """Fission banking for the oracle when the workload is a k-eigenvalue one
+    (a first generation from the box source)."""
+    if getattr(prob, "nu", None) is None:
+        return None
+    return dict(nu=prob.nu, f_fis=prob.f_fis, k_norm=1.0, max_sites=255)
+
+
 def oracle_rate(prob, budget_s, threads, batch=0, cap=None):
     """Particles/s of the CPU oracle on a bounded sample (first ids of a batch)."""
     import oracle
     n = 2000
     t = time.perf_counter()
-    oracle.run(prob, seed=prob.seed, batch=batch, n=n, threads=threads)
+    oracle.run(prob, seed=prob.seed, batch=batch, n=n, threads=threads, eigen=_eigen_of(prob))
     dt = time.perf_counter() - t
     n = int(max(2000, min(budget_s / max(dt, 1e-6) * n, cap or prob.n_particles[0])))
     t = time.perf_counter()
-    oracle.run(prob, seed=prob.seed, batch=batch, n=n, threads=threads)
+    oracle.run(prob, seed=prob.seed, batch=batch, n=n, threads=threads, eigen=_eigen_of(prob))
     dt = time.perf_counter() - t
     return n / dt, n, dt
 
@@ -131,11 +141,12 @@ def run_reference(args, prob, rank):
     # size a step to ~budget seconds of oracle work
     _, n, dt = oracle_rate(prob, args.ref_step_s, threads)
     for w in range(args.warmup):
-        oracle.run(prob, seed=prob.seed, batch=100 + w, n=min(n, 2000), threads=threads)
+        oracle.run(prob, seed=prob.seed, batch=100 + w, n=min(n, 2000), threads=threads,
+                   eigen=_eigen_of(prob))
     times = []
     for k in range(args.steps):
         t = time.perf_counter()
-        oracle.run(prob, seed=prob.seed, batch=k, n=n, threads=threads)
+        oracle.run(prob, seed=prob.seed, batch=k, n=n, threads=threads, eigen=_eigen_of(prob))
         times.append(time.perf_counter() - t)
     tot = sum(times)
     value = n * args.steps / tot
@@ -391,6 +402,84 @@ def run_streams(args, prob, rank, world, local):
         dist.destroy_process_group()
 
 
+def run_eigen(args, prob, rank, world, local):
+    """k-eigenvalue power iteration: `warmup` inactive generations (the first
+    from the box source), then `steps` timed active generations, each from the
+    previous generation's fission bank (kept on the device) with the yield
+    normalised by the previous estimate.  Replicas split each generation's
+    ids and exchange their banks between generations."""
+    import torch
+    import torch.distributed as dist
+    from paper_2403_12345_gb300 import gbmc, replicas
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    stream = torch.cuda.current_stream()
+    N = prob.n_particles[0]
+    ctx = gbmc.Context(local, precision=args.precision, sort=args.sort)
+    ctx.load(prob, (args.precision,))
+    ctx.load_fission(prob.nu, prob.f_fis)
+    g_box = gbmc.geometry_from(prob.geom)
+    g_bank = gbmc.geometry_from(prob.geom)
+    g_bank.source = gbmc.SRC_BANK
+    first, n = replicas.id_range(0, N, rank, world)
+    state = {"k": 1.0, "gen": 0}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def generation(_k=None):
+        gen = state["gen"]
+        ctx.set_eigen(state["k"], 64)
+        g = g_box if gen == 0 else g_bank
+        ctx.run_batch(gbmc.problem(g, prob.seed, n, batch=gen, first_id=first), stream)
+        state["gen"] = gen + 1
+
+    def next_source():
+        if world > 1:
+            bank = replicas.gather_bank(ctx.read_bank())
+            ctx.set_source_bank(bank, N)
+            size = len(bank)
+        else:
+            size = ctx.read_bank(sites=False)
+            ctx.set_source_bank(None, N)
+        k = size / N * state["k"]
+        state["k"] = k
+        return k
+
+    for _ in range(max(args.warmup, 1)):
+        generation()
+        next_source()
+    if world > 1:
+        dist.barrier()
+    ks, ms_all = [], []
+    clocks = None
+    for k_step in range(args.steps):
+        ms, clocks = _timed(lambda _k: generation(), 1, flush, stream, local)
+        ms_all.append(ms[0])
+        ks.append(next_source())        # outside the timed region (bank exchange, k)
+    tot_ms = _max_over_ranks(sum(ms_all), world)
+    value = N * args.steps / (tot_ms * 1e-3)
+    kk = np.array(ks)
+    if rank == 0:
+        cfg = {"workload": prob.name, "description": WORKLOADS[7], "particles_per_generation": N,
+               "inactive_generations": max(args.warmup, 1), "active_generations": args.steps,
+               "table_precision": "fp32" if args.precision == 1 else "fp64",
+               "nuclides": int(prob.n_nuc), "l2": "flushed between timed generations (256 MiB write)",
+               "parallelism": f"replicas{args.gpus}"}
+        print(json.dumps({
+            "metric": "particles/s", "value": value, "unit": "particles/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": "f32" if args.precision == 1 else "f64", "data": "synthetic", "config": cfg,
+            "k_eff": {"mean": float(kk.mean()),
+                      "std_err": float(kk.std(ddof=1) / np.sqrt(len(kk))) if len(kk) > 1 else None,
+                      "per_generation": [float(x) for x in kk]},
+            "e2e": None, "roofline": None, "cpu_baseline": None, "clocks": clocks,
+            "gpu_launches": None}), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def run_windows(args, prob, rank, world, local):
     """Deep-penetration slab: learned weight windows against analog.  One step
     = one batch with the learned windows; the figure of merit FOM = 1/(R^2 T)
@@ -500,6 +589,15 @@ def main():
 
     if args.config == 6:
         run_stress(args, rank, world, local)
+        return
+    if args.config == 7:
+        prob = synth.make_eigen_lattice(n_particles=args.particles or 1_000_000)
+        if args.precision < 0:
+            args.precision = prob.precision
+        if args.impl == "reference":
+            run_reference(args, prob, rank)
+        else:
+            run_eigen(args, prob, rank, world, local)
         return
     prob = synth.make_config(args.config, n_particles=args.particles or None)
     if args.precision < 0:

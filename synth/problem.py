@@ -270,8 +270,9 @@ def make_eigen_lattice(n_particles: int = 1_000_000, grid_scale: float = 1.0,
     """k-eigenvalue workload: the 17x17 lattice of configuration 2 (same
     tables and seeds) with the first n_fissile pin nuclides made fissile:
     sigma_f = g f_abs sigma_t with g uniform on [0.7, 0.95] (fission is part
-    of absorption) and nu uniform on [2.4, 2.9]; with 40 of the 68 pin
-    nuclides the lattice is near critical (k about 1.00).  The source of the first
+    of absorption) and nu uniform on [2.4, 2.9].  With 40 of the 68 pin
+    nuclides k is about 1.0 at grid_scale 0.02 and about 1.47 with the full
+    grids.  The source of the first
     generation is the box source; later generations start from the bank."""
     p = make_config(2, n_particles=n_particles, grid_scale=grid_scale)
     rng = np.random.default_rng(BASE_SEED + 7)
