@@ -688,6 +688,22 @@ def main():
     # problem's tallies and every particle's outcome (collisions, fate) to
     # the host
     e2e_steps = max(1, args.e2e_steps)
+
+    def pinned(shape, dtype):
+        return torch.empty(shape, dtype=dtype, pin_memory=True).numpy()
+
+    # result buffers in pinned host memory, allocated once
+    hosts = []
+    for slot in range(n_geo):
+        nc = gbmc._n_cells(geoms[slot])
+        tal = (pinned((nc, prob.n_bins), torch.float64), pinned(gbmc.NSCAL, torch.int64),
+               pinned(gbmc.NSCAL, torch.float64))
+        m = counts[slot]
+        outc = dict(n_coll=pinned(m, torch.int32), status=pinned(m, torch.int8),
+                    n_flights=pinned(m, torch.int32), n_draws=pinned(m, torch.int32).view(np.uint32),
+                    E=pinned(m, torch.float64), x=pinned(m, torch.float64),
+                    y=pinned(m, torch.float64), z=pinned(m, torch.float64))
+        hosts.append((tal, outc))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     d2h = 0
@@ -695,8 +711,8 @@ def main():
         ctx.run_problems(problems(20_000 + k), stream)
         d2h = 0
         for slot in range(n_geo):
-            fl, cn, wt = ctx.read_tallies(slot)
-            o = ctx.read_outcomes(slot, 0, counts[slot])
+            fl, cn, wt = ctx.read_tallies(slot, out=hosts[slot][0])
+            o = ctx.read_outcomes(slot, 0, counts[slot], out=hosts[slot][1])
             d2h += fl.nbytes + cn.nbytes + wt.nbytes + sum(o[f].nbytes for f in o)
     e2e_s = time.perf_counter() - t0
     h2d = ctypes.sizeof(gbmc.Problem) * n_geo

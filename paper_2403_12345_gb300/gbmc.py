@@ -416,11 +416,17 @@ class Context:
         return out
 
     # -- read-back ------------------------------------------------------------
-    def read_tallies(self, slot: int = 0):
+    def read_tallies(self, slot: int = 0, out=None):
+        """(flux [cells, bins], counts, weights) of a problem slot; `out` may
+        hold preallocated arrays of those shapes (for example in pinned host
+        memory) to fill instead."""
         nc = self._cells[slot]
-        flux = np.zeros((nc, self.n_bins))
-        counts = np.zeros(NSCAL, np.int64)
-        weights = np.zeros(NSCAL)
+        if out is not None:
+            flux, counts, weights = out
+        else:
+            flux = np.zeros((nc, self.n_bins))
+            counts = np.zeros(NSCAL, np.int64)
+            weights = np.zeros(NSCAL)
         self._ck(lib().gbmc_read_tallies(self._h, int(slot), _p(flux, C.c_double), flux.size,
                                          _p(counts, C.c_int64), _p(weights, C.c_double)))
         return flux, counts, weights
@@ -461,10 +467,14 @@ class Context:
         self._ck(lib().gbmc_read_reaction_tally(self._h, int(slot), _p(out, C.c_double), out.size))
         return out
 
-    def read_outcomes(self, slot: int = 0, first: int = 0, n: int = 0):
-        o = dict(n_coll=np.zeros(n, np.int32), status=np.zeros(n, np.int8),
-                 n_flights=np.zeros(n, np.int32), n_draws=np.zeros(n, np.uint32),
-                 E=np.zeros(n), x=np.zeros(n), y=np.zeros(n), z=np.zeros(n))
+    def read_outcomes(self, slot: int = 0, first: int = 0, n: int = 0, out=None):
+        """Per-particle outcomes of ids [first, first + n) of a slot; `out` may
+        be a dict of preallocated arrays (n_coll int32, status int8, n_flights
+        int32, n_draws uint32, E, x, y, z float64) to fill instead."""
+        o = out if out is not None else dict(
+            n_coll=np.zeros(n, np.int32), status=np.zeros(n, np.int8),
+            n_flights=np.zeros(n, np.int32), n_draws=np.zeros(n, np.uint32),
+            E=np.zeros(n), x=np.zeros(n), y=np.zeros(n), z=np.zeros(n))
         self._ck(lib().gbmc_read_outcomes(
             self._h, int(slot), int(first), int(n), _p(o["n_coll"], C.c_int32),
             _p(o["status"], C.c_int8), _p(o["n_flights"], C.c_int32),
