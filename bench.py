@@ -580,7 +580,8 @@ def main():
                     help="K > 1: K independent event loops (contexts) on K concurrent streams, "
                          "the work split between them, instead of one batched launch")
     ap.add_argument("--autotune", type=int, default=-1,
-                    help="1: autotune launch settings before timing (default: config 4 only)")
+                    help="1: autotune launch settings before timing, 0: defaults "
+                         "(default: autotune configs 2-4)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -641,7 +642,7 @@ def main():
                              problem_index=k) for k in range(n_geo)]
 
     tuned = None
-    if args.autotune == 1 or (args.autotune < 0 and args.config == 4):
+    if args.autotune == 1 or (args.autotune < 0 and args.config in (2, 3, 4)):
         tuned = ctx.autotune(problems(40_000), fraction=0.1, stream=stream)
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")

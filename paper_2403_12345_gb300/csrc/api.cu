@@ -1140,6 +1140,7 @@ int prepare_run(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, cudaStre
         d.start = start[p];
         d.flux_off = c->slot_flux_off[p];
         d.plane_off = plane_off[p];
+        d.r2 = probs[p].geom.radius * probs[p].geom.radius;
         d.n_cells = cells[p];
         // plane positions as the transport forms them: walls i * pitch
         // (i = 0..n), then lattice cell centres (i + 0.5) * pitch

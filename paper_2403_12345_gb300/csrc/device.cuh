@@ -77,6 +77,7 @@ struct DevProblem {
     int64_t flux_off;             // offset of its flux tally
     int64_t plane_off;            // its plane table: walls (double)i * pitch, i = 0..n, then
                                   // lattice cell centres ((double)i + 0.5) * pitch, i < n
+    double r2;                    // lattice pin radius squared (radius * radius)
     int32_t n_cells, pad;
 };
 
@@ -798,12 +799,14 @@ struct Cyl {
     int kind;   // 0: no crossing, 1: (sD - k) / a, 2: -c / (k + sD), 3: c / (sD - k)
 };
 
-__device__ __forceinline__ Cyl cylinder_of(double dx, double dy, double u, double v, double r,
-                                           bool inside) {
+// a = u * u + v * v and r2 = r * r come from the caller (they change with
+// the direction and the problem only).
+__device__ __forceinline__ Cyl cylinder_of(double dx, double dy, double u, double v, double a,
+                                           double r2, bool inside) {
     Cyl q;
-    q.a = u * u + v * v;
+    q.a = a;
     q.k = dx * u + dy * v;
-    q.c = (dx * dx + dy * dy) - r * r;
+    q.c = (dx * dx + dy * dy) - r2;
     q.D = q.k * q.k - q.a * q.c;
     bool a0 = (__double_as_longlong(q.a) << 1) == 0;
     if (inside) {

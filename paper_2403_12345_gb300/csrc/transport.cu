@@ -518,6 +518,7 @@ __device__ __forceinline__ void score_segment(const Params& P, const DevProblem&
 
 // One flight (advance event): sample the distance to collision, find the
 // nearest surface of the current cell (ties: cylinder, x, y, z) and compare.
+// a_uv = u * u + v * v of the current direction (a reflection keeps it).
 // Returns true for a collision, leaving the particle where it is: the move
 // by -ln(xi) / Sigma_t and its track-length score are finish_flight's, run
 // by the collision event, where every lane of a warp needs that logarithm.
@@ -526,7 +527,7 @@ __device__ __forceinline__ void score_segment(const Params& P, const DevProblem&
 // spans: a surface decided by its span alone costs one binary64 quotient,
 // taken by all such lanes of a warp together.
 __device__ __forceinline__ bool fly(const Params& P, const DevProblem& pr, Particle& pt,
-                                    Stream& r, double& xi) {
+                                    Stream& r, double& xi, double a_uv) {
     const gbmc_geometry& g = pr.g;
     xi = r.next();
     pt.nflt = pt.nflt + 1;
@@ -543,8 +544,8 @@ __device__ __forceinline__ bool fly(const Params& P, const DevProblem& pr, Parti
     sp[1] = plane_span(nx, pt.u);
     if (lat) {
         const double* ctr = wall + g.n + 1;
-        cy = cylinder_of(pt.x - __ldg(ctr + pt.ci), pt.y - __ldg(ctr + pt.cj), pt.u, pt.v,
-                         g.radius, pt.inside != 0);
+        cy = cylinder_of(pt.x - __ldg(ctr + pt.ci), pt.y - __ldg(ctr + pt.cj), pt.u, pt.v, a_uv,
+                         pr.r2, pt.inside != 0);
         ny = (is_pos(pt.v) ? __ldg(wall + pt.cj + 1) : __ldg(wall + pt.cj)) - pt.y;
         nz = is_pos(pt.w) ? g.height - pt.z : 0.0 - pt.z;
         sp[0] = cylinder_span(cy);
@@ -847,6 +848,7 @@ __global__ void __launch_bounds__(256, 2) k_raytrace(Params P) {
     int32_t slot = 0;
     Stream r;
     int32_t flights = 0;
+    double a_uv = 0.0;
     double fw = 0.0;   // weight summed over this particle's flights
     // the lane's flight scores, summed over its particles of one problem
     int acc_prob = -1;
@@ -867,6 +869,7 @@ __global__ void __launch_bounds__(256, 2) k_raytrace(Params P) {
                     slot = q[idx];
                     pt = P.B.p[slot];
                     stream_of(P.probs[pt.prob], pt, r);
+                    a_uv = pt.u * pt.u + pt.v * pt.v;   // fixed until the particle collides
                     flights = 0;
                     fw = 0.0;
                     have = true;
@@ -882,7 +885,7 @@ __global__ void __launch_bounds__(256, 2) k_raytrace(Params P) {
         if (have) {
             const DevProblem& pr = P.probs[pt.prob];
             double xi;
-            bool col = fly(P, pr, pt, r, xi);
+            bool col = fly(P, pr, pt, r, xi, a_uv);
             ++flights;
             fw += pt.wgt;
             if (col) {
@@ -1052,7 +1055,7 @@ __global__ void __launch_bounds__(256) k_tail(Params P) {
             __syncwarp();     // the lanes' running-sum checkpoints, visible to lane 0
             if (lane == 0) {
                 double xi;
-                bool col = fly(P, pr, pt, r, xi);
+                bool col = fly(P, pr, pt, r, xi, pt.u * pt.u + pt.v * pt.v);
                 ++nf;
                 wf += pt.wgt;
                 if (col) {
