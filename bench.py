@@ -34,7 +34,7 @@ FP64_NOMINAL_TFLOPS = 1.25       # GB300 dense FP64 (recipe table)
 FP64_SLOTS_PER_MICRO = 9 + 9.2
 BRACKET_BYTES = {0: 32, 1: 16}    # E_j, E_j+1, s_j, s_j+1
 LOOKUP_IO_BYTES = 28              # per macro lookup: E 8, material 4, sigma_t and sigma_a 16
-ITER_KERNELS = 9                  # plan, source, 3 sort, 2 lookup (thread/warp mode), ray trace, collision
+ITER_KERNELS = 8                  # plan, source, 2 sort, 2 lookup (thread/warp mode), ray trace, collision
 
 WORKLOADS = {
     1: "infinite medium, 4 nuclides x 2000 log-spaced points, 1e5 particles/batch",

@@ -265,8 +265,8 @@ void free_bank(gbmc_ctx* c) {
     dfree(c->B.p);
     Queues& Q = c->Q;
     dfree(Q.lq[0]); dfree(Q.lq[1]); dfree(Q.aq[0]); dfree(Q.aq[1]);
-    dfree(Q.sq); dfree(Q.cq); dfree(Q.fq); dfree(Q.lqs); dfree(Q.keys);
-    dfree(Q.hist); dfree(Q.cursor); dfree(Q.btot);
+    dfree(Q.sq); dfree(Q.cq); dfree(Q.fq); dfree(Q.lqs); dfree(Q.keys[0]); dfree(Q.keys[1]);
+    dfree(Q.hist[0]); dfree(Q.hist[1]); dfree(Q.cursor); dfree(Q.btot);
     c->capacity = 0;
 }
 
@@ -280,14 +280,16 @@ int ensure_bank(gbmc_ctx* c, int32_t M) {
     rc |= dalloc(c, &Q.lq[0], n); rc |= dalloc(c, &Q.lq[1], n);
     rc |= dalloc(c, &Q.aq[0], n); rc |= dalloc(c, &Q.aq[1], n);
     rc |= dalloc(c, &Q.sq, n); rc |= dalloc(c, &Q.cq, n); rc |= dalloc(c, &Q.fq, n);
-    rc |= dalloc(c, &Q.lqs, n); rc |= dalloc(c, &Q.keys, n);
-    rc |= dalloc(c, &Q.hist, kSortBuckets); rc |= dalloc(c, &Q.cursor, kSortBuckets);
+    rc |= dalloc(c, &Q.lqs, n); rc |= dalloc(c, &Q.keys[0], n); rc |= dalloc(c, &Q.keys[1], n);
+    rc |= dalloc(c, &Q.hist[0], kSortBuckets); rc |= dalloc(c, &Q.hist[1], kSortBuckets);
+    rc |= dalloc(c, &Q.cursor, kSortBuckets);
     rc |= dalloc(c, &Q.btot, kSortBuckets / 1024);
     if (rc) {
         free_bank(c);
         return GBMC_ERR_OOM;
     }
-    CK(cudaMemset(Q.hist, 0, sizeof(uint32_t) * kSortBuckets));
+    CK(cudaMemset(Q.hist[0], 0, sizeof(uint32_t) * kSortBuckets));
+    CK(cudaMemset(Q.hist[1], 0, sizeof(uint32_t) * kSortBuckets));
     c->capacity = M;
     return GBMC_OK;
 }
@@ -1927,12 +1929,11 @@ extern "C" int gbmc_autotune(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* pr
         ++trials;
         if (t_ms < best_ms * keep) { best_ms = t_ms; best = o; }
     }
-    for (int32_t m : {1024, 65536, -1}) {
+    // the sort threshold (sorting itself stays on: its gain grows with the
+    // queue, and the probes' queues are the fraction's size)
+    for (int32_t m : {1024, 65536, 1 << 20}) {
         gbmc_options o = best;
-        if (m < 0)
-            o.sort = -1;
-        else
-            o.sort_min = m;
+        o.sort_min = m;
         double t;
         if ((rc = probe_ms(c, pr, s, o, &t))) return rc;
         ++trials;

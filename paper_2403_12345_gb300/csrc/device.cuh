@@ -120,8 +120,8 @@ struct Queues {
     int32_t* cq;        // collision queue
     int32_t* fq;        // free slots
     int32_t* lqs;       // lookup queue in (material, energy) order
-    uint32_t* keys;     // sort keys of lq
-    uint32_t* hist;     // [kSortBuckets] bucket counts
+    uint32_t* keys[2];  // sort keys of lq[b], written by the kernel that appends the entry
+    uint32_t* hist[2];  // [kSortBuckets] bucket counts of lq[b], counted at the append
     uint32_t* cursor;   // [kSortBuckets] bucket write positions (block-local)
     uint32_t* btot;     // [kSortBuckets / 1024] bucket-block totals
 };

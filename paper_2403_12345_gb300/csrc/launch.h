@@ -31,7 +31,7 @@ cudaError_t launch_bank(const Params& P, const LaunchCfg& L, cudaStream_t s);
 // (ev[0..8]; the lookup's two mode kernels share one interval), for
 // per-kernel device timing; the tail is timed separately.
 constexpr int kIterKernels = 8;
-constexpr int kIterLaunches = 9;   // kernels launched per iteration
+constexpr int kIterLaunches = 8;   // kernels launched per iteration
 constexpr int kTimedKernels = 9;   // + the tail
 cudaError_t launch_iteration_timed(const Params& P, const LaunchCfg& L, cudaStream_t s,
                                    cudaEvent_t* ev);

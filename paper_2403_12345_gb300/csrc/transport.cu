@@ -36,6 +36,41 @@ __device__ __forceinline__ void warp_append(int32_t* q, int32_t* count, int32_t 
     if (pred) q[base + __popc(m & lanemask_lt())] = slot;
 }
 
+// ---------------------------------------------------------------- sort keys at the append
+// Every kernel that appends a particle to a lookup queue already holds its
+// energy and material: it writes the particle's sort key beside the entry
+// and counts it in that queue's bucket histogram, so the sort needs no pass
+// over the particle records of its own.
+__device__ __forceinline__ uint32_t sort_key(const Params& P, double E, int32_t m);
+
+__device__ __forceinline__ void warp_count(uint32_t* hist, uint32_t key, bool valid) {
+    unsigned peers = __match_any_sync(kFull, valid ? key : 0xffffffffu);
+    int lane = threadIdx.x & 31;
+    if (valid && lane == __ffs(peers) - 1) atomicAdd(&hist[key], (uint32_t)__popc(peers));
+}
+
+// warp_append into lookup queue b with the entry's sort key (all 32 lanes).
+__device__ __forceinline__ void lookup_append(const Params& P, int b, int32_t* count, int32_t slot,
+                                              bool pred, double E, int32_t m) {
+    unsigned msk = __ballot_sync(kFull, pred);
+    if (msk == 0) return;
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(msk) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(count, __popc(msk));
+    base = __shfl_sync(kFull, base, leader);
+    uint32_t key = 0;
+    if (pred) {
+        int pos = base + __popc(msk & lanemask_lt());
+        P.Q.lq[b][pos] = slot;
+        if (P.sort) {
+            key = sort_key(P, E, m);
+            P.Q.keys[b][pos] = key;
+        }
+    }
+    if (P.sort) warp_count(P.Q.hist[b], key, pred);
+}
+
 // ---------------------------------------------------------------- scalar tallies
 // Per-block accumulation of the scalar tallies in shared memory (one entry
 // per problem slot and tally kind), flushed with one global atomic per entry
@@ -125,6 +160,13 @@ __global__ void k_init_run(Params P) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M;
          i += (int64_t)gridDim.x * blockDim.x)
         P.Q.fq[i] = (int32_t)i;
+    // the lookup queues' bucket counts start empty
+    if (P.sort)
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < kSortBuckets;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            P.Q.hist[0][i] = 0u;
+            P.Q.hist[1][i] = 0u;
+        }
 }
 
 // One thread: close the previous iteration, plan this one.
@@ -218,11 +260,14 @@ __global__ void __launch_bounds__(256) k_source(Params P) {
     GBMC_WARP_LOOP(idx, valid, n) {
         int prob = 0;
         bool primary = valid && idx >= nch;
+        uint32_t key = 0;   // the entry's sort key (see lookup_append)
         if (valid && !primary) {
             // a split copy: its state was made by the split
             int32_t slot = P.Q.fq[fb + idx];
-            P.B.p[slot] = P.child[cb + idx];
+            const Particle& ch = P.child[cb + idx];
+            P.B.p[slot] = ch;
             P.Q.lq[cur][lb + idx] = slot;
+            if (P.sort) key = sort_key(P, ch.E, ch.mat);
         }
         if (primary) {
             int32_t slot = P.Q.fq[fb + idx];
@@ -291,6 +336,11 @@ __global__ void __launch_bounds__(256) k_source(Params P) {
             rec.hid = (uint64_t)(pr.first_id + (gi - pr.start));
             P.B.p[slot] = rec;
             P.Q.lq[cur][lb + idx] = slot;
+            if (P.sort) key = sort_key(P, rec.E, rec.mat);
+        }
+        if (P.sort) {
+            if (valid) P.Q.keys[cur][lb + idx] = key;
+            warp_count(P.Q.hist[cur], key, valid);
         }
         sc.add(P.Y, primary, prob, GBMC_S_HISTORY, 1.0, 1ull);
     }
@@ -312,27 +362,7 @@ __device__ __forceinline__ uint32_t sort_key(const Params& P, double E, int32_t 
     return (((uint32_t)m << P.bpm_log2) | (uint32_t)b) & (uint32_t)(kSortBuckets - 1);
 }
 
-__device__ __forceinline__ void warp_count(uint32_t* hist, uint32_t key, bool valid) {
-    unsigned peers = __match_any_sync(kFull, valid ? key : 0xffffffffu);
-    int lane = threadIdx.x & 31;
-    if (valid && lane == __ffs(peers) - 1) atomicAdd(&hist[key], (uint32_t)__popc(peers));
-}
 
-__global__ void __launch_bounds__(256) k_sort_keys(Params P) {
-    const Ctl* c = P.ctl;
-    if (!c->sorted) return;
-    int32_t n = c->lookup_n;
-    const int32_t* q = P.Q.lq[c->cur];
-    GBMC_WARP_LOOP(idx, valid, n) {
-        uint32_t key = 0;
-        if (valid) {
-            int32_t slot = q[idx];
-            key = sort_key(P, P.B.p[slot].E, P.B.p[slot].mat);
-            P.Q.keys[idx] = key;
-        }
-        warp_count(P.Q.hist, key, valid);
-    }
-}
 
 // Exclusive scan of the bucket counts, in kScanBlocks blocks of 1024
 // buckets: each block writes block-local offsets into cursor and its total
@@ -384,9 +414,16 @@ __device__ __forceinline__ void block_offsets(const uint32_t* btot, uint32_t* bo
     __syncthreads();
 }
 
+// Bucket offsets of the current lookup queue's histogram (the histogram is
+// cleared for its queue's next use, also when this iteration does not sort).
 __global__ void __launch_bounds__(1024) k_sort_scan(Params P) {
-    if (!P.ctl->sorted) return;
-    scan_bucket_block(P.Q.hist, P.Q.cursor, P.Q.btot);
+    const Ctl* c = P.ctl;
+    uint32_t* hist = P.Q.hist[c->cur];
+    if (!c->sorted) {
+        hist[(int64_t)blockIdx.x * 1024 + threadIdx.x] = 0u;
+        return;
+    }
+    scan_bucket_block(hist, P.Q.cursor, P.Q.btot);
 }
 
 __device__ __forceinline__ void warp_place_off(uint32_t* cursor, const uint32_t* boff, uint32_t key,
@@ -409,7 +446,7 @@ __global__ void __launch_bounds__(256) k_sort_scatter(Params P) {
     int32_t n = c->lookup_n;
     const int32_t* q = P.Q.lq[c->cur];
     GBMC_WARP_LOOP(idx, valid, n) {
-        uint32_t key = valid ? P.Q.keys[idx] : 0u;
+        uint32_t key = valid ? P.Q.keys[c->cur][idx] : 0u;
         int32_t slot = valid ? q[idx] : 0;
         warp_place_off(P.Q.cursor, boff, key, valid, P.Q.lqs, slot);
     }
@@ -933,7 +970,7 @@ __global__ void __launch_bounds__(256, 2) k_raytrace(Params P) {
             sc.add(P.Y, dead && status == GBMC_STATUS_LIMIT, prob, GBMC_S_LIMIT, wgt, 1ull);
             warp_append(P.Q.fq, &c->n_free, slot, dead);
             warp_append(P.Q.cq, &c->n_cq, slot, fin && route == 1);
-            warp_append(P.Q.lq[nxt], &c->n_lq[nxt], slot, fin && route == 2);
+            lookup_append(P, nxt, &c->n_lq[nxt], slot, fin && route == 2, pt.E, pt.mat);
             if (fin) have = false;
         }
     }
@@ -963,6 +1000,8 @@ __global__ void __launch_bounds__(256, 2) k_collision(Params P) {
         int prob = 0;
         int status = 0;
         double wgt = 0.0;
+        double E1 = 0.0;   // energy and material after the collision (the next lookup's)
+        int32_t m1 = 0;
         WwOut wo{0, 0.0, 0.0};
         if (valid) {
             slot = P.Q.cq[idx];
@@ -990,6 +1029,8 @@ __global__ void __launch_bounds__(256, 2) k_collision(Params P) {
             status = collide<PREC>(P, pr, pt, slot, r, wo);
             P.B.p[slot] = pt;
             if (status) record_death(P, pt, status);
+            E1 = pt.E;
+            m1 = pt.mat;
         }
         bool dead = valid && status != 0;
         if (P.ww) {
@@ -1001,7 +1042,7 @@ __global__ void __launch_bounds__(256, 2) k_collision(Params P) {
         sc.add(P.Y, dead && status == GBMC_STATUS_CUTOFF, prob, GBMC_S_CUTOFF, wgt, 1ull);
         sc.add(P.Y, dead && status == GBMC_STATUS_LIMIT, prob, GBMC_S_LIMIT, wgt, 1ull);
         warp_append(P.Q.fq, &c->n_free, slot, dead);
-        warp_append(P.Q.lq[nxt], &c->n_lq[nxt], slot, valid && !dead);
+        lookup_append(P, nxt, &c->n_lq[nxt], slot, valid && !dead, E1, m1);
     }
     sc.flush(P.Y);
 }
@@ -1223,7 +1264,6 @@ cudaError_t launch_iteration(const Params& P, const LaunchCfg& L, cudaStream_t s
     k_plan<<<1, 32, 0, s>>>(P);
     k_source<<<L.grid, 256, 0, s>>>(P);
     if (P.sort) {
-        k_sort_keys<<<L.grid, 256, 0, s>>>(P);
         k_sort_scan<<<kScanBlocks, 1024, 0, s>>>(P);
         k_sort_scatter<<<L.grid, 256, 0, s>>>(P);
     }
@@ -1257,8 +1297,7 @@ cudaError_t launch_iteration_timed(const Params& P, const LaunchCfg& L, cudaStre
     cudaEventRecord(ev[1], s);
     k_source<<<L.grid, 256, 0, s>>>(P);
     cudaEventRecord(ev[2], s);
-    if (P.sort) k_sort_keys<<<L.grid, 256, 0, s>>>(P);
-    cudaEventRecord(ev[3], s);
+    cudaEventRecord(ev[3], s);   // keys and counts come with the appends: no key pass
     if (P.sort) k_sort_scan<<<kScanBlocks, 1024, 0, s>>>(P);
     cudaEventRecord(ev[4], s);
     if (P.sort) k_sort_scatter<<<L.grid, 256, 0, s>>>(P);
