@@ -30,8 +30,9 @@ HBM_FALLBACK_GBS = 6800.0
 FP64_NOMINAL_TFLOPS = 1.25       # GB300 dense FP64 (recipe table)
 # FP64-pipe work of one micro lookup in DFMA issue slots: 9 add/sub/mul plus
 # one division, which costs ~9.2 DFMA slots (measured: 65 G div/s vs 598 G
-# DFMA/s on this GPU)
+# DFMA/s on this GPU); the transport's lookups skip the two Sigma_a terms
 FP64_SLOTS_PER_MICRO = 9 + 9.2
+FP64_SLOTS_PER_MICRO_NO_SA = 7 + 9.2   # without Sigma_a (formed only for the absorption-rate tally)
 BRACKET_BYTES = {0: 32, 1: 16}    # E_j, E_j+1, s_j, s_j+1
 LOOKUP_IO_BYTES = 28              # per macro lookup: E 8, material 4, sigma_t and sigma_a 16
 ITER_KERNELS = 8                  # plan, source, 2 sort, 2 lookup (thread/warp mode), ray trace, collision
@@ -643,7 +644,7 @@ def main():
 
     tuned = None
     if args.autotune == 1 or (args.autotune < 0 and args.config in (2, 3, 4)):
-        tuned = ctx.autotune(problems(40_000), fraction=0.1, stream=stream)
+        tuned = ctx.autotune(problems(40_000), fraction=0.1 if n_geo > 1 else 0.3, stream=stream)
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     for w in range(args.warmup):
@@ -732,7 +733,7 @@ def main():
             "launches": lk_n, "avg_launch_ms": lk_ms / max(lk_n, 1),
             "algorithmic_bytes_per_launch": lk_bytes / max(lk_n, 1)}
     if args.precision == 0:
-        slots = pst["micro_lookups"] * FP64_SLOTS_PER_MICRO / (lk_ms * 1e-3)
+        slots = pst["micro_lookups"] * FP64_SLOTS_PER_MICRO_NO_SA / (lk_ms * 1e-3)
         alu_peak = FP64_NOMINAL_TFLOPS * 1e12 / 2
         if slots / alu_peak > roof["frac"]:
             roof.update({"bound": "alu", "achieved": slots / 1e9, "peak": alu_peak / 1e9,

@@ -520,6 +520,9 @@ __device__ __forceinline__ void brackets(const Tables& T, const NucIndex* nx,
     for (int u = 0; u < kIlp; ++u) pos[u] = (gp[u] - g) + lo[u];
 }
 
+// SA = false skips Sigma_a (sa is then 0): the transport needs it only for
+// the absorption-rate tally.
+template <bool SA = true>
 __device__ __forceinline__ void macro64(const Tables& T, int32_t m, double E, double& st,
                                         double& sa, double* cum = nullptr) {
     double at = 0.0, aa = 0.0;
@@ -541,7 +544,7 @@ __device__ __forceinline__ void macro64(const Tables& T, int32_t m, double E, do
                 int32_t i = __ldg(T.nuc_id + q + u);
                 double t = __ldg(T.density + q + u) * sig;
                 at = at + t;
-                aa = aa + t * __ldg(T.f_abs + i);
+                if (SA) aa = aa + t * __ldg(T.f_abs + i);
             }
             run[u] = at;
         }
@@ -552,6 +555,7 @@ __device__ __forceinline__ void macro64(const Tables& T, int32_t m, double E, do
     sa = aa;
 }
 
+template <bool SA = true>
 __device__ __forceinline__ void macro32(const Tables& T, int32_t m, double E, double& st,
                                         double& sa, float* cum = nullptr) {
     float at = 0.0f, aa = 0.0f;
@@ -580,7 +584,7 @@ __device__ __forceinline__ void macro32(const Tables& T, int32_t m, double E, do
                 float sig = p0[u].y + f * (p1[u].y - p0[u].y);
                 float t = d[u].density * sig;
                 at = at + t;
-                aa = aa + t * d[u].f_abs;
+                if (SA) aa = aa + t * d[u].f_abs;
             }
             run[u] = at;
         }
@@ -601,7 +605,7 @@ __device__ __forceinline__ void macro32(const Tables& T, int32_t m, double E, do
 // Used when the lookup queue is too short to keep the GPU busy with one
 // particle per thread (the per-particle nuclide loop is then a long serial
 // latency chain).
-template <int PREC>
+template <int PREC, bool SA = true>
 __device__ __forceinline__ void macro_warp(const Tables& T, int32_t m, double E, double& st,
                                            double& sa, void* cum, int64_t stride) {
     const unsigned full = 0xffffffffu;
@@ -614,12 +618,12 @@ __device__ __forceinline__ void macro_warp(const Tables& T, int32_t m, double E,
             if (c + lane < q1) {
                 int32_t i = __ldg(T.nuc_id + c + lane);
                 t = __ldg(T.density + c + lane) * micro64(T, i, E);
-                p = t * __ldg(T.f_abs + i);
+                if (SA) p = t * __ldg(T.f_abs + i);
             }
             int32_t kmax = q1 - c < 32 ? q1 - c : 32;
             for (int k = 0; k < kmax; ++k) {
                 at = at + __shfl_sync(full, t, k);
-                aa = aa + __shfl_sync(full, p, k);
+                if (SA) aa = aa + __shfl_sync(full, p, k);
                 if (cum && lane == k && ((c + k - q0) % kCumGroup == kCumGroup - 1 || c + k == q1 - 1))
                     ((double*)cum)[(int64_t)((c + k - q0) / kCumGroup) * stride] = at;
             }
@@ -633,12 +637,12 @@ __device__ __forceinline__ void macro_warp(const Tables& T, int32_t m, double E,
             if (c + lane < q1) {
                 const Desc32* dq = T.d32 + c + lane;
                 t = __ldg(&dq->density) * micro32(T, c + lane, E);
-                p = t * __ldg(&dq->f_abs);
+                if (SA) p = t * __ldg(&dq->f_abs);
             }
             int32_t kmax = q1 - c < 32 ? q1 - c : 32;
             for (int k = 0; k < kmax; ++k) {
                 at = at + __shfl_sync(full, t, k);
-                aa = aa + __shfl_sync(full, p, k);
+                if (SA) aa = aa + __shfl_sync(full, p, k);
                 if (cum && lane == k && ((c + k - q0) % kCumGroup == kCumGroup - 1 || c + k == q1 - 1))
                     ((float*)cum)[(int64_t)((c + k - q0) / kCumGroup) * stride] = at;
             }

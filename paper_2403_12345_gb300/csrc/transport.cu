@@ -454,7 +454,7 @@ __global__ void __launch_bounds__(256) k_sort_scatter(Params P) {
 
 // ---------------------------------------------------------------- lookup event
 
-template <int PREC>
+template <int PREC, bool SA>
 // Thread mode (long queues): one particle per thread.
 __global__ void __launch_bounds__(256, 3) k_lookup(Params P) {
     const Ctl* c = P.ctl;
@@ -471,11 +471,12 @@ __global__ void __launch_bounds__(256, 3) k_lookup(Params P) {
             int32_t m = P.B.p[slot].mat;
             double st, sa;
             if (PREC == GBMC_FP64)
-                macro64(P.T, m, E, st, sa, P.cum ? (double*)P.cum + slot * P.cum_stride : nullptr);
+                macro64<SA>(P.T, m, E, st, sa,
+                            P.cum ? (double*)P.cum + slot * P.cum_stride : nullptr);
             else
-                macro32(P.T, m, E, st, sa, P.cum ? (float*)P.cum + slot * P.cum_stride : nullptr);
+                macro32<SA>(P.T, m, E, st, sa, P.cum ? (float*)P.cum + slot * P.cum_stride : nullptr);
             P.B.p[slot].st = st;
-            P.B.p[slot].sa = sa;
+            if (SA) P.B.p[slot].sa = sa;
             aq[idx] = slot;
             micro += (unsigned long long)(__ldg(P.T.mat_off + m + 1) - __ldg(P.T.mat_off + m));
         }
@@ -485,7 +486,7 @@ __global__ void __launch_bounds__(256, 3) k_lookup(Params P) {
 }
 
 // Warp mode (short queues): one particle per warp.
-template <int PREC>
+template <int PREC, bool SA>
 __global__ void __launch_bounds__(256) k_lookup_warp(Params P) {
     const Ctl* c = P.ctl;
     int32_t n = c->lookup_n;
@@ -505,10 +506,10 @@ __global__ void __launch_bounds__(256) k_lookup_warp(Params P) {
         void* cum = P.cum ? (PREC == GBMC_FP64 ? (void*)((double*)P.cum + slot * P.cum_stride)
                                                : (void*)((float*)P.cum + slot * P.cum_stride))
                           : nullptr;
-        macro_warp<PREC>(P.T, m, E, st, sa, cum, 1);
+        macro_warp<PREC, SA>(P.T, m, E, st, sa, cum, 1);
         if (lane == 0) {
             P.B.p[slot].st = st;
-            P.B.p[slot].sa = sa;
+            if (SA) P.B.p[slot].sa = sa;
             aq[idx] = slot;
             micro += (unsigned long long)(__ldg(P.T.mat_off + m + 1) - __ldg(P.T.mat_off + m));
         }
@@ -1083,7 +1084,10 @@ __global__ void __launch_bounds__(256) k_tail(Params P) {
                                          ? (void*)((double*)P.cum + slot * P.cum_stride)
                                          : (void*)((float*)P.cum + slot * P.cum_stride))
                                   : nullptr;
-                macro_warp<PREC>(P.T, pt.mat, pt.E, st, sa, cum, 1);
+                if (P.Y.absrate)
+                    macro_warp<PREC, true>(P.T, pt.mat, pt.E, st, sa, cum, 1);
+                else
+                    macro_warp<PREC, false>(P.T, pt.mat, pt.E, st, sa, cum, 1);
                 pt.st = st;
                 pt.sa = sa;
                 if (lane == 0) {
@@ -1255,6 +1259,28 @@ cudaError_t launch_bank(const Params& P, const LaunchCfg& L, cudaStream_t s) {
 
 // ---------------------------------------------------------------- host launchers
 
+// The lookup's two mode kernels, with Sigma_a only when a tally needs it.
+static void launch_lookups(const Params& P, const LaunchCfg& L, cudaStream_t s) {
+    bool sa = P.Y.absrate != nullptr;
+    if (P.precision == GBMC_FP64) {
+        if (sa) {
+            k_lookup_warp<GBMC_FP64, true><<<L.grid_lookup, 256, 0, s>>>(P);
+            k_lookup<GBMC_FP64, true><<<L.grid_lookup, 256, 0, s>>>(P);
+        } else {
+            k_lookup_warp<GBMC_FP64, false><<<L.grid_lookup, 256, 0, s>>>(P);
+            k_lookup<GBMC_FP64, false><<<L.grid_lookup, 256, 0, s>>>(P);
+        }
+    } else {
+        if (sa) {
+            k_lookup_warp<GBMC_FP32, true><<<L.grid_lookup, 256, 0, s>>>(P);
+            k_lookup<GBMC_FP32, true><<<L.grid_lookup, 256, 0, s>>>(P);
+        } else {
+            k_lookup_warp<GBMC_FP32, false><<<L.grid_lookup, 256, 0, s>>>(P);
+            k_lookup<GBMC_FP32, false><<<L.grid_lookup, 256, 0, s>>>(P);
+        }
+    }
+}
+
 cudaError_t launch_init_run(const Params& P, const LaunchCfg& L, cudaStream_t s) {
     k_init_run<<<L.grid, 256, 0, s>>>(P);
     return cudaGetLastError();
@@ -1267,13 +1293,7 @@ cudaError_t launch_iteration(const Params& P, const LaunchCfg& L, cudaStream_t s
         k_sort_scan<<<kScanBlocks, 1024, 0, s>>>(P);
         k_sort_scatter<<<L.grid, 256, 0, s>>>(P);
     }
-    if (P.precision == GBMC_FP64) {
-        k_lookup_warp<GBMC_FP64><<<L.grid_lookup, 256, 0, s>>>(P);
-        k_lookup<GBMC_FP64><<<L.grid_lookup, 256, 0, s>>>(P);
-    } else {
-        k_lookup_warp<GBMC_FP32><<<L.grid_lookup, 256, 0, s>>>(P);
-        k_lookup<GBMC_FP32><<<L.grid_lookup, 256, 0, s>>>(P);
-    }
+    launch_lookups(P, L, s);
     k_raytrace<<<L.grid, 256, 0, s>>>(P);
     if (P.precision == GBMC_FP64)
         k_collision<GBMC_FP64><<<L.grid, 256, 0, s>>>(P);
@@ -1302,13 +1322,7 @@ cudaError_t launch_iteration_timed(const Params& P, const LaunchCfg& L, cudaStre
     cudaEventRecord(ev[4], s);
     if (P.sort) k_sort_scatter<<<L.grid, 256, 0, s>>>(P);
     cudaEventRecord(ev[5], s);
-    if (P.precision == GBMC_FP64) {
-        k_lookup_warp<GBMC_FP64><<<L.grid_lookup, 256, 0, s>>>(P);
-        k_lookup<GBMC_FP64><<<L.grid_lookup, 256, 0, s>>>(P);
-    } else {
-        k_lookup_warp<GBMC_FP32><<<L.grid_lookup, 256, 0, s>>>(P);
-        k_lookup<GBMC_FP32><<<L.grid_lookup, 256, 0, s>>>(P);
-    }
+    launch_lookups(P, L, s);
     cudaEventRecord(ev[6], s);
     k_raytrace<<<L.grid, 256, 0, s>>>(P);
     cudaEventRecord(ev[7], s);
