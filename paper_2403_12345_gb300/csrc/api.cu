@@ -298,8 +298,10 @@ int ensure_bank(gbmc_ctx* c, int32_t M) {
 // material rounded up to 8 (rows start on 32-byte boundaries and the lookup
 // stores 4 sums at a time), in the table precision.  Above kCumBudget bytes
 // the collision recomputes instead.
-// checkpoints per slot: one per kCumGroup entries of the largest material
+// running-sum entries per slot: binary64 every sum of the largest material
+// (rounded up to the lookup's groups of 4), binary32 one per kCumGroup
 int64_t cum_row(const gbmc_ctx* c) {
+    if (c->opt.precision == GBMC_FP64) return ((int64_t)c->max_nuc_per_mat + 3) / 4 * 4;
     return ((int64_t)c->max_nuc_per_mat + kCumGroup - 1) / kCumGroup;
 }
 

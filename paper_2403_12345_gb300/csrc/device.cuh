@@ -322,9 +322,14 @@ __device__ __forceinline__ double ln_series(double x) {
 }
 
 // ---------------------------------------------------------------- lookup
-// The lookup stores the running sum after every kCumGroup entries of the
-// material (checkpoints); the collision recomputes at most kCumGroup terms.
-constexpr int kCumGroup = 4;
+// The lookup stores the running sum after every cum_group<PREC>() entries of
+// the material (checkpoints); the collision recomputes at most that many
+// terms.  binary32 tables keep one checkpoint per four entries (a quarter of
+// the stores); binary64 tables keep every sum, since recomputing a binary64
+// term costs a division on the scarce binary64 units.
+constexpr int kCumGroup = 4;   // binary32
+template <int PREC>
+__host__ __device__ constexpr int cum_group() { return PREC == GBMC_FP64 ? 1 : kCumGroup; }
 // Bracket search: the largest j in [0, n-2] with grid[j] <= E.  Positive IEEE
 // values order like their bit patterns, so every comparison runs on the
 // integer pipe (binary64 compares would occupy the scarce FP64 units).
@@ -482,7 +487,7 @@ __device__ __forceinline__ float micro32(const Tables& T, int32_t q, double E) {
 // independent chains of dependent loads in flight per thread); the terms are
 // then formed and added strictly in the listed order.
 constexpr int kIlp = 4;
-static_assert(kIlp == kCumGroup, "one checkpoint per lock-step group");
+static_assert(kIlp == 4, "the running sums are stored four at a time");
 
 template <class U>
 __device__ __forceinline__ void brackets(const Tables& T, const NucIndex* nx,
@@ -548,8 +553,13 @@ __device__ __forceinline__ void macro64(const Tables& T, int32_t m, double E, do
             }
             run[u] = at;
         }
-        // the running sum after each group of kCumGroup entries
-        if (cum) cum[(q - q0) / kCumGroup] = run[kIlp - 1];
+        // every running sum (binary64 tables keep them all); the row holds the
+        // material's count rounded up to 4, so whole groups are written
+        if (cum) {
+            double2* d = reinterpret_cast<double2*>(cum + (q - q0));
+            d[0] = make_double2(run[0], run[1]);
+            d[1] = make_double2(run[2], run[3]);
+        }
     }
     st = at;
     sa = aa;
@@ -624,8 +634,7 @@ __device__ __forceinline__ void macro_warp(const Tables& T, int32_t m, double E,
             for (int k = 0; k < kmax; ++k) {
                 at = at + __shfl_sync(full, t, k);
                 if (SA) aa = aa + __shfl_sync(full, p, k);
-                if (cum && lane == k && ((c + k - q0) % kCumGroup == kCumGroup - 1 || c + k == q1 - 1))
-                    ((double*)cum)[(int64_t)((c + k - q0) / kCumGroup) * stride] = at;
+                if (cum && lane == k) ((double*)cum)[(int64_t)(c + k - q0) * stride] = at;
             }
         }
         st = at;
@@ -683,7 +692,7 @@ __device__ __forceinline__ int32_t pick_nuclide(const Tables& T, int precision, 
 }
 
 // The same choice from the lookup's checkpoints (cum[g * stride]: the
-// running sum after entry kCumGroup g + kCumGroup - 1, non-decreasing in g):
+// running sum after entry G g + G - 1, G = cum_group<PREC>(), non-decreasing in g):
 // the first group whose checkpoint exceeds the target holds the nuclide; its
 // terms are recomputed exactly as the lookup formed them and added to the
 // previous checkpoint in the listed order, so every running sum, and hence
@@ -692,8 +701,9 @@ __device__ __forceinline__ int32_t pick_nuclide(const Tables& T, int precision, 
 template <int PREC>
 __device__ __forceinline__ int32_t pick_from_sums(const Tables& T, int32_t m, const void* cum,
                                                   int64_t stride, double E, double target) {
+    constexpr int G = cum_group<PREC>();
     int32_t q0 = __ldg(T.mat_off + m), nq = __ldg(T.mat_off + m + 1) - q0;
-    int32_t ng = (nq + kCumGroup - 1) / kCumGroup;
+    int32_t ng = (nq + G - 1) / G;
     const double* c64 = (const double*)cum;
     const float* c32 = (const float*)cum;
     int32_t lo = 0, hi = ng;
@@ -706,7 +716,8 @@ __device__ __forceinline__ int32_t pick_from_sums(const Tables& T, int32_t m, co
             lo = mid + 1;
     }
     if (lo >= ng) return -1;
-    int32_t k0 = lo * kCumGroup, k1 = min(k0 + kCumGroup, nq);
+    if (G == 1) return __ldg(T.nuc_id + q0 + lo);   // every sum stored: no recomputation
+    int32_t k0 = lo * G, k1 = min(k0 + G, nq);
     if (PREC == GBMC_FP64) {
         double at = lo > 0 ? c64[(int64_t)(lo - 1) * stride] : 0.0;
         for (int32_t k = k0; k < k1; ++k) {
