@@ -28,11 +28,12 @@ import synth  # noqa: E402
 
 HBM_FALLBACK_GBS = 6800.0
 FP64_NOMINAL_TFLOPS = 1.25       # GB300 dense FP64 (recipe table)
-# FP64-pipe work of one micro lookup in DFMA issue slots: 9 add/sub/mul plus
-# one division, which costs ~9.2 DFMA slots (measured: 65 G div/s vs 598 G
-# DFMA/s on this GPU); the transport's lookups skip the two Sigma_a terms
-FP64_SLOTS_PER_MICRO = 9 + 9.2
-FP64_SLOTS_PER_MICRO_NO_SA = 7 + 9.2   # without Sigma_a (formed only for the absorption-rate tally)
+# FP64-pipe work of one micro lookup in DFMA issue slots: 9 add/sub/mul.  The
+# interpolation factor's division runs on the integer units (a correctly
+# rounded quotient from a fixed-point reciprocal), so it takes no FP64 slot;
+# the transport's lookups skip the two Sigma_a terms
+FP64_SLOTS_PER_MICRO = 9
+FP64_SLOTS_PER_MICRO_NO_SA = 7   # without Sigma_a (formed only for the absorption-rate tally)
 BRACKET_BYTES = {0: 32, 1: 16}    # E_j, E_j+1, s_j, s_j+1
 LOOKUP_IO_BYTES = 28              # per macro lookup: E 8, material 4, sigma_t and sigma_a 16
 ITER_KERNELS = 8                  # plan, source, 2 sort, 2 lookup (thread/warp mode), ray trace, collision

@@ -273,6 +273,17 @@ int gbmc_read_bank(gbmc_ctx *ctx, double *xyz, int64_t n_cap, int64_t *n_out);
  * share one bank start exactly the histories of one run.  Synchronizes. */
 int gbmc_set_source_bank(gbmc_ctx *ctx, const double *xyz, int64_t n, int64_t n_total);
 
+/* Self-check of the library's binary64 division on the integer units
+ * (used where the kernels divide; the binary64 units are this GPU's scarce
+ * resource): n operand pairs from a seeded counter-based stream -- random
+ * significands and signs, exponents across and beyond the normal range,
+ * the significand patterns where rounding is decided, zeros, infinities and
+ * NaNs -- each quotient compared bit for bit with the hardware binary64
+ * division.  *n_bad = the number that differ (0 expected); first_bad (HOST,
+ * 2 doubles, may be NULL) = the first differing pair.  Synchronous. */
+int gbmc_check_division(gbmc_ctx *ctx, int64_t n, uint64_t seed, int64_t *n_bad,
+                        double *first_bad);
+
 /* Track-length absorption-rate tally (reaction-rate tally; the next step
  * after the lookup and tally of Sec. 2 "Tallying", which says tallies are
  * scored in active batches): for every flight segment of length d,

@@ -1418,6 +1418,37 @@ int gbmc_set_source_bank(gbmc_ctx* c, const double* xyz, int64_t n, int64_t n_to
     return GBMC_OK;
 }
 
+int gbmc_check_division(gbmc_ctx* c, int64_t n, uint64_t seed, int64_t* n_bad,
+                        double* first_bad) {
+    if (!c || !n_bad || n < 0) return GBMC_ERR_INVALID_ARG;
+    int rc = set_device(c);
+    if (rc) return rc;
+    unsigned long long* d_bad = nullptr;
+    double* d_first = nullptr;
+    if ((rc = dalloc(c, &d_bad, 1))) return rc;
+    if ((rc = dalloc(c, &d_first, 2))) {
+        dfree(d_bad);
+        return rc;
+    }
+    cudaError_t e = cudaMemset(d_bad, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(d_first, 0, 2 * sizeof(double));
+    if (e == cudaSuccess) e = launch_check_division(n, seed, d_bad, d_first, c->sms, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    unsigned long long nb = 0;
+    double fb[2] = {0.0, 0.0};
+    if (e == cudaSuccess) e = cudaMemcpy(&nb, d_bad, sizeof nb, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(fb, d_first, sizeof fb, cudaMemcpyDeviceToHost);
+    dfree(d_bad);
+    dfree(d_first);
+    if (e != cudaSuccess) return fail(c, GBMC_ERR_CUDA, "division check: %s", cudaGetErrorString(e));
+    *n_bad = (int64_t)nb;
+    if (first_bad) {
+        first_bad[0] = fb[0];
+        first_bad[1] = fb[1];
+    }
+    return GBMC_OK;
+}
+
 int gbmc_read_outcomes(gbmc_ctx* c, int32_t slot, int64_t first, int64_t n, int32_t* n_coll,
                        int8_t* status, int32_t* n_flights, uint32_t* n_draws, double* E, double* x,
                        double* y, double* z) {

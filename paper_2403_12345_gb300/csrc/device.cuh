@@ -288,6 +288,81 @@ struct Stream {
     }
 };
 
+// ---------------------------------------------------------------- division on the integer units
+// Correctly rounded binary64 quotient q = RN(a / b) computed with integer
+// instructions only, for finite normal a, b (or a = 0) with a normal
+// quotient; anything else falls back to the binary64 division.  On this GPU
+// a binary64 division occupies the scarce binary64 pipe for ~9 fused
+// multiply-add slots, while the integer pipes idle in the kernels that divide.
+//
+// With significands A, B in [2^52, 2^53) the quotient's significand comes
+// from Q = floor(R 2^64 / d), d = B 2^11 in [2^63, 2^64), R = A (A >= B) or
+// 2A (A < B), so Q lies in [2^53, 2^54): Q >> 1 are its 53 bits, Q & 1 the
+// round bit and a nonzero remainder the sticky bit.  Q is estimated with a
+// fixed-point reciprocal 2^126 / d (binary32 seed, two Newton steps), then
+// made exact by the 128-bit remainder R 2^64 - Q d (division by an
+// invariant integer through a precomputed reciprocal, as in Moller and
+// Granlund, IEEE Trans. Computers 60(2), 2011).
+__device__ __forceinline__ double div_rn(double a, double b) {
+    const unsigned long long ua = (unsigned long long)__double_as_longlong(a);
+    const unsigned long long ub = (unsigned long long)__double_as_longlong(b);
+    const unsigned long long sign = (ua ^ ub) & 0x8000000000000000ull;
+    const int ea = (int)((ua >> 52) & 0x7ff), eb = (int)((ub >> 52) & 0x7ff);
+    const bool a0 = (ua << 1) == 0ull;
+    if (eb == 0 || eb == 0x7ff || ((ea == 0 || ea == 0x7ff) && !a0)) return a / b;
+    if (a0) return __longlong_as_double((long long)sign);
+    const unsigned long long M = (1ull << 52) - 1ull;
+    const unsigned long long A = (ua & M) | (1ull << 52), B = (ub & M) | (1ull << 52);
+    const bool ge = A >= B;
+    const unsigned long long R = ge ? A : (A << 1);
+    const unsigned long long d = B << 11;
+    // reciprocal y ~ 2^126 / d in (2^62, 2^63]: binary32 seed from d's top 24
+    // bits (about 23 correct bits), then two Newton steps y += y e / 2^126,
+    // e = 2^126 - d y, in 64-bit fixed point (within one unit afterwards)
+    float w = __frcp_rn((float)(unsigned)(d >> 40)) * 16777216.0f;   // 2^64 / d, in (1, 2]
+    unsigned long long y = (unsigned long long)(unsigned)(w * 1073741824.0f) << 32;
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        unsigned long long lo = d * y, hi = __umul64hi(d, y);
+        long long eh = (long long)((1ull << 62) - hi - (lo != 0ull ? 1ull : 0ull));
+        unsigned long long el = 0ull - lo;
+        unsigned long long ae = (unsigned long long)(eh < 0 ? -eh : eh);
+        unsigned long long mag = (__umul64hi(y, ae) << 2) | ((y * ae) >> 62);
+        long long corr = eh < 0 ? -(long long)mag : (long long)mag;
+        corr += (long long)(__umul64hi(y, el) >> 62);
+        y = (unsigned long long)((long long)y + corr);
+    }
+    // quotient estimate R 2^64 / d = (4 R) y / 2^64 and exact correction by
+    // the remainder R 2^64 - Q d (at most a few steps)
+    unsigned long long Q = __umul64hi(R << 2, y);
+    unsigned long long qlo = Q * d, qhi = __umul64hi(Q, d);
+    unsigned long long rlo = 0ull - qlo;
+    long long rhi = (long long)(R - qhi - (qlo != 0ull ? 1ull : 0ull));
+#pragma unroll 1
+    for (int k = 0; k < 4 && rhi < 0; ++k) {   // remainder negative: Q too large
+        --Q;
+        unsigned long long t = rlo + d;
+        rhi += (t < rlo) ? 1 : 0;
+        rlo = t;
+    }
+#pragma unroll 1
+    for (int k = 0; k < 4 && (rhi > 0 || (rhi == 0 && rlo >= d)); ++k) {   // remainder >= d
+        ++Q;
+        rhi -= (rlo < d) ? 1 : 0;
+        rlo -= d;
+    }
+    if (rhi != 0 || rlo >= d || Q < (1ull << 53) || Q >= (1ull << 54)) return a / b;   // not reached
+    unsigned long long m = Q >> 1;
+    if ((Q & 1ull) && (rlo != 0ull || (m & 1ull))) ++m;   // to nearest, ties to even
+    int e = ea - eb + (ge ? 1023 : 1022);
+    if (m == (1ull << 53)) {
+        m >>= 1;
+        ++e;
+    }
+    if (e < 1 || e > 2046) return a / b;   // subnormal or overflowing quotient
+    return __longlong_as_double((long long)(sign | ((unsigned long long)e << 52) | (m & M)));
+}
+
 // ---------------------------------------------------------------- logarithm
 // ln x for positive normal x: x = 2^e m with m in (sqrt(2)/2, sqrt(2)];
 // ln m = 2 atanh(s), s = (m - 1)/(m + 1), as the series
@@ -388,7 +463,7 @@ __device__ __forceinline__ double micro64(const Tables& T, int32_t i, double E) 
     int64_t k = d.off + bracket_in(g, lo, hi, eb);
     double e0 = __ldg(T.e64 + k), e1 = __ldg(T.e64 + k + 1);
     double s0 = __ldg(T.s64 + k), s1 = __ldg(T.s64 + k + 1);
-    double f = (E - e0) / (e1 - e0);
+    double f = div_rn(E - e0, e1 - e0);
     return s0 + f * (s1 - s0);
 }
 
@@ -544,7 +619,7 @@ __device__ __forceinline__ void macro64(const Tables& T, int32_t m, double E, do
                 int64_t k = pos[u];
                 double e0 = __ldg(T.e64 + k), e1 = __ldg(T.e64 + k + 1);
                 double s0 = __ldg(T.s64 + k), s1 = __ldg(T.s64 + k + 1);
-                double f = (E - e0) / (e1 - e0);
+                double f = div_rn(E - e0, e1 - e0);
                 double sig = s0 + f * (s1 - s0);
                 int32_t i = __ldg(T.nuc_id + q + u);
                 double t = __ldg(T.density + q + u) * sig;

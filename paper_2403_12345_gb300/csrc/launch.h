@@ -23,6 +23,12 @@ cudaError_t launch_iteration(const Params& P, const LaunchCfg& L, cudaStream_t s
 // stopped early (a no-op otherwise).
 cudaError_t launch_tail(const Params& P, const LaunchCfg& L, cudaStream_t s);
 
+// Self-check of the integer-pipe division (div_rn) against the binary64
+// division on n drawn operand pairs: *bad counts differing quotients, first
+// holds the first such pair.
+cudaError_t launch_check_division(int64_t n, uint64_t seed, unsigned long long* bad,
+                                  double* first, int sms, cudaStream_t s);
+
 // k-eigenvalue: compacts the run's per-history fission-site slots into
 // P.bank_out (history order), the size into *P.bank_size.
 cudaError_t launch_bank(const Params& P, const LaunchCfg& L, cudaStream_t s);

@@ -1257,6 +1257,57 @@ cudaError_t launch_bank(const Params& P, const LaunchCfg& L, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- division self-check
+// div_rn against the binary64 division on n operand pairs drawn from one
+// Philox stream: random significands and signs, exponents over the whole
+// normal range and near it, and the significand patterns where rounding is
+// decided (equal, adjacent, all ones, powers of two), zeros and specials.
+__device__ __forceinline__ double check_operand(uint64_t w, uint64_t s2) {
+    uint64_t sig = w & ((1ull << 52) - 1ull);
+    switch ((int)(s2 & 7u)) {
+        case 0: sig = 0ull; break;                       // power of two
+        case 1: sig = (1ull << 52) - 1ull; break;        // all ones
+        case 2: sig &= 0xFFull; break;                   // just above a power of two
+        case 3: sig |= (1ull << 52) - 256ull; break;     // just below
+        default: break;
+    }
+    uint64_t e;
+    switch ((int)((s2 >> 3) & 7u)) {
+        case 0: e = (s2 >> 8) % 2047ull; break;          // any, incl. subnormal, inf, nan
+        case 1: e = 1ull + (s2 >> 8) % 60ull; break;     // smallest normals
+        case 2: e = 2046ull - (s2 >> 8) % 60ull; break;  // largest normals
+        default: e = 1023ull - 80ull + (s2 >> 8) % 160ull; break;
+    }
+    if (((s2 >> 20) & 63u) == 0u) return 0.0;
+    return __longlong_as_double((long long)(((s2 >> 30) & 1ull) << 63 | e << 52 | sig));
+}
+
+__global__ void k_check_division(int64_t n, uint64_t seed, unsigned long long* bad,
+                                 double* first) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        Philox h = philox4x64_10((uint64_t)i, 0, 0, 0, seed, 0x0D1F1DE5ull);
+        double a = check_operand(h.c0, h.c2);
+        double b = check_operand(h.c1, h.c3);
+        if ((h.c2 >> 40 & 15u) == 0u) b = __longlong_as_double(__double_as_longlong(a) + (long long)(h.c3 >> 60) - 8);
+        double q = div_rn(a, b), r = a / b;
+        bool same = __double_as_longlong(q) == __double_as_longlong(r) || (q != q && r != r);
+        if (!same) {
+            unsigned long long k = atomicAdd(bad, 1ull);
+            if (k == 0) {
+                first[0] = a;
+                first[1] = b;
+            }
+        }
+    }
+}
+
+cudaError_t launch_check_division(int64_t n, uint64_t seed, unsigned long long* bad,
+                                  double* first, int sms, cudaStream_t s) {
+    k_check_division<<<sms * 8, 256, 0, s>>>(n, seed, bad, first);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- host launchers
 
 // The lookup's two mode kernels, with Sigma_a only when a tally needs it.

@@ -40,7 +40,8 @@ EXPORTS = ["gbmc_default_options", "gbmc_create", "gbmc_destroy", "gbmc_last_err
            "gbmc_mesh_features", "gbmc_weight_windows_from_net", "gbmc_importance_record",
            "gbmc_importance_accumulate", "gbmc_importance_training_set",
            "gbmc_get_weight_windows", "gbmc_set_reaction_tally", "gbmc_read_reaction_tally",
-           "gbmc_load_fission", "gbmc_set_eigen", "gbmc_read_bank", "gbmc_set_source_bank"]
+           "gbmc_load_fission", "gbmc_set_eigen", "gbmc_read_bank", "gbmc_set_source_bank",
+           "gbmc_check_division"]
 MLP_HIDDEN = 64
 MLP_NPARAM = 4545
 NOALLOC_MAX_QUERIES = 1 << 20
@@ -123,6 +124,8 @@ def lib():
                                         _P(C.c_int64), _P(C.c_double)]
         L.gbmc_set_reaction_tally.argtypes = [vp, C.c_int32]
         L.gbmc_load_fission.argtypes = [vp, C.c_int32, _P(C.c_double), _P(C.c_double)]
+        L.gbmc_check_division.argtypes = [vp, C.c_int64, C.c_uint64, _P(C.c_int64),
+                                          _P(C.c_double)]
         L.gbmc_set_eigen.argtypes = [vp, C.c_double, C.c_int32]
         L.gbmc_read_bank.argtypes = [vp, _P(C.c_double), C.c_int64, _P(C.c_int64)]
         L.gbmc_set_source_bank.argtypes = [vp, _P(C.c_double), C.c_int64, C.c_int64]
@@ -457,6 +460,14 @@ class Context:
         else:
             a = _arr(xyz, np.float64).reshape(-1, 3)
             self._ck(lib().gbmc_set_source_bank(self._h, _p(a, C.c_double), len(a), int(n_total)))
+
+    def check_division(self, n: int, seed: int = 1):
+        """(quotients that differ from the hardware division, first such pair)."""
+        bad = C.c_int64()
+        first = np.zeros(2)
+        self._ck(lib().gbmc_check_division(self._h, int(n), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                           C.byref(bad), _p(first, C.c_double)))
+        return bad.value, first
 
     def set_reaction_tally(self, on: bool = True):
         self._ck(lib().gbmc_set_reaction_tally(self._h, 1 if on else 0))
