@@ -28,12 +28,13 @@ import synth  # noqa: E402
 
 HBM_FALLBACK_GBS = 6800.0
 FP64_NOMINAL_TFLOPS = 1.25       # GB300 dense FP64 (recipe table)
-# FP64-pipe work of one micro lookup in DFMA issue slots: 9 add/sub/mul.  The
-# interpolation factor's division runs on the integer units (a correctly
-# rounded quotient from a fixed-point reciprocal), so it takes no FP64 slot;
-# the transport's lookups skip the two Sigma_a terms
-FP64_SLOTS_PER_MICRO = 9
-FP64_SLOTS_PER_MICRO_NO_SA = 7   # without Sigma_a (formed only for the absorption-rate tally)
+# FP64-pipe work of one micro lookup in DFMA issue slots.  Of the
+# interpolation's binary64 steps, E_k+1 - E_k and s_k+1 - s_k come from the
+# interval records, E - E_k and the division run on the integer units
+# (correctly rounded), so f (s_k+1 - s_k), s_k + ..., N sigma and the running
+# sum remain, plus two for Sigma_a (the transport's lookups skip those)
+FP64_SLOTS_PER_MICRO = 6
+FP64_SLOTS_PER_MICRO_NO_SA = 4   # without Sigma_a (formed only for the absorption-rate tally)
 BRACKET_BYTES = {0: 32, 1: 16}    # E_j, E_j+1, s_j, s_j+1
 LOOKUP_IO_BYTES = 28              # per macro lookup: E 8, material 4, sigma_t and sigma_a 16
 ITER_KERNELS = 8                  # plan, source, 2 sort, 2 lookup (thread/warp mode), ray trace, collision

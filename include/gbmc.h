@@ -157,11 +157,12 @@ typedef struct {
 } gbmc_stats;
 
 /* Per-kernel device time of one profiled run (gbmc_profile_problems). */
-#define GBMC_NKERNELS 9
+#define GBMC_NKERNELS 8
 typedef struct {
-    /* kernels: 0 plan, 1 source, 2 sort keys, 3 sort scan, 4 sort scatter,
-       5 lookup, 6 ray trace (advance and surface events), 7 collision,
-       8 tail (finishes the last particles in flight) */
+    /* kernels: 0 plan, 1 source, 2 sort scan (bucket offsets from the
+       counts the queue appends keep), 3 sort scatter, 4 lookup, 5 ray trace
+       (advance and surface events), 6 collision, 7 tail (finishes the last
+       particles in flight) */
     double ms[GBMC_NKERNELS];        /* summed device time (CUDA events) */
     int64_t launches[GBMC_NKERNELS]; /* launches of each kernel */
 } gbmc_kernel_times;
@@ -273,15 +274,23 @@ int gbmc_read_bank(gbmc_ctx *ctx, double *xyz, int64_t n_cap, int64_t *n_out);
  * share one bank start exactly the histories of one run.  Synchronizes. */
 int gbmc_set_source_bank(gbmc_ctx *ctx, const double *xyz, int64_t n, int64_t n_total);
 
-/* Self-check of the library's binary64 division on the integer units
- * (used where the kernels divide; the binary64 units are this GPU's scarce
- * resource): n operand pairs from a seeded counter-based stream -- random
- * significands and signs, exponents across and beyond the normal range,
- * the significand patterns where rounding is decided, zeros, infinities and
- * NaNs -- each quotient compared bit for bit with the hardware binary64
- * division.  *n_bad = the number that differ (0 expected); first_bad (HOST,
- * 2 doubles, may be NULL) = the first differing pair.  Synchronous. */
-int gbmc_check_division(gbmc_ctx *ctx, int64_t n, uint64_t seed, int64_t *n_bad,
+/* Self-checks of the library's binary64 division on the integer units
+ * (the binary64 units are this GPU's scarce resource), each result compared
+ * bit for bit with the hardware binary64 operation, on n samples from a
+ * seeded counter-based stream:
+ *   kind 0: div_rn(a, b) against a / b -- random significands and signs,
+ *           exponents across and beyond the normal range, the significand
+ *           patterns where rounding is decided, zeros, infinities, NaNs;
+ *   kind 1: the lookup's interpolation factor (E - e0) / de from an
+ *           interval record (de = e1 - e0 and its fixed-point reciprocal,
+ *           as the binary64 tables store them) against the same expression
+ *           in binary64 -- 65536 grid-like intervals (widths 2^-52 e0 to
+ *           2^14 e0, some of zero width), E at, next to, inside, below and
+ *           far above the interval.
+ * *n_bad = the number that differ (0 expected); first_bad (HOST, 2 doubles,
+ * may be NULL) = the first differing operands (a, b), or (E, e0).  Errors:
+ * INVALID_ARG for kind not 0/1 or n < 0.  Synchronous. */
+int gbmc_check_division(gbmc_ctx *ctx, int32_t kind, int64_t n, uint64_t seed, int64_t *n_bad,
                         double *first_bad);
 
 /* Track-length absorption-rate tally (reaction-rate tally; the next step

@@ -52,7 +52,8 @@ struct gbmc_ctx {
     std::vector<double> h_gmin, h_gmax;   // per nuclide grid range
     double emin_all = 0, emax_all = 0;
     int64_t* d_grid_off = nullptr;
-    double *d_e64 = nullptr, *d_s64 = nullptr, *d_fabs = nullptr, *d_awr = nullptr;
+    Interval64* d_iv64 = nullptr;
+    double *d_e64 = nullptr, *d_fabs = nullptr, *d_awr = nullptr;
     float2* d_es32 = nullptr;       // binary32 (E, sigma_t) pairs, 8 pairs of padding
     float* d_fabs32 = nullptr;
     NucIndex *d_nx64 = nullptr, *d_nx32 = nullptr;   // coarse search indexes
@@ -392,7 +393,7 @@ Tables make_tables(const gbmc_ctx* c) {
     Tables T{};
     T.grid_off = c->d_grid_off;
     T.nx64 = c->d_nx64; T.idx64 = c->d_idx64; T.bw32 = c->d_bw32; T.d32 = c->d_desc32;
-    T.e64 = c->d_e64; T.s64 = c->d_s64; T.es32 = c->d_es32;
+    T.e64 = c->d_e64; T.iv64 = c->d_iv64; T.es32 = c->d_es32;
     T.f_abs = c->d_fabs; T.f_abs32 = c->d_fabs32; T.awr = c->d_awr;
     T.mat_off = c->d_mat_off; T.nuc_id = c->d_nuc_id;
     T.density = c->d_density; T.density32 = c->d_density32;
@@ -609,6 +610,26 @@ int n_cells_of(const gbmc_geometry& g) {
     return 1;
 }
 
+// The interval record of grid points (e0, s0), (e1, s1): the binary64
+// differences the interpolation takes and the exact fixed-point reciprocal
+// y = floor(2^126 / d) of de's significand d = M_de 2^11 in [2^63, 2^64)
+// (0 unless de is a positive normal number).
+Interval64 interval_record(double e0, double e1, double s0, double s1) {
+    Interval64 r;
+    r.de = e1 - e0;
+    r.ds = s1 - s0;
+    r.s0 = s0;
+    r.y = 0ull;
+    uint64_t x;
+    memcpy(&x, &r.de, 8);
+    const int ex = (int)(x >> 52);   // sign bit included
+    if (ex >= 1 && ex <= 2046) {
+        const unsigned __int128 d = (unsigned __int128)(((x & ((1ull << 52) - 1ull)) | (1ull << 52)) << 11);
+        r.y = (unsigned long long)(((unsigned __int128)1 << 126) / d);
+    }
+    return r;
+}
+
 // Coarse search index of every nuclide grid (binary64 or binary32 bit
 // patterns): buckets (bits - bits(E_0)) >> shift, about 8 grid points per
 // bucket, idx[b] = number of grid points whose bucket is below b.
@@ -769,7 +790,7 @@ int gbmc_destroy(gbmc_ctx* c) {
     dfree(c->Y.flux); dfree(c->Y.counts); dfree(c->Y.weights); dfree(c->Y.absrate);
     dfree(c->d_nu); dfree(c->d_ffis); dfree(c->d_sites); dfree(c->d_site_n); dfree(c->d_site_off);
     dfree(c->d_bank_out); dfree(c->d_bank_size); dfree(c->d_bank_src);
-    dfree(c->d_grid_off); dfree(c->d_e64); dfree(c->d_s64); dfree(c->d_es32);
+    dfree(c->d_grid_off); dfree(c->d_e64); dfree(c->d_iv64); dfree(c->d_es32);
     dfree(c->d_fabs); dfree(c->d_fabs32); dfree(c->d_awr);
     dfree(c->d_nx64); dfree(c->d_nx32); dfree(c->d_idx64); dfree(c->d_idx32); dfree(c->d_bw32);
     dfree(c->d_mat_off); dfree(c->d_nuc_id); dfree(c->d_density); dfree(c->d_density32);
@@ -852,7 +873,7 @@ int gbmc_load_xs_tables(gbmc_ctx* c, int32_t n_nuc, const int64_t* grid_off, con
     bool same = (h == c->table_hash && n_nuc == c->n_nuc);
     if (!same) {
         // new tables: drop the copy of the other precision
-        dfree(c->d_e64); dfree(c->d_s64); dfree(c->d_es32);
+        dfree(c->d_e64); dfree(c->d_iv64); dfree(c->d_es32);
         dfree(c->d_nx64); dfree(c->d_nx32); dfree(c->d_idx64); dfree(c->d_idx32); dfree(c->d_bw32);
         c->has64 = c->has32 = false;
         // materials refer to nuclide ids of the old tables
@@ -871,7 +892,11 @@ int gbmc_load_xs_tables(gbmc_ctx* c, int32_t n_nuc, const int64_t* grid_off, con
     if ((rc = upload(c, &c->d_fabs32, f32.data(), (size_t)n_nuc))) return rc;
     if (precision == GBMC_FP64) {
         if ((rc = upload(c, &c->d_e64, energy, (size_t)tot))) return rc;
-        if ((rc = upload(c, &c->d_s64, sigma_t, (size_t)tot))) return rc;
+        std::vector<Interval64> iv((size_t)tot);
+        for (int32_t i = 0; i < n_nuc; ++i)
+            for (int64_t k = grid_off[i]; k + 1 < grid_off[i + 1]; ++k)
+                iv[k] = interval_record(energy[k], energy[k + 1], sigma_t[k], sigma_t[k + 1]);
+        if ((rc = upload(c, &c->d_iv64, iv.data(), iv.size()))) return rc;
         if ((rc = build_index(c, n_nuc, grid_off, energy, GBMC_FP64, &c->d_nx64, &c->d_idx64)))
             return rc;
         c->has64 = true;
@@ -1233,7 +1258,7 @@ int gbmc_profile_problems(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs
             float ms = 0;
             e = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
             if (e != cudaSuccess) break;
-            bool launched = (k < 2 || k > 4 || P.sort);
+            bool launched = (k < 2 || k > 3 || P.sort);
             out->ms[k] += ms;
             out->launches[k] += launched ? 1 : 0;
             if (trace_ms && it < trace_cap) trace_ms[(int64_t)it * kTimedKernels + k] = ms;
@@ -1418,28 +1443,64 @@ int gbmc_set_source_bank(gbmc_ctx* c, const double* xyz, int64_t n, int64_t n_to
     return GBMC_OK;
 }
 
-int gbmc_check_division(gbmc_ctx* c, int64_t n, uint64_t seed, int64_t* n_bad,
+int gbmc_check_division(gbmc_ctx* c, int32_t kind, int64_t n, uint64_t seed, int64_t* n_bad,
                         double* first_bad) {
-    if (!c || !n_bad || n < 0) return GBMC_ERR_INVALID_ARG;
+    if (!c || !n_bad || n < 0 || kind < 0 || kind > 1) return GBMC_ERR_INVALID_ARG;
     int rc = set_device(c);
     if (rc) return rc;
     unsigned long long* d_bad = nullptr;
     double* d_first = nullptr;
-    if ((rc = dalloc(c, &d_bad, 1))) return rc;
-    if ((rc = dalloc(c, &d_first, 2))) {
+    double *d_e0 = nullptr, *d_e1 = nullptr;
+    Interval64* d_iv = nullptr;
+    auto release = [&]() {
         dfree(d_bad);
+        dfree(d_first);
+        dfree(d_e0);
+        dfree(d_e1);
+        dfree(d_iv);
+    };
+    if ((rc = dalloc(c, &d_bad, 1)) || (rc = dalloc(c, &d_first, 2))) {
+        release();
         return rc;
+    }
+    const int32_t K = 1 << 16;
+    if (kind == 1) {
+        // grid-like intervals: e0 log-uniform on [1e-6, 1e8] eV, relative
+        // widths from 2^-52 to 2^14, one in 64 of zero width (a repeated point)
+        uint64_t st = seed ^ 0x9E3779B97F4A7C15ull;
+        auto next = [&st]() {   // splitmix64
+            uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+            return z ^ (z >> 31);
+        };
+        auto unit = [&next]() { return (double)(next() >> 11) * 0x1.0p-53; };
+        std::vector<double> e0(K), e1(K);
+        std::vector<Interval64> iv(K);
+        for (int32_t j = 0; j < K; ++j) {
+            e0[j] = std::pow(10.0, -6.0 + 14.0 * unit());
+            double g = std::exp2(j % 3 == 0 ? -52.0 + 66.0 * unit() : -50.0 + 51.0 * unit());
+            e1[j] = j % 64 == 63 ? e0[j] : e0[j] * (1.0 + g);
+            if (e1[j] == e0[j] && j % 64 != 63) e1[j] = std::nextafter(e0[j], 1e300);
+            iv[j] = interval_record(e0[j], e1[j], 1.0, 2.0);
+        }
+        if ((rc = upload(c, &d_e0, e0.data(), (size_t)K)) || (rc = upload(c, &d_e1, e1.data(), (size_t)K)) ||
+            (rc = upload(c, &d_iv, iv.data(), (size_t)K))) {
+            release();
+            return rc;
+        }
     }
     cudaError_t e = cudaMemset(d_bad, 0, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(d_first, 0, 2 * sizeof(double));
-    if (e == cudaSuccess) e = launch_check_division(n, seed, d_bad, d_first, c->sms, 0);
+    if (e == cudaSuccess)
+        e = kind == 0 ? launch_check_division(n, seed, d_bad, d_first, c->sms, 0)
+                      : launch_check_interp(n, seed, d_e0, d_e1, d_iv, K, d_bad, d_first, c->sms, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     unsigned long long nb = 0;
     double fb[2] = {0.0, 0.0};
     if (e == cudaSuccess) e = cudaMemcpy(&nb, d_bad, sizeof nb, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(fb, d_first, sizeof fb, cudaMemcpyDeviceToHost);
-    dfree(d_bad);
-    dfree(d_first);
+    release();
     if (e != cudaSuccess) return fail(c, GBMC_ERR_CUDA, "division check: %s", cudaGetErrorString(e));
     *n_bad = (int64_t)nb;
     if (first_bad) {

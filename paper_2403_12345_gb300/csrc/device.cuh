@@ -46,6 +46,20 @@ struct alignas(16) Desc32 {
 };
 static_assert(sizeof(Desc32) == 32, "Desc32 is read as two int4");
 
+// Interval k of a binary64 grid (from point k to point k+1): the operands of
+// the lin-lin interpolation that depend on the interval alone, computed on
+// the host with the same binary64 subtractions the interpolation states, so
+// the kernels form bit-identical results with fewer binary64 operations.
+//   de = E_k+1 - E_k, ds = s_k+1 - s_k (rounded to nearest), s0 = s_k,
+//   y  = floor(2^126 / (M_de 2^11)) for the significand M_de in [2^52, 2^53)
+//        of de (a fixed-point reciprocal for the division by de), or 0 when
+//        de is not a positive normal number (the kernels then divide by de
+//        in binary64).
+struct alignas(32) Interval64 {
+    double de, ds, s0;
+    unsigned long long y;
+};
+
 struct Tables {
     const int64_t* grid_off;   // [n_nuc+1]
     const NucIndex* nx64;      // [n_nuc] descriptors over the binary64 grid
@@ -53,7 +67,7 @@ struct Tables {
     const float4* bw32;        // binary32 bucket windows (four float4 each)
     const Desc32* d32;         // [mat_off[n_mat]] per material entry (binary32)
     const double* e64;         // binary64 grid (eV)
-    const double* s64;         // binary64 sigma_t (b)
+    const Interval64* iv64;    // binary64 intervals, indexed like e64 (last of each grid unused)
     const float2* es32;        // binary32 (E, sigma_t) pairs, each nuclide followed by
                                // kPad32 pairs (+inf, 0)
     const double* f_abs;       // [n_nuc]
@@ -363,6 +377,68 @@ __device__ __forceinline__ double div_rn(double a, double b) {
     return __longlong_as_double((long long)(sign | ((unsigned long long)e << 52) | (m & M)));
 }
 
+// The interpolation factor f = (E - e0) / de (both steps rounded to nearest,
+// as in binary64) for a bracket e0 <= E, with y the interval's fixed-point
+// reciprocal of de.  E - e0 is formed exactly on the integer units when the
+// exponents of E and e0 differ by at most 10 (the difference then fits in 64
+// bits and is rounded once, to nearest even); the quotient's significand is
+// floor(R 2^64 / d) estimated as (4 R) y / 2^64, which is off by at most one
+// (y is exact to one unit and R < 2^54), then made exact by the remainder.
+// Other operands (E below e0, far above the interval, special values, y = 0)
+// take the binary64 subtraction and div_rn.
+__device__ __forceinline__ double frac_rn(double E, double e0, double de, unsigned long long y) {
+    const unsigned long long xE = (unsigned long long)__double_as_longlong(E);
+    const unsigned long long x0 = (unsigned long long)__double_as_longlong(e0);
+    const int eE = (int)(xE >> 52), e0x = (int)(x0 >> 52);   // sign bit included
+    const int sh = eE - e0x;
+    if (y == 0ull || e0x == 0 || eE >= 0x7ff || sh < 0 || sh > 10 || xE < x0)
+        return div_rn(E - e0, de);
+    if (xE == x0) return 0.0;
+    const unsigned long long M = (1ull << 52) - 1ull;
+    // exact D 2^(e0x - 1075) = E - e0, D in (0, 2^63)
+    const unsigned long long D = (((xE & M) | (1ull << 52)) << sh) - ((x0 & M) | (1ull << 52));
+    const int nz = __clzll((long long)D);
+    unsigned long long A;
+    int ea;
+    if (nz >= 11) {   // at most 53 bits: exact
+        A = D << (nz - 11);
+        ea = e0x - (nz - 11);
+    } else {          // round to 53 bits, to nearest even
+        const int r = 11 - nz;
+        A = D >> r;
+        const unsigned long long rem = D & ((1ull << r) - 1ull), half = 1ull << (r - 1);
+        if (rem > half || (rem == half && (A & 1ull))) ++A;
+        ea = e0x + r;
+        if (A == (1ull << 53)) {
+            A >>= 1;
+            ++ea;
+        }
+    }
+    const unsigned long long xd = (unsigned long long)__double_as_longlong(de);
+    const int eb = (int)(xd >> 52);   // de is a positive normal number (y != 0)
+    const unsigned long long B = (xd & M) | (1ull << 52);
+    const bool ge = A >= B;
+    const unsigned long long R = ge ? A : (A << 1);
+    const unsigned long long d = B << 11;
+    unsigned long long Q = __umul64hi(R << 2, y);
+    const unsigned long long qlo = Q * d, qhi = __umul64hi(Q, d);
+    unsigned long long rlo = 0ull - qlo;
+    const unsigned long long rhi = R - qhi - (qlo != 0ull ? 1ull : 0ull);   // remainder < 2d
+    if (rhi != 0ull || rlo >= d) {
+        ++Q;
+        rlo -= d;
+    }
+    unsigned long long m = Q >> 1;
+    if ((Q & 1ull) && (rlo != 0ull || (m & 1ull))) ++m;
+    int e = ea - eb + (ge ? 1023 : 1022);
+    if (m == (1ull << 53)) {
+        m >>= 1;
+        ++e;
+    }
+    if (e < 1 || e > 2046) return div_rn(E - e0, de);   // subnormal or overflowing factor
+    return __longlong_as_double((long long)(((unsigned long long)e << 52) | (m & M)));
+}
+
 // ---------------------------------------------------------------- logarithm
 // ln x for positive normal x: x = 2^e m with m in (sqrt(2)/2, sqrt(2)];
 // ln m = 2 atanh(s), s = (m - 1)/(m + 1), as the series
@@ -452,19 +528,25 @@ __device__ __forceinline__ NucIndex load_index(const NucIndex* p) {
     return d;
 }
 
-// Micro cross section of nuclide i at E: lin-lin interpolation between the
-// bracketing grid points, f = (E - E_j) / (E_j+1 - E_j), s_j + f (s_j+1 - s_j).
+// Lin-lin interpolation on the grid interval k that brackets E:
+// f = (E - E_k) / (E_k+1 - E_k), sigma = s_k + f (s_k+1 - s_k), every step
+// rounded to nearest in binary64 (the interval's differences come from its
+// record).
+__device__ __forceinline__ double interp64(const Tables& T, int64_t k, double E) {
+    const double2* r = reinterpret_cast<const double2*>(T.iv64 + k);
+    const double2 a = __ldg(r), b = __ldg(r + 1);   // (de, ds), (s0, y)
+    const double f = frac_rn(E, __ldg(T.e64 + k), a.x, (unsigned long long)__double_as_longlong(b.y));
+    return b.x + f * a.y;
+}
+
+// Micro cross section of nuclide i at E.
 __device__ __forceinline__ double micro64(const Tables& T, int32_t i, double E) {
     NucIndex d = load_index(T.nx64 + i);
     unsigned long long eb = (unsigned long long)__double_as_longlong(E);
     int32_t lo, hi;
     coarse_range(d, T.idx64, eb, lo, hi);
     const unsigned long long* g = reinterpret_cast<const unsigned long long*>(T.e64 + d.off);
-    int64_t k = d.off + bracket_in(g, lo, hi, eb);
-    double e0 = __ldg(T.e64 + k), e1 = __ldg(T.e64 + k + 1);
-    double s0 = __ldg(T.s64 + k), s1 = __ldg(T.s64 + k + 1);
-    double f = div_rn(E - e0, e1 - e0);
-    return s0 + f * (s1 - s0);
+    return interp64(T, d.off + bracket_in(g, lo, hi, eb), E);
 }
 
 // binary32 tables: the bracket satisfies (double)E_j <= E, found by
@@ -616,11 +698,7 @@ __device__ __forceinline__ void macro64(const Tables& T, int32_t m, double E, do
 #pragma unroll
         for (int u = 0; u < kIlp; ++u) {
             if (q + u < q1) {
-                int64_t k = pos[u];
-                double e0 = __ldg(T.e64 + k), e1 = __ldg(T.e64 + k + 1);
-                double s0 = __ldg(T.s64 + k), s1 = __ldg(T.s64 + k + 1);
-                double f = div_rn(E - e0, e1 - e0);
-                double sig = s0 + f * (s1 - s0);
+                double sig = interp64(T, pos[u], E);
                 int32_t i = __ldg(T.nuc_id + q + u);
                 double t = __ldg(T.density + q + u) * sig;
                 at = at + t;

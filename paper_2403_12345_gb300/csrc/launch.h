@@ -28,17 +28,20 @@ cudaError_t launch_tail(const Params& P, const LaunchCfg& L, cudaStream_t s);
 // holds the first such pair.
 cudaError_t launch_check_division(int64_t n, uint64_t seed, unsigned long long* bad,
                                   double* first, int sms, cudaStream_t s);
+cudaError_t launch_check_interp(int64_t n, uint64_t seed, const double* e0s, const double* e1s,
+                                const Interval64* iv, int32_t K, unsigned long long* bad,
+                                double* first, int sms, cudaStream_t s);
 
 // k-eigenvalue: compacts the run's per-history fission-site slots into
 // P.bank_out (history order), the size into *P.bank_size.
 cudaError_t launch_bank(const Params& P, const LaunchCfg& L, cudaStream_t s);
 
 // The iteration launched eagerly with an event before and after each kernel
-// (ev[0..8]; the lookup's two mode kernels share one interval), for
+// (ev[0..7]; the lookup's two mode kernels share one interval), for
 // per-kernel device timing; the tail is timed separately.
-constexpr int kIterKernels = 8;
+constexpr int kIterKernels = 7;
 constexpr int kIterLaunches = 8;   // kernels launched per iteration
-constexpr int kTimedKernels = 9;   // + the tail
+constexpr int kTimedKernels = 8;   // + the tail
 cudaError_t launch_iteration_timed(const Params& P, const LaunchCfg& L, cudaStream_t s,
                                    cudaEvent_t* ev);
 

@@ -1302,9 +1302,52 @@ __global__ void k_check_division(int64_t n, uint64_t seed, unsigned long long* b
     }
 }
 
+// frac_rn against (E - e0) / de in binary64 over K grid intervals (e0, e1)
+// and n energies drawn per sample: inside the interval, at and next to its
+// ends, just below e0 and far above e1.
+__global__ void k_check_interp(int64_t n, uint64_t seed, const double* e0s, const double* e1s,
+                               const Interval64* iv, int32_t K, unsigned long long* bad,
+                               double* first) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        Philox h = philox4x64_10((uint64_t)i, 0, 0, 0, seed, 0x1E7E4F0Cull);
+        int32_t j = (int32_t)(h.c0 % (uint64_t)K);
+        double e0 = e0s[j], e1 = e1s[j];
+        Interval64 r = iv[j];
+        long long b0 = __double_as_longlong(e0), b1 = __double_as_longlong(e1);
+        long long k = (long long)(h.c2 >> 61) + 1;   // 1 .. 8
+        double E;
+        switch ((int)(h.c1 & 7u)) {
+            case 0: E = e0; break;
+            case 1: E = e1; break;
+            case 2: E = __longlong_as_double(b0 + k); break;
+            case 3: E = __longlong_as_double(b1 - k + 1); break;
+            case 4: E = __longlong_as_double(b0 - k); break;
+            case 5: E = __longlong_as_double(b1 + ((long long)(h.c2 >> 40 & 15u) << 52)); break;
+            default: E = e0 + Stream::u01(h.c3) * r.de; break;
+        }
+        double q = frac_rn(E, e0, r.de, r.y), t = (E - e0) / r.de;
+        bool same = __double_as_longlong(q) == __double_as_longlong(t) || (q != q && t != t);
+        if (!same) {
+            unsigned long long c = atomicAdd(bad, 1ull);
+            if (c == 0) {
+                first[0] = E;
+                first[1] = e0;
+            }
+        }
+    }
+}
+
 cudaError_t launch_check_division(int64_t n, uint64_t seed, unsigned long long* bad,
                                   double* first, int sms, cudaStream_t s) {
     k_check_division<<<sms * 8, 256, 0, s>>>(n, seed, bad, first);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_interp(int64_t n, uint64_t seed, const double* e0s, const double* e1s,
+                                const Interval64* iv, int32_t K, unsigned long long* bad,
+                                double* first, int sms, cudaStream_t s) {
+    k_check_interp<<<sms * 8, 256, 0, s>>>(n, seed, e0s, e1s, iv, K, bad, first);
     return cudaGetLastError();
 }
 
@@ -1367,21 +1410,20 @@ cudaError_t launch_iteration_timed(const Params& P, const LaunchCfg& L, cudaStre
     k_plan<<<1, 32, 0, s>>>(P);
     cudaEventRecord(ev[1], s);
     k_source<<<L.grid, 256, 0, s>>>(P);
-    cudaEventRecord(ev[2], s);
-    cudaEventRecord(ev[3], s);   // keys and counts come with the appends: no key pass
+    cudaEventRecord(ev[2], s);   // keys and counts come with the appends: no key pass
     if (P.sort) k_sort_scan<<<kScanBlocks, 1024, 0, s>>>(P);
-    cudaEventRecord(ev[4], s);
+    cudaEventRecord(ev[3], s);
     if (P.sort) k_sort_scatter<<<L.grid, 256, 0, s>>>(P);
-    cudaEventRecord(ev[5], s);
+    cudaEventRecord(ev[4], s);
     launch_lookups(P, L, s);
-    cudaEventRecord(ev[6], s);
+    cudaEventRecord(ev[5], s);
     k_raytrace<<<L.grid, 256, 0, s>>>(P);
-    cudaEventRecord(ev[7], s);
+    cudaEventRecord(ev[6], s);
     if (P.precision == GBMC_FP64)
         k_collision<GBMC_FP64><<<L.grid, 256, 0, s>>>(P);
     else
         k_collision<GBMC_FP32><<<L.grid, 256, 0, s>>>(P);
-    cudaEventRecord(ev[8], s);
+    cudaEventRecord(ev[7], s);
     return cudaGetLastError();
 }
 

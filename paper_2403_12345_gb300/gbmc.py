@@ -45,7 +45,7 @@ EXPORTS = ["gbmc_default_options", "gbmc_create", "gbmc_destroy", "gbmc_last_err
 MLP_HIDDEN = 64
 MLP_NPARAM = 4545
 NOALLOC_MAX_QUERIES = 1 << 20
-KERNEL_NAMES = ["plan", "source", "sort_keys", "sort_scan", "sort_scatter", "lookup", "raytrace",
+KERNEL_NAMES = ["plan", "source", "sort_scan", "sort_scatter", "lookup", "raytrace",
                 "collision", "tail"]
 
 
@@ -89,7 +89,7 @@ class AutotuneReport(C.Structure):
 
 
 class KernelTimes(C.Structure):
-    _fields_ = [("ms", C.c_double * 9), ("launches", C.c_int64 * 9)]
+    _fields_ = [("ms", C.c_double * len(KERNEL_NAMES)), ("launches", C.c_int64 * len(KERNEL_NAMES))]
 
 
 _P = C.POINTER
@@ -124,7 +124,7 @@ def lib():
                                         _P(C.c_int64), _P(C.c_double)]
         L.gbmc_set_reaction_tally.argtypes = [vp, C.c_int32]
         L.gbmc_load_fission.argtypes = [vp, C.c_int32, _P(C.c_double), _P(C.c_double)]
-        L.gbmc_check_division.argtypes = [vp, C.c_int64, C.c_uint64, _P(C.c_int64),
+        L.gbmc_check_division.argtypes = [vp, C.c_int32, C.c_int64, C.c_uint64, _P(C.c_int64),
                                           _P(C.c_double)]
         L.gbmc_set_eigen.argtypes = [vp, C.c_double, C.c_int32]
         L.gbmc_read_bank.argtypes = [vp, _P(C.c_double), C.c_int64, _P(C.c_int64)]
@@ -388,11 +388,11 @@ class Context:
     def profile_problems(self, probs, stream=None, trace_cap: int = 0):
         """Run with every kernel launched eagerly between CUDA events; returns
         {kernel: (total ms, launches)}, and with trace_cap > 0 also a
-        per-iteration trace (ms [iters, 9]; lookups, ray-traced particles,
+        per-iteration trace (ms [iters, len(KERNEL_NAMES)]; lookups, ray-traced particles,
         collisions and particles in flight [iters, 4])."""
         arr = (Problem * len(probs))(*probs)
         kt = KernelTimes()
-        tms = np.zeros((max(trace_cap, 1), 9))
+        tms = np.zeros((max(trace_cap, 1), len(KERNEL_NAMES)))
         tq = np.zeros((max(trace_cap, 1), 4), np.int32)
         tl = C.c_int32(0)
         self._ck(lib().gbmc_profile_problems(self._h, len(probs), arr, _stream(stream),
@@ -461,12 +461,16 @@ class Context:
             a = _arr(xyz, np.float64).reshape(-1, 3)
             self._ck(lib().gbmc_set_source_bank(self._h, _p(a, C.c_double), len(a), int(n_total)))
 
-    def check_division(self, n: int, seed: int = 1):
-        """(quotients that differ from the hardware division, first such pair)."""
+    def check_division(self, n: int, seed: int = 1, kind: int = 0):
+        """gbmc_check_division: kind 0 checks the integer-unit division, kind 1
+        the lookup's interpolation factor from interval records; returns
+        (results that differ from the hardware binary64 ones, first such
+        operand pair)."""
         bad = C.c_int64()
         first = np.zeros(2)
-        self._ck(lib().gbmc_check_division(self._h, int(n), int(seed) & 0xFFFFFFFFFFFFFFFF,
-                                           C.byref(bad), _p(first, C.c_double)))
+        self._ck(lib().gbmc_check_division(self._h, int(kind), int(n),
+                                           int(seed) & 0xFFFFFFFFFFFFFFFF, C.byref(bad),
+                                           _p(first, C.c_double)))
         return bad.value, first
 
     def set_reaction_tally(self, on: bool = True):
