@@ -56,7 +56,7 @@ struct gbmc_ctx {
     double *d_e64 = nullptr, *d_fabs = nullptr, *d_awr = nullptr;
     float2* d_es32 = nullptr;       // binary32 (E, sigma_t) pairs, 8 pairs of padding
     float* d_fabs32 = nullptr;
-    NucIndex *d_nx64 = nullptr, *d_nx32 = nullptr;   // coarse search indexes
+    NucIndex* d_nx32 = nullptr;       // coarse search descriptors (binary32 index build)
     uint32_t *d_idx64 = nullptr, *d_idx32 = nullptr;
     uint64_t table_hash = 0;   // identifies the tables both copies were built from
 
@@ -65,6 +65,8 @@ struct gbmc_ctx {
     std::vector<int32_t> h_mat_off, h_nuc_id;
     std::vector<double> h_density, h_fabs;
     std::vector<NucIndex> h_nx32;     // binary32 search descriptors (offsets into d_es32)
+    std::vector<NucIndex> h_nx64;     // binary64 search descriptors
+    Desc64* d_desc64 = nullptr;       // per material entry: binary64 search descriptor
     Desc32* d_desc32 = nullptr;       // per material entry: search + density + f_abs
     float4* d_bw32 = nullptr;         // binary32 bucket windows (4 float4 each)
     std::vector<int64_t> h_bw_off;    // first window of each nuclide
@@ -392,7 +394,7 @@ int ensure_tallies(gbmc_ctx* c, const std::vector<int32_t>& cells, cudaStream_t 
 Tables make_tables(const gbmc_ctx* c) {
     Tables T{};
     T.grid_off = c->d_grid_off;
-    T.nx64 = c->d_nx64; T.idx64 = c->d_idx64; T.bw32 = c->d_bw32; T.d32 = c->d_desc32;
+    T.d64 = c->d_desc64; T.idx64 = c->d_idx64; T.bw32 = c->d_bw32; T.d32 = c->d_desc32;
     T.e64 = c->d_e64; T.iv64 = c->d_iv64; T.es32 = c->d_es32;
     T.f_abs = c->d_fabs; T.f_abs32 = c->d_fabs32; T.awr = c->d_awr;
     T.mat_off = c->d_mat_off; T.nuc_id = c->d_nuc_id;
@@ -653,10 +655,10 @@ int build_index(gbmc_ctx* c, int32_t n_nuc, const int64_t* grid_off, const doubl
     for (int32_t i = 0; i < n_nuc; ++i) {
         int64_t off = grid_off[i], n = grid_off[i + 1] - off;
         uint64_t base = bits(off), range = bits(off + n - 1) - base;
-        // binary64: about 4-8 points a bucket (a few bisection steps follow);
-        // binary32: about 1-2, so that a bucket window (seven pairs) holds it
-        int32_t per = precision == GBMC_FP64 ? 8 : 2;
-        int32_t cap = precision == GBMC_FP64 ? (1 << 16) : (1 << 20);
+        // about 1-2 points a bucket: binary64 bisects within the bucket's
+        // range (about one step), binary32 reads it as one bucket window
+        int32_t per = 2;
+        int32_t cap = 1 << 20;
         int32_t nb = 16;
         while ((int64_t)nb * per < n && nb < cap) nb <<= 1;
         int32_t shift = 0;
@@ -701,6 +703,27 @@ int build_desc32(gbmc_ctx* c) {
         e.f_abs = (float)c->h_fabs[c->h_nuc_id[q]];
     }
     return upload(c, &c->d_desc32, d.data(), tot);
+}
+
+// Per material entry search descriptors of the binary64 lookup (needs the
+// binary64 tables and the materials).
+int build_desc64(gbmc_ctx* c) {
+    if (!c->has64 || !c->n_mat) return GBMC_OK;
+    size_t tot = c->h_nuc_id.size();
+    std::vector<Desc64> d(tot);
+    for (size_t q = 0; q < tot; ++q) {
+        const NucIndex& x = c->h_nx64[c->h_nuc_id[q]];
+        if (x.idx_off + x.nb > ((int64_t)1 << 31) - 1)
+            return fail(c, GBMC_ERR_INVALID_ARG, "binary64 tables over 2^31 index buckets");
+        Desc64& e = d[q];
+        e.off = x.off;
+        e.base = x.base;
+        e.idx_off = (int32_t)x.idx_off;
+        e.n = x.n;
+        e.shift = x.shift;
+        e.nb = x.nb;
+    }
+    return upload(c, &c->d_desc64, d.data(), tot);
 }
 
 int read_ctl(gbmc_ctx* c) {
@@ -792,7 +815,7 @@ int gbmc_destroy(gbmc_ctx* c) {
     dfree(c->d_bank_out); dfree(c->d_bank_size); dfree(c->d_bank_src);
     dfree(c->d_grid_off); dfree(c->d_e64); dfree(c->d_iv64); dfree(c->d_es32);
     dfree(c->d_fabs); dfree(c->d_fabs32); dfree(c->d_awr);
-    dfree(c->d_nx64); dfree(c->d_nx32); dfree(c->d_idx64); dfree(c->d_idx32); dfree(c->d_bw32);
+    dfree(c->d_nx32); dfree(c->d_idx64); dfree(c->d_idx32); dfree(c->d_bw32); dfree(c->d_desc64);
     dfree(c->d_mat_off); dfree(c->d_nuc_id); dfree(c->d_density); dfree(c->d_density32);
     dfree(c->d_desc32);
     dfree(c->d_edges); dfree(c->d_probs); dfree(c->d_planes); dfree(c->d_ctl);
@@ -874,7 +897,7 @@ int gbmc_load_xs_tables(gbmc_ctx* c, int32_t n_nuc, const int64_t* grid_off, con
     if (!same) {
         // new tables: drop the copy of the other precision
         dfree(c->d_e64); dfree(c->d_iv64); dfree(c->d_es32);
-        dfree(c->d_nx64); dfree(c->d_nx32); dfree(c->d_idx64); dfree(c->d_idx32); dfree(c->d_bw32);
+        dfree(c->d_nx32); dfree(c->d_idx64); dfree(c->d_idx32); dfree(c->d_bw32);
         c->has64 = c->has32 = false;
         // materials refer to nuclide ids of the old tables
         if (c->n_mat) {
@@ -897,7 +920,8 @@ int gbmc_load_xs_tables(gbmc_ctx* c, int32_t n_nuc, const int64_t* grid_off, con
             for (int64_t k = grid_off[i]; k + 1 < grid_off[i + 1]; ++k)
                 iv[k] = interval_record(energy[k], energy[k + 1], sigma_t[k], sigma_t[k + 1]);
         if ((rc = upload(c, &c->d_iv64, iv.data(), iv.size()))) return rc;
-        if ((rc = build_index(c, n_nuc, grid_off, energy, GBMC_FP64, &c->d_nx64, &c->d_idx64)))
+        if ((rc = build_index(c, n_nuc, grid_off, energy, GBMC_FP64, nullptr, &c->d_idx64, nullptr,
+                              &c->h_nx64)))
             return rc;
         c->has64 = true;
     } else {
@@ -956,7 +980,7 @@ int gbmc_load_xs_tables(gbmc_ctx* c, int32_t n_nuc, const int64_t* grid_off, con
     }
     c->n_nuc = n_nuc;
     c->h_fabs.assign(f_abs, f_abs + n_nuc);
-    if ((rc = build_desc32(c))) return rc;
+    if ((rc = build_desc32(c)) || (rc = build_desc64(c))) return rc;
     c->table_hash = h;
     c->h_grid_off.assign(grid_off, grid_off + n_nuc + 1);
     // the grid range check uses the tighter of the two copies
@@ -1008,7 +1032,7 @@ int gbmc_init_materials(gbmc_ctx* c, int32_t n_mat, const int32_t* mat_off, cons
     c->h_mat_off.assign(mat_off, mat_off + n_mat + 1);
     c->h_nuc_id.assign(nuc_id, nuc_id + tot);
     c->h_density.assign(density, density + tot);
-    if ((rc = build_desc32(c))) return rc;
+    if ((rc = build_desc32(c)) || (rc = build_desc64(c))) return rc;
     c->graph_valid = false;
     return GBMC_OK;
 }

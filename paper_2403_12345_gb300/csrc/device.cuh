@@ -46,6 +46,18 @@ struct alignas(16) Desc32 {
 };
 static_assert(sizeof(Desc32) == 32, "Desc32 is read as two int4");
 
+// Per material entry q, binary64 tables: the search descriptor of nuclide
+// nuc_id[q] in one 32-byte record (two 16-byte loads).
+struct alignas(16) Desc64 {
+    int64_t off;       // first grid point of the nuclide in e64 / iv64
+    uint64_t base;     // bit pattern of its first grid energy
+    int32_t idx_off;   // first entry of its coarse index in idx64
+    int32_t n;         // grid points
+    int32_t shift;     // bucket of E = (bits(E) - base) >> shift
+    int32_t nb;        // buckets
+};
+static_assert(sizeof(Desc64) == 32, "Desc64 is read as two int4");
+
 // Interval k of a binary64 grid (from point k to point k+1): the operands of
 // the lin-lin interpolation that depend on the interval alone, computed on
 // the host with the same binary64 subtractions the interpolation states, so
@@ -62,7 +74,7 @@ struct alignas(32) Interval64 {
 
 struct Tables {
     const int64_t* grid_off;   // [n_nuc+1]
-    const NucIndex* nx64;      // [n_nuc] descriptors over the binary64 grid
+    const Desc64* d64;         // [mat_off[n_mat]] per material entry (binary64)
     const uint32_t* idx64;     // coarse index of the binary64 grids
     const float4* bw32;        // binary32 bucket windows (four float4 each)
     const Desc32* d32;         // [mat_off[n_mat]] per material entry (binary32)
@@ -493,8 +505,8 @@ __host__ __device__ constexpr int cum_group() { return PREC == GBMC_FP64 ? 1 : k
 // because the bracket is unique (the "double indexing" of the CPU codes the
 // paper compares against, Sec. 3).
 
-template <class U>
-__device__ __forceinline__ void coarse_range(const NucIndex& d, const uint32_t* __restrict__ idx,
+template <class D, class U>
+__device__ __forceinline__ void coarse_range(const D& d, const uint32_t* __restrict__ idx,
                                              U eb, int32_t& lo, int32_t& hi) {
     U base = (U)d.base;
     U b = eb >= base ? (U)((eb - base) >> d.shift) : (U)0;
@@ -518,13 +530,12 @@ __device__ __forceinline__ int32_t bracket_in(const U* __restrict__ g, int32_t l
     return lo;
 }
 
-__device__ __forceinline__ NucIndex load_index(const NucIndex* p) {
-    NucIndex d;
+__device__ __forceinline__ Desc64 load_desc64(const Desc64* p) {
+    Desc64 d;
     const int4* q = reinterpret_cast<const int4*>(p);
-    int4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
+    int4 a = __ldg(q), b = __ldg(q + 1);
     memcpy(&d, &a, 16);
     memcpy(reinterpret_cast<char*>(&d) + 16, &b, 16);
-    memcpy(reinterpret_cast<char*>(&d) + 32, &c, 16);
     return d;
 }
 
@@ -539,9 +550,9 @@ __device__ __forceinline__ double interp64(const Tables& T, int64_t k, double E)
     return b.x + f * a.y;
 }
 
-// Micro cross section of nuclide i at E.
-__device__ __forceinline__ double micro64(const Tables& T, int32_t i, double E) {
-    NucIndex d = load_index(T.nx64 + i);
+// Micro cross section at E of the nuclide of material entry q.
+__device__ __forceinline__ double micro64(const Tables& T, int32_t q, double E) {
+    Desc64 d = load_desc64(T.d64 + q);
     unsigned long long eb = (unsigned long long)__double_as_longlong(E);
     int32_t lo, hi;
     coarse_range(d, T.idx64, eb, lo, hi);
@@ -647,9 +658,8 @@ constexpr int kIlp = 4;
 static_assert(kIlp == 4, "the running sums are stored four at a time");
 
 template <class U>
-__device__ __forceinline__ void brackets(const Tables& T, const NucIndex* nx,
-                                         const uint32_t* idx, const U* g, int32_t q, int32_t q1,
-                                         U eb, int64_t* pos) {
+__device__ __forceinline__ void brackets(const Tables& T, const Desc64* dq, const uint32_t* idx,
+                                         const U* g, int32_t q, int32_t q1, U eb, int64_t* pos) {
     int32_t lo[kIlp], hi[kIlp];
     const U* gp[kIlp];
 #pragma unroll
@@ -658,7 +668,7 @@ __device__ __forceinline__ void brackets(const Tables& T, const NucIndex* nx,
         hi[u] = 1;
         gp[u] = g;
         if (q + u < q1) {
-            NucIndex d = load_index(nx + __ldg(T.nuc_id + q + u));
+            Desc64 d = load_desc64(dq + q + u);
             gp[u] = g + d.off;
             coarse_range(d, idx, eb, lo[u], hi[u]);
         }
@@ -694,7 +704,7 @@ __device__ __forceinline__ void macro64(const Tables& T, int32_t m, double E, do
     for (int32_t q = q0; q < q1; q += kIlp) {
         int64_t pos[kIlp];
         double run[kIlp];
-        brackets(T, T.nx64, T.idx64, g, q, q1, eb, pos);
+        brackets(T, T.d64, T.idx64, g, q, q1, eb, pos);
 #pragma unroll
         for (int u = 0; u < kIlp; ++u) {
             if (q + u < q1) {
@@ -779,9 +789,8 @@ __device__ __forceinline__ void macro_warp(const Tables& T, int32_t m, double E,
         for (int32_t c = q0; c < q1; c += 32) {
             double t = 0.0, p = 0.0;
             if (c + lane < q1) {
-                int32_t i = __ldg(T.nuc_id + c + lane);
-                t = __ldg(T.density + c + lane) * micro64(T, i, E);
-                if (SA) p = t * __ldg(T.f_abs + i);
+                t = __ldg(T.density + c + lane) * micro64(T, c + lane, E);
+                if (SA) p = t * __ldg(T.f_abs + __ldg(T.nuc_id + c + lane));
             }
             int32_t kmax = q1 - c < 32 ? q1 - c : 32;
             for (int k = 0; k < kmax; ++k) {
@@ -826,7 +835,7 @@ __device__ __forceinline__ int32_t pick_nuclide(const Tables& T, int precision, 
         double cum = 0.0;
         for (int32_t q = q0; q < q1; ++q) {
             int32_t i = __ldg(T.nuc_id + q);
-            double t = __ldg(T.density + q) * micro64(T, i, E);
+            double t = __ldg(T.density + q) * micro64(T, q, E);
             cum = cum + t;
             if (t > 0.0) last = i;
             if (target < cum) return i;
@@ -875,7 +884,7 @@ __device__ __forceinline__ int32_t pick_from_sums(const Tables& T, int32_t m, co
         double at = lo > 0 ? c64[(int64_t)(lo - 1) * stride] : 0.0;
         for (int32_t k = k0; k < k1; ++k) {
             int32_t i = __ldg(T.nuc_id + q0 + k);
-            at = at + __ldg(T.density + q0 + k) * micro64(T, i, E);
+            at = at + __ldg(T.density + q0 + k) * micro64(T, q0 + k, E);
             if (target < at) return i;
         }
     } else {

@@ -456,7 +456,7 @@ __global__ void __launch_bounds__(256) k_sort_scatter(Params P) {
 
 template <int PREC, bool SA>
 // Thread mode (long queues): one particle per thread.
-__global__ void __launch_bounds__(256, 3) k_lookup(Params P) {
+__global__ void __launch_bounds__(256, PREC == GBMC_FP64 ? 4 : 3) k_lookup(Params P) {
     const Ctl* c = P.ctl;
     int32_t n = c->lookup_n;
     if (n == 0 || c->warp_lookup) return;
