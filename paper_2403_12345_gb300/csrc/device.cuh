@@ -963,6 +963,11 @@ __device__ __forceinline__ bool is_pos(double x) {
     long long b = __double_as_longlong(x);
     return b > 0;
 }
+// -x (a reflection), as a flip of the sign bit.
+__device__ __forceinline__ double flip_sign(double x) {
+    return __longlong_as_double((long long)((unsigned long long)__double_as_longlong(x) ^
+                                            0x8000000000000000ull));
+}
 
 // Cylinder of radius r about the pin axis, from (dx, dy) relative to the
 // axis along (u, v): a d^2 + 2 k d + c = 0 with a = u^2 + v^2,

@@ -546,9 +546,10 @@ __device__ __forceinline__ int32_t cell_of(const gbmc_geometry& g, const Particl
 
 // Track-length scores of a segment of length d in the particle's (cell,
 // energy bin): flux w d and, when on, the absorption rate (w d) Sigma_a.
+// ebin = energy_bin(P.T, pt.E), which the caller keeps while E is unchanged.
 __device__ __forceinline__ void score_segment(const Params& P, const DevProblem& pr,
-                                              const Particle& pt, double d) {
-    int64_t k = pr.flux_off + (int64_t)cell_of(pr.g, pt) * P.T.n_bins + energy_bin(P.T, pt.E);
+                                              const Particle& pt, double d, int32_t ebin) {
+    int64_t k = pr.flux_off + (int64_t)cell_of(pr.g, pt) * P.T.n_bins + ebin;
     double wd = pt.wgt * d;
     atomicAdd(&P.Y.flux[k], wd);
     if (P.Y.absrate) atomicAdd(&P.Y.absrate[k], wd * pt.sa);
@@ -556,7 +557,8 @@ __device__ __forceinline__ void score_segment(const Params& P, const DevProblem&
 
 // One flight (advance event): sample the distance to collision, find the
 // nearest surface of the current cell (ties: cylinder, x, y, z) and compare.
-// a_uv = u * u + v * v of the current direction (a reflection keeps it).
+// a_uv = u * u + v * v of the current direction (a reflection keeps it);
+// ebin = the tally energy bin of pt.E.
 // Returns true for a collision, leaving the particle where it is: the move
 // by -ln(xi) / Sigma_t and its track-length score are finish_flight's, run
 // by the collision event, where every lane of a warp needs that logarithm.
@@ -565,7 +567,7 @@ __device__ __forceinline__ void score_segment(const Params& P, const DevProblem&
 // spans: a surface decided by its span alone costs one binary64 quotient,
 // taken by all such lanes of a warp together.
 __device__ __forceinline__ bool fly(const Params& P, const DevProblem& pr, Particle& pt,
-                                    Stream& r, double& xi, double a_uv) {
+                                    Stream& r, double& xi, double a_uv, int32_t ebin) {
     const gbmc_geometry& g = pr.g;
     xi = r.next();
     pt.nflt = pt.nflt + 1;
@@ -646,7 +648,7 @@ __device__ __forceinline__ bool fly(const Params& P, const DevProblem& pr, Parti
         pt.x = pt.x + dbnd * pt.u;
         pt.y = pt.y + dbnd * pt.v;
         pt.z = pt.z + dbnd * pt.w;
-        score_segment(P, pr, pt, dbnd);
+        score_segment(P, pr, pt, dbnd, ebin);
     }
     return collide;
 }
@@ -659,7 +661,7 @@ __device__ __forceinline__ void finish_flight(const Params& P, const DevProblem&
     pt.x = pt.x + d * pt.u;
     pt.y = pt.y + d * pt.v;
     pt.z = pt.z + d * pt.w;
-    score_segment(P, pr, pt, d);
+    score_segment(P, pr, pt, d, energy_bin(P.T, pt.E));
 }
 
 // Weight-window check at the particle's (cell, energy bin), problem slot 0
@@ -731,7 +733,7 @@ __device__ __forceinline__ int cross(const Params& P, const DevProblem& pr, Part
     relook = false;
     const double* wall = P.planes + pr.plane_off;   // (double)i * pitch (or layer width)
     if (g.kind == GBMC_GEOM_SLAB) {
-        if (pt.u > 0.0) {
+        if (is_pos(pt.u)) {
             pt.x = __ldg(wall + pt.ci + 1);
             if (pt.ci < g.n_layers - 1) pt.ci += 1;
             else status = GBMC_STATUS_LEAKED_FAR;
@@ -751,32 +753,32 @@ __device__ __forceinline__ int cross(const Params& P, const DevProblem& pr, Part
         relook = m != pt.mat;
         pt.mat = m;
     } else if (pt.surf == kSurfX) {
-        if (pt.u > 0.0) {
+        if (is_pos(pt.u)) {
             pt.x = __ldg(wall + pt.ci + 1);
             if (pt.ci < g.n - 1) pt.ci += 1;
-            else if (g.bc_side == GBMC_BC_REFLECT) pt.u = -pt.u;
+            else if (g.bc_side == GBMC_BC_REFLECT) pt.u = flip_sign(pt.u);
             else status = GBMC_STATUS_LEAKED;
         } else {
             pt.x = __ldg(wall + pt.ci);
             if (pt.ci > 0) pt.ci -= 1;
-            else if (g.bc_side == GBMC_BC_REFLECT) pt.u = -pt.u;
+            else if (g.bc_side == GBMC_BC_REFLECT) pt.u = flip_sign(pt.u);
             else status = GBMC_STATUS_LEAKED;
         }
     } else if (pt.surf == kSurfY) {
-        if (pt.v > 0.0) {
+        if (is_pos(pt.v)) {
             pt.y = __ldg(wall + pt.cj + 1);
             if (pt.cj < g.n - 1) pt.cj += 1;
-            else if (g.bc_side == GBMC_BC_REFLECT) pt.v = -pt.v;
+            else if (g.bc_side == GBMC_BC_REFLECT) pt.v = flip_sign(pt.v);
             else status = GBMC_STATUS_LEAKED;
         } else {
             pt.y = __ldg(wall + pt.cj);
             if (pt.cj > 0) pt.cj -= 1;
-            else if (g.bc_side == GBMC_BC_REFLECT) pt.v = -pt.v;
+            else if (g.bc_side == GBMC_BC_REFLECT) pt.v = flip_sign(pt.v);
             else status = GBMC_STATUS_LEAKED;
         }
     } else {  // z planes
-        pt.z = pt.w > 0.0 ? g.height : 0.0;
-        if (g.bc_z == GBMC_BC_REFLECT) pt.w = -pt.w;
+        pt.z = is_pos(pt.w) ? g.height : 0.0;
+        if (g.bc_z == GBMC_BC_REFLECT) pt.w = flip_sign(pt.w);
         else status = GBMC_STATUS_LEAKED;
     }
     if (!status && g.kind == GBMC_GEOM_SLAB) {
@@ -887,6 +889,7 @@ __global__ void __launch_bounds__(256, 2) k_raytrace(Params P) {
     Stream r;
     int32_t flights = 0;
     double a_uv = 0.0;
+    int32_t ebin = 0;
     double fw = 0.0;   // weight summed over this particle's flights
     // the lane's flight scores, summed over its particles of one problem
     int acc_prob = -1;
@@ -908,6 +911,7 @@ __global__ void __launch_bounds__(256, 2) k_raytrace(Params P) {
                     pt = P.B.p[slot];
                     stream_of(P.probs[pt.prob], pt, r);
                     a_uv = pt.u * pt.u + pt.v * pt.v;   // fixed until the particle collides
+                    ebin = energy_bin(P.T, pt.E);        // so is the tally energy bin
                     flights = 0;
                     fw = 0.0;
                     have = true;
@@ -923,7 +927,7 @@ __global__ void __launch_bounds__(256, 2) k_raytrace(Params P) {
         if (have) {
             const DevProblem& pr = P.probs[pt.prob];
             double xi;
-            bool col = fly(P, pr, pt, r, xi, a_uv);
+            bool col = fly(P, pr, pt, r, xi, a_uv, ebin);
             ++flights;
             fw += pt.wgt;
             if (col) {
@@ -1100,7 +1104,7 @@ __global__ void __launch_bounds__(256) k_tail(Params P) {
             __syncwarp();     // the lanes' running-sum checkpoints, visible to lane 0
             if (lane == 0) {
                 double xi;
-                bool col = fly(P, pr, pt, r, xi, pt.u * pt.u + pt.v * pt.v);
+                bool col = fly(P, pr, pt, r, xi, pt.u * pt.u + pt.v * pt.v, energy_bin(P.T, pt.E));
                 ++nf;
                 wf += pt.wgt;
                 if (col) {
