@@ -269,6 +269,7 @@ void free_bank(gbmc_ctx* c) {
     Queues& Q = c->Q;
     dfree(Q.lq[0]); dfree(Q.lq[1]); dfree(Q.aq[0]); dfree(Q.aq[1]);
     dfree(Q.sq); dfree(Q.cq); dfree(Q.fq); dfree(Q.lqs); dfree(Q.keys[0]); dfree(Q.keys[1]);
+    dfree(Q.rank[0]); dfree(Q.rank[1]);
     dfree(Q.hist[0]); dfree(Q.hist[1]); dfree(Q.cursor); dfree(Q.btot);
     c->capacity = 0;
 }
@@ -284,6 +285,7 @@ int ensure_bank(gbmc_ctx* c, int32_t M) {
     rc |= dalloc(c, &Q.aq[0], n); rc |= dalloc(c, &Q.aq[1], n);
     rc |= dalloc(c, &Q.sq, n); rc |= dalloc(c, &Q.cq, n); rc |= dalloc(c, &Q.fq, n);
     rc |= dalloc(c, &Q.lqs, n); rc |= dalloc(c, &Q.keys[0], n); rc |= dalloc(c, &Q.keys[1], n);
+    rc |= dalloc(c, &Q.rank[0], n); rc |= dalloc(c, &Q.rank[1], n);
     rc |= dalloc(c, &Q.hist[0], kSortBuckets); rc |= dalloc(c, &Q.hist[1], kSortBuckets);
     rc |= dalloc(c, &Q.cursor, kSortBuckets);
     rc |= dalloc(c, &Q.btot, kSortBuckets / 1024);

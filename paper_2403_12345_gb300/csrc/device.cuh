@@ -147,6 +147,7 @@ struct Queues {
     int32_t* fq;        // free slots
     int32_t* lqs;       // lookup queue in (material, energy) order
     uint32_t* keys[2];  // sort keys of lq[b], written by the kernel that appends the entry
+    uint32_t* rank[2];  // each entry's rank within its bucket, from the append's count
     uint32_t* hist[2];  // [kSortBuckets] bucket counts of lq[b], counted at the append
     uint32_t* cursor;   // [kSortBuckets] bucket write positions (block-local)
     uint32_t* btot;     // [kSortBuckets / 1024] bucket-block totals

@@ -49,6 +49,18 @@ __device__ __forceinline__ void warp_count(uint32_t* hist, uint32_t key, bool va
     if (valid && lane == __ffs(peers) - 1) atomicAdd(&hist[key], (uint32_t)__popc(peers));
 }
 
+// warp_count that also returns the lane's rank among the entries of its
+// bucket counted so far (the sort's scatter then needs no atomics).
+__device__ __forceinline__ uint32_t warp_count_rank(uint32_t* hist, uint32_t key, bool valid) {
+    unsigned peers = __match_any_sync(kFull, valid ? key : 0xffffffffu);
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(peers) - 1;
+    uint32_t base = 0u;
+    if (valid && lane == leader) base = atomicAdd(&hist[key], (uint32_t)__popc(peers));
+    base = __shfl_sync(kFull, base, leader);
+    return base + (uint32_t)__popc(peers & lanemask_lt());
+}
+
 // warp_append into lookup queue b with the entry's sort key (all 32 lanes).
 __device__ __forceinline__ void lookup_append(const Params& P, int b, int32_t* count, int32_t slot,
                                               bool pred, double E, int32_t m) {
@@ -60,15 +72,18 @@ __device__ __forceinline__ void lookup_append(const Params& P, int b, int32_t* c
     if (lane == leader) base = atomicAdd(count, __popc(msk));
     base = __shfl_sync(kFull, base, leader);
     uint32_t key = 0;
+    int pos = base + __popc(msk & lanemask_lt());
     if (pred) {
-        int pos = base + __popc(msk & lanemask_lt());
         P.Q.lq[b][pos] = slot;
         if (P.sort) {
             key = sort_key(P, E, m);
             P.Q.keys[b][pos] = key;
         }
     }
-    if (P.sort) warp_count(P.Q.hist[b], key, pred);
+    if (P.sort) {
+        uint32_t rk = warp_count_rank(P.Q.hist[b], key, pred);
+        if (pred) P.Q.rank[b][pos] = rk;
+    }
 }
 
 // ---------------------------------------------------------------- scalar tallies
@@ -339,8 +354,11 @@ __global__ void __launch_bounds__(256) k_source(Params P) {
             if (P.sort) key = sort_key(P, rec.E, rec.mat);
         }
         if (P.sort) {
-            if (valid) P.Q.keys[cur][lb + idx] = key;
-            warp_count(P.Q.hist[cur], key, valid);
+            uint32_t rk = warp_count_rank(P.Q.hist[cur], key, valid);
+            if (valid) {
+                P.Q.keys[cur][lb + idx] = key;
+                P.Q.rank[cur][lb + idx] = rk;
+            }
         }
         sc.add(P.Y, primary, prob, GBMC_S_HISTORY, 1.0, 1ull);
     }
@@ -445,10 +463,17 @@ __global__ void __launch_bounds__(256) k_sort_scatter(Params P) {
     block_offsets(P.Q.btot, boff);
     int32_t n = c->lookup_n;
     const int32_t* q = P.Q.lq[c->cur];
-    GBMC_WARP_LOOP(idx, valid, n) {
-        uint32_t key = valid ? P.Q.keys[c->cur][idx] : 0u;
-        int32_t slot = valid ? q[idx] : 0;
-        warp_place_off(P.Q.cursor, boff, key, valid, P.Q.lqs, slot);
+    const uint32_t* keys = P.Q.keys[c->cur];
+    const uint32_t* rank = P.Q.rank[c->cur];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        // bucket start (block offset + offset within the block) + rank
+        uint32_t key = keys[i];
+        uint32_t pos = boff[key >> 10] + __ldg(P.Q.cursor + key) + rank[i];
+        if (pos < (uint32_t)n)
+            P.Q.lqs[pos] = q[i];
+        else
+            atomicCAS(&P.ctl->err, 0, GBMC_ERR_DEVICE_FLAG);   // counts out of step: not reached
     }
 }
 

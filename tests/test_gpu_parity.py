@@ -212,6 +212,46 @@ def test_lookup_macro_matches_oracle(precision, sort):
         assert np.array_equal(sa[sel].view(np.int64), ra.view(np.int64))
 
 
+def _edge_energies(prob, mat):
+    """Every grid point of the material's nuclides, one ulp either side,
+    interval midpoints, and energies below and above every grid."""
+    pts = []
+    for q in range(prob.mat_off[mat], prob.mat_off[mat + 1]):
+        i = prob.nuc_id[q]
+        g = prob.energy[prob.grid_off[i]:prob.grid_off[i + 1]]
+        pts += [g, np.nextafter(g, 0.0), np.nextafter(g, np.inf), 0.5 * (g[1:] + g[:-1])]
+    E = np.concatenate(pts + [np.array([1e-9, 1e-7, 3e7, 1e9])])
+    return np.ascontiguousarray(E[E > 0.0])
+
+
+@pytest.mark.parametrize("precision", [gbmc.FP64, gbmc.FP32])
+@pytest.mark.parametrize("which", ["dense", "sparse"])
+def test_lookup_macro_at_grid_points_and_edges(precision, which):
+    """Exact hits (E - E_k = 0), neighbours, extrapolation outside the grids;
+    dense grids take the integer-unit interpolation, the sparse ones (2-9
+    points over 12 decades: intervals wider than 2^10) its binary64 fallback."""
+    import torch
+    if which == "dense":
+        prob, _, _ = synth.make_stress_lookup(n_queries=1, n_nuc=12, n_in_mat=8, n_points=400)
+    else:
+        prob = synth.make_tiny_problem(seed=11, n_nuc=6, n_points=(2, 9))
+    E = _edge_energies(prob, 0)
+    ctx = make_ctx(prob, (precision,))
+    try:
+        dE = torch.tensor(E, device="cuda")
+        dm = torch.zeros(len(E), dtype=torch.int32, device="cuda")
+        st = torch.empty_like(dE)
+        sa = torch.empty_like(dE)
+        ctx.lookup_macro(dE, dm, st, sa, precision=precision)
+        torch.cuda.synchronize()
+        st, sa = st.cpu().numpy(), sa.cpu().numpy()
+    finally:
+        ctx.close()
+    rt, ra = oracle.macro(prob, 0, E, precision=precision)
+    assert np.array_equal(st.view(np.int64), rt.view(np.int64))
+    assert np.array_equal(sa.view(np.int64), ra.view(np.int64))
+
+
 def test_invalid_inputs_rejected_before_launch():
     p = synth.make_tiny_problem(seed=35, n_nuc=2, n_points=(5, 9))
     ctx = gbmc.Context(0)
