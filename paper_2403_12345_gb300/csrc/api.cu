@@ -307,7 +307,9 @@ int ensure_bank(gbmc_ctx* c, int32_t M) {
 // (rounded up to the lookup's groups of 4), binary32 one per kCumGroup
 int64_t cum_row(const gbmc_ctx* c) {
     if (c->opt.precision == GBMC_FP64) return ((int64_t)c->max_nuc_per_mat + 3) / 4 * 4;
-    return ((int64_t)c->max_nuc_per_mat + kCumGroup - 1) / kCumGroup;
+    // binary32: one checkpoint per kCumGroup entries, rows padded to whole
+    // float4s (the lookup stores four checkpoints at a time)
+    return ((int64_t)c->max_nuc_per_mat + 4 * kCumGroup - 1) / (4 * kCumGroup) * 4;
 }
 
 constexpr size_t kCumBudget = (size_t)16 << 30;

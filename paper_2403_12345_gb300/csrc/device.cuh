@@ -575,7 +575,7 @@ __device__ __forceinline__ double micro64(const Tables& T, int32_t q, double E) 
 // per nuclide replaces the index load, the bisection probes and the bracket
 // loads; a bucket with hi - lo > 6 is searched by bisection instead.
 constexpr int kIlp32 = 4;   // nuclides whose windows are in flight together
-static_assert(kIlp32 % kCumGroup == 0, "whole checkpoint groups per lock-step group");
+static_assert(kIlp32 == kCumGroup, "one checkpoint per lock-step group");
 constexpr int kPad32 = 8;   // sentinel pairs after each nuclide's grid
 
 __device__ __forceinline__ Desc32 load_desc32(const Desc32* p) {
@@ -736,6 +736,7 @@ __device__ __forceinline__ void macro32(const Tables& T, int32_t m, double E, do
     int32_t q0 = __ldg(T.mat_off + m), q1 = __ldg(T.mat_off + m + 1);
     uint32_t eb = (uint32_t)__float_as_int(__double2float_rd(E));
     float Ef = __double2float_rn(E);
+    float4 pend = make_float4(0.0f, 0.0f, 0.0f, 0.0f);   // checkpoints not yet stored
     for (int32_t q = q0; q < q1; q += kIlp32) {
         Desc32 d[kIlp32];
         const float4* pw[kIlp32];
@@ -763,9 +764,16 @@ __device__ __forceinline__ void macro32(const Tables& T, int32_t m, double E, do
             run[u] = at;
         }
         if (cum) {
-#pragma unroll
-            for (int u = kCumGroup - 1; u < kIlp32; u += kCumGroup)
-                if (q + u - (kCumGroup - 1) < q1) cum[(q - q0 + u) / kCumGroup] = run[u];
+            // the group's checkpoint; four of them leave as one 16-byte store
+            // (the rows are padded to whole float4s)
+            int32_t g = (q - q0) / kCumGroup;
+            float v = run[kIlp32 - 1];
+            int k = g & 3;
+            pend.x = k == 0 ? v : pend.x;
+            pend.y = k == 1 ? v : pend.y;
+            pend.z = k == 2 ? v : pend.z;
+            pend.w = k == 3 ? v : pend.w;
+            if (k == 3 || q + kIlp32 >= q1) reinterpret_cast<float4*>(cum)[g >> 2] = pend;
         }
     }
     st = (double)at;
