@@ -575,7 +575,8 @@ __device__ __forceinline__ double micro64(const Tables& T, int32_t q, double E) 
 // per nuclide replaces the index load, the bisection probes and the bracket
 // loads; a bucket with hi - lo > 6 is searched by bisection instead.
 constexpr int kIlp32 = 4;   // nuclides whose windows are in flight together
-static_assert(kIlp32 == kCumGroup, "one checkpoint per lock-step group");
+static_assert(kIlp32 % kCumGroup == 0 && kIlp32 / kCumGroup <= 4,
+              "whole checkpoint groups per lock-step group");
 constexpr int kPad32 = 8;   // sentinel pairs after each nuclide's grid
 
 __device__ __forceinline__ Desc32 load_desc32(const Desc32* p) {
@@ -764,16 +765,23 @@ __device__ __forceinline__ void macro32(const Tables& T, int32_t m, double E, do
             run[u] = at;
         }
         if (cum) {
-            // the group's checkpoint; four of them leave as one 16-byte store
-            // (the rows are padded to whole float4s)
-            int32_t g = (q - q0) / kCumGroup;
-            float v = run[kIlp32 - 1];
-            int k = g & 3;
-            pend.x = k == 0 ? v : pend.x;
-            pend.y = k == 1 ? v : pend.y;
-            pend.z = k == 2 ? v : pend.z;
-            pend.w = k == 3 ? v : pend.w;
-            if (k == 3 || q + kIlp32 >= q1) reinterpret_cast<float4*>(cum)[g >> 2] = pend;
+            // the group's checkpoints (one per kCumGroup entries) gathered
+            // into whole float4s, each leaving as one 16-byte store (the rows
+            // are padded to whole float4s)
+            constexpr int kPer = kIlp32 / kCumGroup;   // checkpoints per lock-step group
+            constexpr int kGroups = 4 / kPer;          // lock-step groups per float4
+            int32_t g = (q - q0) / kIlp32;
+            int k = g % kGroups;
+#pragma unroll
+            for (int j = 0; j < kPer; ++j) {
+                float v = run[(j + 1) * kCumGroup - 1];
+                int e = k * kPer + j;
+                pend.x = e == 0 ? v : pend.x;
+                pend.y = e == 1 ? v : pend.y;
+                pend.z = e == 2 ? v : pend.z;
+                pend.w = e == 3 ? v : pend.w;
+            }
+            if (k == kGroups - 1 || q + kIlp32 >= q1) reinterpret_cast<float4*>(cum)[g / kGroups] = pend;
         }
     }
     st = (double)at;
