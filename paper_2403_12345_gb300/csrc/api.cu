@@ -299,14 +299,13 @@ int ensure_bank(gbmc_ctx* c, int32_t M) {
     return GBMC_OK;
 }
 
-// Running-sum cache: one row per bank slot of the most nuclides of any
-// material rounded up to 8 (rows start on 32-byte boundaries and the lookup
-// stores 4 sums at a time), in the table precision.  Above kCumBudget bytes
-// the collision recomputes instead.
-// running-sum entries per slot: binary64 every sum of the largest material
-// (rounded up to the lookup's groups of 4), binary32 one per kCumGroup
+// Running-sum cache: one row per bank slot, in the table precision; above
+// kCumBudget bytes the collision recomputes instead.  Entries per row:
+// binary64 every sum of the largest material, rounded up to the lookup's
+// lock-step groups (kIlp, whole 32-byte stores); binary32 one checkpoint per
+// kCumGroup entries, rounded up to whole float4s.
 int64_t cum_row(const gbmc_ctx* c) {
-    if (c->opt.precision == GBMC_FP64) return ((int64_t)c->max_nuc_per_mat + 3) / 4 * 4;
+    if (c->opt.precision == GBMC_FP64) return ((int64_t)c->max_nuc_per_mat + kIlp - 1) / kIlp * kIlp;
     // binary32: one checkpoint per kCumGroup entries, rows padded to whole
     // float4s (the lookup stores four checkpoints at a time)
     return ((int64_t)c->max_nuc_per_mat + 4 * kCumGroup - 1) / (4 * kCumGroup) * 4;

@@ -657,7 +657,7 @@ __device__ __forceinline__ float micro32(const Tables& T, int32_t q, double E) {
 // independent chains of dependent loads in flight per thread); the terms are
 // then formed and added strictly in the listed order.
 constexpr int kIlp = 4;
-static_assert(kIlp == 4, "the running sums are stored four at a time");
+static_assert(kIlp % 4 == 0, "the running sums are stored in whole 32-byte groups");
 
 template <class U>
 __device__ __forceinline__ void brackets(const Tables& T, const Desc64* dq, const uint32_t* idx,
@@ -719,11 +719,11 @@ __device__ __forceinline__ void macro64(const Tables& T, int32_t m, double E, do
             run[u] = at;
         }
         // every running sum (binary64 tables keep them all); the row holds the
-        // material's count rounded up to 4, so whole groups are written
+        // material's count rounded up to kIlp, so whole groups are written
         if (cum) {
             double2* d = reinterpret_cast<double2*>(cum + (q - q0));
-            d[0] = make_double2(run[0], run[1]);
-            d[1] = make_double2(run[2], run[3]);
+#pragma unroll
+            for (int j = 0; j < kIlp; j += 2) d[j / 2] = make_double2(run[j], run[j + 1]);
         }
     }
     st = at;
