@@ -300,12 +300,17 @@ int ensure_bank(gbmc_ctx* c, int32_t M) {
 }
 
 // Running-sum cache: one row per bank slot, in the table precision; above
-// kCumBudget bytes the collision recomputes instead.  Entries per row:
-// binary64 every sum of the largest material, rounded up to the lookup's
-// lock-step groups (kIlp, whole 32-byte stores); binary32 one checkpoint per
-// kCumGroup entries, rounded up to whole float4s.
+// kCumBudget bytes the collision recomputes instead.  Entries per row, for
+// the largest material: binary64 one checkpoint per kCumGroup64 entries
+// (every sum when that is 1, rounded up to the lookup's lock-step groups for
+// whole 32-byte stores; else rounded up to an even count for 16-byte
+// stores); binary32 one checkpoint per kCumGroup entries, rounded up to
+// whole float4s.
 int64_t cum_row(const gbmc_ctx* c) {
-    if (c->opt.precision == GBMC_FP64) return ((int64_t)c->max_nuc_per_mat + kIlp - 1) / kIlp * kIlp;
+    if (c->opt.precision == GBMC_FP64) {
+        if (kCumGroup64 == 1) return ((int64_t)c->max_nuc_per_mat + kIlp - 1) / kIlp * kIlp;
+        return ((int64_t)c->max_nuc_per_mat + 2 * kCumGroup64 - 1) / (2 * kCumGroup64) * 2;
+    }
     // binary32: one checkpoint per kCumGroup entries, rows padded to whole
     // float4s (the lookup stores four checkpoints at a time)
     return ((int64_t)c->max_nuc_per_mat + 4 * kCumGroup - 1) / (4 * kCumGroup) * 4;

@@ -488,12 +488,14 @@ __device__ __forceinline__ double ln_series(double x) {
 // ---------------------------------------------------------------- lookup
 // The lookup stores the running sum after every cum_group<PREC>() entries of
 // the material (checkpoints); the collision recomputes at most that many
-// terms.  binary32 tables keep one checkpoint per four entries (a quarter of
-// the stores); binary64 tables keep every sum, since recomputing a binary64
-// term costs a division on the scarce binary64 units.
-constexpr int kCumGroup = 4;   // binary32
+// terms.  Both precisions keep one checkpoint per four entries: a quarter of
+// the stores of keeping every sum, whose write stream (8 bytes a nuclide in
+// binary64) evicted the tables from L2; the collision's few recomputed terms
+// cost less than those stores.
+constexpr int kCumGroup = 4;     // binary32
+constexpr int kCumGroup64 = 4;   // binary64: 1 (every sum) or kIlp (one per lock-step group)
 template <int PREC>
-__host__ __device__ constexpr int cum_group() { return PREC == GBMC_FP64 ? 1 : kCumGroup; }
+__host__ __device__ constexpr int cum_group() { return PREC == GBMC_FP64 ? kCumGroup64 : kCumGroup; }
 // Bracket search: the largest j in [0, n-2] with grid[j] <= E.  Positive IEEE
 // values order like their bit patterns, so every comparison runs on the
 // integer pipe (binary64 compares would occupy the scarce FP64 units).
@@ -658,6 +660,7 @@ __device__ __forceinline__ float micro32(const Tables& T, int32_t q, double E) {
 // then formed and added strictly in the listed order.
 constexpr int kIlp = 4;
 static_assert(kIlp % 4 == 0, "the running sums are stored in whole 32-byte groups");
+static_assert(kCumGroup64 == 1 || kCumGroup64 == kIlp, "binary64 checkpoints: every sum or one per group");
 
 template <class U>
 __device__ __forceinline__ void brackets(const Tables& T, const Desc64* dq, const uint32_t* idx,
@@ -703,6 +706,7 @@ __device__ __forceinline__ void macro64(const Tables& T, int32_t m, double E, do
     int32_t q0 = __ldg(T.mat_off + m), q1 = __ldg(T.mat_off + m + 1);
     const unsigned long long* g = reinterpret_cast<const unsigned long long*>(T.e64);
     unsigned long long eb = (unsigned long long)__double_as_longlong(E);
+    double2 pend = make_double2(0.0, 0.0);   // checkpoint not yet stored
     for (int32_t q = q0; q < q1; q += kIlp) {
         int64_t pos[kIlp];
         double run[kIlp];
@@ -718,12 +722,20 @@ __device__ __forceinline__ void macro64(const Tables& T, int32_t m, double E, do
             }
             run[u] = at;
         }
-        // every running sum (binary64 tables keep them all); the row holds the
-        // material's count rounded up to kIlp, so whole groups are written
         if (cum) {
-            double2* d = reinterpret_cast<double2*>(cum + (q - q0));
+            if (kCumGroup64 == 1) {
+                // every running sum; the row holds the material's count
+                // rounded up to kIlp, so whole groups are written
+                double2* d = reinterpret_cast<double2*>(cum + (q - q0));
 #pragma unroll
-            for (int j = 0; j < kIlp; j += 2) d[j / 2] = make_double2(run[j], run[j + 1]);
+                for (int j = 0; j < kIlp; j += 2) d[j / 2] = make_double2(run[j], run[j + 1]);
+            } else {
+                // one checkpoint per group, two groups to a 16-byte store (the
+                // row is rounded up to an even count)
+                int32_t gq = (q - q0) / kIlp;
+                if (gq & 1) pend.y = run[kIlp - 1]; else pend.x = run[kIlp - 1];
+                if ((gq & 1) || q + kIlp >= q1) reinterpret_cast<double2*>(cum)[gq >> 1] = pend;
+            }
         }
     }
     st = at;
@@ -813,7 +825,9 @@ __device__ __forceinline__ void macro_warp(const Tables& T, int32_t m, double E,
             for (int k = 0; k < kmax; ++k) {
                 at = at + __shfl_sync(full, t, k);
                 if (SA) aa = aa + __shfl_sync(full, p, k);
-                if (cum && lane == k) ((double*)cum)[(int64_t)(c + k - q0) * stride] = at;
+                if (cum && lane == k &&
+                    ((c + k - q0) % kCumGroup64 == kCumGroup64 - 1 || c + k == q1 - 1))
+                    ((double*)cum)[(int64_t)((c + k - q0) / kCumGroup64) * stride] = at;
             }
         }
         st = at;
