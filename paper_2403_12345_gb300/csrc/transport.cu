@@ -898,6 +898,15 @@ __device__ __forceinline__ int leak_kind(int status) {
 // Work-stealing: each lane flies its particle one flight per step; a lane
 // whose particle has left takes the next queue entry (one atomic per warp
 // per refill), so no lane idles behind a long-streaming neighbour.
+//
+// Drain: once the queue is exhausted, a warp with at most kDrainLanes busy
+// lanes hands its particles (each after at least one flight since it was
+// taken) to the next iteration's advance queue, where they are packed with
+// the other work, instead of flying them with the rest of its lanes idle.
+// Only for queues of at least kDrainMinQueue entries, so that a few particles
+// left in flight are not passed from iteration to iteration.
+constexpr int kDrainLanes = 8;
+constexpr int32_t kDrainMinQueue = 4096;
 
 __global__ void __launch_bounds__(256, 2) k_raytrace(Params P) {
     Ctl* c = P.ctl;
@@ -946,10 +955,17 @@ __global__ void __launch_bounds__(256, 2) k_raytrace(Params P) {
             }
         }
         if (!__any_sync(kFull, have)) break;
-        int status = 0, route = 0;   // route 1: collision, 2: lookup
+        bool drain = n >= kDrainMinQueue && __any_sync(kFull, exhausted) &&
+                     __popc(__ballot_sync(kFull, have)) <= kDrainLanes;
+        int status = 0, route = 0;   // route 1: collision, 2: lookup, 3: next iteration
         bool fin = false;
         WwOut wo{0, 0.0, 0.0};
-        if (have) {
+        if (have && drain && flights > 0) {
+            route = 3;
+            fin = true;
+            P.B.p[slot] = pt;
+            nflights += (unsigned long long)flights;
+        } else if (have) {
             const DevProblem& pr = P.probs[pt.prob];
             double xi;
             bool col = fly(P, pr, pt, r, xi, a_uv, ebin);
@@ -1001,6 +1017,7 @@ __global__ void __launch_bounds__(256, 2) k_raytrace(Params P) {
             warp_append(P.Q.fq, &c->n_free, slot, dead);
             warp_append(P.Q.cq, &c->n_cq, slot, fin && route == 1);
             lookup_append(P, nxt, &c->n_lq[nxt], slot, fin && route == 2, pt.E, pt.mat);
+            warp_append(P.Q.aq[nxt], &c->n_aq[nxt], slot, fin && route == 3);
             if (fin) have = false;
         }
     }
