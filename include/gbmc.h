@@ -109,7 +109,13 @@ typedef struct {
                                 particles are in flight, the loop stops and a
                                 tail kernel finishes them, one warp per particle
                                 (default 4096; -1: never) */
-    int32_t reserved[5];
+    int32_t wide_windows;    /* binary32 lookup reads each 64-byte bucket window as
+                                two 32-byte loads (1) instead of four 16-byte ones
+                                (0, default): half the L1 wavefronts when the lanes
+                                of a warp read distinct windows (tables far beyond
+                                L2, sparse particles), more registers otherwise.
+                                Same results either way. */
+    int32_t reserved[4];
 } gbmc_options;
 
 /* One geometry (and its source).  Fields of other kinds are ignored. */

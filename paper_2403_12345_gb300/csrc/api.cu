@@ -239,6 +239,8 @@ void fill_defaults(gbmc_options* o) {
 int check_options(gbmc_ctx* c, const gbmc_options* o) {
     if (o->precision != GBMC_FP64 && o->precision != GBMC_FP32)
         return fail(c, GBMC_ERR_INVALID_ARG, "precision must be GBMC_FP64 or GBMC_FP32");
+    if (o->wide_windows != 0 && o->wide_windows != 1)
+        return fail(c, GBMC_ERR_INVALID_ARG, "wide_windows must be 0 or 1");
     if (o->block_lookup != 256 || o->block_event != 256)
         return fail(c, GBMC_ERR_UNSUPPORTED, "block sizes other than 256 are not built");
     if (o->blocks_per_sm > 32)
@@ -449,6 +451,7 @@ Params make_params(gbmc_ctx* c) {
     P.sort_min = c->opt.sort_min;
     P.warp_lookup_max = c->opt.warp_lookup_max;
     P.tail_max = c->opt.tail_max;
+    P.wide_windows = c->opt.wide_windows;
     P.max_iter = c->opt.max_iterations;
     sort_params(c, P);
     P.planes = c->d_planes;
@@ -2054,6 +2057,15 @@ extern "C" int gbmc_autotune(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* pr
         if ((rc = probe_ms(c, pr, s, o, &t_ms))) return rc;
         ++trials;
         if (t_ms < best_ms * keep) { best_ms = t_ms; best = o; }
+    }
+    // binary32 bucket windows as 32-byte loads
+    if (best.precision == GBMC_FP32) {
+        gbmc_options o = best;
+        o.wide_windows = 1 - best.wide_windows;
+        double t;
+        if ((rc = probe_ms(c, pr, s, o, &t))) return rc;
+        ++trials;
+        if (t < best_ms * keep) { best_ms = t; best = o; }
     }
     // the sort threshold (sorting itself stays on: its gain grows with the
     // queue, and the probes' queues are the fraction's size)

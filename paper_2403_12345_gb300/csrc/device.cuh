@@ -214,6 +214,7 @@ struct Params {
     int32_t tail_max;        // stop the loop and finish in the tail kernel at or below
                              // this many particles in flight (source exhausted)
     int32_t max_iter;
+    int32_t wide_windows;    // binary32 bucket windows as two 32-byte loads (host: kernel choice)
     uint32_t sort_shift;     // energy-bits >> shift = bucket within a material
     uint32_t bpm_log2;       // log2 buckets per material
     int32_t use_cond;        // 1 inside the graph while-body, 0 for eager launches
@@ -597,9 +598,24 @@ __device__ __forceinline__ const float4* window_of(const Tables& T, const Desc32
     return T.bw32 + ((int64_t)d.bw_off + b) * 4;
 }
 
+// A bucket window (64 bytes, 64-byte aligned in the pool) as four 16-byte
+// loads, or (WIDE) as two 256-bit loads: with the lanes of a warp on distinct
+// windows each load instruction costs one L1 wavefront per lane, so two loads
+// take half the wavefronts of four, at the price of registers (a 256-bit load
+// fills eight consecutive ones).
+template <bool WIDE = false>
 __device__ __forceinline__ void load_window(const float4* p, float4* q) {
+    if (WIDE) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) q[k] = __ldg(p + k);
+        for (int k = 0; k < 4; k += 2)
+            asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                : "=f"(q[k].x), "=f"(q[k].y), "=f"(q[k].z), "=f"(q[k].w), "=f"(q[k + 1].x),
+                  "=f"(q[k + 1].y), "=f"(q[k + 1].z), "=f"(q[k + 1].w)
+                : "l"(p + k));
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) q[k] = __ldg(p + k);
+    }
 }
 
 // The bracket's end points (its pair and the next) from the window w loaded
@@ -742,7 +758,7 @@ __device__ __forceinline__ void macro64(const Tables& T, int32_t m, double E, do
     sa = aa;
 }
 
-template <bool SA = true>
+template <bool SA = true, bool WIDE = false>
 __device__ __forceinline__ void macro32(const Tables& T, int32_t m, double E, double& st,
                                         double& sa, float* cum = nullptr) {
     float at = 0.0f, aa = 0.0f;
@@ -760,7 +776,7 @@ __device__ __forceinline__ void macro32(const Tables& T, int32_t m, double E, do
         }
         float4 w[kIlp32][4];
 #pragma unroll
-        for (int u = 0; u < kIlp32; ++u) load_window(pw[u], w[u]);
+        for (int u = 0; u < kIlp32; ++u) load_window<WIDE>(pw[u], w[u]);
         float2 p0[kIlp32], p1[kIlp32];
 #pragma unroll
         for (int u = 0; u < kIlp32; ++u) bracket32(T, d[u], pw[u], w[u], eb, p0[u], p1[u]);

@@ -479,8 +479,9 @@ __global__ void __launch_bounds__(256) k_sort_scatter(Params P) {
 
 // ---------------------------------------------------------------- lookup event
 
-template <int PREC, bool SA>
-// Thread mode (long queues): one particle per thread.
+// Thread mode (long queues): one particle per thread.  WIDE: binary32
+// bucket windows as 32-byte loads.
+template <int PREC, bool SA, bool WIDE = false>
 __global__ void __launch_bounds__(256, PREC == GBMC_FP64 ? 4 : 3) k_lookup(Params P) {
     const Ctl* c = P.ctl;
     int32_t n = c->lookup_n;
@@ -499,7 +500,8 @@ __global__ void __launch_bounds__(256, PREC == GBMC_FP64 ? 4 : 3) k_lookup(Param
                 macro64<SA>(P.T, m, E, st, sa,
                             P.cum ? (double*)P.cum + slot * P.cum_stride : nullptr);
             else
-                macro32<SA>(P.T, m, E, st, sa, P.cum ? (float*)P.cum + slot * P.cum_stride : nullptr);
+                macro32<SA, WIDE>(P.T, m, E, st, sa,
+                                  P.cum ? (float*)P.cum + slot * P.cum_stride : nullptr);
             P.B.p[slot].st = st;
             if (SA) P.B.p[slot].sa = sa;
             aq[idx] = slot;
@@ -1413,10 +1415,16 @@ static void launch_lookups(const Params& P, const LaunchCfg& L, cudaStream_t s) 
     } else {
         if (sa) {
             k_lookup_warp<GBMC_FP32, true><<<L.grid_lookup, 256, 0, s>>>(P);
-            k_lookup<GBMC_FP32, true><<<L.grid_lookup, 256, 0, s>>>(P);
+            if (P.wide_windows)
+                k_lookup<GBMC_FP32, true, true><<<L.grid_lookup, 256, 0, s>>>(P);
+            else
+                k_lookup<GBMC_FP32, true><<<L.grid_lookup, 256, 0, s>>>(P);
         } else {
             k_lookup_warp<GBMC_FP32, false><<<L.grid_lookup, 256, 0, s>>>(P);
-            k_lookup<GBMC_FP32, false><<<L.grid_lookup, 256, 0, s>>>(P);
+            if (P.wide_windows)
+                k_lookup<GBMC_FP32, false, true><<<L.grid_lookup, 256, 0, s>>>(P);
+            else
+                k_lookup<GBMC_FP32, false><<<L.grid_lookup, 256, 0, s>>>(P);
         }
     }
 }

@@ -56,6 +56,12 @@ def test_lattice_fp32_tables_parity_and_error_vs_fp64():
     assert rel < 1e-2
 
 
+def test_lattice_fp32_wide_windows_parity():
+    # the binary32 lookup's 32-byte window loads give the same results
+    p = synth.make_config(3, grid_scale=0.05)
+    _parity(p, 20_000, precision=gbmc.FP32, wide_windows=1)
+
+
 def test_slab_parity():
     p = synth.make_tiny_problem(seed=31, n_nuc=4, n_points=(20, 200), kind=synth.GEOM_SLAB,
                                 n_particles=20_000)
