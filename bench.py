@@ -768,7 +768,8 @@ def main():
             "roofline": roof,
             "kernel_ms_per_batch": {k: v[0] for k, v in kt.items()},
             "events_per_batch": {k: pst[k] for k in ("lookups", "micro_lookups", "flights",
-                                                     "crossings", "collisions", "histories")},
+                                                     "crossings", "collisions", "histories",
+                                                     "handoffs")},
             "top_kernel": top,
             "cpu_baseline": cpu,
             "clocks": clk.summary(),

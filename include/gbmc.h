@@ -160,6 +160,10 @@ typedef struct {
     int64_t histories;        /* particles born */
     int32_t device_error;     /* 0, or the first GBMC_ERR_* a kernel flagged */
     int32_t reserved;
+    int64_t handoffs;         /* particles a ray-trace warp handed to the next
+                                 iteration once its queue was exhausted and at
+                                 most a quarter of its lanes were busy (each after
+                                 at least one flight) */
 } gbmc_stats;
 
 /* Per-kernel device time of one profiled run (gbmc_profile_problems). */

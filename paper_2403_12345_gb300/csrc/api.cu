@@ -1584,6 +1584,7 @@ int gbmc_read_stats(gbmc_ctx* c, gbmc_stats* out) {
     out->crossings = (int64_t)k.st_cross;
     out->collisions = (int64_t)k.st_coll;
     out->histories = (int64_t)k.st_hist;
+    out->handoffs = (int64_t)k.st_handoff;
     out->device_error = k.err;
     return rc;
 }

@@ -190,6 +190,7 @@ struct Ctl {
     int32_t n_prob;
     int32_t done, err, iter, pad;
     unsigned long long st_lookups, st_micro, st_flights, st_cross, st_coll, st_hist;
+    unsigned long long st_handoff;   // particles a drained ray-trace warp handed on
     double k_norm;               // k-eigenvalue: fission yield normalisation of this run
     int64_t bank_n, bank_total;  // source bank size, generation size (GBMC_SRC_BANK)
 };

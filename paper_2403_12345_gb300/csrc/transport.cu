@@ -919,7 +919,7 @@ __global__ void __launch_bounds__(256, 2) k_raytrace(Params P) {
     const int32_t* q = P.Q.aq[cur];
     int nxt = 1 - cur;
     int lane = threadIdx.x & 31;
-    unsigned long long crossings = 0, nflights = 0;
+    unsigned long long crossings = 0, nflights = 0, handoffs = 0;
     Particle pt;
     int32_t slot = 0;
     Stream r;
@@ -967,6 +967,7 @@ __global__ void __launch_bounds__(256, 2) k_raytrace(Params P) {
             fin = true;
             P.B.p[slot] = pt;
             nflights += (unsigned long long)flights;
+            ++handoffs;
         } else if (have) {
             const DevProblem& pr = P.probs[pt.prob];
             double xi;
@@ -1027,10 +1028,12 @@ __global__ void __launch_bounds__(256, 2) k_raytrace(Params P) {
     for (int o = 16; o > 0; o >>= 1) {
         crossings += __shfl_xor_sync(kFull, crossings, o);
         nflights += __shfl_xor_sync(kFull, nflights, o);
+        handoffs += __shfl_xor_sync(kFull, handoffs, o);
     }
     if (lane == 0 && nflights) {
         atomicAdd(&c->st_cross, crossings);
         atomicAdd(&c->st_flights, nflights);
+        if (handoffs) atomicAdd(&c->st_handoff, handoffs);
     }
     sc.flush(P.Y);
 }

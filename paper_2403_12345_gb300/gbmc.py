@@ -81,7 +81,8 @@ class Problem(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("iterations", C.c_int64), ("lookups", C.c_int64), ("micro_lookups", C.c_int64),
                 ("flights", C.c_int64), ("crossings", C.c_int64), ("collisions", C.c_int64),
-                ("histories", C.c_int64), ("device_error", C.c_int32), ("reserved", C.c_int32)]
+                ("histories", C.c_int64), ("device_error", C.c_int32), ("reserved", C.c_int32),
+                ("handoffs", C.c_int64)]
 
 
 class AutotuneReport(C.Structure):

@@ -56,6 +56,15 @@ def test_lattice_fp32_tables_parity_and_error_vs_fp64():
     assert rel < 1e-2
 
 
+def test_drained_warps_hand_particles_on():
+    # one batch far larger than a warp's share: warps drain, and the particles
+    # they hand to the next iteration end exactly as in the oracle
+    p = synth.make_config(2, grid_scale=0.05)
+    g, ref, st = _parity(p, 30_000)
+    assert st["handoffs"] > 0
+    assert st["flights"] == ref["counts"][oracle.S_FLIGHT]
+
+
 def test_lattice_fp32_wide_windows_parity():
     # the binary32 lookup's 32-byte window loads give the same results
     p = synth.make_config(3, grid_scale=0.05)
