@@ -643,6 +643,8 @@ Interval64 interval_record(double e0, double e1, double s0, double s1) {
     return r;
 }
 
+constexpr int32_t kIndexPer64 = 1;   // grid points per bucket of the binary64 coarse index
+
 // Coarse search index of every nuclide grid (binary64 or binary32 bit
 // patterns): buckets (bits - bits(E_0)) >> shift, about 8 grid points per
 // bucket, idx[b] = number of grid points whose bucket is below b.
@@ -666,9 +668,10 @@ int build_index(gbmc_ctx* c, int32_t n_nuc, const int64_t* grid_off, const doubl
     for (int32_t i = 0; i < n_nuc; ++i) {
         int64_t off = grid_off[i], n = grid_off[i + 1] - off;
         uint64_t base = bits(off), range = bits(off + n - 1) - base;
-        // about 1-2 points a bucket: binary64 bisects within the bucket's
-        // range (about one step), binary32 reads it as one bucket window
-        int32_t per = 2;
+        // binary64: about one point a bucket (the bisection within the
+        // bucket's range then takes at most about one step, none for an
+        // empty bucket); binary32: about 1-2, read as one bucket window
+        int32_t per = precision == GBMC_FP64 ? kIndexPer64 : 2;
         int32_t cap = 1 << 20;
         int32_t nb = 16;
         while ((int64_t)nb * per < n && nb < cap) nb <<= 1;
