@@ -38,6 +38,12 @@ FP64_SLOTS_PER_MICRO_NO_SA = 4   # without Sigma_a (formed only for the absorpti
 BRACKET_BYTES = {0: 32, 1: 16}    # E_j, E_j+1, s_j, s_j+1
 LOOKUP_IO_BYTES = 28              # per macro lookup: E 8, material 4, sigma_t and sigma_a 16
 ITER_KERNELS = 8                  # plan, source, 2 sort, 2 lookup (thread/warp mode), ray trace, collision
+# DRAM bytes (read + write) of all lookup launches of one profiled batch, from
+# one ncu capture of these exact workloads
+# (profiles/lookup_traffic_lattice17_batched64.md), keyed by (config, table
+# precision, 32-byte window loads); divided by this run's lookup launches.
+# Other runs report null.
+LOOKUP_TRAFFIC_BATCH_BYTES = {(2, 0, 0): 2.2271e9, (3, 1, 0): 23.329e9, (4, 1, 1): 31.647e9}
 
 WORKLOADS = {
     1: "infinite medium, 4 nuclides x 2000 log-spaced points, 1e5 particles/batch",
@@ -730,8 +736,14 @@ def main():
     lk_ms, lk_n = kt["lookup"]
     lk_bytes = pst["micro_lookups"] * BRACKET_BYTES[args.precision] + pst["lookups"] * LOOKUP_IO_BYTES
     lk_gbs = lk_bytes / (lk_ms * 1e-3) / 1e9
+    stock = (args.particles == 0 and args.max_in_flight == 0 and args.blocks_per_sm == 0
+             and args.sort == 1 and args.streams == 1)
+    tb = LOOKUP_TRAFFIC_BATCH_BYTES.get((args.config, args.precision,
+                                         int(ctx.options.wide_windows))) if stock else None
     roof = {"kernel": "lookup", "bound": "hbm", "achieved": lk_gbs, "peak": hbm, "unit": "GB/s",
-            "frac": lk_gbs / hbm, "traffic": None, "peak_source": peak_src,
+            "frac": lk_gbs / hbm, "traffic": tb / max(lk_n, 1) if tb else None,
+            "traffic_source": "profiles/lookup_traffic_lattice17_batched64.md" if tb else None,
+            "peak_source": peak_src,
             "launches": lk_n, "avg_launch_ms": lk_ms / max(lk_n, 1),
             "algorithmic_bytes_per_launch": lk_bytes / max(lk_n, 1)}
     if args.precision == 0:
