@@ -56,8 +56,7 @@ struct gbmc_ctx {
     double *d_e64 = nullptr, *d_fabs = nullptr, *d_awr = nullptr;
     float2* d_es32 = nullptr;       // binary32 (E, sigma_t) pairs, 8 pairs of padding
     float* d_fabs32 = nullptr;
-    NucIndex* d_nx32 = nullptr;       // coarse search descriptors (binary32 index build)
-    uint32_t *d_idx64 = nullptr, *d_idx32 = nullptr;
+    uint32_t* d_idx64 = nullptr;      // binary64 coarse index
     uint64_t table_hash = 0;   // identifies the tables both copies were built from
 
     // materials
@@ -270,7 +269,7 @@ void free_bank(gbmc_ctx* c) {
     dfree(c->B.p);
     Queues& Q = c->Q;
     dfree(Q.lq[0]); dfree(Q.lq[1]); dfree(Q.aq[0]); dfree(Q.aq[1]);
-    dfree(Q.sq); dfree(Q.cq); dfree(Q.fq); dfree(Q.lqs); dfree(Q.keys[0]); dfree(Q.keys[1]);
+    dfree(Q.cq); dfree(Q.fq); dfree(Q.lqs); dfree(Q.keys[0]); dfree(Q.keys[1]);
     dfree(Q.rank[0]); dfree(Q.rank[1]);
     dfree(Q.hist[0]); dfree(Q.hist[1]); dfree(Q.cursor); dfree(Q.btot);
     c->capacity = 0;
@@ -285,7 +284,7 @@ int ensure_bank(gbmc_ctx* c, int32_t M) {
     Queues& Q = c->Q;
     rc |= dalloc(c, &Q.lq[0], n); rc |= dalloc(c, &Q.lq[1], n);
     rc |= dalloc(c, &Q.aq[0], n); rc |= dalloc(c, &Q.aq[1], n);
-    rc |= dalloc(c, &Q.sq, n); rc |= dalloc(c, &Q.cq, n); rc |= dalloc(c, &Q.fq, n);
+    rc |= dalloc(c, &Q.cq, n); rc |= dalloc(c, &Q.fq, n);
     rc |= dalloc(c, &Q.lqs, n); rc |= dalloc(c, &Q.keys[0], n); rc |= dalloc(c, &Q.keys[1], n);
     rc |= dalloc(c, &Q.rank[0], n); rc |= dalloc(c, &Q.rank[1], n);
     rc |= dalloc(c, &Q.hist[0], kSortBuckets); rc |= dalloc(c, &Q.hist[1], kSortBuckets);
@@ -829,7 +828,7 @@ int gbmc_destroy(gbmc_ctx* c) {
     dfree(c->d_bank_out); dfree(c->d_bank_size); dfree(c->d_bank_src);
     dfree(c->d_grid_off); dfree(c->d_e64); dfree(c->d_iv64); dfree(c->d_es32);
     dfree(c->d_fabs); dfree(c->d_fabs32); dfree(c->d_awr);
-    dfree(c->d_nx32); dfree(c->d_idx64); dfree(c->d_idx32); dfree(c->d_bw32); dfree(c->d_desc64);
+    dfree(c->d_idx64); dfree(c->d_bw32); dfree(c->d_desc64);
     dfree(c->d_mat_off); dfree(c->d_nuc_id); dfree(c->d_density); dfree(c->d_density32);
     dfree(c->d_desc32);
     dfree(c->d_edges); dfree(c->d_probs); dfree(c->d_planes); dfree(c->d_ctl);
@@ -911,7 +910,7 @@ int gbmc_load_xs_tables(gbmc_ctx* c, int32_t n_nuc, const int64_t* grid_off, con
     if (!same) {
         // new tables: drop the copy of the other precision
         dfree(c->d_e64); dfree(c->d_iv64); dfree(c->d_es32);
-        dfree(c->d_nx32); dfree(c->d_idx64); dfree(c->d_idx32); dfree(c->d_bw32);
+        dfree(c->d_idx64); dfree(c->d_bw32);
         c->has64 = c->has32 = false;
         // materials refer to nuclide ids of the old tables
         if (c->n_mat) {

@@ -20,7 +20,8 @@ namespace gbmc {
 
 // ---------------------------------------------------------------- layouts
 
-// Per-nuclide search descriptor (48 bytes, three 16-byte loads).
+// Per-nuclide search descriptor, built on the host; the kernels read its
+// fields through the per-material-entry records Desc64 and Desc32.
 struct NucIndex {
     int64_t off;        // first grid point of the nuclide in the pooled grid
     int64_t idx_off;    // first entry of its coarse index
@@ -28,9 +29,7 @@ struct NucIndex {
     int32_t n;          // grid points
     int32_t shift;      // bucket of E = (bits(E) - base) >> shift
     int32_t nb;         // buckets; index entries idx[idx_off .. idx_off + nb]
-    int32_t pad[3];
 };
-static_assert(sizeof(NucIndex) == 48, "NucIndex is read as three int4");
 
 // Per material entry q, binary32 tables: what the lookup reads for nuclide
 // nuc_id[q] in one 32-byte record (two 16-byte loads).
@@ -142,7 +141,6 @@ struct Bank {
 struct Queues {
     int32_t* lq[2];     // lookup queue (double buffered)
     int32_t* aq[2];     // advance queue (double buffered)
-    int32_t* sq;        // surface queue
     int32_t* cq;        // collision queue
     int32_t* fq;        // free slots
     int32_t* lqs;       // lookup queue in (material, energy) order
@@ -170,7 +168,7 @@ struct Tallies {
 
 // Device-resident event-loop state.
 struct Ctl {
-    int32_t n_lq[2], n_aq[2], n_sq, n_cq, n_free;
+    int32_t n_lq[2], n_aq[2], n_cq, n_free;
     int32_t cur;                 // queues[cur] are consumed this iteration
     int32_t lookup_n, aq_base;   // lookups of this iteration, where they append in aq[cur]
     int32_t n_birth, free_base, lq_base, sorted;

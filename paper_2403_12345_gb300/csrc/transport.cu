@@ -194,7 +194,6 @@ __global__ void k_plan(Params P) {
     c->cur = cur;
     c->n_lq[1 - cur] = 0;
     c->n_aq[1 - cur] = 0;
-    c->n_sq = 0;
     c->n_cq = 0;
     // refill free slots: split copies first, then the batch's unborn
     // particles (with weight windows the source leaves birth_reserve slots
