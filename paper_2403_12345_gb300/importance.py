@@ -15,8 +15,9 @@ Orchestration only; every step runs in libgbmc's kernels:
    (gbmc_weight_windows_from_net): lower bound = C / importance, the source
    cell holding survival weight 1.
 
-The analog method stays the fallback and the judge: figure of merit
-FOM = 1 / (R^2 T) of the far-face leakage against the analog run.
+The analog method stays the fallback and the reference the windows are
+measured against: figure of merit FOM = 1 / (R^2 T) of the far-face leakage,
+compared with the analog run's.
 """
 from __future__ import annotations
 
