@@ -176,6 +176,7 @@ struct Ctl {
     int32_t adv_n;               // particles the ray-trace kernel takes this iteration
     int32_t tail;                // the loop stopped early: the tail kernel finishes
     int32_t adv_cursor;          // next ray-trace queue entry to hand out
+    int32_t lookup_cursor;       // next lookup queue chunk to hand out (thread mode)
     int32_t n_child;             // split copies waiting to be born
     int32_t n_birth_child;       // copies born this iteration (the first births)
     int32_t child_base;          // first of them in the copy buffer

@@ -241,6 +241,7 @@ __global__ void k_plan(Params P) {
         c->n_aq[cur] = c->adv_n;
     }
     c->adv_cursor = 0;
+    c->lookup_cursor = 0;
     c->sorted = (P.sort && c->lookup_n >= P.sort_min) ? 1 : 0;
     c->warp_lookup = c->lookup_n < P.warp_lookup_max ? 1 : 0;
     c->st_lookups += (unsigned long long)c->lookup_n;
@@ -489,8 +490,17 @@ __global__ void __launch_bounds__(256, PREC == GBMC_FP64 ? 4 : 3) k_lookup(Param
     const int32_t* q = c->sorted ? P.Q.lqs : P.Q.lq[cur];
     int32_t* aq = P.Q.aq[cur] + c->aq_base;
     unsigned long long micro = 0;
-    GBMC_WARP_LOOP(idx, valid, n) {
-        if (valid) {
+    // warps take 32-entry chunks from a cursor: a material's lookups cost in
+    // proportion to its nuclides, so a static stride leaves late blocks with
+    // the long ones
+    int lane = threadIdx.x & 31;
+    for (;;) {
+        int64_t b0 = 0;
+        if (lane == 0) b0 = atomicAdd(&P.ctl->lookup_cursor, 32);
+        b0 = __shfl_sync(kFull, b0, 0);
+        if (b0 >= n) break;
+        int64_t idx = b0 + lane;
+        if (idx < n) {
             int32_t slot = q[idx];
             double E = P.B.p[slot].E;
             int32_t m = P.B.p[slot].mat;
