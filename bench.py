@@ -43,7 +43,7 @@ ITER_KERNELS = 8                  # plan, source, 2 sort, 2 lookup (thread/warp 
 # (profiles/lookup_traffic_lattice17_batched64.md), keyed by (config, table
 # precision, 32-byte window loads); divided by this run's lookup launches.
 # Other runs report null.
-LOOKUP_TRAFFIC_BATCH_BYTES = {}
+LOOKUP_TRAFFIC_BATCH_BYTES = {(2, 0, 0): 2.4267e9, (3, 1, 0): 23.487e9, (4, 1, 0): 30.631e9}
 
 WORKLOADS = {
     1: "infinite medium, 4 nuclides x 2000 log-spaced points, 1e5 particles/batch",
