@@ -75,6 +75,12 @@ def lib():
         L.or_search.restype = C.c_int64
         L.or_micro.argtypes = [_P(_Problem), C.c_int32, C.c_double]
         L.or_micro.restype = C.c_double
+        L.or_search_f32.argtypes = [_P(C.c_float), C.c_int64, C.c_double]
+        L.or_search_f32.restype = C.c_int64
+        L.or_micro_f32.argtypes = [_P(C.c_float), _P(C.c_float), C.c_int64, C.c_double]
+        L.or_micro_f32.restype = C.c_float
+        L.or_pick_nuclide.argtypes = [_P(_Problem), C.c_int32, C.c_double, C.c_double]
+        L.or_pick_nuclide.restype = C.c_int32
         L.or_macro.argtypes = [_P(_Problem), C.c_int32, _P(C.c_double), C.c_int64,
                                _P(C.c_double), _P(C.c_double)]
         L.or_macro.restype = C.c_int
@@ -117,6 +123,32 @@ def log(x: float) -> float:
 def search(g, E: float) -> int:
     g = np.ascontiguousarray(g, dtype=np.float64)
     return int(lib().or_search(_ptr(g, C.c_double), len(g), float(E)))
+
+
+def search_f32(g, E: float) -> int:
+    """Bracket of E on a binary32 grid g (compared exactly, in binary64)."""
+    g = np.ascontiguousarray(g, dtype=np.float32)
+    return int(lib().or_search_f32(_ptr(g, C.c_float), len(g), float(E)))
+
+
+def micro_f32(g, s, E: float) -> float:
+    """Binary32 lin-lin micro cross section of one nuclide's binary32 grid g
+    and values s at E."""
+    g = np.ascontiguousarray(g, dtype=np.float32)
+    s = np.ascontiguousarray(s, dtype=np.float32)
+    if len(g) != len(s):
+        raise ValueError("grid and values differ in length")
+    return float(np.float32(lib().or_micro_f32(_ptr(g, C.c_float), _ptr(s, C.c_float), len(g),
+                                               float(E))))
+
+
+def pick_nuclide(prob, mat: int, E: float, target: float, precision=None) -> int:
+    """Collision nuclide of material mat at E for target = xi Sigma_t."""
+    b = _Bound(prob, precision=precision)
+    i = lib().or_pick_nuclide(C.byref(b.p), int(mat), float(E), float(target))
+    if i < 0:
+        raise MemoryError("oracle tables could not be built")
+    return int(i)
 
 
 def dist_cylinder(dx, dy, u, v, r, inside) -> float:

@@ -164,8 +164,10 @@ int64_t or_search(const double *g, int64_t n, double E)
     return lo;
 }
 
-/* float grid compared in binary64: (double)g[j] <= E */
-static int64_t or_search_f32(const float *g, int64_t n, double E)
+/* Binary32 tables: the same bracket, the largest j in [0, n-2] with
+ * (double)g[j] <= E.  Widening a binary32 value to binary64 is exact, so the
+ * comparison is exact: E itself is never rounded for the search. */
+int64_t or_search_f32(const float *g, int64_t n, double E)
 {
     int64_t lo = 0, hi = n - 1;
     while (hi - lo > 1) {
@@ -195,17 +197,55 @@ double or_micro(const or_problem *P, int32_t nuc, double E)
     return s[j] + f * (s[j + 1] - s[j]);
 }
 
+/* Binary32 micro cross section on one nuclide's binary32 grid g and values
+ * s (n points): the bracket of E as above, then the lin-lin interpolation
+ * with every operation in binary32 on E rounded to nearest binary32. */
+float or_micro_f32(const float *g, const float *s, int64_t n, double E)
+{
+    int64_t j = or_search_f32(g, n, E);
+    float Ef = (float)E;
+    float f = (Ef - g[j]) / (g[j + 1] - g[j]);
+    return s[j] + f * (s[j + 1] - s[j]);
+}
+
 static float micro_f32(const tables_t *T, int32_t nuc, double E)
 {
     const or_problem *P = T->P;
     int64_t lo = P->grid_off[nuc];
     int64_t n = P->grid_off[nuc + 1] - lo;
-    const float *g = T->ef + lo;
-    const float *s = T->sf + lo;
-    int64_t j = or_search_f32(g, n, E);
-    float Ef = (float)E;
-    float f = (Ef - g[j]) / (g[j + 1] - g[j]);
-    return s[j] + f * (s[j + 1] - s[j]);
+    return or_micro_f32(T->ef + lo, T->sf + lo, n, E);
+}
+
+/* The tables of problem P as the lookup reads them: binary32 copies (each
+ * grid energy and cross section rounded to nearest) in precision 1. */
+static int tables_init(tables_t *T, const or_problem *P)
+{
+    T->P = P;
+    T->ef = NULL;
+    T->sf = NULL;
+    if (P->precision == 1) {
+        int64_t tot = P->grid_off[P->n_nuc];
+        T->ef = (float *)malloc(sizeof(float) * (size_t)(tot > 0 ? tot : 1));
+        T->sf = (float *)malloc(sizeof(float) * (size_t)(tot > 0 ? tot : 1));
+        if (!T->ef || !T->sf) {
+            free(T->ef);
+            free(T->sf);
+            return -1;
+        }
+        for (int64_t k = 0; k < tot; ++k) {
+            T->ef[k] = (float)P->energy[k];
+            T->sf[k] = (float)P->sigma_t[k];
+        }
+    }
+    return 0;
+}
+
+static void tables_free(tables_t *T)
+{
+    free(T->ef);
+    free(T->sf);
+    T->ef = NULL;
+    T->sf = NULL;
 }
 
 /* Macroscopic sigma_t and sigma_a of material m at energy E. */
@@ -239,20 +279,10 @@ static void macro_xs(const tables_t *T, int32_t m, double E, double *st, double 
 int or_macro(const or_problem *P, int32_t m, const double *E, int64_t n,
              double *st, double *sa)
 {
-    tables_t T = {P, NULL, NULL};
-    if (P->precision == 1) {
-        int64_t tot = P->grid_off[P->n_nuc];
-        T.ef = (float *)malloc(sizeof(float) * (size_t)tot);
-        T.sf = (float *)malloc(sizeof(float) * (size_t)tot);
-        if (!T.ef || !T.sf) return -1;
-        for (int64_t k = 0; k < tot; ++k) {
-            T.ef[k] = (float)P->energy[k];
-            T.sf[k] = (float)P->sigma_t[k];
-        }
-    }
+    tables_t T;
+    if (tables_init(&T, P)) return -1;
     for (int64_t k = 0; k < n; ++k) macro_xs(&T, m, E[k], &st[k], &sa[k]);
-    free(T.ef);
-    free(T.sf);
+    tables_free(&T);
     return 0;
 }
 
@@ -284,6 +314,18 @@ static int32_t pick_nuclide(const tables_t *T, int32_t m, double E, double targe
         }
     }
     return last >= 0 ? last : P->nuc_id[P->mat_off[m]];
+}
+
+/* exported for tests: the collision nuclide of material m at energy E for
+ * target = xi Sigma_t, in the problem's precision; -1 if the tables cannot
+ * be built */
+int32_t or_pick_nuclide(const or_problem *P, int32_t m, double E, double target)
+{
+    tables_t T;
+    if (tables_init(&T, P)) return -1;
+    int32_t i = pick_nuclide(&T, m, E, target);
+    tables_free(&T);
+    return i;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -807,17 +849,8 @@ void or_birth_state(const or_problem *P, uint64_t seed, uint64_t key_hi, int64_t
 int or_run(const or_problem *P, uint64_t seed, uint64_t key_hi, int64_t first_id, int64_t n,
            int n_threads, or_result *R)
 {
-    tables_t T = {P, NULL, NULL};
-    if (P->precision == 1) {
-        int64_t tot = P->grid_off[P->n_nuc];
-        T.ef = (float *)malloc(sizeof(float) * (size_t)tot);
-        T.sf = (float *)malloc(sizeof(float) * (size_t)tot);
-        if (!T.ef || !T.sf) return -1;
-        for (int64_t k = 0; k < tot; ++k) {
-            T.ef[k] = (float)P->energy[k];
-            T.sf[k] = (float)P->sigma_t[k];
-        }
-    }
+    tables_t T;
+    if (tables_init(&T, P)) return -1;
     const int64_t nf = (int64_t)n_cells(P) * P->n_bins;
     if (n_threads <= 0) n_threads = 1;
     acc_t *acc = (acc_t *)calloc((size_t)n_threads, sizeof(acc_t));
@@ -899,8 +932,7 @@ int or_run(const or_problem *P, uint64_t seed, uint64_t key_hi, int64_t first_id
         free(acc[t].ac);
     }
     free(acc);
-    free(T.ef);
-    free(T.sf);
+    tables_free(&T);
     return overflow == 3 ? -3 : (overflow ? -2 : 0);
 }
 
