@@ -5,9 +5,10 @@ nuclear data that is not available):
 
 * energy grid of a nuclide: endpoints 1e-5 eV and 2e7 eV; either log-spaced
   (the infinite-medium configuration) or n-2 sorted log-uniform interior
-  points.  Every grid point is rounded to the nearest binary32 value and
-  duplicates are dropped, so the binary64 and binary32 tables share one
-  strictly increasing grid;
+  points, kept as binary64 values.  An interior point whose nearest binary32
+  value equals the previous point's is dropped (and one equal to the last
+  point's), so the binary32 copy of the tables (each value rounded to
+  nearest) is strictly increasing too;
 * sigma_t(E) = a / sqrt(E) + sum_k h_k (G_k/2)^2 / ((E - E_k)^2 + (G_k/2)^2)
   with a log-uniform in [1, 1e3] b eV^1/2, E_k log-uniform in [1, 1e5] eV,
   h_k log-uniform in [10, 1e4] b, G_k = E_k g_k with g_k log-uniform in
@@ -122,9 +123,17 @@ def _loguniform(rng, lo, hi, size=None):
     return np.exp(rng.uniform(np.log(lo), np.log(hi), size))
 
 
-def _f32_grid(e: np.ndarray) -> np.ndarray:
-    g = np.unique(e.astype(np.float32))
-    return g.astype(np.float64)
+def _grid(e: np.ndarray) -> np.ndarray:
+    """Strictly increasing binary64 grid from the drawn points e (first and
+    last kept): an interior point is dropped when its binary32 rounding
+    equals that of the point before it or that of the last point."""
+    e = np.unique(np.asarray(e, dtype=np.float64))
+    f = e.astype(np.float32)
+    keep = np.ones(len(e), dtype=bool)
+    keep[1:] = f[1:] != f[:-1]
+    keep[1:-1] &= f[1:-1] != f[-1]
+    keep[-1] = True
+    return e[keep]
 
 
 def _nuclide(rng, n_points: int, n_res: int, log_spaced: bool,
@@ -134,7 +143,7 @@ def _nuclide(rng, n_points: int, n_res: int, log_spaced: bool,
     else:
         inner = np.sort(_loguniform(rng, E_MIN, E_MAX, n_points - 2))
         e = np.concatenate([[E_MIN], inner, [E_MAX]])
-    e = _f32_grid(e)
+    e = _grid(e)
     a = _loguniform(rng, 1.0, 1e3)
     ek = _loguniform(rng, 1.0, 1e5, n_res)
     hk = _loguniform(rng, 10.0, 1e4, n_res)
@@ -325,7 +334,7 @@ def make_tiny_problem(seed: int = 7, n_nuc: int = 3, n_points=(2, 9),
     for i in range(n_nuc):
         ng = int(rng.integers(n_points[0], n_points[1] + 1))
         if flat:
-            e = _f32_grid(np.geomspace(E_MIN, E_MAX, ng))
+            e = _grid(np.geomspace(E_MIN, E_MAX, ng))
             sig = np.full_like(e, float(rng.uniform(1.0, 10.0)))
             f = float(rng.uniform(0.05, 0.5))
             a = float(rng.uniform(1.0, 240.0))
