@@ -27,23 +27,17 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 HBM_FALLBACK_GBS = 6800.0
-FP64_NOMINAL_TFLOPS = 1.25       # GB300 dense FP64 (recipe table)
-# FP64-pipe work of one micro lookup in DFMA issue slots.  Of the
-# interpolation's binary64 steps, E_k+1 - E_k and s_k+1 - s_k come from the
-# interval records, E - E_k and the division run on the integer units
-# (correctly rounded), so f (s_k+1 - s_k), s_k + ..., N sigma and the running
-# sum remain, plus two for Sigma_a (the transport's lookups skip those)
-FP64_SLOTS_PER_MICRO = 6
-FP64_SLOTS_PER_MICRO_NO_SA = 4   # without Sigma_a (formed only for the absorption-rate tally)
 BRACKET_BYTES = {0: 32, 1: 16}    # E_j, E_j+1, s_j, s_j+1
 LOOKUP_IO_BYTES = 28              # per macro lookup: E 8, material 4, sigma_t and sigma_a 16
 ITER_KERNELS = 8                  # plan, source, 2 sort, 2 lookup (thread/warp mode), ray trace, collision
-# DRAM bytes (read + write) of all lookup launches of one profiled batch, from
-# one ncu capture of these exact workloads
-# (profiles/lookup_traffic_lattice17_batched64.md), keyed by (config, table
-# precision, 32-byte window loads); divided by this run's lookup launches.
-# Other runs report null.
-LOOKUP_TRAFFIC_BATCH_BYTES = {(2, 0, 0): 2.4267e9, (3, 1, 0): 23.487e9, (4, 1, 0): 30.631e9}
+# DRAM (and L2) bytes of every lookup launch of one eager profiled batch, from
+# ncu counters, written by `bench.py --record-traffic` and keyed by workload,
+# table precision and window-load width; each entry carries a hash of the
+# kernel sources it was measured on and is ignored once they change
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "lookup_traffic.json")
+KERNEL_SOURCES = ("paper_2403_12345_gb300/csrc/device.cuh",
+                  "paper_2403_12345_gb300/csrc/transport.cu")
+FP32_TALLY_L2_GATE = 1e-4         # binary32 tables against binary64, whole-batch flux
 
 WORKLOADS = {
     1: "infinite medium, 4 nuclides x 2000 log-spaced points, 1e5 particles/batch",
@@ -128,18 +122,224 @@ def _eigen_of(prob):
     return dict(nu=prob.nu, f_fis=prob.f_fis, k_norm=1.0, max_sites=255)
 
 
-def oracle_rate(prob, budget_s, threads, batch=0, cap=None):
-    """Particles/s of the CPU oracle on a bounded sample (first ids of a batch)."""
+def oracle_rate(prob, budget_s, threads, batch=0, cap=None, geom_index=0):
+    """Particles/s of the CPU oracle on a bounded sample (the first ids of a
+    batch of problem `geom_index`); also returns the sample's result."""
     import oracle
     n = 2000
+    kw = dict(seed=prob.seed, batch=batch, threads=threads, eigen=_eigen_of(prob),
+              geom_index=geom_index, problem_index=geom_index)
     t = time.perf_counter()
-    oracle.run(prob, seed=prob.seed, batch=batch, n=n, threads=threads, eigen=_eigen_of(prob))
+    oracle.run(prob, n=n, **kw)
     dt = time.perf_counter() - t
-    n = int(max(2000, min(budget_s / max(dt, 1e-6) * n, cap or prob.n_particles[0])))
+    n = int(max(2000, min(budget_s / max(dt, 1e-6) * n, cap or prob.n_particles[geom_index])))
     t = time.perf_counter()
-    oracle.run(prob, seed=prob.seed, batch=batch, n=n, threads=threads, eigen=_eigen_of(prob))
+    res = oracle.run(prob, n=n, **kw)
     dt = time.perf_counter() - t
-    return n / dt, n, dt
+    return n / dt, n, dt, res
+
+
+def kernel_source_sha():
+    import hashlib
+    h = hashlib.sha1()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_key(config, precision, wide):
+    return f"config{config}-{'fp32' if precision == 1 else 'fp64'}-w{int(wide)}"
+
+
+def recorded_traffic(config, precision, wide):
+    """The recorded lookup traffic of this workload, or None (no record, or
+    one taken on other kernel sources)."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f).get(traffic_key(config, precision, wide))
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("kernel_sha") != kernel_source_sha():
+        return None
+    return rec
+
+
+def record_traffic(csv_path, config, precision, wide, command):
+    """Sums the DRAM and L2 bytes of every lookup launch in an ncu CSV log
+    (metrics dram__bytes_read.sum, dram__bytes_write.sum, lts__t_bytes.sum)
+    into TRAFFIC_FILE under this workload's key."""
+    import csv
+    rows = []
+    with open(csv_path) as f:
+        lines = [ln for ln in f if ln.startswith('"')]
+    for r in csv.DictReader(lines):
+        if "k_lookup" not in r.get("Kernel Name", ""):
+            continue
+        rows.append(r)
+    if not rows:
+        raise SystemExit(f"no lookup launches in {csv_path}")
+    unit = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1024, "MB": 1 << 20,
+            "GB": 1 << 30}
+    tot = {}
+    launches = set()
+    for r in rows:
+        launches.add(r["ID"])
+        v = float(r["Metric Value"].replace(",", "")) * unit.get(r.get("Metric Unit", "byte"), 1)
+        tot[r["Metric Name"]] = tot.get(r["Metric Name"], 0.0) + v
+    dram = tot.get("dram__bytes_read.sum", 0.0) + tot.get("dram__bytes_write.sum", 0.0)
+    data = {}
+    if os.path.exists(TRAFFIC_FILE):
+        with open(TRAFFIC_FILE) as f:
+            data = json.load(f)
+    data[traffic_key(config, precision, wide)] = {
+        "dram_bytes_per_batch": dram, "l2_bytes_per_batch": tot.get("lts__t_bytes.sum"),
+        "launches": len(launches), "kernel_sha": kernel_source_sha(), "command": command}
+    with open(TRAFFIC_FILE, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+        f.write("\n")
+    print(json.dumps(data[traffic_key(config, precision, wide)]))
+
+
+def compare_outcomes(gpu, ref):
+    """Counts of identical per-particle outcomes (floats as bit patterns)."""
+    n = len(ref["n_coll"])
+    same = np.ones(n, dtype=bool)
+    fields = {}
+    for k in ("n_coll", "status", "n_flights", "n_draws", "E", "x", "y", "z"):
+        a, b = np.asarray(gpu[k])[:n], np.asarray(ref[k])
+        eq = a.view(np.int64) == b.view(np.int64) if a.dtype == np.float64 else a == b
+        fields[k] = int(eq.sum())
+        same &= eq
+    return int(same.sum()), fields
+
+
+def tally_error(gpu_flux, ref_flux):
+    nz = ref_flux > 0
+    rel = np.abs(gpu_flux[nz] - ref_flux[nz]) / ref_flux[nz]
+    return {"max_rel": float(rel.max()) if rel.size else 0.0,
+            "scored_where_oracle_zero": int(np.count_nonzero(gpu_flux[~nz])),
+            "bins_compared": int(nz.sum())}
+
+
+def parity_record(ctx, geom, prob, n, ref, precision, stream):
+    """The GPU on the oracle sample's histories (batch 0, problem 0, ids
+    [0, n)) against the oracle's result for them."""
+    from paper_2403_12345_gb300 import gbmc
+    ctx.reset_tallies(stream)
+    ctx.run_problems([gbmc.problem(geom, prob.seed, n, batch=0, problem_index=0)], stream)
+    flux, counts, _ = ctx.read_tallies(0)
+    out = ctx.read_outcomes(0, 0, n)
+    same, fields = compare_outcomes(out, ref)
+    te = tally_error(flux, ref["flux"])
+    return {"against": "oracle (history-based CPU definition), same histories",
+            "precision": "fp32" if precision == 1 else "fp64", "batch": 0, "problem": 0,
+            "ids": n, "outcomes_identical": same, "identical_per_field": fields,
+            "flux_per_bin": te, "scalar_counts_equal": bool(np.array_equal(counts, ref["counts"])),
+            "gate": "every outcome bit for bit; flux per bin within 1e-12 relative",
+            "pass": bool(same == n and te["max_rel"] <= 1e-12
+                         and te["scored_where_oracle_zero"] == 0
+                         and np.array_equal(counts, ref["counts"]))}
+
+
+def fp32_vs_fp64_record(stream, local, steps=3):
+    """The 17x17 lattice at 1e7 particles per batch with binary32 tables
+    against binary64 tables: throughput of each (autotuned, CUDA events, L2
+    flushed between batches), and the binary32 tally error on the same
+    histories against the binary64 path (whose outcomes are the oracle's bit
+    for bit and tallies its to 1e-12: the parity record)."""
+    import torch
+    from paper_2403_12345_gb300 import gbmc
+    prob = synth.make_config(3)
+    n = prob.n_particles[0]
+    geom = gbmc.geometry_from(prob.geom)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    res = {}
+    with gbmc.Context(local) as ctx:
+        ctx.load(prob, (gbmc.FP64, gbmc.FP32))
+        for prec in (gbmc.FP64, gbmc.FP32):
+            ctx.set_options(precision=prec)
+            ctx.autotune([gbmc.problem(geom, prob.seed, n, batch=40_000)], fraction=0.1,
+                         stream=stream)
+            ctx.run_batch(gbmc.problem(geom, prob.seed, n, batch=10_000), stream)
+            ms, clocks = _timed(lambda k: ctx.run_batch(gbmc.problem(geom, prob.seed, n,
+                                                                     batch=1 + k), stream),
+                                steps, flush, stream, local)
+            ctx.reset_tallies(stream)
+            ctx.run_batch(gbmc.problem(geom, prob.seed, n, batch=0), stream)
+            flux, _, _ = ctx.read_tallies(0)
+            o = ctx.read_outcomes(0, 0, n)
+            res[prec] = dict(rate=n * steps / (sum(ms) * 1e-3), flux=flux,
+                             n_coll=o["n_coll"].copy(), status=o["status"].copy(), clocks=clocks)
+    f32, f64 = res[gbmc.FP32]["flux"], res[gbmc.FP64]["flux"]
+    nz = f64 > 0
+    per_bin = np.abs(f32[nz] - f64[nz]) / f64[nz]
+    l2 = float(np.linalg.norm(f32 - f64) / np.linalg.norm(f64))
+    div = float(np.mean((res[gbmc.FP32]["n_coll"] != res[gbmc.FP64]["n_coll"]) |
+                        (res[gbmc.FP32]["status"] != res[gbmc.FP64]["status"])))
+    r32, r64 = res[gbmc.FP32]["rate"], res[gbmc.FP64]["rate"]
+    return {"workload": "17x17 lattice, 1e7 particles per batch, same histories in both",
+            "fp64_particles_per_s": r64, "fp32_particles_per_s": r32, "ratio": r32 / r64,
+            "tally": "flux [289 cells x 200 bins], batch 0",
+            "l2_rel_err": l2, "per_bin_rel_err_p50": float(np.median(per_bin)),
+            "per_bin_rel_err_p99": float(np.percentile(per_bin, 99)),
+            "diverged_walk_fraction": div, "gate_l2": FP32_TALLY_L2_GATE,
+            "pass": l2 <= FP32_TALLY_L2_GATE, "clocks_fp32": res[gbmc.FP32]["clocks"]}
+
+
+def stress_measure(prec, nq, steps, warmup, stream, local, seed_offset=0, e2e_steps=3,
+                   barrier=None):
+    """Lookup-only stress set: lookups/s through gbmc_lookup_macro (the
+    library's sort included), the lookup kernel alone on sorted queries
+    (roofline), and end to end from pinned host memory."""
+    import torch
+    from paper_2403_12345_gb300 import gbmc
+    prob, E, mat = synth.make_stress_lookup(n_queries=nq, seed_offset=seed_offset)
+    micro_per = int(prob.mat_off[1] - prob.mat_off[0])
+    ctx = gbmc.Context(local, precision=prec)
+    ctx.load(prob, (prec,))
+    dE = torch.from_numpy(E).cuda()
+    dm = torch.from_numpy(mat).cuda()
+    st = torch.empty_like(dE)
+    sa = torch.empty_like(dE)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(warmup):
+        ctx.lookup_macro(dE, dm, st, sa, precision=prec, sort=True, stream=stream)
+    if barrier:
+        barrier()
+    ms, clocks = _timed(lambda k: ctx.lookup_macro(dE, dm, st, sa, precision=prec, sort=True,
+                                                   stream=stream), steps, flush, stream, local)
+    # the lookup kernel alone: queries in sorted order, no library sort
+    order = np.argsort(E, kind="stable")
+    dEs = torch.from_numpy(E[order]).cuda()
+    for _ in range(2):
+        ctx.lookup_macro(dEs, dm, st, sa, precision=prec, sort=False, stream=stream)
+    kms, _ = _timed(lambda k: ctx.lookup_macro(dEs, dm, st, sa, precision=prec, sort=False,
+                                               stream=stream), steps, flush, stream, local)
+    lk_ms = statistics.median(kms)
+    alg = nq * (micro_per * BRACKET_BYTES[prec] + LOOKUP_IO_BYTES)
+    hbm, peak_src = peaks()
+    gbs = alg / (lk_ms * 1e-3) / 1e9
+    hE = torch.from_numpy(E).pin_memory()
+    hst = torch.empty(nq, dtype=torch.float64).pin_memory()
+    hsa = torch.empty(nq, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        dE.copy_(hE, non_blocking=True)
+        ctx.lookup_macro(dE, dm, st, sa, precision=prec, sort=True, stream=stream)
+        hst.copy_(st, non_blocking=True)
+        hsa.copy_(sa, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e = nq * e2e_steps / (time.perf_counter() - t0)
+    ctx.close()
+    return {"prob": prob, "E": E, "micro_per": micro_per, "ms": ms, "clocks": clocks,
+            "e2e": e2e,
+            "roofline": {"kernel": "lookup (sorted queries, no library sort)", "bound": "hbm",
+                         "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                         "traffic": None, "peak_source": peak_src, "launches": 1,
+                         "avg_launch_ms": lk_ms, "algorithmic_bytes_per_launch": alg,
+                         "table_bytes": int(prob.table_bytes(prec))}}
 
 
 def run_reference(args, prob, rank):
@@ -148,7 +348,7 @@ def run_reference(args, prob, rank):
     threads = len(os.sched_getaffinity(0))
     import oracle
     # size a step to ~budget seconds of oracle work
-    _, n, dt = oracle_rate(prob, args.ref_step_s, threads)
+    _, n, dt, _ = oracle_rate(prob, args.ref_step_s, threads)
     for w in range(args.warmup):
         oracle.run(prob, seed=prob.seed, batch=100 + w, n=min(n, 2000), threads=threads,
                    eigen=_eigen_of(prob))
@@ -258,46 +458,11 @@ def run_stress(args, rank, world, local):
     if world > 1:
         dist.init_process_group("nccl")
     stream = torch.cuda.current_stream()
-    ctx = gbmc.Context(local, precision=prec)
-    ctx.load(prob, (prec,))
-    dE = torch.from_numpy(E).cuda()
-    dm = torch.from_numpy(mat).cuda()
-    st = torch.empty_like(dE)
-    sa = torch.empty_like(dE)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    for _ in range(args.warmup):
-        ctx.lookup_macro(dE, dm, st, sa, precision=prec, sort=True, stream=stream)
-    if world > 1:
-        dist.barrier()
-    ms, clocks = _timed(lambda k: ctx.lookup_macro(dE, dm, st, sa, precision=prec, sort=True,
-                                                   stream=stream),
-                        args.steps, flush, stream, local)
-    tot_ms = _max_over_ranks(sum(ms), world)
+    m = stress_measure(prec, nq, args.steps, args.warmup, stream, local, seed_offset=rank,
+                       e2e_steps=args.e2e_steps,
+                       barrier=(lambda: dist.barrier()) if world > 1 else None)
+    tot_ms = _max_over_ranks(sum(m["ms"]), world)
     value = nq * args.steps * world / (tot_ms * 1e-3)
-    # the lookup kernel alone: queries in sorted order, no library sort
-    order = np.argsort(E, kind="stable")
-    dEs = torch.from_numpy(E[order]).cuda()
-    for _ in range(2):
-        ctx.lookup_macro(dEs, dm, st, sa, precision=prec, sort=False, stream=stream)
-    kms, _ = _timed(lambda k: ctx.lookup_macro(dEs, dm, st, sa, precision=prec, sort=False,
-                                               stream=stream), args.steps, flush, stream, local)
-    lk_ms = statistics.median(kms)
-    alg = nq * (micro_per * bracket + LOOKUP_IO_BYTES)
-    hbm, peak_src = peaks()
-    gbs = alg / (lk_ms * 1e-3) / 1e9
-    # end to end: queries from pinned host memory, results back to the host
-    hE = torch.from_numpy(E).pin_memory()
-    hst = torch.empty(nq, dtype=torch.float64).pin_memory()
-    hsa = torch.empty(nq, dtype=torch.float64).pin_memory()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        dE.copy_(hE, non_blocking=True)
-        ctx.lookup_macro(dE, dm, st, sa, precision=prec, sort=True, stream=stream)
-        hst.copy_(st, non_blocking=True)
-        hsa.copy_(sa, non_blocking=True)
-        torch.cuda.synchronize()
-    e2e = nq * args.e2e_steps / (time.perf_counter() - t0)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
@@ -310,18 +475,6 @@ def run_stress(args, rank, world, local):
         dt = time.perf_counter() - t
         cpu = {"value": n / dt, "unit": "lookups/s", "cores": 1, "kind": "oracle",
                "sample": f"first {n} queries ({dt:.1f} s, one thread)"}
-    roof = {"kernel": "lookup (sorted queries, no library sort)", "bound": "hbm",
-            "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": None,
-            "peak_source": peak_src, "launches": 1, "avg_launch_ms": lk_ms,
-            "algorithmic_bytes_per_launch": alg}
-    if prec == 0:
-        slots = nq * micro_per * FP64_SLOTS_PER_MICRO / (lk_ms * 1e-3)
-        alu_peak = FP64_NOMINAL_TFLOPS * 1e12 / 2
-        if slots / alu_peak > roof["frac"]:
-            roof.update({"bound": "alu", "achieved": slots / 1e9, "peak": alu_peak / 1e9,
-                         "unit": "G FP64-slot/s", "frac": slots / alu_peak,
-                         "peak_source": "nominal 1.25 TFLOP/s FP64 = 625 G DFMA slots/s",
-                         "hbm_equiv_gbs": gbs})
     if rank == 0:
         print(json.dumps({
             "metric": "XS lookups/s", "value": value, "unit": "lookups/s", "n_gpus": world,
@@ -329,12 +482,11 @@ def run_stress(args, rank, world, local):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if prec == 1 else "f64", "data": "synthetic", "config": cfg,
             "micro_lookups_per_s": value * micro_per,
-            "e2e": {"value": e2e, "unit": "lookups/s", "h2d_bytes_per_step": nq * 8,
+            "e2e": {"value": m["e2e"], "unit": "lookups/s", "h2d_bytes_per_step": nq * 8,
                     "d2h_bytes_per_step": nq * 16},
-            "roofline": roof,
-            "cpu_baseline": cpu, "clocks": clocks,
+            "roofline": m["roofline"],
+            "cpu_baseline": cpu, "clocks": m["clocks"],
             "gpu_launches": 4 * args.steps}), flush=True)
-    ctx.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -538,7 +690,7 @@ def run_windows(args, prob, rank, world, local):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         threads = len(os.sched_getaffinity(0))
-        rate, n, dt = oracle_rate(prob, args.cpu_budget_s, threads)
+        rate, n, dt, _ = oracle_rate(prob, args.cpu_budget_s, threads)
         cpu = {"value": rate, "unit": "particles/s", "cores": threads, "kind": "oracle",
                "sample": f"first {n} analog histories of batch 0 ({dt:.1f} s)"}
     if rank == 0:
@@ -591,7 +743,26 @@ def main():
     ap.add_argument("--autotune", type=int, default=-1,
                     help="1: autotune launch settings before timing, 0: defaults "
                          "(default: autotune configs 2-4)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the sub-records of the default run (binary32 against binary64 "
+                         "at 1e7 particles, the lookup-only stress set)")
+    ap.add_argument("--profile-batch", action="store_true",
+                    help="set up, autotune and warm up as the timed run does, then run one "
+                         "eager profiled batch and exit (the command the lookup-traffic ncu "
+                         "capture wraps)")
+    ap.add_argument("--record-traffic", metavar="NCU_CSV",
+                    help="sum the lookup launches' DRAM/L2 bytes of an ncu CSV log of "
+                         "--profile-batch into the traffic file for this workload and exit")
+    ap.add_argument("--wide-windows", type=int, default=-1,
+                    help="with --record-traffic: the window-load width the capture ran with")
+    ap.add_argument("--ncu-command", default="",
+                    help="with --record-traffic: the capture command, kept with the record")
     args = ap.parse_args()
+    if args.record_traffic:
+        prec = args.precision if args.precision >= 0 else (0 if args.config in (1, 2) else 1)
+        record_traffic(args.record_traffic, args.config, prec, max(args.wide_windows, 0),
+                       args.ncu_command)
+        return
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -658,6 +829,12 @@ def main():
     for w in range(args.warmup):
         ctx.run_problems(problems(10_000 + w), stream)
     torch.cuda.synchronize()
+    if args.profile_batch:
+        kt = ctx.profile_problems(problems(30_000), stream)
+        print(json.dumps({"profiled_batch": {k: v[0] for k, v in kt.items()},
+                          "wide_windows": int(ctx.options.wide_windows)}), flush=True)
+        ctx.close()
+        return
     ctx.reset_tallies(stream)
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -738,29 +915,38 @@ def main():
     lk_gbs = lk_bytes / (lk_ms * 1e-3) / 1e9
     stock = (args.particles == 0 and args.max_in_flight == 0 and args.blocks_per_sm == 0
              and args.sort == 1 and args.streams == 1)
-    tb = LOOKUP_TRAFFIC_BATCH_BYTES.get((args.config, args.precision,
-                                         int(ctx.options.wide_windows))) if stock else None
+    tr = recorded_traffic(args.config, args.precision, ctx.options.wide_windows) if stock else None
+    l2_size = torch.cuda.get_device_properties(local).L2_cache_size
     roof = {"kernel": "lookup", "bound": "hbm", "achieved": lk_gbs, "peak": hbm, "unit": "GB/s",
-            "frac": lk_gbs / hbm, "traffic": tb / max(lk_n, 1) if tb else None,
-            "traffic_source": "profiles/lookup_traffic_lattice17_batched64.md" if tb else None,
-            "peak_source": peak_src,
+            "frac": lk_gbs / hbm, "peak_source": peak_src,
+            "traffic": tr["dram_bytes_per_batch"] / tr["launches"] if tr else None,
+            "l2_bytes": (tr["l2_bytes_per_batch"] / tr["launches"]
+                         if tr and tr.get("l2_bytes_per_batch") else None),
             "launches": lk_n, "avg_launch_ms": lk_ms / max(lk_n, 1),
-            "algorithmic_bytes_per_launch": lk_bytes / max(lk_n, 1)}
-    if args.precision == 0:
-        slots = pst["micro_lookups"] * FP64_SLOTS_PER_MICRO_NO_SA / (lk_ms * 1e-3)
-        alu_peak = FP64_NOMINAL_TFLOPS * 1e12 / 2
-        if slots / alu_peak > roof["frac"]:
-            roof.update({"bound": "alu", "achieved": slots / 1e9, "peak": alu_peak / 1e9,
-                         "unit": "G FP64-slot/s", "frac": slots / alu_peak,
-                         "peak_source": "nominal 1.25 TFLOP/s FP64 = 625 G DFMA slots/s",
-                         "hbm_equiv_gbs": lk_gbs})
+            "algorithmic_bytes_per_launch": lk_bytes / max(lk_n, 1),
+            "timing": "CUDA events around each lookup launch of one eager batch of this workload",
+            "table_bytes": int(prob.table_bytes(args.precision)), "l2_capacity": int(l2_size)}
 
     cpu = None
+    parity = None
     if rank == 0 and not args.no_cpu_baseline:
         threads = len(os.sched_getaffinity(0))
-        rate, n, dt = oracle_rate(prob, args.cpu_budget_s, threads)
+        rate, n, dt, ref = oracle_rate(prob, args.cpu_budget_s, threads)
         cpu = {"value": rate, "unit": "particles/s", "cores": threads, "kind": "oracle",
-               "sample": f"first {n} histories of batch 0 ({dt:.1f} s)"}
+               "sample": f"first {n} histories of batch 0 of problem 0 ({dt:.1f} s)"}
+        parity = parity_record(ctx, geoms[0], prob, n, ref, args.precision, stream)
+
+    extras = {}
+    if rank == 0 and args.config == 2 and stock and not args.no_extras:
+        ctx.close()
+        ctx = None
+        extras["fp32_vs_fp64"] = fp32_vs_fp64_record(stream, local)
+        m = stress_measure(1, 10_000_000, args.steps, args.warmup, stream, local)
+        extras["lookup_stress_fp32"] = {
+            "workload": m["prob"].name, "description": WORKLOADS[6],
+            "lookups_per_s": 10_000_000 * args.steps / (sum(m["ms"]) * 1e-3),
+            "micro_lookups_per_s": 10_000_000 * m["micro_per"] * args.steps / (sum(m["ms"]) * 1e-3),
+            "roofline": m["roofline"], "clocks": m["clocks"]}
 
     launches = sum(2 + ITER_KERNELS * s["iterations"] for s in stats)   # + init, tail
     if rank == 0:
@@ -784,11 +970,14 @@ def main():
                                                      "handoffs")},
             "top_kernel": top,
             "cpu_baseline": cpu,
+            "parity": parity,
             "clocks": clk.summary(),
             "gpu_launches": launches,
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
-    ctx.close()
+    if ctx is not None:
+        ctx.close()
     if world > 1:
         dist.destroy_process_group()
 

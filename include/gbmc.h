@@ -333,8 +333,12 @@ int gbmc_read_stats(gbmc_ctx *ctx, gbmc_stats *out);
 
 /* Macroscopic lookup only (the lookup event of Sec. 2 "Sorting", outside
  * the transport loop), on DEVICE pointers owned by the caller:
- *   d_E [n] binary64 energies within the tables' grids, d_mat [n] int32
- *   material ids, outputs d_sigma_t and d_sigma_a [n] binary64.
+ *   d_E [n] binary64 energies within the tables' grids (outside them the
+ *   first or last interval is extrapolated), d_mat [n] int32 material ids,
+ *   outputs d_sigma_t and d_sigma_a [n] binary64.  A query whose material id
+ *   is not in [0, n_mat) gets NaN in both outputs and reads no table.  The
+ *   four arrays must each hold n elements of these types; the library cannot
+ *   check device buffers, so shorter ones are read or written out of bounds.
  * precision selects the loaded table copy.  sort = 1 sorts the queries by
  * (material, energy) into context-owned scratch first (results are written
  * back in query order).  Asynchronous on `stream`. */
@@ -493,6 +497,9 @@ int gbmc_autotune(gbmc_ctx *ctx, int32_t n_prob, const gbmc_problem *probs, doub
  *   - all calls share the one area: calls whose work overlaps on the GPU
  *     (other streams, other threads, other contexts on the same device)
  *     race and corrupt each other's results; order them on one stream;
+ *   - the area's address is kept per device for the life of the process:
+ *     the calls assume the device's primary context (the one the CUDA
+ *     runtime uses) and no cudaDeviceReset between them;
  *   - it calls no cudaMalloc / cudaFree and no allocating library routine.
  * Inputs and outputs are DEVICE pointers owned by the caller, as in
  * gbmc_lookup_macro.  Asynchronous on `stream`. */

@@ -153,6 +153,7 @@ struct gbmc_ctx {
 
     // importance network (fp32 master, Adam state, gradient, BF16 copy)
     bool net_set = false;
+    bool mlp_dead = false;           // a tensor-core forward never completed: refuse the network
     float *d_net_p = nullptr, *d_net_m = nullptr, *d_net_v = nullptr, *d_net_g = nullptr;
     float *d_net_scratch = nullptr;   // [0]: 1 / sum of weights, [1]: loss
     __nv_bfloat16* d_net_w = nullptr;
@@ -1700,17 +1701,23 @@ namespace {
 
 int need_net(gbmc_ctx* c) {
     if (!c->net_set) return fail(c, GBMC_ERR_NOT_INITIALIZED, "set the importance network first");
+    if (c->mlp_dead)
+        return fail(c, GBMC_ERR_TIMEOUT,
+                    "an earlier network forward never completed on the tensor cores; "
+                    "create a new context");
     return GBMC_OK;
 }
 
 // Waits for stream s and reports (and clears) a tensor-core wait that gave
-// up in the network forward.
+// up in the network forward.  Flag 2: the products never arrived, so a CTA
+// kept its tensor memory; the network is refused from then on.
 int mlp_status(gbmc_ctx* c, cudaStream_t s) {
     CK(cudaStreamSynchronize(s));
     int flag = 0;
     CK(cudaMemcpy(&flag, c->d_mlp_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (flag) {
         CK(cudaMemset(c->d_mlp_err, 0, sizeof(int)));
+        if (flag >= 2) c->mlp_dead = true;
         return fail(c, GBMC_ERR_TIMEOUT, "network forward: tensor-core wait gave up");
     }
     return GBMC_OK;

@@ -758,6 +758,121 @@ __device__ __forceinline__ void macro64(const Tables& T, int32_t m, double E, do
     sa = aa;
 }
 
+// Tile mode of the binary64 macroscopic lookup, for 32 queue entries of one
+// material taken in (material, energy) order by one warp (all 32 lanes call;
+// lanes >= nv hold no entry).  Instead of every lane walking the material's
+// nuclides for its own particle (a chain of dependent loads per nuclide:
+// descriptor, coarse index, probe, interval), each lane takes one nuclide
+// over a run of consecutive particles: sorted energies mostly share the
+// bracket of the previous particle, which the lane keeps in registers, so
+// most micro lookups load nothing.  The terms N_i sigma_i(E_p) go through a
+// shared-memory tile (row = nuclide, column = particle), and each lane then
+// adds its particle's terms in the listed order: every term, running sum and
+// checkpoint is the one macro64 forms.
+//
+// Nuclides are taken kTileG at a time.  With gn nuclides in a group and gp
+// the power of two at or above gn, lane l takes nuclide l % gp (if < gn) over
+// particles (l / gp) gp .. + gp - 1.  Rows are kTileStride doubles apart:
+// for every gp the 16 lanes of each half-warp then store to distinct 8-byte
+// banks, and the column reads of the sums are contiguous.
+constexpr int kTileG = 8;
+constexpr int kTileStride = 33;
+static_assert(kTileG == 8, "the lane mapping covers groups of at most 8 nuclides");
+static_assert(kCumGroup64 == 4, "tile checkpoints: one per four entries, two to a 16-byte store");
+
+// A chunk takes the tile only when its energies are close: over at most
+// 2^44 units of their binary64 bit patterns (about 0.3% relative), so that a
+// run of consecutive particles mostly shares each nuclide's bracket.  A
+// chunk spread wider (the sparse tail of a sorted queue) would miss at
+// almost every particle, and each miss in the tile is a dependent search
+// that the lane's other particles wait behind; such chunks take the
+// per-particle lookup, whose lanes search their nuclides in lock step.
+constexpr unsigned long long kTileSpan = 1ull << 44;
+
+// All 32 lanes call; E of lanes without an entry is ignored (valid false).
+__device__ __forceinline__ bool tile_span_ok(double E, bool valid) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(E);
+    unsigned long long lo = valid ? b : ~0ull, hi = valid ? b : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        unsigned long long h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        lo = l2 < lo ? l2 : lo;
+        hi = h2 > hi ? h2 : hi;
+    }
+    return hi - lo < kTileSpan;
+}
+
+struct LookupTile {
+    double t[kTileG * kTileStride];   // terms of the group, row = nuclide, column = particle
+    double E[32];                     // the chunk's energies
+};
+
+template <bool SA>
+__device__ __forceinline__ void macro64_tile(const Tables& T, int32_t m, int nv, double E_lane,
+                                             LookupTile& sm, double* cum, double& st,
+                                             double& sa) {
+    const int lane = threadIdx.x & 31;
+    sm.E[lane] = E_lane;
+    __syncwarp();
+    const int32_t q0 = __ldg(T.mat_off + m), nq = __ldg(T.mat_off + m + 1) - q0;
+    const unsigned long long* g = reinterpret_cast<const unsigned long long*>(T.e64);
+    double at = 0.0, aa = 0.0;
+    double2 pend = make_double2(0.0, 0.0);   // checkpoint pair not yet stored
+    for (int32_t g0 = 0; g0 < nq; g0 += kTileG) {
+        const int gn = min(kTileG, nq - g0);
+        const int gp = gn > 4 ? 8 : (gn > 2 ? 4 : gn);
+        const int i = lane & (gp - 1), s = lane / gp;
+        if (i < gn) {
+            const int32_t q = q0 + g0 + i;
+            const Desc64 d = load_desc64(T.d64 + q);
+            const double N = __ldg(T.density + q);
+            const unsigned long long* gg = g + d.off;
+            int32_t k = -1;                               // bracket held in registers
+            unsigned long long elo = 0ull, ehi = 0ull;    // bits of E_k, E_k+1
+            double2 r0 = make_double2(0.0, 0.0), r1 = make_double2(0.0, 0.0);   // (de, ds), (s0, y)
+            for (int j = 0; j < gp; ++j) {
+                const int p = s * gp + j;
+                if (p >= nv) break;
+                const double E = sm.E[p];
+                const unsigned long long eb = (unsigned long long)__double_as_longlong(E);
+                // the held bracket is E's if it is the largest j <= n-2 with E_j <= E
+                const bool hit = k >= 0 && (eb >= elo || k == 0) && (eb < ehi || k == d.n - 2);
+                if (!hit) {
+                    int32_t lo, hi;
+                    coarse_range(d, T.idx64, eb, lo, hi);
+                    k = bracket_in(gg, lo, hi, eb);
+                    elo = __ldg(gg + k);
+                    ehi = __ldg(gg + k + 1);
+                    const double2* rp = reinterpret_cast<const double2*>(T.iv64 + d.off + k);
+                    r0 = __ldg(rp);
+                    r1 = __ldg(rp + 1);
+                }
+                const double f = frac_rn(E, __longlong_as_double((long long)elo), r0.x,
+                                         (unsigned long long)__double_as_longlong(r1.y));
+                sm.t[i * kTileStride + p] = N * (r1.x + f * r0.y);
+            }
+        }
+        __syncwarp();
+        if (lane < nv) {
+            for (int ii = 0; ii < gn; ++ii) {
+                const double t = sm.t[ii * kTileStride + lane];
+                const int32_t a = g0 + ii;   // entry index within the material
+                at = at + t;
+                if (SA) aa = aa + t * __ldg(T.f_abs + __ldg(T.nuc_id + q0 + a));
+                if (cum && ((a & 3) == 3 || a == nq - 1)) {
+                    const int32_t gq = a >> 2;
+                    if (gq & 1) pend.y = at; else pend.x = at;
+                    if ((gq & 1) || a == nq - 1) reinterpret_cast<double2*>(cum)[gq >> 1] = pend;
+                }
+            }
+        }
+        __syncwarp();
+    }
+    st = at;
+    sa = aa;
+}
+
 template <bool SA = true, bool WIDE = false>
 __device__ __forceinline__ void macro32(const Tables& T, int32_t m, double E, double& st,
                                         double& sa, float* cum = nullptr) {

@@ -252,6 +252,7 @@ __global__ void __launch_bounds__(128) k_mlp_forward_tc(const __nv_bfloat16* __r
     const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
     uint32_t phase = 0;
     bool ok = true;
+    bool drained = true;   // no product is still being written to the accumulator
 
     for (int64_t base = (int64_t)blockIdx.x * 128; base < n && ok; base += (int64_t)gridDim.x * 128) {
         // layer 1 (fp32) for row tid; relu(z1) as bf16 into the A tile
@@ -296,9 +297,12 @@ __global__ void __launch_bounds__(128) k_mlp_forward_tc(const __nv_bfloat16* __r
         }
         // wait for the products (bounded; the whole CTA gives up together)
         if (__syncthreads_or(!wait_phase(mbar, phase))) {
-            if (tid == 0) atomicExch(err, 1);
             ok = false;
-            wait_phase(mbar, phase);   // once more (bounded) for the products in flight
+            // once more (bounded) for the products in flight; if they still
+            // have not arrived the accumulator may be in use, so it is not
+            // freed (flag 2: the network's tensor-core path is unusable)
+            drained = !__syncthreads_or(!wait_phase(mbar, phase));
+            if (tid == 0) atomicMax(err, drained ? 1 : 2);
             break;
         }
         phase ^= 1u;
@@ -328,7 +332,7 @@ __global__ void __launch_bounds__(128) k_mlp_forward_tc(const __nv_bfloat16* __r
         __syncthreads();   // the A tile and the accumulator are free again
     }
     __syncthreads();
-    if (warp == 0)
+    if (warp == 0 && drained)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
                      "r"(kTcCols));
 }

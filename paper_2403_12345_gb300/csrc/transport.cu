@@ -490,6 +490,7 @@ __global__ void __launch_bounds__(256, PREC == GBMC_FP64 ? 4 : 3) k_lookup(Param
     const int32_t* q = c->sorted ? P.Q.lqs : P.Q.lq[cur];
     int32_t* aq = P.Q.aq[cur] + c->aq_base;
     unsigned long long micro = 0;
+    const bool sorted = c->sorted != 0;
     // warps take 32-entry chunks from a cursor: a material's lookups cost in
     // proportion to its nuclides, so a static stride leaves late blocks with
     // the long ones
@@ -500,17 +501,29 @@ __global__ void __launch_bounds__(256, PREC == GBMC_FP64 ? 4 : 3) k_lookup(Param
         b0 = __shfl_sync(kFull, b0, 0);
         if (b0 >= n) break;
         int64_t idx = b0 + lane;
-        if (idx < n) {
-            int32_t slot = q[idx];
-            double E = P.B.p[slot].E;
-            int32_t m = P.B.p[slot].mat;
-            double st, sa;
-            if (PREC == GBMC_FP64)
+        bool valid = idx < n;
+        int32_t slot = valid ? q[idx] : 0;
+        double E = valid ? P.B.p[slot].E : 0.0;
+        int32_t m = valid ? P.B.p[slot].mat : 0;
+        double st = 0.0, sa = 0.0;
+        if constexpr (PREC == GBMC_FP64) {
+            // a sorted chunk of one material: the nuclide-major tile
+            __shared__ LookupTile tile[8];
+            int32_t m0 = __shfl_sync(kFull, m, 0);
+            if (sorted && __all_sync(kFull, !valid || m == m0) && tile_span_ok(E, valid)) {
+                int nv = (int)(n - b0 < 32 ? n - b0 : 32);
+                macro64_tile<SA>(P.T, m0, nv, E, tile[threadIdx.x >> 5],
+                                 valid && P.cum ? (double*)P.cum + slot * P.cum_stride : nullptr,
+                                 st, sa);
+            } else if (valid) {
                 macro64<SA>(P.T, m, E, st, sa,
                             P.cum ? (double*)P.cum + slot * P.cum_stride : nullptr);
-            else
-                macro32<SA, WIDE>(P.T, m, E, st, sa,
-                                  P.cum ? (float*)P.cum + slot * P.cum_stride : nullptr);
+            }
+        } else if (valid) {
+            macro32<SA, WIDE>(P.T, m, E, st, sa,
+                              P.cum ? (float*)P.cum + slot * P.cum_stride : nullptr);
+        }
+        if (valid) {
             P.B.p[slot].st = st;
             if (SA) P.B.p[slot].sa = sa;
             aq[idx] = slot;
@@ -1227,7 +1240,8 @@ __global__ void __launch_bounds__(256) k_query_keys(Params P, const double* E, c
     GBMC_WARP_LOOP(idx, valid, n) {
         uint32_t key = 0;
         if (valid) {
-            key = sort_key(P, E[idx], mat[idx]);
+            int32_t m = mat[idx];
+            key = sort_key(P, E[idx], (uint32_t)m < (uint32_t)P.T.n_mat ? m : 0);
             keys[idx] = key;
         }
         warp_count(hist, key, valid);
@@ -1259,11 +1273,14 @@ __global__ void __launch_bounds__(256, 4) k_query_lookup(Tables T, const double*
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
         int64_t i = perm ? (int64_t)perm[k] : k;
-        double a, b;
-        if (PREC == GBMC_FP64)
-            macro64(T, mat[i], E[i], a, b);
-        else
-            macro32(T, mat[i], E[i], a, b);
+        int32_t m = mat[i];
+        double a = CUDART_NAN, b = CUDART_NAN;   // a material id out of range: NaN, no lookup
+        if ((uint32_t)m < (uint32_t)T.n_mat) {
+            if (PREC == GBMC_FP64)
+                macro64(T, m, E[i], a, b);
+            else
+                macro32(T, m, E[i], a, b);
+        }
         st[i] = a;
         sa[i] = b;
     }

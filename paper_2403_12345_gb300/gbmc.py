@@ -510,27 +510,54 @@ class Context:
         return ms.value
 
     def lookup_macro(self, E, mat, sigma_t, sigma_a, precision=FP64, sort=False, stream=None):
-        """E (float64), mat (int32), sigma_t, sigma_a (float64): CUDA tensors
-        (or raw device addresses) of equal length, written in query order."""
-        def ptr(t):
-            return C.c_void_p(t if isinstance(t, int) else t.data_ptr())
-        n = E.numel() if hasattr(E, "numel") else len(E)
-        self._ck(lib().gbmc_lookup_macro(self._h, int(precision), ptr(E), ptr(mat), int(n),
-                                         ptr(sigma_t), ptr(sigma_a), 1 if sort else 0,
+        """E (float64), mat (int32), sigma_t, sigma_a (float64): contiguous
+        CUDA tensors of equal length on this context's device, written in
+        query order."""
+        n = _lookup_args(E, mat, sigma_t, sigma_a)
+        self._ck(lib().gbmc_lookup_macro(self._h, int(precision), C.c_void_p(E.data_ptr()),
+                                         C.c_void_p(mat.data_ptr()), n,
+                                         C.c_void_p(sigma_t.data_ptr()),
+                                         C.c_void_p(sigma_a.data_ptr()), 1 if sort else 0,
                                          _stream(stream)))
 
     def lookup_macro_noalloc(self, E, mat, sigma_t, sigma_a, precision=FP64, stream=None):
         """The sorted lookup of lookup_macro(sort=True) with no device
-        allocation: for callers that cannot allocate (for example while a
-        stream is being captured).  At most NOALLOC_MAX_QUERIES queries per
-        call; calls that overlap on the GPU must not be issued (they share one
-        scratch area).  Make the first call on a device before any capture."""
-        def ptr(t):
-            return C.c_void_p(t if isinstance(t, int) else t.data_ptr())
-        n = E.numel() if hasattr(E, "numel") else len(E)
-        self._ck(lib().gbmc_lookup_macro_noalloc(self._h, int(precision), ptr(E), ptr(mat),
-                                                 int(n), ptr(sigma_t), ptr(sigma_a),
+        allocation, for callers that cannot allocate device memory while they
+        call the library.  At most NOALLOC_MAX_QUERIES queries per call;
+        calls that overlap on the GPU must not be issued (they share one
+        scratch area).  Make the first call on a device before any stream
+        capture.  Arguments as in lookup_macro."""
+        n = _lookup_args(E, mat, sigma_t, sigma_a)
+        self._ck(lib().gbmc_lookup_macro_noalloc(self._h, int(precision),
+                                                 C.c_void_p(E.data_ptr()),
+                                                 C.c_void_p(mat.data_ptr()), n,
+                                                 C.c_void_p(sigma_t.data_ptr()),
+                                                 C.c_void_p(sigma_a.data_ptr()),
                                                  _stream(stream)))
+
+
+def _lookup_args(E, mat, sigma_t, sigma_a) -> int:
+    """Checks the standalone lookup's tensors (the library cannot check device
+    buffers): float64 energies and outputs, int32 materials, all contiguous
+    CUDA tensors of one length on one device.  Returns the length."""
+    want = (("E", E, "torch.float64"), ("mat", mat, "torch.int32"),
+            ("sigma_t", sigma_t, "torch.float64"), ("sigma_a", sigma_a, "torch.float64"))
+    dev = None
+    for name, t, dt in want:
+        if not (hasattr(t, "data_ptr") and hasattr(t, "is_cuda")):
+            raise TypeError(f"{name} must be a torch tensor")
+        if str(t.dtype) != dt:
+            raise TypeError(f"{name} must be {dt}, got {t.dtype}")
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CUDA tensor")
+        if dev is None:
+            dev = t.device
+        elif t.device != dev:
+            raise ValueError(f"{name} is on {t.device}, E on {dev}")
+    n = E.numel()
+    if any(t.numel() != n for _, t, _ in want):
+        raise ValueError("E, mat, sigma_t and sigma_a must have the same length")
+    return int(n)
 
 
 def _n_cells(g: Geometry) -> int:

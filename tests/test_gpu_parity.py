@@ -300,3 +300,65 @@ def test_invalid_inputs_rejected_before_launch():
         assert ex.value.code == gbmc.ERR_NOT_INITIALIZED
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("precision", [gbmc.FP64, gbmc.FP32])
+def test_lookup_macro_material_out_of_range_gives_nan(precision):
+    import torch
+    prob, E, mat = synth.make_stress_lookup(n_queries=4099, n_nuc=20, n_in_mat=12, n_points=500)
+    mat[1::5] = 1
+    bad = np.arange(2, len(mat), 7)
+    mat[bad] = np.array([-1, 2, 1 << 30, -(1 << 31)], np.int32)[np.arange(len(bad)) % 4]
+    ctx = make_ctx(prob, (precision,))
+    try:
+        for sort in (False, True):
+            dE = torch.tensor(E, device="cuda")
+            dm = torch.tensor(mat, device="cuda")
+            st = torch.zeros_like(dE)
+            sa = torch.zeros_like(dE)
+            ctx.lookup_macro(dE, dm, st, sa, precision=precision, sort=sort)
+            torch.cuda.synchronize()
+            st, sa = st.cpu().numpy(), sa.cpu().numpy()
+            assert np.isnan(st[bad]).all() and np.isnan(sa[bad]).all()
+            for m in (0, 1):
+                sel = mat == m
+                rt, ra = oracle.macro(prob, m, E[sel], precision=precision)
+                assert np.array_equal(st[sel].view(np.int64), rt.view(np.int64)), sort
+                assert np.array_equal(sa[sel].view(np.int64), ra.view(np.int64)), sort
+        out = torch.zeros_like(dE)
+        with pytest.raises(TypeError):   # int64 material ids are refused by the binding
+            ctx.lookup_macro(dE, dm.to(torch.int64), out, out)
+    finally:
+        ctx.close()
+
+
+@pytest.mark.parametrize("sizes", [(17, 9), (5, 1), (8, 3), (2, 16), (4, 7)])
+@pytest.mark.parametrize("reaction", [False, True])
+def test_sorted_thread_lookups_every_group_size(sizes, reaction):
+    """Every lookup in thread mode and sorted (the nuclide-major tile of the
+    binary64 lookup), on materials whose nuclide counts leave partial groups
+    of every size; ragged chunk tails; with and without Sigma_a (the
+    absorption-rate tally); the collision's nuclide choice from the tile's
+    checkpoints."""
+    a, b = sizes
+    p = synth.make_tiny_problem(seed=36 + a, n_nuc=a + b, n_points=(200, 3000),
+                                kind=synth.GEOM_LATTICE, lattice_n=6, n_particles=20_011)
+    rng = np.random.default_rng(a * 100 + b)
+    p.mat_off = np.array([0, a, a + b], np.int32)
+    p.nuc_id = np.concatenate([rng.permutation(a), a + rng.permutation(b)]).astype(np.int32)
+    p.density = rng.uniform(0.01, 1.0, a + b)
+    ctx = make_ctx(p, warp_lookup_max=-1, sort_min=1, tail_max=-1, max_in_flight=7_001)
+    try:
+        if reaction:
+            ctx.set_reaction_tally(True)
+        g = run_gpu(ctx, gpu_problem(p, n=20_011, batch=3))
+        ar = ctx.read_reaction_tally(0) if reaction else None
+    finally:
+        ctx.close()
+    ref = oracle.run(p, seed=p.seed, batch=3, n=20_011)
+    assert_outcomes_equal(g, ref, label=f"materials {sizes}")
+    assert_tallies_close(g, ref)
+    if reaction:
+        assert_tallies_close(dict(flux=ar, counts=ref["counts"], weights=ref["weights"]),
+                             dict(flux=ref["absrate"], counts=ref["counts"],
+                                  weights=ref["weights"]))
