@@ -743,6 +743,9 @@ def main():
     ap.add_argument("--autotune", type=int, default=-1,
                     help="1: autotune launch settings before timing, 0: defaults "
                          "(default: autotune configs 2-4)")
+    ap.add_argument("--loops", type=int, default=0,
+                    help="concurrent event loops over the steps' batches (gbmc_run_concurrent); "
+                         "0: the fastest of 1-4 in a short trial after autotuning")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the sub-records of the default run (binary32 against binary64 "
                          "at 1e7 particles, the lookup-only stress set)")
@@ -835,28 +838,68 @@ def main():
                           "wide_windows": int(ctx.options.wide_windows)}), flush=True)
         ctx.close()
         return
+    # concurrent event loops (Sec. 2, "GPU Streams"): a short trial of 1-4
+    # loops, each also at 4 blocks per SM, picks the fastest (a candidate must
+    # beat one loop by 2%)
+    loops, loop_trials = max(args.loops, 1), None
+    if args.loops == 0 and args.config in (2, 3, 4) and args.streams == 1:
+        loop_trials = {}
+        tuned_bps = ctx.options.blocks_per_sm
+        best = None
+        for L in (1, 2, 3, 4):
+            for bps in sorted({tuned_bps, 4}):
+                ctx.set_options(blocks_per_sm=bps)
+                nb = 2 * L
+                for rep in range(2):   # the first builds the loops' graphs
+                    batch = [pr for b in range(nb) for pr in problems(50_000 + 10 * rep + b)]
+                    torch.cuda.synchronize()
+                    t = time.perf_counter()
+                    ctx.run_concurrent(batch, n_loops=L, per_run=n_geo, stream=stream)
+                    torch.cuda.synchronize()
+                    dt = time.perf_counter() - t
+                rate = nb * npart / dt
+                loop_trials[f"{L}x{bps}"] = rate
+                if best is None or (rate > best[0] * 1.02 if L > 1 else rate > best[0]):
+                    best = (rate, L, bps)
+        _, loops, bps = best
+        ctx.set_options(blocks_per_sm=bps)
     ctx.reset_tallies(stream)
 
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
     stats = []
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    with Clocks(local) as clk:
-        t0 = time.perf_counter()
-        for k in range(args.steps):
-            flush.zero_()
-            ev[k][0].record(stream)
-            ctx.run_problems(problems(k), stream)
-            ev[k][1].record(stream)
-            stats.append(ctx.read_stats())   # synchronizes; outside the events
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
+    if loops > 1:
+        # every step's batch in one concurrent call (batch k in tally slots
+        # k n_geo ..): the steps overlap, so the time is the call's
+        all_probs = [pr for k in range(args.steps) for pr in problems(k)]
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with Clocks(local) as clk:
+            t0 = time.perf_counter()
+            e0.record(stream)
+            ctx.run_concurrent(all_probs, n_loops=loops, per_run=n_geo, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+        stats.append(ctx.read_stats())
+        tot_ms = e0.elapsed_time(e1)
+    else:
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        with Clocks(local) as clk:
+            t0 = time.perf_counter()
+            for k in range(args.steps):
+                flush.zero_()
+                ev[k][0].record(stream)
+                ctx.run_problems(problems(k), stream)
+                ev[k][1].record(stream)
+                stats.append(ctx.read_stats())   # synchronizes; outside the events
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+        tot_ms = sum(a.elapsed_time(b) for a, b in ev)
     if world > 1:
         dist.barrier()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    tot_ms = sum(step_ms)
     if world > 1:
         t = torch.tensor([tot_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -894,13 +937,25 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     d2h = 0
-    for k in range(e2e_steps):
-        ctx.run_problems(problems(20_000 + k), stream)
-        d2h = 0
-        for slot in range(n_geo):
-            fl, cn, wt = ctx.read_tallies(slot, out=hosts[slot][0])
-            o = ctx.read_outcomes(slot, 0, counts[slot], out=hosts[slot][1])
-            d2h += fl.nbytes + cn.nbytes + wt.nbytes + sum(o[f].nbytes for f in o)
+    if loops > 1:
+        # all e2e batches in one concurrent call, then every batch's tallies
+        # and outcomes read back (per step: one batch's worth)
+        ctx.run_concurrent([pr for k in range(e2e_steps) for pr in problems(20_000 + k)],
+                           n_loops=loops, per_run=n_geo, stream=stream)
+        for k in range(e2e_steps):
+            d2h = 0
+            for slot in range(n_geo):
+                fl, cn, wt = ctx.read_tallies(k * n_geo + slot, out=hosts[slot][0])
+                o = ctx.read_outcomes(k * n_geo + slot, 0, counts[slot], out=hosts[slot][1])
+                d2h += fl.nbytes + cn.nbytes + wt.nbytes + sum(o[f].nbytes for f in o)
+    else:
+        for k in range(e2e_steps):
+            ctx.run_problems(problems(20_000 + k), stream)
+            d2h = 0
+            for slot in range(n_geo):
+                fl, cn, wt = ctx.read_tallies(slot, out=hosts[slot][0])
+                o = ctx.read_outcomes(slot, 0, counts[slot], out=hosts[slot][1])
+                d2h += fl.nbytes + cn.nbytes + wt.nbytes + sum(o[f].nbytes for f in o)
     e2e_s = time.perf_counter() - t0
     h2d = ctypes.sizeof(gbmc.Problem) * n_geo
 
@@ -936,6 +991,7 @@ def main():
                "sample": f"first {n} histories of batch 0 of problem 0 ({dt:.1f} s)"}
         parity = parity_record(ctx, geoms[0], prob, n, ref, args.precision, stream)
 
+    run_bps = int(ctx.options.blocks_per_sm)
     extras = {}
     if rank == 0 and args.config == 2 and stock and not args.no_extras:
         ctx.close()
@@ -948,7 +1004,8 @@ def main():
             "micro_lookups_per_s": 10_000_000 * m["micro_per"] * args.steps / (sum(m["ms"]) * 1e-3),
             "roofline": m["roofline"], "clocks": m["clocks"]}
 
-    launches = sum(2 + ITER_KERNELS * s["iterations"] for s in stats)   # + init, tail
+    runs = args.steps if loops > 1 else 1   # graph launches per entry of stats
+    launches = sum(2 * runs + ITER_KERNELS * s["iterations"] for s in stats)   # + init, tail
     if rank == 0:
         line = {
             "metric": "particles/s", "value": value, "unit": "particles/s", "n_gpus": world,
@@ -963,6 +1020,11 @@ def main():
             "e2e": {"value": npart * e2e_steps / e2e_s, "unit": "particles/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "autotune": tuned,
+            "concurrent_loops": {"loops": loops, "blocks_per_sm": run_bps,
+                                 "trial_particles_per_s": loop_trials,
+                                 "how": "gbmc_run_concurrent: the steps' batches spread over this "
+                                        "many event loops on their own streams (Sec. 2 'GPU "
+                                        "Streams'); one loop: one graph launch per step"},
             "roofline": roof,
             "kernel_ms_per_batch": {k: v[0] for k, v in kt.items()},
             "events_per_batch": {k: pst[k] for k in ("lookups", "micro_lookups", "flights",
@@ -974,6 +1036,11 @@ def main():
             "clocks": clk.summary(),
             "gpu_launches": launches,
         }
+        if loops > 1:
+            line["config"]["l2"] = ("flushed once before the timed call (256 MiB write); the "
+                                    "steps' batches overlap on the loops, each with a working set "
+                                    "(tables, particle bank, running sums) beyond the L2")
+            line["config"]["parallelism"] += f" x {loops} concurrent event loops"
         line.update(extras)
         print(json.dumps(line), flush=True)
     if ctx is not None:

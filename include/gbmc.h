@@ -244,6 +244,30 @@ int gbmc_run_batch(gbmc_ctx *ctx, const gbmc_problem *prob, void *stream);
 int gbmc_run_problems(gbmc_ctx *ctx, int32_t n_prob, const gbmc_problem *probs,
                       void *stream);
 
+/* Concurrent event loops (Sec. 2, "GPU Streams": several independent event
+ * loops share one GPU, so that the short final iterations of one, bound by
+ * latency rather than work, overlap the full iterations of another).
+ * Results are those of gbmc_run_problems(ctx, n_prob, probs, stream):
+ * problem p's histories, outcomes (problem slot p), flux and scalar tallies
+ * (slot p) are the same, and the tallies follow the same slot layout.  Only
+ * the execution differs: the problems are taken in runs of per_run
+ * consecutive problems, run r goes to event loop r % n_loops, each loop runs
+ * its runs one after another, and the loops run concurrently.  A loop is a
+ * particle bank, queues, control block, graph and CUDA stream of its own,
+ * created on first use and kept by the context; all loops read the
+ * context's tables and add into its tallies and outcome buffers.  The loops
+ * start after the work already queued on `stream`, and `stream` waits for
+ * all of them: the call is asynchronous on `stream`.
+ *   n_loops  1..16 (device memory: one bank, queues and running-sum cache
+ *            per loop, sized for its largest run);
+ *   per_run  problems per run, >= 1 (1: one batch at a time per loop).
+ * Afterwards gbmc_read_stats sums the counters of every run of the call and
+ * gbmc_last_run_ms times the whole call.  Weight windows, k-eigenvalue
+ * banking, bank sources and importance recording give GBMC_ERR_UNSUPPORTED
+ * (they run in one event loop).  Other errors as gbmc_run_problems. */
+int gbmc_run_concurrent(gbmc_ctx *ctx, int32_t n_prob, const gbmc_problem *probs,
+                        int32_t n_loops, int32_t per_run, void *stream);
+
 /* Synchronize the last run's stream and copy the tallies of problem slot
  * `slot`: flux [n_cells * n_bins] (cell-major; n_flux must equal it; NULL
  * skips), counts [GBMC_NSCAL] and weights [GBMC_NSCAL] (NULL skips).

@@ -25,6 +25,8 @@ static_assert(sizeof(gbmc_problem) == 136, "gbmc_problem layout is part of the A
 namespace {
 
 thread_local std::string g_create_error;
+constexpr int32_t kMaxLoops = 16;   // concurrent event loops of one context
+void destroy_loop(gbmc_ctx* l);
 
 // Free a device buffer; work still queued on any stream may use it, so the
 // device is drained first (reallocation is rare: buffers only grow).
@@ -121,6 +123,8 @@ struct gbmc_ctx {
     int64_t h_planes_cap = 0;
     Ctl* d_ctl = nullptr;
     Ctl* h_ctl = nullptr;            // pinned staging / read-back
+    RunStats* d_stats = nullptr;     // counters of the last call's runs
+    RunStats* h_stats = nullptr;     // pinned read-back
     cudaEvent_t staged = nullptr;
 
     // graph of the event loop
@@ -171,6 +175,15 @@ struct gbmc_ctx {
     bool imp_on = false;
     double *d_imp_cnt = nullptr, *d_imp_scr = nullptr, *d_imp_cellsum = nullptr;
     int64_t imp_cells = 0;
+
+    // concurrent event loops (gbmc_run_concurrent): each a context of its
+    // own bank, queues, control block, graph and stream that borrows this
+    // context's tables, materials, tally definition, tallies and outcomes
+    bool borrowed = false;           // this context is such a loop
+    cudaStream_t own_stream = nullptr;
+    cudaEvent_t done_ev = nullptr;   // the loop's last run of a call
+    std::vector<gbmc_ctx*> loops;
+    int32_t last_loops = 0;          // loops the last run call used (0: this context's own loop)
 
     // standalone-lookup scratch
     int64_t q_cap = 0;
@@ -444,6 +457,7 @@ Params make_params(gbmc_ctx* c) {
     P.O = c->O;
     P.Y = c->Y;
     P.ctl = c->d_ctl;
+    P.st = c->d_stats;
     P.probs = c->d_probs;
     P.capacity = c->capacity;
     P.precision = c->opt.precision;
@@ -740,15 +754,34 @@ int build_desc64(gbmc_ctx* c) {
     return upload(c, &c->d_desc64, d.data(), tot);
 }
 
+// Waits for the last run call and reads the counters of its runs (this
+// context's own loop, or every concurrent loop it used) into h_stats; the
+// first error any of them flagged decides the status.
 int read_ctl(gbmc_ctx* c) {
     if (!c->ran) return fail(c, GBMC_ERR_NOT_INITIALIZED, "no run has been launched");
     CK(cudaStreamSynchronize(c->last_stream));
-    CK(cudaMemcpy(c->h_ctl, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
-    if (c->h_ctl->err == GBMC_ERR_TIMEOUT)
+    int err = 0;
+    if (c->last_loops == 0) {
+        CK(cudaMemcpy(c->h_ctl, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(c->h_stats, c->d_stats, sizeof(RunStats), cudaMemcpyDeviceToHost));
+        err = c->h_ctl->err ? c->h_ctl->err : c->h_stats->err;
+    } else {
+        RunStats sum{};
+        for (int32_t j = 0; j < c->last_loops; ++j) {
+            RunStats one;
+            CK(cudaMemcpy(&one, c->loops[j]->d_stats, sizeof(RunStats), cudaMemcpyDeviceToHost));
+            sum.iterations += one.iterations; sum.lookups += one.lookups; sum.micro += one.micro;
+            sum.flights += one.flights; sum.cross += one.cross; sum.coll += one.coll;
+            sum.hist += one.hist; sum.handoff += one.handoff;
+            if (!sum.err) sum.err = one.err;
+        }
+        *c->h_stats = sum;
+        err = sum.err;
+    }
+    if (err == GBMC_ERR_TIMEOUT)
         return fail(c, GBMC_ERR_TIMEOUT, "event loop stopped at its iteration bound (%d)",
                     c->opt.max_iterations);
-    if (c->h_ctl->err)
-        return fail(c, GBMC_ERR_DEVICE_FLAG, "device flagged error %d", c->h_ctl->err);
+    if (err) return fail(c, GBMC_ERR_DEVICE_FLAG, "device flagged error %d", err);
     return GBMC_OK;
 }
 
@@ -807,6 +840,10 @@ int gbmc_create(gbmc_ctx** out, int device, const gbmc_options* opt) {
     c->sms = prop.multiProcessorCount;
     if ((e = cudaMalloc((void**)&c->d_ctl, sizeof(Ctl))) != cudaSuccess) return bail("ctl", e);
     if ((e = cudaMallocHost((void**)&c->h_ctl, sizeof(Ctl))) != cudaSuccess) return bail("ctl host", e);
+    if ((e = cudaMalloc((void**)&c->d_stats, sizeof(RunStats))) != cudaSuccess) return bail("stats", e);
+    if ((e = cudaMallocHost((void**)&c->h_stats, sizeof(RunStats))) != cudaSuccess)
+        return bail("stats host", e);
+    if ((e = cudaMemset(c->d_stats, 0, sizeof(RunStats))) != cudaSuccess) return bail("stats", e);
     if ((e = cudaEventCreate(&c->staged)) != cudaSuccess) return bail("event", e);
     if ((e = cudaEventCreate(&c->ev0)) != cudaSuccess) return bail("event", e);
     if ((e = cudaEventCreate(&c->ev1)) != cudaSuccess) return bail("event", e);
@@ -818,6 +855,8 @@ int gbmc_destroy(gbmc_ctx* c) {
     if (!c) return GBMC_OK;
     cudaSetDevice(c->device);
     if (c->ran && c->last_stream) cudaStreamSynchronize(c->last_stream);
+    for (gbmc_ctx* l : c->loops) destroy_loop(l);
+    c->loops.clear();
     destroy_graph(c);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     free_bank(c);
@@ -844,6 +883,10 @@ int gbmc_destroy(gbmc_ctx* c) {
     if (c->h_probs) cudaFreeHost(c->h_probs);
     if (c->h_planes) cudaFreeHost(c->h_planes);
     if (c->h_ctl) cudaFreeHost(c->h_ctl);
+    dfree(c->d_stats);
+    if (c->h_stats) cudaFreeHost(c->h_stats);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    if (c->done_ev) cudaEventDestroy(c->done_ev);
     if (c->staged) cudaEventDestroy(c->staged);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
@@ -1088,10 +1131,21 @@ int gbmc_reset_tallies(gbmc_ctx* c, void* stream) {
 
 namespace {
 
+// Where a concurrent loop's run puts its results: per problem of the run,
+// its flux offset, the outcome index of its first particle and its tally
+// slot in the borrowed tallies and outcomes.
+struct RunLayout {
+    const int64_t* flux_off;
+    const int64_t* out_base;
+    const int32_t* slot;
+    bool keep_stats;   // add to the loop's counters (a later run of the same call)
+};
+
 // Validate a run, size the buffers, stage descriptors and the control block
-// (stream-ordered copies on s).  Fills the launch parameters.
+// (stream-ordered copies on s).  Fills the launch parameters.  With lay (a
+// concurrent loop's run) the tallies and outcomes are the borrowed ones.
 int prepare_run(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, cudaStream_t s,
-                Params* Pout, LaunchCfg* Lout) {
+                Params* Pout, LaunchCfg* Lout, const RunLayout* lay = nullptr) {
     if (n_prob < 1 || !probs) return fail(c, GBMC_ERR_INVALID_ARG, "n_prob >= 1 and probs required");
     if (!c->n_nuc || !c->n_mat || !c->n_bins)
         return fail(c, GBMC_ERR_NOT_INITIALIZED, "tables, materials and tally must be set first");
@@ -1165,8 +1219,10 @@ int prepare_run(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, cudaStre
         }
         CK(cudaMemsetAsync(c->d_site_n, 0, sizeof(int32_t) * (size_t)std::max<int64_t>(total, 1), s));
     }
-    if ((rc = ensure_outcomes(c, total > 0 ? total : 1))) return rc;
-    if ((rc = ensure_tallies(c, cells, s))) return rc;
+    if (!lay) {
+        if ((rc = ensure_outcomes(c, total > 0 ? total : 1))) return rc;
+        if ((rc = ensure_tallies(c, cells, s))) return rc;
+    }
     if (n_prob > c->probs_cap) {
         if ((rc = dalloc(c, &c->d_probs, (size_t)n_prob))) return rc;
         c->probs_cap = n_prob;
@@ -1205,7 +1261,9 @@ int prepare_run(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, cudaStre
         d.first_id = probs[p].first_id;
         d.n = probs[p].n_particles;
         d.start = start[p];
-        d.flux_off = c->slot_flux_off[p];
+        d.flux_off = lay ? lay->flux_off[p] : c->slot_flux_off[p];
+        d.out_base = lay ? lay->out_base[p] : start[p];
+        d.slot = lay ? lay->slot[p] : p;
         d.plane_off = plane_off[p];
         d.r2 = probs[p].geom.radius * probs[p].geom.radius;
         d.n_cells = cells[p];
@@ -1234,26 +1292,25 @@ int prepare_run(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, cudaStre
     CK(cudaMemcpyAsync(c->d_probs, c->h_probs, sizeof(DevProblem) * n_prob, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c->d_planes, c->h_planes, sizeof(double) * n_planes, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c->d_ctl, c->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    if (!lay || !lay->keep_stats) CK(cudaMemsetAsync(c->d_stats, 0, sizeof(RunStats), s));
     CK(cudaEventRecord(c->staged, s));
-    c->run_start = start;
-    c->run_n = nn;
+    if (!lay) {
+        c->run_start = start;
+        c->run_n = nn;
+    }
     return GBMC_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-int gbmc_run_problems(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, void* stream) {
-    if (!c) return GBMC_ERR_INVALID_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
+// Launch one run (its graph, rebuilt when the launch parameters changed).
+int launch_run(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, cudaStream_t s,
+               const RunLayout* lay) {
     if (c->ran) {
         int rc0 = set_device(c);
         if (rc0) return rc0;
     }
     Params P;
     LaunchCfg L;
-    int rc = prepare_run(c, n_prob, probs, s, &P, &L);
+    int rc = prepare_run(c, n_prob, probs, s, &P, &L, lay);
     if (rc) return rc;
     if (!c->graph_valid || !same_params(P, c->graph_params) ||
         memcmp(&L, &c->graph_launch, sizeof L) != 0) {
@@ -1269,6 +1326,152 @@ int gbmc_run_problems(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, vo
     return GBMC_OK;
 }
 
+// The pointers a concurrent loop borrows from its context, cleared so that
+// destroying the loop frees only its own buffers.
+void release_borrowed(gbmc_ctx* l) {
+    l->d_grid_off = nullptr; l->d_iv64 = nullptr; l->d_e64 = nullptr; l->d_fabs = nullptr;
+    l->d_awr = nullptr; l->d_es32 = nullptr; l->d_fabs32 = nullptr; l->d_idx64 = nullptr;
+    l->d_desc64 = nullptr; l->d_desc32 = nullptr; l->d_bw32 = nullptr;
+    l->d_mat_off = nullptr; l->d_nuc_id = nullptr; l->d_density = nullptr;
+    l->d_density32 = nullptr; l->d_edges = nullptr; l->d_nu = nullptr; l->d_ffis = nullptr;
+    l->O = Outcomes{};
+    l->Y = Tallies{};
+    l->out_cap = 0;
+}
+
+void destroy_loop(gbmc_ctx* l) {
+    release_borrowed(l);
+    gbmc_destroy(l);
+}
+
+// A concurrent loop takes the context's tables, materials, tally definition,
+// tallies, outcomes and options (pointers and host copies; nothing is copied
+// on the device).
+void borrow_from(gbmc_ctx* l, const gbmc_ctx* c) {
+    l->opt = c->opt;
+    l->n_nuc = c->n_nuc; l->has64 = c->has64; l->has32 = c->has32;
+    l->h_grid_off = c->h_grid_off; l->h_gmin = c->h_gmin; l->h_gmax = c->h_gmax;
+    l->emin_all = c->emin_all; l->emax_all = c->emax_all;
+    l->d_grid_off = c->d_grid_off; l->d_iv64 = c->d_iv64; l->d_e64 = c->d_e64;
+    l->d_fabs = c->d_fabs; l->d_awr = c->d_awr; l->d_es32 = c->d_es32;
+    l->d_fabs32 = c->d_fabs32; l->d_idx64 = c->d_idx64;
+    l->d_desc64 = c->d_desc64; l->d_desc32 = c->d_desc32; l->d_bw32 = c->d_bw32;
+    l->n_mat = c->n_mat; l->h_mat_off = c->h_mat_off; l->h_nuc_id = c->h_nuc_id;
+    l->h_density = c->h_density; l->h_fabs = c->h_fabs; l->max_nuc_per_mat = c->max_nuc_per_mat;
+    l->d_mat_off = c->d_mat_off; l->d_nuc_id = c->d_nuc_id; l->d_density = c->d_density;
+    l->d_density32 = c->d_density32;
+    l->n_bins = c->n_bins; l->d_edges = c->d_edges;
+    l->d_nu = c->d_nu; l->d_ffis = c->d_ffis;
+    l->O = c->O; l->out_cap = c->out_cap;
+    l->Y = c->Y; l->rr_on = c->rr_on;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gbmc_run_problems(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, void* stream) {
+    if (!c) return GBMC_ERR_INVALID_ARG;
+    if (c->ran && c->last_loops > 0) {
+        // the previous call's loops write into this context's tallies and
+        // outcomes: let them finish before the buffers are reused
+        CK(cudaStreamSynchronize(c->last_stream));
+    }
+    int rc = launch_run(c, n_prob, probs, (cudaStream_t)stream, nullptr);
+    if (rc == GBMC_OK) c->last_loops = 0;
+    return rc;
+}
+
+int gbmc_run_concurrent(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, int32_t n_loops,
+                        int32_t per_run, void* stream) {
+    if (!c) return GBMC_ERR_INVALID_ARG;
+    if (c->borrowed) return fail(c, GBMC_ERR_UNSUPPORTED, "a concurrent loop runs no loops itself");
+    if (n_prob < 1 || !probs) return fail(c, GBMC_ERR_INVALID_ARG, "n_prob >= 1 and probs required");
+    if (n_loops < 1 || n_loops > kMaxLoops)
+        return fail(c, GBMC_ERR_INVALID_ARG, "n_loops must be in [1, %d]", kMaxLoops);
+    if (per_run < 1) return fail(c, GBMC_ERR_INVALID_ARG, "per_run must be at least 1");
+    if (!c->n_nuc || !c->n_mat || !c->n_bins)
+        return fail(c, GBMC_ERR_NOT_INITIALIZED, "tables, materials and tally must be set first");
+    if ((c->opt.precision == GBMC_FP64 && !c->has64) || (c->opt.precision == GBMC_FP32 && !c->has32))
+        return fail(c, GBMC_ERR_NOT_INITIALIZED, "tables not loaded in the selected precision");
+    if (c->ww_on || c->eig_on || c->imp_on)
+        return fail(c, GBMC_ERR_UNSUPPORTED,
+                    "weight windows, k-eigenvalue banking and importance recording run in one "
+                    "event loop (gbmc_run_problems)");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = set_device(c);
+    if (rc) return rc;
+    // every problem validated and laid out as gbmc_run_problems would
+    std::vector<int32_t> cells(n_prob);
+    std::vector<int64_t> start(n_prob), nn(n_prob);
+    int64_t total = 0;
+    for (int32_t p = 0; p < n_prob; ++p) {
+        if ((rc = check_geometry(c, probs[p].geom, p))) return rc;
+        if (probs[p].n_particles < 0 || probs[p].first_id < 0 ||
+            probs[p].first_id > std::numeric_limits<int64_t>::max() - probs[p].n_particles)
+            return fail(c, GBMC_ERR_INVALID_ARG, "problem %d: bad particle range", p);
+        if (probs[p].geom.source == GBMC_SRC_BANK)
+            return fail(c, GBMC_ERR_UNSUPPORTED, "problem %d: bank sources run in one event loop", p);
+        cells[p] = n_cells_of(probs[p].geom);
+        start[p] = total;
+        nn[p] = probs[p].n_particles;
+        total += probs[p].n_particles;
+        if (total > ((int64_t)1 << 40))
+            return fail(c, GBMC_ERR_INVALID_ARG, "more than 2^40 particles in one call");
+    }
+    if (c->ran) CK(cudaStreamSynchronize(c->last_stream));
+    if ((rc = ensure_outcomes(c, total > 0 ? total : 1))) return rc;
+    if ((rc = ensure_tallies(c, cells, s))) return rc;
+    while ((int32_t)c->loops.size() < n_loops) {
+        gbmc_ctx* l = nullptr;
+        if ((rc = gbmc_create(&l, c->device, &c->opt)))
+            return fail(c, rc, "concurrent loop: %s", gbmc_last_error(nullptr));
+        l->borrowed = true;
+        cudaError_t e = cudaStreamCreateWithFlags(&l->own_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&l->done_ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            gbmc_destroy(l);
+            return fail(c, GBMC_ERR_CUDA, "concurrent loop stream: %s", cudaGetErrorString(e));
+        }
+        c->loops.push_back(l);
+    }
+    for (int32_t j = 0; j < n_loops; ++j) borrow_from(c->loops[j], c);
+    c->run_start = start;
+    c->run_n = nn;
+    const int32_t n_runs = (n_prob + per_run - 1) / per_run;
+    const int32_t used = std::min(n_loops, n_runs);
+    CK(cudaEventRecord(c->ev0, s));
+    for (int32_t j = 0; j < used; ++j) CK(cudaStreamWaitEvent(c->loops[j]->own_stream, c->ev0, 0));
+    // runs of per_run consecutive problems, run r on loop r % n_loops,
+    // enqueued round by round so that every loop has work queued
+    std::vector<int64_t> fo(per_run), ob(per_run);
+    std::vector<int32_t> sl(per_run);
+    int erc = GBMC_OK;
+    for (int32_t r = 0; r < n_runs && erc == GBMC_OK; ++r) {
+        gbmc_ctx* l = c->loops[r % n_loops];
+        const int32_t p0 = r * per_run, np = std::min(per_run, n_prob - p0);
+        for (int32_t k = 0; k < np; ++k) {
+            fo[k] = c->slot_flux_off[p0 + k];
+            ob[k] = start[p0 + k];
+            sl[k] = p0 + k;
+        }
+        RunLayout lay{fo.data(), ob.data(), sl.data(), r >= n_loops};
+        erc = launch_run(l, np, probs + p0, l->own_stream, &lay);
+        if (erc) c->err = std::string("concurrent loop ") + std::to_string(r % n_loops) + ": " + l->err;
+    }
+    // join: `stream` waits for every loop (also after a failed launch, so
+    // that nothing a loop queued outlives the call unseen)
+    for (int32_t j = 0; j < used; ++j) {
+        CK(cudaEventRecord(c->loops[j]->done_ev, c->loops[j]->own_stream));
+        CK(cudaStreamWaitEvent(s, c->loops[j]->done_ev, 0));
+    }
+    CK(cudaEventRecord(c->ev1, s));
+    c->ran = true;
+    c->last_stream = s;
+    c->last_loops = used;
+    return erc;
+}
+
 int gbmc_profile_problems(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, void* stream,
                           gbmc_kernel_times* out, int32_t trace_cap, double* trace_ms,
                           int32_t* trace_queues, int32_t* trace_len) {
@@ -1281,6 +1484,7 @@ int gbmc_profile_problems(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs
     int rc = prepare_run(c, n_prob, probs, s, &P, &L);
     if (rc) return rc;
     P.use_cond = 0;
+    c->last_loops = 0;
     cudaEvent_t ev[kTimedKernels + 1];
     for (int k = 0; k <= kTimedKernels; ++k) CK(cudaEventCreate(&ev[k]));
     cudaError_t e = launch_init_run(P, L, s);
@@ -1579,16 +1783,17 @@ int gbmc_read_stats(gbmc_ctx* c, gbmc_stats* out) {
     memset(out, 0, sizeof *out);
     rc = read_ctl(c);
     if (rc && rc != GBMC_ERR_TIMEOUT && rc != GBMC_ERR_DEVICE_FLAG) return rc;
-    const Ctl& k = *c->h_ctl;
-    out->iterations = k.iter;
-    out->lookups = (int64_t)k.st_lookups;
-    out->micro_lookups = (int64_t)k.st_micro;
-    out->flights = (int64_t)k.st_flights;
-    out->crossings = (int64_t)k.st_cross;
-    out->collisions = (int64_t)k.st_coll;
-    out->histories = (int64_t)k.st_hist;
-    out->handoffs = (int64_t)k.st_handoff;
-    out->device_error = k.err;
+    const RunStats& k = *c->h_stats;
+    out->iterations = (int64_t)k.iterations;
+    out->lookups = (int64_t)k.lookups;
+    out->micro_lookups = (int64_t)k.micro;
+    out->flights = (int64_t)k.flights;
+    out->crossings = (int64_t)k.cross;
+    out->collisions = (int64_t)k.coll;
+    out->histories = (int64_t)k.hist;
+    out->handoffs = (int64_t)k.handoff;
+    out->device_error = rc == GBMC_ERR_TIMEOUT ? GBMC_ERR_TIMEOUT
+                      : rc == GBMC_ERR_DEVICE_FLAG ? GBMC_ERR_DEVICE_FLAG : 0;
     return rc;
 }
 

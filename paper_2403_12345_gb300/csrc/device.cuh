@@ -100,10 +100,12 @@ struct DevProblem {
     uint64_t seed, key_hi;
     int64_t first_id, n, start;   // start: index of its first particle in the run
     int64_t flux_off;             // offset of its flux tally
+    int64_t out_base;             // outcome index of its first particle
     int64_t plane_off;            // its plane table: walls (double)i * pitch, i = 0..n, then
                                   // lattice cell centres ((double)i + 0.5) * pitch, i < n
     double r2;                    // lattice pin radius squared (radius * radius)
-    int32_t n_cells, pad;
+    int32_t n_cells;
+    int32_t slot;                 // its tally slot (scalar tallies)
 };
 
 // One slot of the particle bank: a 128-byte, 128-byte-aligned record (array
@@ -120,7 +122,7 @@ struct alignas(128) Particle {
     double x, y, z, wgt;
     // sector 2
     double u, v, w;
-    int64_t gidx;        // index of the particle in the run (-1: a split copy)
+    int64_t gidx;        // outcome index of the history (-1: a split copy)
     // sector 3
     int32_t ci, cj;      // lattice cell (slab: layer in ci)
     int32_t ncoll, nflt; // collisions, flights so far
@@ -188,10 +190,18 @@ struct Ctl {
     int32_t M;                   // in-flight cap of this run (<= capacity)
     int32_t n_prob;
     int32_t done, err, iter, pad;
-    unsigned long long st_lookups, st_micro, st_flights, st_cross, st_coll, st_hist;
-    unsigned long long st_handoff;   // particles a drained ray-trace warp handed on
     double k_norm;               // k-eigenvalue: fission yield normalisation of this run
     int64_t bank_n, bank_total;  // source bank size, generation size (GBMC_SRC_BANK)
+};
+
+// Counters of the runs since they were last zeroed (one run, or every run
+// one event loop takes in a concurrent call), kept apart from the per-run
+// control block so that they can add up across runs.
+struct RunStats {
+    unsigned long long iterations, lookups, micro, flights, cross, coll, hist;
+    unsigned long long handoff;   // particles a drained ray-trace warp handed on
+    int32_t err;                  // the first error a run of them flagged (0: none)
+    int32_t pad;
 };
 
 constexpr int kSortBuckets = 1 << 16;
@@ -205,6 +215,7 @@ struct Params {
     Outcomes O;
     Tallies Y;
     Ctl* ctl;
+    RunStats* st;
     const DevProblem* probs;
     int32_t capacity;        // bank slots allocated
     int32_t precision;       // GBMC_FP64 / GBMC_FP32

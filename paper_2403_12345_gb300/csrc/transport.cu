@@ -88,17 +88,20 @@ __device__ __forceinline__ void lookup_append(const Params& P, int b, int32_t* c
 
 // ---------------------------------------------------------------- scalar tallies
 // Per-block accumulation of the scalar tallies in shared memory (one entry
-// per problem slot and tally kind), flushed with one global atomic per entry
-// at the end of the kernel; problem slots beyond the shared table go straight
-// to global memory.
+// per problem of the run and tally kind), flushed with one global atomic per
+// entry at the end of the kernel into the problem's tally slot; problems
+// beyond the shared table go straight to global memory.
 struct BlockScalars {
     double* w;
     unsigned long long* c;
+    const DevProblem* probs;
     int nslot;
 
-    __device__ __forceinline__ void init(double* sw, unsigned long long* sc, int n_prob) {
+    __device__ __forceinline__ void init(double* sw, unsigned long long* sc, int n_prob,
+                                         const DevProblem* pr) {
         w = sw;
         c = sc;
+        probs = pr;
         nslot = min(n_prob, kMaxSharedProblems);
         for (int e = threadIdx.x; e < nslot * GBMC_NSCAL; e += blockDim.x) {
             w[e] = 0.0;
@@ -136,16 +139,18 @@ struct BlockScalars {
             atomicAdd(&w[prob * GBMC_NSCAL + kind], s);
             atomicAdd(&c[prob * GBMC_NSCAL + kind], k);
         } else {
-            atomicAdd(&Y.weights[prob * GBMC_NSCAL + kind], s);
-            atomicAdd(&Y.counts[prob * GBMC_NSCAL + kind], k);
+            int64_t g = (int64_t)probs[prob].slot * GBMC_NSCAL + kind;
+            atomicAdd(&Y.weights[g], s);
+            atomicAdd(&Y.counts[g], k);
         }
     }
     __device__ __forceinline__ void flush(const Tallies& Y) {
         __syncthreads();
         for (int e = threadIdx.x; e < nslot * GBMC_NSCAL; e += blockDim.x) {
             if (c[e]) {
-                atomicAdd(&Y.weights[e], w[e]);
-                atomicAdd(&Y.counts[e], c[e]);
+                int64_t g = (int64_t)probs[e / GBMC_NSCAL].slot * GBMC_NSCAL + e % GBMC_NSCAL;
+                atomicAdd(&Y.weights[g], w[e]);
+                atomicAdd(&Y.counts[g], c[e]);
             }
         }
     }
@@ -155,7 +160,7 @@ struct BlockScalars {
     __shared__ double name##_w[kMaxSharedProblems * GBMC_NSCAL];                  \
     __shared__ unsigned long long name##_c[kMaxSharedProblems * GBMC_NSCAL];      \
     BlockScalars name;                                                            \
-    name.init(name##_w, name##_c, n_prob)
+    name.init(name##_w, name##_c, n_prob, P.probs)
 
 // Warp-uniform grid-stride loop: every lane of a warp runs the same number of
 // iterations (so warp collectives inside are safe); `valid` marks real items.
@@ -189,7 +194,7 @@ __global__ void k_plan(Params P) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     Ctl* c = P.ctl;
     // collisions of the previous iteration
-    c->st_coll += (unsigned long long)c->n_cq;
+    P.st->coll += (unsigned long long)c->n_cq;
     int cur = 1 - c->cur;
     c->cur = cur;
     c->n_lq[1 - cur] = 0;
@@ -213,13 +218,16 @@ __global__ void k_plan(Params P) {
     c->next += k;
     c->lq_base = c->n_lq[cur];
     c->n_lq[cur] += nc + k;
-    c->st_hist += (unsigned long long)k;
+    P.st->hist += (unsigned long long)k;
     int alive = c->M - c->n_free;
     int done = alive == 0;   // nothing in flight, no copy waiting, nothing left to birth
     c->iter += 1;
+    P.st->iterations += 1;
     c->tail = 0;
-    if (!done && !P.ww && c->next == c->total && alive <= P.tail_max) {
+    if (!done && !P.ww && !P.imp_mesh && c->next == c->total && alive <= P.tail_max) {
         // few particles left: the tail kernel after the loop finishes them
+        // (not while importance samples are recorded: only the collision
+        // event records them)
         c->tail = 1;
         done = 1;
     } else if (!done && c->iter > P.max_iter) {
@@ -244,7 +252,7 @@ __global__ void k_plan(Params P) {
     c->lookup_cursor = 0;
     c->sorted = (P.sort && c->lookup_n >= P.sort_min) ? 1 : 0;
     c->warp_lookup = c->lookup_n < P.warp_lookup_max ? 1 : 0;
-    c->st_lookups += (unsigned long long)c->lookup_n;
+    P.st->lookups += (unsigned long long)c->lookup_n;
     c->done = done;
     if (P.use_cond) cudaGraphSetConditional(P.cond, done ? 0u : 1u);
 }
@@ -344,7 +352,7 @@ __global__ void __launch_bounds__(256) k_source(Params P) {
             rec.prob = prob;
             rec.x = x; rec.y = y; rec.z = z; rec.wgt = 1.0;
             rec.u = u; rec.v = v; rec.w = w;
-            rec.gidx = gi;
+            rec.gidx = pr.out_base + (gi - pr.start);
             rec.ci = ci; rec.cj = cj;
             rec.rj = r.j;
             rec.inside = inside;
@@ -531,7 +539,7 @@ __global__ void __launch_bounds__(256, PREC == GBMC_FP64 ? 4 : 3) k_lookup(Param
         }
     }
     for (int o = 16; o > 0; o >>= 1) micro += __shfl_xor_sync(kFull, micro, o);
-    if ((threadIdx.x & 31) == 0 && micro) atomicAdd(&P.ctl->st_micro, micro);
+    if ((threadIdx.x & 31) == 0 && micro) atomicAdd(&P.st->micro, micro);
 }
 
 // Warp mode (short queues): one particle per warp.
@@ -563,7 +571,7 @@ __global__ void __launch_bounds__(256) k_lookup_warp(Params P) {
             micro += (unsigned long long)(__ldg(P.T.mat_off + m + 1) - __ldg(P.T.mat_off + m));
         }
     }
-    if (lane == 0 && micro) atomicAdd(&P.ctl->st_micro, micro);
+    if (lane == 0 && micro) atomicAdd(&P.st->micro, micro);
 }
 
 // ---------------------------------------------------------------- per-particle steps
@@ -1053,9 +1061,9 @@ __global__ void __launch_bounds__(256, 2) k_raytrace(Params P) {
         handoffs += __shfl_xor_sync(kFull, handoffs, o);
     }
     if (lane == 0 && nflights) {
-        atomicAdd(&c->st_cross, crossings);
-        atomicAdd(&c->st_flights, nflights);
-        if (handoffs) atomicAdd(&c->st_handoff, handoffs);
+        atomicAdd(&P.st->cross, crossings);
+        atomicAdd(&P.st->flights, nflights);
+        if (handoffs) atomicAdd(&P.st->handoff, handoffs);
     }
     sc.flush(P.Y);
 }
@@ -1132,6 +1140,9 @@ __global__ void __launch_bounds__(256, 2) k_collision(Params P) {
 template <int PREC>
 __global__ void __launch_bounds__(256) k_tail(Params P) {
     Ctl* c = P.ctl;
+    // after the loop: keep the loop's error in the counters, which outlive
+    // the run's control block
+    if (blockIdx.x == 0 && threadIdx.x == 0 && c->err) atomicCAS(&P.st->err, 0, c->err);
     if (!c->tail) return;
     int cur = c->cur;
     int32_t nl = c->n_lq[cur], na = c->n_aq[cur];
@@ -1203,7 +1214,7 @@ __global__ void __launch_bounds__(256) k_tail(Params P) {
             record_death(P, pt, status);
             flights += nf;
             colls += nc;
-            int b = pt.prob * GBMC_NSCAL;
+            int64_t b = (int64_t)pr.slot * GBMC_NSCAL;
             atomicAdd(&P.Y.weights[b + GBMC_S_FLIGHT], wf);
             atomicAdd(&P.Y.counts[b + GBMC_S_FLIGHT], nf);
             if (nc) {
@@ -1225,11 +1236,11 @@ __global__ void __launch_bounds__(256) k_tail(Params P) {
         }
     }
     if (lane == 0 && (lookups | flights)) {
-        atomicAdd(&c->st_lookups, lookups);
-        atomicAdd(&c->st_micro, micro);
-        atomicAdd(&c->st_flights, flights);
-        atomicAdd(&c->st_cross, crossings);
-        atomicAdd(&c->st_coll, colls);
+        atomicAdd(&P.st->lookups, lookups);
+        atomicAdd(&P.st->micro, micro);
+        atomicAdd(&P.st->flights, flights);
+        atomicAdd(&P.st->cross, crossings);
+        atomicAdd(&P.st->coll, colls);
     }
 }
 

@@ -41,7 +41,7 @@ EXPORTS = ["gbmc_default_options", "gbmc_create", "gbmc_destroy", "gbmc_last_err
            "gbmc_importance_accumulate", "gbmc_importance_training_set",
            "gbmc_get_weight_windows", "gbmc_set_reaction_tally", "gbmc_read_reaction_tally",
            "gbmc_load_fission", "gbmc_set_eigen", "gbmc_read_bank", "gbmc_set_source_bank",
-           "gbmc_check_division"]
+           "gbmc_check_division", "gbmc_run_concurrent"]
 MLP_HIDDEN = 64
 MLP_NPARAM = 4545
 NOALLOC_MAX_QUERIES = 1 << 20
@@ -122,6 +122,7 @@ def lib():
         L.gbmc_reset_tallies.argtypes = [vp, vp]
         L.gbmc_run_batch.argtypes = [vp, _P(Problem), vp]
         L.gbmc_run_problems.argtypes = [vp, C.c_int32, _P(Problem), vp]
+        L.gbmc_run_concurrent.argtypes = [vp, C.c_int32, _P(Problem), C.c_int32, C.c_int32, vp]
         L.gbmc_read_tallies.argtypes = [vp, C.c_int32, _P(C.c_double), C.c_int64,
                                         _P(C.c_int64), _P(C.c_double)]
         L.gbmc_set_reaction_tally.argtypes = [vp, C.c_int32]
@@ -385,6 +386,15 @@ class Context:
     def run_problems(self, probs, stream=None):
         arr = (Problem * len(probs))(*probs)
         self._ck(lib().gbmc_run_problems(self._h, len(probs), arr, _stream(stream)))
+        self._cells = [_n_cells(p.geom) for p in probs]
+
+    def run_concurrent(self, probs, n_loops: int, per_run: int = 1, stream=None):
+        """gbmc_run_concurrent: the results of run_problems(probs), computed by
+        n_loops concurrent event loops, each taking runs of per_run
+        consecutive problems in turn."""
+        arr = (Problem * len(probs))(*probs)
+        self._ck(lib().gbmc_run_concurrent(self._h, len(probs), arr, int(n_loops), int(per_run),
+                                           _stream(stream)))
         self._cells = [_n_cells(p.geom) for p in probs]
 
     def profile_problems(self, probs, stream=None, trace_cap: int = 0):

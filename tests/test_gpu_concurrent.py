@@ -1,0 +1,79 @@
+"""Concurrent event loops (gbmc_run_concurrent; Sec. 2, "GPU Streams")
+through the C ABI: every problem's outcomes and tallies are the oracle's, as
+with one event loop, whatever the number of loops and the problems per run;
+the counters add up over every run of the call."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from paper_2403_12345_gb300 import gbmc
+
+from gpu_helpers import assert_outcomes_equal, assert_tallies_close, gpu_problem, make_ctx
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("n_loops,per_run", [(2, 1), (3, 2), (4, 1), (1, 3)])
+def test_concurrent_loops_match_oracle_per_problem(n_loops, per_run):
+    p = synth.make_config(4, n_problems=7, grid_scale=0.02)
+    for k in range(7):
+        p.n_particles[k] = 1500 + 613 * k
+    ctx = make_ctx(p, (gbmc.FP32,), precision=gbmc.FP32)
+    try:
+        probs = [gpu_problem(p, geom_index=k, problem_index=k, batch=3) for k in range(7)]
+        ctx.run_concurrent(probs, n_loops=n_loops, per_run=per_run)
+        st = ctx.read_stats()
+        colls = flights = 0
+        for k in range(7):
+            ref = oracle.run(p, seed=p.seed, batch=3, geom_index=k, problem_index=k, precision=1)
+            out = ctx.read_outcomes(k, 0, p.n_particles[k])
+            assert_outcomes_equal(out, ref, label=f"problem {k}")
+            flux, counts, weights = ctx.read_tallies(k)
+            assert_tallies_close(dict(flux=flux, counts=counts, weights=weights), ref,
+                                 label=f"problem {k}")
+            colls += ref["counts"][oracle.S_COLLISION]
+            flights += ref["counts"][oracle.S_FLIGHT]
+        assert st["histories"] == sum(p.n_particles)
+        assert st["collisions"] == colls and st["flights"] == flights
+    finally:
+        ctx.close()
+
+
+def test_concurrent_batches_then_one_loop_again():
+    # batches of one lattice as separate problems on three loops, each batch
+    # tallied in its own slot; then an ordinary run on the same context
+    p = synth.make_config(2, grid_scale=0.03)
+    ctx = make_ctx(p)
+    try:
+        probs = [gpu_problem(p, n=9_001, batch=b) for b in range(5)]
+        ctx.run_concurrent(probs, n_loops=3)
+        for b in range(5):
+            ref = oracle.run(p, seed=p.seed, batch=b, n=9_001)
+            assert_outcomes_equal(ctx.read_outcomes(b, 0, 9_001), ref, label=f"batch {b}")
+            flux, counts, weights = ctx.read_tallies(b)
+            assert_tallies_close(dict(flux=flux, counts=counts, weights=weights), ref)
+        ctx.reset_tallies()
+        ctx.run_batch(gpu_problem(p, n=4_000, batch=9))
+        ref = oracle.run(p, seed=p.seed, batch=9, n=4_000)
+        assert_outcomes_equal(ctx.read_outcomes(0, 0, 4_000), ref, label="single loop after")
+        assert ctx.read_stats()["histories"] == 4_000
+    finally:
+        ctx.close()
+
+
+def test_concurrent_refuses_single_loop_features():
+    p = synth.make_tiny_problem(seed=37, n_nuc=3, n_points=(10, 50), kind=synth.GEOM_SLAB,
+                                n_particles=100)
+    ctx = make_ctx(p)
+    try:
+        ctx.set_weight_windows(np.full((p.geom.n_cells(), p.n_bins), 0.1))
+        with pytest.raises(gbmc.GbmcError) as ex:
+            ctx.run_concurrent([gpu_problem(p, n=100)], n_loops=2)
+        assert ex.value.code == gbmc.ERR_UNSUPPORTED
+        ctx.clear_weight_windows()
+        with pytest.raises(gbmc.GbmcError) as ex:
+            ctx.run_concurrent([gpu_problem(p, n=100)], n_loops=17)
+        assert ex.value.code == gbmc.ERR_INVALID_ARG
+    finally:
+        ctx.close()
