@@ -288,7 +288,7 @@ def fp32_vs_fp64_record(stream, local, steps=3):
 
 
 def stress_measure(prec, nq, steps, warmup, stream, local, seed_offset=0, e2e_steps=3,
-                   barrier=None):
+                   barrier=None, search=1):
     """Lookup-only stress set: lookups/s through gbmc_lookup_macro (the
     library's sort included), the lookup kernel alone on sorted queries
     (roofline), and end to end from pinned host memory."""
@@ -296,7 +296,7 @@ def stress_measure(prec, nq, steps, warmup, stream, local, seed_offset=0, e2e_st
     from paper_2403_12345_gb300 import gbmc
     prob, E, mat = synth.make_stress_lookup(n_queries=nq, seed_offset=seed_offset)
     micro_per = int(prob.mat_off[1] - prob.mat_off[0])
-    ctx = gbmc.Context(local, precision=prec)
+    ctx = gbmc.Context(local, precision=prec, search=search)
     ctx.load(prob, (prec,))
     dE = torch.from_numpy(E).cuda()
     dm = torch.from_numpy(mat).cuda()
@@ -491,78 +491,6 @@ def run_stress(args, rank, world, local):
         dist.destroy_process_group()
 
 
-def run_streams(args, prob, rank, world, local):
-    """K independent event loops on K concurrent CUDA streams (the paper's
-    several ranks per GPU, Sec. 2 "GPU Streams"): each context runs a share
-    of the step's work -- whole problems balanced by size, or for a single
-    problem an id range -- and a step ends when all K have finished."""
-    import torch
-    import torch.distributed as dist
-    from paper_2403_12345_gb300 import gbmc, replicas
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl")
-    K = args.streams
-    opts = dict(precision=args.precision, sort=args.sort)
-    if args.max_in_flight:
-        opts["max_in_flight"] = args.max_in_flight
-    if args.blocks_per_sm:
-        opts["blocks_per_sm"] = args.blocks_per_sm
-    ctxs = [gbmc.Context(local, **opts) for _ in range(K)]
-    for c in ctxs:
-        c.load(prob, (args.precision,))
-    geoms = [gbmc.geometry_from(g) for g in prob.geoms]
-    counts = [args.particles or n for n in prob.n_particles]
-    by = "ids" if len(geoms) == 1 else "problems"
-
-    def shares(batch):
-        probs = [gbmc.problem(geoms[k], prob.seed, counts[k], batch=batch * world + rank,
-                              problem_index=k) for k in range(len(geoms))]
-        return [replicas.shard_problems(probs, r, K, by=by)[0] for r in range(K)]
-
-    streams = [torch.cuda.Stream() for _ in range(K)]
-    main = torch.cuda.current_stream()
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-
-    def step(batch):
-        go = torch.cuda.Event()
-        go.record(main)
-        done = []
-        for c, st, sh in zip(ctxs, streams, shares(batch)):
-            st.wait_event(go)
-            if sh:
-                c.run_problems(sh, st)
-            e = torch.cuda.Event()
-            e.record(st)
-            done.append(e)
-        for e in done:
-            main.wait_event(e)
-
-    for w in range(args.warmup):
-        step(10_000 + w)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    ms, clocks = _timed(step, args.steps, flush, main, local)
-    tot_ms = _max_over_ranks(sum(ms), world)
-    npart = sum(counts)
-    value = npart * args.steps * world / (tot_ms * 1e-3)
-    if rank == 0:
-        cfg = config_of(args, prob)
-        cfg["parallelism"] = f"replicas{args.gpus} x {K} concurrent event loops ({by} split)"
-        print(json.dumps({
-            "metric": "particles/s", "value": value, "unit": "particles/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.precision == 1 else "f64", "data": "synthetic", "config": cfg,
-            "streams": K, "e2e": None, "roofline": None, "cpu_baseline": None, "clocks": clocks,
-            "gpu_launches": None}), flush=True)
-    for c in ctxs:
-        c.close()
-    if world > 1:
-        dist.destroy_process_group()
-
-
 def run_eigen(args, prob, rank, world, local):
     """k-eigenvalue power iteration: `warmup` inactive generations (the first
     from the box source), then `steps` timed active generations, each from the
@@ -737,12 +665,11 @@ def main():
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
     ap.add_argument("--ref-step-s", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--streams", type=int, default=1,
-                    help="K > 1: K independent event loops (contexts) on K concurrent streams, "
-                         "the work split between them, instead of one batched launch")
     ap.add_argument("--autotune", type=int, default=-1,
                     help="1: autotune launch settings before timing, 0: defaults "
                          "(default: autotune configs 2-4)")
+    ap.add_argument("--search", type=int, default=1,
+                    help="grid search: 1 coarse index (default), -1 plain binary search")
     ap.add_argument("--loops", type=int, default=0,
                     help="concurrent event loops over the steps' batches (gbmc_run_concurrent); "
                          "0: the fastest of 1-4 in a short trial after autotuning")
@@ -794,9 +721,6 @@ def main():
     if args.config == 5:
         run_windows(args, prob, rank, world, local)
         return
-    if args.streams > 1:
-        run_streams(args, prob, rank, world, local)
-        return
 
     import torch
     import torch.distributed as dist
@@ -807,7 +731,7 @@ def main():
         dist.init_process_group("nccl")
     stream = torch.cuda.current_stream()
 
-    opts = dict(precision=args.precision, sort=args.sort)
+    opts = dict(precision=args.precision, sort=args.sort, search=args.search)
     if args.max_in_flight:
         opts["max_in_flight"] = args.max_in_flight
     if args.blocks_per_sm:
@@ -842,7 +766,7 @@ def main():
     # loops, each also at 4 blocks per SM, picks the fastest (a candidate must
     # beat one loop by 2%)
     loops, loop_trials = max(args.loops, 1), None
-    if args.loops == 0 and args.config in (2, 3, 4) and args.streams == 1:
+    if args.loops == 0 and args.config in (2, 3, 4):
         loop_trials = {}
         tuned_bps = ctx.options.blocks_per_sm
         best = None
@@ -969,7 +893,7 @@ def main():
     lk_bytes = pst["micro_lookups"] * BRACKET_BYTES[args.precision] + pst["lookups"] * LOOKUP_IO_BYTES
     lk_gbs = lk_bytes / (lk_ms * 1e-3) / 1e9
     stock = (args.particles == 0 and args.max_in_flight == 0 and args.blocks_per_sm == 0
-             and args.sort == 1 and args.streams == 1)
+             and args.sort == 1 and args.search == 1)
     tr = recorded_traffic(args.config, args.precision, ctx.options.wide_windows) if stock else None
     l2_size = torch.cuda.get_device_properties(local).L2_cache_size
     roof = {"kernel": "lookup", "bound": "hbm", "achieved": lk_gbs, "peak": hbm, "unit": "GB/s",
@@ -994,10 +918,22 @@ def main():
     run_bps = int(ctx.options.blocks_per_sm)
     extras = {}
     if rank == 0 and args.config == 2 and stock and not args.no_extras:
+        # the coarse index against a plain binary search of each grid, on the
+        # lookup kernel of one eager batch each (same histories, same results)
+        ctx.set_options(search=-1)
+        kp = ctx.profile_problems(problems(30_000), stream)
+        ctx.set_options(search=1)
+        ki = ctx.profile_problems(problems(30_000), stream)
+        search_cmp = {"lattice17_fp64_lookup_ms_per_batch": {"index": ki["lookup"][0],
+                                                             "plain": kp["lookup"][0]}}
         ctx.close()
         ctx = None
         extras["fp32_vs_fp64"] = fp32_vs_fp64_record(stream, local)
         m = stress_measure(1, 10_000_000, args.steps, args.warmup, stream, local)
+        mp = stress_measure(1, 10_000_000, 3, 1, stream, local, e2e_steps=1, search=-1)
+        search_cmp["stress_fp32_lookup_kernel_ms"] = {
+            "index": m["roofline"]["avg_launch_ms"], "plain": mp["roofline"]["avg_launch_ms"]}
+        extras["search_comparison"] = search_cmp
         extras["lookup_stress_fp32"] = {
             "workload": m["prob"].name, "description": WORKLOADS[6],
             "lookups_per_s": 10_000_000 * args.steps / (sum(m["ms"]) * 1e-3),

@@ -115,7 +115,15 @@ typedef struct {
                                 of a warp read distinct windows (tables far beyond
                                 L2, sparse particles), more registers otherwise.
                                 Same results either way. */
-    int32_t reserved[4];
+    int32_t search;          /* bracket search of the energy grids: 1 (default) a
+                                coarse index over each grid's bit patterns (binary64:
+                                about one point a bucket, then at most about one
+                                bisection step; binary32: a bucket window of the
+                                bracket's pairs), the "double indexing" of the codes
+                                the paper compares against (Sec. 3); -1 a plain
+                                binary search of each whole grid.  Same results
+                                either way (the bracket is unique). */
+    int32_t reserved[3];
 } gbmc_options;
 
 /* One geometry (and its source).  Fields of other kinds are ignored. */

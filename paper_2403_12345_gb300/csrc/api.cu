@@ -247,6 +247,7 @@ void fill_defaults(gbmc_options* o) {
     if (o->warp_lookup_max < 0) o->warp_lookup_max = 0;   // never
     if (o->tail_max == 0) o->tail_max = 4096;
     if (o->tail_max < 0) o->tail_max = 0;                 // never
+    if (o->search == 0) o->search = 1;
 }
 
 int check_options(gbmc_ctx* c, const gbmc_options* o) {
@@ -254,6 +255,8 @@ int check_options(gbmc_ctx* c, const gbmc_options* o) {
         return fail(c, GBMC_ERR_INVALID_ARG, "precision must be GBMC_FP64 or GBMC_FP32");
     if (o->wide_windows != 0 && o->wide_windows != 1)
         return fail(c, GBMC_ERR_INVALID_ARG, "wide_windows must be 0 or 1");
+    if (o->search != 1 && o->search != -1)
+        return fail(c, GBMC_ERR_INVALID_ARG, "search must be 1 (coarse index) or -1 (plain)");
     if (o->block_lookup != 256 || o->block_event != 256)
         return fail(c, GBMC_ERR_UNSUPPORTED, "block sizes other than 256 are not built");
     if (o->blocks_per_sm > 32)
@@ -452,6 +455,7 @@ void sort_params(const gbmc_ctx* c, Params& P) {
 Params make_params(gbmc_ctx* c) {
     Params P{};
     P.T = make_tables(c);
+    P.T.plain = c->opt.search < 0 ? 1 : 0;
     P.B = c->B;
     P.Q = c->Q;
     P.O = c->O;

@@ -91,7 +91,8 @@ struct Tables {
     const double* edges;       // [n_bins+1] tally energy edges
     const double* nu;          // [n_nuc] mean neutrons per fission (k-eigenvalue)
     const double* f_fis;       // [n_nuc] sigma_f / sigma_t
-    int32_t n_nuc, n_mat, n_bins, pad;
+    int32_t n_nuc, n_mat, n_bins;
+    int32_t plain;             // 1: plain binary search of each grid (no coarse index, no windows)
 };
 
 // One problem of a run, as the kernels see it.
@@ -569,8 +570,8 @@ __device__ __forceinline__ double interp64(const Tables& T, int64_t k, double E)
 __device__ __forceinline__ double micro64(const Tables& T, int32_t q, double E) {
     Desc64 d = load_desc64(T.d64 + q);
     unsigned long long eb = (unsigned long long)__double_as_longlong(E);
-    int32_t lo, hi;
-    coarse_range(d, T.idx64, eb, lo, hi);
+    int32_t lo = 0, hi = d.n - 1;
+    if (!T.plain) coarse_range(d, T.idx64, eb, lo, hi);
     const unsigned long long* g = reinterpret_cast<const unsigned long long*>(T.e64 + d.off);
     return interp64(T, d.off + bracket_in(g, lo, hi, eb), E);
 }
@@ -629,6 +630,22 @@ __device__ __forceinline__ void load_window(const float4* p, float4* q) {
     }
 }
 
+// The bracket's end points (its pair and the next) by bisection of the
+// grid's pairs within [lo, hi].
+__device__ __forceinline__ void bracket32_bisect(const Tables& T, const Desc32& d, int32_t lo,
+                                                 int32_t hi, uint32_t eb, float2& p0, float2& p1) {
+    const float2* g = T.es32 + d.off;
+    while (hi - lo > 1) {
+        int32_t mid = (lo + hi) >> 1;
+        if (__float_as_uint(__ldg(&g[mid].x)) <= eb)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    p0 = __ldg(g + lo);
+    p1 = __ldg(g + lo + 1);
+}
+
 // The bracket's end points (its pair and the next) from the window w loaded
 // from p.
 __device__ __forceinline__ void bracket32(const Tables& T, const Desc32& d, const float4* p,
@@ -650,27 +667,22 @@ __device__ __forceinline__ void bracket32(const Tables& T, const Desc32& d, cons
         p1 = __ldg(pp + 1);
         return;
     }
-    const float2* g = T.es32 + d.off;
-    while (hi - lo > 1) {
-        int32_t mid = (lo + hi) >> 1;
-        if (__float_as_uint(__ldg(&g[mid].x)) <= eb)
-            lo = mid;
-        else
-            hi = mid;
-    }
-    p0 = __ldg(g + lo);
-    p1 = __ldg(g + lo + 1);
+    bracket32_bisect(T, d, lo, hi, eb, p0, p1);
 }
 
 // Micro cross section of material entry q (binary32) at E.
 __device__ __forceinline__ float micro32(const Tables& T, int32_t q, double E) {
     Desc32 d = load_desc32(T.d32 + q);
     uint32_t eb = (uint32_t)__float_as_int(__double2float_rd(E));
-    const float4* p = window_of(T, d, eb);
-    float4 w[4];
-    load_window(p, w);
     float2 p0, p1;
-    bracket32(T, d, p, w, eb, p0, p1);
+    if (T.plain) {
+        bracket32_bisect(T, d, 0, d.n - 1, eb, p0, p1);
+    } else {
+        const float4* p = window_of(T, d, eb);
+        float4 w[4];
+        load_window(p, w);
+        bracket32(T, d, p, w, eb, p0, p1);
+    }
     float Ef = __double2float_rn(E);
     float f = (Ef - p0.x) / (p1.x - p0.x);
     return p0.y + f * (p1.y - p0.y);
@@ -702,7 +714,8 @@ __device__ __forceinline__ void brackets(const Tables& T, const Desc64* dq, cons
         if (q + u < q1) {
             Desc64 d = load_desc64(dq + q + u);
             gp[u] = g + d.off;
-            coarse_range(d, idx, eb, lo[u], hi[u]);
+            hi[u] = d.n - 1;
+            if (!T.plain) coarse_range(d, idx, eb, lo[u], hi[u]);
         }
     }
     bool more = true;
@@ -850,8 +863,8 @@ __device__ __forceinline__ void macro64_tile(const Tables& T, int32_t m, int nv,
                 // the held bracket is E's if it is the largest j <= n-2 with E_j <= E
                 const bool hit = k >= 0 && (eb >= elo || k == 0) && (eb < ehi || k == d.n - 2);
                 if (!hit) {
-                    int32_t lo, hi;
-                    coarse_range(d, T.idx64, eb, lo, hi);
+                    int32_t lo = 0, hi = d.n - 1;
+                    if (!T.plain) coarse_range(d, T.idx64, eb, lo, hi);
                     k = bracket_in(gg, lo, hi, eb);
                     elo = __ldg(gg + k);
                     ehi = __ldg(gg + k + 1);
@@ -894,18 +907,47 @@ __device__ __forceinline__ void macro32(const Tables& T, int32_t m, double E, do
     float4 pend = make_float4(0.0f, 0.0f, 0.0f, 0.0f);   // checkpoints not yet stored
     for (int32_t q = q0; q < q1; q += kIlp32) {
         Desc32 d[kIlp32];
-        const float4* pw[kIlp32];
 #pragma unroll
-        for (int u = 0; u < kIlp32; ++u) {
-            d[u] = load_desc32(T.d32 + (q + u < q1 ? q + u : q));
-            pw[u] = window_of(T, d[u], eb);
-        }
-        float4 w[kIlp32][4];
-#pragma unroll
-        for (int u = 0; u < kIlp32; ++u) load_window<WIDE>(pw[u], w[u]);
+        for (int u = 0; u < kIlp32; ++u) d[u] = load_desc32(T.d32 + (q + u < q1 ? q + u : q));
         float2 p0[kIlp32], p1[kIlp32];
+        if (T.plain) {
+            // plain binary search of each grid, the group's searches in lock step
+            int32_t lo[kIlp32], hi[kIlp32];
 #pragma unroll
-        for (int u = 0; u < kIlp32; ++u) bracket32(T, d[u], pw[u], w[u], eb, p0[u], p1[u]);
+            for (int u = 0; u < kIlp32; ++u) {
+                lo[u] = 0;
+                hi[u] = d[u].n - 1;
+            }
+            bool more = true;
+            while (more) {
+                more = false;
+#pragma unroll
+                for (int u = 0; u < kIlp32; ++u) {
+                    if (hi[u] - lo[u] > 1) {
+                        int32_t mid = (lo[u] + hi[u]) >> 1;
+                        if (__float_as_uint(__ldg(&T.es32[d[u].off + mid].x)) <= eb)
+                            lo[u] = mid;
+                        else
+                            hi[u] = mid;
+                        more = true;
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kIlp32; ++u) {
+                p0[u] = __ldg(T.es32 + d[u].off + lo[u]);
+                p1[u] = __ldg(T.es32 + d[u].off + lo[u] + 1);
+            }
+        } else {
+            const float4* pw[kIlp32];
+#pragma unroll
+            for (int u = 0; u < kIlp32; ++u) pw[u] = window_of(T, d[u], eb);
+            float4 w[kIlp32][4];
+#pragma unroll
+            for (int u = 0; u < kIlp32; ++u) load_window<WIDE>(pw[u], w[u]);
+#pragma unroll
+            for (int u = 0; u < kIlp32; ++u) bracket32(T, d[u], pw[u], w[u], eb, p0[u], p1[u]);
+        }
         float run[kIlp32];
 #pragma unroll
         for (int u = 0; u < kIlp32; ++u) {

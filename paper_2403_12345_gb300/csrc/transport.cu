@@ -604,12 +604,54 @@ __device__ __forceinline__ int32_t cell_of(const gbmc_geometry& g, const Particl
 // Track-length scores of a segment of length d in the particle's (cell,
 // energy bin): flux w d and, when on, the absorption rate (w d) Sigma_a.
 // ebin = energy_bin(P.T, pt.E), which the caller keeps while E is unchanged.
-__device__ __forceinline__ void score_segment(const Params& P, const DevProblem& pr,
-                                              const Particle& pt, double d, int32_t ebin) {
-    int64_t k = pr.flux_off + (int64_t)cell_of(pr.g, pt) * P.T.n_bins + ebin;
-    double wd = pt.wgt * d;
-    atomicAdd(&P.Y.flux[k], wd);
-    if (P.Y.absrate) atomicAdd(&P.Y.absrate[k], wd * pt.sa);
+struct Score {
+    int64_t k;     // tally bin (-1: nothing to score)
+    double wd, wa; // w d and (w d) Sigma_a
+};
+
+__device__ __forceinline__ Score segment_score(const Params& P, const DevProblem& pr,
+                                               const Particle& pt, double d, int32_t ebin) {
+    Score s;
+    s.k = pr.flux_off + (int64_t)cell_of(pr.g, pt) * P.T.n_bins + ebin;
+    s.wd = pt.wgt * d;
+    s.wa = P.Y.absrate ? s.wd * pt.sa : 0.0;
+    return s;
+}
+
+// One lane's score, added on its own (the tail kernel's single-lane steps).
+__device__ __forceinline__ void score_now(const Params& P, const Score& s) {
+    if (s.k < 0) return;
+    atomicAdd(&P.Y.flux[s.k], s.wd);
+    if (P.Y.absrate) atomicAdd(&P.Y.absrate[s.k], s.wa);
+}
+
+// Warp-aggregated tally add (all 32 lanes call): lanes that score the same
+// bin are grouped with __match_any_sync; the group's lowest lane gathers the
+// others' values in lane order and issues one atomic for the group.  Lanes
+// scoring distinct bins (the common case when cells differ) pay only the
+// match.
+__device__ __forceinline__ void tally_add_warp(double* t, int64_t k, double v, bool pred) {
+    if (__ballot_sync(kFull, pred) == 0) return;
+    const int lane = threadIdx.x & 31;
+    const unsigned peers = __match_any_sync(kFull, pred ? (unsigned long long)k : ~0ull);
+    const int leader = __ffs(peers) - 1;
+    unsigned rest = (pred && lane == leader) ? (peers & ~(1u << lane)) : 0u;
+    double s = v;
+    while (__any_sync(kFull, rest != 0u)) {
+        const int src = rest ? __ffs(rest) - 1 : lane;
+        const double o = __shfl_sync(kFull, v, src);
+        if (rest) {
+            s += o;
+            rest &= rest - 1u;
+        }
+    }
+    if (pred && lane == leader) atomicAdd(t + k, s);
+}
+
+__device__ __forceinline__ void score_warp(const Params& P, const Score& s) {
+    const bool pred = s.k >= 0;
+    tally_add_warp(P.Y.flux, s.k, s.wd, pred);
+    if (P.Y.absrate) tally_add_warp(P.Y.absrate, s.k, s.wa, pred);
 }
 
 // One flight (advance event): sample the distance to collision, find the
@@ -619,12 +661,13 @@ __device__ __forceinline__ void score_segment(const Params& P, const DevProblem&
 // Returns true for a collision, leaving the particle where it is: the move
 // by -ln(xi) / Sigma_t and its track-length score are finish_flight's, run
 // by the collision event, where every lane of a warp needs that logarithm.
-// Otherwise the particle moves to pt.surf and scores w d in the (cell,
-// energy bin) flux tally.  The candidates are screened by their binary32
+// Otherwise the particle moves to pt.surf and its track-length score (w d
+// in its cell and energy bin) is returned in seg for the caller to add.  The candidates are screened by their binary32
 // spans: a surface decided by its span alone costs one binary64 quotient,
 // taken by all such lanes of a warp together.
 __device__ __forceinline__ bool fly(const Params& P, const DevProblem& pr, Particle& pt,
-                                    Stream& r, double& xi, double a_uv, int32_t ebin) {
+                                    Stream& r, double& xi, double a_uv, int32_t ebin,
+                                    Score& seg) {
     const gbmc_geometry& g = pr.g;
     xi = r.next();
     pt.nflt = pt.nflt + 1;
@@ -705,20 +748,20 @@ __device__ __forceinline__ bool fly(const Params& P, const DevProblem& pr, Parti
         pt.x = pt.x + dbnd * pt.u;
         pt.y = pt.y + dbnd * pt.v;
         pt.z = pt.z + dbnd * pt.w;
-        score_segment(P, pr, pt, dbnd, ebin);
+        seg = segment_score(P, pr, pt, dbnd, ebin);
     }
     return collide;
 }
 
 // The end of a flight that reached its collision site: d = -ln(xi) /
-// Sigma_t, the move and the track-length score.
-__device__ __forceinline__ void finish_flight(const Params& P, const DevProblem& pr, Particle& pt,
-                                              double xi) {
+// Sigma_t, the move, and the track-length score (returned to be added).
+__device__ __forceinline__ Score finish_flight(const Params& P, const DevProblem& pr, Particle& pt,
+                                               double xi) {
     double d = (0.0 - ln_series(xi)) / pt.st;
     pt.x = pt.x + d * pt.u;
     pt.y = pt.y + d * pt.v;
     pt.z = pt.z + d * pt.w;
-    score_segment(P, pr, pt, d, energy_bin(P.T, pt.E));
+    return segment_score(P, pr, pt, d, energy_bin(P.T, pt.E));
 }
 
 // Weight-window check at the particle's (cell, energy bin), problem slot 0
@@ -992,6 +1035,7 @@ __global__ void __launch_bounds__(256, 2) k_raytrace(Params P) {
         int status = 0, route = 0;   // route 1: collision, 2: lookup, 3: next iteration
         bool fin = false;
         WwOut wo{0, 0.0, 0.0};
+        Score sg{-1, 0.0, 0.0};
         if (have && drain && flights > 0) {
             route = 3;
             fin = true;
@@ -1001,7 +1045,7 @@ __global__ void __launch_bounds__(256, 2) k_raytrace(Params P) {
         } else if (have) {
             const DevProblem& pr = P.probs[pt.prob];
             double xi;
-            bool col = fly(P, pr, pt, r, xi, a_uv, ebin);
+            bool col = fly(P, pr, pt, r, xi, a_uv, ebin, sg);
             ++flights;
             fw += pt.wgt;
             if (col) {
@@ -1024,6 +1068,7 @@ __global__ void __launch_bounds__(256, 2) k_raytrace(Params P) {
                 nflights += (unsigned long long)flights;
             }
         }
+        score_warp(P, sg);
         if (P.ww && __any_sync(kFull, wo.copies > 0 || wo.roulette_w > 0.0)) {
             int pw = have ? pt.prob : 0;
             sc.add(P.Y, wo.copies > 0, pw, GBMC_S_SPLIT, wo.copy_w, (unsigned long long)wo.copies);
@@ -1085,6 +1130,7 @@ __global__ void __launch_bounds__(256, 2) k_collision(Params P) {
         double E1 = 0.0;   // energy and material after the collision (the next lookup's)
         int32_t m1 = 0;
         WwOut wo{0, 0.0, 0.0};
+        Score sg{-1, 0.0, 0.0};
         if (valid) {
             slot = P.Q.cq[idx];
             Particle pt = P.B.p[slot];
@@ -1107,13 +1153,14 @@ __global__ void __launch_bounds__(256, 2) k_collision(Params P) {
             // the flight's distance draw is the stream's last one
             Stream r;
             r.init(pr.seed, pr.key_hi, pt.hid, pt.rj - 1u);
-            finish_flight(P, pr, pt, r.next());
+            sg = finish_flight(P, pr, pt, r.next());
             status = collide<PREC>(P, pr, pt, slot, r, wo);
             P.B.p[slot] = pt;
             if (status) record_death(P, pt, status);
             E1 = pt.E;
             m1 = pt.mat;
         }
+        score_warp(P, sg);
         bool dead = valid && status != 0;
         if (P.ww) {
             sc.add(P.Y, wo.copies > 0, prob, GBMC_S_SPLIT, wo.copy_w, (unsigned long long)wo.copies);
@@ -1184,13 +1231,16 @@ __global__ void __launch_bounds__(256) k_tail(Params P) {
             __syncwarp();     // the lanes' running-sum checkpoints, visible to lane 0
             if (lane == 0) {
                 double xi;
-                bool col = fly(P, pr, pt, r, xi, pt.u * pt.u + pt.v * pt.v, energy_bin(P.T, pt.E));
+                Score sg{-1, 0.0, 0.0};
+                bool col = fly(P, pr, pt, r, xi, pt.u * pt.u + pt.v * pt.v, energy_bin(P.T, pt.E),
+                               sg);
+                score_now(P, sg);
                 ++nf;
                 wf += pt.wgt;
                 if (col) {
                     ++nc;
                     wc += pt.wgt;
-                    finish_flight(P, pr, pt, xi);
+                    score_now(P, finish_flight(P, pr, pt, xi));
                     WwOut wo{0, 0.0, 0.0};
                     status = collide<PREC>(P, pr, pt, slot, r, wo);
                     action = status ? 2 : 1;

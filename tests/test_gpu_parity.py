@@ -239,9 +239,10 @@ def _edge_energies(prob, mat):
     return np.ascontiguousarray(E[E > 0.0])
 
 
+@pytest.mark.parametrize("search", [1, -1])
 @pytest.mark.parametrize("precision", [gbmc.FP64, gbmc.FP32])
 @pytest.mark.parametrize("which", ["dense", "sparse"])
-def test_lookup_macro_at_grid_points_and_edges(precision, which):
+def test_lookup_macro_at_grid_points_and_edges(precision, which, search):
     """Exact hits (E - E_k = 0), neighbours, extrapolation outside the grids;
     dense grids take the integer-unit interpolation, the sparse ones (2-9
     points over 12 decades: intervals wider than 2^10) its binary64 fallback."""
@@ -251,7 +252,7 @@ def test_lookup_macro_at_grid_points_and_edges(precision, which):
     else:
         prob = synth.make_tiny_problem(seed=11, n_nuc=6, n_points=(2, 9))
     E = _edge_energies(prob, 0)
-    ctx = make_ctx(prob, (precision,))
+    ctx = make_ctx(prob, (precision,), search=search)
     try:
         dE = torch.tensor(E, device="cuda")
         dm = torch.zeros(len(E), dtype=torch.int32, device="cuda")
@@ -362,3 +363,20 @@ def test_sorted_thread_lookups_every_group_size(sizes, reaction):
         assert_tallies_close(dict(flux=ar, counts=ref["counts"], weights=ref["weights"]),
                              dict(flux=ref["absrate"], counts=ref["counts"],
                                   weights=ref["weights"]))
+
+
+@pytest.mark.parametrize("precision", [gbmc.FP64, gbmc.FP32])
+@pytest.mark.parametrize("wmax", [-1, 1 << 30])
+def test_plain_binary_search_transport_matches_oracle(precision, wmax):
+    """The plain binary search of each grid (search = -1, no coarse index
+    and no bucket windows) finds the same brackets: sorted thread-mode
+    lookups (the binary64 tile included) and warp-mode ones."""
+    p = synth.make_config(2, grid_scale=0.05)
+    ctx = make_ctx(p, (precision,), precision=precision, search=-1, warp_lookup_max=wmax)
+    try:
+        g = run_gpu(ctx, gpu_problem(p, n=30_011, batch=6))
+    finally:
+        ctx.close()
+    ref = oracle.run(p, seed=p.seed, batch=6, n=30_011, precision=precision)
+    assert_outcomes_equal(g, ref, label=f"plain search, warp_lookup_max {wmax}")
+    assert_tallies_close(g, ref)
