@@ -625,27 +625,29 @@ __device__ __forceinline__ void score_now(const Params& P, const Score& s) {
     if (P.Y.absrate) atomicAdd(&P.Y.absrate[s.k], s.wa);
 }
 
-// Warp-aggregated tally add (all 32 lanes call): lanes that score the same
-// bin are grouped with __match_any_sync; the group's lowest lane gathers the
-// others' values in lane order and issues one atomic for the group.  Lanes
-// scoring distinct bins (the common case when cells differ) pay only the
-// match.
+// Warp-aggregated tally add (all 32 lanes call; lanes with pred add v into
+// t[k]).  When every scoring lane of the warp scores the same bin (one cell
+// and energy bin: an infinite medium, a slab layer, a sorted queue in one
+// cell) the warp sums the values and one lane issues one atomic; otherwise
+// each lane adds its own.  Used by the collision kernel, which scores the
+// flights that end in a collision (in an infinite medium the whole warp
+// shares a bin: config 1's collision kernel 1.08 -> 0.61 ms per batch); the
+// ray trace's surface flights, in lattice cells that rarely coincide, add
+// per lane (aggregating them cost 4-5% there, also when lanes were grouped
+// by __match_any_sync).
 __device__ __forceinline__ void tally_add_warp(double* t, int64_t k, double v, bool pred) {
-    if (__ballot_sync(kFull, pred) == 0) return;
-    const int lane = threadIdx.x & 31;
-    const unsigned peers = __match_any_sync(kFull, pred ? (unsigned long long)k : ~0ull);
-    const int leader = __ffs(peers) - 1;
-    unsigned rest = (pred && lane == leader) ? (peers & ~(1u << lane)) : 0u;
-    double s = v;
-    while (__any_sync(kFull, rest != 0u)) {
-        const int src = rest ? __ffs(rest) - 1 : lane;
-        const double o = __shfl_sync(kFull, v, src);
-        if (rest) {
-            s += o;
-            rest &= rest - 1u;
-        }
+    const unsigned m = __ballot_sync(kFull, pred);
+    if (m == 0u) return;
+    const int leader = __ffs(m) - 1;
+    const long long k0 = __shfl_sync(kFull, (long long)k, leader);
+    if (__all_sync(kFull, !pred || k == k0)) {
+        double s = pred ? v : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+        if ((int)(threadIdx.x & 31) == leader) atomicAdd(t + k0, s);
+    } else if (pred) {
+        atomicAdd(t + k, v);
     }
-    if (pred && lane == leader) atomicAdd(t + k, s);
 }
 
 __device__ __forceinline__ void score_warp(const Params& P, const Score& s) {
@@ -1035,7 +1037,6 @@ __global__ void __launch_bounds__(256, 2) k_raytrace(Params P) {
         int status = 0, route = 0;   // route 1: collision, 2: lookup, 3: next iteration
         bool fin = false;
         WwOut wo{0, 0.0, 0.0};
-        Score sg{-1, 0.0, 0.0};
         if (have && drain && flights > 0) {
             route = 3;
             fin = true;
@@ -1045,7 +1046,9 @@ __global__ void __launch_bounds__(256, 2) k_raytrace(Params P) {
         } else if (have) {
             const DevProblem& pr = P.probs[pt.prob];
             double xi;
+            Score sg{-1, 0.0, 0.0};
             bool col = fly(P, pr, pt, r, xi, a_uv, ebin, sg);
+            score_now(P, sg);   // surface flights: lanes in other cells rarely share a bin
             ++flights;
             fw += pt.wgt;
             if (col) {
@@ -1068,7 +1071,6 @@ __global__ void __launch_bounds__(256, 2) k_raytrace(Params P) {
                 nflights += (unsigned long long)flights;
             }
         }
-        score_warp(P, sg);
         if (P.ww && __any_sync(kFull, wo.copies > 0 || wo.roulette_w > 0.0)) {
             int pw = have ? pt.prob : 0;
             sc.add(P.Y, wo.copies > 0, pw, GBMC_S_SPLIT, wo.copy_w, (unsigned long long)wo.copies);
