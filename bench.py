@@ -28,6 +28,11 @@ import synth  # noqa: E402
 
 HBM_FALLBACK_GBS = 6800.0
 BRACKET_BYTES = {0: 32, 1: 16}    # E_j, E_j+1, s_j, s_j+1
+# binary64 operations a micro lookup must perform (the workload
+# description's count: the two differences and the quotient of the
+# interpolation factor, its multiply-add, and the multiply-add of the sum);
+# the kernel issues fewer on the binary64 pipe (part runs on the integer units)
+ALGO_FP64_OPS_PER_MICRO = 6
 LOOKUP_IO_BYTES = 28              # per macro lookup: E 8, material 4, sigma_t and sigma_a 16
 ITER_KERNELS = 8                  # plan, source, 2 sort, 2 lookup (thread/warp mode), ray trace, collision
 # DRAM (and L2) bytes of every lookup launch of one eager profiled batch, from
@@ -677,14 +682,15 @@ def main():
                     help="skip the sub-records of the default run (binary32 against binary64 "
                          "at 1e7 particles, the lookup-only stress set)")
     ap.add_argument("--profile-batch", action="store_true",
-                    help="set up, autotune and warm up as the timed run does, then run one "
-                         "eager profiled batch and exit (the command the lookup-traffic ncu "
-                         "capture wraps)")
+                    help="set up as the timed run does, then run one eager profiled batch at "
+                         "the command line's options (no autotuning, no graph launches) and "
+                         "exit: the command the lookup-traffic ncu capture wraps")
     ap.add_argument("--record-traffic", metavar="NCU_CSV",
                     help="sum the lookup launches' DRAM/L2 bytes of an ncu CSV log of "
                          "--profile-batch into the traffic file for this workload and exit")
     ap.add_argument("--wide-windows", type=int, default=-1,
-                    help="with --record-traffic: the window-load width the capture ran with")
+                    help="with --profile-batch or --record-traffic: binary32 window-load width "
+                         "(0/1) of the captured batch")
     ap.add_argument("--ncu-command", default="",
                     help="with --record-traffic: the capture command, kept with the record")
     args = ap.parse_args()
@@ -748,6 +754,17 @@ def main():
         return [gbmc.problem(geoms[k], prob.seed, counts[k], batch=batch * world + rank,
                              problem_index=k) for k in range(n_geo)]
 
+    if args.profile_batch:
+        # the command an ncu capture wraps: one eager profiled batch at the
+        # options given on the command line, no graph launches
+        if args.wide_windows >= 0:
+            ctx.set_options(wide_windows=args.wide_windows)
+        kt = ctx.profile_problems(problems(30_000), stream)
+        print(json.dumps({"profiled_batch": {k: v[0] for k, v in kt.items()},
+                          "wide_windows": int(ctx.options.wide_windows)}), flush=True)
+        ctx.close()
+        return
+
     tuned = None
     if args.autotune == 1 or (args.autotune < 0 and args.config in (2, 3, 4)):
         tuned = ctx.autotune(problems(40_000), fraction=0.1 if n_geo > 1 else 0.3, stream=stream)
@@ -756,12 +773,6 @@ def main():
     for w in range(args.warmup):
         ctx.run_problems(problems(10_000 + w), stream)
     torch.cuda.synchronize()
-    if args.profile_batch:
-        kt = ctx.profile_problems(problems(30_000), stream)
-        print(json.dumps({"profiled_batch": {k: v[0] for k, v in kt.items()},
-                          "wide_windows": int(ctx.options.wide_windows)}), flush=True)
-        ctx.close()
-        return
     # concurrent event loops (Sec. 2, "GPU Streams"): a short trial of 1-4
     # loops, each also at 4 blocks per SM, picks the fastest (a candidate must
     # beat one loop by 2%)
@@ -898,13 +909,31 @@ def main():
     l2_size = torch.cuda.get_device_properties(local).L2_cache_size
     roof = {"kernel": "lookup", "bound": "hbm", "achieved": lk_gbs, "peak": hbm, "unit": "GB/s",
             "frac": lk_gbs / hbm, "peak_source": peak_src,
-            "traffic": tr["dram_bytes_per_batch"] / tr["launches"] if tr else None,
-            "l2_bytes": (tr["l2_bytes_per_batch"] / tr["launches"]
+            # per lookup event of the batch, as `achieved` (the capture counts the
+            # thread- and warp-mode kernels of an event separately)
+            "traffic": tr["dram_bytes_per_batch"] / max(lk_n, 1) if tr else None,
+            "l2_bytes": (tr["l2_bytes_per_batch"] / max(lk_n, 1)
                          if tr and tr.get("l2_bytes_per_batch") else None),
             "launches": lk_n, "avg_launch_ms": lk_ms / max(lk_n, 1),
             "algorithmic_bytes_per_launch": lk_bytes / max(lk_n, 1),
             "timing": "CUDA events around each lookup launch of one eager batch of this workload",
             "table_bytes": int(prob.table_bytes(args.precision)), "l2_capacity": int(l2_size)}
+    if args.precision == 0:
+        # binary64 tables: the lookup is bound by the binary64 pipe (ncu: 73%
+        # of it busy on full queues, DRAM under 10%); algorithmic operations
+        # against the rate the library's own probe measures
+        fp64_rate = ctx.measure_fp64_rate()
+        ops = pst["micro_lookups"] * ALGO_FP64_OPS_PER_MICRO
+        hbm_rec = {k: roof[k] for k in ("achieved", "peak", "unit", "frac", "peak_source",
+                                         "algorithmic_bytes_per_launch")}
+        roof.update({"bound": "alu", "achieved": ops / (lk_ms * 1e-3) / 1e9,
+                     "peak": fp64_rate / 1e9, "unit": "G binary64 op/s",
+                     "frac": ops / (lk_ms * 1e-3) / fp64_rate,
+                     "peak_source": "measured: gbmc_measure_fp64_rate (binary64 fused "
+                                    "multiply-add chains, CUDA events)",
+                     "algorithmic_ops_per_launch": ops / max(lk_n, 1),
+                     "ops_per_micro_lookup": ALGO_FP64_OPS_PER_MICRO, "hbm": hbm_rec})
+        del roof["algorithmic_bytes_per_launch"]
 
     cpu = None
     parity = None

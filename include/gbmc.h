@@ -539,6 +539,15 @@ int gbmc_lookup_macro_noalloc(gbmc_ctx *ctx, int32_t precision, const double *d_
                               const int32_t *d_mat, int64_t n, double *d_sigma_t,
                               double *d_sigma_a, void *stream);
 
+/* Measured binary64 throughput of this device (the denominator of the
+ * binary64 kernels' rooflines; the paper names no such figure): independent
+ * fused multiply-add chains, 8 per thread, 2^14 steps each, over SMs x 8
+ * blocks of 256 threads, timed with CUDA events on the legacy default
+ * stream (best of three after a warm-up).  *ops_per_s = binary64
+ * instructions per second, counted per thread.  Synchronous; allocates
+ * and frees a small device buffer. */
+int gbmc_measure_fp64_rate(gbmc_ctx *ctx, double *ops_per_s);
+
 /* Device timing of the last run's event loop (ms, CUDA events on the run's
  * stream around the graph launch); synchronizes. */
 int gbmc_last_run_ms(gbmc_ctx *ctx, double *ms);

@@ -1756,6 +1756,35 @@ int gbmc_check_division(gbmc_ctx* c, int32_t kind, int64_t n, uint64_t seed, int
     return GBMC_OK;
 }
 
+int gbmc_measure_fp64_rate(gbmc_ctx* c, double* ops_per_s) {
+    if (!c || !ops_per_s) return GBMC_ERR_INVALID_ARG;
+    int rc = set_device(c);
+    if (rc) return rc;
+    const int blocks = c->sms * 8;
+    const int32_t iters = 1 << 14;
+    double* out = nullptr;
+    if ((rc = dalloc(c, &out, (size_t)blocks))) return rc;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best = 0.0f;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {   // the first warms up
+        e = cudaEventRecord(e0, 0);
+        if (e == cudaSuccess) e = launch_fp64_rate(blocks, iters, out, 0);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, 0);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && rep > 0 && (best == 0.0f || ms < best)) best = ms;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    dfree(out);
+    if (e != cudaSuccess) return fail(c, GBMC_ERR_CUDA, "rate probe: %s", cudaGetErrorString(e));
+    *ops_per_s = (double)blocks * 256.0 * 8.0 * (double)iters / (best * 1e-3);
+    return GBMC_OK;
+}
+
 int gbmc_read_outcomes(gbmc_ctx* c, int32_t slot, int64_t first, int64_t n, int32_t* n_coll,
                        int8_t* status, int32_t* n_flights, uint32_t* n_draws, double* E, double* x,
                        double* y, double* z) {

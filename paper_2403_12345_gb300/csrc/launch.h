@@ -32,6 +32,10 @@ cudaError_t launch_check_interp(int64_t n, uint64_t seed, const double* e0s, con
                                 const Interval64* iv, int32_t K, unsigned long long* bad,
                                 double* first, int sms, cudaStream_t s);
 
+// Binary64 rate probe: blocks x 256 threads, each kRateChains (8)
+// independent fused multiply-add chains of iters steps.
+cudaError_t launch_fp64_rate(int blocks, int32_t iters, double* out, cudaStream_t s);
+
 // k-eigenvalue: compacts the run's per-history fission-site slots into
 // P.bank_out (history order), the size into *P.bank_size.
 cudaError_t launch_bank(const Params& P, const LaunchCfg& L, cudaStream_t s);

@@ -1491,6 +1491,33 @@ cudaError_t launch_check_interp(int64_t n, uint64_t seed, const double* e0s, con
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- binary64 rate probe
+// The binary64 pipe's throughput, for the rooflines of the binary64 kernels:
+// every thread advances kRateChains independent fused multiply-add chains
+// for `iters` steps (each step one binary64 instruction per chain), and
+// writes a value that depends on every chain so that none is removed.
+constexpr int kRateChains = 8;
+
+__global__ void __launch_bounds__(256) k_fp64_rate(int32_t iters, double a, double b,
+                                                   double* __restrict__ out) {
+    double x[kRateChains];
+#pragma unroll
+    for (int k = 0; k < kRateChains; ++k) x[k] = (double)(threadIdx.x + k) * 1e-3;
+    for (int32_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < kRateChains; ++k) x[k] = __fma_rn(x[k], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < kRateChains; ++k) s += x[k];
+    if (s == 12345.678) out[blockIdx.x] = s;   // never true for these a, b; keeps the chains
+}
+
+cudaError_t launch_fp64_rate(int blocks, int32_t iters, double* out, cudaStream_t s) {
+    k_fp64_rate<<<blocks, 256, 0, s>>>(iters, 0.999999, 1e-7, out);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- host launchers
 
 // The lookup's two mode kernels, with Sigma_a only when a tally needs it.

@@ -41,7 +41,7 @@ EXPORTS = ["gbmc_default_options", "gbmc_create", "gbmc_destroy", "gbmc_last_err
            "gbmc_importance_accumulate", "gbmc_importance_training_set",
            "gbmc_get_weight_windows", "gbmc_set_reaction_tally", "gbmc_read_reaction_tally",
            "gbmc_load_fission", "gbmc_set_eigen", "gbmc_read_bank", "gbmc_set_source_bank",
-           "gbmc_check_division", "gbmc_run_concurrent"]
+           "gbmc_check_division", "gbmc_run_concurrent", "gbmc_measure_fp64_rate"]
 MLP_HIDDEN = 64
 MLP_NPARAM = 4545
 NOALLOC_MAX_QUERIES = 1 << 20
@@ -123,6 +123,7 @@ def lib():
         L.gbmc_run_batch.argtypes = [vp, _P(Problem), vp]
         L.gbmc_run_problems.argtypes = [vp, C.c_int32, _P(Problem), vp]
         L.gbmc_run_concurrent.argtypes = [vp, C.c_int32, _P(Problem), C.c_int32, C.c_int32, vp]
+        L.gbmc_measure_fp64_rate.argtypes = [vp, _P(C.c_double)]
         L.gbmc_read_tallies.argtypes = [vp, C.c_int32, _P(C.c_double), C.c_int64,
                                         _P(C.c_int64), _P(C.c_double)]
         L.gbmc_set_reaction_tally.argtypes = [vp, C.c_int32]
@@ -484,6 +485,12 @@ class Context:
                                            int(seed) & 0xFFFFFFFFFFFFFFFF, C.byref(bad),
                                            _p(first, C.c_double)))
         return bad.value, first
+
+    def measure_fp64_rate(self) -> float:
+        """gbmc_measure_fp64_rate: binary64 instructions per second (per thread)."""
+        r = C.c_double()
+        self._ck(lib().gbmc_measure_fp64_rate(self._h, C.byref(r)))
+        return r.value
 
     def set_reaction_tally(self, on: bool = True):
         self._ck(lib().gbmc_set_reaction_tally(self._h, 1 if on else 0))
