@@ -34,7 +34,8 @@ BRACKET_BYTES = {0: 32, 1: 16}    # E_j, E_j+1, s_j, s_j+1
 # the kernel issues fewer on the binary64 pipe (part runs on the integer units)
 ALGO_FP64_OPS_PER_MICRO = 6
 LOOKUP_IO_BYTES = 28              # per macro lookup: E 8, material 4, sigma_t and sigma_a 16
-ITER_KERNELS = 8                  # plan, source, 2 sort, 2 lookup (thread/warp mode), ray trace, collision
+# kernels an iteration launches: plan, source, 2 sort, lookup, ray trace, collision
+ITER_KERNELS = {0: 7, 1: 7}
 # DRAM (and L2) bytes of every lookup launch of one eager profiled batch, from
 # ncu counters, written by `bench.py --record-traffic` and keyed by workload,
 # table precision and window-load width; each entry carries a hash of the
@@ -677,7 +678,7 @@ def main():
                     help="grid search: 1 coarse index (default), -1 plain binary search")
     ap.add_argument("--loops", type=int, default=0,
                     help="concurrent event loops over the steps' batches (gbmc_run_concurrent); "
-                         "0: the fastest of 1-4 in a short trial after autotuning")
+                         "0: the fastest of 1-6 in a short trial after autotuning")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the sub-records of the default run (binary32 against binary64 "
                          "at 1e7 particles, the lookup-only stress set)")
@@ -773,7 +774,7 @@ def main():
     for w in range(args.warmup):
         ctx.run_problems(problems(10_000 + w), stream)
     torch.cuda.synchronize()
-    # concurrent event loops (Sec. 2, "GPU Streams"): a short trial of 1-4
+    # concurrent event loops (Sec. 2, "GPU Streams"): a short trial of 1-6
     # loops, each also at 4 blocks per SM, picks the fastest (a candidate must
     # beat one loop by 2%)
     loops, loop_trials = max(args.loops, 1), None
@@ -781,7 +782,7 @@ def main():
         loop_trials = {}
         tuned_bps = ctx.options.blocks_per_sm
         best = None
-        for L in (1, 2, 3, 4):
+        for L in (1, 2, 3, 4, 6):
             for bps in sorted({tuned_bps, 4}):
                 ctx.set_options(blocks_per_sm=bps)
                 nb = 2 * L
@@ -970,7 +971,8 @@ def main():
             "roofline": m["roofline"], "clocks": m["clocks"]}
 
     runs = args.steps if loops > 1 else 1   # graph launches per entry of stats
-    launches = sum(2 * runs + ITER_KERNELS * s["iterations"] for s in stats)   # + init, tail
+    launches = sum(2 * runs + ITER_KERNELS[args.precision] * s["iterations"]
+                   for s in stats)   # + init and tail per run
     if rank == 0:
         line = {
             "metric": "particles/s", "value": value, "unit": "particles/s", "n_gpus": world,

@@ -104,7 +104,8 @@ typedef struct {
     int32_t sort_min;        /* sort only iterations with at least this many
                                 lookups (default 4096) */
     int32_t warp_lookup_max; /* iterations with fewer lookups run one warp per
-                                particle instead of one thread (default 32768) */
+                                particle instead of one thread (default 4096;
+                                -1: never) */
     int32_t tail_max;        /* once the source is exhausted and at most this many
                                 particles are in flight, the loop stops and a
                                 tail kernel finishes them, one warp per particle
@@ -115,6 +116,11 @@ typedef struct {
                                 of a warp read distinct windows (tables far beyond
                                 L2, sparse particles), more registers otherwise.
                                 Same results either way. */
+    int32_t group_lookup_max; /* binary64 tables: iterations with fewer lookups (and
+                                at least warp_lookup_max) run 4 lanes per particle,
+                                each with a quarter of the nuclides (default 160000;
+                                -1: never): shorter chains of dependent loads per
+                                warp where the queue is too short to hide them */
     int32_t search;          /* bracket search of the energy grids: 1 (default) a
                                 coarse index over each grid's bit patterns (binary64:
                                 about one point a bucket, then at most about one
@@ -123,7 +129,7 @@ typedef struct {
                                 the paper compares against (Sec. 3); -1 a plain
                                 binary search of each whole grid.  Same results
                                 either way (the bracket is unique). */
-    int32_t reserved[3];
+    int32_t reserved[2];
 } gbmc_options;
 
 /* One geometry (and its source).  Fields of other kinds are ignored. */

@@ -243,11 +243,13 @@ void fill_defaults(gbmc_options* o) {
     if (o->blocks_per_sm <= 0) o->blocks_per_sm = 8;
     if (o->max_iterations <= 0) o->max_iterations = 4 * GBMC_MAX_FLIGHTS;
     if (o->sort_min <= 0) o->sort_min = 4096;
-    if (o->warp_lookup_max == 0) o->warp_lookup_max = 32768;
+    if (o->warp_lookup_max == 0) o->warp_lookup_max = 4096;
     if (o->warp_lookup_max < 0) o->warp_lookup_max = 0;   // never
     if (o->tail_max == 0) o->tail_max = 4096;
     if (o->tail_max < 0) o->tail_max = 0;                 // never
     if (o->search == 0) o->search = 1;
+    if (o->group_lookup_max == 0) o->group_lookup_max = 160000;
+    if (o->group_lookup_max < 0) o->group_lookup_max = 0;   // never
 }
 
 int check_options(gbmc_ctx* c, const gbmc_options* o) {
@@ -468,6 +470,7 @@ Params make_params(gbmc_ctx* c) {
     P.sort = c->opt.sort > 0 ? 1 : 0;
     P.sort_min = c->opt.sort_min;
     P.warp_lookup_max = c->opt.warp_lookup_max;
+    P.group_lookup_max = c->opt.group_lookup_max;
     P.tail_max = c->opt.tail_max;
     P.wide_windows = c->opt.wide_windows;
     P.max_iter = c->opt.max_iterations;
@@ -2290,13 +2293,23 @@ extern "C" int gbmc_autotune(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* pr
         ++trials;
         if (t < best_ms * keep) { best_ms = t; best = o; }
     }
-    for (int32_t w : {-1, 8192, 131072}) {
+    for (int32_t w : {-1, 1024, 16384, 32768}) {
         gbmc_options o = best;
         o.warp_lookup_max = w;
         double t;
         if ((rc = probe_ms(c, pr, s, o, &t))) return rc;
         ++trials;
         if (t < best_ms * keep) { best_ms = t; best = o; }
+    }
+    if (best.precision == GBMC_FP64) {
+        for (int32_t g : {-1, 100000, 262144}) {
+            gbmc_options o = best;
+            o.group_lookup_max = g;
+            double t;
+            if ((rc = probe_ms(c, pr, s, o, &t))) return rc;
+            ++trials;
+            if (t < best_ms * keep) { best_ms = t; best = o; }
+        }
     }
     for (int32_t t : {-1, 1024, 16384, 65536}) {
         gbmc_options o = best;

@@ -176,6 +176,7 @@ struct Ctl {
     int32_t lookup_n, aq_base;   // lookups of this iteration, where they append in aq[cur]
     int32_t n_birth, free_base, lq_base, sorted;
     int32_t warp_lookup;         // this iteration's lookups run one warp per particle
+    int32_t group_lookup;        // this iteration's lookups run kGroupLanes lanes per particle
     int32_t adv_n;               // particles the ray-trace kernel takes this iteration
     int32_t tail;                // the loop stopped early: the tail kernel finishes
     int32_t adv_cursor;          // next ray-trace queue entry to hand out
@@ -223,6 +224,7 @@ struct Params {
     int32_t sort;            // sort the lookup queue
     int32_t sort_min;        // sort only when at least this many lookups
     int32_t warp_lookup_max; // below this many lookups: one warp per particle
+    int32_t group_lookup_max; // below this many (and not warp mode): kGroupLanes lanes per particle
     int32_t tail_max;        // stop the loop and finish in the tail kernel at or below
                              // this many particles in flight (source exhausted)
     int32_t max_iter;
@@ -735,6 +737,114 @@ __device__ __forceinline__ void brackets(const Tables& T, const Desc64* dq, cons
     }
 #pragma unroll
     for (int u = 0; u < kIlp; ++u) pos[u] = (gp[u] - g) + lo[u];
+}
+
+// Group mode of the binary64 lookup, for queues too short to hide the
+// dependent loads of one lane walking all of a particle's nuclides: a warp
+// takes 32 / kGroupLanes particles and kGroupLanes lanes per particle.  Lane
+// r of particle p forms the terms of nuclides r, r + kGroupLanes, ... of each
+// group of kGroupN nuclides, four searches in lock step, into a shared-memory
+// row of the particle; then lane 0 of the particle adds the row's terms in
+// the listed order and stores the checkpoints, so every term, sum and
+// checkpoint is macro64's.  Rows are kGroupStride doubles apart: the four
+// particles of a half-warp start 4 banks apart, so the stores of a half-warp
+// (four sub-lanes each) and the adders' reads fall in distinct banks.
+constexpr int kGroupLanes = 4;
+constexpr int kGroupN = 32;
+constexpr int kGroupStride = 36;
+static_assert(kGroupN % (kGroupLanes * 4) == 0, "whole lock-step rounds per group");
+
+struct LookupGroupTile {
+    double t[(32 / kGroupLanes) * kGroupStride];
+};
+
+// The brackets of the (up to kIlp) nuclides q, q + s, q + 2s, ... below q1,
+// searched in lock step (as brackets() for consecutive nuclides).
+__device__ __forceinline__ void brackets_strided(const Tables& T, int32_t q, int32_t s, int32_t q1,
+                                                 unsigned long long eb, int64_t* pos) {
+    const unsigned long long* g = reinterpret_cast<const unsigned long long*>(T.e64);
+    int32_t lo[kIlp], hi[kIlp];
+    const unsigned long long* gp[kIlp];
+#pragma unroll
+    for (int u = 0; u < kIlp; ++u) {
+        lo[u] = 0;
+        hi[u] = 1;
+        gp[u] = g;
+        const int32_t qu = q + u * s;
+        if (qu < q1) {
+            Desc64 d = load_desc64(T.d64 + qu);
+            gp[u] = g + d.off;
+            hi[u] = d.n - 1;
+            if (!T.plain) coarse_range(d, T.idx64, eb, lo[u], hi[u]);
+        }
+    }
+    bool more = true;
+    while (more) {
+        more = false;
+#pragma unroll
+        for (int u = 0; u < kIlp; ++u) {
+            if (hi[u] - lo[u] > 1) {
+                int32_t mid = (lo[u] + hi[u]) >> 1;
+                if (__ldg(gp[u] + mid) <= eb)
+                    lo[u] = mid;
+                else
+                    hi[u] = mid;
+                more = true;
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < kIlp; ++u) pos[u] = (gp[u] - g) + lo[u];
+}
+
+// All 32 lanes call (the loops are warp-uniform); particle p = lane /
+// kGroupLanes has material m (nq_max: the most nuclides of the warp's
+// particles), valid marks the lanes of real entries, cum the particle's
+// checkpoint row (read by its lane 0 only).
+template <bool SA>
+__device__ __forceinline__ void macro64_group(const Tables& T, int32_t m, double E, bool valid,
+                                              int32_t nq_max, LookupGroupTile& sm, double* cum,
+                                              double& st, double& sa) {
+    const int lane = threadIdx.x & 31;
+    const int p = lane / kGroupLanes, r = lane % kGroupLanes;
+    const int32_t q0 = valid ? __ldg(T.mat_off + m) : 0;
+    const int32_t nq = valid ? __ldg(T.mat_off + m + 1) - q0 : 0;
+    const unsigned long long eb = (unsigned long long)__double_as_longlong(E);
+    double at = 0.0, aa = 0.0;
+    double2 pend = make_double2(0.0, 0.0);
+    double* row = sm.t + p * kGroupStride;
+    for (int32_t g0 = 0; g0 < nq_max; g0 += kGroupN) {
+        const int32_t ge = min(nq, g0 + kGroupN);   // this particle's nuclides end in the group
+#pragma unroll
+        for (int k = 0; k < kGroupN / (kGroupLanes * kIlp); ++k) {
+            const int32_t a0 = g0 + r + k * kGroupLanes * kIlp;   // entry of the first of four
+            if (a0 < ge) {
+                int64_t pos[kIlp];
+                brackets_strided(T, q0 + a0, kGroupLanes, q0 + ge, eb, pos);
+#pragma unroll
+                for (int u = 0; u < kIlp; ++u) {
+                    const int32_t a = a0 + u * kGroupLanes;
+                    if (a < ge) row[a - g0] = __ldg(T.density + q0 + a) * interp64(T, pos[u], E);
+                }
+            }
+        }
+        __syncwarp();
+        if (r == 0) {
+            for (int32_t a = g0; a < ge; ++a) {
+                const double t = row[a - g0];
+                at = at + t;
+                if (SA) aa = aa + t * __ldg(T.f_abs + __ldg(T.nuc_id + q0 + a));
+                if (cum && ((a & 3) == 3 || a == nq - 1)) {
+                    const int32_t gq = a >> 2;
+                    if (gq & 1) pend.y = at; else pend.x = at;
+                    if ((gq & 1) || a == nq - 1) reinterpret_cast<double2*>(cum)[gq >> 1] = pend;
+                }
+            }
+        }
+        __syncwarp();
+    }
+    st = at;
+    sa = aa;
 }
 
 // SA = false skips Sigma_a (sa is then 0): the transport needs it only for

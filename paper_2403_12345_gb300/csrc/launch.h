@@ -44,7 +44,7 @@ cudaError_t launch_bank(const Params& P, const LaunchCfg& L, cudaStream_t s);
 // (ev[0..7]; the lookup's two mode kernels share one interval), for
 // per-kernel device timing; the tail is timed separately.
 constexpr int kIterKernels = 7;
-constexpr int kIterLaunches = 8;   // kernels launched per iteration
+constexpr int kIterLaunches = 7;   // kernels launched per iteration
 constexpr int kTimedKernels = 8;   // + the tail
 cudaError_t launch_iteration_timed(const Params& P, const LaunchCfg& L, cudaStream_t s,
                                    cudaEvent_t* ev);

@@ -252,6 +252,8 @@ __global__ void k_plan(Params P) {
     c->lookup_cursor = 0;
     c->sorted = (P.sort && c->lookup_n >= P.sort_min) ? 1 : 0;
     c->warp_lookup = c->lookup_n < P.warp_lookup_max ? 1 : 0;
+    c->group_lookup = !c->warp_lookup && P.precision == GBMC_FP64 &&
+                      c->lookup_n < P.group_lookup_max ? 1 : 0;
     P.st->lookups += (unsigned long long)c->lookup_n;
     c->done = done;
     if (P.use_cond) cudaGraphSetConditional(P.cond, done ? 0u : 1u);
@@ -489,11 +491,10 @@ __global__ void __launch_bounds__(256) k_sort_scatter(Params P) {
 
 // Thread mode (long queues): one particle per thread.  WIDE: binary32
 // bucket windows as 32-byte loads.
-template <int PREC, bool SA, bool WIDE = false>
-__global__ void __launch_bounds__(256, PREC == GBMC_FP64 ? 4 : 3) k_lookup(Params P) {
+template <int PREC, bool SA, bool WIDE>
+__device__ __forceinline__ void lookup_threads(const Params& P, LookupTile* tiles) {
     const Ctl* c = P.ctl;
-    int32_t n = c->lookup_n;
-    if (n == 0 || c->warp_lookup) return;
+    const int32_t n = c->lookup_n;
     int cur = c->cur;
     const int32_t* q = c->sorted ? P.Q.lqs : P.Q.lq[cur];
     int32_t* aq = P.Q.aq[cur] + c->aq_base;
@@ -516,11 +517,10 @@ __global__ void __launch_bounds__(256, PREC == GBMC_FP64 ? 4 : 3) k_lookup(Param
         double st = 0.0, sa = 0.0;
         if constexpr (PREC == GBMC_FP64) {
             // a sorted chunk of one material: the nuclide-major tile
-            __shared__ LookupTile tile[8];
             int32_t m0 = __shfl_sync(kFull, m, 0);
             if (sorted && __all_sync(kFull, !valid || m == m0) && tile_span_ok(E, valid)) {
                 int nv = (int)(n - b0 < 32 ? n - b0 : 32);
-                macro64_tile<SA>(P.T, m0, nv, E, tile[threadIdx.x >> 5],
+                macro64_tile<SA>(P.T, m0, nv, E, tiles[threadIdx.x >> 5],
                                  valid && P.cum ? (double*)P.cum + slot * P.cum_stride : nullptr,
                                  st, sa);
             } else if (valid) {
@@ -542,12 +542,52 @@ __global__ void __launch_bounds__(256, PREC == GBMC_FP64 ? 4 : 3) k_lookup(Param
     if ((threadIdx.x & 31) == 0 && micro) atomicAdd(&P.st->micro, micro);
 }
 
+// Group mode (binary64, medium queues): kGroupLanes lanes per particle,
+// 32 / kGroupLanes particles per warp-chunk (macro64_group).
+template <bool SA>
+__device__ __forceinline__ void lookup_groups(const Params& P, LookupGroupTile* tile) {
+    const Ctl* c = P.ctl;
+    const int32_t n = c->lookup_n;
+    const int cur = c->cur;
+    const int32_t* q = c->sorted ? P.Q.lqs : P.Q.lq[cur];
+    int32_t* aq = P.Q.aq[cur] + c->aq_base;
+    constexpr int kPer = 32 / kGroupLanes;   // particles per warp-chunk
+    const int lane = threadIdx.x & 31;
+    const int p = lane / kGroupLanes;
+    unsigned long long micro = 0;
+    for (;;) {
+        int64_t b0 = 0;
+        if (lane == 0) b0 = atomicAdd(&P.ctl->lookup_cursor, kPer);
+        b0 = __shfl_sync(kFull, b0, 0);
+        if (b0 >= n) break;
+        const int64_t idx = b0 + p;
+        const bool valid = idx < n;
+        const int32_t slot = valid ? q[idx] : 0;
+        const double E = valid ? P.B.p[slot].E : 0.0;
+        const int32_t m = valid ? P.B.p[slot].mat : 0;
+        int32_t nq = valid ? __ldg(P.T.mat_off + m + 1) - __ldg(P.T.mat_off + m) : 0;
+        int32_t nq_max = nq;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) nq_max = max(nq_max, __shfl_xor_sync(kFull, nq_max, o));
+        double st, sa;
+        macro64_group<SA>(P.T, m, E, valid, nq_max, tile[threadIdx.x >> 5],
+                          valid && P.cum ? (double*)P.cum + slot * P.cum_stride : nullptr, st, sa);
+        if (valid && lane % kGroupLanes == 0) {
+            P.B.p[slot].st = st;
+            if (SA) P.B.p[slot].sa = sa;
+            aq[idx] = slot;
+            micro += (unsigned long long)nq;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) micro += __shfl_xor_sync(kFull, micro, o);
+    if (lane == 0 && micro) atomicAdd(&P.st->micro, micro);
+}
+
 // Warp mode (short queues): one particle per warp.
 template <int PREC, bool SA>
-__global__ void __launch_bounds__(256) k_lookup_warp(Params P) {
+__device__ __forceinline__ void lookup_warps(const Params& P) {
     const Ctl* c = P.ctl;
-    int32_t n = c->lookup_n;
-    if (n == 0 || !c->warp_lookup) return;
+    const int32_t n = c->lookup_n;
     int cur = c->cur;
     const int32_t* q = c->sorted ? P.Q.lqs : P.Q.lq[cur];
     int32_t* aq = P.Q.aq[cur] + c->aq_base;
@@ -572,6 +612,25 @@ __global__ void __launch_bounds__(256) k_lookup_warp(Params P) {
         }
     }
     if (lane == 0 && micro) atomicAdd(&P.st->micro, micro);
+}
+
+// The lookup event: one launch per iteration, in the mode the plan picked
+// for the queue's length (warp, group -- binary64 only -- or thread); the
+// thread and group modes' shared-memory tiles share one buffer.
+template <int PREC, bool SA, bool WIDE = false>
+__global__ void __launch_bounds__(256, PREC == GBMC_FP64 ? 4 : 3) k_lookup(Params P) {
+    const Ctl* c = P.ctl;
+    if (c->lookup_n == 0) return;
+    constexpr size_t kTileBytes = sizeof(LookupTile) > sizeof(LookupGroupTile)
+                                      ? sizeof(LookupTile) : sizeof(LookupGroupTile);
+    __shared__ __align__(16) unsigned char tiles[PREC == GBMC_FP64 ? 8 * kTileBytes : 16];
+    if (c->warp_lookup) {
+        lookup_warps<PREC, SA>(P);
+    } else if (PREC == GBMC_FP64 && c->group_lookup) {
+        lookup_groups<SA>(P, reinterpret_cast<LookupGroupTile*>(tiles));
+    } else {
+        lookup_threads<PREC, SA, WIDE>(P, reinterpret_cast<LookupTile*>(tiles));
+    }
 }
 
 // ---------------------------------------------------------------- per-particle steps
@@ -1520,26 +1579,21 @@ cudaError_t launch_fp64_rate(int blocks, int32_t iters, double* out, cudaStream_
 
 // ---------------------------------------------------------------- host launchers
 
-// The lookup's two mode kernels, with Sigma_a only when a tally needs it.
+// The lookup kernel, with Sigma_a only when a tally needs it.
 static void launch_lookups(const Params& P, const LaunchCfg& L, cudaStream_t s) {
     bool sa = P.Y.absrate != nullptr;
     if (P.precision == GBMC_FP64) {
-        if (sa) {
-            k_lookup_warp<GBMC_FP64, true><<<L.grid_lookup, 256, 0, s>>>(P);
+        if (sa)
             k_lookup<GBMC_FP64, true><<<L.grid_lookup, 256, 0, s>>>(P);
-        } else {
-            k_lookup_warp<GBMC_FP64, false><<<L.grid_lookup, 256, 0, s>>>(P);
+        else
             k_lookup<GBMC_FP64, false><<<L.grid_lookup, 256, 0, s>>>(P);
-        }
     } else {
         if (sa) {
-            k_lookup_warp<GBMC_FP32, true><<<L.grid_lookup, 256, 0, s>>>(P);
             if (P.wide_windows)
                 k_lookup<GBMC_FP32, true, true><<<L.grid_lookup, 256, 0, s>>>(P);
             else
                 k_lookup<GBMC_FP32, true><<<L.grid_lookup, 256, 0, s>>>(P);
         } else {
-            k_lookup_warp<GBMC_FP32, false><<<L.grid_lookup, 256, 0, s>>>(P);
             if (P.wide_windows)
                 k_lookup<GBMC_FP32, false, true><<<L.grid_lookup, 256, 0, s>>>(P);
             else

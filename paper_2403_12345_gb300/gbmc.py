@@ -60,8 +60,9 @@ class Options(C.Structure):
                 ("block_lookup", C.c_int32), ("block_event", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("max_iterations", C.c_int32),
                 ("sort_min", C.c_int32), ("warp_lookup_max", C.c_int32),
-                ("tail_max", C.c_int32), ("wide_windows", C.c_int32), ("search", C.c_int32),
-                ("reserved", C.c_int32 * 3)]
+                ("tail_max", C.c_int32), ("wide_windows", C.c_int32),
+                ("group_lookup_max", C.c_int32), ("search", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
 
 
 class Geometry(C.Structure):

@@ -333,14 +333,16 @@ def test_lookup_macro_material_out_of_range_gives_nan(precision):
         ctx.close()
 
 
-@pytest.mark.parametrize("sizes", [(17, 9), (5, 1), (8, 3), (2, 16), (4, 7)])
+@pytest.mark.parametrize("sizes", [(17, 9), (5, 1), (8, 3), (2, 16), (4, 7), (40, 33)])
 @pytest.mark.parametrize("reaction", [False, True])
-def test_sorted_thread_lookups_every_group_size(sizes, reaction):
-    """Every lookup in thread mode and sorted (the nuclide-major tile of the
-    binary64 lookup), on materials whose nuclide counts leave partial groups
-    of every size; ragged chunk tails; with and without Sigma_a (the
-    absorption-rate tally); the collision's nuclide choice from the tile's
-    checkpoints."""
+@pytest.mark.parametrize("mode", ["thread", "group"])
+def test_sorted_thread_lookups_every_group_size(sizes, reaction, mode):
+    """Every lookup sorted, in thread mode (the nuclide-major tile of the
+    binary64 lookup) or in group mode (four lanes per particle), on materials
+    whose nuclide counts leave partial groups of every size (more than one
+    32-nuclide group of the group mode too); ragged chunk tails; with and
+    without Sigma_a (the absorption-rate tally); the collision's nuclide
+    choice from the checkpoints the lookup stored."""
     a, b = sizes
     p = synth.make_tiny_problem(seed=36 + a, n_nuc=a + b, n_points=(200, 3000),
                                 kind=synth.GEOM_LATTICE, lattice_n=6, n_particles=20_011)
@@ -348,7 +350,8 @@ def test_sorted_thread_lookups_every_group_size(sizes, reaction):
     p.mat_off = np.array([0, a, a + b], np.int32)
     p.nuc_id = np.concatenate([rng.permutation(a), a + rng.permutation(b)]).astype(np.int32)
     p.density = rng.uniform(0.01, 1.0, a + b)
-    ctx = make_ctx(p, warp_lookup_max=-1, sort_min=1, tail_max=-1, max_in_flight=7_001)
+    ctx = make_ctx(p, warp_lookup_max=-1, sort_min=1, tail_max=-1, max_in_flight=7_001,
+                   group_lookup_max=(1 << 30) if mode == "group" else -1)
     try:
         if reaction:
             ctx.set_reaction_tally(True)
