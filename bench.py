@@ -294,7 +294,7 @@ def fp32_vs_fp64_record(stream, local, steps=3):
 
 
 def stress_measure(prec, nq, steps, warmup, stream, local, seed_offset=0, e2e_steps=3,
-                   barrier=None, search=1):
+                   barrier=None, search=1, sparse=0):
     """Lookup-only stress set: lookups/s through gbmc_lookup_macro (the
     library's sort included), the lookup kernel alone on sorted queries
     (roofline), and end to end from pinned host memory."""
@@ -302,7 +302,7 @@ def stress_measure(prec, nq, steps, warmup, stream, local, seed_offset=0, e2e_st
     from paper_2403_12345_gb300 import gbmc
     prob, E, mat = synth.make_stress_lookup(n_queries=nq, seed_offset=seed_offset)
     micro_per = int(prob.mat_off[1] - prob.mat_off[0])
-    ctx = gbmc.Context(local, precision=prec, search=search)
+    ctx = gbmc.Context(local, precision=prec, search=search, sparse_windows=sparse)
     ctx.load(prob, (prec,))
     dE = torch.from_numpy(E).cuda()
     dm = torch.from_numpy(mat).cuda()
@@ -485,7 +485,8 @@ def run_stress(args, rank, world, local):
     stream = torch.cuda.current_stream()
     m = stress_measure(prec, nq, args.steps, args.warmup, stream, local, seed_offset=rank,
                        e2e_steps=args.e2e_steps,
-                       barrier=(lambda: dist.barrier()) if world > 1 else None)
+                       barrier=(lambda: dist.barrier()) if world > 1 else None,
+                       sparse=max(args.sparse_windows, 0))
     tot_ms = _max_over_ranks(sum(m["ms"]), world)
     value = nq * args.steps * world / (tot_ms * 1e-3)
     cpu = None
@@ -708,15 +709,16 @@ def main():
     ap.add_argument("--record-traffic", metavar="NCU_CSV",
                     help="sum the lookup launches' DRAM/L2 bytes of an ncu CSV log of "
                          "--profile-batch into the traffic file for this workload and exit")
-    ap.add_argument("--wide-windows", type=int, default=-1,
-                    help="with --profile-batch or --record-traffic: binary32 window-load width "
-                         "(0/1) of the captured batch")
+    ap.add_argument("--sparse-windows", type=int, default=-1,
+                    help="binary32 window form (0: 64-byte windows, 1: short windows) of the "
+                         "lookup-only stress set (config 6), and with --profile-batch or "
+                         "--record-traffic of the captured batch")
     ap.add_argument("--ncu-command", default="",
                     help="with --record-traffic: the capture command, kept with the record")
     args = ap.parse_args()
     if args.record_traffic:
         prec = args.precision if args.precision >= 0 else (0 if args.config in (1, 2) else 1)
-        record_traffic(args.record_traffic, args.config, prec, max(args.wide_windows, 0),
+        record_traffic(args.record_traffic, args.config, prec, max(args.sparse_windows, 0),
                        args.ncu_command)
         return
 
@@ -777,11 +779,11 @@ def main():
     if args.profile_batch:
         # the command an ncu capture wraps: one eager profiled batch at the
         # options given on the command line, no graph launches
-        if args.wide_windows >= 0:
-            ctx.set_options(wide_windows=args.wide_windows)
+        if args.sparse_windows >= 0:
+            ctx.set_options(sparse_windows=args.sparse_windows)
         kt = ctx.profile_problems(problems(30_000), stream)
         print(json.dumps({"profiled_batch": {k: v[0] for k, v in kt.items()},
-                          "wide_windows": int(ctx.options.wide_windows)}), flush=True)
+                          "sparse_windows": int(ctx.options.sparse_windows)}), flush=True)
         ctx.close()
         return
 
@@ -925,7 +927,7 @@ def main():
     lk_gbs = lk_bytes / (lk_ms * 1e-3) / 1e9
     stock = (args.particles == 0 and args.max_in_flight == 0 and args.blocks_per_sm == 0
              and args.sort == 1 and args.search == 1)
-    tr = recorded_traffic(args.config, args.precision, ctx.options.wide_windows) if stock else None
+    tr = recorded_traffic(args.config, args.precision, ctx.options.sparse_windows) if stock else None
     l2_size = torch.cuda.get_device_properties(local).L2_cache_size
     roof = {"kernel": "lookup", "bound": "hbm", "achieved": lk_gbs, "peak": hbm, "unit": "GB/s",
             "frac": lk_gbs / hbm, "peak_source": peak_src,

@@ -110,11 +110,14 @@ typedef struct {
                                 particles are in flight, the loop stops and a
                                 tail kernel finishes them, one warp per particle
                                 (default 4096; -1: never) */
-    int32_t wide_windows;    /* binary32 lookup reads each 64-byte bucket window as
-                                two 32-byte loads (1) instead of four 16-byte ones
-                                (0, default): half the L1 wavefronts when the lanes
-                                of a warp read distinct windows (tables far beyond
-                                L2, sparse particles), more registers otherwise.
+    int32_t sparse_windows;  /* binary32 lookup searches a finer coarse index (about
+                                two buckets a grid point) whose buckets each hold a
+                                32-byte window of four (E, sigma) pairs, read as one
+                                256-bit load (1), instead of the 64-byte windows of
+                                seven pairs (0, default).  One sector and one L1
+                                wavefront per lane and nuclide where the lanes of a
+                                warp read distinct windows (tables far beyond L2,
+                                particles sparser in energy than the grid points).
                                 Same results either way. */
     int32_t group_lookup_max; /* binary64 tables: iterations with fewer lookups (and
                                 at least warp_lookup_max) run 4 lanes per particle,

@@ -66,11 +66,16 @@ struct gbmc_ctx {
     std::vector<int32_t> h_mat_off, h_nuc_id;
     std::vector<double> h_density, h_fabs;
     std::vector<NucIndex> h_nx32;     // binary32 search descriptors (offsets into d_es32)
+    std::vector<NucIndex> h_nx32s;    // the same over the finer index of the short windows
     std::vector<NucIndex> h_nx64;     // binary64 search descriptors
     Desc64* d_desc64 = nullptr;       // per material entry: binary64 search descriptor
     Desc32* d_desc32 = nullptr;       // per material entry: search + density + f_abs
     float4* d_bw32 = nullptr;         // binary32 bucket windows (4 float4 each)
     std::vector<int64_t> h_bw_off;    // first window of each nuclide
+    Desc32* d_desc32s = nullptr;      // per material entry, finer index
+    float4* d_bs32 = nullptr;         // binary32 short windows (2 float4 each)
+    int2* d_br32 = nullptr;           // (lo, hi) of each short window's bucket
+    std::vector<int64_t> h_bs_off;    // first short window of each nuclide
     int32_t *d_mat_off = nullptr, *d_nuc_id = nullptr;
     double* d_density = nullptr;
     float* d_density32 = nullptr;
@@ -255,8 +260,8 @@ void fill_defaults(gbmc_options* o) {
 int check_options(gbmc_ctx* c, const gbmc_options* o) {
     if (o->precision != GBMC_FP64 && o->precision != GBMC_FP32)
         return fail(c, GBMC_ERR_INVALID_ARG, "precision must be GBMC_FP64 or GBMC_FP32");
-    if (o->wide_windows != 0 && o->wide_windows != 1)
-        return fail(c, GBMC_ERR_INVALID_ARG, "wide_windows must be 0 or 1");
+    if (o->sparse_windows != 0 && o->sparse_windows != 1)
+        return fail(c, GBMC_ERR_INVALID_ARG, "sparse_windows must be 0 or 1");
     if (o->search != 1 && o->search != -1)
         return fail(c, GBMC_ERR_INVALID_ARG, "search must be 1 (coarse index) or -1 (plain)");
     if (o->block_lookup != 256 || o->block_event != 256)
@@ -423,6 +428,7 @@ Tables make_tables(const gbmc_ctx* c) {
     Tables T{};
     T.grid_off = c->d_grid_off;
     T.d64 = c->d_desc64; T.idx64 = c->d_idx64; T.bw32 = c->d_bw32; T.d32 = c->d_desc32;
+    T.bs32 = c->d_bs32; T.br32 = c->d_br32; T.d32s = c->d_desc32s;
     T.e64 = c->d_e64; T.iv64 = c->d_iv64; T.es32 = c->d_es32;
     T.f_abs = c->d_fabs; T.f_abs32 = c->d_fabs32; T.awr = c->d_awr;
     T.mat_off = c->d_mat_off; T.nuc_id = c->d_nuc_id;
@@ -472,7 +478,7 @@ Params make_params(gbmc_ctx* c) {
     P.warp_lookup_max = c->opt.warp_lookup_max;
     P.group_lookup_max = c->opt.group_lookup_max;
     P.tail_max = c->opt.tail_max;
-    P.wide_windows = c->opt.wide_windows;
+    P.sparse_windows = c->opt.sparse_windows;
     P.max_iter = c->opt.max_iterations;
     sort_params(c, P);
     P.planes = c->d_planes;
@@ -665,6 +671,7 @@ Interval64 interval_record(double e0, double e1, double s0, double s1) {
 }
 
 constexpr int32_t kIndexPer64 = 1;   // grid points per bucket of the binary64 coarse index
+constexpr int32_t kShortFine = 1;    // log2 buckets per grid point of the short windows' index
 
 // Coarse search index of every nuclide grid (binary64 or binary32 bit
 // patterns): buckets (bits - bits(E_0)) >> shift, about 8 grid points per
@@ -672,7 +679,8 @@ constexpr int32_t kIndexPer64 = 1;   // grid points per bucket of the binary64 c
 int build_index(gbmc_ctx* c, int32_t n_nuc, const int64_t* grid_off, const double* energy,
                 int32_t precision, NucIndex** d_nx, uint32_t** d_idx,
                 const int64_t* table_off = nullptr, std::vector<NucIndex>* keep = nullptr,
-                std::vector<uint32_t>* keep_idx = nullptr) {
+                std::vector<uint32_t>* keep_idx = nullptr, int32_t per = 0,
+                int32_t fine = 0) {
     auto bits = [&](int64_t k) -> uint64_t {
         if (precision == GBMC_FP64) {
             uint64_t b;
@@ -692,10 +700,10 @@ int build_index(gbmc_ctx* c, int32_t n_nuc, const int64_t* grid_off, const doubl
         // binary64: about one point a bucket (the bisection within the
         // bucket's range then takes at most about one step, none for an
         // empty bucket); binary32: about 1-2, read as one bucket window
-        int32_t per = precision == GBMC_FP64 ? kIndexPer64 : 2;
+        if (per <= 0) per = precision == GBMC_FP64 ? kIndexPer64 : 2;
         int32_t cap = 1 << 20;
         int32_t nb = 16;
-        while ((int64_t)nb * per < n && nb < cap) nb <<= 1;
+        while ((int64_t)nb * per < (n << fine) && nb < cap) nb <<= 1;
         int32_t shift = 0;
         while ((range >> shift) >= (uint64_t)nb) ++shift;
         NucIndex d{};
@@ -725,19 +733,26 @@ int build_desc32(gbmc_ctx* c) {
     if (!c->has32 || !c->n_mat) return GBMC_OK;
     size_t tot = c->h_nuc_id.size();
     std::vector<Desc32> d(tot);
-    for (size_t q = 0; q < tot; ++q) {
-        const NucIndex& x = c->h_nx32[c->h_nuc_id[q]];
-        Desc32& e = d[q];
-        e.off = x.off;
-        e.bw_off = (int32_t)c->h_bw_off[c->h_nuc_id[q]];
-        e.base = (uint32_t)x.base;
-        e.n = x.n;
-        e.shift = x.shift;
-        e.nb = x.nb;
-        e.density = (float)c->h_density[q];
-        e.f_abs = (float)c->h_fabs[c->h_nuc_id[q]];
+    // the 64-byte windows' records, then the short windows' (finer index)
+    for (int form = 0; form < 2; ++form) {
+        const std::vector<NucIndex>& nx = form ? c->h_nx32s : c->h_nx32;
+        const std::vector<int64_t>& woff = form ? c->h_bs_off : c->h_bw_off;
+        for (size_t q = 0; q < tot; ++q) {
+            const NucIndex& x = nx[c->h_nuc_id[q]];
+            Desc32& e = d[q];
+            e.off = (int32_t)x.off;
+            e.bw_off = (int32_t)woff[c->h_nuc_id[q]];
+            e.base = (uint32_t)x.base;
+            e.n = x.n;
+            e.shift = x.shift;
+            e.nb = x.nb;
+            e.density = (float)c->h_density[q];
+            e.f_abs = (float)c->h_fabs[c->h_nuc_id[q]];
+        }
+        int rc = upload(c, form ? &c->d_desc32s : &c->d_desc32, d.data(), tot);
+        if (rc) return rc;
     }
-    return upload(c, &c->d_desc32, d.data(), tot);
+    return GBMC_OK;
 }
 
 // Per material entry search descriptors of the binary64 lookup (needs the
@@ -877,7 +892,7 @@ int gbmc_destroy(gbmc_ctx* c) {
     dfree(c->d_fabs); dfree(c->d_fabs32); dfree(c->d_awr);
     dfree(c->d_idx64); dfree(c->d_bw32); dfree(c->d_desc64);
     dfree(c->d_mat_off); dfree(c->d_nuc_id); dfree(c->d_density); dfree(c->d_density32);
-    dfree(c->d_desc32);
+    dfree(c->d_desc32); dfree(c->d_desc32s); dfree(c->d_bs32); dfree(c->d_br32);
     dfree(c->d_edges); dfree(c->d_probs); dfree(c->d_planes); dfree(c->d_ctl);
     dfree(c->d_ww); dfree(c->d_child);
     dfree(c->d_net_p); dfree(c->d_net_m); dfree(c->d_net_v); dfree(c->d_net_g);
@@ -961,7 +976,7 @@ int gbmc_load_xs_tables(gbmc_ctx* c, int32_t n_nuc, const int64_t* grid_off, con
     if (!same) {
         // new tables: drop the copy of the other precision
         dfree(c->d_e64); dfree(c->d_iv64); dfree(c->d_es32);
-        dfree(c->d_idx64); dfree(c->d_bw32);
+        dfree(c->d_idx64); dfree(c->d_bw32); dfree(c->d_bs32); dfree(c->d_br32);
         c->has64 = c->has32 = false;
         // materials refer to nuclide ids of the old tables
         if (c->n_mat) {
@@ -1040,6 +1055,39 @@ int gbmc_load_xs_tables(gbmc_ctx* c, int32_t n_nuc, const int64_t* grid_off, con
             }
         }
         if ((rc = upload(c, &c->d_bw32, bw.data(), bw.size()))) return rc;
+        bw = std::vector<float4>();
+        // short windows over a finer index (about two buckets a point): bucket
+        // b holds the pairs lo .. lo + 3 of its bracket range [lo, hi] (as
+        // above); (lo, hi) itself goes to br32 at the same index
+        std::vector<uint32_t> idx_s;
+        if ((rc = build_index(c, n_nuc, grid_off, energy, GBMC_FP32, nullptr, nullptr,
+                              poff.data(), &c->h_nx32s, &idx_s, 1, kShortFine)))
+            return rc;
+        c->h_bs_off.assign(n_nuc, 0);
+        int64_t ns = 0;
+        for (int32_t i = 0; i < n_nuc; ++i) {
+            c->h_bs_off[i] = ns;
+            ns += c->h_nx32s[i].nb;
+        }
+        if (ns > ((int64_t)1 << 31) - 1)
+            return fail(c, GBMC_ERR_INVALID_ARG, "binary32 tables over 2^31 index buckets");
+        std::vector<float4> bs((size_t)ns * 2);
+        std::vector<int2> br((size_t)ns);
+        for (int32_t i = 0; i < n_nuc; ++i) {
+            const NucIndex& x = c->h_nx32s[i];
+            const float2* g = es.data() + x.off;
+            for (int32_t b = 0; b < x.nb; ++b) {
+                int32_t s0 = (int32_t)idx_s[x.idx_off + b], s1 = (int32_t)idx_s[x.idx_off + b + 1];
+                int32_t lo = std::min(s0 > 0 ? s0 - 1 : 0, x.n - 2);
+                int32_t hi = std::min(s1, x.n - 1);
+                size_t k = (size_t)(c->h_bs_off[i] + b);
+                bs[2 * k] = make_float4(g[lo].x, g[lo].y, g[lo + 1].x, g[lo + 1].y);
+                bs[2 * k + 1] = make_float4(g[lo + 2].x, g[lo + 2].y, g[lo + 3].x, g[lo + 3].y);
+                br[k] = make_int2(lo, hi);
+            }
+        }
+        if ((rc = upload(c, &c->d_bs32, bs.data(), bs.size()))) return rc;
+        if ((rc = upload(c, &c->d_br32, br.data(), br.size()))) return rc;
         c->has32 = true;
     }
     c->n_nuc = n_nuc;
@@ -1339,6 +1387,7 @@ void release_borrowed(gbmc_ctx* l) {
     l->d_grid_off = nullptr; l->d_iv64 = nullptr; l->d_e64 = nullptr; l->d_fabs = nullptr;
     l->d_awr = nullptr; l->d_es32 = nullptr; l->d_fabs32 = nullptr; l->d_idx64 = nullptr;
     l->d_desc64 = nullptr; l->d_desc32 = nullptr; l->d_bw32 = nullptr;
+    l->d_desc32s = nullptr; l->d_bs32 = nullptr; l->d_br32 = nullptr;
     l->d_mat_off = nullptr; l->d_nuc_id = nullptr; l->d_density = nullptr;
     l->d_density32 = nullptr; l->d_edges = nullptr; l->d_nu = nullptr; l->d_ffis = nullptr;
     l->O = Outcomes{};
@@ -1363,6 +1412,7 @@ void borrow_from(gbmc_ctx* l, const gbmc_ctx* c) {
     l->d_fabs = c->d_fabs; l->d_awr = c->d_awr; l->d_es32 = c->d_es32;
     l->d_fabs32 = c->d_fabs32; l->d_idx64 = c->d_idx64;
     l->d_desc64 = c->d_desc64; l->d_desc32 = c->d_desc32; l->d_bw32 = c->d_bw32;
+    l->d_desc32s = c->d_desc32s; l->d_bs32 = c->d_bs32; l->d_br32 = c->d_br32;
     l->n_mat = c->n_mat; l->h_mat_off = c->h_mat_off; l->h_nuc_id = c->h_nuc_id;
     l->h_density = c->h_density; l->h_fabs = c->h_fabs; l->max_nuc_per_mat = c->max_nuc_per_mat;
     l->d_mat_off = c->d_mat_off; l->d_nuc_id = c->d_nuc_id; l->d_density = c->d_density;
@@ -2319,10 +2369,10 @@ extern "C" int gbmc_autotune(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* pr
         ++trials;
         if (t_ms < best_ms * keep) { best_ms = t_ms; best = o; }
     }
-    // binary32 bucket windows as 32-byte loads
+    // binary32 lookups on the short windows
     if (best.precision == GBMC_FP32) {
         gbmc_options o = best;
-        o.wide_windows = 1 - best.wide_windows;
+        o.sparse_windows = 1 - best.sparse_windows;
         double t;
         if ((rc = probe_ms(c, pr, s, o, &t))) return rc;
         ++trials;

@@ -77,6 +77,10 @@ struct Tables {
     const uint32_t* idx64;     // coarse index of the binary64 grids
     const float4* bw32;        // binary32 bucket windows (four float4 each)
     const Desc32* d32;         // [mat_off[n_mat]] per material entry (binary32)
+    const float4* bs32;        // binary32 short windows of the finer index (two float4 each)
+    const int2* br32;          // bracket range (lo, hi) of each short window's bucket
+    const Desc32* d32s;        // [mat_off[n_mat]] per material entry, finer index (bw_off,
+                               // shift, nb refer to the short windows)
     const double* e64;         // binary64 grid (eV)
     const Interval64* iv64;    // binary64 intervals, indexed like e64 (last of each grid unused)
     const float2* es32;        // binary32 (E, sigma_t) pairs, each nuclide followed by
@@ -228,7 +232,7 @@ struct Params {
     int32_t tail_max;        // stop the loop and finish in the tail kernel at or below
                              // this many particles in flight (source exhausted)
     int32_t max_iter;
-    int32_t wide_windows;    // binary32 bucket windows as two 32-byte loads (host: kernel choice)
+    int32_t sparse_windows;  // binary32 lookup on the short windows (host: kernel choice)
     uint32_t sort_shift;     // energy-bits >> shift = bucket within a material
     uint32_t bpm_log2;       // log2 buckets per material
     int32_t use_cond;        // 1 inside the graph while-body, 0 for eager launches
@@ -613,23 +617,10 @@ __device__ __forceinline__ const float4* window_of(const Tables& T, const Desc32
 }
 
 // A bucket window (64 bytes, 64-byte aligned in the pool) as four 16-byte
-// loads, or (WIDE) as two 256-bit loads: with the lanes of a warp on distinct
-// windows each load instruction costs one L1 wavefront per lane, so two loads
-// take half the wavefronts of four, at the price of registers (a 256-bit load
-// fills eight consecutive ones).
-template <bool WIDE = false>
+// loads.
 __device__ __forceinline__ void load_window(const float4* p, float4* q) {
-    if (WIDE) {
 #pragma unroll
-        for (int k = 0; k < 4; k += 2)
-            asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                : "=f"(q[k].x), "=f"(q[k].y), "=f"(q[k].z), "=f"(q[k].w), "=f"(q[k + 1].x),
-                  "=f"(q[k + 1].y), "=f"(q[k + 1].z), "=f"(q[k + 1].w)
-                : "l"(p + k));
-    } else {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) q[k] = __ldg(p + k);
-    }
+    for (int k = 0; k < 4; ++k) q[k] = __ldg(p + k);
 }
 
 // The bracket's end points (its pair and the next) by bisection of the
@@ -672,13 +663,69 @@ __device__ __forceinline__ void bracket32(const Tables& T, const Desc32& d, cons
     bracket32_bisect(T, d, lo, hi, eb, p0, p1);
 }
 
-// Micro cross section of material entry q (binary32) at E.
+// Short windows (the sparse form of the binary32 search).  When the lanes of
+// a warp read distinct windows (tables far beyond L2, particles sparser in
+// energy than the grid points) each load instruction costs one L1 wavefront
+// per lane and each window at least one 32-byte sector, so this form reads
+// exactly one sector per nuclide: a finer index of about two buckets a grid
+// point, whose bucket b holds the four pairs lo .. lo + 3 (lo = first point
+// of the bucket - 1, clamped to [0, n - 2]; sentinel pairs past the grid),
+// with (lo, hi) of the bucket kept apart in br32 for the rare fallback.
+// E_lo <= E unless lo = 0, and every entry past point n - 1 is +inf, so with
+// c entries of the window at or below E:
+//   c < 4: the bracket is lo + c - 1, capped to n - 2 (entry 1 is always a
+//          grid point, so the cap is min(2, finite entries - 2)) and at
+//          least 0; both end points are in the window's registers;
+//   c = 4: E is at or past point lo + 3 < hi (or = hi = n - 1), and the
+//          bracket is found by bisection of [min(lo + 3, n - 2), hi].
+__device__ __forceinline__ int64_t short_bucket(const Desc32& d, uint32_t eb) {
+    uint32_t b = eb >= d.base ? (eb - d.base) >> d.shift : 0u;
+    if (b > (uint32_t)(d.nb - 1)) b = (uint32_t)(d.nb - 1);
+    return (int64_t)d.bw_off + b;
+}
+
+// One short window (32 bytes, 32-byte aligned) as one 256-bit load.
+__device__ __forceinline__ void load_short(const float4* p, float (&w)[8]) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(w[0]), "=f"(w[1]), "=f"(w[2]), "=f"(w[3]), "=f"(w[4]), "=f"(w[5]), "=f"(w[6]),
+          "=f"(w[7])
+        : "l"(p));
+}
+
+__device__ __forceinline__ void bracket32_short(const Tables& T, const Desc32& d, int64_t wb,
+                                                const float (&w)[8], uint32_t eb, float2& p0,
+                                                float2& p1) {
+    const uint32_t e0 = __float_as_uint(w[0]), e1 = __float_as_uint(w[2]),
+                   e2 = __float_as_uint(w[4]), e3 = __float_as_uint(w[6]);
+    const int32_t c = (e0 <= eb) + (e1 <= eb) + (e2 <= eb) + (e3 <= eb);
+    if (c == 4) {
+        const int2 r = __ldg(T.br32 + wb);
+        bracket32_bisect(T, d, min(r.x + 3, d.n - 2), r.y, eb, p0, p1);
+        return;
+    }
+    constexpr uint32_t kInfBits = 0x7f800000u;
+    const int32_t fin = 2 + (e2 < kInfBits) + (e3 < kInfBits);   // finite entries
+    const int32_t r = max(min(c - 1, fin - 2), 0);
+    const float2 a = make_float2(w[0], w[1]), b = make_float2(w[2], w[3]),
+                 e = make_float2(w[4], w[5]), f = make_float2(w[6], w[7]);
+    p0 = r == 0 ? a : (r == 1 ? b : e);
+    p1 = r == 0 ? b : (r == 1 ? e : f);
+}
+
+// Micro cross section of material entry q (binary32) at E (SPARSE: on the
+// short windows).
+template <bool SPARSE = false>
 __device__ __forceinline__ float micro32(const Tables& T, int32_t q, double E) {
-    Desc32 d = load_desc32(T.d32 + q);
+    Desc32 d = load_desc32((SPARSE ? T.d32s : T.d32) + q);
     uint32_t eb = (uint32_t)__float_as_int(__double2float_rd(E));
     float2 p0, p1;
     if (T.plain) {
         bracket32_bisect(T, d, 0, d.n - 1, eb, p0, p1);
+    } else if (SPARSE) {
+        const int64_t wb = short_bucket(d, eb);
+        float w[8];
+        load_short(T.bs32 + 2 * wb, w);
+        bracket32_short(T, d, wb, w, eb, p0, p1);
     } else {
         const float4* p = window_of(T, d, eb);
         float4 w[4];
@@ -1007,7 +1054,7 @@ __device__ __forceinline__ void macro64_tile(const Tables& T, int32_t m, int nv,
     sa = aa;
 }
 
-template <bool SA = true, bool WIDE = false>
+template <bool SA = true, bool SPARSE = false>
 __device__ __forceinline__ void macro32(const Tables& T, int32_t m, double E, double& st,
                                         double& sa, float* cum = nullptr) {
     float at = 0.0f, aa = 0.0f;
@@ -1018,7 +1065,8 @@ __device__ __forceinline__ void macro32(const Tables& T, int32_t m, double E, do
     for (int32_t q = q0; q < q1; q += kIlp32) {
         Desc32 d[kIlp32];
 #pragma unroll
-        for (int u = 0; u < kIlp32; ++u) d[u] = load_desc32(T.d32 + (q + u < q1 ? q + u : q));
+        for (int u = 0; u < kIlp32; ++u)
+            d[u] = load_desc32((SPARSE ? T.d32s : T.d32) + (q + u < q1 ? q + u : q));
         float2 p0[kIlp32], p1[kIlp32];
         if (T.plain) {
             // plain binary search of each grid, the group's searches in lock step
@@ -1048,13 +1096,22 @@ __device__ __forceinline__ void macro32(const Tables& T, int32_t m, double E, do
                 p0[u] = __ldg(T.es32 + d[u].off + lo[u]);
                 p1[u] = __ldg(T.es32 + d[u].off + lo[u] + 1);
             }
+        } else if (SPARSE) {
+            int64_t wb[kIlp32];
+#pragma unroll
+            for (int u = 0; u < kIlp32; ++u) wb[u] = short_bucket(d[u], eb);
+            float w[kIlp32][8];
+#pragma unroll
+            for (int u = 0; u < kIlp32; ++u) load_short(T.bs32 + 2 * wb[u], w[u]);
+#pragma unroll
+            for (int u = 0; u < kIlp32; ++u) bracket32_short(T, d[u], wb[u], w[u], eb, p0[u], p1[u]);
         } else {
             const float4* pw[kIlp32];
 #pragma unroll
             for (int u = 0; u < kIlp32; ++u) pw[u] = window_of(T, d[u], eb);
             float4 w[kIlp32][4];
 #pragma unroll
-            for (int u = 0; u < kIlp32; ++u) load_window<WIDE>(pw[u], w[u]);
+            for (int u = 0; u < kIlp32; ++u) load_window(pw[u], w[u]);
 #pragma unroll
             for (int u = 0; u < kIlp32; ++u) bracket32(T, d[u], pw[u], w[u], eb, p0[u], p1[u]);
         }
@@ -1101,7 +1158,7 @@ __device__ __forceinline__ void macro32(const Tables& T, int32_t m, double E, do
 // Used when the lookup queue is too short to keep the GPU busy with one
 // particle per thread (the per-particle nuclide loop is then a long serial
 // latency chain).
-template <int PREC, bool SA = true>
+template <int PREC, bool SA = true, bool SPARSE = false>
 __device__ __forceinline__ void macro_warp(const Tables& T, int32_t m, double E, double& st,
                                            double& sa, void* cum, int64_t stride) {
     const unsigned full = 0xffffffffu;
@@ -1132,7 +1189,7 @@ __device__ __forceinline__ void macro_warp(const Tables& T, int32_t m, double E,
             float t = 0.0f, p = 0.0f;
             if (c + lane < q1) {
                 const Desc32* dq = T.d32 + c + lane;
-                t = __ldg(&dq->density) * micro32(T, c + lane, E);
+                t = __ldg(&dq->density) * micro32<SPARSE>(T, c + lane, E);
                 if (SA) p = t * __ldg(&dq->f_abs);
             }
             int32_t kmax = q1 - c < 32 ? q1 - c : 32;

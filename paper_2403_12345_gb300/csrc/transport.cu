@@ -489,9 +489,9 @@ __global__ void __launch_bounds__(256) k_sort_scatter(Params P) {
 
 // ---------------------------------------------------------------- lookup event
 
-// Thread mode (long queues): one particle per thread.  WIDE: binary32
-// bucket windows as 32-byte loads.
-template <int PREC, bool SA, bool WIDE>
+// Thread mode (long queues): one particle per thread.  SPARSE: binary32
+// lookups on the short windows.
+template <int PREC, bool SA, bool SPARSE>
 __device__ __forceinline__ void lookup_threads(const Params& P, LookupTile* tiles) {
     const Ctl* c = P.ctl;
     const int32_t n = c->lookup_n;
@@ -528,8 +528,8 @@ __device__ __forceinline__ void lookup_threads(const Params& P, LookupTile* tile
                             P.cum ? (double*)P.cum + slot * P.cum_stride : nullptr);
             }
         } else if (valid) {
-            macro32<SA, WIDE>(P.T, m, E, st, sa,
-                              P.cum ? (float*)P.cum + slot * P.cum_stride : nullptr);
+            macro32<SA, SPARSE>(P.T, m, E, st, sa,
+                                P.cum ? (float*)P.cum + slot * P.cum_stride : nullptr);
         }
         if (valid) {
             P.B.p[slot].st = st;
@@ -584,7 +584,7 @@ __device__ __forceinline__ void lookup_groups(const Params& P, LookupGroupTile* 
 }
 
 // Warp mode (short queues): one particle per warp.
-template <int PREC, bool SA>
+template <int PREC, bool SA, bool SPARSE>
 __device__ __forceinline__ void lookup_warps(const Params& P) {
     const Ctl* c = P.ctl;
     const int32_t n = c->lookup_n;
@@ -603,7 +603,7 @@ __device__ __forceinline__ void lookup_warps(const Params& P) {
         void* cum = P.cum ? (PREC == GBMC_FP64 ? (void*)((double*)P.cum + slot * P.cum_stride)
                                                : (void*)((float*)P.cum + slot * P.cum_stride))
                           : nullptr;
-        macro_warp<PREC, SA>(P.T, m, E, st, sa, cum, 1);
+        macro_warp<PREC, SA, SPARSE>(P.T, m, E, st, sa, cum, 1);
         if (lane == 0) {
             P.B.p[slot].st = st;
             if (SA) P.B.p[slot].sa = sa;
@@ -617,7 +617,7 @@ __device__ __forceinline__ void lookup_warps(const Params& P) {
 // The lookup event: one launch per iteration, in the mode the plan picked
 // for the queue's length (warp, group -- binary64 only -- or thread); the
 // thread and group modes' shared-memory tiles share one buffer.
-template <int PREC, bool SA, bool WIDE = false>
+template <int PREC, bool SA, bool SPARSE = false>
 __global__ void __launch_bounds__(256, PREC == GBMC_FP64 ? 4 : 3) k_lookup(Params P) {
     const Ctl* c = P.ctl;
     if (c->lookup_n == 0) return;
@@ -625,11 +625,11 @@ __global__ void __launch_bounds__(256, PREC == GBMC_FP64 ? 4 : 3) k_lookup(Param
                                       ? sizeof(LookupTile) : sizeof(LookupGroupTile);
     __shared__ __align__(16) unsigned char tiles[PREC == GBMC_FP64 ? 8 * kTileBytes : 16];
     if (c->warp_lookup) {
-        lookup_warps<PREC, SA>(P);
+        lookup_warps<PREC, SA, SPARSE>(P);
     } else if (PREC == GBMC_FP64 && c->group_lookup) {
         lookup_groups<SA>(P, reinterpret_cast<LookupGroupTile*>(tiles));
     } else {
-        lookup_threads<PREC, SA, WIDE>(P, reinterpret_cast<LookupTile*>(tiles));
+        lookup_threads<PREC, SA, SPARSE>(P, reinterpret_cast<LookupTile*>(tiles));
     }
 }
 
@@ -1386,7 +1386,7 @@ __global__ void __launch_bounds__(256) k_query_scatter(int64_t n, const uint32_t
     }
 }
 
-template <int PREC>
+template <int PREC, bool SPARSE = false>
 __global__ void __launch_bounds__(256, 4) k_query_lookup(Tables T, const double* __restrict__ E,
                                                       const int32_t* __restrict__ mat, int64_t n,
                                                       const int32_t* __restrict__ perm,
@@ -1401,7 +1401,7 @@ __global__ void __launch_bounds__(256, 4) k_query_lookup(Tables T, const double*
             if (PREC == GBMC_FP64)
                 macro64(T, m, E[i], a, b);
             else
-                macro32(T, m, E[i], a, b);
+                macro32<true, SPARSE>(T, m, E[i], a, b);
         }
         st[i] = a;
         sa[i] = b;
@@ -1589,12 +1589,12 @@ static void launch_lookups(const Params& P, const LaunchCfg& L, cudaStream_t s) 
             k_lookup<GBMC_FP64, false><<<L.grid_lookup, 256, 0, s>>>(P);
     } else {
         if (sa) {
-            if (P.wide_windows)
+            if (P.sparse_windows)
                 k_lookup<GBMC_FP32, true, true><<<L.grid_lookup, 256, 0, s>>>(P);
             else
                 k_lookup<GBMC_FP32, true><<<L.grid_lookup, 256, 0, s>>>(P);
         } else {
-            if (P.wide_windows)
+            if (P.sparse_windows)
                 k_lookup<GBMC_FP32, false, true><<<L.grid_lookup, 256, 0, s>>>(P);
             else
                 k_lookup<GBMC_FP32, false><<<L.grid_lookup, 256, 0, s>>>(P);
@@ -1665,6 +1665,8 @@ cudaError_t launch_query_lookup(const Params& P, const LaunchCfg& L, const doubl
     }
     if (P.precision == GBMC_FP64)
         k_query_lookup<GBMC_FP64><<<L.grid_lookup, 256, 0, s>>>(P.T, E, mat, n, perm, st, sa);
+    else if (P.sparse_windows)
+        k_query_lookup<GBMC_FP32, true><<<L.grid_lookup, 256, 0, s>>>(P.T, E, mat, n, perm, st, sa);
     else
         k_query_lookup<GBMC_FP32><<<L.grid_lookup, 256, 0, s>>>(P.T, E, mat, n, perm, st, sa);
     return cudaGetLastError();

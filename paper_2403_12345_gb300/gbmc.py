@@ -60,7 +60,7 @@ class Options(C.Structure):
                 ("block_lookup", C.c_int32), ("block_event", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("max_iterations", C.c_int32),
                 ("sort_min", C.c_int32), ("warp_lookup_max", C.c_int32),
-                ("tail_max", C.c_int32), ("wide_windows", C.c_int32),
+                ("tail_max", C.c_int32), ("sparse_windows", C.c_int32),
                 ("group_lookup_max", C.c_int32), ("search", C.c_int32),
                 ("reserved", C.c_int32 * 2)]
 

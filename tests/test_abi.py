@@ -51,7 +51,7 @@ def test_default_options_without_gpu(built):
     assert opt.precision == gbmc.FP64 and opt.sort == 1 and opt.blocks_per_sm == 8
     assert opt.max_iterations == 4 * gbmc.MAX_FLIGHTS
     assert opt.sort_min == 4096 and opt.warp_lookup_max == 4096 and opt.tail_max == 4096
-    assert opt.group_lookup_max == 160000 and opt.search == 1 and opt.wide_windows == 0
+    assert opt.group_lookup_max == 160000 and opt.search == 1 and opt.sparse_windows == 0
     # the same sizes are static_asserts of the C side
     assert ctypes.sizeof(gbmc.Options) == 72
     assert ctypes.sizeof(gbmc.Geometry) == 104 and ctypes.sizeof(gbmc.Problem) == 136

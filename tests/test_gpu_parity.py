@@ -65,10 +65,10 @@ def test_drained_warps_hand_particles_on():
     assert st["flights"] == ref["counts"][oracle.S_FLIGHT]
 
 
-def test_lattice_fp32_wide_windows_parity():
+def test_lattice_fp32_sparse_windows_parity():
     # the binary32 lookup's 32-byte window loads give the same results
     p = synth.make_config(3, grid_scale=0.05)
-    _parity(p, 20_000, precision=gbmc.FP32, wide_windows=1)
+    _parity(p, 20_000, precision=gbmc.FP32, sparse_windows=1)
 
 
 def test_slab_parity():
@@ -239,20 +239,47 @@ def _edge_energies(prob, mat):
     return np.ascontiguousarray(E[E > 0.0])
 
 
-@pytest.mark.parametrize("search", [1, -1])
+def _clustered_problem():
+    """Grids with tight clusters of points (30 within a relative width of
+    3e-4) beside log-spaced points: coarse-index buckets that hold many
+    points, so the window searches fall back to bisection there."""
+    base = synth.make_tiny_problem(seed=13, n_nuc=4, n_points=(40, 80))
+    en, sg, off = [], [], [0]
+    rng = np.random.default_rng(5)
+    for i in range(base.n_nuc):
+        c = float(np.exp(rng.uniform(np.log(1.0), np.log(1e5))))
+        e = np.concatenate([np.geomspace(1e-5, 2e7, 50), c * (1.0 + 1e-5 * np.arange(30))])
+        e = synth.problem._grid(e)
+        en.append(e)
+        sg.append(rng.uniform(1.0, 50.0, len(e)))
+        off.append(off[-1] + len(e))
+    import dataclasses
+    return dataclasses.replace(base, grid_off=np.array(off, np.int64), energy=np.concatenate(en),
+                               sigma_t=np.concatenate(sg))
+
+
+@pytest.mark.parametrize("form", ["index", "plain", "sparse"])
 @pytest.mark.parametrize("precision", [gbmc.FP64, gbmc.FP32])
-@pytest.mark.parametrize("which", ["dense", "sparse"])
-def test_lookup_macro_at_grid_points_and_edges(precision, which, search):
+@pytest.mark.parametrize("which", ["dense", "sparse", "clustered"])
+def test_lookup_macro_at_grid_points_and_edges(precision, which, form):
     """Exact hits (E - E_k = 0), neighbours, extrapolation outside the grids;
     dense grids take the integer-unit interpolation, the sparse ones (2-9
-    points over 12 decades: intervals wider than 2^10) its binary64 fallback."""
+    points over 12 decades: intervals wider than 2^10) its binary64 fallback,
+    the clustered ones the window searches' bisection fallback.  Forms: the
+    coarse index, a plain binary search, and (binary32) the short windows."""
     import torch
+    if form == "sparse" and precision == gbmc.FP64:
+        pytest.skip("short windows are a binary32 form")
     if which == "dense":
         prob, _, _ = synth.make_stress_lookup(n_queries=1, n_nuc=12, n_in_mat=8, n_points=400)
-    else:
+    elif which == "sparse":
         prob = synth.make_tiny_problem(seed=11, n_nuc=6, n_points=(2, 9))
+    else:
+        prob = _clustered_problem()
     E = _edge_energies(prob, 0)
-    ctx = make_ctx(prob, (precision,), search=search)
+    opts = {"index": dict(search=1), "plain": dict(search=-1),
+            "sparse": dict(search=1, sparse_windows=1)}[form]
+    ctx = make_ctx(prob, (precision,), **opts)
     try:
         dE = torch.tensor(E, device="cuda")
         dm = torch.zeros(len(E), dtype=torch.int32, device="cuda")
