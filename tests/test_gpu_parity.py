@@ -105,6 +105,32 @@ def test_thread_and_warp_lookup_modes_agree_with_oracle(precision):
         assert_tallies_close(g, ref)
 
 
+@pytest.mark.parametrize("precision,sparse", [(gbmc.FP64, 0), (gbmc.FP32, 0), (gbmc.FP32, 1)])
+def test_lookup_modes_on_a_150_nuclide_material(precision, sparse):
+    """More nuclides than the warp-mode lookup's four lock-step rounds of 32
+    (a second pass of rounds, a ragged last round, every checkpoint), with
+    the absorption-rate tally on (the Sigma_a sums): thread, warp and tail
+    lookups against the oracle."""
+    p = synth.make_tiny_problem(seed=41, n_nuc=150, n_points=(20, 120), n_particles=3000)
+    ref = oracle.run(p, seed=p.seed, n=3000, precision=precision)
+    for wmax, tmax in ((-1, -1), (1 << 30, -1), (-1, 1 << 22)):
+        ctx = make_ctx(p, (precision,), precision=precision, warp_lookup_max=wmax,
+                       tail_max=tmax, sparse_windows=sparse)
+        try:
+            ctx.set_reaction_tally(True)
+            g = run_gpu(ctx, gpu_problem(p, n=3000))
+            ra = ctx.read_reaction_tally(0)
+        finally:
+            ctx.close()
+        label = f"warp_lookup_max {wmax}, tail_max {tmax}"
+        assert_outcomes_equal(g, ref, label=label)
+        assert_tallies_close(g, ref, label=label)
+        zero = ref["absrate"] == 0
+        assert ref["absrate"].sum() > 0 and np.all(ra[zero] == 0), label
+        rel = np.abs(ra[~zero] - ref["absrate"][~zero]) / ref["absrate"][~zero]
+        assert rel.max() <= 1e-12, (label, rel.max())
+
+
 @pytest.mark.parametrize("tail_max", [-1, 4096, 1 << 22])
 def test_tail_kernel_threshold_does_not_change_outcomes(tail_max):
     # -1: the event loop runs to the end; 1 << 22: once the source is
