@@ -889,40 +889,28 @@ def main():
     def pinned(shape, dtype):
         return torch.empty(shape, dtype=dtype, pin_memory=True).numpy()
 
-    # result buffers in pinned host memory, allocated once
-    hosts = []
-    for slot in range(n_geo):
+    # result buffers in pinned host memory, one set per e2e batch and problem
+    # (the copies of all batches are in flight together), allocated before
+    # the timed region
+    def dest(slot):
         nc = gbmc._n_cells(geoms[slot])
-        tal = (pinned((nc, prob.n_bins), torch.float64), pinned(gbmc.NSCAL, torch.int64),
-               pinned(gbmc.NSCAL, torch.float64))
         m = counts[slot]
-        outc = dict(n_coll=pinned(m, torch.int32), status=pinned(m, torch.int8),
-                    n_flights=pinned(m, torch.int32), n_draws=pinned(m, torch.int32).view(np.uint32),
-                    E=pinned(m, torch.float64), x=pinned(m, torch.float64),
-                    y=pinned(m, torch.float64), z=pinned(m, torch.float64))
-        hosts.append((tal, outc))
+        return dict(flux=pinned(nc * prob.n_bins, torch.float64), counts=pinned(gbmc.NSCAL, torch.int64),
+                    weights=pinned(gbmc.NSCAL, torch.float64), n_coll=pinned(m, torch.int32),
+                    status=pinned(m, torch.int8), n_flights=pinned(m, torch.int32),
+                    n_draws=pinned(m, torch.int32).view(np.uint32), E=pinned(m, torch.float64),
+                    x=pinned(m, torch.float64), y=pinned(m, torch.float64), z=pinned(m, torch.float64))
+    e2e_probs = [pr for k in range(e2e_steps) for pr in problems(20_000 + k)]
+    dests = [dest(i % n_geo) for i in range(len(e2e_probs))]
+    d2h = sum(a.nbytes for d in dests for a in d.values()) // e2e_steps
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    d2h = 0
-    if loops > 1:
-        # all e2e batches in one concurrent call, then every batch's tallies
-        # and outcomes read back (per step: one batch's worth)
-        ctx.run_concurrent([pr for k in range(e2e_steps) for pr in problems(20_000 + k)],
-                           n_loops=loops, per_run=n_geo, stream=stream)
-        for k in range(e2e_steps):
-            d2h = 0
-            for slot in range(n_geo):
-                fl, cn, wt = ctx.read_tallies(k * n_geo + slot, out=hosts[slot][0])
-                o = ctx.read_outcomes(k * n_geo + slot, 0, counts[slot], out=hosts[slot][1])
-                d2h += fl.nbytes + cn.nbytes + wt.nbytes + sum(o[f].nbytes for f in o)
-    else:
-        for k in range(e2e_steps):
-            ctx.run_problems(problems(20_000 + k), stream)
-            d2h = 0
-            for slot in range(n_geo):
-                fl, cn, wt = ctx.read_tallies(slot, out=hosts[slot][0])
-                o = ctx.read_outcomes(slot, 0, counts[slot], out=hosts[slot][1])
-                d2h += fl.nbytes + cn.nbytes + wt.nbytes + sum(o[f].nbytes for f in o)
+    # the e2e batches through the C ABI with host destinations: each run's
+    # tallies and outcomes are copied to pinned host memory as soon as it
+    # ends, overlapping the runs still going (one loop: the next batch)
+    ctx.run_concurrent_to_host(e2e_probs, n_loops=loops, dests=dests, per_run=n_geo,
+                               stream=stream)
+    stream.synchronize()
     e2e_s = time.perf_counter() - t0
     h2d = ctypes.sizeof(gbmc.Problem) * n_geo
 

@@ -285,6 +285,38 @@ int gbmc_run_problems(gbmc_ctx *ctx, int32_t n_prob, const gbmc_problem *probs,
 int gbmc_run_concurrent(gbmc_ctx *ctx, int32_t n_prob, const gbmc_problem *probs,
                         int32_t n_loops, int32_t per_run, void *stream);
 
+/* Host destination of one problem's results for
+ * gbmc_run_concurrent_to_host: HOST arrays (pinned -- cudaHostAlloc or
+ * cudaHostRegister -- for the copies to run asynchronously; a pageable one
+ * makes its copy block the calling thread until the run has ended).  Any
+ * pointer may be NULL (that part is not copied).  flux [n_cells * n_bins]
+ * (cell-major), counts and weights [GBMC_NSCAL] (as gbmc_read_tallies gives
+ * them), and the problem's per-particle outcomes [n_particles] each (as
+ * gbmc_read_outcomes gives them for first 0). */
+typedef struct {
+    double *flux;
+    int64_t *counts;
+    double *weights;
+    int32_t *n_coll;
+    int8_t *status;
+    int32_t *n_flights;
+    uint32_t *n_draws;
+    double *E, *x, *y, *z;
+} gbmc_host_results;
+
+/* gbmc_run_concurrent, and each run's results copied to the host as soon as
+ * that run has ended: a loop's copies go on a copy stream of the loop's own,
+ * so they overlap its next run and the other loops' work (the overlap of
+ * transfers with compute the paper's streams give).  dst[p] (HOST array of
+ * n_prob) receives problem p's tallies (slot p) and outcomes.  Asynchronous
+ * on `stream`: the host arrays hold the results once `stream` has passed the
+ * call (e.g. cudaStreamSynchronize).  Errors a run flags on the device are
+ * reported by the next gbmc_read_stats / gbmc_read_tallies.  dst NULL:
+ * INVALID_ARG; other errors as gbmc_run_concurrent. */
+int gbmc_run_concurrent_to_host(gbmc_ctx *ctx, int32_t n_prob, const gbmc_problem *probs,
+                                int32_t n_loops, int32_t per_run, const gbmc_host_results *dst,
+                                void *stream);
+
 /* Synchronize the last run's stream and copy the tallies of problem slot
  * `slot`: flux [n_cells * n_bins] (cell-major; n_flux must equal it; NULL
  * skips), counts [GBMC_NSCAL] and weights [GBMC_NSCAL] (NULL skips).

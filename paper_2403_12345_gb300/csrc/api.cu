@@ -187,6 +187,9 @@ struct gbmc_ctx {
     bool borrowed = false;           // this context is such a loop
     cudaStream_t own_stream = nullptr;
     cudaEvent_t done_ev = nullptr;   // the loop's last run of a call
+    cudaStream_t copy_stream = nullptr;   // its runs' results to the host
+    cudaEvent_t run_ev = nullptr;         // end of its latest run (the copies wait for it)
+    cudaEvent_t copied_ev = nullptr;      // its last copies of a call
     std::vector<gbmc_ctx*> loops;
     int32_t last_loops = 0;          // loops the last run call used (0: this context's own loop)
 
@@ -909,6 +912,9 @@ int gbmc_destroy(gbmc_ctx* c) {
     if (c->h_stats) cudaFreeHost(c->h_stats);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     if (c->done_ev) cudaEventDestroy(c->done_ev);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    if (c->run_ev) cudaEventDestroy(c->run_ev);
+    if (c->copied_ev) cudaEventDestroy(c->copied_ev);
     if (c->staged) cudaEventDestroy(c->staged);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
@@ -1439,8 +1445,51 @@ int gbmc_run_problems(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, vo
     return rc;
 }
 
+// The device-to-host copies of problem p's results (its outcomes at base
+// start and its tally slot p) on stream s.
+static int copy_results(gbmc_ctx* c, int32_t p, int64_t start, int64_t n,
+                        const gbmc_host_results& d, cudaStream_t s) {
+    auto cp = [&](void* dst, const void* src, size_t bytes) -> int {
+        if (!dst || !bytes) return GBMC_OK;
+        CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s));
+        return GBMC_OK;
+    };
+    const Outcomes& O = c->O;
+    const size_t m = (size_t)n;
+    int rc = 0;
+    rc |= cp(d.n_coll, O.ncoll + start, sizeof(int32_t) * m);
+    rc |= cp(d.status, O.status + start, sizeof(int8_t) * m);
+    rc |= cp(d.n_flights, O.nflt + start, sizeof(int32_t) * m);
+    rc |= cp(d.n_draws, O.ndraw + start, sizeof(uint32_t) * m);
+    rc |= cp(d.E, O.E + start, sizeof(double) * m);
+    rc |= cp(d.x, O.x + start, sizeof(double) * m);
+    rc |= cp(d.y, O.y + start, sizeof(double) * m);
+    rc |= cp(d.z, O.z + start, sizeof(double) * m);
+    rc |= cp(d.flux, c->Y.flux + c->slot_flux_off[p],
+             sizeof(double) * (size_t)c->slot_cells[p] * (size_t)c->n_bins);
+    rc |= cp(d.counts, c->Y.counts + (size_t)p * GBMC_NSCAL, sizeof(int64_t) * GBMC_NSCAL);
+    rc |= cp(d.weights, c->Y.weights + (size_t)p * GBMC_NSCAL, sizeof(double) * GBMC_NSCAL);
+    return rc;
+}
+
+static int run_concurrent(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, int32_t n_loops,
+                          int32_t per_run, const gbmc_host_results* dst, void* stream);
+
 int gbmc_run_concurrent(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, int32_t n_loops,
                         int32_t per_run, void* stream) {
+    return run_concurrent(c, n_prob, probs, n_loops, per_run, nullptr, stream);
+}
+
+int gbmc_run_concurrent_to_host(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs,
+                                int32_t n_loops, int32_t per_run, const gbmc_host_results* dst,
+                                void* stream) {
+    if (!c) return GBMC_ERR_INVALID_ARG;
+    if (!dst) return fail(c, GBMC_ERR_INVALID_ARG, "dst required");
+    return run_concurrent(c, n_prob, probs, n_loops, per_run, dst, stream);
+}
+
+static int run_concurrent(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, int32_t n_loops,
+                          int32_t per_run, const gbmc_host_results* dst, void* stream) {
     if (!c) return GBMC_ERR_INVALID_ARG;
     if (c->borrowed) return fail(c, GBMC_ERR_UNSUPPORTED, "a concurrent loop runs no loops itself");
     if (n_prob < 1 || !probs) return fail(c, GBMC_ERR_INVALID_ARG, "n_prob >= 1 and probs required");
@@ -1486,6 +1535,9 @@ int gbmc_run_concurrent(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, 
         l->borrowed = true;
         cudaError_t e = cudaStreamCreateWithFlags(&l->own_stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&l->done_ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&l->copy_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&l->run_ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&l->copied_ev, cudaEventDisableTiming);
         if (e != cudaSuccess) {
             gbmc_destroy(l);
             return fail(c, GBMC_ERR_CUDA, "concurrent loop stream: %s", cudaGetErrorString(e));
@@ -1514,13 +1566,26 @@ int gbmc_run_concurrent(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, 
         }
         RunLayout lay{fo.data(), ob.data(), sl.data(), r >= n_loops};
         erc = launch_run(l, np, probs + p0, l->own_stream, &lay);
-        if (erc) c->err = std::string("concurrent loop ") + std::to_string(r % n_loops) + ": " + l->err;
+        if (erc) {
+            c->err = std::string("concurrent loop ") + std::to_string(r % n_loops) + ": " + l->err;
+        } else if (dst) {
+            // this run's results to the host on the loop's copy stream: they
+            // overlap the loop's next run and the other loops
+            CK(cudaEventRecord(l->run_ev, l->own_stream));
+            CK(cudaStreamWaitEvent(l->copy_stream, l->run_ev, 0));
+            for (int32_t k = 0; k < np && erc == GBMC_OK; ++k)
+                erc = copy_results(c, p0 + k, start[p0 + k], nn[p0 + k], dst[p0 + k], l->copy_stream);
+        }
     }
-    // join: `stream` waits for every loop (also after a failed launch, so
-    // that nothing a loop queued outlives the call unseen)
+    // join: `stream` waits for every loop and its copies (also after a
+    // failed launch, so that nothing a loop queued outlives the call unseen)
     for (int32_t j = 0; j < used; ++j) {
         CK(cudaEventRecord(c->loops[j]->done_ev, c->loops[j]->own_stream));
         CK(cudaStreamWaitEvent(s, c->loops[j]->done_ev, 0));
+        if (dst) {
+            CK(cudaEventRecord(c->loops[j]->copied_ev, c->loops[j]->copy_stream));
+            CK(cudaStreamWaitEvent(s, c->loops[j]->copied_ev, 0));
+        }
     }
     CK(cudaEventRecord(c->ev1, s));
     c->ran = true;

@@ -41,7 +41,8 @@ EXPORTS = ["gbmc_default_options", "gbmc_create", "gbmc_destroy", "gbmc_last_err
            "gbmc_importance_accumulate", "gbmc_importance_training_set",
            "gbmc_get_weight_windows", "gbmc_set_reaction_tally", "gbmc_read_reaction_tally",
            "gbmc_load_fission", "gbmc_set_eigen", "gbmc_read_bank", "gbmc_set_source_bank",
-           "gbmc_check_division", "gbmc_run_concurrent", "gbmc_measure_fp64_rate"]
+           "gbmc_check_division", "gbmc_run_concurrent", "gbmc_measure_fp64_rate",
+           "gbmc_run_concurrent_to_host"]
 MLP_HIDDEN = 64
 MLP_NPARAM = 4545
 NOALLOC_MAX_QUERIES = 1 << 20
@@ -72,6 +73,23 @@ class Geometry(C.Structure):
                 ("mat_pin", C.c_int32), ("mat_mod", C.c_int32), ("bc_side", C.c_int32),
                 ("bc_z", C.c_int32), ("n_layers", C.c_int32), ("layer_dx", C.c_double),
                 ("n_first", C.c_int32), ("mat_a", C.c_int32), ("mat_b", C.c_int32)]
+
+
+class HostResults(C.Structure):
+    """gbmc_host_results: host destinations of one problem's results."""
+    _fields_ = [("flux", C.c_void_p), ("counts", C.c_void_p), ("weights", C.c_void_p),
+                ("n_coll", C.c_void_p), ("status", C.c_void_p), ("n_flights", C.c_void_p),
+                ("n_draws", C.c_void_p), ("E", C.c_void_p), ("x", C.c_void_p), ("y", C.c_void_p),
+                ("z", C.c_void_p)]
+
+
+# dtype of each HostResults field and whether it has one entry per particle
+# (else: flux [cells * bins], counts / weights [NSCAL])
+_RESULT_FIELDS = {"flux": (np.float64, None), "counts": (np.int64, None),
+                  "weights": (np.float64, None), "n_coll": (np.int32, True),
+                  "status": (np.int8, True), "n_flights": (np.int32, True),
+                  "n_draws": (np.uint32, True), "E": (np.float64, True),
+                  "x": (np.float64, True), "y": (np.float64, True), "z": (np.float64, True)}
 
 
 class Problem(C.Structure):
@@ -124,6 +142,8 @@ def lib():
         L.gbmc_run_batch.argtypes = [vp, _P(Problem), vp]
         L.gbmc_run_problems.argtypes = [vp, C.c_int32, _P(Problem), vp]
         L.gbmc_run_concurrent.argtypes = [vp, C.c_int32, _P(Problem), C.c_int32, C.c_int32, vp]
+        L.gbmc_run_concurrent_to_host.argtypes = [vp, C.c_int32, _P(Problem), C.c_int32, C.c_int32,
+                                                  _P(HostResults), vp]
         L.gbmc_measure_fp64_rate.argtypes = [vp, _P(C.c_double)]
         L.gbmc_read_tallies.argtypes = [vp, C.c_int32, _P(C.c_double), C.c_int64,
                                         _P(C.c_int64), _P(C.c_double)]
@@ -397,6 +417,35 @@ class Context:
         arr = (Problem * len(probs))(*probs)
         self._ck(lib().gbmc_run_concurrent(self._h, len(probs), arr, int(n_loops), int(per_run),
                                            _stream(stream)))
+        self._cells = [_n_cells(p.geom) for p in probs]
+
+    def run_concurrent_to_host(self, probs, n_loops: int, dests, per_run: int = 1, stream=None):
+        """gbmc_run_concurrent_to_host: run_concurrent, each run's results
+        copied to the host as soon as it ends.  dests[p] is a dict with any of
+        the keys flux, counts, weights, n_coll, status, n_flights, n_draws, E,
+        x, y, z, each a C-contiguous numpy array (pinned memory for the copies
+        to overlap the work) of the dtype and size read_tallies / read_outcomes
+        give for problem p; the arrays hold the results once `stream` has
+        passed the call.  The arrays must stay alive until then."""
+        if len(dests) != len(probs):
+            raise ValueError("one destination per problem")
+        arr = (Problem * len(probs))(*probs)
+        dst = (HostResults * len(probs))()
+        for p, (pr, d) in enumerate(zip(probs, dests)):
+            cells = _n_cells(pr.geom)
+            for name, a in d.items():
+                if name not in _RESULT_FIELDS:
+                    raise KeyError(name)
+                dt, per_particle = _RESULT_FIELDS[name]
+                want = (pr.n_particles if per_particle else
+                        cells * self.n_bins if name == "flux" else NSCAL)
+                if (not isinstance(a, np.ndarray) or a.dtype != dt or a.size != want
+                        or not a.flags["C_CONTIGUOUS"]):
+                    raise TypeError(f"problem {p}: {name} must be a C-contiguous {np.dtype(dt)} "
+                                    f"array of {want}")
+                setattr(dst[p], name, a.ctypes.data)
+        self._ck(lib().gbmc_run_concurrent_to_host(self._h, len(probs), arr, int(n_loops),
+                                                   int(per_run), dst, _stream(stream)))
         self._cells = [_n_cells(p.geom) for p in probs]
 
     def profile_problems(self, probs, stream=None, trace_cap: int = 0):

@@ -55,6 +55,7 @@ def test_default_options_without_gpu(built):
     # the same sizes are static_asserts of the C side
     assert ctypes.sizeof(gbmc.Options) == 72
     assert ctypes.sizeof(gbmc.Geometry) == 104 and ctypes.sizeof(gbmc.Problem) == 136
+    assert ctypes.sizeof(gbmc.HostResults) == 11 * 8   # gbmc_host_results: 11 pointers
 
 
 def test_create_without_gpu_fails_cleanly(built):

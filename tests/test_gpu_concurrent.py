@@ -77,3 +77,60 @@ def test_concurrent_refuses_single_loop_features():
         assert ex.value.code == gbmc.ERR_INVALID_ARG
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("n_loops,pinned", [(3, True), (1, True), (2, False)])
+def test_concurrent_results_copied_to_host(n_loops, pinned):
+    """gbmc_run_concurrent_to_host: each run's outcomes and tallies reach the
+    host arrays (pinned, or pageable) once the stream has passed the call,
+    equal to the oracle and to what the synchronous readers return; a
+    destination with only some arrays copies only those."""
+    import torch
+    p = synth.make_config(4, n_problems=5, grid_scale=0.02)
+    for k in range(5):
+        p.n_particles[k] = 1200 + 517 * k
+    ctx = make_ctx(p, (gbmc.FP32,), precision=gbmc.FP32)
+
+    def host(n, dtype):
+        if pinned:
+            tdt = {np.float64: torch.float64, np.int64: torch.int64, np.int32: torch.int32,
+                   np.int8: torch.int8, np.uint32: torch.int32}[dtype]
+            a = torch.zeros(n, dtype=tdt, pin_memory=True).numpy()
+            return a.view(np.uint32) if dtype is np.uint32 else a
+        return np.zeros(n, dtype)
+
+    try:
+        probs = [gpu_problem(p, geom_index=k, problem_index=k, batch=5) for k in range(5)]
+        dests = []
+        for k, pr in enumerate(probs):
+            nc = gbmc._n_cells(pr.geom)
+            n = p.n_particles[k]
+            d = dict(flux=host(nc * ctx.n_bins, np.float64), counts=host(gbmc.NSCAL, np.int64),
+                     weights=host(gbmc.NSCAL, np.float64))
+            if k != 2:   # problem 2: tallies only
+                d.update(n_coll=host(n, np.int32), status=host(n, np.int8),
+                         n_flights=host(n, np.int32), n_draws=host(n, np.uint32),
+                         E=host(n, np.float64), x=host(n, np.float64), y=host(n, np.float64),
+                         z=host(n, np.float64))
+            dests.append(d)
+        stream = torch.cuda.Stream()
+        ctx.run_concurrent_to_host(probs, n_loops=n_loops, dests=dests, stream=stream)
+        stream.synchronize()
+        for k in range(5):
+            ref = oracle.run(p, seed=p.seed, batch=5, geom_index=k, problem_index=k, precision=1)
+            d = dests[k]
+            nc = gbmc._n_cells(probs[k].geom)
+            got = dict(flux=d["flux"].reshape(nc, ctx.n_bins), counts=d["counts"],
+                       weights=d["weights"])
+            assert_tallies_close(got, ref, label=f"problem {k}")
+            flux, counts, weights = ctx.read_tallies(k)
+            assert np.array_equal(flux.ravel(), d["flux"]) and np.array_equal(counts, d["counts"])
+            assert np.array_equal(weights, d["weights"])
+            if k != 2:
+                assert_outcomes_equal(d, ref, label=f"problem {k}")
+        with pytest.raises(TypeError):   # a destination of the wrong size
+            bad = [dict(dests[0]) for _ in probs]
+            bad[0]["E"] = np.zeros(3)
+            ctx.run_concurrent_to_host(probs, n_loops=2, dests=bad)
+    finally:
+        ctx.close()
