@@ -154,16 +154,16 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def traffic_key(config, precision, wide):
-    return f"config{config}-{'fp32' if precision == 1 else 'fp64'}-w{int(wide)}"
+def traffic_key(config, precision, sparse):
+    return f"config{config}-{'fp32' if precision == 1 else 'fp64'}-w{int(sparse)}"
 
 
-def recorded_traffic(config, precision, wide):
+def recorded_traffic(config, precision, sparse):
     """The recorded lookup traffic of this workload, or None (no record, or
     one taken on other kernel sources)."""
     try:
         with open(TRAFFIC_FILE) as f:
-            rec = json.load(f).get(traffic_key(config, precision, wide))
+            rec = json.load(f).get(traffic_key(config, precision, sparse))
     except (OSError, ValueError):
         return None
     if not rec or rec.get("kernel_sha") != kernel_source_sha():
@@ -171,7 +171,7 @@ def recorded_traffic(config, precision, wide):
     return rec
 
 
-def record_traffic(csv_path, config, precision, wide, command):
+def record_traffic(csv_path, config, precision, sparse, command):
     """Sums the DRAM and L2 bytes of every lookup launch in an ncu CSV log
     (metrics dram__bytes_read.sum, dram__bytes_write.sum, lts__t_bytes.sum)
     into TRAFFIC_FILE under this workload's key."""
@@ -198,13 +198,13 @@ def record_traffic(csv_path, config, precision, wide, command):
     if os.path.exists(TRAFFIC_FILE):
         with open(TRAFFIC_FILE) as f:
             data = json.load(f)
-    data[traffic_key(config, precision, wide)] = {
+    data[traffic_key(config, precision, sparse)] = {
         "dram_bytes_per_batch": dram, "l2_bytes_per_batch": tot.get("lts__t_bytes.sum"),
         "launches": len(launches), "kernel_sha": kernel_source_sha(), "command": command}
     with open(TRAFFIC_FILE, "w") as f:
         json.dump(data, f, indent=1, sort_keys=True)
         f.write("\n")
-    print(json.dumps(data[traffic_key(config, precision, wide)]))
+    print(json.dumps(data[traffic_key(config, precision, sparse)]))
 
 
 def compare_outcomes(gpu, ref):

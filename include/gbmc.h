@@ -412,9 +412,11 @@ int gbmc_read_stats(gbmc_ctx *ctx, gbmc_stats *out);
  *   is not in [0, n_mat) gets NaN in both outputs and reads no table.  The
  *   four arrays must each hold n elements of these types; the library cannot
  *   check device buffers, so shorter ones are read or written out of bounds.
- * precision selects the loaded table copy.  sort = 1 sorts the queries by
- * (material, energy) into context-owned scratch first (results are written
- * back in query order).  Asynchronous on `stream`. */
+ * precision selects the loaded table copy; binary32 lookups search the
+ * window form the context's sparse_windows option selects (same results).
+ * sort = 1 sorts the queries by (material, energy) into context-owned
+ * scratch first (results are written back in query order).  Asynchronous
+ * on `stream`. */
 int gbmc_lookup_macro(gbmc_ctx *ctx, int32_t precision, const double *d_E,
                       const int32_t *d_mat, int64_t n, double *d_sigma_t,
                       double *d_sigma_a, int32_t sort, void *stream);
