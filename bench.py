@@ -825,9 +825,11 @@ def main():
         _, loops, bps = best
         ctx.set_options(blocks_per_sm=bps)
     if loops > 1:
-        # one untimed round at the chosen setting: each loop builds its graph
-        # for it (a warm-up step of the timed configuration)
-        ctx.run_concurrent([pr for b in range(loops) for pr in problems(60_000 + b)],
+        # one untimed call of the timed configuration (as many batches on as
+        # many loops): the context sizes its outcome and tally buffers for
+        # the call, and each loop builds its graph on them, outside the timed
+        # region
+        ctx.run_concurrent([pr for b in range(args.steps) for pr in problems(60_000 + b)],
                            n_loops=loops, per_run=n_geo, stream=stream)
         torch.cuda.synchronize()
     ctx.reset_tallies(stream)
