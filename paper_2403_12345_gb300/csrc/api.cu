@@ -369,8 +369,14 @@ int ensure_cum(gbmc_ctx* c) {
     return GBMC_OK;
 }
 
+// Buffers that the run's size sets grow by at least half their size, so that
+// calls of slowly growing size do not reallocate them (and rebuild every
+// loop's graph, whose launch parameters hold their addresses) each time.
+static int64_t grown(int64_t need, int64_t cap) { return std::max(need, cap + cap / 2); }
+
 int ensure_outcomes(gbmc_ctx* c, int64_t n) {
     if (n <= c->out_cap) return GBMC_OK;
+    n = grown(n, c->out_cap);
     Outcomes& O = c->O;
     int rc = 0;
     rc |= dalloc(c, &O.ncoll, n); rc |= dalloc(c, &O.status, n); rc |= dalloc(c, &O.nflt, n);
@@ -396,9 +402,10 @@ int ensure_tallies(gbmc_ctx* c, const std::vector<int32_t>& cells, cudaStream_t 
         tot += (int64_t)cells[p] * c->n_bins;
     }
     if (tot > c->flux_cap || !c->Y.flux) {
-        int rc = dalloc(c, &c->Y.flux, (size_t)tot);
+        const int64_t cap = grown(std::max<int64_t>(tot, 1), c->flux_cap);
+        int rc = dalloc(c, &c->Y.flux, (size_t)cap);
         if (rc) return rc;
-        c->flux_cap = tot;
+        c->flux_cap = cap;
         c->graph_valid = false;
         if (c->Y.absrate) {
             dfree(c->Y.absrate);
@@ -412,10 +419,11 @@ int ensure_tallies(gbmc_ctx* c, const std::vector<int32_t>& cells, cudaStream_t 
     }
     int32_t ns = (int32_t)cells.size();
     if (ns > c->slots_cap || !c->Y.counts) {
-        int rc = dalloc(c, &c->Y.counts, (size_t)ns * GBMC_NSCAL);
-        rc |= dalloc(c, &c->Y.weights, (size_t)ns * GBMC_NSCAL);
+        const int32_t cap = (int32_t)grown(ns, c->slots_cap);
+        int rc = dalloc(c, &c->Y.counts, (size_t)cap * GBMC_NSCAL);
+        rc |= dalloc(c, &c->Y.weights, (size_t)cap * GBMC_NSCAL);
         if (rc) return GBMC_ERR_OOM;
-        c->slots_cap = ns;
+        c->slots_cap = cap;
         c->graph_valid = false;
     }
     CK(cudaMemsetAsync(c->Y.flux, 0, sizeof(double) * (size_t)(tot ? tot : 1), s));
