@@ -885,8 +885,9 @@ def main():
 
     # end to end through the C ABI with host buffers: run, then copy every
     # problem's tallies and every particle's outcome (collisions, fate) to
-    # the host
-    e2e_steps = max(1, args.e2e_steps)
+    # the host; at least one batch per loop, so the loops run as concurrently
+    # as in the timed region
+    e2e_steps = max(1, args.e2e_steps, min(loops, args.steps))
 
     def pinned(shape, dtype):
         return torch.empty(shape, dtype=dtype, pin_memory=True).numpy()
