@@ -1,6 +1,5 @@
-"""Pins of the oracle's binary32-table mode (the reduced-precision lookup of
-the north-star precision item; the paper's lookup itself, Sec. 2 "Sorting",
-is binary64).
+"""Pins of the oracle's binary32-table mode (a reduced-precision variant of
+the lookup; the paper's lookup itself, Sec. 2 "Sorting", is binary64).
 
 What the mode states: each grid energy and cross section is rounded to the
 nearest binary32 value; the bracket of E is the largest j <= n-2 with
