@@ -61,6 +61,47 @@ WORKLOADS = {
 }
 
 
+def bf16_peak():
+    """The measured dense bf16 tensor rate (TFLOP/s, burst) and its source."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def mlp_forward_measure(ctx, stream, rows=1 << 24, reps=5):
+    """The importance network's forward (gbmc_mlp_forward: the 64 x 64 layer
+    on the tensor cores) over `rows` feature rows, timed with CUDA events
+    after three warm-up calls: rows/s, the network's flops against the
+    measured bf16 rate, and its 20 bytes a row against measured HBM."""
+    import torch
+    feat = torch.rand((rows, 4), dtype=torch.float32, device="cuda")
+    out = torch.empty(rows, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        ctx.mlp_forward(feat, out, stream)
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.mlp_forward(feat, out, stream)
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    ms = statistics.median(ts)
+    flops = 2 * (4 * 64 + 64 * 64 + 64 * 1) * rows
+    tensor = 2 * 64 * 64 * rows
+    peak, src = bf16_peak()
+    hbm, hsrc = peaks()
+    return {"rows": rows, "ms": ms, "rows_per_s": rows / (ms * 1e-3),
+            "tflops_all_layers": flops / (ms * 1e-3) / 1e12,
+            "tensor_tflops": tensor / (ms * 1e-3) / 1e12,
+            "tensor_frac": tensor / (ms * 1e-3) / 1e12 / peak, "bf16_peak": peak,
+            "bf16_peak_source": src,
+            "hbm_gbs": 20 * rows / (ms * 1e-3) / 1e9, "hbm_frac": 20 * rows / (ms * 1e-3) / 1e9 / hbm,
+            "timing": "CUDA events, median of 5 calls"}
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -641,6 +682,7 @@ def run_windows(args, prob, rank, world, local):
     e2e = n_ww * e2e_steps / (time.perf_counter() - t0)
     ctx.clear_weight_windows()
     fa = imp.figure_of_merit(ctx, analog, range(3000, 3020), n_an, stream)
+    mlp = mlp_forward_measure(ctx, stream)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         threads = len(os.sched_getaffinity(0))
@@ -664,6 +706,7 @@ def run_windows(args, prob, rank, world, local):
                     "learned_leak_far": [fw["mean"], fw["mean"] * fw["rel_err"]],
                     "z": (fw["mean"] - fa["mean"]) / se if se > 0 else None,
                     "batches": 20, "train_loss": loss, "setup_s": setup_s},
+            "mlp_forward": mlp,
             "e2e": {"value": e2e, "unit": "particles/s",
                     "h2d_bytes_per_step": ctypes.sizeof(gbmc.Problem),
                     "d2h_bytes_per_step": int(flux.nbytes + 16 * gbmc.NSCAL)},
@@ -713,6 +756,10 @@ def main():
                     help="binary32 window form (0: 64-byte windows, 1: short windows) of the "
                          "lookup-only stress set (config 6), and with --profile-batch or "
                          "--record-traffic of the captured batch")
+    ap.add_argument("--mlp-forward-only", action="store_true",
+                    help="time the importance network's tensor-core forward alone (random "
+                         "BF16 weights, 2^24 random feature rows) and exit: the command an ncu "
+                         "capture of that kernel wraps")
     ap.add_argument("--ncu-command", default="",
                     help="with --record-traffic: the capture command, kept with the record")
     args = ap.parse_args()
@@ -726,6 +773,18 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
+    if args.mlp_forward_only:
+        import torch
+        from paper_2403_12345_gb300 import gbmc
+        torch.cuda.set_device(local)
+        ctx = gbmc.Context(local)
+        g = torch.Generator().manual_seed(7)
+        w = (torch.randn(gbmc.MLP_NPARAM, generator=g) * 0.2).to(torch.bfloat16)
+        ctx.set_importance_net(w.view(torch.int16).numpy().view(np.uint16), np.zeros(4), np.ones(4))
+        print(json.dumps({"mlp_forward": mlp_forward_measure(ctx, torch.cuda.current_stream())}),
+              flush=True)
+        ctx.close()
+        return
     if args.config == 6:
         run_stress(args, rank, world, local)
         return
