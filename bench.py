@@ -530,6 +530,9 @@ def run_stress(args, rank, world, local):
                        sparse=max(args.sparse_windows, 0))
     tot_ms = _max_over_ranks(sum(m["ms"]), world)
     value = nq * args.steps * world / (tot_ms * 1e-3)
+    # end to end, whole job: every rank's queries over the slowest rank's time
+    e2e_steps = max(1, args.e2e_steps)
+    e2e = nq * e2e_steps * world / _max_over_ranks(nq * e2e_steps / m["e2e"], world)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
@@ -549,7 +552,7 @@ def run_stress(args, rank, world, local):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if prec == 1 else "f64", "data": "synthetic", "config": cfg,
             "micro_lookups_per_s": value * micro_per,
-            "e2e": {"value": m["e2e"], "unit": "lookups/s", "h2d_bytes_per_step": nq * 8,
+            "e2e": {"value": e2e, "unit": "lookups/s", "h2d_bytes_per_step": nq * 8,
                     "d2h_bytes_per_step": nq * 16},
             "roofline": m["roofline"],
             "cpu_baseline": cpu, "clocks": m["clocks"],
@@ -679,7 +682,8 @@ def run_windows(args, prob, rank, world, local):
     for k in range(e2e_steps):
         ctx.run_batch(learned(2000 + k), stream)
         flux, _, _ = ctx.read_tallies(0)
-    e2e = n_ww * e2e_steps / (time.perf_counter() - t0)
+    # whole job: every rank's batches over the slowest rank's time
+    e2e = n_ww * e2e_steps * world / _max_over_ranks(time.perf_counter() - t0, world)
     ctx.clear_weight_windows()
     fa = imp.figure_of_merit(ctx, analog, range(3000, 3020), n_an, stream)
     mlp = mlp_forward_measure(ctx, stream)
@@ -966,6 +970,8 @@ def main():
     dests = [dest(i % n_geo) for i in range(len(e2e_probs))]
     d2h = sum(a.nbytes for d in dests for a in d.values()) // e2e_steps
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     t0 = time.perf_counter()
     # the e2e batches through the C ABI with host destinations: each run's
     # tallies and outcomes are copied to pinned host memory as soon as it
@@ -973,7 +979,8 @@ def main():
     ctx.run_concurrent_to_host(e2e_probs, n_loops=loops, dests=dests, per_run=n_geo,
                                stream=stream)
     stream.synchronize()
-    e2e_s = time.perf_counter() - t0
+    # whole job: every rank's batches over the slowest rank's time
+    e2e_s = _max_over_ranks(time.perf_counter() - t0, world)
     h2d = ctypes.sizeof(gbmc.Problem) * n_geo
 
     # per-kernel device times (eager launches between CUDA events) on one
@@ -1065,7 +1072,7 @@ def main():
             "micro_lookups_per_s": micro * world / (tot_ms * 1e-3),
             "iterations_per_step": iters / args.steps,
             "wall_s": wall,
-            "e2e": {"value": npart * e2e_steps / e2e_s, "unit": "particles/s",
+            "e2e": {"value": npart * e2e_steps * world / e2e_s, "unit": "particles/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "autotune": tuned,
             "concurrent_loops": {"loops": loops, "blocks_per_sm": run_bps,
