@@ -853,6 +853,11 @@ def main():
     tuned = None
     if args.autotune == 1 or (args.autotune < 0 and args.config in (2, 3, 4)):
         tuned = ctx.autotune(problems(40_000), fraction=0.1 if n_geo > 1 else 0.3, stream=stream)
+    # the settings of one event loop (the autotuner's): the per-kernel profile
+    # and the lookup roofline below run at them
+    o = ctx.options
+    single_opts = {"blocks_per_sm": int(o.blocks_per_sm), "tail_max": int(o.tail_max),
+                   "group_lookup_max": int(o.group_lookup_max)}
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     for w in range(args.warmup):
@@ -887,14 +892,57 @@ def main():
                     best = (t_steps, L, bps)
         _, loops, bps = best
         ctx.set_options(blocks_per_sm=bps)
+    conc_tune = None
     if loops > 1:
+        def full_call(base):
+            ctx.run_concurrent([pr for b in range(args.steps) for pr in problems(base + b)],
+                               n_loops=loops, per_run=n_geo, stream=stream)
+            torch.cuda.synchronize()
+
         # one untimed call of the timed configuration (as many batches on as
         # many loops): the context sizes its outcome and tally buffers for
         # the call, and each loop builds its graph on them, outside the timed
         # region
-        ctx.run_concurrent([pr for b in range(args.steps) for pr in problems(60_000 + b)],
-                           n_loops=loops, per_run=n_geo, stream=stream)
-        torch.cuda.synchronize()
+        full_call(60_000)
+        if args.loops == 0:
+            # the single-loop autotuner's settings, tuned again for concurrent
+            # loops (their late iterations overlap, which shifts the best
+            # thresholds): coordinate descent over blocks per SM, the tail
+            # threshold and (binary64) the group-lookup threshold, each
+            # candidate timed on one round of runs (a 1% gain to switch)
+            def round_rate(opts, rep):
+                ctx.set_options(**opts)
+                batch = [pr for b in range(loops) for pr in problems(70_000 + 10 * rep + b)]
+                ctx.run_concurrent(batch, n_loops=loops, per_run=n_geo, stream=stream)   # graphs
+                torch.cuda.synchronize()
+                a = torch.cuda.Event(enable_timing=True)
+                e = torch.cuda.Event(enable_timing=True)
+                batch = [pr for b in range(loops) for pr in problems(80_000 + 10 * rep + b)]
+                a.record(stream)
+                ctx.run_concurrent(batch, n_loops=loops, per_run=n_geo, stream=stream)
+                e.record(stream)
+                e.synchronize()
+                return loops * npart / (a.elapsed_time(e) * 1e-3)
+            o = ctx.options
+            cur = {"blocks_per_sm": o.blocks_per_sm, "tail_max": o.tail_max,
+                   "group_lookup_max": o.group_lookup_max}
+            cands = [("blocks_per_sm", (2, 3, 4)), ("tail_max", (1024, 4096, 16384))]
+            if args.precision == 0:
+                cands.append(("group_lookup_max", (60_000, 160_000)))
+            best_rate, trials, rep = round_rate(cur, 0), {}, 1
+            for key, vals in cands:
+                for v in vals:
+                    if v == cur[key]:
+                        continue
+                    trial = dict(cur, **{key: v})
+                    r = round_rate(trial, rep)
+                    rep += 1
+                    trials[f"{key}={v}"] = r
+                    if r > best_rate * 1.01:
+                        best_rate, cur = r, trial
+            ctx.set_options(**cur)
+            conc_tune = {"options": cur, "round_particles_per_s": best_rate, "trials": trials}
+            full_call(90_000)   # the graphs at the chosen settings, outside the timed region
     ctx.reset_tallies(stream)
 
     stats = []
@@ -984,7 +1032,9 @@ def main():
     h2d = ctypes.sizeof(gbmc.Problem) * n_geo
 
     # per-kernel device times (eager launches between CUDA events) on one
-    # more batch of the same workload
+    # more batch of the same workload, at one event loop's settings
+    timed_opts = {k: int(getattr(ctx.options, k)) for k in single_opts}
+    ctx.set_options(**single_opts)
     kt = ctx.profile_problems(problems(30_000), stream)
     pst = ctx.read_stats()
     top = max(kt, key=lambda k: kt[k][0])
@@ -998,14 +1048,14 @@ def main():
     l2_size = torch.cuda.get_device_properties(local).L2_cache_size
     roof = {"kernel": "lookup", "bound": "hbm", "achieved": lk_gbs, "peak": hbm, "unit": "GB/s",
             "frac": lk_gbs / hbm, "peak_source": peak_src,
-            # per lookup event of the batch, as `achieved` (the capture counts the
-            # thread- and warp-mode kernels of an event separately)
+            # per lookup event (one launch) of the batch, as `achieved`
             "traffic": tr["dram_bytes_per_batch"] / max(lk_n, 1) if tr else None,
             "l2_bytes": (tr["l2_bytes_per_batch"] / max(lk_n, 1)
                          if tr and tr.get("l2_bytes_per_batch") else None),
             "launches": lk_n, "avg_launch_ms": lk_ms / max(lk_n, 1),
             "algorithmic_bytes_per_launch": lk_bytes / max(lk_n, 1),
-            "timing": "CUDA events around each lookup launch of one eager batch of this workload",
+            "timing": "CUDA events around each lookup launch of one eager batch of this workload, "
+                      "at the single-loop autotuned settings",
             "table_bytes": int(prob.table_bytes(args.precision)), "l2_capacity": int(l2_size)}
     if args.precision == 0:
         # binary64 tables: the lookup is bound by the binary64 pipe (ncu: 73%
@@ -1023,6 +1073,16 @@ def main():
                      "algorithmic_ops_per_launch": ops / max(lk_n, 1),
                      "ops_per_micro_lookup": ALGO_FP64_OPS_PER_MICRO, "hbm": hbm_rec})
         del roof["algorithmic_bytes_per_launch"]
+    if timed_opts != single_opts:
+        # the same batch at the settings the concurrent loops were timed at
+        # (tuned for several loops whose late iterations overlap; one loop
+        # alone runs its lookups at them less efficiently)
+        ctx.set_options(**timed_opts)
+        kt2 = ctx.profile_problems(problems(30_000), stream)
+        ms2 = kt2["lookup"][0]
+        roof["at_timed_settings"] = {"settings": timed_opts, "lookup_ms_per_batch": ms2,
+                                     "frac": roof["frac"] * lk_ms / ms2}
+    ctx.set_options(**timed_opts)
 
     cpu = None
     parity = None
@@ -1077,6 +1137,7 @@ def main():
             "autotune": tuned,
             "concurrent_loops": {"loops": loops, "blocks_per_sm": run_bps,
                                  "trial_particles_per_s": loop_trials,
+                                 "concurrent_tuning": conc_tune,
                                  "how": "gbmc_run_concurrent: the steps' batches spread over this "
                                         "many event loops on their own streams (Sec. 2 'GPU "
                                         "Streams'); one loop: one graph launch per step"},
