@@ -910,23 +910,24 @@ def main():
             # thresholds): coordinate descent over blocks per SM, the tail
             # threshold and (binary64) the group-lookup threshold, each
             # candidate timed on one round of runs (a 1% gain to switch)
-            def round_rate(opts, rep):
+            def round_rate(opts, rep, n_loops=None):
+                n_loops = n_loops or loops
                 ctx.set_options(**opts)
-                batch = [pr for b in range(loops) for pr in problems(70_000 + 10 * rep + b)]
-                ctx.run_concurrent(batch, n_loops=loops, per_run=n_geo, stream=stream)   # graphs
+                batch = [pr for b in range(n_loops) for pr in problems(70_000 + 20 * rep + b)]
+                ctx.run_concurrent(batch, n_loops=n_loops, per_run=n_geo, stream=stream)   # graphs
                 torch.cuda.synchronize()
                 a = torch.cuda.Event(enable_timing=True)
                 e = torch.cuda.Event(enable_timing=True)
-                batch = [pr for b in range(loops) for pr in problems(80_000 + 10 * rep + b)]
+                batch = [pr for b in range(n_loops) for pr in problems(80_000 + 20 * rep + b)]
                 a.record(stream)
-                ctx.run_concurrent(batch, n_loops=loops, per_run=n_geo, stream=stream)
+                ctx.run_concurrent(batch, n_loops=n_loops, per_run=n_geo, stream=stream)
                 e.record(stream)
                 e.synchronize()
-                return loops * npart / (a.elapsed_time(e) * 1e-3)
+                return n_loops * npart / (a.elapsed_time(e) * 1e-3)
             o = ctx.options
             cur = {"blocks_per_sm": o.blocks_per_sm, "tail_max": o.tail_max,
                    "group_lookup_max": o.group_lookup_max}
-            cands = [("blocks_per_sm", (2, 3, 4)), ("tail_max", (1024, 4096, 16384))]
+            cands = [("blocks_per_sm", (1, 2, 3, 4)), ("tail_max", (1024, 4096, 16384))]
             if args.precision == 0:
                 cands.append(("group_lookup_max", (60_000, 160_000)))
             best_rate, trials, rep = round_rate(cur, 0), {}, 1
@@ -940,8 +941,22 @@ def main():
                     trials[f"{key}={v}"] = r
                     if r > best_rate * 1.01:
                         best_rate, cur = r, trial
+            # the loop count again at these settings (fewer blocks per loop
+            # leave room for more loops): ceil(steps / L) rounds of one
+            # round's time, more loops to gain 2%
+            best_t = -(-args.steps // loops) * npart * loops / best_rate
+            for L in (2, 3, 4, 5, 6, 7, 8, 10, 12):
+                if L == loops or L > args.steps:
+                    continue
+                r = round_rate(cur, rep, L)
+                rep += 1
+                trials[f"loops={L}"] = r
+                t_steps = -(-args.steps // L) * L * npart / r
+                if t_steps < best_t / (1.02 if L > loops else 1.0):
+                    best_t, loops = t_steps, L
             ctx.set_options(**cur)
-            conc_tune = {"options": cur, "round_particles_per_s": best_rate, "trials": trials}
+            conc_tune = {"options": cur, "loops": loops, "round_particles_per_s": best_rate,
+                         "trials": trials}
             full_call(90_000)   # the graphs at the chosen settings, outside the timed region
     ctx.reset_tallies(stream)
 
