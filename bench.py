@@ -1021,16 +1021,29 @@ def main():
     # result buffers in pinned host memory, one set per e2e batch and problem
     # (the copies of all batches are in flight together), allocated before
     # the timed region
-    def dest(slot):
-        nc = gbmc._n_cells(geoms[slot])
-        m = counts[slot]
-        return dict(flux=pinned(nc * prob.n_bins, torch.float64), counts=pinned(gbmc.NSCAL, torch.int64),
-                    weights=pinned(gbmc.NSCAL, torch.float64), n_coll=pinned(m, torch.int32),
-                    status=pinned(m, torch.int8), n_flights=pinned(m, torch.int32),
-                    n_draws=pinned(m, torch.int32).view(np.uint32), E=pinned(m, torch.float64),
-                    x=pinned(m, torch.float64), y=pinned(m, torch.float64), z=pinned(m, torch.float64))
+    def batch_dests():
+        # one pinned array per result field for the whole batch, each
+        # problem's destination a contiguous slice of it (the library then
+        # copies a run's results in one piece per field)
+        ncs = [gbmc._n_cells(geoms[k]) * prob.n_bins for k in range(n_geo)]
+        spec = {"flux": (torch.float64, ncs), "counts": (torch.int64, [gbmc.NSCAL] * n_geo),
+                "weights": (torch.float64, [gbmc.NSCAL] * n_geo),
+                "n_coll": (torch.int32, counts), "status": (torch.int8, counts),
+                "n_flights": (torch.int32, counts), "n_draws": (torch.int32, counts),
+                "E": (torch.float64, counts), "x": (torch.float64, counts),
+                "y": (torch.float64, counts), "z": (torch.float64, counts)}
+        out = [dict() for _ in range(n_geo)]
+        for name, (dt, sizes) in spec.items():
+            whole = pinned(int(sum(sizes)), dt)
+            if name == "n_draws":
+                whole = whole.view(np.uint32)
+            at = 0
+            for k in range(n_geo):
+                out[k][name] = whole[at:at + sizes[k]]
+                at += sizes[k]
+        return out
     e2e_probs = [pr for k in range(e2e_steps) for pr in problems(20_000 + k)]
-    dests = [dest(i % n_geo) for i in range(len(e2e_probs))]
+    dests = [d for _ in range(e2e_steps) for d in batch_dests()]
     d2h = sum(a.nbytes for d in dests for a in d.values()) // e2e_steps
     torch.cuda.synchronize()
     if world > 1:

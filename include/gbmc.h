@@ -310,7 +310,10 @@ typedef struct {
  * transfers with compute the paper's streams give).  dst[p] (HOST array of
  * n_prob) receives problem p's tallies (slot p) and outcomes.  Asynchronous
  * on `stream`: the host arrays hold the results once `stream` has passed the
- * call (e.g. cudaStreamSynchronize).  Errors a run flags on the device are
+ * call (e.g. cudaStreamSynchronize).  Where the destinations of consecutive
+ * problems of one run are adjacent in host memory (problem p + 1's array of a
+ * field starting where problem p's ends), that field of those problems goes
+ * in one copy; overlapping destinations are not allowed.  Errors a run flags on the device are
  * reported by the next gbmc_read_stats / gbmc_read_tallies.  dst NULL:
  * INVALID_ARG; other errors as gbmc_run_concurrent. */
 int gbmc_run_concurrent_to_host(gbmc_ctx *ctx, int32_t n_prob, const gbmc_problem *probs,

@@ -1453,30 +1453,74 @@ int gbmc_run_problems(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, vo
     return rc;
 }
 
-// The device-to-host copies of problem p's results (its outcomes at base
-// start and its tally slot p) on stream s.
-static int copy_results(gbmc_ctx* c, int32_t p, int64_t start, int64_t n,
-                        const gbmc_host_results& d, cudaStream_t s) {
-    auto cp = [&](void* dst, const void* src, size_t bytes) -> int {
-        if (!dst || !bytes) return GBMC_OK;
-        CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s));
+// The device-to-host copies of the results of problems p0 .. p0 + np - 1
+// (one run: outcomes at bases start[p], tally slots p) on stream s.  Each
+// result array of a run is contiguous on the device, so the problems whose
+// host destinations are contiguous too go in one copy.
+static int copy_results(gbmc_ctx* c, int32_t p0, int32_t np, const std::vector<int64_t>& start,
+                        const std::vector<int64_t>& nn, const gbmc_host_results* dst,
+                        cudaStream_t s) {
+    char* pd = nullptr;          // pending copy: host destination, device source, bytes
+    const char* ps = nullptr;
+    size_t pb = 0;
+    auto flush = [&]() -> int {
+        if (pd && pb) CK(cudaMemcpyAsync(pd, ps, pb, cudaMemcpyDeviceToHost, s));
+        pd = nullptr;
+        ps = nullptr;
+        pb = 0;
         return GBMC_OK;
     };
+    // one result array: dst_of(p) host pointer, src_of(p) device pointer, bytes_of(p)
+    auto field = [&](auto dst_of, auto src_of, auto bytes_of) -> int {
+        for (int32_t p = p0; p < p0 + np; ++p) {
+            char* d = (char*)dst_of(p);
+            const char* sp = (const char*)src_of(p);
+            const size_t b = bytes_of(p);
+            if (d && b && pd && d == pd + pb && sp == ps + pb) {
+                pb += b;
+                continue;
+            }
+            int rc = flush();
+            if (rc) return rc;
+            if (d && b) {
+                pd = d;
+                ps = sp;
+                pb = b;
+            }
+        }
+        return flush();
+    };
     const Outcomes& O = c->O;
-    const size_t m = (size_t)n;
+    auto n_of = [&](int32_t p) { return (size_t)nn[p]; };
     int rc = 0;
-    rc |= cp(d.n_coll, O.ncoll + start, sizeof(int32_t) * m);
-    rc |= cp(d.status, O.status + start, sizeof(int8_t) * m);
-    rc |= cp(d.n_flights, O.nflt + start, sizeof(int32_t) * m);
-    rc |= cp(d.n_draws, O.ndraw + start, sizeof(uint32_t) * m);
-    rc |= cp(d.E, O.E + start, sizeof(double) * m);
-    rc |= cp(d.x, O.x + start, sizeof(double) * m);
-    rc |= cp(d.y, O.y + start, sizeof(double) * m);
-    rc |= cp(d.z, O.z + start, sizeof(double) * m);
-    rc |= cp(d.flux, c->Y.flux + c->slot_flux_off[p],
-             sizeof(double) * (size_t)c->slot_cells[p] * (size_t)c->n_bins);
-    rc |= cp(d.counts, c->Y.counts + (size_t)p * GBMC_NSCAL, sizeof(int64_t) * GBMC_NSCAL);
-    rc |= cp(d.weights, c->Y.weights + (size_t)p * GBMC_NSCAL, sizeof(double) * GBMC_NSCAL);
+#define GBMC_OUTCOME_FIELD(member, arr, T)                                                    \
+    if (!rc)                                                                                    \
+        rc = field([&](int32_t p) { return (void*)dst[p].member; },                             \
+                   [&](int32_t p) { return (const void*)(O.arr + start[p]); },                  \
+                   [&](int32_t p) { return sizeof(T) * n_of(p); });
+    GBMC_OUTCOME_FIELD(n_coll, ncoll, int32_t)
+    GBMC_OUTCOME_FIELD(status, status, int8_t)
+    GBMC_OUTCOME_FIELD(n_flights, nflt, int32_t)
+    GBMC_OUTCOME_FIELD(n_draws, ndraw, uint32_t)
+    GBMC_OUTCOME_FIELD(E, E, double)
+    GBMC_OUTCOME_FIELD(x, x, double)
+    GBMC_OUTCOME_FIELD(y, y, double)
+    GBMC_OUTCOME_FIELD(z, z, double)
+#undef GBMC_OUTCOME_FIELD
+    if (!rc)
+        rc = field([&](int32_t p) { return (void*)dst[p].flux; },
+                   [&](int32_t p) { return (const void*)(c->Y.flux + c->slot_flux_off[p]); },
+                   [&](int32_t p) {
+                       return sizeof(double) * (size_t)c->slot_cells[p] * (size_t)c->n_bins;
+                   });
+    if (!rc)
+        rc = field([&](int32_t p) { return (void*)dst[p].counts; },
+                   [&](int32_t p) { return (const void*)(c->Y.counts + (size_t)p * GBMC_NSCAL); },
+                   [&](int32_t) { return sizeof(int64_t) * GBMC_NSCAL; });
+    if (!rc)
+        rc = field([&](int32_t p) { return (void*)dst[p].weights; },
+                   [&](int32_t p) { return (const void*)(c->Y.weights + (size_t)p * GBMC_NSCAL); },
+                   [&](int32_t) { return sizeof(double) * GBMC_NSCAL; });
     return rc;
 }
 
@@ -1581,8 +1625,7 @@ static int run_concurrent(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs
             // overlap the loop's next run and the other loops
             CK(cudaEventRecord(l->run_ev, l->own_stream));
             CK(cudaStreamWaitEvent(l->copy_stream, l->run_ev, 0));
-            for (int32_t k = 0; k < np && erc == GBMC_OK; ++k)
-                erc = copy_results(c, p0 + k, start[p0 + k], nn[p0 + k], dst[p0 + k], l->copy_stream);
+            erc = copy_results(c, p0, np, start, nn, dst, l->copy_stream);
         }
     }
     // join: `stream` waits for every loop and its copies (also after a
