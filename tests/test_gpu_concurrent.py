@@ -134,3 +134,73 @@ def test_concurrent_results_copied_to_host(n_loops, pinned):
             ctx.run_concurrent_to_host(probs, n_loops=2, dests=bad)
     finally:
         ctx.close()
+
+
+def test_adjacent_host_destinations_match_the_readers():
+    """Destinations that are slices of one pinned array per field (the case
+    the library copies in one piece per field and run) hold what the
+    synchronous readers return, with a run split by a destination outside
+    the shared array (problem 4's flux and E) and a run whose problems skip
+    the outcomes of one of them (problem 1)."""
+    import torch
+    n_prob = 6
+    p = synth.make_config(4, n_problems=n_prob, grid_scale=0.02)
+    for k in range(n_prob):
+        p.n_particles[k] = 900 + 331 * k
+    ctx = make_ctx(p, (gbmc.FP32,), precision=gbmc.FP32)
+
+    def pinned(n, tdt):
+        return torch.full((n,), -7, dtype=tdt, pin_memory=True).numpy()
+
+    try:
+        probs = [gpu_problem(p, geom_index=k, problem_index=k, batch=7) for k in range(n_prob)]
+        ncs = [gbmc._n_cells(pr.geom) * ctx.n_bins for pr in probs]
+        ns = [int(n) for n in p.n_particles[:n_prob]]
+        spec = {"flux": (torch.float64, ncs), "counts": (torch.int64, [gbmc.NSCAL] * n_prob),
+                "weights": (torch.float64, [gbmc.NSCAL] * n_prob),
+                "n_coll": (torch.int32, ns), "status": (torch.int8, ns),
+                "n_flights": (torch.int32, ns), "n_draws": (torch.int32, ns),
+                "E": (torch.float64, ns), "x": (torch.float64, ns), "y": (torch.float64, ns),
+                "z": (torch.float64, ns)}
+        dests = [dict() for _ in range(n_prob)]
+        wholes = {}
+        for name, (tdt, sizes) in spec.items():
+            whole = pinned(int(sum(sizes)), tdt)
+            if name == "n_draws":
+                whole = whole.view(np.uint32)
+            wholes[name] = whole
+            at = 0
+            for k in range(n_prob):
+                dests[k][name] = whole[at:at + sizes[k]]
+                at += sizes[k]
+        dests[4]["flux"] = pinned(ncs[4], torch.float64)
+        dests[4]["E"] = pinned(ns[4], torch.float64)
+        skipped = ("n_coll", "status", "n_flights", "n_draws", "E", "x", "y", "z")
+        for name in skipped:
+            del dests[1][name]
+        stream = torch.cuda.Stream()
+        ctx.run_concurrent_to_host(probs, n_loops=2, dests=dests, per_run=3, stream=stream)
+        stream.synchronize()
+        for k in range(n_prob):
+            d = dests[k]
+            flux, counts, weights = ctx.read_tallies(k)
+            assert np.array_equal(flux.ravel(), d["flux"]), f"problem {k}: flux"
+            assert np.array_equal(counts, d["counts"]) and np.array_equal(weights, d["weights"])
+            if k == 1:
+                continue
+            out = ctx.read_outcomes(k, 0, ns[k])
+            for name in skipped:
+                assert np.array_equal(out[name], d[name]), f"problem {k}: {name}"
+        # problem 1's outcome slices were not written: the fill value is still there
+        for name in skipped:
+            part = wholes[name][ns[0]:ns[0] + ns[1]]
+            if name == "n_draws":
+                part = part.view(np.int32)
+            assert np.all(part == -7), name
+        # problem 4's flux and E went to arrays of their own: its shared slices are untouched
+        assert np.all(wholes["E"][sum(ns[:4]):sum(ns[:5])] == -7)
+        assert np.all(wholes["flux"][sum(ncs[:4]):sum(ncs[:5])] == -7)
+        ref = oracle.run(p, seed=p.seed, batch=7, geom_index=4, problem_index=4, precision=1)
+        assert_outcomes_equal(dests[4], ref, label="problem 4")
+    finally:
+        ctx.close()
