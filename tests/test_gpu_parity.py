@@ -284,8 +284,10 @@ def _clustered_problem():
                                sigma_t=np.concatenate(sg))
 
 
-@pytest.mark.parametrize("form", ["index", "plain", "sparse"])
-@pytest.mark.parametrize("precision", [gbmc.FP64, gbmc.FP32])
+# short windows are a binary32 form
+@pytest.mark.parametrize("precision,form", [(gbmc.FP64, "index"), (gbmc.FP64, "plain"),
+                                            (gbmc.FP32, "index"), (gbmc.FP32, "plain"),
+                                            (gbmc.FP32, "sparse")])
 @pytest.mark.parametrize("which", ["dense", "sparse", "clustered"])
 def test_lookup_macro_at_grid_points_and_edges(precision, which, form):
     """Exact hits (E - E_k = 0), neighbours, extrapolation outside the grids;
@@ -294,8 +296,6 @@ def test_lookup_macro_at_grid_points_and_edges(precision, which, form):
     the clustered ones the window searches' bisection fallback.  Forms: the
     coarse index, a plain binary search, and (binary32) the short windows."""
     import torch
-    if form == "sparse" and precision == gbmc.FP64:
-        pytest.skip("short windows are a binary32 form")
     if which == "dense":
         prob, _, _ = synth.make_stress_lookup(n_queries=1, n_nuc=12, n_in_mat=8, n_points=400)
     elif which == "sparse":
