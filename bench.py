@@ -1125,13 +1125,15 @@ def main():
     extras = {}
     if rank == 0 and args.config == 2 and stock and not args.no_extras:
         # the coarse index against a plain binary search of each grid, on the
-        # lookup kernel of one eager batch each (same histories, same results)
-        ctx.set_options(search=-1)
+        # lookup kernel of one eager batch each (same histories, same results),
+        # at one event loop's autotuned settings as the roofline
+        ctx.set_options(search=-1, **single_opts)
         kp = ctx.profile_problems(problems(30_000), stream)
         ctx.set_options(search=1)
         ki = ctx.profile_problems(problems(30_000), stream)
         search_cmp = {"lattice17_fp64_lookup_ms_per_batch": {"index": ki["lookup"][0],
-                                                             "plain": kp["lookup"][0]}}
+                                                             "plain": kp["lookup"][0]},
+                      "settings": dict(single_opts)}
         ctx.close()
         ctx = None
         extras["fp32_vs_fp64"] = fp32_vs_fp64_record(stream, local)

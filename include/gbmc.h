@@ -569,15 +569,12 @@ int gbmc_autotune(gbmc_ctx *ctx, int32_t n_prob, const gbmc_problem *probs, doub
  *     GBMC_ERR_INVALID_ARG before anything is launched;
  *   - every GPU that loads the library holds that area (about 8.5 MB) until
  *     the process exits;
- *   - the first call on a device looks up the area's device address
- *     (cudaGetSymbolAddress, which may load the library's device code);
- *     make that first call before any stream capture;
+ *   - every call looks up the area's device address in the current context
+ *     (cudaGetSymbolAddress; the first lookup in a context may load the
+ *     library's device code), so it stays valid across cudaDeviceReset;
  *   - all calls share the one area: calls whose work overlaps on the GPU
  *     (other streams, other threads, other contexts on the same device)
  *     race and corrupt each other's results; order them on one stream;
- *   - the area's address is kept per device for the life of the process:
- *     the calls assume the device's primary context (the one the CUDA
- *     runtime uses) and no cudaDeviceReset between them;
  *   - it calls no cudaMalloc / cudaFree and no allocating library routine.
  * Inputs and outputs are DEVICE pointers owned by the caller, as in
  * gbmc_lookup_macro.  Asynchronous on `stream`. */

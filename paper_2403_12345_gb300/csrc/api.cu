@@ -7,7 +7,6 @@
 #include <cstdio>
 #include <cstring>
 #include <limits>
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -2536,8 +2535,10 @@ extern "C" int gbmc_autotune(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* pr
 //
 // The scratch is a file-scope __device__ array, so every GPU that loads the
 // library reserves it (about 8.5 MB) until the process exits.  Its device
-// address is fetched once per device with cudaGetSymbolAddress; the host
-// symbol itself is only a stand-in and is never handed to a kernel.
+// address is fetched on every call with cudaGetSymbolAddress (a lookup in the
+// loaded module, no allocation), so it follows the current context, also after
+// cudaDeviceReset; the host symbol itself is only a stand-in and is never
+// handed to a kernel.
 namespace {
 
 constexpr int64_t kNoAllocMaxQueries = (int64_t)1 << 20;
@@ -2549,21 +2550,12 @@ constexpr size_t kNoAllocBytes =
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-constexpr int kNoAllocMaxDevices = 64;
-std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
-
-// Device address of the scratch on `device` (which must be current).
-cudaError_t noalloc_scratch(int device, unsigned char** out) {
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[device]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_noalloc_ptr[device] = p;
-    }
-    *out = (unsigned char*)g_noalloc_ptr[device];
-    return cudaSuccess;
+// Device address of the scratch in the current context.
+cudaError_t noalloc_scratch(unsigned char** out) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    *out = (unsigned char*)p;
+    return e;
 }
 
 }  // namespace
@@ -2584,12 +2576,10 @@ extern "C" int gbmc_lookup_macro_noalloc(gbmc_ctx* c, int32_t precision, const d
     if ((precision == GBMC_FP64 && !c->has64) || (precision == GBMC_FP32 && !c->has32))
         return fail(c, GBMC_ERR_NOT_INITIALIZED, "tables not loaded in that precision");
     if (n == 0) return GBMC_OK;
-    if (c->device < 0 || c->device >= kNoAllocMaxDevices)
-        return fail(c, GBMC_ERR_UNSUPPORTED, "device index above %d", kNoAllocMaxDevices - 1);
     int rc = set_device(c);
     if (rc) return rc;
     unsigned char* base = nullptr;
-    CK(noalloc_scratch(c->device, &base));
+    CK(noalloc_scratch(&base));
     int32_t* perm = (int32_t*)base;
     uint32_t* keys = (uint32_t*)(base + kNoAllocPermBytes);
     uint32_t* hist = (uint32_t*)(base + kNoAllocPermBytes + kNoAllocKeysBytes);

@@ -140,13 +140,14 @@ def test_adjacent_host_destinations_match_the_readers():
     """Destinations that are slices of one pinned array per field (the case
     the library copies in one piece per field and run) hold what the
     synchronous readers return, with a run split by a destination outside
-    the shared array (problem 4's flux and E) and a run whose problems skip
-    the outcomes of one of them (problem 1)."""
+    the shared array (problem 4's flux and E), a run whose problems skip
+    the outcomes of one of them (problem 1) and an empty problem (3)."""
     import torch
     n_prob = 6
     p = synth.make_config(4, n_problems=n_prob, grid_scale=0.02)
     for k in range(n_prob):
         p.n_particles[k] = 900 + 331 * k
+    p.n_particles[3] = 0   # an empty problem opening the second run
     ctx = make_ctx(p, (gbmc.FP32,), precision=gbmc.FP32)
 
     def pinned(n, tdt):
@@ -200,6 +201,7 @@ def test_adjacent_host_destinations_match_the_readers():
         # problem 4's flux and E went to arrays of their own: its shared slices are untouched
         assert np.all(wholes["E"][sum(ns[:4]):sum(ns[:5])] == -7)
         assert np.all(wholes["flux"][sum(ncs[:4]):sum(ncs[:5])] == -7)
+        assert not dests[3]["flux"].any() and not dests[3]["counts"].any()
         ref = oracle.run(p, seed=p.seed, batch=7, geom_index=4, problem_index=4, precision=1)
         assert_outcomes_equal(dests[4], ref, label="problem 4")
     finally:
