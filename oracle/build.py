@@ -1,7 +1,8 @@
 """Build the CPU oracle shared library (test infrastructure only).
 
-Compiled with -ffp-contract=off so that no multiply-add is fused: every
-binary64 / binary32 operation is rounded as written.
+Compiled with -ffp-contract=off so that the compiler fuses no multiply-add:
+every binary64 / binary32 operation is rounded as written, and the only fused
+multiply-adds are the explicit fma() calls of the source.
 """
 import os
 import subprocess

@@ -8,7 +8,11 @@
  * written, one IEEE-754 round-to-nearest operation at a time, so that the
  * GPU path (compiled without FMA contraction) can reproduce each particle's
  * random walk bit for bit.  Parenthesised sub-expressions fix the operation
- * order wherever the grouping is not obvious.
+ * order wherever the grouping is not obvious.  Where a step is written as
+ * fma(a, b, c) it is the IEEE-754 fused multiply-add a * b + c with one
+ * rounding (C99 fma; the GPU path issues the same operation): the binary64
+ * lookup's interpolation and its density-weighted sums, the logarithm's
+ * series, the position update and the scatter kinematics.
  *
  * What is computed (paper: Sec. 2 "Event-Based Parallelism" for the event /
  * history duality; Sec. 2 "Sorting" for the macroscopic cross-section lookup
@@ -126,21 +130,22 @@ double or_log(double x)
     }
     double s = (m - 1.0) / (m + 1.0);
     double z = s * s;
+    /* Horner's rule, each step c_k + z q rounded once */
     double q = 0x1.8618618618618p-5;            /* 1/21 */
-    q = 0x1.af286bca1af28p-5 + z * q;           /* 1/19 */
-    q = 0x1.e1e1e1e1e1e1ep-5 + z * q;           /* 1/17 */
-    q = 0x1.1111111111111p-4 + z * q;           /* 1/15 */
-    q = 0x1.3b13b13b13b14p-4 + z * q;           /* 1/13 */
-    q = 0x1.745d1745d1746p-4 + z * q;           /* 1/11 */
-    q = 0x1.c71c71c71c71cp-4 + z * q;           /* 1/9 */
-    q = 0x1.2492492492492p-3 + z * q;           /* 1/7 */
-    q = 0x1.999999999999ap-3 + z * q;           /* 1/5 */
-    q = 0x1.5555555555555p-2 + z * q;           /* 1/3 */
+    q = fma(z, q, 0x1.af286bca1af28p-5);        /* 1/19 */
+    q = fma(z, q, 0x1.e1e1e1e1e1e1ep-5);        /* 1/17 */
+    q = fma(z, q, 0x1.1111111111111p-4);        /* 1/15 */
+    q = fma(z, q, 0x1.3b13b13b13b14p-4);        /* 1/13 */
+    q = fma(z, q, 0x1.745d1745d1746p-4);        /* 1/11 */
+    q = fma(z, q, 0x1.c71c71c71c71cp-4);        /* 1/9 */
+    q = fma(z, q, 0x1.2492492492492p-3);        /* 1/7 */
+    q = fma(z, q, 0x1.999999999999ap-3);        /* 1/5 */
+    q = fma(z, q, 0x1.5555555555555p-2);        /* 1/3 */
     q = z * q;
     double t = 2.0 * s;
-    double logm = t + t * q;
+    double logm = fma(t, q, t);                 /* 2s + 2s q */
     double de = (double)e;
-    return de * OR_LN2_HI + (logm + de * OR_LN2_LO);
+    return fma(de, OR_LN2_HI, fma(de, OR_LN2_LO, logm));
 }
 
 /* ------------------------------------------------------------------------ */
@@ -194,7 +199,8 @@ double or_micro(const or_problem *P, int32_t nuc, double E)
     const double *s = P->sigma_t + lo;
     int64_t j = or_search(g, n, E);
     double f = (E - g[j]) / (g[j + 1] - g[j]);
-    return s[j] + f * (s[j + 1] - s[j]);
+    /* sigma_j + f (sigma_j+1 - sigma_j), the product and sum rounded once */
+    return fma(f, s[j + 1] - s[j], s[j]);
 }
 
 /* Binary32 micro cross section on one nuclide's binary32 grid g and values
@@ -248,7 +254,10 @@ static void tables_free(tables_t *T)
     T->sf = NULL;
 }
 
-/* Macroscopic sigma_t and sigma_a of material m at energy E. */
+/* Macroscopic sigma_t and sigma_a of material m at energy E.  Binary64:
+ * Sigma_t = sum of N_i sigma_i and Sigma_a = sum of (N_i f_i) sigma_i in the
+ * listed order, each term added by one fused multiply-add (N_i f_i is
+ * rounded first).  Binary32: product, then sum, each rounded in binary32. */
 static void macro_xs(const tables_t *T, int32_t m, double E, double *st, double *sa)
 {
     const or_problem *P = T->P;
@@ -256,9 +265,10 @@ static void macro_xs(const tables_t *T, int32_t m, double E, double *st, double 
         double at = 0.0, aa = 0.0;
         for (int32_t q = P->mat_off[m]; q < P->mat_off[m + 1]; ++q) {
             int32_t i = P->nuc_id[q];
-            double t = P->density[q] * or_micro(P, i, E);
-            at = at + t;
-            aa = aa + t * P->f_abs[i];
+            double N = P->density[q];
+            double sig = or_micro(P, i, E);
+            at = fma(N, sig, at);
+            aa = fma(N * P->f_abs[i], sig, aa);
         }
         *st = at;
         *sa = aa;
@@ -289,7 +299,8 @@ int or_macro(const or_problem *P, int32_t m, const double *E, int64_t n,
 /* Collision nuclide: first i (listed order) whose running sum of N_i sigma_i
  * exceeds target = xi * Sigma_t; the running sums are formed exactly as in
  * macro_xs.  If rounding leaves none, the last nuclide with a positive term
- * (the first listed nuclide if no term is positive). */
+ * (binary64: N_i > 0 and sigma_i > 0; binary32: the rounded product) --
+ * the first listed nuclide if no term is positive. */
 static int32_t pick_nuclide(const tables_t *T, int32_t m, double E, double target)
 {
     const or_problem *P = T->P;
@@ -298,9 +309,10 @@ static int32_t pick_nuclide(const tables_t *T, int32_t m, double E, double targe
         double cum = 0.0;
         for (int32_t q = P->mat_off[m]; q < P->mat_off[m + 1]; ++q) {
             int32_t i = P->nuc_id[q];
-            double t = P->density[q] * or_micro(P, i, E);
-            cum = cum + t;
-            if (t > 0.0) last = i;
+            double N = P->density[q];
+            double sig = or_micro(P, i, E);
+            cum = fma(N, sig, cum);
+            if (N > 0.0 && sig > 0.0) last = i;
             if (target < cum) return i;
         }
     } else {
@@ -490,27 +502,31 @@ static int cross_surface(const or_problem *P, particle_t *p, int surf)
 /* target at rest.                                                          */
 /* ------------------------------------------------------------------------ */
 
-/* Outgoing energy and lab-frame cosine for CM cosine mu and mass ratio A. */
+/* Outgoing energy and lab-frame cosine for CM cosine mu and mass ratio A:
+ * E' = E (A^2 + 2 A mu + 1) / (A + 1)^2, mu_lab = (1 + A mu) / sqrt(A^2 +
+ * 2 A mu + 1). */
 void or_elastic(double E, double A, double mu, double *E_out, double *mu_lab)
 {
-    double t1 = (A * A + (2.0 * A) * mu) + 1.0;
+    double t1 = fma(2.0 * A, mu, A * A) + 1.0;
     double ap1 = A + 1.0;
     *E_out = (E * t1) / (ap1 * ap1);
-    *mu_lab = (1.0 + A * mu) / sqrt(t1);
+    *mu_lab = fma(A, mu, 1.0) / sqrt(t1);
 }
 
-/* Rotate direction (u,v,w) by polar cosine mu and azimuth (cphi, sphi). */
+/* Rotate direction (u,v,w) by polar cosine mu and azimuth (cphi, sphi):
+ * the textbook rotation, each product-plus-term one fused multiply-add. */
 void or_rotate(double *u, double *v, double *w, double mu, double cphi, double sphi)
 {
-    double m2 = 1.0 - mu * mu;
+    double m2 = fma(-mu, mu, 1.0);              /* 1 - mu^2 */
     if (m2 < 0.0) m2 = 0.0;
     double st = sqrt(m2);
     double u0 = *u, v0 = *v, w0 = *w;
     if (fabs(w0) < 0.9999999999) {
-        double q = sqrt(1.0 - w0 * w0);
-        *u = mu * u0 + (st * ((u0 * w0) * cphi - v0 * sphi)) / q;
-        *v = mu * v0 + (st * ((v0 * w0) * cphi + u0 * sphi)) / q;
-        *w = mu * w0 - (st * q) * cphi;
+        double q = sqrt(fma(-w0, w0, 1.0));    /* sqrt(1 - w^2) */
+        /* u' = mu u + st (u w cos phi - v sin phi) / q, and so on */
+        *u = fma(mu, u0, (st * fma(u0 * w0, cphi, -(v0 * sphi))) / q);
+        *v = fma(mu, v0, (st * fma(v0 * w0, cphi, u0 * sphi)) / q);
+        *w = fma(mu, w0, -((st * q) * cphi));
     } else {
         *u = st * cphi;
         *v = st * sphi;
@@ -524,7 +540,7 @@ static double disk_pair(rng_t *r, double *a, double *b)
     for (;;) {
         *a = 2.0 * rng_next(r) - 1.0;
         *b = 2.0 * rng_next(r) - 1.0;
-        double s = *a * *a + *b * *b;
+        double s = fma(*a, *a, *b * *b);        /* a^2 + b^2 */
         if (s > 0.0 && s < 1.0) return s;
     }
 }
@@ -729,11 +745,12 @@ static void transport(const or_problem *P, const tables_t *T, rng_t *r, particle
         dist_boundary(P, &p, &dbnd, &surf);
         int collide = dcol < dbnd;
         double d = collide ? dcol : dbnd;
-        /* move and score the track length */
+        /* move (r + d Omega, each coordinate one fused multiply-add) and
+         * score the track length */
         int32_t cell = cell_of(P, &p);
-        p.x = p.x + d * p.u;
-        p.y = p.y + d * p.v;
-        p.z = p.z + d * p.w;
+        p.x = fma(d, p.u, p.x);
+        p.y = fma(d, p.v, p.y);
+        p.z = fma(d, p.w, p.z);
         {
             /* track-length estimators: flux w d and absorption rate
              * (w d) Sigma_a of the segment's (cell, energy bin) */
@@ -773,7 +790,7 @@ static void transport(const or_problem *P, const tables_t *T, rng_t *r, particle
                 double mu = 2.0 * rng_next(r) - 1.0;
                 double a, b;
                 double s = disk_pair(r, &a, &b);
-                double cphi = (a * a - b * b) / s;
+                double cphi = fma(a, a, -(b * b)) / s;   /* (a^2 - b^2) / s */
                 double sphi = ((2.0 * a) * b) / s;
                 double E1, mul;
                 or_elastic(p.E, P->awr[nuc], mu, &E1, &mul);

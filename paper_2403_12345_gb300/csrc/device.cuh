@@ -475,8 +475,9 @@ __device__ __forceinline__ double frac_rn(double E, double e0, double de, unsign
 // ln x for positive normal x: x = 2^e m with m in (sqrt(2)/2, sqrt(2)];
 // ln m = 2 atanh(s), s = (m - 1)/(m + 1), as the series
 // 2s (1 + s^2/3 + ... + s^20/21) (Abramowitz & Stegun 4.1.28), evaluated by
-// Horner's rule from the 1/21 term; e ln 2 with ln 2 split in a high part
-// carrying 21 trailing zero bits (so e * high is exact) and a low part.
+// Horner's rule from the 1/21 term, each step one fused multiply-add; e ln 2
+// with ln 2 split in a high part carrying 21 trailing zero bits (so e * high
+// is exact) and a low part.
 __device__ __forceinline__ double ln_series(double x) {
     long long b = __double_as_longlong(x);
     int e = (int)((b >> 52) & 0x7ff) - 1023;
@@ -488,20 +489,20 @@ __device__ __forceinline__ double ln_series(double x) {
     double s = (m - 1.0) / (m + 1.0);
     double z = s * s;
     double q = 0x1.8618618618618p-5;
-    q = 0x1.af286bca1af28p-5 + z * q;
-    q = 0x1.e1e1e1e1e1e1ep-5 + z * q;
-    q = 0x1.1111111111111p-4 + z * q;
-    q = 0x1.3b13b13b13b14p-4 + z * q;
-    q = 0x1.745d1745d1746p-4 + z * q;
-    q = 0x1.c71c71c71c71cp-4 + z * q;
-    q = 0x1.2492492492492p-3 + z * q;
-    q = 0x1.999999999999ap-3 + z * q;
-    q = 0x1.5555555555555p-2 + z * q;
+    q = __fma_rn(z, q, 0x1.af286bca1af28p-5);
+    q = __fma_rn(z, q, 0x1.e1e1e1e1e1e1ep-5);
+    q = __fma_rn(z, q, 0x1.1111111111111p-4);
+    q = __fma_rn(z, q, 0x1.3b13b13b13b14p-4);
+    q = __fma_rn(z, q, 0x1.745d1745d1746p-4);
+    q = __fma_rn(z, q, 0x1.c71c71c71c71cp-4);
+    q = __fma_rn(z, q, 0x1.2492492492492p-3);
+    q = __fma_rn(z, q, 0x1.999999999999ap-3);
+    q = __fma_rn(z, q, 0x1.5555555555555p-2);
     q = z * q;
     double t = 2.0 * s;
-    double lm = t + t * q;
+    double lm = __fma_rn(t, q, t);
     double de = (double)e;
-    return de * 0x1.62e42fee00000p-1 + (lm + de * 0x1.a39ef35793c76p-33);
+    return __fma_rn(de, 0x1.62e42fee00000p-1, __fma_rn(de, 0x1.a39ef35793c76p-33, lm));
 }
 
 // ---------------------------------------------------------------- lookup
@@ -562,14 +563,14 @@ __device__ __forceinline__ Desc64 load_desc64(const Desc64* p) {
 }
 
 // Lin-lin interpolation on the grid interval k that brackets E:
-// f = (E - E_k) / (E_k+1 - E_k), sigma = s_k + f (s_k+1 - s_k), every step
-// rounded to nearest in binary64 (the interval's differences come from its
-// record).
+// f = (E - E_k) / (E_k+1 - E_k) rounded to nearest in binary64, then
+// sigma = s_k + f (s_k+1 - s_k) as one fused multiply-add (the interval's
+// differences, each rounded, come from its record).
 __device__ __forceinline__ double interp64(const Tables& T, int64_t k, double E) {
     const double2* r = reinterpret_cast<const double2*>(T.iv64 + k);
     const double2 a = __ldg(r), b = __ldg(r + 1);   // (de, ds), (s0, y)
     const double f = frac_rn(E, __ldg(T.e64 + k), a.x, (unsigned long long)__double_as_longlong(b.y));
-    return b.x + f * a.y;
+    return __fma_rn(f, a.y, b.x);
 }
 
 // Micro cross section at E of the nuclide of material entry q.
@@ -871,16 +872,17 @@ __device__ __forceinline__ void macro64_group(const Tables& T, int32_t m, double
 #pragma unroll
                 for (int u = 0; u < kIlp; ++u) {
                     const int32_t a = a0 + u * kGroupLanes;
-                    if (a < ge) row[a - g0] = __ldg(T.density + q0 + a) * interp64(T, pos[u], E);
+                    if (a < ge) row[a - g0] = interp64(T, pos[u], E);
                 }
             }
         }
         __syncwarp();
         if (r == 0) {
             for (int32_t a = g0; a < ge; ++a) {
-                const double t = row[a - g0];
-                at = at + t;
-                if (SA) aa = aa + t * __ldg(T.f_abs + __ldg(T.nuc_id + q0 + a));
+                const double sig = row[a - g0];
+                const double N = __ldg(T.density + q0 + a);
+                at = __fma_rn(N, sig, at);
+                if (SA) aa = __fma_rn(N * __ldg(T.f_abs + __ldg(T.nuc_id + q0 + a)), sig, aa);
                 if (cum && ((a & 3) == 3 || a == nq - 1)) {
                     const int32_t gq = a >> 2;
                     if (gq & 1) pend.y = at; else pend.x = at;
@@ -912,10 +914,9 @@ __device__ __forceinline__ void macro64(const Tables& T, int32_t m, double E, do
         for (int u = 0; u < kIlp; ++u) {
             if (q + u < q1) {
                 double sig = interp64(T, pos[u], E);
-                int32_t i = __ldg(T.nuc_id + q + u);
-                double t = __ldg(T.density + q + u) * sig;
-                at = at + t;
-                if (SA) aa = aa + t * __ldg(T.f_abs + i);
+                double N = __ldg(T.density + q + u);
+                at = __fma_rn(N, sig, at);
+                if (SA) aa = __fma_rn(N * __ldg(T.f_abs + __ldg(T.nuc_id + q + u)), sig, aa);
             }
             run[u] = at;
         }
@@ -1007,7 +1008,6 @@ __device__ __forceinline__ void macro64_tile(const Tables& T, int32_t m, int nv,
         if (i < gn) {
             const int32_t q = q0 + g0 + i;
             const Desc64 d = load_desc64(T.d64 + q);
-            const double N = __ldg(T.density + q);
             const unsigned long long* gg = g + d.off;
             int32_t k = -1;                               // bracket held in registers
             unsigned long long elo = 0ull, ehi = 0ull;    // bits of E_k, E_k+1
@@ -1031,16 +1031,17 @@ __device__ __forceinline__ void macro64_tile(const Tables& T, int32_t m, int nv,
                 }
                 const double f = frac_rn(E, __longlong_as_double((long long)elo), r0.x,
                                          (unsigned long long)__double_as_longlong(r1.y));
-                sm.t[i * kTileStride + p] = N * (r1.x + f * r0.y);
+                sm.t[i * kTileStride + p] = __fma_rn(f, r0.y, r1.x);
             }
         }
         __syncwarp();
         if (lane < nv) {
             for (int ii = 0; ii < gn; ++ii) {
-                const double t = sm.t[ii * kTileStride + lane];
+                const double sig = sm.t[ii * kTileStride + lane];
                 const int32_t a = g0 + ii;   // entry index within the material
-                at = at + t;
-                if (SA) aa = aa + t * __ldg(T.f_abs + __ldg(T.nuc_id + q0 + a));
+                const double N = __ldg(T.density + q0 + a);
+                at = __fma_rn(N, sig, at);
+                if (SA) aa = __fma_rn(N * __ldg(T.f_abs + __ldg(T.nuc_id + q0 + a)), sig, aa);
                 if (cum && ((a & 3) == 3 || a == nq - 1)) {
                     const int32_t gq = a >> 2;
                     if (gq & 1) pend.y = at; else pend.x = at;
@@ -1167,15 +1168,17 @@ __device__ __forceinline__ void macro_warp(const Tables& T, int32_t m, double E,
     if (PREC == GBMC_FP64) {
         double at = 0.0, aa = 0.0;
         for (int32_t c = q0; c < q1; c += 32) {
-            double t = 0.0, p = 0.0;
+            double sig = 0.0, N = 0.0, Na = 0.0;
             if (c + lane < q1) {
-                t = __ldg(T.density + c + lane) * micro64(T, c + lane, E);
-                if (SA) p = t * __ldg(T.f_abs + __ldg(T.nuc_id + c + lane));
+                N = __ldg(T.density + c + lane);
+                sig = micro64(T, c + lane, E);
+                if (SA) Na = N * __ldg(T.f_abs + __ldg(T.nuc_id + c + lane));
             }
             int32_t kmax = q1 - c < 32 ? q1 - c : 32;
             for (int k = 0; k < kmax; ++k) {
-                at = at + __shfl_sync(full, t, k);
-                if (SA) aa = aa + __shfl_sync(full, p, k);
+                const double sk = __shfl_sync(full, sig, k);
+                at = __fma_rn(__shfl_sync(full, N, k), sk, at);
+                if (SA) aa = __fma_rn(__shfl_sync(full, Na, k), sk, aa);
                 if (cum && lane == k &&
                     ((c + k - q0) % kCumGroup64 == kCumGroup64 - 1 || c + k == q1 - 1))
                     ((double*)cum)[(int64_t)((c + k - q0) / kCumGroup64) * stride] = at;
@@ -1208,7 +1211,8 @@ __device__ __forceinline__ void macro_warp(const Tables& T, int32_t m, double E,
 // Collision nuclide: first nuclide (listed order) whose running sum of
 // N_i sigma_i exceeds target = xi Sigma_t, with the running sums formed as
 // in the macroscopic lookup; if rounding leaves none, the last nuclide with
-// a positive term (the first listed one if no term is positive).
+// a positive term (binary64: N_i > 0 and sigma_i > 0; binary32: the rounded
+// product), the first listed one if no term is positive.
 __device__ __forceinline__ int32_t pick_nuclide(const Tables& T, int precision, int32_t m,
                                                 double E, double target) {
     int32_t last = -1;
@@ -1217,9 +1221,10 @@ __device__ __forceinline__ int32_t pick_nuclide(const Tables& T, int precision, 
         double cum = 0.0;
         for (int32_t q = q0; q < q1; ++q) {
             int32_t i = __ldg(T.nuc_id + q);
-            double t = __ldg(T.density + q) * micro64(T, q, E);
-            cum = cum + t;
-            if (t > 0.0) last = i;
+            double N = __ldg(T.density + q);
+            double sig = micro64(T, q, E);
+            cum = __fma_rn(N, sig, cum);
+            if (N > 0.0 && sig > 0.0) last = i;
             if (target < cum) return i;
         }
     } else {
@@ -1266,7 +1271,7 @@ __device__ __forceinline__ int32_t pick_from_sums(const Tables& T, int32_t m, co
         double at = lo > 0 ? c64[(int64_t)(lo - 1) * stride] : 0.0;
         for (int32_t k = k0; k < k1; ++k) {
             int32_t i = __ldg(T.nuc_id + q0 + k);
-            at = at + __ldg(T.density + q0 + k) * micro64(T, q0 + k, E);
+            at = __fma_rn(__ldg(T.density + q0 + k), micro64(T, q0 + k, E), at);
             if (target < at) return i;
         }
     } else {
@@ -1433,27 +1438,29 @@ __device__ __forceinline__ Span collision_span(double xi, double st) {
 
 // Elastic scatter off a nucleus at rest, isotropic in the centre-of-mass
 // frame: E' = E (A^2 + 2 A mu + 1) / (A + 1)^2,
-// mu_lab = (1 + A mu) / sqrt(A^2 + 2 A mu + 1).
+// mu_lab = (1 + A mu) / sqrt(A^2 + 2 A mu + 1); A^2 + 2 A mu and 1 + A mu
+// are fused multiply-adds.
 __device__ __forceinline__ void elastic(double E, double A, double mu, double& E_out,
                                         double& mu_lab) {
-    double t1 = (A * A + (2.0 * A) * mu) + 1.0;
+    double t1 = __fma_rn(2.0 * A, mu, A * A) + 1.0;
     double ap1 = A + 1.0;
     E_out = (E * t1) / (ap1 * ap1);
-    mu_lab = (1.0 + A * mu) / sqrt(t1);
+    mu_lab = __fma_rn(A, mu, 1.0) / sqrt(t1);
 }
 
-// Rotate (u, v, w) by polar cosine mu and azimuth (cos phi, sin phi).
+// Rotate (u, v, w) by polar cosine mu and azimuth (cos phi, sin phi); each
+// product-plus-term below is one fused multiply-add.
 __device__ __forceinline__ void rotate(double& u, double& v, double& w, double mu, double cphi,
                                        double sphi) {
-    double m2 = 1.0 - mu * mu;
+    double m2 = __fma_rn(-mu, mu, 1.0);
     if (m2 < 0.0) m2 = 0.0;
     double st = sqrt(m2);
     double u0 = u, v0 = v, w0 = w;
     if (fabs(w0) < 0.9999999999) {
-        double q = sqrt(1.0 - w0 * w0);
-        u = mu * u0 + (st * ((u0 * w0) * cphi - v0 * sphi)) / q;
-        v = mu * v0 + (st * ((v0 * w0) * cphi + u0 * sphi)) / q;
-        w = mu * w0 - (st * q) * cphi;
+        double q = sqrt(__fma_rn(-w0, w0, 1.0));
+        u = __fma_rn(mu, u0, (st * __fma_rn(u0 * w0, cphi, -(v0 * sphi))) / q);
+        v = __fma_rn(mu, v0, (st * __fma_rn(v0 * w0, cphi, u0 * sphi)) / q);
+        w = __fma_rn(mu, w0, -((st * q) * cphi));
     } else {
         u = st * cphi;
         v = st * sphi;
@@ -1462,12 +1469,13 @@ __device__ __forceinline__ void rotate(double& u, double& v, double& w, double m
 }
 
 // Marsaglia (1972): (a, b) uniform in the unit disk by rejection; returns
-// s = a^2 + b^2 in (0, 1).
+// s = a^2 + b^2 in (0, 1), one fused multiply-add.  2 xi - 1 as a fused
+// multiply-add equals the separately rounded form: 2 xi is exact.
 __device__ __forceinline__ double disk_pair(Stream& r, double& a, double& b) {
     for (;;) {
-        a = 2.0 * r.next() - 1.0;
-        b = 2.0 * r.next() - 1.0;
-        double s = a * a + b * b;
+        a = __fma_rn(2.0, r.next(), -1.0);
+        b = __fma_rn(2.0, r.next(), -1.0);
+        double s = __fma_rn(a, a, b * b);
         if (s > 0.0 && s < 1.0) return s;
     }
 }

@@ -806,22 +806,23 @@ __device__ __forceinline__ bool fly(const Params& P, const DevProblem& pr, Parti
     }
     if (!collide) {
         pt.surf = surf;
-        pt.x = pt.x + dbnd * pt.u;
-        pt.y = pt.y + dbnd * pt.v;
-        pt.z = pt.z + dbnd * pt.w;
+        pt.x = __fma_rn(dbnd, pt.u, pt.x);
+        pt.y = __fma_rn(dbnd, pt.v, pt.y);
+        pt.z = __fma_rn(dbnd, pt.w, pt.z);
         seg = segment_score(P, pr, pt, dbnd, ebin);
     }
     return collide;
 }
 
 // The end of a flight that reached its collision site: d = -ln(xi) /
-// Sigma_t, the move, and the track-length score (returned to be added).
+// Sigma_t, the move (each coordinate x + d u one fused multiply-add), and
+// the track-length score (returned to be added).
 __device__ __forceinline__ Score finish_flight(const Params& P, const DevProblem& pr, Particle& pt,
                                                double xi) {
     double d = (0.0 - ln_series(xi)) / pt.st;
-    pt.x = pt.x + d * pt.u;
-    pt.y = pt.y + d * pt.v;
-    pt.z = pt.z + d * pt.w;
+    pt.x = __fma_rn(d, pt.u, pt.x);
+    pt.y = __fma_rn(d, pt.v, pt.y);
+    pt.z = __fma_rn(d, pt.w, pt.z);
     return segment_score(P, pr, pt, d, energy_bin(P.T, pt.E));
 }
 
@@ -997,10 +998,10 @@ __device__ __forceinline__ int collide(const Params& P, const DevProblem& pr, Pa
     if (xa < __ldg(P.T.f_abs + nuc)) {
         status = GBMC_STATUS_ABSORBED;
     } else {
-        double mu = 2.0 * r.next() - 1.0;
+        double mu = __fma_rn(2.0, r.next(), -1.0);   // = 2 xi - 1 (2 xi is exact)
         double a, b;
         double s = disk_pair(r, a, b);
-        double cphi = (a * a - b * b) / s;
+        double cphi = __fma_rn(a, a, -(b * b)) / s;
         double sphi = ((2.0 * a) * b) / s;
         double E1, mul;
         elastic(pt.E, __ldg(P.T.awr + nuc), mu, E1, mul);

@@ -117,14 +117,96 @@ def test_micro_against_exact_rationals():
             f = (Fraction(E) - Fraction(g[j])) / (Fraction(g[j + 1]) - Fraction(g[j]))
             exact = Fraction(s[j]) + f * (Fraction(s[j + 1]) - Fraction(s[j]))
             got = oracle.micro(p, nuc, E)
-            # six roundings (two differences, a quotient, a difference, a
-            # product, a sum): |error| <= ~6u (|s_j| + |s_j+1|), u = 2^-53
+            # five roundings (two differences, a quotient, a difference, a
+            # fused multiply-add): |error| <= ~5u (|s_j| + |s_j+1|), u = 2^-53
             bound = 8 * 2.0**-53 * (abs(Fraction(s[j])) + abs(Fraction(s[j + 1])))
             assert abs(Fraction(got) - exact) <= bound, (nuc, E)
         # at grid points the tabulated value is returned exactly
         for j in range(len(g) - 1):
             assert oracle.micro(p, nuc, g[j]) == s[j]
         assert ulps(oracle.micro(p, nuc, g[-1]), s[-1])[0] <= 1
+
+
+def test_micro_interpolation_is_one_fused_rounding():
+    # f = (E - E_j) / (E_j+1 - E_j) and d = s_j+1 - s_j are each rounded
+    # once (Python float arithmetic is IEEE binary64, round to nearest); the
+    # value is then s_j + f d rounded ONCE: the exact rational, rounded to
+    # nearest (float(Fraction) rounds correctly, ties to even)
+    p = synth.make_tiny_problem(seed=13, n_nuc=3, n_points=(20, 60))
+    rng = np.random.default_rng(14)
+    unfused_differs = 0
+    for nuc in range(p.n_nuc):
+        lo, hi = p.grid_off[nuc], p.grid_off[nuc + 1]
+        g, s = [float(v) for v in p.energy[lo:hi]], [float(v) for v in p.sigma_t[lo:hi]]
+        for E in np.exp(rng.uniform(math.log(g[0]), math.log(g[-1]), 400)):
+            E = float(E)
+            j = _scan(np.array(g), E)
+            f = (E - g[j]) / (g[j + 1] - g[j])
+            d = s[j + 1] - s[j]
+            want = float(Fraction(s[j]) + Fraction(f) * Fraction(d))
+            got = oracle.micro(p, nuc, E)
+            assert got == want, (nuc, E)
+            unfused_differs += got != s[j] + f * d
+    # the separately rounded product would miss some of these
+    assert unfused_differs > 0
+
+
+def _flat_nuclides(sigma, density, f_abs):
+    """One binary64 material whose nuclides have flat cross sections."""
+    import types
+    n = len(sigma)
+    return types.SimpleNamespace(
+        grid_off=np.arange(0, 2 * n + 1, 2, dtype=np.int64),
+        energy=np.tile(np.array([1e-5, 2e7]), n), sigma_t=np.repeat(np.asarray(sigma, float), 2),
+        f_abs=np.asarray(f_abs, float), awr=np.full(n, 10.0),
+        mat_off=np.array([0, n], np.int32), nuc_id=np.arange(n, dtype=np.int32),
+        density=np.asarray(density, float), edges=np.geomspace(1e-5, 2e7, 3), precision=0,
+        geoms=[synth.Geometry()], n_particles=[1])
+
+
+def test_macro_terms_added_by_fused_multiply_add():
+    # Sigma_t: acc <- RN(acc + N_i sigma_i); Sigma_a: acc <- RN(acc +
+    # RN(N_i f_i) sigma_i), in the listed order (exact rationals, rounded once
+    # per term); flat cross sections make each micro value exactly sigma_i
+    rng = np.random.default_rng(15)
+    unfused_differs = 0
+    for _ in range(40):
+        n = int(rng.integers(2, 9))
+        sig = rng.uniform(0.1, 50.0, n)
+        den = rng.uniform(0.01, 1.0, n)
+        fab = rng.uniform(0.05, 0.5, n)
+        st, sa = oracle.macro(_flat_nuclides(sig, den, fab), 0, np.array([1.0, 3e5]))
+        at, aa, ut = 0.0, 0.0, 0.0
+        for i in range(n):
+            at = float(Fraction(at) + Fraction(float(den[i])) * Fraction(float(sig[i])))
+            na = float(den[i]) * float(fab[i])
+            aa = float(Fraction(aa) + Fraction(na) * Fraction(float(sig[i])))
+            ut = ut + float(den[i]) * float(sig[i])
+        assert np.all(st == at) and np.all(sa == aa)
+        unfused_differs += ut != at
+    assert unfused_differs > 0
+
+
+def test_pick_uses_the_fused_running_sums():
+    # the collision's running sums are the lookup's: a target between the
+    # fused and the separately rounded first sum tells them apart
+    rng = np.random.default_rng(16)
+    found = 0
+    for _ in range(200):
+        sig = rng.uniform(0.1, 50.0, 3)
+        den = rng.uniform(0.01, 1.0, 3)
+        fused = float(Fraction(float(den[0])) * Fraction(float(sig[0])))
+        c1 = float(Fraction(fused) + Fraction(float(den[1])) * Fraction(float(sig[1])))
+        u1 = fused + float(den[1]) * float(sig[1])
+        if c1 == u1:
+            continue
+        found += 1
+        p = _flat_nuclides(sig, den, [0.1] * 3)
+        lo, hi = min(c1, u1), max(c1, u1)
+        # target in [lo, hi): below the larger second sum only
+        want = 1 if c1 > lo else 2
+        assert oracle.pick_nuclide(p, 0, 1.0, lo, precision=0) == want
+    assert found > 0
 
 
 def test_macro_against_numpy_interp():
@@ -150,9 +232,9 @@ def test_macro_single_nuclide_is_exact_product():
     E = np.geomspace(1e-5, 2e7, 500)
     st, sa = oracle.macro(p, 0, E)
     for k, e in enumerate(E):
-        t = p.density[0] * oracle.micro(p, 0, e)
-        assert st[k] == t
-        assert sa[k] == t * p.f_abs[0]
+        sig = oracle.micro(p, 0, e)
+        assert st[k] == p.density[0] * sig
+        assert sa[k] == (p.density[0] * p.f_abs[0]) * sig
 
 
 def test_macro_permutation_within_summation_bound():
