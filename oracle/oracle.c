@@ -12,7 +12,8 @@
  * fma(a, b, c) it is the IEEE-754 fused multiply-add a * b + c with one
  * rounding (C99 fma; the GPU path issues the same operation): the binary64
  * lookup's interpolation and its density-weighted sums, the logarithm's
- * series, the position update and the scatter kinematics.
+ * series, the position update, the cylinder's quadratic and the scatter
+ * kinematics.
  *
  * What is computed (paper: Sec. 2 "Event-Based Parallelism" for the event /
  * history duality; Sec. 2 "Sorting" for the macroscopic cross-section lookup
@@ -364,10 +365,12 @@ typedef struct {
  * (entry) root.  Quadratic a d^2 + 2 k d + c = 0 in its stable forms. */
 double or_dist_cylinder(double dx, double dy, double u, double v, double r, int inside)
 {
-    double a = u * u + v * v;
-    double k = dx * u + dy * v;
-    double c = (dx * dx + dy * dy) - r * r;
-    double D = k * k - a * c;
+    /* a = u^2 + v^2, k = dx u + dy v, c = dx^2 + dy^2 - r^2, D = k^2 - a c,
+     * each product-plus-term one fused multiply-add */
+    double a = fma(u, u, v * v);
+    double k = fma(dx, u, dy * v);
+    double c = fma(dx, dx, dy * dy) - r * r;
+    double D = fma(k, k, -(a * c));
     if (inside) {
         if (a == 0.0) return INFINITY;
         if (D < 0.0) D = 0.0;

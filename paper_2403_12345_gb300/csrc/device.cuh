@@ -1368,15 +1368,16 @@ struct Cyl {
     int kind;   // 0: no crossing, 1: (sD - k) / a, 2: -c / (k + sD), 3: c / (sD - k)
 };
 
-// a = u * u + v * v and r2 = r * r come from the caller (they change with
-// the direction and the problem only).
+// a = u^2 + v^2 (one fused multiply-add) and r2 = r * r come from the
+// caller (they change with the direction and the problem only); k = dx u +
+// dy v, dx^2 + dy^2 and D = k^2 - a c are fused multiply-adds too.
 __device__ __forceinline__ Cyl cylinder_of(double dx, double dy, double u, double v, double a,
                                            double r2, bool inside) {
     Cyl q;
     q.a = a;
-    q.k = dx * u + dy * v;
-    q.c = (dx * dx + dy * dy) - r2;
-    q.D = q.k * q.k - q.a * q.c;
+    q.k = __fma_rn(dx, u, dy * v);
+    q.c = __fma_rn(dx, dx, dy * dy) - r2;
+    q.D = __fma_rn(q.k, q.k, -(q.a * q.c));
     bool a0 = (__double_as_longlong(q.a) << 1) == 0;
     if (inside) {
         if (is_neg(q.D)) q.D = 0.0;

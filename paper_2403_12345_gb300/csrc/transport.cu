@@ -717,7 +717,7 @@ __device__ __forceinline__ void score_warp(const Params& P, const Score& s) {
 
 // One flight (advance event): sample the distance to collision, find the
 // nearest surface of the current cell (ties: cylinder, x, y, z) and compare.
-// a_uv = u * u + v * v of the current direction (a reflection keeps it);
+// a_uv = u^2 + v^2 of the current direction (a reflection keeps it);
 // ebin = the tally energy bin of pt.E.
 // Returns true for a collision, leaving the particle where it is: the move
 // by -ln(xi) / Sigma_t and its track-length score are finish_flight's, run
@@ -1081,7 +1081,7 @@ __global__ void __launch_bounds__(256, 2) k_raytrace(Params P) {
                     slot = q[idx];
                     pt = P.B.p[slot];
                     stream_of(P.probs[pt.prob], pt, r);
-                    a_uv = pt.u * pt.u + pt.v * pt.v;   // fixed until the particle collides
+                    a_uv = __fma_rn(pt.u, pt.u, pt.v * pt.v);   // fixed until the particle collides
                     ebin = energy_bin(P.T, pt.E);        // so is the tally energy bin
                     flights = 0;
                     fw = 0.0;
@@ -1294,7 +1294,7 @@ __global__ void __launch_bounds__(256) k_tail(Params P) {
             if (lane == 0) {
                 double xi;
                 Score sg{-1, 0.0, 0.0};
-                bool col = fly(P, pr, pt, r, xi, pt.u * pt.u + pt.v * pt.v, energy_bin(P.T, pt.E),
+                bool col = fly(P, pr, pt, r, xi, __fma_rn(pt.u, pt.u, pt.v * pt.v), energy_bin(P.T, pt.E),
                                sg);
                 score_now(P, sg);
                 ++nf;
