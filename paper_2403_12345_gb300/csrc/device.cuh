@@ -505,6 +505,12 @@ __device__ __forceinline__ double ln_series(double x) {
     return __fma_rn(de, 0x1.62e42fee00000p-1, __fma_rn(de, 0x1.a39ef35793c76p-33, lm));
 }
 
+// a < b for a, b in [+0, +inf]: such values order like their bit patterns,
+// so the comparison runs on the integer units, not the scarce binary64 pipe.
+__device__ __forceinline__ bool lt_nonneg(double a, double b) {
+    return (unsigned long long)__double_as_longlong(a) < (unsigned long long)__double_as_longlong(b);
+}
+
 // ---------------------------------------------------------------- lookup
 // The lookup stores the running sum after every cum_group<PREC>() entries of
 // the material (checkpoints); the collision recomputes at most that many
@@ -1225,7 +1231,7 @@ __device__ __forceinline__ int32_t pick_nuclide(const Tables& T, int precision, 
             double sig = micro64(T, q, E);
             cum = __fma_rn(N, sig, cum);
             if (N > 0.0 && sig > 0.0) last = i;
-            if (target < cum) return i;
+            if (lt_nonneg(target, cum)) return i;
         }
     } else {
         float cum = 0.0f;
@@ -1234,7 +1240,7 @@ __device__ __forceinline__ int32_t pick_nuclide(const Tables& T, int precision, 
             float t = __ldg(&T.d32[q].density) * micro32(T, q, E);
             cum = cum + t;
             if (t > 0.0f) last = i;
-            if (target < (double)cum) return i;
+            if (lt_nonneg(target, (double)cum)) return i;
         }
     }
     return last >= 0 ? last : __ldg(T.nuc_id + q0);
@@ -1259,7 +1265,7 @@ __device__ __forceinline__ int32_t pick_from_sums(const Tables& T, int32_t m, co
     while (lo < hi) {
         int32_t mid = (lo + hi) >> 1;
         double v = PREC == GBMC_FP64 ? c64[(int64_t)mid * stride] : (double)c32[(int64_t)mid * stride];
-        if (target < v)
+        if (lt_nonneg(target, v))
             hi = mid;
         else
             lo = mid + 1;
@@ -1272,14 +1278,14 @@ __device__ __forceinline__ int32_t pick_from_sums(const Tables& T, int32_t m, co
         for (int32_t k = k0; k < k1; ++k) {
             int32_t i = __ldg(T.nuc_id + q0 + k);
             at = __fma_rn(__ldg(T.density + q0 + k), micro64(T, q0 + k, E), at);
-            if (target < at) return i;
+            if (lt_nonneg(target, at)) return i;
         }
     } else {
         float at = lo > 0 ? c32[(int64_t)(lo - 1) * stride] : 0.0f;
         for (int32_t k = k0; k < k1; ++k) {
             float t = __ldg(&T.d32[q0 + k].density) * micro32(T, q0 + k, E);
             at = at + t;
-            if (target < (double)at) return __ldg(T.nuc_id + q0 + k);
+            if (lt_nonneg(target, (double)at)) return __ldg(T.nuc_id + q0 + k);
         }
     }
     return -1;   // not reached: the group's checkpoint exceeds the target
@@ -1454,10 +1460,11 @@ __device__ __forceinline__ void elastic(double E, double A, double mu, double& E
 __device__ __forceinline__ void rotate(double& u, double& v, double& w, double mu, double cphi,
                                        double sphi) {
     double m2 = __fma_rn(-mu, mu, 1.0);
-    if (m2 < 0.0) m2 = 0.0;
+    if (is_neg(m2)) m2 = 0.0;
     double st = sqrt(m2);
     double u0 = u, v0 = v, w0 = w;
-    if (fabs(w0) < 0.9999999999) {
+    const unsigned long long aw = (unsigned long long)__double_as_longlong(w0) & 0x7FFFFFFFFFFFFFFFull;
+    if (aw < (unsigned long long)__double_as_longlong(0.9999999999)) {   // |w| < 1 - 1e-10
         double q = sqrt(__fma_rn(-w0, w0, 1.0));
         u = __fma_rn(mu, u0, (st * __fma_rn(u0 * w0, cphi, -(v0 * sphi))) / q);
         v = __fma_rn(mu, v0, (st * __fma_rn(v0 * w0, cphi, u0 * sphi)) / q);
@@ -1465,7 +1472,7 @@ __device__ __forceinline__ void rotate(double& u, double& v, double& w, double m
     } else {
         u = st * cphi;
         v = st * sphi;
-        w = w0 > 0.0 ? mu : -mu;
+        w = is_pos(w0) ? mu : -mu;
     }
 }
 
@@ -1476,8 +1483,9 @@ __device__ __forceinline__ double disk_pair(Stream& r, double& a, double& b) {
     for (;;) {
         a = __fma_rn(2.0, r.next(), -1.0);
         b = __fma_rn(2.0, r.next(), -1.0);
-        double s = __fma_rn(a, a, b * b);
-        if (s > 0.0 && s < 1.0) return s;
+        double s = __fma_rn(a, a, b * b);   // >= +0: 0 < s < 1 on its bits
+        const unsigned long long sb = (unsigned long long)__double_as_longlong(s);
+        if (sb != 0ull && sb < 0x3FF0000000000000ull) return s;
     }
 }
 

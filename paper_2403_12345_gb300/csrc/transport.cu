@@ -995,7 +995,7 @@ __device__ __forceinline__ int collide(const Params& P, const DevProblem& pr, Pa
     if (P.sites) bank_sites(P, pt, nuc, r);
     int status = 0;
     double xa = r.next();
-    if (xa < __ldg(P.T.f_abs + nuc)) {
+    if (lt_nonneg(xa, __ldg(P.T.f_abs + nuc))) {   // f_abs in [0, 1]
         status = GBMC_STATUS_ABSORBED;
     } else {
         double mu = __fma_rn(2.0, r.next(), -1.0);   // = 2 xi - 1 (2 xi is exact)
@@ -1011,7 +1011,7 @@ __device__ __forceinline__ int collide(const Params& P, const DevProblem& pr, Pa
         pt.v = v;
         pt.w = w;
         pt.E = E1;
-        if (pt.E < pr.g.E_cut)
+        if (lt_nonneg(pt.E, pr.g.E_cut))   // both positive
             status = GBMC_STATUS_CUTOFF;
         else
             status = ww_check(P, pr, pt, r, wo);
