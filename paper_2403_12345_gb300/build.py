@@ -1,8 +1,9 @@
 """Build libgbmc.so (the C-ABI transport library) for sm_103a, in-tree.
 
 Translation units compile in parallel with nvcc; no FMA contraction
-(-fmad=false), so every expression rounds as written.  The shared library
-links the CUDA runtime statically.
+(-fmad=false), so every expression rounds as written and the only fused
+multiply-adds are the explicit __fma_rn calls of the source.  The shared
+library links the CUDA runtime statically.
 """
 import concurrent.futures as cf
 import os

@@ -3,10 +3,12 @@
 // lookup, surface distances and elastic-scatter kinematics.
 //
 // Every binary64/binary32 expression here is compiled without FMA
-// contraction (-fmad=false) and evaluated exactly in the written order, so a
-// particle's random walk is a pure function of its inputs and matches a
-// serial history-based evaluation of the same definitions bit for bit
-// (reproducibility between CPU and GPU up to summation order: Sec. 4.3).
+// contraction (-fmad=false) and evaluated exactly in the written order; the
+// fused multiply-adds of the method's reading are written out (__fma_rn, one
+// rounding). A particle's random walk is therefore a pure function of its
+// inputs and matches a serial history-based evaluation of the same
+// definitions bit for bit (reproducibility between CPU and GPU up to
+// summation order: Sec. 4.3).
 #pragma once
 
 #include <cstdint>
