@@ -31,8 +31,11 @@ BRACKET_BYTES = {0: 32, 1: 16}    # E_j, E_j+1, s_j, s_j+1
 # binary64 operations a micro lookup must perform (the workload
 # description's count: the two differences and the quotient of the
 # interpolation factor, its multiply-add, and the multiply-add of the sum);
-# the kernel issues fewer on the binary64 pipe (part runs on the integer units)
+# the kernel issues fewer on the binary64 pipe: the interpolation's and the
+# sum's fused multiply-adds, while E - E_k and the quotient run exactly on the
+# integer units, so against the binary64 rate the algorithmic count can pass 1
 ALGO_FP64_OPS_PER_MICRO = 6
+ISSUED_FP64_PER_MICRO = 2         # binary64 instructions the kernel issues per micro lookup (Sigma_t)
 LOOKUP_IO_BYTES = 28              # per macro lookup: E 8, material 4, sigma_t and sigma_a 16
 # kernels an iteration launches: plan, source, 2 sort, lookup, ray trace, collision
 ITER_KERNELS = {0: 7, 1: 7}
@@ -378,7 +381,10 @@ def stress_measure(prec, nq, steps, warmup, stream, local, seed_offset=0, e2e_st
                      "frac": ops / (lk_ms * 1e-3) / fp64_rate,
                      "peak_source": "measured: gbmc_measure_fp64_rate (binary64 fused "
                                     "multiply-add chains, CUDA events)",
-                     "ops_per_micro_lookup": ALGO_FP64_OPS_PER_MICRO}
+                     "ops_per_micro_lookup": ALGO_FP64_OPS_PER_MICRO,
+                     "issued_binary64_frac": nq * micro_per * ISSUED_FP64_PER_MICRO
+                     / (lk_ms * 1e-3) / fp64_rate,
+                     "issued_per_micro_lookup": ISSUED_FP64_PER_MICRO}
     else:
         fp64_roof = None
     hE = torch.from_numpy(E).pin_memory()
@@ -1095,9 +1101,10 @@ def main():
                       "at the single-loop autotuned settings",
             "table_bytes": int(prob.table_bytes(args.precision)), "l2_capacity": int(l2_size)}
     if args.precision == 0:
-        # binary64 tables: the lookup is bound by the binary64 pipe (ncu: 73%
-        # of it busy on full queues, DRAM under 10%); algorithmic operations
-        # against the rate the library's own probe measures
+        # binary64 tables: the algorithmic operations against the rate the
+        # library's own probe measures (ncu on a full queue: DRAM under 10%,
+        # binary64 pipe 41%, integer ALU 74%, issue 71%), and the binary64
+        # instructions the kernel issues against the same rate
         fp64_rate = ctx.measure_fp64_rate()
         ops = pst["micro_lookups"] * ALGO_FP64_OPS_PER_MICRO
         hbm_rec = {k: roof[k] for k in ("achieved", "peak", "unit", "frac", "peak_source",
@@ -1108,7 +1115,10 @@ def main():
                      "peak_source": "measured: gbmc_measure_fp64_rate (binary64 fused "
                                     "multiply-add chains, CUDA events)",
                      "algorithmic_ops_per_launch": ops / max(lk_n, 1),
-                     "ops_per_micro_lookup": ALGO_FP64_OPS_PER_MICRO, "hbm": hbm_rec})
+                     "ops_per_micro_lookup": ALGO_FP64_OPS_PER_MICRO,
+                     "issued_binary64_frac": pst["micro_lookups"] * ISSUED_FP64_PER_MICRO
+                     / (lk_ms * 1e-3) / fp64_rate,
+                     "issued_per_micro_lookup": ISSUED_FP64_PER_MICRO, "hbm": hbm_rec})
         del roof["algorithmic_bytes_per_launch"]
     if timed_opts != single_opts:
         # the same batch at the settings the concurrent loops were timed at
