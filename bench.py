@@ -1022,28 +1022,23 @@ def main():
     # as in the timed region
     e2e_steps = max(1, args.e2e_steps, min(loops, args.steps))
 
-    def pinned(shape, dtype):
-        return torch.empty(shape, dtype=dtype, pin_memory=True).numpy()
-
-    # result buffers in pinned host memory, one set per e2e batch and problem
-    # (the copies of all batches are in flight together), allocated before
-    # the timed region
+    # result buffers in page-locked host memory from the library's allocator
+    # (gbmc_host_alloc), one set per e2e batch and problem (the copies of all
+    # batches are in flight together), allocated before the timed region
     def batch_dests():
-        # one pinned array per result field for the whole batch, each
-        # problem's destination a contiguous slice of it (the library then
-        # copies a run's results in one piece per field)
+        # one array per result field for the whole batch, each problem's
+        # destination a contiguous slice of it (the library then copies a
+        # run's results in one piece per field)
         ncs = [gbmc._n_cells(geoms[k]) * prob.n_bins for k in range(n_geo)]
-        spec = {"flux": (torch.float64, ncs), "counts": (torch.int64, [gbmc.NSCAL] * n_geo),
-                "weights": (torch.float64, [gbmc.NSCAL] * n_geo),
-                "n_coll": (torch.int32, counts), "status": (torch.int8, counts),
-                "n_flights": (torch.int32, counts), "n_draws": (torch.int32, counts),
-                "E": (torch.float64, counts), "x": (torch.float64, counts),
-                "y": (torch.float64, counts), "z": (torch.float64, counts)}
+        spec = {"flux": (np.float64, ncs), "counts": (np.int64, [gbmc.NSCAL] * n_geo),
+                "weights": (np.float64, [gbmc.NSCAL] * n_geo),
+                "n_coll": (np.int32, counts), "status": (np.int8, counts),
+                "n_flights": (np.int32, counts), "n_draws": (np.uint32, counts),
+                "E": (np.float64, counts), "x": (np.float64, counts),
+                "y": (np.float64, counts), "z": (np.float64, counts)}
         out = [dict() for _ in range(n_geo)]
         for name, (dt, sizes) in spec.items():
-            whole = pinned(int(sum(sizes)), dt)
-            if name == "n_draws":
-                whole = whole.view(np.uint32)
+            whole = gbmc.host_array(int(sum(sizes)), dt)
             at = 0
             for k in range(n_geo):
                 out[k][name] = whole[at:at + sizes[k]]

@@ -320,6 +320,18 @@ int gbmc_run_concurrent_to_host(gbmc_ctx *ctx, int32_t n_prob, const gbmc_proble
                                 int32_t n_loops, int32_t per_run, const gbmc_host_results *dst,
                                 void *stream);
 
+/* Page-locked host memory for result destinations (the paper has no
+ * counterpart; the overlap of copies with compute that its streams give
+ * needs such memory).  gbmc_host_alloc stores in *ptr a HOST pointer to
+ * `bytes` bytes (bytes >= 1) of page-locked memory from cudaHostAlloc with
+ * default flags, aligned for any element type, usable as any destination
+ * of gbmc_host_results and by plain host code; the caller owns it and
+ * releases it with gbmc_host_free.  Errors: ptr NULL or bytes 0 -> INVALID_ARG; the
+ * allocation failing -> OOM (*ptr is then NULL).  gbmc_host_free(NULL) is
+ * a no-op; freeing another pointer is undefined. */
+int gbmc_host_alloc(size_t bytes, void **ptr);
+int gbmc_host_free(void *ptr);
+
 /* Synchronize the last run's stream and copy the tallies of problem slot
  * `slot`: flux [n_cells * n_bins] (cell-major; n_flux must equal it; NULL
  * skips), counts [GBMC_NSCAL] and weights [GBMC_NSCAL] (NULL skips).

@@ -1531,6 +1531,23 @@ int gbmc_run_concurrent(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs, 
     return run_concurrent(c, n_prob, probs, n_loops, per_run, nullptr, stream);
 }
 
+int gbmc_host_alloc(size_t bytes, void** ptr) {
+    if (!ptr || bytes == 0) return GBMC_ERR_INVALID_ARG;
+    *ptr = nullptr;
+    void* p = nullptr;
+    if (cudaHostAlloc(&p, bytes, cudaHostAllocDefault) != cudaSuccess || !p) {
+        cudaGetLastError();   // clear the runtime's last-error state
+        return GBMC_ERR_OOM;
+    }
+    *ptr = p;
+    return GBMC_OK;
+}
+
+int gbmc_host_free(void* ptr) {
+    if (!ptr) return GBMC_OK;
+    return cudaFreeHost(ptr) == cudaSuccess ? GBMC_OK : GBMC_ERR_CUDA;
+}
+
 int gbmc_run_concurrent_to_host(gbmc_ctx* c, int32_t n_prob, const gbmc_problem* probs,
                                 int32_t n_loops, int32_t per_run, const gbmc_host_results* dst,
                                 void* stream) {

@@ -42,7 +42,7 @@ EXPORTS = ["gbmc_default_options", "gbmc_create", "gbmc_destroy", "gbmc_last_err
            "gbmc_get_weight_windows", "gbmc_set_reaction_tally", "gbmc_read_reaction_tally",
            "gbmc_load_fission", "gbmc_set_eigen", "gbmc_read_bank", "gbmc_set_source_bank",
            "gbmc_check_division", "gbmc_run_concurrent", "gbmc_measure_fp64_rate",
-           "gbmc_run_concurrent_to_host"]
+           "gbmc_run_concurrent_to_host", "gbmc_host_alloc", "gbmc_host_free"]
 MLP_HIDDEN = 64
 MLP_NPARAM = 4545
 NOALLOC_MAX_QUERIES = 1 << 20
@@ -186,11 +186,44 @@ def lib():
         L.gbmc_profile_problems.argtypes = [vp, C.c_int32, _P(Problem), vp, _P(KernelTimes),
                                             C.c_int32, _P(C.c_double), _P(C.c_int32),
                                             _P(C.c_int32)]
+        L.gbmc_host_alloc.argtypes = [C.c_size_t, _P(vp)]
+        L.gbmc_host_free.argtypes = [vp]
         for name in EXPORTS:
             if name != "gbmc_last_error":
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
+
+
+class _HostBlock:
+    """One gbmc_host_alloc allocation seen as a 1-D array (numpy's array
+    interface); numpy arrays made from it keep it alive, and it is freed
+    with the last of them."""
+
+    def __init__(self, n: int, dt: np.dtype):
+        ptr = C.c_void_p()
+        nbytes = max(n * dt.itemsize, 1)
+        rc = lib().gbmc_host_alloc(C.c_size_t(nbytes), C.byref(ptr))
+        if rc:
+            raise GbmcError(rc, f"gbmc_host_alloc of {nbytes} bytes failed")
+        self.ptr = ptr.value
+        self.__array_interface__ = {"data": (self.ptr, False), "shape": (n,),
+                                    "typestr": dt.str, "version": 3}
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            try:
+                lib().gbmc_host_free(C.c_void_p(self.ptr))
+            except Exception:   # interpreter shutdown: the process releases it
+                pass
+            self.ptr = None
+
+
+def host_array(n: int, dtype) -> np.ndarray:
+    """A numpy array of n elements in page-locked host memory from the
+    library's allocator (gbmc_host_alloc), e.g. for the destinations of
+    run_concurrent_to_host; the memory is freed with the last view of it."""
+    return np.asarray(_HostBlock(int(n), np.dtype(dtype)))
 
 
 def _arr(a, dtype):

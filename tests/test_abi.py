@@ -66,3 +66,14 @@ def test_create_without_gpu_fails_cleanly(built):
     with pytest.raises(gbmc.GbmcError) as e:
         gbmc.Context(0)
     assert e.value.code == gbmc.ERR_CUDA
+
+
+def test_host_alloc_argument_checks_without_gpu(built):
+    # gbmc_host_alloc checks its arguments before any CUDA call; freeing NULL
+    # is a no-op (no compute call is made)
+    from paper_2403_12345_gb300 import gbmc
+    L = gbmc.lib()
+    p = ctypes.c_void_p(1234)
+    assert L.gbmc_host_alloc(ctypes.c_size_t(0), ctypes.byref(p)) == gbmc.ERR_INVALID_ARG
+    assert L.gbmc_host_alloc(ctypes.c_size_t(64), None) == gbmc.ERR_INVALID_ARG
+    assert L.gbmc_host_free(None) == 0

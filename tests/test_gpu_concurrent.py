@@ -206,3 +206,48 @@ def test_adjacent_host_destinations_match_the_readers():
         assert_outcomes_equal(dests[4], ref, label="problem 4")
     finally:
         ctx.close()
+
+
+def test_library_host_memory_destinations():
+    """Destinations from the library's page-locked allocator (host_array,
+    gbmc_host_alloc) receive what the synchronous readers return; the arrays
+    are ordinary numpy arrays and are freed with their last view."""
+    import gc
+    import torch
+    p = synth.make_config(4, n_problems=4, grid_scale=0.02)
+    for k in range(4):
+        p.n_particles[k] = 700 + 211 * k
+    ctx = make_ctx(p, (gbmc.FP32,), precision=gbmc.FP32)
+    try:
+        probs = [gpu_problem(p, geom_index=k, problem_index=k, batch=9) for k in range(4)]
+        ns = [int(n) for n in p.n_particles[:4]]
+        ncs = [gbmc._n_cells(pr.geom) * ctx.n_bins for pr in probs]
+        fields = {"flux": (np.float64, ncs), "counts": (np.int64, [gbmc.NSCAL] * 4),
+                  "weights": (np.float64, [gbmc.NSCAL] * 4), "n_coll": (np.int32, ns),
+                  "status": (np.int8, ns), "n_flights": (np.int32, ns),
+                  "n_draws": (np.uint32, ns), "E": (np.float64, ns), "x": (np.float64, ns),
+                  "y": (np.float64, ns), "z": (np.float64, ns)}
+        dests = [dict() for _ in range(4)]
+        for name, (dt, sizes) in fields.items():
+            whole = gbmc.host_array(sum(sizes), dt)
+            assert whole.dtype == np.dtype(dt) and whole.size == sum(sizes)
+            whole[:] = 0
+            at = 0
+            for k in range(4):
+                dests[k][name] = whole[at:at + sizes[k]]
+                at += sizes[k]
+        stream = torch.cuda.Stream()
+        ctx.run_concurrent_to_host(probs, n_loops=2, dests=dests, per_run=2, stream=stream)
+        stream.synchronize()
+        for k in range(4):
+            flux, counts, weights = ctx.read_tallies(k)
+            assert np.array_equal(flux.ravel(), dests[k]["flux"])
+            assert np.array_equal(counts, dests[k]["counts"])
+            assert np.array_equal(weights, dests[k]["weights"])
+            out = ctx.read_outcomes(k, 0, ns[k])
+            for name in ("n_coll", "status", "n_flights", "n_draws", "E", "x", "y", "z"):
+                assert np.array_equal(out[name], dests[k][name]), (k, name)
+        del dests
+        gc.collect()
+    finally:
+        ctx.close()
