@@ -209,6 +209,22 @@ def test_pick_uses_the_fused_running_sums():
     assert found > 0
 
 
+def test_pick_beyond_every_running_sum_takes_the_last_positive_term():
+    # binary64: a target at or above the final running sum (rounding can put
+    # xi Sigma_t there) picks the last nuclide whose term is positive, here
+    # the last listed one; a target below the first sum picks the first
+    sig, den = [2.0, 3.0, 5.0], [0.25, 0.5, 0.125]
+    p = _flat_nuclides(sig, den, [0.1] * 3)
+    total, _ = oracle.macro(p, 0, np.array([1.0]))
+    assert oracle.pick_nuclide(p, 0, 1.0, float(total[0]), precision=0) == 2
+    assert oracle.pick_nuclide(p, 0, 1.0, float(total[0]) * 2.0, precision=0) == 2
+    assert oracle.pick_nuclide(p, 0, 1.0, 0.0, precision=0) == 0
+    # exact sums here: 0.5, 2.0, 2.625
+    assert float(total[0]) == 2.625
+    assert oracle.pick_nuclide(p, 0, 1.0, 0.5, precision=0) == 1
+    assert oracle.pick_nuclide(p, 0, 1.0, 2.0, precision=0) == 2
+
+
 def test_macro_against_numpy_interp():
     p = synth.make_config(2, n_particles=1, grid_scale=0.05)
     rng = np.random.default_rng(5)
